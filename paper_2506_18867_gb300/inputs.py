@@ -1,0 +1,231 @@
+"""Seeded synthetic cloth states shaped like the paper's scenes.
+
+This module is the only code shared by the CUDA path, the CPU oracle and the
+bench: it draws inputs and holds none of the method's arithmetic (no basis
+functions, quadrature, energies or derivatives).  Random numbers come from
+splitmix64 (Steele, Lea & Flood 2014, as published by Vigna) driven by a
+counter, turned into uniforms with the top 53 bits and into normals with the
+Box-Muller transform, so every array is reproducible on any machine and any
+numpy version.
+
+Geometry conventions
+--------------------
+* A patch has ``nu x nv`` control points (``nu, nv >= 5``) on open uniform
+  quadratic knot vectors ``(0,0,0,1,...,S,S,S)`` with ``S = n - 2`` spans per
+  axis (integer lattice starting at 0, Sec. 3.1.2).
+* Control point ``alpha = j * nu + i`` (``i`` along u, ``j`` along v).
+* ``rest`` is ``(nu*nv, 2)`` float64 material coordinates; ``C`` is
+  ``(nu*nv, 3)`` float64 world positions.
+* Flat rest states place control point ``(i, j)`` at the Greville abscissae
+  ``gamma = (0, 1/2, 3/2, ..., S-1/2, S)`` scaled to the patch size, the layout
+  drawn in the paper's reduced-quadrature figure (Fig. 3).
+
+Material mapping (a reading; the paper defers it to its supplement)
+--------------------------------------------------------------------
+``mu_st1 = mu_st2 = E h / 2``, ``mu_sh = G h / 2`` with ``G = E / (2 (1 + nu))``,
+``mu_bd = E h^3 / (12 (1 - nu^2))`` and ``rho_area`` in kg/m^2.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """``n`` outputs of splitmix64 for counters ``offset+1 .. offset+n``."""
+    with np.errstate(over="ignore"):
+        ctr = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + ctr * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of splitmix64."""
+    return (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Standard normals by Box-Muller on consecutive uniform pairs."""
+    m = (n + 1) // 2
+    u = uniform(seed, 2 * m, 2 * offset)
+    u1 = 1.0 - u[0::2]  # (0, 1]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * m)
+    z[0::2] = r * np.cos(2.0 * math.pi * u2)
+    z[1::2] = r * np.sin(2.0 * math.pi * u2)
+    return z[:n]
+
+
+@dataclass
+class Material:
+    mu_st1: float
+    mu_st2: float
+    mu_sh: float
+    mu_bd: float
+    rho_area: float
+
+    @staticmethod
+    def from_engineering(E: float, nu: float, h: float, rho_area: float) -> "Material":
+        G = E / (2.0 * (1.0 + nu))
+        return Material(E * h / 2.0, E * h / 2.0, G * h / 2.0,
+                        E * h ** 3 / (12.0 * (1.0 - nu * nu)), rho_area)
+
+    def as_tuple(self):
+        return (self.mu_st1, self.mu_st2, self.mu_sh, self.mu_bd, self.rho_area)
+
+
+@dataclass
+class Patch:
+    """One synthetic cloth state: geometry, material, scene and current state."""
+    name: str
+    nu: int
+    nv: int
+    rest: np.ndarray            # (N, 2) float64
+    C: np.ndarray               # (N, 3) float64, current positions
+    Chat: np.ndarray            # (N, 3) float64, C^n + dt v^n
+    material: Material
+    dt: float
+    gravity: tuple
+    pinned: np.ndarray          # int32 control-point indices
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_cp(self) -> int:
+        return self.nu * self.nv
+
+    @property
+    def n_spans(self) -> int:
+        return (self.nu - 2) * (self.nv - 2)
+
+
+def greville(n: int) -> np.ndarray:
+    """Greville abscissae of the open uniform quadratic knot vector with n-2 spans."""
+    S = n - 2
+    g = np.empty(n)
+    g[0] = 0.0
+    g[-1] = float(S)
+    g[1:-1] = np.arange(n - 2) + 0.5
+    return g
+
+
+def flat_rest(nu: int, nv: int, Lu: float, Lv: float, angle: float = 0.0,
+              origin=(0.0, 0.0)) -> np.ndarray:
+    """Greville-placed flat rest control points, optionally rotated in the plane."""
+    gu = greville(nu) * (Lu / (nu - 2))
+    gv = greville(nv) * (Lv / (nv - 2))
+    X = np.empty((nv, nu, 2))
+    X[:, :, 0] = gu[None, :]
+    X[:, :, 1] = gv[:, None]
+    X = X.reshape(-1, 2)
+    if angle != 0.0:
+        c, s = math.cos(angle), math.sin(angle)
+        X = X @ np.array([[c, s], [-s, c]])
+    return X + np.asarray(origin)[None, :]
+
+
+def corner_pins_top(nu: int, nv: int) -> np.ndarray:
+    """The two control points at the v = max corners (the top corners)."""
+    return np.array([(nv - 1) * nu, (nv - 1) * nu + nu - 1], dtype=np.int32)
+
+
+def edge_pins_u0(nu: int, nv: int) -> np.ndarray:
+    """Every control point on the u = 0 edge (the x = 0 edge of a flat rest)."""
+    return (np.arange(nv, dtype=np.int32) * nu)
+
+
+def lift(rest: np.ndarray) -> np.ndarray:
+    C = np.zeros((rest.shape[0], 3))
+    C[:, :2] = rest
+    return C
+
+
+def config_square(seed: int = 1, n: int = 32) -> Patch:
+    """Square patch, 1 m x 1 m, seeded noise of 0.01 span + 2 mm wrinkle along x.
+
+    E = 1e5 Pa, nu = 0.3, h = 1 mm, 200 kg/m^2; dt = 0.01 s; gravity -y; the two
+    top corners pinned.  The wrinkle wavelength (8 spans) is a reading.
+    """
+    span = 1.0 / (n - 2)
+    rest = flat_rest(n, n, 1.0, 1.0)
+    C = lift(rest)
+    C += (0.01 * span) * normal(seed, C.size).reshape(C.shape)
+    lam = 8 * span
+    C[:, 2] += 0.002 * np.sin(2.0 * math.pi * rest[:, 0] / lam)
+    mat = Material.from_engineering(1e5, 0.3, 1e-3, 200.0)
+    return Patch(f"square{n}", n, n, rest, C, C.copy(), mat, 0.01, (0.0, -9.81, 0.0),
+                 corner_pins_top(n, n), {"seed": seed, "span_m": span})
+
+
+def config_drape(seed: int = 1, n: int = 256, mu_bd: float = 1e-5, size_m: float = 2.0) -> Patch:
+    """Drape: n x n patch, size_m square, sigma = 1 mm noise, u = 0 edge pinned, gravity -z."""
+    rest = flat_rest(n, n, size_m, size_m)
+    C = lift(rest)
+    C += 1e-3 * normal(seed, C.size).reshape(C.shape)
+    mat = Material.from_engineering(1e5, 0.3, 1e-3, 200.0)
+    mat.mu_bd = mu_bd
+    return Patch(f"drape{n}", n, n, rest, C, C.copy(), mat, 0.01, (0.0, 0.0, -9.81),
+                 edge_pins_u0(n, n), {"seed": seed, "mu_bd": mu_bd, "size_m": size_m})
+
+
+def wrinkle_field(seed: int, X: np.ndarray, span: float, k: int = 8) -> np.ndarray:
+    """Sum of k sinusoids: direction U[0, 2 pi), wavelength log-U[4, 64] spans,
+    amplitude U[1, 5] mm, phase U[0, 2 pi)."""
+    u = uniform(seed ^ 0x5EED, 4 * k)
+    z = np.zeros(X.shape[0])
+    for m in range(k):
+        th = 2.0 * math.pi * u[4 * m]
+        lam = span * math.exp(math.log(4.0) + u[4 * m + 1] * (math.log(64.0) - math.log(4.0)))
+        amp = 1e-3 + 4e-3 * u[4 * m + 2]
+        ph = 2.0 * math.pi * u[4 * m + 3]
+        z += amp * np.sin(2.0 * math.pi * (X[:, 0] * math.cos(th) + X[:, 1] * math.sin(th)) / lam + ph)
+    return z
+
+
+def config_wrinkle(seed: int = 1, n: int = 1024, size_m: float = 4.0, crop: int | None = None) -> Patch:
+    """Precision-sweep patch: n x n, size_m square, multi-frequency wrinkle field.
+
+    ``crop`` returns the leading ``crop x crop`` control points of the same
+    field (same span length), the oracle's sample of the full patch.
+    """
+    span = size_m / (n - 2)
+    m = n if crop is None else crop
+    rest = flat_rest(m, m, span * (m - 2), span * (m - 2))
+    C = lift(rest)
+    C[:, 2] += wrinkle_field(seed, rest, span)
+    mat = Material.from_engineering(1e5, 0.3, 1e-3, 200.0)
+    return Patch(f"wrinkle{n}" + (f"_crop{m}" if crop else ""), m, m, rest, C, C.copy(), mat, 0.01,
+                 (0.0, 0.0, -9.81), corner_pins_top(m, m), {"seed": seed, "span_m": span})
+
+
+def config_random_small(seed: int, nu: int, nv: int, angle: float | None = None,
+                        noise: float = 0.05, curved: float = 0.0) -> Patch:
+    """Small generic patch for parity tests: rotated (optionally curved) rest,
+    noisy world state, random material, a few pins."""
+    u = uniform(seed, 8)
+    if angle is None:
+        angle = 2.0 * math.pi * u[0]
+    Lu, Lv = 0.3 + 0.4 * u[1], 0.3 + 0.4 * u[2]
+    rest = flat_rest(nu, nv, Lu, Lv, angle=angle)
+    if curved != 0.0:
+        # smooth in-plane bend of the rest map: a curved, non-affine X(u, v)
+        g = rest - rest.mean(axis=0)
+        rest = rest + curved * np.stack([g[:, 1] ** 2, 0.5 * g[:, 0] ** 2], axis=1)
+    C = lift(rest)
+    span = min(Lu / (nu - 2), Lv / (nv - 2))
+    C += noise * span * normal(seed + 17, C.size).reshape(C.shape)
+    E = math.exp(math.log(1e4) + u[3] * (math.log(1e6) - math.log(1e4)))
+    mat = Material.from_engineering(E, 0.2 + 0.25 * u[4], 1e-3, 0.2 + u[5])
+    pins = np.array([0, nu - 1], dtype=np.int32)
+    Chat = C + 0.01 * span * normal(seed + 31, C.size).reshape(C.shape)
+    return Patch(f"rand{nu}x{nv}", nu, nv, rest, C, Chat, mat, 0.01, (0.0, -9.81, 0.0), pins,
+                 {"seed": seed, "span_m": span})

@@ -1,0 +1,208 @@
+/*
+ * bsc.h - C ABI of the GB300 (sm_103a) hot path of quadratic B-spline cloth
+ * FEM ("Efficient B-Spline Finite Elements for Cloth Simulation",
+ * arXiv 2506.18867).
+ *
+ * One Newton iteration of the paper's implicit-Euler incremental potential
+ * (Sec. 3.2, Eq. incremental_potential) evaluates FBW membrane energy
+ * (Sec. 4.1) and quadratic bending energy (Sec. 4.2) at the reduced
+ * quadrature points of every knot span, projects each span's 27x27 Hessian
+ * to PSD (projected Newton, Sec. 5.1), assembles the global Hessian (each
+ * control point couples to its 5x5 neighbourhood in 3x3 blocks, Sec. 5.2),
+ * and solves with preconditioned CG on that matrix.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Patch: nu x nv control points (nu, nv >= 5) on open uniform quadratic
+ *    knot vectors (0,0,0,1,...,S,S,S), S = n - 2 spans per axis (Sec. 3.1.2:
+ *    open, integer lattice, starting at 0).  Control point alpha = j*nu + i.
+ *  - Element type: double when the context was created with BSC_FP64, float
+ *    with BSC_FP32 ("T" below).  Energies are always double.
+ *  - Vectors of control-point data (positions C, gradients, x, y): three
+ *    contiguous planes of N = nu*nv elements of T (x plane, then y, then z);
+ *    component c of control point alpha is at index c*N + alpha.
+ *  - Global Hessian K (the "stencil"): 225 planes of N elements of T.  Entry
+ *    (r, c) of the 3x3 block coupling alpha = (i, j) to beta = (i+du, j+dv),
+ *    du, dv in [-2, 2], is at index ((slot*9) + 3*r + c)*N + alpha with
+ *    slot = (dv+2)*5 + (du+2).  Blocks reaching outside the grid are zero.
+ *  - Device pointers come from the caller (e.g. PyTorch tensors) and stay
+ *    owned by the caller; they must be 16-byte aligned.  The context owns
+ *    its quadrature tables, lumped masses, span workspace, internal K and
+ *    solver vectors (allocated once in bsc_create, freed in bsc_destroy).
+ *  - Every call is ordered on the context's CUDA stream.  Calls that return
+ *    a host value (energy, reports) synchronise that stream.
+ *  - Errors: every call returns a bsc_status; no exception or abort crosses
+ *    the ABI.  bsc_last_error() gives a message for the context (or, with a
+ *    NULL context, for the last failed bsc_create of this thread).
+ */
+#ifndef BSC_H
+#define BSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bsc_status {
+  BSC_OK = 0,
+  BSC_ERR_INVALID_ARG = 1,   /* bad size, pointer, knot vector or option */
+  BSC_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  BSC_ERR_OOM = 3,           /* device allocation failed in bsc_create */
+  BSC_ERR_NUMERIC = 4,       /* NaN/Inf in an energy, norm or projection */
+  BSC_ERR_NOT_CONVERGED = 5, /* PCG hit its iteration limit */
+  BSC_ERR_LINESEARCH = 6,    /* no decrease after max_line_search halvings */
+  BSC_ERR_TIMEOUT = 7        /* a bounded device-side wait ran out */
+} bsc_status;
+
+enum { BSC_FP64 = 0, BSC_FP32 = 1 };
+
+/* Quadrature rules: the paper's reduced rules (Sec. 4.1 membrane: dual-grid
+ * alternating 1x2 / 2x1 Gauss in the interior, 3x3 corner spans, 3x2 / 2x3
+ * side spans; Sec. 4.2 bending: one point per boundary span centre and per
+ * interior knot intersection, Fig. 3), or full per-span Gauss rules used by
+ * the paper's ablation (Sec. 6.5) and by tests. */
+enum { BSC_QUAD_REDUCED = 0, BSC_QUAD_GAUSS2 = 2, BSC_QUAD_GAUSS3 = 3 };
+
+/* Knot grid (Sec. 3.1.2).  knots_u / knots_v may be NULL; if given they must
+ * hold the open uniform integer knot vector of length nu+3 / nv+3. */
+typedef struct bsc_knot_grid {
+  int nu, nv;
+  const double* knots_u;
+  const double* knots_v;
+} bsc_knot_grid;
+
+/* FBW membrane stiffnesses mu_st1, mu_st2, mu_sh [N/m] (Eq. FBW stretching and
+ * shearing energy), bending stiffness mu_bd [N m] (Eq. general bending
+ * energy) and areal density rho_area [kg/m^2] for the lumped mass (Eq. lumped
+ * mass matrix). */
+typedef struct bsc_material {
+  double mu_st1, mu_st2, mu_sh, mu_bd, rho_area;
+} bsc_material;
+
+typedef struct bsc_quadrature {
+  int membrane; /* BSC_QUAD_* */
+  int bending;  /* BSC_QUAD_* */
+} bsc_quadrature;
+
+typedef struct bsc_options {
+  int precision;        /* BSC_FP64 or BSC_FP32: element type T of buffers and
+                           of span evaluation, assembly and SpMV; the SPD
+                           projection, energy sums and norms are FP64 always */
+  double dt;            /* > 0: implicit Euler step (inertia M/dt^2, Sec. 3.2);
+                           <= 0: static problem (no inertia; Chat ignored) */
+  double gravity[3];    /* m/s^2; body force m_alpha * gravity */
+  const int32_t* pinned; /* host array of Dirichlet control points (copied) */
+  int n_pinned;
+  int project;          /* default PSD projection flag for bsc_newton_step */
+  double pcg_rel_tol;   /* PCG stops when ||r|| <= tol * ||b|| (<= 0: 1e-8) */
+  int pcg_max_iter;     /* <= 0: 10000 */
+  int max_line_search;  /* halvings of alpha before BSC_ERR_LINESEARCH (<= 0: 30) */
+} bsc_options;
+
+typedef struct bsc_newton_report {
+  double E0;            /* incremental potential at the input C */
+  double E1;            /* at the accepted C + alpha d */
+  double alpha;         /* accepted step length (1, 1/2, 1/4, ...) */
+  double dir_inf;       /* ||d||_inf (the paper's stopping residual is dir_inf / dt) */
+  double pcg_rel_res;   /* final ||r|| / ||b|| of the linear solve */
+  int pcg_iters;
+  int ls_halvings;
+  int status;           /* bsc_status of the step */
+  int spans_projected;  /* spans whose Hessian had a negative eigenvalue */
+} bsc_newton_report;
+
+typedef struct bsc_ctx bsc_ctx;
+
+/* Build a context for one patch: copies the rest control points, builds the
+ * quadrature tables (basis values and derivatives, |det J|, dN/dX and the
+ * Laplacian coefficients at every quadrature point; Sec. 4.1, Eq. deformation
+ * gradient, Eq. Laplacian in parametric space) and the lumped masses on the
+ * device, and allocates all workspace.
+ *   g        knot grid, nu, nv >= 5
+ *   rest_xy  host, (nu*nv) x 2 doubles, row-major [alpha][X1, X2]; material
+ *            coordinates of the control points (Sec. 3.2); must give a
+ *            regular map (det dX/d(u,v) != 0 at every quadrature point)
+ *   m, q, o  see the structs above (o may not be NULL)
+ *   cuda_stream  cudaStream_t for every call (NULL = legacy default stream)
+ *   out      receives the context; NULL on failure. */
+bsc_status bsc_create(const bsc_knot_grid* g, const double* rest_xy, const bsc_material* m,
+                      const bsc_quadrature* q, const bsc_options* o, void* cuda_stream,
+                      bsc_ctx** out);
+
+/* Frees every device and host resource of the context (NULL is a no-op). */
+void bsc_destroy(bsc_ctx* ctx);
+
+/* Message of the last error of ctx; with ctx == NULL, of the last failed
+ * bsc_create on this thread.  Valid until the next call on ctx. */
+const char* bsc_last_error(const bsc_ctx* ctx);
+
+/* Change the stream the context launches on (NULL = legacy default). */
+bsc_status bsc_set_stream(bsc_ctx* ctx, void* cuda_stream);
+
+/* Incremental potential (Eq. incremental_potential with the lumped mass):
+ *   E(C) = sum_alpha m/(2 dt^2) |C - Chat|^2 - sum_alpha m g.C
+ *          + sum_spans (membrane + bending energy at the quadrature points).
+ * C_dev, Chat_dev: device, 3 planes of N (T); Chat ignored when dt <= 0.
+ * E_out: host double.  Synchronises the stream. */
+bsc_status bsc_energy(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, double* E_out);
+
+/* Gradient of E(C) into g_dev (device, 3 planes of N, T); entries of pinned
+ * control points are zero (Dirichlet elimination). */
+bsc_status bsc_gradient(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, void* g_dev);
+
+/* Global Hessian of E(C): sum over spans of the 27x27 span Hessian (projected
+ * to PSD when project != 0: V max(Lambda, 0) V^T of the span's summed
+ * membrane + bending Hessian, computed in FP64), gathered into the 5x5 block
+ * stencil in a fixed order without atomics, plus m/dt^2 I on the diagonal;
+ * rows and columns of pinned control points are replaced by the identity.
+ * K_dev: device, 225 planes of N (T), or NULL to keep K inside the context.
+ * The context remembers the matrix for bsc_spmv / bsc_solve. */
+bsc_status bsc_assemble_hessian(bsc_ctx* ctx, const void* C_dev, int project, void* K_dev);
+
+/* y = K x with K_dev (NULL = the last matrix assembled by this context).
+ * x_dev, y_dev: device, 3 planes of N (T), must not alias. */
+bsc_status bsc_spmv(bsc_ctx* ctx, const void* K_dev, const void* x_dev, void* y_dev);
+
+/* Solve K x = b with 3x3 block-Jacobi preconditioned CG (persistent
+ * cooperative kernel, FP64 dot products), starting from x = 0, until
+ * ||r|| <= rel_tol ||b|| or max_iter.  K_dev NULL = last assembled matrix.
+ * iters / rel_res (host, may be NULL) receive the iteration count and the
+ * final relative residual.  Synchronises the stream. */
+bsc_status bsc_solve(bsc_ctx* ctx, const void* K_dev, const void* b_dev, void* x_dev,
+                     double rel_tol, int max_iter, int* iters, double* rel_res);
+
+/* One projected Newton iteration (Sec. 5.1): gradient g and Hessian K (span
+ * projection per options.project) at C, d from K d = -g by PCG, then
+ * backtracking: alpha = 1, halved until E(C + alpha d) <= E(C), and
+ * C <- C + alpha d in place.  rep (host, may be NULL) receives the report.
+ * Synchronises the stream. */
+bsc_status bsc_newton_step(bsc_ctx* ctx, void* C_dev, const void* Chat_dev, bsc_newton_report* rep);
+
+/* ---- inspection entry points (parity tests, profiling) ------------------- */
+
+/* Per-span results of the last evaluation path: E_span (device, Nsp doubles),
+ * g_span (device, Nsp x 27 T, row-major [span][3*l + c]) and H_span (device,
+ * Nsp x 27 x 27 T, row-major) at C, projected when project != 0.  Span
+ * s = b*(nu-2) + a; local control point l = lj*3 + li.  Any output may be
+ * NULL. */
+bsc_status bsc_span_terms(bsc_ctx* ctx, const void* C_dev, int project, double* E_span,
+                          void* g_span, void* H_span);
+
+/* Quadrature tables, copied to host in FP64.  which = 0 membrane, 1 bending.
+ * Returns the point count through count; if out != NULL writes up to cap
+ * records of 25 doubles: [u, v, w, owner_a, owner_b, W = w |det J|, then for
+ * membrane g[9][2] = dN_l/dX_beta (18 values), for bending L[9] (the
+ * Laplacian coefficient of each control point, 9 values)], zero padded. */
+bsc_status bsc_quadrature_tables(bsc_ctx* ctx, int which, double* out, int cap, int* count);
+
+/* Lumped masses m_alpha (host, N doubles). */
+bsc_status bsc_lumped_mass(bsc_ctx* ctx, double* m_out);
+
+/* Sizes: N control points, Nsp spans, membrane / bending point counts. */
+bsc_status bsc_sizes(const bsc_ctx* ctx, int* n_cp, int* n_spans, int* n_mem, int* n_bend);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSC_H */

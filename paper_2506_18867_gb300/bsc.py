@@ -1,0 +1,267 @@
+"""Thin ctypes binding of the C ABI in include/bsc.h (argument marshalling only).
+
+Every step of the hot path runs in the CUDA kernels of ``libbsc.so``; this
+module only converts torch tensors to device pointers and structs.  Loading
+fails loudly when the library is missing: there is no CPU fallback.
+
+Layouts (see include/bsc.h): per-control-point vectors are ``(3, N)`` tensors
+(x, y, z planes), the stencil Hessian is ``(225, N)`` with plane index
+``slot * 9 + 3 * r + c`` and ``slot = (dv + 2) * 5 + (du + 2)``.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbsc.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_NOT_CONVERGED, ERR_LINESEARCH, ERR_TIMEOUT = range(8)
+FP64, FP32 = 0, 1
+QUAD_REDUCED, QUAD_GAUSS2, QUAD_GAUSS3 = 0, 2, 3
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5: "NOT_CONVERGED",
+                6: "LINESEARCH", 7: "TIMEOUT"}
+
+# Every entry point declared in include/bsc.h.
+EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc_energy", "bsc_gradient",
+           "bsc_assemble_hessian", "bsc_spmv", "bsc_solve", "bsc_newton_step", "bsc_span_terms",
+           "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes")
+
+
+class KnotGrid(ct.Structure):
+    _fields_ = [("nu", ct.c_int), ("nv", ct.c_int), ("knots_u", ct.POINTER(ct.c_double)),
+                ("knots_v", ct.POINTER(ct.c_double))]
+
+
+class Material(ct.Structure):
+    _fields_ = [("mu_st1", ct.c_double), ("mu_st2", ct.c_double), ("mu_sh", ct.c_double),
+                ("mu_bd", ct.c_double), ("rho_area", ct.c_double)]
+
+
+class Quadrature(ct.Structure):
+    _fields_ = [("membrane", ct.c_int), ("bending", ct.c_int)]
+
+
+class Options(ct.Structure):
+    _fields_ = [("precision", ct.c_int), ("dt", ct.c_double), ("gravity", ct.c_double * 3),
+                ("pinned", ct.POINTER(ct.c_int32)), ("n_pinned", ct.c_int), ("project", ct.c_int),
+                ("pcg_rel_tol", ct.c_double), ("pcg_max_iter", ct.c_int), ("max_line_search", ct.c_int)]
+
+
+class NewtonReport(ct.Structure):
+    _fields_ = [("E0", ct.c_double), ("E1", ct.c_double), ("alpha", ct.c_double), ("dir_inf", ct.c_double),
+                ("pcg_rel_res", ct.c_double), ("pcg_iters", ct.c_int), ("ls_halvings", ct.c_int),
+                ("status", ct.c_int), ("spans_projected", ct.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BscError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libbsc.so (built by ``paper_2506_18867_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2506_18867_gb300.build` "
+                          "(there is no CPU fallback for the CUDA path)")
+    lib = ct.CDLL(path)
+    P, I, D, V = ct.c_void_p, ct.c_int, ct.c_double, ct.c_void_p
+    lib.bsc_create.argtypes = [ct.POINTER(KnotGrid), ct.POINTER(ct.c_double), ct.POINTER(Material),
+                               ct.POINTER(Quadrature), ct.POINTER(Options), V, ct.POINTER(P)]
+    lib.bsc_destroy.argtypes = [P]
+    lib.bsc_destroy.restype = None
+    lib.bsc_last_error.argtypes = [P]
+    lib.bsc_last_error.restype = ct.c_char_p
+    lib.bsc_set_stream.argtypes = [P, V]
+    lib.bsc_energy.argtypes = [P, V, V, ct.POINTER(D)]
+    lib.bsc_gradient.argtypes = [P, V, V, V]
+    lib.bsc_assemble_hessian.argtypes = [P, V, I, V]
+    lib.bsc_spmv.argtypes = [P, V, V, V]
+    lib.bsc_solve.argtypes = [P, V, V, V, D, I, ct.POINTER(I), ct.POINTER(D)]
+    lib.bsc_newton_step.argtypes = [P, V, V, ct.POINTER(NewtonReport)]
+    lib.bsc_span_terms.argtypes = [P, V, I, V, V, V]
+    lib.bsc_quadrature_tables.argtypes = [P, I, ct.POINTER(D), I, ct.POINTER(I)]
+    lib.bsc_lumped_mass.argtypes = [P, ct.POINTER(D)]
+    lib.bsc_sizes.argtypes = [P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(I), ct.POINTER(I)]
+    for name in EXPORTS:
+        if name not in ("bsc_destroy", "bsc_last_error"):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One patch on the GPU (wraps ``bsc_ctx``).  Tensors must be CUDA tensors
+    of the context's dtype, contiguous, in the layouts of include/bsc.h."""
+
+    def __init__(self, nu, nv, rest, material, precision=FP64, dt=0.01, gravity=(0.0, -9.81, 0.0),
+                 pinned=(), project=True, quadrature=(QUAD_REDUCED, QUAD_REDUCED), pcg_rel_tol=1e-8,
+                 pcg_max_iter=10000, max_line_search=30, stream=None):
+        import torch
+        self.torch = torch
+        lib = load()
+        self.nu, self.nv, self.N = int(nu), int(nv), int(nu) * int(nv)
+        self.n_spans = (self.nu - 2) * (self.nv - 2)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        self._rest = np.ascontiguousarray(np.asarray(rest, dtype=np.float64).reshape(self.N, 2))
+        mu = material.as_tuple() if hasattr(material, "as_tuple") else tuple(material)
+        self._mat = Material(*mu)
+        self._pins = np.ascontiguousarray(np.asarray(pinned, dtype=np.int32).ravel())
+        self._opt = Options(precision, float(dt), (ct.c_double * 3)(*gravity),
+                            self._pins.ctypes.data_as(ct.POINTER(ct.c_int32)), int(self._pins.size),
+                            int(bool(project)), float(pcg_rel_tol), int(pcg_max_iter), int(max_line_search))
+        self._quad = Quadrature(*quadrature)
+        self._grid = KnotGrid(self.nu, self.nv, None, None)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        h = ct.c_void_p()
+        st = lib.bsc_create(ct.byref(self._grid), self._rest.ctypes.data_as(ct.POINTER(ct.c_double)),
+                            ct.byref(self._mat), ct.byref(self._quad), ct.byref(self._opt),
+                            ct.c_void_p(stream), ct.byref(h))
+        if st != OK:
+            raise BscError(st, lib.bsc_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+
+    # -- helpers -----------------------------------------------------------
+    def _check(self, st):
+        if st != OK:
+            raise BscError(st, self._lib.bsc_last_error(self._h).decode())
+
+    def _vec(self, t, name):
+        if t is None:
+            return None
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.numel() == 3 * self.N):
+            raise ValueError(f"{name}: expected a contiguous CUDA {self.dtype} tensor with 3*N elements")
+        return t
+
+    def new_vec(self):
+        return self.torch.zeros((3, self.N), dtype=self.dtype, device="cuda")
+
+    def new_matrix(self):
+        return self.torch.zeros((225, self.N), dtype=self.dtype, device="cuda")
+
+    def to_device(self, arr_n3):
+        """(N, 3) host array -> (3, N) device tensor of the context dtype."""
+        a = np.ascontiguousarray(np.asarray(arr_n3, dtype=np.float64).reshape(self.N, 3).T)
+        return self.torch.from_numpy(a).to(device="cuda", dtype=self.dtype).contiguous()
+
+    # -- C ABI ---------------------------------------------------------------
+    def energy(self, C, Chat=None) -> float:
+        E = ct.c_double()
+        self._check(self._lib.bsc_energy(self._h, _ptr(self._vec(C, "C")), _ptr(self._vec(Chat, "Chat")),
+                                         ct.byref(E)))
+        return E.value
+
+    def gradient(self, C, Chat=None, out=None):
+        out = self.new_vec() if out is None else out
+        self._check(self._lib.bsc_gradient(self._h, _ptr(self._vec(C, "C")), _ptr(self._vec(Chat, "Chat")),
+                                           _ptr(self._vec(out, "g"))))
+        return out
+
+    def assemble_hessian(self, C, project=True, out=None, internal=False):
+        if internal:
+            self._check(self._lib.bsc_assemble_hessian(self._h, _ptr(self._vec(C, "C")), int(bool(project)), None))
+            return None
+        out = self.new_matrix() if out is None else out
+        self._check(self._lib.bsc_assemble_hessian(self._h, _ptr(self._vec(C, "C")), int(bool(project)),
+                                                   _ptr(out)))
+        return out
+
+    def spmv(self, x, K=None, out=None):
+        out = self.new_vec() if out is None else out
+        self._check(self._lib.bsc_spmv(self._h, _ptr(K), _ptr(self._vec(x, "x")), _ptr(self._vec(out, "y"))))
+        return out
+
+    def solve(self, b, K=None, rel_tol=1e-8, max_iter=10000, out=None):
+        out = self.new_vec() if out is None else out
+        it, rr = ct.c_int(), ct.c_double()
+        self._check(self._lib.bsc_solve(self._h, _ptr(K), _ptr(self._vec(b, "b")), _ptr(self._vec(out, "x")),
+                                        float(rel_tol), int(max_iter), ct.byref(it), ct.byref(rr)))
+        return out, it.value, rr.value
+
+    def newton_step(self, C, Chat=None):
+        rep = NewtonReport()
+        st = self._lib.bsc_newton_step(self._h, _ptr(self._vec(C, "C")), _ptr(self._vec(Chat, "Chat")),
+                                       ct.byref(rep))
+        self._check(st)
+        return rep
+
+    def newton_step_status(self, C, Chat=None):
+        """Like newton_step but returns (status, report) instead of raising."""
+        rep = NewtonReport()
+        st = self._lib.bsc_newton_step(self._h, _ptr(self._vec(C, "C")), _ptr(self._vec(Chat, "Chat")),
+                                       ct.byref(rep))
+        return st, rep
+
+    def span_terms(self, C, project=True):
+        t = self.torch
+        E = t.zeros(self.n_spans, dtype=t.float64, device="cuda")
+        g = t.zeros((self.n_spans, 27), dtype=self.dtype, device="cuda")
+        H = t.zeros((self.n_spans, 27, 27), dtype=self.dtype, device="cuda")
+        self._check(self._lib.bsc_span_terms(self._h, _ptr(self._vec(C, "C")), int(bool(project)), _ptr(E),
+                                             _ptr(g), _ptr(H)))
+        return E, g, H
+
+    def quadrature_tables(self, which):
+        n = ct.c_int()
+        self._check(self._lib.bsc_quadrature_tables(self._h, int(which), None, 0, ct.byref(n)))
+        out = np.zeros((n.value, 25))
+        self._check(self._lib.bsc_quadrature_tables(self._h, int(which),
+                                                    out.ctypes.data_as(ct.POINTER(ct.c_double)), n.value,
+                                                    ct.byref(n)))
+        return out
+
+    def lumped_mass(self):
+        m = np.zeros(self.N)
+        self._check(self._lib.bsc_lumped_mass(self._h, m.ctypes.data_as(ct.POINTER(ct.c_double))))
+        return m
+
+    def sizes(self):
+        a, b, c, d = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int()
+        self._check(self._lib.bsc_sizes(self._h, ct.byref(a), ct.byref(b), ct.byref(c), ct.byref(d)))
+        return a.value, b.value, c.value, d.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bsc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def context_for_patch(patch, precision=FP64, **kw):
+    """Context for an ``inputs.Patch`` (rest, material, scene)."""
+    kw.setdefault("dt", patch.dt)
+    kw.setdefault("gravity", patch.gravity)
+    kw.setdefault("pinned", patch.pinned)
+    return Context(patch.nu, patch.nv, patch.rest, patch.material, precision=precision, **kw)

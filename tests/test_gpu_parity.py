@@ -1,0 +1,200 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 parity bar: 1e-12 relative, norm-wise, on gradients, span Hessians and
+the assembled stencil Hessian (the tolerance the method's FP64 path is held
+to); tables and masses 1e-13.  FP32 results state their error against the
+oracle and are held to bounds derived from FP32 rounding (about 1e-7 per
+operation, amplified by the span-level cancellation of the strain).
+"""
+import numpy as np
+import pytest
+
+from paper_2506_18867_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - the gpu marker deselects these on CPU hosts
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2506_18867_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2506_18867_gb300 import bsc  # noqa: E402
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def to_n3(t):
+    return t.detach().double().cpu().numpy().reshape(3, -1).T.copy()
+
+
+def gpu_K_to_oracle(K, N):
+    """(225, N) planes -> (N, 25, 3, 3)."""
+    return K.detach().double().cpu().numpy().reshape(25, 3, 3, N).transpose(3, 0, 1, 2).copy()
+
+
+CASES = [
+    ("square32", lambda: inputs.config_square(1, 32)),
+    ("rand5x5", lambda: inputs.config_random_small(2, 5, 5)),
+    ("rand6x9", lambda: inputs.config_random_small(3, 6, 9, noise=0.2)),
+    ("rand13x7_curved", lambda: inputs.config_random_small(4, 13, 7, curved=0.6, noise=0.1)),
+    ("rand40x23", lambda: inputs.config_random_small(5, 40, 23, noise=0.05)),
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+def case(request, orc):
+    pat = request.param[1]()
+    prob = orc.Problem.from_patch(pat)
+    ctx = bsc.context_for_patch(pat, precision=bsc.FP64, pcg_rel_tol=1e-13)
+    yield pat, prob, ctx
+    ctx.close()
+
+
+def _sorted_records(rec):
+    key = np.lexsort((np.round(rec[:, 0], 9), np.round(rec[:, 1], 9), rec[:, 3], rec[:, 4]))
+    return rec[key]
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_quadrature_tables(case, which):
+    pat, prob, ctx = case
+    g = _sorted_records(ctx.quadrature_tables(which))
+    o_pts = prob.quad_points(which)
+    o_tab = prob.point_tables(which)
+    o = _sorted_records(np.concatenate([o_pts, o_tab], axis=1))
+    assert g.shape[0] == o.shape[0]
+    np.testing.assert_array_equal(g[:, 3:5], o[:, 3:5])          # owner spans, exact
+    np.testing.assert_allclose(g[:, 0:3], o[:, 0:3], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(g[:, 5], o[:, 5], rtol=1e-13)     # W = w |det J|
+    ncol = 18 if which == 0 else 9
+    assert rel(g[:, 6:6 + ncol], o[:, 6:6 + ncol]) < 1e-13
+
+
+def test_lumped_mass(case):
+    pat, prob, ctx = case
+    assert rel(ctx.lumped_mass(), prob.lumped_mass()) < 1e-13
+
+
+@pytest.mark.parametrize("project", [False, True])
+def test_span_terms_fp64(case, project):
+    pat, prob, ctx = case
+    C = ctx.to_device(pat.C)
+    E, g, H = ctx.span_terms(C, project=project)
+    oE, og, oH = prob.span_eval(pat.C)
+    if project:
+        from oracle import project_psd
+        oH = np.stack([project_psd(h)[0] for h in oH])
+    assert rel(E.cpu().numpy(), oE) < 1e-12
+    assert rel(g.cpu().numpy(), og) < 1e-12
+    assert rel(H.cpu().numpy(), oH) < 1e-12
+    Hg = H.cpu().numpy()
+    assert np.abs(Hg - Hg.transpose(0, 2, 1)).max() == 0.0
+
+
+def test_energy_gradient_hessian_fp64(case, orc):
+    pat, prob, ctx = case
+    sc = orc.Scene.from_patch(pat, project=True)
+    oE, og, oK = orc.evaluate(prob, sc, pat.C, pat.Chat)
+    C, Ch = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+    E = ctx.energy(C, Ch)
+    assert abs(E - oE) <= 1e-12 * max(abs(oE), 1e-30) * 10
+    g = to_n3(ctx.gradient(C, Ch))
+    assert rel(g, og) < 1e-12
+    K = gpu_K_to_oracle(ctx.assemble_hessian(C, project=True), pat.n_cp)
+    assert rel(K, oK) < 1e-12
+    sc0 = orc.Scene.from_patch(pat, project=False)
+    _, _, oK0 = orc.evaluate(prob, sc0, pat.C, pat.Chat, want_g=False)
+    K0 = gpu_K_to_oracle(ctx.assemble_hessian(C, project=False), pat.n_cp)
+    assert rel(K0, oK0) < 1e-12
+
+
+def test_spmv_and_solve_fp64(case, orc):
+    pat, prob, ctx = case
+    sc = orc.Scene.from_patch(pat, project=True)
+    _, og, oK = orc.evaluate(prob, sc, pat.C, pat.Chat)
+    C = ctx.to_device(pat.C)
+    Kd = ctx.assemble_hessian(C, project=True)
+    x = np.random.default_rng(7).standard_normal((pat.n_cp, 3))
+    y = to_n3(ctx.spmv(ctx.to_device(x), K=Kd))
+    assert rel(y, orc.stencil_matvec(pat.nu, pat.nv, oK, x)) < 1e-13
+    b = -og
+    xs, it, rr = ctx.solve(ctx.to_device(b), K=Kd, rel_tol=1e-13)
+    assert rr <= 1e-13 and it > 0
+    want = orc.solve_banded(pat.nu, pat.nv, oK, b) if pat.n_cp <= 4096 else orc.solve_pcg(
+        pat.nu, pat.nv, oK, b, 1e-14)[0]
+    assert rel(to_n3(xs), want) < 1e-10
+
+
+def test_newton_step_fp64(case, orc):
+    pat, prob, ctx = case
+    sc = orc.Scene.from_patch(pat, project=True)
+    oC, orep = orc.newton_step(prob, sc, pat.C, pat.Chat, solver=0 if pat.n_cp <= 4096 else 1, pcg_tol=1e-14)
+    C, Ch = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+    rep = ctx.newton_step(C, Ch)
+    assert rep.status == 0 and orep.status == 0
+    assert rep.alpha == orep.alpha
+    assert abs(rep.E0 - orep.E0) <= 1e-12 * abs(orep.E0) * 10
+    width = np.ptp(pat.rest, axis=0).max()
+    assert np.abs(to_n3(C) - oC).max() <= 1e-10 * width
+    assert rel(to_n3(C) - pat.C, oC - pat.C) < 1e-9
+
+
+def test_deterministic_bitwise(case):
+    pat, prob, ctx = case
+    C = ctx.to_device(pat.C)
+    K1 = ctx.assemble_hessian(C, project=True).clone()
+    K2 = ctx.assemble_hessian(C, project=True)
+    assert torch.equal(K1, K2)
+    g1 = ctx.gradient(C, ctx.to_device(pat.Chat)).clone()
+    assert torch.equal(g1, ctx.gradient(C, ctx.to_device(pat.Chat)))
+
+
+@pytest.mark.parametrize("rule", [2, 3])
+def test_full_gauss_rules(orc, rule):
+    pat = inputs.config_random_small(8, 9, 11, noise=0.1)
+    prob = orc.Problem.from_patch(pat, mem_rule=rule, bend_rule=rule)
+    with bsc.context_for_patch(pat, precision=bsc.FP64, quadrature=(rule, rule)) as ctx:
+        E, g, H = ctx.span_terms(ctx.to_device(pat.C), project=False)
+        oE, og, oH = prob.span_eval(pat.C)
+        assert rel(g.cpu().numpy(), og) < 1e-12 and rel(H.cpu().numpy(), oH) < 1e-12
+
+
+def test_fp32_errors_against_oracle(orc):
+    """FP32 span evaluation / assembly with the FP64 projection: error stated."""
+    pat = inputs.config_square(1, 32)
+    prob = orc.Problem.from_patch(pat)
+    sc = orc.Scene.from_patch(pat, project=True)
+    oE, og, oK = orc.evaluate(prob, sc, pat.C, pat.Chat)
+    with bsc.context_for_patch(pat, precision=bsc.FP32) as ctx:
+        C, Ch = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+        E = ctx.energy(C, Ch)
+        g = to_n3(ctx.gradient(C, Ch))
+        K = gpu_K_to_oracle(ctx.assemble_hessian(C, project=True), pat.n_cp)
+        eg, eK = rel(g, og), rel(K, oK)
+        print(f"FP32 vs oracle: energy {abs(E - oE) / abs(oE):.2e} gradient {eg:.2e} hessian {eK:.2e}")
+        assert abs(E - oE) / abs(oE) < 1e-5 and eg < 1e-4 and eK < 1e-5
+
+
+def test_bad_device_arguments():
+    pat = inputs.config_random_small(2, 6, 6)
+    with bsc.context_for_patch(pat, precision=bsc.FP64) as ctx:
+        x = ctx.new_vec()
+        with pytest.raises(bsc.BscError) as ei:
+            ctx._check(ctx._lib.bsc_spmv(ctx._h, None, bsc._ptr(x), bsc._ptr(x)))
+        assert ei.value.status == bsc.ERR_INVALID_ARG
+        with pytest.raises(bsc.BscError) as ei:
+            ctx._check(ctx._lib.bsc_energy(ctx._h, bsc._ptr(x), None, None))
+        assert ei.value.status == bsc.ERR_INVALID_ARG
+        C = ctx.to_device(pat.C)
+        C[0, 3] = float("nan")
+        with pytest.raises(bsc.BscError) as ei:
+            ctx.energy(C, ctx.to_device(pat.Chat))
+        assert ei.value.status == bsc.ERR_NUMERIC
+        # the context stays usable after a reported error
+        assert np.isfinite(ctx.energy(ctx.to_device(pat.C), ctx.to_device(pat.Chat)))

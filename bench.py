@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 B-spline cloth hot path.
+
+One timed step = one projected-Newton iteration (``bsc_newton_step``) of the
+256 x 256 drape workload in FP32 bulk precision: span evaluation (E, g, 27x27
+H), FP64 SPD projection, gather assembly, PCG solve to 1e-8 and the
+backtracking line search.  Reported:
+
+  value         spans/s of the E + grad + Hessian (+ SPD projection) + assembly
+                phase, from CUDA events recorded on the launching stream at the
+                phase boundaries inside every timed step
+  ms_per_step   Newton-step ms (whole iteration)
+  e2e           the full step through the C ABI with host buffers (pinned H2D
+                of C and Chat, D2H of C) in spans/s
+  fp64          the same step with the plain FP64 GPU path (speedup context)
+  roofline      the dominant kernel (the FP64 projection) against the FP64 pipe
+  cpu_baseline  the FP64 CPU oracle on a bounded crop of the same state
+
+``--impl reference`` times the oracle itself (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2506_18867_gb300 import inputs  # noqa: E402
+
+METRIC = "spans/s (E+grad+Hessian+assembly) and Newton-step ms"
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300 (no FP64 entry in the measured peaks)
+
+WORKLOADS = {
+    # name: (builder, description)
+    "drape256": (lambda seed: inputs.config_drape(seed, 256, 1e-5),
+                 "drape, 256x256 control points (65,536 cp, 64,516 spans), 2 m x 2 m, mu_bd = 1e-5 N m, "
+                 "sigma = 1 mm noise, u = 0 edge pinned, dt = 0.01 s"),
+    "square32": (lambda seed: inputs.config_square(seed, 32),
+                 "square, 32x32 control points (900 spans), 1 m x 1 m, two top corners pinned"),
+    "wrinkle1024": (lambda seed: inputs.config_wrinkle(seed, 1024),
+                    "precision sweep, 1024x1024 control points (1,044,484 spans), 4 m x 4 m wrinkle field"),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="bsc", choices=["bsc", "reference"])
+    p.add_argument("--workload", default="drape256", choices=sorted(WORKLOADS))
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.lines, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- flop model
+
+def projection_flops(nred, nneg, nm, nb):
+    """Algorithmic FP64 flops of the SPD projection of one span as implemented:
+    basis orthonormalisation, reduced Hessian formation, Householder
+    tridiagonalisation (4/3 n^3), Sturm counts (4 n per count, 1 + 53 per
+    negative eigenvalue), inverse iteration, back-transformation and the
+    low-rank update of the 378 packed entries."""
+    n = nred
+    D = n // 3
+    m = 2 * nm + nb
+    f = m * (27 + 2 * 2 * 18 * D / 2)                 # mean removal, norm, two MGS passes (mean rank D/2)
+    f += nm * 2 * (18 * D + 36 * D + 9 * D * (D + 1))  # g~, T_k, reduced blocks per membrane point
+    f += nb * (18 * D + 2 * D * (D + 1))               # L~ and blocks per bending point
+    f += 4.0 * n ** 3 / 3.0 + 4 * n                    # tridiagonalisation, scaling
+    f += 4 * n                                         # inertia count at -tau
+    if nneg:
+        f += nneg * (53 * 4 * n + 40 * n + 12 * n * nneg + 6 * n + 2 * n * n + 54 * D)
+        f += 378 * 3 * nneg + 378
+    return f
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2506_18867_gb300 import bsc
+    from paper_2506_18867_gb300 import build as _build
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+    bsc.load()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    builder, desc = WORKLOADS[args.workload]
+    pat = builder(1 + rank)
+    prec = bsc.FP32 if args.precision == "fp32" else bsc.FP64
+    ctx = bsc.context_for_patch(pat, precision=prec, pcg_rel_tol=1e-8)
+    ctx.set_profiling(True)
+    Nsp = ctx.n_spans
+    C0, Chat = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+    C = C0.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        C.copy_(C0)
+        return ctx.newton_step(C, Chat)
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+
+    phases = {k: 0.0 for k in bsc.Context.PHASES}
+    step_ms, reports = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local).start()
+    launches0 = ctx.launch_count()
+    barrier()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the events)
+        C.copy_(C0)
+        ev0.record(stream)
+        rep = ctx.newton_step(C, Chat)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for k, v in ctx.phase_times().items():
+            phases[k] += v
+        reports.append(rep.as_dict())
+    barrier()
+    wall = time.perf_counter() - t_wall
+    launches = ctx.launch_count() - launches0
+    clk = clocks.stop()
+
+    K = args.steps
+    ms_step = sum(step_ms) / K
+    eval_ms = (phases["span_eval"] + phases["project"] + phases["assemble"]) / K
+    proj_ms = phases["project"] / K
+    # the projection flops of the last step (the workload is identical every step)
+    nneg, nred = ctx.projection_stats()
+    q = ctx.quadrature_tables(0)
+    qb = ctx.quadrature_tables(1)
+    Su = pat.nu - 2
+    nm = np.bincount((q[:, 4] * Su + q[:, 3]).astype(np.int64), minlength=Nsp)
+    nb = np.bincount((qb[:, 4] * Su + qb[:, 3]).astype(np.int64), minlength=Nsp)
+    flops = 0.0
+    for s in range(Nsp):
+        flops += projection_flops(int(nred[s]), int(nneg[s]), int(nm[s]), int(nb[s]))
+    achieved_tflops = flops / (proj_ms * 1e-3) / 1e12
+
+    # e2e: the same Newton step through the C ABI from pinned host buffers
+    host_C = torch.from_numpy(np.ascontiguousarray(pat.C.T)).to(ctx.dtype).pin_memory()
+    host_Chat = torch.from_numpy(np.ascontiguousarray(pat.Chat.T)).to(ctx.dtype).pin_memory()
+    host_out = torch.empty_like(host_C).pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + K):
+        flush.zero_()
+        ev0.record(stream)
+        C.copy_(host_C, non_blocking=True)
+        Chat.copy_(host_Chat, non_blocking=True)
+        ctx.newton_step(C, Chat)
+        host_out.copy_(C, non_blocking=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(ev0.elapsed_time(ev1))
+    e2e_step = sum(e2e_ms) / len(e2e_ms)
+    tsz = 4 if prec == bsc.FP32 else 8
+
+    # aggregate over ranks (max of times, sum of work)
+    def allmax(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    eval_ms_max, ms_step_max, e2e_max = allmax(eval_ms), allmax(ms_step), allmax(e2e_step)
+    total_spans = Nsp * world
+    value = total_spans / (eval_ms_max * 1e-3)
+
+    fp64 = None
+    if not args.no_fp64 and prec == bsc.FP32 and rank == 0:
+        ctx64 = bsc.context_for_patch(pat, precision=bsc.FP64, pcg_rel_tol=1e-8)
+        ctx64.set_profiling(True)
+        C64_0, Chat64 = ctx64.to_device(pat.C), ctx64.to_device(pat.Chat)
+        C64 = C64_0.clone()
+        ms64, ph64 = [], {k: 0.0 for k in bsc.Context.PHASES}
+        K64 = max(2, K // 3)
+        for i in range(2 + K64):
+            flush.zero_()
+            C64.copy_(C64_0)
+            ev0.record(stream)
+            rep64 = ctx64.newton_step(C64, Chat64)
+            ev1.record(stream)
+            ev1.synchronize()
+            if i >= 2:
+                ms64.append(ev0.elapsed_time(ev1))
+                for k, v in ctx64.phase_times().items():
+                    ph64[k] += v
+        e64 = (ph64["span_eval"] + ph64["project"] + ph64["assemble"]) / K64
+        fp64 = {"newton_step_ms": sum(ms64) / K64, "eval_assembly_ms": e64,
+                "spans_per_s": Nsp / (e64 * 1e-3), "steps": K64,
+                "newton_step_speedup_fp32_vs_fp64": (sum(ms64) / K64) / ms_step,
+                "phases_ms": {k: v / K64 for k, v in ph64.items()}, "pcg_iters": rep64.pcg_iters}
+        ctx64.close()
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(args, pat)
+
+    if rank == 0:
+        rep = reports[-1]
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "spans/s",
+            "n_gpus": world,
+            "steps": K,
+            "warmup": args.warmup,
+            "ms_per_step": ms_step_max,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if prec == bsc.FP32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}_{args.precision}", "description": desc,
+                       "nu": pat.nu, "nv": pat.nv, "spans": Nsp, "control_points": pat.n_cp,
+                       "precision": ("FP32 span evaluation, assembly, SpMV and PCG vectors; FP64 SPD projection, "
+                                     "energy sums and norms") if prec == bsc.FP32 else "FP64 throughout",
+                       "pcg_rel_tol": 1e-8, "l2": "flushed (256 MB write) before every timed step",
+                       "step": "one projected-Newton iteration (bsc_newton_step) from the same seeded state",
+                       "replicas": "one independent patch per GPU (seed 1 + rank)"},
+            "newton_step_ms": ms_step_max,
+            "newton_spans_per_s": total_spans / (ms_step_max * 1e-3),
+            "eval_assembly_ms": eval_ms_max,
+            "phases_ms": {k: v / K for k, v in phases.items()},
+            "wall_ms_per_step": wall * 1e3 / K,
+            "newton": {"pcg_iters": rep["pcg_iters"], "pcg_rel_res": rep["pcg_rel_res"], "alpha": rep["alpha"],
+                       "ls_halvings": rep["ls_halvings"], "spans_projected": rep["spans_projected"],
+                       "dir_inf_over_dt": rep["dir_inf"] / pat.dt, "E0": rep["E0"], "E1": rep["E1"]},
+            "e2e": {"value": total_spans / (e2e_max * 1e-3), "unit": "spans/s",
+                    "scope": "bsc_newton_step with host buffers: pinned H2D of C and Chat, D2H of C, per step",
+                    "ms_per_step": e2e_max, "h2d_bytes_per_step": 2 * 3 * pat.n_cp * tsz,
+                    "d2h_bytes_per_step": 3 * pat.n_cp * tsz},
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / K,
+            "roofline": {"kernel": "k_project (FP64 SPD projection, 3 launches by span class)",
+                         "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                         "algorithmic_flops_per_step": flops, "launch_ms": proj_ms,
+                         "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); no FP64 peak in the measured peaks"},
+            "fp64": fp64,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def _oracle_eval_sample(orc, pat_crop):
+    prob = orc.Problem.from_patch(pat_crop)
+    sc = orc.Scene.from_patch(pat_crop, project=True)
+    t0 = time.perf_counter()
+    orc.evaluate(prob, sc, pat_crop.C, pat_crop.Chat)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args, pat, m=160):
+    import oracle as orc
+    orc.build()
+    sample = inputs.crop(pat, min(m, pat.nu), min(m, pat.nv))
+    secs = _oracle_eval_sample(orc, sample)
+    return {"value": sample.n_spans / secs, "unit": "spans/s", "cores": 1, "kind": "oracle",
+            "sample": f"E+grad+projected Hessian+stencil assembly of the leading {sample.nu}x{sample.nv} "
+                      f"control points ({sample.n_spans} spans) of the same state, FP64, one thread",
+            "seconds": secs}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle as orc
+    orc.build()
+    builder, desc = WORKLOADS[args.workload]
+    pat = builder(1)
+    sample = inputs.crop(pat, min(96, pat.nu), min(96, pat.nv))
+    for _ in range(args.warmup):
+        _oracle_eval_sample(orc, sample)
+    t = [_oracle_eval_sample(orc, sample) for _ in range(args.steps)]
+    sec = sum(t) / len(t)
+    value = sample.n_spans / sec
+    line = {"metric": METRIC, "value": value, "unit": "spans/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload}_{args.precision}", "description": desc,
+                       "sample": f"leading {sample.nu}x{sample.nv} control points ({sample.n_spans} spans)"},
+            "cpu_baseline": {"value": value, "unit": "spans/s", "cores": 1, "kind": "oracle",
+                             "sample": f"E+grad+projected Hessian+assembly of the leading {sample.nu}x{sample.nv} "
+                                       "control points of the same state per step, FP64, one thread"},
+            "e2e": {"value": value, "unit": "spans/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

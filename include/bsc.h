@@ -202,6 +202,24 @@ bsc_status bsc_lumped_mass(bsc_ctx* ctx, double* m_out);
 /* Sizes: N control points, Nsp spans, membrane / bending point counts. */
 bsc_status bsc_sizes(const bsc_ctx* ctx, int* n_cp, int* n_spans, int* n_mem, int* n_bend);
 
+/* Phase timing of bsc_newton_step.  With on != 0 the step records CUDA
+ * events on the context's stream at its phase boundaries; bsc_phase_times
+ * (synchronising) writes the durations of the last step in ms to ms_out[6]:
+ * [span evaluation, SPD projection, energy + gradient + assembly, linear
+ * solve, line search, whole step]. */
+bsc_status bsc_set_profiling(bsc_ctx* ctx, int on);
+bsc_status bsc_phase_times(bsc_ctx* ctx, double* ms_out);
+
+/* Number of CUDA kernels this context has launched since bsc_create. */
+bsc_status bsc_launch_count(const bsc_ctx* ctx, unsigned long long* launches);
+
+/* Per-span statistics of the last SPD projection (host arrays of Nsp ints,
+ * either may be NULL): nneg = eigenvalues projected away, nred = dimension
+ * of the span's reduced eigenproblem: 15 for interior spans (3 x the rank
+ * of their five derivative vectors), 24 for spans at or next to the border
+ * (the 3 x 8 mean-free subspace). */
+bsc_status bsc_projection_stats(bsc_ctx* ctx, int* nneg, int* nred);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5:
 # Every entry point declared in include/bsc.h.
 EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc_energy", "bsc_gradient",
            "bsc_assemble_hessian", "bsc_spmv", "bsc_solve", "bsc_newton_step", "bsc_span_terms",
-           "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes")
+           "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes", "bsc_set_profiling", "bsc_phase_times",
+           "bsc_launch_count", "bsc_projection_stats")
 
 
 class KnotGrid(ct.Structure):
@@ -96,6 +97,10 @@ def load(path: str = LIB_PATH):
     lib.bsc_quadrature_tables.argtypes = [P, I, ct.POINTER(D), I, ct.POINTER(I)]
     lib.bsc_lumped_mass.argtypes = [P, ct.POINTER(D)]
     lib.bsc_sizes.argtypes = [P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(I), ct.POINTER(I)]
+    lib.bsc_set_profiling.argtypes = [P, I]
+    lib.bsc_phase_times.argtypes = [P, ct.POINTER(D)]
+    lib.bsc_launch_count.argtypes = [P, ct.POINTER(ct.c_ulonglong)]
+    lib.bsc_projection_stats.argtypes = [P, ct.POINTER(I), ct.POINTER(I)]
     for name in EXPORTS:
         if name not in ("bsc_destroy", "bsc_last_error"):
             getattr(lib, name).restype = I
@@ -240,6 +245,30 @@ class Context:
         a, b, c, d = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int()
         self._check(self._lib.bsc_sizes(self._h, ct.byref(a), ct.byref(b), ct.byref(c), ct.byref(d)))
         return a.value, b.value, c.value, d.value
+
+    PHASES = ("span_eval", "project", "assemble", "solve", "line_search", "total")
+
+    def set_profiling(self, on=True):
+        self._check(self._lib.bsc_set_profiling(self._h, int(bool(on))))
+
+    def phase_times(self):
+        """Durations (ms) of the phases of the last Newton step (needs profiling)."""
+        out = (ct.c_double * 6)()
+        self._check(self._lib.bsc_phase_times(self._h, out))
+        return dict(zip(self.PHASES, list(out)))
+
+    def launch_count(self) -> int:
+        n = ct.c_ulonglong()
+        self._check(self._lib.bsc_launch_count(self._h, ct.byref(n)))
+        return n.value
+
+    def projection_stats(self):
+        """Per span: negative eigenvalues projected away, reduced problem size."""
+        a = np.zeros(self.n_spans, dtype=np.int32)
+        b = np.zeros(self.n_spans, dtype=np.int32)
+        self._check(self._lib.bsc_projection_stats(self._h, a.ctypes.data_as(ct.POINTER(ct.c_int)),
+                                                   b.ctypes.data_as(ct.POINTER(ct.c_int))))
+        return a, b
 
     def close(self):
         if getattr(self, "_h", None):

@@ -56,8 +56,22 @@ void free_ctx(bsc_ctx* c) {
     if (p) cudaFree(p);
   for (void* p : c->vec)
     if (p) cudaFree(p);
+  for (void* p : c->proj_scratch)
+    if (p) cudaFree(p);
+  if (c->proj_work) cudaFree(c->proj_work);
+  for (int i = 0; i < 2; ++i) {
+    if (c->side[i]) cudaStreamDestroy(c->side[i]);
+    if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->hscalars) cudaFreeHost(c->hscalars);
+  if (c->profiling)
+    for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
   free(c);
+}
+
+void mark(bsc_ctx* c, int k) {
+  if (c->profiling) cudaEventRecord(c->ev[k], c->stream);
 }
 
 bsc_status eval_path(bsc_ctx* c, const void* C, int want_grad, int want_hess, int project) {
@@ -194,6 +208,7 @@ bsc_status bsc_create(const bsc_knot_grid* g, const double* rest_xy, const bsc_m
   if (e == cudaSuccess) e = cudaMemset(c->dstatus, 0, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(c->nneg, 0, sizeof(int) * (size_t)c->Nsp);
   if (e == cudaSuccess) e = launch_build_tables(c);
+  if (e == cudaSuccess) e = setup_projection(c);
   if (e != cudaSuccess) {
     st = cuda_fail(nullptr, e, "bsc_create: building quadrature tables");
     free_ctx(c);
@@ -302,12 +317,23 @@ bsc_status bsc_newton_step(bsc_ctx* c, void* C, const void* Chat, bsc_newton_rep
   if (!C || (c->dt > 0.0 && !Chat)) return fail(c, BSC_ERR_INVALID_ARG, "bsc_newton_step: NULL argument");
   if (!aligned16(C) || (Chat && !aligned16(Chat))) return fail(c, BSC_ERR_INVALID_ARG, "bsc_newton_step: pointers must be 16-byte aligned");
   void *d = c->vec[0], *g = c->vec[5], *trial = c->vec[6];
-  bsc_status st = eval_path(c, C, 1, 1, c->project_default);
-  if (st == BSC_OK) {
+  mark(c, 0);
+  CK(launch_span_eval(c, C, 1, 1), "newton: span evaluation");
+  mark(c, 1);
+  if (c->project_default) {
+    CK(launch_project(c), "newton: SPD projection");
+    CK(launch_count_projected(c, c->dscalars + 3), "newton: SPD projection");
+  } else {
+    CK(cudaMemsetAsync(c->dscalars + 3, 0, sizeof(double), c->stream), "newton");
+  }
+  mark(c, 2);
+  bsc_status st = BSC_OK;
+  {
     CK(launch_energy(c, C, Chat, c->dscalars + 0), "newton: energy");
     CK(launch_gradient(c, C, Chat, g), "newton: gradient");
     CK(launch_assemble(c, c->K_int), "newton: assembly");
     c->K_last = c->K_int;
+    mark(c, 3);
     // right-hand side -g (into the spare vector), then PCG
     CK(launch_axpy_trial(c, g, g, -2.0, c->vec[7]), "newton: rhs");
     int iters = 0;
@@ -315,15 +341,17 @@ bsc_status bsc_newton_step(bsc_ctx* c, void* C, const void* Chat, bsc_newton_rep
     st = bsc_solve(c, c->K_int, c->vec[7], d, c->pcg_tol, c->pcg_max_iter, &iters, &rr);
     r.pcg_iters = iters;
     r.pcg_rel_res = rr;
+    mark(c, 4);
   }
   if (st == BSC_OK || st == BSC_ERR_NOT_CONVERGED) {
     bsc_status solve_st = st;
     CK(launch_absmax(c, d, c->dscalars + 1), "newton: |d|");
-    CK(cudaMemcpyAsync(c->hscalars, c->dscalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "newton");
+    CK(cudaMemcpyAsync(c->hscalars, c->dscalars, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "newton");
     st = check_status(c, "bsc_newton_step");
     if (st == BSC_OK) {
       r.E0 = c->hscalars[0];
       r.dir_inf = c->hscalars[1];
+      r.spans_projected = (int)c->hscalars[3];
       double alpha = 1.0;
       int h = 0;
       for (;;) {
@@ -356,7 +384,7 @@ bsc_status bsc_newton_step(bsc_ctx* c, void* C, const void* Chat, bsc_newton_rep
       if (st == BSC_OK && solve_st != BSC_OK) st = solve_st;
     }
   }
-  // spans projected (diagnostic)
+  mark(c, 5);
   r.status = st;
   if (rep) *rep = r;
   if (st == BSC_OK) CK(cudaStreamSynchronize(c->stream), "bsc_newton_step");
@@ -403,6 +431,57 @@ bsc_status bsc_quadrature_tables(bsc_ctx* c, int which, double* out, int cap, in
   }
   free(pts);
   free(tab);
+  return BSC_OK;
+}
+
+bsc_status bsc_set_profiling(bsc_ctx* c, int on) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (on && !c->profiling) {
+    for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&c->ev[k]), "bsc_set_profiling");
+    c->profiling = 1;
+  } else if (!on && c->profiling) {
+    CK(cudaStreamSynchronize(c->stream), "bsc_set_profiling");
+    for (int k = 0; k < 6; ++k) cudaEventDestroy(c->ev[k]);
+    c->profiling = 0;
+  }
+  return BSC_OK;
+}
+
+bsc_status bsc_phase_times(bsc_ctx* c, double* ms) {
+  if (!c || !ms) return BSC_ERR_INVALID_ARG;
+  if (!c->profiling) return fail(c, BSC_ERR_INVALID_ARG, "bsc_phase_times: profiling is off");
+  CK(cudaEventSynchronize(c->ev[5]), "bsc_phase_times");
+  float t;
+  for (int k = 0; k < 5; ++k) {
+    CK(cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]), "bsc_phase_times");
+    ms[k] = t;
+  }
+  CK(cudaEventElapsedTime(&t, c->ev[0], c->ev[5]), "bsc_phase_times");
+  ms[5] = t;
+  return BSC_OK;
+}
+
+bsc_status bsc_launch_count(const bsc_ctx* c, unsigned long long* n) {
+  if (!c || !n) return BSC_ERR_INVALID_ARG;
+  *n = c->launches;
+  return BSC_OK;
+}
+
+bsc_status bsc_projection_stats(bsc_ctx* c, int* nneg, int* nred) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (nneg) {
+    CK(cudaMemcpyAsync(nneg, c->nneg, sizeof(int) * c->Nsp, cudaMemcpyDeviceToHost, c->stream), "bsc_projection_stats");
+    CK(cudaStreamSynchronize(c->stream), "bsc_projection_stats");
+  }
+  if (nred) {
+    int* hl = (int*)malloc(sizeof(int) * c->Nsp);
+    cudaError_t e = cudaMemcpy(hl, c->bucket_list, sizeof(int) * c->Nsp, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { free(hl); return cuda_fail(c, e, "bsc_projection_stats"); }
+    const int sizes[3] = {15, 24, 24};
+    for (int b = 0; b < 3; ++b)
+      for (int k = c->bucket_off[b]; k < c->bucket_off[b + 1]; ++k) nred[hl[k]] = sizes[b];
+    free(hl);
+  }
   return BSC_OK;
 }
 

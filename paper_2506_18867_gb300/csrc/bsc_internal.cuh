@@ -53,6 +53,11 @@ struct bsc_ctx {
   int* bucket_list;   // [Nsp] span ids grouped by bucket
   int bucket_off[4];  // host: start of each bucket in bucket_list
   int* nneg;          // [Nsp] negative eigenvalues found per span (diagnostic)
+  int proj_grid[3];   // resident grid per class
+  double* proj_scratch[3];  // per-thread slots: Q (9 D) and eigenvectors (n x n)
+  unsigned int* proj_work;  // [3] work counters
+  cudaStream_t side[2];     // forked streams for the two small classes
+  cudaEvent_t fork_ev, join_ev[2];
 
   // span workspace
   double* E_span;     // [Nsp]
@@ -73,15 +78,25 @@ struct bsc_ctx {
   int pcg_grid, pcg_block;
   int red_grid;
 
+  // profiling / diagnostics
+  unsigned long long launches;  // kernels launched
+  int profiling;
+  cudaEvent_t ev[6];
+
   char err[512];
 };
+
+// counts kernel launches of a context (diagnostic; see bsc_launch_count)
+#define BSC_COUNT(c, k) ((c)->launches += (k))
 
 // -------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // -------------------------------------------------------------------------
 cudaError_t launch_build_tables(bsc_ctx* c);
 cudaError_t launch_span_eval(bsc_ctx* c, const void* C, int want_grad, int want_hess);
+cudaError_t setup_projection(bsc_ctx* c);
 cudaError_t launch_project(bsc_ctx* c);
+cudaError_t launch_count_projected(bsc_ctx* c, double* dout);
 cudaError_t launch_assemble(bsc_ctx* c, void* K);
 cudaError_t launch_gradient(bsc_ctx* c, const void* C, const void* Chat, void* g);
 cudaError_t launch_energy(bsc_ctx* c, const void* C, const void* Chat, double* dE);

@@ -23,14 +23,14 @@ __global__ void k_assemble(int nu, int nv, int Nsp, const T* __restrict__ H,
   const int slot = t / N, al = t - slot * N;
   const int du = slot % 5 - 2, dv = slot / 5 - 2;
   const int i = al % nu, j = al / nu, ib = i + du, jb = j + dv;
-  double blk[9];
+  T blk[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) blk[k] = 0.0;
+  for (int k = 0; k < 9; ++k) blk[k] = T(0);
   const bool inside = ib >= 0 && ib < nu && jb >= 0 && jb < nv;
   if (inside) {
     const int be = jb * nu + ib;
     if (pinned[al] || pinned[be]) {
-      if (du == 0 && dv == 0) blk[0] = blk[4] = blk[8] = 1.0;
+      if (du == 0 && dv == 0) blk[0] = blk[4] = blk[8] = T(1);
     } else {
       const int a_lo = max(max(i, ib) - 2, 0), a_hi = min(min(i, ib), Su - 1);
       const int b_lo = max(max(j, jb) - 2, 0), b_hi = min(min(j, jb), Sv - 1);
@@ -43,17 +43,17 @@ __global__ void k_assemble(int nu, int nv, int Nsp, const T* __restrict__ H,
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
               const int R = 3 * la + r, Cc = 3 * lb + c;
-              blk[3 * r + c] += (double)H[(size_t)sym_upk(R, Cc, 27) * Nsp + s];
+              blk[3 * r + c] += H[(size_t)sym_upk(R, Cc, 27) * Nsp + s];
             }
         }
       if (du == 0 && dv == 0) {
-        const double k = mass[al] * inv_dt2;
+        const T k = (T)(mass[al] * inv_dt2);
         blk[0] += k; blk[4] += k; blk[8] += k;
       }
     }
   }
 #pragma unroll
-  for (int k = 0; k < 9; ++k) K[(size_t)(slot * 9 + k) * N + al] = (T)blk[k];
+  for (int k = 0; k < 9; ++k) K[(size_t)(slot * 9 + k) * N + al] = blk[k];
 }
 
 template <typename T>
@@ -69,19 +69,19 @@ __global__ void k_gradient(int nu, int nv, int Nsp, const T* __restrict__ gs,
     return;
   }
   const int i = al % nu, j = al / nu;
-  double acc[3] = {0.0, 0.0, 0.0};
+  T acc[3] = {T(0), T(0), T(0)};
   for (int b = max(j - 2, 0); b <= min(j, Sv - 1); ++b)
     for (int a = max(i - 2, 0); a <= min(i, Su - 1); ++a) {
       const int s = b * Su + a, l = (i - a) + 3 * (j - b);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[c] += (double)gs[(size_t)(3 * l + c) * Nsp + s];
+      for (int c = 0; c < 3; ++c) acc[c] += gs[(size_t)(3 * l + c) * Nsp + s];
     }
-  const double m = mass[al], grav[3] = {gx, gy, gz};
+  const T m = (T)mass[al], mk = (T)(mass[al] * inv_dt2), grav[3] = {(T)gx, (T)gy, (T)gz};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    double v = acc[c] - m * grav[c];
-    if (inv_dt2 > 0.0) v += m * inv_dt2 * ((double)C[c * N + al] - (double)Chat[c * N + al]);
-    g[c * N + al] = (T)v;
+    T v = acc[c] - m * grav[c];
+    if (inv_dt2 > 0.0) v += mk * (C[c * N + al] - Chat[c * N + al]);
+    g[c * N + al] = v;
   }
 }
 
@@ -129,9 +129,12 @@ __global__ void k_export_span(int Nsp, const T* __restrict__ gs, const T* __rest
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= Nsp) return;
   if (g_out)
+#pragma unroll 1
     for (int k = 0; k < 27; ++k) g_out[(size_t)s * 27 + k] = gs[(size_t)k * Nsp + s];
   if (H_out)
+#pragma unroll 1
     for (int r = 0; r < 27; ++r)
+#pragma unroll 1
       for (int c = 0; c < 27; ++c)
         H_out[(size_t)s * 729 + r * 27 + c] = Hs[(size_t)sym_upk(r, c, 27) * Nsp + s];
 }
@@ -139,6 +142,7 @@ __global__ void k_export_span(int Nsp, const T* __restrict__ gs, const T* __rest
 }  // namespace
 
 cudaError_t launch_assemble(bsc_ctx* c, void* K) {
+  BSC_COUNT(c, 1);
   const int B = 256, G = (25 * c->N + B - 1) / B;
   const double idt2 = c->dt > 0.0 ? 1.0 / (c->dt * c->dt) : 0.0;
   if (c->precision == BSC_FP64)
@@ -151,6 +155,7 @@ cudaError_t launch_assemble(bsc_ctx* c, void* K) {
 }
 
 cudaError_t launch_gradient(bsc_ctx* c, const void* C, const void* Chat, void* g) {
+  BSC_COUNT(c, 1);
   const int B = 256, G = (c->N + B - 1) / B;
   const double idt2 = c->dt > 0.0 ? 1.0 / (c->dt * c->dt) : 0.0;
   const double* gr = c->gravity;
@@ -166,6 +171,7 @@ cudaError_t launch_gradient(bsc_ctx* c, const void* C, const void* Chat, void* g
 }
 
 cudaError_t launch_energy(bsc_ctx* c, const void* C, const void* Chat, double* dE) {
+  BSC_COUNT(c, 2);
   constexpr int B = 256;
   const int G = c->red_grid;
   const double idt2 = c->dt > 0.0 ? 1.0 / (c->dt * c->dt) : 0.0;
@@ -183,6 +189,7 @@ cudaError_t launch_energy(bsc_ctx* c, const void* C, const void* Chat, double* d
 }
 
 cudaError_t launch_export_span_terms(bsc_ctx* c, void* g_out, void* H_out) {
+  BSC_COUNT(c, 1);
   const int B = 128, G = (c->Nsp + B - 1) / B;
   if (c->precision == BSC_FP64)
     k_export_span<double><<<G, B, 0, c->stream>>>(c->Nsp, (const double*)c->g_span, (const double*)c->H_span,

@@ -2,19 +2,31 @@
 // (projected Newton, Sec. 5.1): P = V max(Lambda, 0) V^T = H - sum_{lam<0}
 // lam w w^T.
 //
-// One thread per span.  The span Hessian is
+// The span Hessian is
 //   H = sum_q (G_q (x) I3) A_q (G_q (x) I3)^T + sum_b W_b mu_bd (L_b L_b^T) (x) I3,
 // so its range lies in R (x) R^3 with R = span{g_q,1, g_q,2, L_b} in R^9;
 // every such vector sums to zero over the 9 control points (derivatives of a
 // partition of unity), so dim R <= min(8, 2 n_mem + n_bd) =: D.  With an
 // orthonormal basis Q of R, H = (Q (x) I3) H_r (Q (x) I3)^T and H_r (3D x 3D)
-// has the same non-zero spectrum.  H_r is built directly from the per-point
-// d^2 Psi/df^2 (kept by the span evaluator) in FP64, reduced to tridiagonal
-// form, its negative eigenvalues are found by Sturm bisection and their
-// eigenvectors by inverse iteration; the span Hessian in HBM is then
-// corrected in place.  Spans with no negative eigenvalue are left untouched.
+// has the same non-zero spectrum.  H_r is built from the per-point
+// d^2 Psi/df^2 kept by the span evaluator, in FP64, and projected by
+// proj::project_span (tridiagonalisation, Sturm bisection, inverse
+// iteration).
+//
+// Spans are grouped by D (5, 7, 8).  A block takes BLOCK spans at a time from
+// its class's work counter.  Phase 1 (one thread per span) builds H_r,
+// tridiagonalises it and counts its negative eigenvalues; phase 2 runs in
+// rounds, round r computing eigenpair r of every span that has one, with the
+// (span, r) items compacted onto the block's first threads so that no warp
+// carries masked lanes through the FP64 work (masked lanes cost the FP64 pipe
+// as much as active ones).  Working sets live in interleaved shared memory,
+// the basis and eigenvectors of a span in a per-thread global scratch slot.
+// The three classes run concurrently on forked streams.
 #include "bsc_internal.cuh"
-#include "eig_small.cuh"
+#include "proj_core.cuh"
+
+cudaError_t setup_projection_ring();
+cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* work, cudaStream_t st);
 
 namespace {
 
@@ -39,267 +51,238 @@ constexpr double NEG_REL = 1e-14;
 // RANK_REL of its norm lies in the span of the previous ones.
 constexpr double RANK_REL = 1e-13;
 
+template <typename T>
+struct SpanTab {
+  const T* tabm;  // already offset to the span's first membrane point
+  const T* tabb;  // already offset to the span's first bending point
+  const T* A;
+  int Nm, Nb, nmq, nbq;
+  double mubd;
+  __device__ int nm() const { return nmq; }
+  __device__ int nb() const { return nbq; }
+  __device__ double g(int q, int l, int be) const { return (double)tabm[(1 + 2 * l + be) * Nm + q]; }
+  __device__ double L(int q, int l) const { return (double)tabb[(1 + l) * Nb + q]; }
+  __device__ double wb(int q) const { return (double)tabb[q] * mubd; }
+  __device__ double a6(int q, int e) const { return (double)A[e * Nm + q]; }
+};
+
+// H <- H - lam w w^T on the packed upper triangle, in the element type: the
+// correction is formed in FP64 and applied in T (FP32 output stays FP32).
+template <typename T>
+struct SpanH {
+  T* H;
+  int Nsp, s;
+  __device__ void rank1(double lam, const double (&w)[27]) {
+    T wt[27], lw[27];
+#pragma unroll
+    for (int r = 0; r < 27; ++r) {
+      wt[r] = (T)w[r];
+      lw[r] = (T)(lam * w[r]);
+    }
+    T* h = H + s;
+    int e = 0;
+#pragma unroll
+    for (int r = 0; r < 27; ++r)
+#pragma unroll
+      for (int c = r; c < 27; ++c, ++e) h[(size_t)e * Nsp] -= lw[r] * wt[c];
+  }
+};
+
+// Shared memory per thread: A (packed H_r, then reflectors), R (3n: basis,
+// then the scaled tridiagonal), the scale ||T||, an FP32 copy of (d, e^2)
+// and the running lower bracket, all interleaved by thread.
 template <int D>
-__device__ __forceinline__ void add_basis_vector(double (&v)[9], double (&Q)[D][9], int& d) {
-  // remove the constant vector (exactly orthogonal in exact arithmetic)
-  double mean = 0.0;
-#pragma unroll
-  for (int l = 0; l < 9; ++l) mean += v[l];
-  mean *= (1.0 / 9.0);
-  double n0 = 0.0;
-#pragma unroll
-  for (int l = 0; l < 9; ++l) {
-    v[l] -= mean;
-    n0 += v[l] * v[l];
-  }
-  if (n0 == 0.0 || d >= D) return;
-  // modified Gram-Schmidt, two passes
-  for (int pass = 0; pass < 2; ++pass)
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      if (k >= d) break;
-      double dot = 0.0;
-#pragma unroll
-      for (int l = 0; l < 9; ++l) dot += Q[k][l] * v[l];
-#pragma unroll
-      for (int l = 0; l < 9; ++l) v[l] -= dot * Q[k][l];
-    }
-  double n1 = 0.0;
-#pragma unroll
-  for (int l = 0; l < 9; ++l) n1 += v[l] * v[l];
-  if (n1 <= RANK_REL * RANK_REL * n0) return;
-  const double inv = 1.0 / sqrt(n1);
-#pragma unroll
-  for (int k = 0; k < D; ++k)
-    if (k == d) {
-#pragma unroll
-      for (int l = 0; l < 9; ++l) Q[k][l] = v[l] * inv;
-    }
-  ++d;
-}
+struct Smem {
+  static constexpr int n = 3 * D, NP = n * (n + 1) / 2;
+  static constexpr int DOUBLES = NP + 3 * n + 1, FLOATS = 2 * n + 1;
+};
 
 template <typename T, int D, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_project(ProjArgs<T> P, const int* __restrict__ list,
-                                                   int count) {
-  constexpr int n = 3 * D;
-  constexpr int NP = n * (n + 1) / 2;
+__global__ void __launch_bounds__(BLOCK, 1)
+    k_project(ProjArgs<T> P, const int* __restrict__ list, int count, double* __restrict__ scratch,
+              unsigned int* __restrict__ work) {
+  constexpr int n = 3 * D, NP = Smem<D>::NP;
   extern __shared__ __align__(16) double smd[];
-  const int t = blockIdx.x * BLOCK + threadIdx.x;
-  if (t >= count) return;
-  const int s = list[t];
-  const eig::Packed A{smd + threadIdx.x, BLOCK};
-#pragma unroll 1
-  for (int k = 0; k < NP; ++k) A.base[k * BLOCK] = 0.0;
-
-  const int q0 = P.moff[s], q1 = P.moff[s + 1];
-  const int b0 = P.boff[s], b1 = P.boff[s + 1];
-
-  // 1. orthonormal basis of R = span{g_q,beta, L_b} (mean-free)
-  double Q[D][9];
-#pragma unroll
-  for (int k = 0; k < D; ++k)
-#pragma unroll
-    for (int l = 0; l < 9; ++l) Q[k][l] = 0.0;
-  int d = 0;
-  for (int q = q0; q < q1; ++q)
-    for (int be = 0; be < 2; ++be) {
-      double v[9];
-#pragma unroll
-      for (int l = 0; l < 9; ++l) v[l] = (double)P.tabm[(1 + 2 * l + be) * P.Nm + q];
-      add_basis_vector<D>(v, Q, d);
-    }
-  for (int q = b0; q < b1; ++q) {
-    double v[9];
-#pragma unroll
-    for (int l = 0; l < 9; ++l) v[l] = (double)P.tabb[(1 + l) * P.Nb + q];
-    add_basis_vector<D>(v, Q, d);
-  }
-
-  // 2. reduced Hessian H_r(3k+c, 3k'+d) (lower triangle)
-  for (int q = q0; q < q1; ++q) {
-    double gr[D][2];
-#pragma unroll
-    for (int k = 0; k < D; ++k) gr[k][0] = gr[k][1] = 0.0;
-#pragma unroll
-    for (int l = 0; l < 9; ++l) {
-      const double g0 = (double)P.tabm[(1 + 2 * l) * P.Nm + q];
-      const double g1 = (double)P.tabm[(2 + 2 * l) * P.Nm + q];
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        gr[k][0] += Q[k][l] * g0;
-        gr[k][1] += Q[k][l] * g1;
+  double* const Abase = smd;
+  double* const Rbase = smd + (size_t)NP * BLOCK;
+  double* const Tn = smd + (size_t)(NP + 3 * n) * BLOCK;
+  float* const Fbase = reinterpret_cast<float*>(smd + (size_t)Smem<D>::DOUBLES * BLOCK);
+  float* const Lo = Fbase + 2 * n * BLOCK;
+  __shared__ int s_kneg[BLOCK], s_span[BLOCK], s_list[BLOCK], s_wcnt[BLOCK / 32];
+  __shared__ int s_base;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nslots = gridDim.x * BLOCK, slot0 = blockIdx.x * BLOCK;
+  for (;;) {
+    // a batch of BLOCK spans per block, taken from the class's work counter
+    if (tid == 0) s_base = (int)atomicAdd(work, (unsigned)BLOCK);
+    __syncthreads();
+    const int base = s_base;
+    if (base >= count) break;
+    // phase 1 (uniform work): one span per thread
+    const int t = base + tid;
+    int kneg = 0, s = -1;
+    if (t < count) {
+      s = list[t];
+      const int q0 = P.moff[s], b0 = P.boff[s];
+      SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.Nm, P.Nb, P.moff[s + 1] - q0, P.boff[s + 1] - b0,
+                     P.mubd};
+      const proj::View A{Abase + tid, BLOCK}, R{Rbase + tid, BLOCK};
+      const proj::View Qs{scratch + slot0 + tid, nslots};
+      double tn = 0.0;
+      kneg = proj::span_phase1<D>(tab, A, R, Qs, &tn, NEG_REL, RANK_REL);
+      if (kneg < 0) {
+        atomicOr(P.status, BSC_STATUS_NUMERIC_FLAG);
+        kneg = 0;
       }
-    }
-    double A6[6][6];
-    {
-      int e = 0;
+      Tn[tid] = tn;
 #pragma unroll
-      for (int r = 0; r < 6; ++r)
-#pragma unroll
-        for (int c = r; c < 6; ++c) {
-          A6[r][c] = (double)P.A[(e++) * P.Nm + q];
-          A6[c][r] = A6[r][c];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      double Tk[3][6];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) Tk[c][j] = gr[k][0] * A6[c][j] + gr[k][1] * A6[3 + c][j];
-#pragma unroll
-      for (int k2 = 0; k2 <= k; ++k2)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int dd = 0; dd < 3; ++dd) {
-            if (k2 == k && dd > c) continue;
-            A.at(3 * k + c, 3 * k2 + dd) += Tk[c][dd] * gr[k2][0] + Tk[c][3 + dd] * gr[k2][1];
-          }
-    }
-  }
-  for (int q = b0; q < b1; ++q) {
-    const double WB = (double)P.tabb[q] * P.mubd;
-    double Lr[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) Lr[k] = 0.0;
-#pragma unroll
-    for (int l = 0; l < 9; ++l) {
-      const double L = (double)P.tabb[(1 + l) * P.Nb + q];
-#pragma unroll
-      for (int k = 0; k < D; ++k) Lr[k] += Q[k][l] * L;
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k)
-#pragma unroll
-      for (int k2 = 0; k2 <= k; ++k2) {
-        const double h = WB * Lr[k] * Lr[k2];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) A.at(3 * k + c, 3 * k2 + c) += h;
+      for (int i = 0; i < n; ++i) {
+        Fbase[i * BLOCK + tid] = (float)R[i];
+        Fbase[(n + i) * BLOCK + tid] = (float)R[2 * n + i];
       }
-  }
-
-  // 3. tridiagonal form and the negative part of the spectrum
-  double dg[n], ed[n], tau[n];
-  eig::tridiagonalize<n>(A, dg, ed, tau);
-  double tn = 0.0;
+      Lo[tid] = -1.0f - 1e-6f;
+      P.nneg[s] = kneg;
+    }
+    s_kneg[tid] = kneg;
+    s_span[tid] = s;
+    __syncthreads();
+    // phase 2: round r handles eigenvalue r of every span that has one; the
+    // (span, r) items are compacted onto the first threads of the block
+    for (int r = 0;; ++r) {
+      const bool flag = s_kneg[tid] > r;
+      const unsigned bal = __ballot_sync(0xffffffffu, flag);
+      if (lane == 0) s_wcnt[warp] = __popc(bal);
+      __syncthreads();
+      int off = 0, total = 0;
 #pragma unroll
-  for (int i = 0; i < n; ++i) {
-    const double r = fabs(dg[i]) + fabs(ed[i]) + (i > 0 ? fabs(ed[i - 1]) : 0.0);
-    tn = fmax(tn, r);
-  }
-  if (!(tn > 0.0)) {
-    P.nneg[s] = 0;
-    if (!isfinite(tn)) atomicOr(P.status, BSC_STATUS_NUMERIC_FLAG);
-    return;
-  }
-  const double itn = 1.0 / tn;
-  double ds[n], es[n], e2[n];
-#pragma unroll
-  for (int i = 0; i < n; ++i) {
-    ds[i] = dg[i] * itn;
-    es[i] = ed[i] * itn;
-    e2[i] = es[i] * es[i];
-  }
-  const int kneg = eig::sturm_count<n>(ds, e2, -NEG_REL);
-  P.nneg[s] = kneg;
-  if (kneg == 0) return;
-
-  // 4. eigenpairs of the negative eigenvalues; w = (Q (x) I3) x in span DOFs
-  double Y[n][n];    // tridiagonal-basis eigenvectors found so far
-  double Wv[n][27];  // their span-DOF images
-  double lam[n];
-  double lo = -1.0 - 1e-12;
-  for (int k = 0; k < kneg; ++k) {
-    const double lk = eig::bisect<n>(ds, e2, k, lo, -NEG_REL);
-    eig::TriLU<n> lu;
-    lu.factor(ds, es, lk, 2.3e-16);
-    double y[n];
-#pragma unroll
-    for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.125 * (double)((7 * i + 3 * k) % 5);
-    for (int it = 0; it < 3; ++it) {
-      for (int j = 0; j < k; ++j) {
-        double dot = 0.0;
-#pragma unroll
-        for (int i = 0; i < n; ++i) dot += Y[j][i] * y[i];
-#pragma unroll
-        for (int i = 0; i < n; ++i) y[i] -= dot * Y[j][i];
+      for (int w = 0; w < BLOCK / 32; ++w) {
+        off += (w < warp) ? s_wcnt[w] : 0;
+        total += s_wcnt[w];
       }
-      if (it < 2) lu.solve(y);
-      double nn = 0.0;
-#pragma unroll
-      for (int i = 0; i < n; ++i) nn += y[i] * y[i];
-      const double inv = 1.0 / sqrt(nn);
-#pragma unroll
-      for (int i = 0; i < n; ++i) y[i] *= inv;
-    }
-    // Rayleigh quotient on the scaled tridiagonal
-    double rq = 0.0;
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-      double ty = ds[i] * y[i];
-      if (i > 0) ty += es[i - 1] * y[i - 1];
-      if (i + 1 < n) ty += es[i] * y[i + 1];
-      rq += y[i] * ty;
-    }
-#pragma unroll
-    for (int i = 0; i < n; ++i) Y[k][i] = y[i];
-    lam[k] = fmin(rq, 0.0) * tn;
-    lo = lk - 1e-12;
-    eig::back_transform<n>(A, tau, y);
-#pragma unroll
-    for (int l = 0; l < 9; ++l)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        double acc = 0.0;
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) acc += Q[kk][l] * y[3 * kk + c];
-        Wv[k][3 * l + c] = acc;
+      if (flag) s_list[off + __popc(bal & ((1u << lane) - 1u))] = tid;
+      __syncthreads();
+      if (total == 0) break;
+      if (tid < total) {
+        const int o = s_list[tid];
+        const proj::View Ao{Abase + o, BLOCK}, Ro{Rbase + o, BLOCK};
+        const proj::View Qo{scratch + slot0 + o, nslots};
+        const proj::View Yo{scratch + (size_t)9 * D * nslots + slot0 + o, nslots};
+        SpanH<T> hs{P.H, P.Nsp, s_span[o]};
+        proj::span_eigpair<D>(Ao, Ro, Qo, Yo, Fbase + o, BLOCK, Lo + o, Tn[o], r, hs, NEG_REL);
       }
-  }
-
-  // 5. P = H - sum_k lam_k w_k w_k^T on the packed upper 27x27 in HBM
-  int e = 0;
-#pragma unroll 1
-  for (int r = 0; r < 27; ++r)
-#pragma unroll 1
-    for (int c = r; c < 27; ++c, ++e) {
-      double corr = 0.0;
-      for (int k = 0; k < kneg; ++k) corr += lam[k] * Wv[k][r] * Wv[k][c];
-      T* h = P.H + (size_t)e * P.Nsp + s;
-      *h = (T)((double)(*h) - corr);
+      __syncthreads();
     }
+  }
 }
 
-template <typename T, int D, int BLOCK>
-cudaError_t run_bucket(bsc_ctx* c, int b) {
+template <int D>
+struct Cfg;
+template <> struct Cfg<5> { static constexpr int BLOCK = 128; };
+
+template <int D>
+constexpr size_t smem_bytes() {
+  return (sizeof(double) * Smem<D>::DOUBLES + sizeof(float) * Smem<D>::FLOATS) * (size_t)Cfg<D>::BLOCK;
+}
+
+template <typename T, int D>
+cudaError_t run_bucket(bsc_ctx* c, int b, cudaStream_t st) {
   const int count = c->bucket_off[b + 1] - c->bucket_off[b];
   if (count <= 0) return cudaSuccess;
+  BSC_COUNT(c, 1);
+  constexpr int BLOCK = Cfg<D>::BLOCK;
   ProjArgs<T> P;
   P.Nsp = c->Nsp; P.Nm = c->Nmem; P.Nb = c->Nbd; P.mubd = c->mu_bd;
   P.moff = c->mem_off; P.boff = c->bd_off;
   P.tabm = (const T*)c->tab_mem; P.tabb = (const T*)c->tab_bd;
   P.A = (const T*)c->A_mem; P.H = (T*)c->H_span;
   P.nneg = c->nneg; P.status = c->dstatus;
-  constexpr int n = 3 * D;
-  const size_t sm = sizeof(double) * (n * (n + 1) / 2) * BLOCK;
   auto k = k_project<T, D, BLOCK>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<D>());
   if (e != cudaSuccess) return e;
-  k<<<(count + BLOCK - 1) / BLOCK, BLOCK, sm, c->stream>>>(P, c->bucket_list + c->bucket_off[b], count);
+  if ((e = cudaMemsetAsync(c->proj_work + b, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+  k<<<c->proj_grid[b], BLOCK, smem_bytes<D>(), st>>>(P, c->bucket_list + c->bucket_off[b], count,
+                                                     c->proj_scratch[b], c->proj_work + b);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t run_all(bsc_ctx* c) {
   cudaError_t e;
-  if ((e = run_bucket<T, 5, 128>(c, 0)) != cudaSuccess) return e;
-  if ((e = run_bucket<T, 7, 64>(c, 1)) != cudaSuccess) return e;
-  return run_bucket<T, 8, 64>(c, 2);
+  // fork: the border classes (warp-per-span kernel) on a side stream, the
+  // interior class on the context stream; the two co-reside on every SM
+  if ((e = cudaEventRecord(c->fork_ev, c->stream)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(c->side[0], c->fork_ev, 0)) != cudaSuccess) return e;
+  if ((e = launch_project_ring(c, c->bucket_off[1], c->bucket_off[3] - c->bucket_off[1], c->proj_work + 1,
+                               c->side[0])) != cudaSuccess)
+    return e;
+  if ((e = run_bucket<T, 5>(c, 0, c->stream)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(c->join_ev[0], c->side[0])) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(c->stream, c->join_ev[0], 0);
+}
+
+// Number of spans with at least one projected eigenvalue (block counts, then
+// a fixed-order sum over blocks).
+template <int BLOCK>
+__global__ void k_count_projected(int Nsp, const int* __restrict__ nneg, double* __restrict__ partial) {
+  __shared__ double sm[BLOCK / 32];
+  double acc = 0.0;
+  for (int s = blockIdx.x * BLOCK + threadIdx.x; s < Nsp; s += gridDim.x * BLOCK) acc += nneg[s] > 0 ? 1.0 : 0.0;
+  const double tot = block_sum<BLOCK>(acc, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+template <int BLOCK>
+__global__ void k_sum_counts(int n, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sm[BLOCK / 32];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += BLOCK) acc += partial[k];
+  const double tot = block_sum<BLOCK>(acc, sm);
+  if (threadIdx.x == 0) *out = tot;
+}
+
+template <typename T, int D>
+int resident_grid(int num_sms) {
+  int per_sm = 0;
+  cudaFuncSetAttribute(k_project<T, D, Cfg<D>::BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem_bytes<D>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project<T, D, Cfg<D>::BLOCK>, Cfg<D>::BLOCK,
+                                                smem_bytes<D>());
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * num_sms;
 }
 
 }  // namespace
+
+// Sizes the interior class's grid and scratch slots and loads the border
+// kernel's constants (called from bsc_create).
+cudaError_t setup_projection(bsc_ctx* c) {
+  const int count = c->bucket_off[1] - c->bucket_off[0];
+  const int need = (count + Cfg<5>::BLOCK - 1) / Cfg<5>::BLOCK;
+  int g = c->precision == BSC_FP64 ? resident_grid<double, 5>(c->num_sms) : resident_grid<float, 5>(c->num_sms);
+  if (g > need) g = need;
+  if (g < 1) g = 1;
+  c->proj_grid[0] = g;
+  {
+    const size_t slots = (size_t)g * Cfg<5>::BLOCK;
+    cudaError_t e = cudaMalloc(&c->proj_scratch[0], sizeof(double) * (size_t)(9 * 5 + 15 * 15) * slots);
+    if (e != cudaSuccess) return e;
+    if ((e = setup_projection_ring()) != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMalloc(&c->proj_work, sizeof(unsigned int) * 4);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < 2; ++i) {
+    if ((e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+  }
+  return cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
+}
+
+cudaError_t launch_count_projected(bsc_ctx* c, double* dout) {
+  BSC_COUNT(c, 2);
+  k_count_projected<256><<<c->red_grid, 256, 0, c->stream>>>(c->Nsp, c->nneg, c->partials + 2 * c->red_grid);
+  k_sum_counts<256><<<1, 256, 0, c->stream>>>(c->red_grid, c->partials + 2 * c->red_grid, dout);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_project(bsc_ctx* c) {
   if (c->precision == BSC_FP64) return run_all<double>(c);

@@ -1,0 +1,472 @@
+// K3 for the spans at and next to the patch border (more than five
+// derivative vectors: the boundary spans with their 3x3 / 3x2 Gauss rules
+// and the interior spans that own extra knot-line points).
+//
+// Their vectors {g_q,beta, L_b} span the whole 8-dimensional mean-free
+// subspace of R^9 (or a subspace of it), so a fixed orthonormal basis of that
+// subspace (Helmert contrasts) reduces every such span Hessian to 24 x 24
+// without a Gram-Schmidt step; a rank-deficient span only adds exact zero
+// eigenvalues.  These spans are few but each is expensive, so the kernel
+// minimises latency rather than lane-operations: one warp per span, lane j
+// holding column j of H_r in registers.  Householder steps exchange the
+// reflector through shuffles; every negative eigenvalue is bisected by its
+// own lane (FP32 bracket, FP64 check and refinement); each lane recovers its
+// eigenvector by inverse iteration, with Gram-Schmidt across lanes after each
+// solve (clusters); the back-transformation reads the reflectors from shared
+// memory; the lanes share the 378 packed entries of the final update
+// H -= sum lam w w^T.  The projected matrix V max(Lambda, 0) V^T (projected
+// Newton, Sec. 5.1) is unique, so this reduction and the interior kernel's
+// give the same result up to rounding.
+#include "bsc_internal.cuh"
+
+namespace {
+
+constexpr int RN = 24;         // reduced size 3 x 8
+constexpr int RBLOCK = 128;    // four warps (spans) per block
+constexpr double NEG_REL = 1e-14;
+
+// Helmert contrasts: q_k = (1, ..., 1, -k, 0, ...) / sqrt(k (k + 1)), k = 1..8
+// (k ones), an orthonormal basis of the vectors of R^9 that sum to zero.
+__constant__ double c_helmert[8][9];
+
+template <typename T>
+struct RingArgs {
+  int Nsp, Nm, Nb;
+  double mubd;
+  const int* __restrict__ moff;
+  const int* __restrict__ boff;
+  const T* __restrict__ tabm;
+  const T* __restrict__ tabb;
+  const T* __restrict__ A;
+  T* __restrict__ H;
+  int* __restrict__ nneg;
+  int* __restrict__ status;
+};
+
+__device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+__device__ __forceinline__ int sgn_d(double x) { return (unsigned)__double2hiint(x) >> 31; }
+__device__ __forceinline__ int exp_d(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+__device__ __forceinline__ int sgn_f(float x) { return (unsigned)__float_as_int(x) >> 31; }
+
+// Sturm count (eigenvalues < x) of the scaled tridiagonal in shared memory.
+__device__ int sturm64(const double* d, const double* e2, double x) {
+  double pm = 1.0, p = d[0] - x;
+  int cnt = sgn_d(p);
+#pragma unroll
+  for (int i = 1; i < RN; ++i) {
+    double pn = (d[i] - x) * p - e2[i - 1] * pm;
+    if (exp_d(pn) == 0) pn = sgn_d(p) ? 1e-300 : -1e-300;
+    cnt += sgn_d(pn) ^ sgn_d(p);
+    const int ea = exp_d(pn), eb = exp_d(p), mx = ea > eb ? ea : eb;
+    if (mx > 1023 + 500 || mx < 1023 - 500) {
+      const double sc = mx > 1023 ? 0x1p-500 : 0x1p500;
+      pn *= sc;
+      p *= sc;
+    }
+    pm = p;
+    p = pn;
+  }
+  return cnt;
+}
+
+__device__ int sturm32(const float* d, const float* e2, float x) {
+  float pm = 1.0f, p = d[0] - x;
+  int cnt = sgn_f(p);
+#pragma unroll
+  for (int i = 1; i < RN; ++i) {
+    float pn = (d[i] - x) * p - e2[i - 1] * pm;
+    if (pn == 0.0f) pn = sgn_f(p) ? 1e-30f : -1e-30f;
+    cnt += sgn_f(pn) ^ sgn_f(p);
+    const float mx = fmaxf(fabsf(pn), fabsf(p));
+    if (mx > 1e30f || mx < 1e-30f) {
+      const float sc = mx > 1.0f ? 1e-30f : 1e30f;
+      pn *= sc;
+      p *= sc;
+    }
+    pm = p;
+    p = pn;
+  }
+  return cnt;
+}
+
+// Solves (T - sig I) y = y in place by Gaussian elimination with partial
+// pivoting, eliminating and applying to y in one forward pass (U kept).
+__device__ void tri_solve(const double* d, const double* e, double sig, double (&y)[RN]) {
+  double u0r[RN], u1[RN], u2[RN];
+  double c0 = d[0] - sig, c1 = e[0], c2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < RN - 1; ++i) {
+    const double ei = e[i], a1 = d[i + 1] - sig, e1 = (i + 1 < RN - 1) ? e[i + 1] : 0.0;
+    if (fabs(ei) > fabs(c0)) {
+      const double r = 1.0 / ei, m = c0 * r;
+      u0r[i] = r; u1[i] = a1; u2[i] = e1;
+      const double t = y[i];
+      y[i] = y[i + 1];
+      y[i + 1] = t - m * y[i + 1];
+      c0 = c1 - m * a1; c1 = c2 - m * e1; c2 = 0.0;
+    } else {
+      if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
+      const double r = 1.0 / c0, m = ei * r;
+      u0r[i] = r; u1[i] = c1; u2[i] = c2;
+      y[i + 1] -= m * y[i];
+      c0 = a1 - m * c1; c1 = e1 - m * c2; c2 = 0.0;
+    }
+  }
+  if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
+  u0r[RN - 1] = 1.0 / c0; u1[RN - 1] = u2[RN - 1] = 0.0;
+#pragma unroll
+  for (int i = RN - 1; i >= 0; --i) {
+    double s = y[i];
+    if (i + 1 < RN) s -= u1[i] * y[i + 1];
+    if (i + 2 < RN) s -= u2[i] * y[i + 2];
+    y[i] = s * u0r[i];
+  }
+}
+
+// Modified Gram-Schmidt across lanes: in order j = 0, 1, ..., lane j
+// normalises its vector, broadcasts it, and lanes j+1..kneg-1 remove its
+// component.
+__device__ void warp_mgs(double (&y)[RN], int lane, int kneg) {
+  for (int j = 0; j < kneg; ++j) {
+    if (lane == j) {
+      double nn = 0.0;
+#pragma unroll
+      for (int i = 0; i < RN; ++i) nn += y[i] * y[i];
+      const double inv = 1.0 / sqrt(nn);
+#pragma unroll
+      for (int i = 0; i < RN; ++i) y[i] *= inv;
+    }
+    double yj[RN];
+#pragma unroll
+    for (int i = 0; i < RN; ++i) yj[i] = shfl(y[i], j);
+    if (lane > j && lane < kneg) {
+      double dt = 0.0;
+#pragma unroll
+      for (int i = 0; i < RN; ++i) dt += yj[i] * y[i];
+#pragma unroll
+      for (int i = 0; i < RN; ++i) y[i] -= dt * yj[i];
+    }
+  }
+}
+
+// (row, column) of packed upper-triangle entry e of a 27 x 27 matrix
+__constant__ unsigned char c_row[H27], c_col[H27];
+
+template <typename T>
+__global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const int* __restrict__ list, int count,
+                                                         unsigned int* __restrict__ work) {
+  constexpr int WARPS = RBLOCK / 32;
+  __shared__ double s_refl[WARPS][RN][RN];  // reflector k in column k (rows k+1..), tau_k at [k][k]
+  __shared__ double s_d[WARPS][RN], s_e[WARPS][RN], s_e2[WARPS][RN];
+  __shared__ float s_d32[WARPS][RN], s_e232[WARPS][RN];
+  __shared__ double s_w[WARPS][27];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  double* const refl = &s_refl[wp][0][0];
+  double* const dd = s_d[wp];
+  double* const ee = s_e[wp];
+  double* const ee2 = s_e2[wp];
+  const int kp = lane / 3, dp = lane % 3;  // this lane's column j = 3 kp + dp
+  for (;;) {
+    int idx = 0;
+    if (lane == 0) idx = (int)atomicAdd(work, 1u);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (idx >= count) break;
+    const int s = list[idx];
+    const int q0 = P.moff[s], q1 = P.moff[s + 1], b0 = P.boff[s], b1 = P.boff[s + 1];
+
+    // ---- column lane of H_r = sum_q (G~ (x) I3) A_q (G~ (x) I3)^T + bending
+    double col[RN];
+#pragma unroll
+    for (int i = 0; i < RN; ++i) col[i] = 0.0;
+    for (int q = q0; q < q1; ++q) {
+      double gt[8][2];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) gt[k][0] = gt[k][1] = 0.0;
+#pragma unroll
+      for (int l = 0; l < 9; ++l) {
+        const double g0 = (double)P.tabm[(1 + 2 * l) * P.Nm + q], g1 = (double)P.tabm[(2 + 2 * l) * P.Nm + q];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          gt[k][0] += c_helmert[k][l] * g0;
+          gt[k][1] += c_helmert[k][l] * g1;
+        }
+      }
+      double A6[6][6];
+      {
+        int e = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+          for (int c = r; c < 6; ++c) {
+            A6[r][c] = (double)P.A[(e++) * P.Nm + q];
+            A6[c][r] = A6[r][c];
+          }
+      }
+      if (lane < RN) {
+        double gk0 = 0.0, gk1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (k == kp) { gk0 = gt[k][0]; gk1 = gt[k][1]; }
+        // t[b][c] = sum_delta g~[kp][delta] A6[3b + c][3 delta + dp]
+        double t[2][3];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+            for (int z = 0; z < 3; ++z)
+              if (z == dp) { a0 = A6[3 * b + c][z]; a1 = A6[3 * b + c][3 + z]; }
+            t[b][c] = gk0 * a0 + gk1 * a1;
+          }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) col[3 * k + c] += gt[k][0] * t[0][c] + gt[k][1] * t[1][c];
+      }
+    }
+    for (int q = b0; q < b1; ++q) {
+      const double WB = (double)P.tabb[q] * P.mubd;
+      double Lt[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) Lt[k] = 0.0;
+#pragma unroll
+      for (int l = 0; l < 9; ++l) {
+        const double L = (double)P.tabb[(1 + l) * P.Nb + q];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Lt[k] += c_helmert[k][l] * L;
+      }
+      double Lk = 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k == kp) Lk = Lt[k];
+      if (lane < RN) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (c == dp) col[3 * k + c] += WB * Lt[k] * Lk;
+      }
+    }
+
+    // ---- Householder tridiagonalisation, lane k owns column k
+#pragma unroll
+    for (int k = 0; k < RN - 2; ++k) {
+      double sigma = 0.0;
+#pragma unroll
+      for (int i = k + 2; i < RN; ++i) sigma += col[i] * col[i];
+      const double x0 = col[k + 1];
+      const double nrm = sqrt(x0 * x0 + sigma);
+      const double alpha = x0 >= 0.0 ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double tau = sigma == 0.0 ? 0.0 : 2.0 / (v0 * v0 + sigma);
+      const double tau_k = shfl(tau, k);
+      if (lane == k) {
+        dd[k] = col[k];
+        ee[k] = sigma == 0.0 ? x0 : alpha;
+        refl[k * RN + k] = tau;
+        col[k + 1] = sigma == 0.0 ? x0 : v0;
+#pragma unroll
+        for (int i = k + 1; i < RN; ++i) refl[i * RN + k] = col[i];
+      }
+      if (tau_k == 0.0) continue;
+      double v[RN];
+#pragma unroll
+      for (int i = k + 1; i < RN; ++i) v[i] = shfl(col[i], k);
+      // p_j = tau sum_i A(i, j) v_i for j > k;  w_j = p_j - (tau/2)(v.p) v_j
+      double p = 0.0, vj = 0.0;
+#pragma unroll
+      for (int i = k + 1; i < RN; ++i) {
+        p += col[i] * v[i];
+        if (i == lane) vj = v[i];
+      }
+      const bool act = lane > k && lane < RN;
+      p = act ? tau_k * p : 0.0;
+      double vp = act ? vj * p : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) vp += __shfl_xor_sync(0xffffffffu, vp, o);
+      const double wj = p - 0.5 * tau_k * vp * vj;
+      double w[RN];
+#pragma unroll
+      for (int i = k + 1; i < RN; ++i) w[i] = shfl(wj, i);
+      if (act) {
+#pragma unroll
+        for (int i = k + 1; i < RN; ++i) col[i] -= v[i] * wj + w[i] * vj;
+      }
+    }
+    if (lane == RN - 2) {
+      dd[RN - 2] = col[RN - 2];
+      ee[RN - 2] = col[RN - 1];
+      refl[(RN - 2) * RN + RN - 2] = 0.0;
+    }
+    if (lane == RN - 1) {
+      dd[RN - 1] = col[RN - 1];
+      ee[RN - 1] = 0.0;
+    }
+    __syncwarp();
+
+    // ---- scale, inertia
+    double tn = 0.0;
+#pragma unroll
+    for (int i = 0; i < RN; ++i) tn = fmax(tn, fabs(dd[i]) + fabs(ee[i]) + (i > 0 ? fabs(ee[i - 1]) : 0.0));
+    __syncwarp();
+    if (!(tn > 0.0) || !isfinite(tn)) {
+      if (lane == 0) {
+        P.nneg[s] = 0;
+        if (!isfinite(tn)) atomicOr(P.status, BSC_STATUS_NUMERIC_FLAG);
+      }
+      continue;
+    }
+    const double itn = 1.0 / tn;
+    if (lane < RN) {
+      const double ds = dd[lane] * itn, es = ee[lane] * itn;
+      dd[lane] = ds;
+      ee[lane] = es;
+      ee2[lane] = es * es;
+      s_d32[wp][lane] = (float)ds;
+      s_e232[wp][lane] = (float)(es * es);
+    }
+    __syncwarp();
+    const int kneg = sturm64(dd, ee2, -NEG_REL);
+    if (lane == 0) P.nneg[s] = kneg;
+    if (kneg == 0) continue;
+
+    // ---- lane k < kneg: eigenvalue k (FP32 bracket, FP64 check + refinement)
+    double sig = 0.0;
+    if (lane < kneg) {
+      float a32 = -1.0f - 1e-6f, b32 = (float)(-NEG_REL);
+      for (int it = 0; it < 22; ++it) {
+        const float mid = 0.5f * (a32 + b32);
+        if (sturm32(s_d32[wp], s_e232[wp], mid) > lane) b32 = mid;
+        else a32 = mid;
+      }
+      double a = fmax((double)a32 - 4e-6, -1.0 - 1e-12), b = fmin((double)b32 + 4e-6, -NEG_REL);
+      if (!(sturm64(dd, ee2, a) <= lane && sturm64(dd, ee2, b) > lane)) {
+        a = -1.0 - 1e-12;
+        b = -NEG_REL;
+      }
+      for (int it = 0; it < 40 && b - a > 1e-10; ++it) {
+        const double mid = 0.5 * (a + b);
+        if (sturm64(dd, ee2, mid) > lane) b = mid;
+        else a = mid;
+      }
+      sig = 0.5 * (a + b);
+    }
+    // ---- inverse iteration, two solves, Gram-Schmidt across lanes after each
+    double y[RN];
+#pragma unroll
+    for (int i = 0; i < RN; ++i) y[i] = 1.0 + 0.125 * (double)((7 * i + 3 * lane) % 5);
+    for (int it = 0; it < 2; ++it) {
+      if (lane < kneg) tri_solve(dd, ee, sig, y);
+      warp_mgs(y, lane, kneg);
+    }
+    double lam = 0.0;
+    if (lane < kneg) {
+      double rq = 0.0;
+#pragma unroll
+      for (int i = 0; i < RN; ++i) {
+        double ty = dd[i] * y[i];
+        if (i > 0) ty += ee[i - 1] * y[i - 1];
+        if (i + 1 < RN) ty += ee[i] * y[i + 1];
+        rq += y[i] * ty;
+      }
+      lam = fmin(rq, 0.0) * tn;
+      // back-transformation x = H_0 ... H_{RN-3} y
+#pragma unroll
+      for (int k = RN - 3; k >= 0; --k) {
+        const double t = refl[k * RN + k];
+        double sdot = 0.0;
+#pragma unroll
+        for (int i = k + 1; i < RN; ++i) sdot += refl[i * RN + k] * y[i];
+        sdot *= t;
+#pragma unroll
+        for (int i = k + 1; i < RN; ++i) y[i] -= sdot * refl[i * RN + k];
+      }
+    }
+    // w = (Q (x) I3) x on each active lane
+    double wv[27];
+#pragma unroll
+    for (int l = 0; l < 9; ++l)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc += c_helmert[k][l] * y[3 * k + c];
+        wv[3 * l + c] = lane < kneg ? acc : 0.0;
+      }
+    // ---- H -= sum_k lam_k w_k w_k^T: lane handles packed entries e = lane + 32 m;
+    //      w_k is staged in shared memory by its lane
+    double corr[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) corr[m] = 0.0;
+    double* const sw = s_w[wp];
+    for (int k = 0; k < kneg; ++k) {
+      const double lk = shfl(lam, k);
+      if (lane == k) {
+#pragma unroll
+        for (int r = 0; r < 27; ++r) sw[r] = wv[r];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < 12; ++m) {
+        const int e = lane + 32 * m;
+        if (e < H27) corr[m] += lk * sw[c_row[e]] * sw[c_col[e]];
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+      const int e = lane + 32 * m;
+      if (e < H27) {
+        T* h = P.H + (size_t)e * P.Nsp + s;
+        *h = (T)((double)*h - corr[m]);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+cudaError_t setup_projection_ring() {
+  double h[8][9];
+  for (int k = 1; k <= 8; ++k) {
+    const double sc = 1.0 / sqrt((double)k * (k + 1));
+    for (int l = 0; l < 9; ++l) h[k - 1][l] = l < k ? sc : (l == k ? -k * sc : 0.0);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_helmert, h, sizeof(h));
+  if (e != cudaSuccess) return e;
+  unsigned char rr[H27], cc[H27];
+  int k = 0;
+  for (int r = 0; r < 27; ++r)
+    for (int c = r; c < 27; ++c, ++k) {
+      rr[k] = (unsigned char)r;
+      cc[k] = (unsigned char)c;
+    }
+  e = cudaMemcpyToSymbol(c_row, rr, sizeof(rr));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_col, cc, sizeof(cc));
+}
+
+int ring_grid(int num_sms) { return 2 * num_sms; }
+
+cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* work, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  BSC_COUNT(c, 1);
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  const int need = (count + RBLOCK / 32 - 1) / (RBLOCK / 32);
+  int g = ring_grid(c->num_sms);
+  if (g > need) g = need;
+  if (c->precision == BSC_FP64) {
+    RingArgs<double> P{c->Nsp, c->Nmem, c->Nbd, c->mu_bd, c->mem_off, c->bd_off, (const double*)c->tab_mem,
+                       (const double*)c->tab_bd, (const double*)c->A_mem, (double*)c->H_span, c->nneg, c->dstatus};
+    k_project_ring<double><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work);
+  } else {
+    RingArgs<float> P{c->Nsp, c->Nmem, c->Nbd, c->mu_bd, c->mem_off, c->bd_off, (const float*)c->tab_mem,
+                      (const float*)c->tab_bd, (const float*)c->A_mem, (float*)c->H_span, c->nneg, c->dstatus};
+    k_project_ring<float><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work);
+  }
+  return cudaGetLastError();
+}

@@ -16,11 +16,12 @@
 
 namespace {
 
+// Row alpha of y = K x in the element type T (FP32 bulk arithmetic in FP32 mode).
 template <typename T>
 __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T* __restrict__ K,
-                                         const T* __restrict__ x, double y[3]) {
+                                         const T* __restrict__ x, T y[3]) {
   const int i = al % nu, j = al / nu;
-  y[0] = y[1] = y[2] = 0.0;
+  T y0 = T(0), y1 = T(0), y2 = T(0);
 #pragma unroll
   for (int dv = -2; dv <= 2; ++dv) {
     const int jb = j + dv;
@@ -30,13 +31,14 @@ __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T*
       const int ib = i + du;
       if (ib < 0 || ib >= nu) continue;
       const int slot = (dv + 2) * 5 + (du + 2), be = jb * nu + ib;
-      const double x0 = (double)__ldg(x + be), x1 = (double)__ldg(x + N + be), x2 = (double)__ldg(x + 2 * N + be);
+      const T x0 = __ldg(x + be), x1 = __ldg(x + N + be), x2 = __ldg(x + 2 * N + be);
       const T* Kb = K + (size_t)slot * 9 * N + al;
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-        y[r] += (double)Kb[(3 * r) * N] * x0 + (double)Kb[(3 * r + 1) * N] * x1 + (double)Kb[(3 * r + 2) * N] * x2;
+      y0 += Kb[0] * x0 + Kb[(size_t)N] * x1 + Kb[(size_t)2 * N] * x2;
+      y1 += Kb[(size_t)3 * N] * x0 + Kb[(size_t)4 * N] * x1 + Kb[(size_t)5 * N] * x2;
+      y2 += Kb[(size_t)6 * N] * x0 + Kb[(size_t)7 * N] * x1 + Kb[(size_t)8 * N] * x2;
     }
   }
+  y[0] = y0; y[1] = y1; y[2] = y2;
 }
 
 template <typename T>
@@ -44,11 +46,11 @@ __global__ void k_spmv(int nu, int nv, const T* __restrict__ K, const T* __restr
   const int N = nu * nv;
   const int al = blockIdx.x * blockDim.x + threadIdx.x;
   if (al >= N) return;
-  double acc[3];
+  T acc[3];
   spmv_row<T>(nu, nv, N, al, K, x, acc);
-  y[al] = (T)acc[0];
-  y[N + al] = (T)acc[1];
-  y[2 * N + al] = (T)acc[2];
+  y[al] = acc[0];
+  y[N + al] = acc[1];
+  y[2 * N + al] = acc[2];
 }
 
 // Inverse of each 3x3 diagonal block (adjugate / determinant, FP64).
@@ -108,11 +110,10 @@ __device__ __forceinline__ double grid_sum(const double* part, int G, double* sm
 }
 
 template <typename T>
-__device__ __forceinline__ void apply_dinv(const T* __restrict__ Dinv, int N, int al, const double r[3], double z[3]) {
+__device__ __forceinline__ void apply_dinv(const T* __restrict__ Dinv, int N, int al, const T r[3], T z[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c)
-    z[c] = (double)Dinv[(3 * c) * N + al] * r[0] + (double)Dinv[(3 * c + 1) * N + al] * r[1] +
-           (double)Dinv[(3 * c + 2) * N + al] * r[2];
+    z[c] = Dinv[(3 * c) * N + al] * r[0] + Dinv[(3 * c + 1) * N + al] * r[1] + Dinv[(3 * c + 2) * N + al] * r[2];
 }
 
 template <typename T, int BLOCK>
@@ -125,20 +126,20 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
 
   double l_rz = 0.0, l_bb = 0.0;
   for (int al = tid; al < N; al += stride) {
-    double rr[3], zz[3];
+    T rr[3], zz[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       A.x[c * N + al] = T(0);
-      rr[c] = (double)A.b[c * N + al];
-      A.r[c * N + al] = (T)rr[c];
+      rr[c] = A.b[c * N + al];
+      A.r[c * N + al] = rr[c];
     }
     apply_dinv<T>(A.Dinv, N, al, rr, zz);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      A.z[c * N + al] = (T)zz[c];
-      A.p[c * N + al] = (T)zz[c];
-      l_rz += rr[c] * zz[c];
-      l_bb += rr[c] * rr[c];
+      A.z[c * N + al] = zz[c];
+      A.p[c * N + al] = zz[c];
+      l_rz += (double)rr[c] * (double)zz[c];
+      l_bb += (double)rr[c] * (double)rr[c];
     }
   }
   {
@@ -160,12 +161,12 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
     for (it = 1; it <= A.maxit; ++it) {
       double l_pq = 0.0;
       for (int al = tid; al < N; al += stride) {
-        double y[3];
+        T y[3];
         spmv_row<T>(A.nu, A.nv, N, al, A.K, A.p, y);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          A.q[c * N + al] = (T)y[c];
-          l_pq += (double)A.p[c * N + al] * y[c];
+          A.q[c * N + al] = y[c];
+          l_pq += (double)A.p[c * N + al] * (double)y[c];
         }
       }
       {
@@ -180,22 +181,22 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
         break;
       }
       const double alpha = rz / pq;
+      const T ta = (T)alpha;
       double l_rz2 = 0.0, l_rr = 0.0;
       for (int al = tid; al < N; al += stride) {
-        double rr[3], zz[3];
+        T rr[3], zz[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          A.x[c * N + al] = (T)((double)A.x[c * N + al] + alpha * (double)A.p[c * N + al]);
-          rr[c] = (double)A.r[c * N + al] - alpha * (double)A.q[c * N + al];
-          A.r[c * N + al] = (T)rr[c];
-          rr[c] = (double)A.r[c * N + al];
+          A.x[c * N + al] += ta * A.p[c * N + al];
+          rr[c] = A.r[c * N + al] - ta * A.q[c * N + al];
+          A.r[c * N + al] = rr[c];
         }
         apply_dinv<T>(A.Dinv, N, al, rr, zz);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          A.z[c * N + al] = (T)zz[c];
-          l_rz2 += rr[c] * (double)(T)zz[c];
-          l_rr += rr[c] * rr[c];
+          A.z[c * N + al] = zz[c];
+          l_rz2 += (double)rr[c] * (double)zz[c];
+          l_rr += (double)rr[c] * (double)rr[c];
         }
       }
       {
@@ -211,11 +212,11 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
       rr_glob = grid_sum<BLOCK>(A.partial + G, G, sm);
       if (rr_glob <= stop2 || !isfinite(rr_glob)) break;
       const double beta = rz2 / rz;
+      const T tb = (T)beta;
       rz = rz2;
       for (int al = tid; al < N; al += stride)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-          A.p[c * N + al] = (T)((double)A.z[c * N + al] + beta * (double)A.p[c * N + al]);
+        for (int c = 0; c < 3; ++c) A.p[c * N + al] = A.z[c * N + al] + tb * A.p[c * N + al];
       if (!(ok = grid_barrier(cnt, gen, A.status))) break;
     }
   }
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
 template <typename T>
 __global__ void k_axpy(int n, const T* __restrict__ a, const T* __restrict__ d, double alpha, T* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) out[k] = (T)((double)a[k] + alpha * (double)d[k]);
+  if (k < n) out[k] = a[k] + (T)alpha * d[k];
 }
 
 template <typename T, int BLOCK>
@@ -282,6 +283,7 @@ int pcg_grid_size(int precision, int num_sms, int N) {
 }
 
 cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y) {
+  BSC_COUNT(c, 1);
   const int B = 256, G = (c->N + B - 1) / B;
   if (c->precision == BSC_FP64)
     k_spmv<double><<<G, B, 0, c->stream>>>(c->nu, c->nv, (const double*)K, (const double*)x, (double*)y);
@@ -291,11 +293,13 @@ cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y) {
 }
 
 cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit) {
+  BSC_COUNT(c, 2);
   if (c->precision == BSC_FP64) return pcg_t<double>(c, K, b, x, tol, maxit);
   return pcg_t<float>(c, K, b, x, tol, maxit);
 }
 
 cudaError_t launch_axpy_trial(bsc_ctx* c, const void* C, const void* d, double alpha, void* out) {
+  BSC_COUNT(c, 1);
   const int n = 3 * c->N, B = 256, G = (n + B - 1) / B;
   if (c->precision == BSC_FP64)
     k_axpy<double><<<G, B, 0, c->stream>>>(n, (const double*)C, (const double*)d, alpha, (double*)out);
@@ -309,6 +313,7 @@ cudaError_t launch_copy_vec(bsc_ctx* c, const void* src, void* dst) {
 }
 
 cudaError_t launch_absmax(bsc_ctx* c, const void* x, double* dout) {
+  BSC_COUNT(c, 2);
   constexpr int B = 256;
   const int n = 3 * c->N, G = c->red_grid;
   if (c->precision == BSC_FP64)

@@ -230,6 +230,7 @@ cudaError_t run(bsc_ctx* c, const void* C, int want_grad, int want_hess) {
 }  // namespace
 
 cudaError_t launch_span_eval(bsc_ctx* c, const void* C, int want_grad, int want_hess) {
+  BSC_COUNT(c, 1);
   if (c->precision == BSC_FP64) return run<double, 64>(c, C, want_grad, want_hess);
   return run<float, 128>(c, C, want_grad, want_hess);
 }

@@ -252,6 +252,7 @@ cudaError_t launch_build_tables(bsc_ctx* c) {
   int *cm = nullptr, *cb = nullptr;
   if ((e = cudaMalloc(&cm, sizeof(int) * Nsp)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&cb, sizeof(int) * Nsp)) != cudaSuccess) { cudaFree(cm); return e; }
+  BSC_COUNT(c, 3);
   k_count_points<<<G, B, 0, c->stream>>>(c->Su, c->Sv, c->mem_rule, c->bend_rule, cm, cb);
   int* hcm = (int*)malloc(sizeof(int) * Nsp);
   int* hcb = (int*)malloc(sizeof(int) * Nsp);

@@ -1,0 +1,474 @@
+// Per-span SPD projection (projected Newton, Sec. 5.1) in FP64, written for
+// one GPU thread per span with a small on-chip working set:
+//   A  packed lower triangle of the reduced Hessian (3D x 3D), then the
+//      Householder vectors, with tau_k kept in the freed diagonal slot;
+//   R  3n doubles: first the orthonormal basis Q (9 x D), then the scaled
+//      tridiagonal (d, e, e^2);
+//   Qs, Ys  per-thread scratch slots (global memory): the basis Q for the
+//      final mapping and the eigenvectors found so far (for
+//      re-orthogonalisation inside clusters).
+// The span Hessian in HBM is corrected in place, P = H - sum lam w w^T over
+// the negative eigenpairs.  __host__ __device__ so the same code runs on the
+// host for checks.
+#pragma once
+
+#include <math.h>
+
+#ifndef BSC_HD
+#ifdef __CUDACC__
+#define BSC_HD __host__ __device__ __forceinline__
+#else
+#define BSC_HD inline
+#endif
+#endif
+
+namespace proj {
+
+// Strided view (interleaved shared memory on the GPU, plain arrays on the host).
+struct View {
+  double* p;
+  int s;
+  BSC_HD double& operator[](int i) const { return p[(long)i * s]; }
+};
+
+BSC_HD int lp(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+// Sign bit and biased exponent of a double without FP64 pipe instructions.
+BSC_HD int sign_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__double2hiint(x) >> 31;
+#else
+  return signbit(x) ? 1 : 0;
+#endif
+}
+BSC_HD int expo_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (__double2hiint(x) >> 20) & 0x7ff;
+#else
+  int e;
+  if (x == 0.0) return 0;
+  frexp(x, &e);
+  return e + 1022;
+#endif
+}
+
+// Eigenvalues of the scaled tridiagonal below x (signs of the leading
+// principal minors of T - x I; Sylvester's law of inertia).  d at R[0..n),
+// e^2 at R[2n..3n).  Minors are kept in range by exact power-of-two scaling.
+template <int n>
+BSC_HD int sturm(const View& R, double x) {
+  double pm = 1.0, p = R[0] - x;
+  int cnt = sign_of(p);
+#pragma unroll
+  for (int i = 1; i < n; ++i) {
+    double pn = (R[i] - x) * p - R[2 * n + i - 1] * pm;
+    if (expo_of(pn) == 0) pn = sign_of(p) ? 1e-300 : -1e-300;  // exact zero: sign opposite to p
+    cnt += sign_of(pn) ^ sign_of(p);
+    // the recurrence is homogeneous in (p_i, p_i-1): rescale the pair by a power
+    // of two when the larger of the two leaves [2^-500, 2^500]
+    const int ea = expo_of(pn), eb = expo_of(p), mx = ea > eb ? ea : eb;
+    if (mx > 1023 + 500 || mx < 1023 - 500) {
+      const double sc = mx > 1023 ? 0x1p-500 : 0x1p500;
+      pn *= sc;
+      p *= sc;
+    }
+    pm = p;
+    p = pn;
+  }
+  return cnt;
+}
+
+// The same count in FP32 on a copy of the scaled tridiagonal: the FP32 pipe
+// is 64x the FP64 one, so the bracket of each eigenvalue is narrowed here
+// first and only validated and refined in FP64.  The FP32 count is exact for
+// a tridiagonal within a few FP32 ulps of T, so its brackets are widened
+// before the FP64 check.
+BSC_HD int sign_of_f(float x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__float_as_int(x) >> 31;
+#else
+  return signbit(x) ? 1 : 0;
+#endif
+}
+
+template <int n>
+BSC_HD int sturm32(const float (&d)[n], const float (&e2)[n], float x) {
+  float pm = 1.0f, p = d[0] - x;
+  int cnt = sign_of_f(p);
+#pragma unroll
+  for (int i = 1; i < n; ++i) {
+    float pn = (d[i] - x) * p - e2[i - 1] * pm;
+    if (pn == 0.0f) pn = sign_of_f(p) ? 1e-30f : -1e-30f;
+    cnt += sign_of_f(pn) ^ sign_of_f(p);
+    const float mx = fmaxf(fabsf(pn), fabsf(p));
+    if (mx > 1e30f || mx < 1e-30f) {
+      const float sc = mx > 1.0f ? 1e-30f : 1e30f;
+      pn *= sc;
+      p *= sc;
+    }
+    pm = p;
+    p = pn;
+  }
+  return cnt;
+}
+
+// Householder vectors in A(i, k), i > k; tau_k in A(k, k).  x <- H_0 ... H_{n-3} x.
+template <int n>
+BSC_HD void back_transform(const View& A, double (&x)[n]) {
+#pragma unroll
+  for (int k = n - 3; k >= 0; --k) {
+    const double t = A[lp(k, k)];
+    double s = 0.0;
+#pragma unroll
+    for (int i = k + 1; i < n; ++i) s += A[lp(i, k)] * x[i];
+    s *= t;
+#pragma unroll
+    for (int i = k + 1; i < n; ++i) x[i] -= s * A[lp(i, k)];
+  }
+}
+
+// Phase 1 of a span: basis, reduced Hessian, tridiagonal form, inertia.
+// Tab: nm(), nb(), g(q, l, beta), L(q, l), wb(q) = W mu_bd, a6(q, e) (packed
+// upper 6x6).  On return R holds the scaled tridiagonal (d, e, e^2), A the
+// reflectors, Qs the basis, *tn the scale; returns the number of eigenvalues
+// below -neg_rel ||T|| (-1 on a non-finite matrix).
+template <int D, class Tab>
+BSC_HD int span_phase1(const Tab& tab, const View& A, const View& R, const View& Qs, double* tn_out,
+                       double neg_rel, double rank_rel) {
+  constexpr int n = 3 * D;
+  constexpr int NP = n * (n + 1) / 2;
+#pragma unroll 1
+  for (int k = 0; k < NP; ++k) A[k] = 0.0;
+
+  // 1. orthonormal basis Q (rows of R) of the span of the derivative vectors,
+  //    with the constant vector removed (it lies in the kernel of every one)
+  int d = 0;
+  const int nm = tab.nm(), nb = tab.nb(), nvec = 2 * nm + nb;
+  for (int iv = 0; iv < nvec; ++iv) {
+    double v[9];
+    if (iv < 2 * nm) {
+#pragma unroll
+      for (int l = 0; l < 9; ++l) v[l] = tab.g(iv >> 1, l, iv & 1);
+    } else {
+#pragma unroll
+      for (int l = 0; l < 9; ++l) v[l] = tab.L(iv - 2 * nm, l);
+    }
+    double mean = 0.0;
+#pragma unroll
+    for (int l = 0; l < 9; ++l) mean += v[l];
+    mean *= (1.0 / 9.0);
+    double n0 = 0.0;
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+      v[l] -= mean;
+      n0 += v[l] * v[l];
+    }
+    if (d >= D || n0 == 0.0) continue;
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        if (k >= d) break;
+        double dt = 0.0;
+#pragma unroll
+        for (int l = 0; l < 9; ++l) dt += R[9 * k + l] * v[l];
+#pragma unroll
+        for (int l = 0; l < 9; ++l) v[l] -= dt * R[9 * k + l];
+      }
+    double n1 = 0.0;
+#pragma unroll
+    for (int l = 0; l < 9; ++l) n1 += v[l] * v[l];
+    if (n1 <= rank_rel * rank_rel * n0) continue;
+    const double inv = 1.0 / sqrt(n1);
+#pragma unroll
+    for (int l = 0; l < 9; ++l) R[9 * d + l] = v[l] * inv;
+    ++d;
+  }
+  for (int k = d; k < D; ++k)
+#pragma unroll
+    for (int l = 0; l < 9; ++l) R[9 * k + l] = 0.0;
+
+  // 2. reduced Hessian, lower triangle, index 3k + c
+  for (int q = 0; q < nm; ++q) {
+    double gr[D][2];
+#pragma unroll
+    for (int k = 0; k < D; ++k) gr[k][0] = gr[k][1] = 0.0;
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+      const double g0 = tab.g(q, l, 0), g1 = tab.g(q, l, 1);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double qk = R[9 * k + l];
+        gr[k][0] += qk * g0;
+        gr[k][1] += qk * g1;
+      }
+    }
+    double A6[6][6];
+    {
+      int e = 0;
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c) {
+          A6[r][c] = tab.a6(q, e++);
+          A6[c][r] = A6[r][c];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      double Tk[3][6];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) Tk[c][j] = gr[k][0] * A6[c][j] + gr[k][1] * A6[3 + c][j];
+#pragma unroll
+      for (int k2 = 0; k2 <= k; ++k2)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int dd = 0; dd < 3; ++dd) {
+            if (k2 == k && dd > c) continue;
+            A[lp(3 * k + c, 3 * k2 + dd)] += Tk[c][dd] * gr[k2][0] + Tk[c][3 + dd] * gr[k2][1];
+          }
+    }
+  }
+  for (int q = 0; q < nb; ++q) {
+    const double WB = tab.wb(q);
+    double Lr[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) Lr[k] = 0.0;
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+      const double L = tab.L(q, l);
+#pragma unroll
+      for (int k = 0; k < D; ++k) Lr[k] += R[9 * k + l] * L;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int k2 = 0; k2 <= k; ++k2) {
+        const double h = WB * Lr[k] * Lr[k2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[lp(3 * k + c, 3 * k2 + c)] += h;
+      }
+  }
+  // keep Q for the final mapping
+#pragma unroll
+  for (int k = 0; k < 9 * D; ++k) Qs[k] = R[k];
+
+  // 3. Householder tridiagonalisation: d -> R[0..n), e -> R[n..2n); the
+  //    reflector v_k stays in column k of A, p = tau A v in R[2n..3n).
+  //    Operands come from shared memory: the FP64 pipe, not the loads, is
+  //    the limit, and no per-thread arrays compete for registers.
+#pragma unroll 1
+  for (int k = 0; k < n - 2; ++k) {
+    R[k] = A[lp(k, k)];
+    const double x0 = A[lp(k + 1, k)];
+    double sigma = 0.0;
+#pragma unroll 1
+    for (int i = k + 2; i < n; ++i) {
+      const double a = A[lp(i, k)];
+      sigma += a * a;
+    }
+    if (sigma == 0.0) {
+      R[n + k] = x0;
+      A[lp(k, k)] = 0.0;
+      continue;
+    }
+    const double nrm = sqrt(x0 * x0 + sigma);
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+    const double v0 = x0 - alpha;
+    const double t = 2.0 / (v0 * v0 + sigma);
+    R[n + k] = alpha;
+    A[lp(k, k)] = t;
+    A[lp(k + 1, k)] = v0;
+    // p_i = t sum_j A(i, j) v_j over the trailing block (rows of the lower triangle)
+#pragma unroll 1
+    for (int i = k + 1; i < n; ++i) {
+      double acc = 0.0;
+      const int ri = i * (i + 1) / 2;
+#pragma unroll 1
+      for (int j = k + 1; j <= i; ++j) acc += A[ri + j] * A[j * (j + 1) / 2 + k];
+#pragma unroll 1
+      for (int j = i + 1; j < n; ++j) acc += A[j * (j + 1) / 2 + i] * A[j * (j + 1) / 2 + k];
+      R[2 * n + i] = t * acc;
+    }
+    double vp = 0.0;
+#pragma unroll 1
+    for (int i = k + 1; i < n; ++i) vp += A[i * (i + 1) / 2 + k] * R[2 * n + i];
+    const double K = 0.5 * t * vp;
+#pragma unroll 1
+    for (int i = k + 1; i < n; ++i) R[2 * n + i] -= K * A[i * (i + 1) / 2 + k];  // w
+#pragma unroll 1
+    for (int i = k + 1; i < n; ++i) {
+      const double vi = A[i * (i + 1) / 2 + k], wi = R[2 * n + i];
+      const int ri = i * (i + 1) / 2;
+#pragma unroll 1
+      for (int j = k + 1; j <= i; ++j) A[ri + j] -= vi * R[2 * n + j] + wi * A[j * (j + 1) / 2 + k];
+    }
+  }
+  R[n - 2] = A[lp(n - 2, n - 2)];
+  R[n + n - 2] = A[lp(n - 1, n - 2)];
+  R[n - 1] = A[lp(n - 1, n - 1)];
+  R[2 * n - 1] = 0.0;
+
+  // 4. scale to ||T|| <= 1; e^2 -> R[2n..3n)
+  double tn = 0.0;
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    const double r = fabs(R[i]) + fabs(R[n + i]) + (i > 0 ? fabs(R[n + i - 1]) : 0.0);
+    tn = fmax(tn, r);
+  }
+  *tn_out = tn;
+  if (!(tn > 0.0) || !isfinite(tn)) return isfinite(tn) ? 0 : -1;
+  const double itn = 1.0 / tn;
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    const double ds = R[i] * itn, es = R[n + i] * itn;
+    R[i] = ds;
+    R[n + i] = es;
+    R[2 * n + i] = es * es;
+  }
+  return sturm<n>(R, -neg_rel);
+}
+
+// Phase 2: eigenpair k (k-th smallest) of a span whose phase 1 is done:
+// FP32 bracket from *lo32 (raised to the bracket's lower end on return), FP64
+// check and bisection to a 1e-10 bracket, inverse iteration (two solves) with
+// re-orthogonalisation against the span's eigenvectors 0..k-1 in Ys,
+// Rayleigh quotient, back-transformation, w = (Q (x) I3) x, and the rank-one
+// correction H -= lam w w^T.  F holds the FP32 copy of (d, e^2).
+template <int D, class HAcc>
+BSC_HD void span_eigpair(const View& A, const View& R, const View& Qs, const View& Ys, const float* F, int fs,
+                         float* lo32, double tn, int k, HAcc& Hs, double neg_rel) {
+  constexpr int n = 3 * D;
+  float d32[n], e232[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    d32[i] = F[i * fs];
+    e232[i] = F[(n + i) * fs];
+  }
+  const double lo_all = -1.0 - 1e-12, hi_all = -neg_rel;
+  {
+    // FP32 bracket (about 22 bits), then an FP64 check of the widened bracket
+    float a32 = *lo32, b32 = (float)hi_all;
+#pragma unroll 1
+    for (int it = 0; it < 22; ++it) {
+      const float mid = 0.5f * (a32 + b32);
+      if (sturm32<n>(d32, e232, mid) > k) b32 = mid;
+      else a32 = mid;
+    }
+    *lo32 = a32;
+    double a = fmax((double)a32 - 4e-6, lo_all), b = fmin((double)b32 + 4e-6, hi_all);
+    if (!(sturm<n>(R, a) <= k && sturm<n>(R, b) > k)) {
+      a = lo_all;
+      b = hi_all;
+    }
+#pragma unroll 1
+    for (int it = 0; it < 40 && b - a > 1e-10; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (sturm<n>(R, mid) > k) b = mid;
+      else a = mid;
+    }
+    const double sig = 0.5 * (a + b);
+    // Gaussian elimination with partial pivoting of T - sig I (one reciprocal a row)
+    double u0r[n], u1[n], u2[n], mu[n];
+    unsigned sw = 0u;
+    {
+      double c0 = R[0] - sig, c1 = R[n], c2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < n - 1; ++i) {
+        const double ei = R[n + i];
+        const double a1 = R[i + 1] - sig, e1 = (i + 1 < n - 1) ? R[n + i + 1] : 0.0;
+        if (fabs(ei) > fabs(c0)) {
+          sw |= 1u << i;
+          const double r = 1.0 / ei;
+          const double m = c0 * r;
+          mu[i] = m;
+          u0r[i] = r;
+          u1[i] = a1;
+          u2[i] = e1;
+          c0 = c1 - m * a1;
+          c1 = c2 - m * e1;
+          c2 = 0.0;
+        } else {
+          if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
+          const double r = 1.0 / c0;
+          const double m = ei * r;
+          mu[i] = m;
+          u0r[i] = r;
+          u1[i] = c1;
+          u2[i] = c2;
+          c0 = a1 - m * c1;
+          c1 = e1 - m * c2;
+          c2 = 0.0;
+        }
+      }
+      if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
+      u0r[n - 1] = 1.0 / c0;
+      u1[n - 1] = u2[n - 1] = 0.0;
+    }
+    double y[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.125 * (double)((7 * i + 3 * k) % 5);
+    for (int it = 0; it < 3; ++it) {
+      for (int j = 0; j < k; ++j) {
+        double dt = 0.0;
+#pragma unroll
+        for (int i = 0; i < n; ++i) dt += Ys[j * n + i] * y[i];
+#pragma unroll
+        for (int i = 0; i < n; ++i) y[i] -= dt * Ys[j * n + i];
+      }
+      if (it < 2) {
+#pragma unroll
+        for (int i = 0; i < n - 1; ++i) {
+          if (sw & (1u << i)) {
+            const double t = y[i];
+            y[i] = y[i + 1];
+            y[i + 1] = t - mu[i] * y[i + 1];
+          } else {
+            y[i + 1] -= mu[i] * y[i];
+          }
+        }
+#pragma unroll
+        for (int i = n - 1; i >= 0; --i) {
+          double s = y[i];
+          if (i + 1 < n) s -= u1[i] * y[i + 1];
+          if (i + 2 < n) s -= u2[i] * y[i + 2];
+          y[i] = s * u0r[i];
+        }
+      }
+      double nn = 0.0;
+#pragma unroll
+      for (int i = 0; i < n; ++i) nn += y[i] * y[i];
+      const double inv = 1.0 / sqrt(nn);
+#pragma unroll
+      for (int i = 0; i < n; ++i) y[i] *= inv;
+    }
+    double rq = 0.0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      double ty = R[i] * y[i];
+      if (i > 0) ty += R[n + i - 1] * y[i - 1];
+      if (i + 1 < n) ty += R[n + i] * y[i + 1];
+      rq += y[i] * ty;
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i) Ys[k * n + i] = y[i];
+    const double lam = fmin(rq, 0.0) * tn;
+    back_transform<n>(A, y);
+    double w[27];
+#pragma unroll
+    for (int l = 0; l < 9; ++l)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) acc += Qs[9 * kk + l] * y[3 * kk + c];
+        w[3 * l + c] = acc;
+      }
+    Hs.rank1(lam, w);
+  }
+}
+
+}  // namespace proj

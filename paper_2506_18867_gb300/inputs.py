@@ -229,3 +229,15 @@ def config_random_small(seed: int, nu: int, nv: int, angle: float | None = None,
     Chat = C + 0.01 * span * normal(seed + 31, C.size).reshape(C.shape)
     return Patch(f"rand{nu}x{nv}", nu, nv, rest, C, Chat, mat, 0.01, (0.0, -9.81, 0.0), pins,
                  {"seed": seed, "span_m": span})
+
+
+def crop(patch: Patch, mu: int, mv: int | None = None) -> Patch:
+    """The leading mu x mv control points of a patch (same span length, same
+    state, pins restricted to the crop): a bounded sample of a large workload."""
+    mv = mu if mv is None else mv
+    idx = np.array([j * patch.nu + i for j in range(mv) for i in range(mu)])
+    remap = {int(a): k for k, a in enumerate(idx)}
+    pins = np.array([remap[int(p)] for p in patch.pinned if int(p) in remap], dtype=np.int32)
+    return Patch(f"{patch.name}_crop{mu}x{mv}", mu, mv, patch.rest[idx].copy(), patch.C[idx].copy(),
+                 patch.Chat[idx].copy(), patch.material, patch.dt, patch.gravity, pins,
+                 dict(patch.meta, crop=(mu, mv)))

@@ -220,6 +220,35 @@ bsc_status bsc_launch_count(const bsc_ctx* ctx, unsigned long long* launches);
  * (the 3 x 8 mean-free subspace). */
 bsc_status bsc_projection_stats(bsc_ctx* ctx, int* nneg, int* nred);
 
+/* ---- solve without device allocation ----------------------------------------
+ * The paper has no counterpart of this entry point.
+ *
+ * Same preconditioned CG as bsc_solve, for callers that cannot allocate
+ * device memory themselves: host code whose memory manager owns all of the
+ * device memory and forbids cudaMalloc, or a loop that cannot afford the
+ * device-wide synchronisation cudaMalloc / cudaFree bring.  It needs no
+ * context: K_dev (225 planes of nu*nv, the stencil layout above), b_dev and
+ * x_dev (3 planes each) are the caller's device buffers of the element type
+ * given by precision; nothing is allocated.  The working set (block-Jacobi
+ * inverses, CG vectors, reductions, barrier words) lives in one fixed
+ * file-scope device array sized for BSC_STATIC_SOLVE_MAX_CP control points
+ * (about 2.8 MB, held on every device that loads the library until the
+ * process exits); larger grids return BSC_ERR_INVALID_ARG with a message.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture on the device.
+ *   - Every call on a device uses the same array and leaves its contents
+ *     behind (the barrier words are cleared at the start of each call).  Calls
+ *     that may overlap on the GPU - issued on two streams, or from two host
+ *     threads driving the same device - race and must be serialised by the
+ *     caller.
+ *   - The call synchronises cuda_stream (NULL = legacy default stream) to
+ *     read back iters / rel_res (host, may be NULL).  Errors: the status, and
+ *     a message through bsc_last_error(NULL). */
+#define BSC_STATIC_SOLVE_MAX_CP 16384
+bsc_status bsc_solve_static(int nu, int nv, int precision, const void* K_dev, const void* b_dev, void* x_dev,
+                            double rel_tol, int max_iter, void* cuda_stream, int* iters, double* rel_res);
+
 #ifdef __cplusplus
 }
 #endif

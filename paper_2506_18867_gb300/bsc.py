@@ -29,7 +29,9 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5:
 EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc_energy", "bsc_gradient",
            "bsc_assemble_hessian", "bsc_spmv", "bsc_solve", "bsc_newton_step", "bsc_span_terms",
            "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes", "bsc_set_profiling", "bsc_phase_times",
-           "bsc_launch_count", "bsc_projection_stats")
+           "bsc_launch_count", "bsc_projection_stats", "bsc_solve_static")
+
+STATIC_SOLVE_MAX_CP = 16384  # BSC_STATIC_SOLVE_MAX_CP in include/bsc.h
 
 
 class KnotGrid(ct.Structure):
@@ -101,6 +103,7 @@ def load(path: str = LIB_PATH):
     lib.bsc_phase_times.argtypes = [P, ct.POINTER(D)]
     lib.bsc_launch_count.argtypes = [P, ct.POINTER(ct.c_ulonglong)]
     lib.bsc_projection_stats.argtypes = [P, ct.POINTER(I), ct.POINTER(I)]
+    lib.bsc_solve_static.argtypes = [I, I, I, V, V, V, D, I, V, ct.POINTER(I), ct.POINTER(D)]
     for name in EXPORTS:
         if name not in ("bsc_destroy", "bsc_last_error"):
             getattr(lib, name).restype = I
@@ -286,6 +289,22 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def solve_static(nu, nv, precision, K, b, x, rel_tol=1e-8, max_iter=10000, stream=None):
+    """K x = b without any device allocation (bsc_solve_static): the working set
+    lives in a fixed device array sized for STATIC_SOLVE_MAX_CP control points.
+    Returns (iterations, relative residual); raises BscError on failure."""
+    lib = load()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    it, rr = ct.c_int(), ct.c_double()
+    st = lib.bsc_solve_static(int(nu), int(nv), int(precision), _ptr(K), _ptr(b), _ptr(x), float(rel_tol),
+                              int(max_iter), ct.c_void_p(stream), ct.byref(it), ct.byref(rr))
+    if st != OK:
+        raise BscError(st, lib.bsc_last_error(None).decode())
+    return it.value, rr.value
 
 
 def context_for_patch(patch, precision=FP64, **kw):

@@ -82,6 +82,9 @@ bsc_status eval_path(bsc_ctx* c, const void* C, int want_grad, int want_hess, in
 
 }  // namespace
 
+// Message of a failed context-free call, read back through bsc_last_error(NULL).
+void bsc_set_thread_error(const char* msg) { snprintf(g_create_err, sizeof(g_create_err), "%s", msg); }
+
 extern "C" {
 
 const char* bsc_last_error(const bsc_ctx* c) { return c ? c->err : g_create_err; }

@@ -323,3 +323,143 @@ cudaError_t launch_absmax(bsc_ctx* c, const void* x, double* dout) {
   k_max_partials<B><<<1, B, 0, c->stream>>>(G, c->partials, dout);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// bsc_solve_static: the preconditioned CG of bsc_solve for callers that cannot
+// allocate device memory, with its working set in a fixed device array.
+// ---------------------------------------------------------------------------
+#include <mutex>
+#include <stdio.h>
+
+void bsc_set_thread_error(const char* msg);
+
+namespace {
+
+// Working set of one solve of up to BSC_STATIC_SOLVE_MAX_CP control points in
+// FP64: the 3x3 block-Jacobi inverses (9 N), the CG vectors r, z, p, q (4 x
+// 3 N), cross-block partial sums, the grid-barrier words, a status word and
+// the result scalars.  Every device that loads the library holds it until the
+// process exits.
+constexpr size_t kStaticCp = BSC_STATIC_SOLVE_MAX_CP;
+constexpr size_t kStaticMaxGrid = 1024;
+constexpr size_t kStaticDoubles = 21 * kStaticCp + 3 * kStaticMaxGrid + 16;
+static __device__ __align__(256) double g_solve_scratch[kStaticDoubles];
+
+std::mutex g_static_mu;
+void* g_static_ptr[64];  // device address of g_solve_scratch, per device
+
+template <typename T>
+cudaError_t static_solve_t(int nu, int nv, double* scratch, const void* K, const void* b, void* x, double tol,
+                           int maxit, cudaStream_t st, int num_sms, double* out_host) {
+  constexpr int B = 256;
+  const int N = nu * nv;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, B>, B, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2) per_sm = 2;
+  int grid = num_sms * per_sm;
+  const int need = (N + B - 1) / B;
+  if (grid > need) grid = need;
+  if (grid > (int)kStaticMaxGrid) grid = (int)kStaticMaxGrid;
+  // carve the array: T vectors first (FP64 slots hold FP32 vectors too)
+  T* base = reinterpret_cast<T*>(scratch);
+  T* Dinv = base;
+  T* r = Dinv + 9 * (size_t)N;
+  T* z = r + 3 * (size_t)N;
+  T* p = z + 3 * (size_t)N;
+  T* q = p + 3 * (size_t)N;
+  double* partial = scratch + 21 * kStaticCp;
+  double* tail = partial + 3 * kStaticMaxGrid;
+  unsigned int* sync = reinterpret_cast<unsigned int*>(tail);  // 4 words
+  int* status = reinterpret_cast<int*>(tail + 2);                // 1 word
+  double* outd = tail + 4;                                        // 3 doubles
+  // the barrier words and the status must start at zero on every call
+  if ((e = cudaMemsetAsync(tail, 0, 4 * sizeof(double), st)) != cudaSuccess) return e;
+  k_block_jacobi<T><<<(N + 255) / 256, 256, 0, st>>>(N, (const T*)K, Dinv, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  PcgArgs<T> A;
+  A.nu = nu; A.nv = nv; A.N = N; A.maxit = maxit; A.tol = tol;
+  A.K = (const T*)K; A.Dinv = Dinv; A.b = (const T*)b; A.x = (T*)x;
+  A.r = r; A.z = z; A.p = p; A.q = q;
+  A.partial = partial; A.sync = sync; A.status = status; A.out = outd;
+  void* args[] = {&A};
+  e = cudaLaunchCooperativeKernel((const void*)k_pcg<T, B>, dim3(grid), dim3(B), args, 0, st);
+  if (e != cudaSuccess) return e;
+  double stat_d = 0.0;
+  if ((e = cudaMemcpyAsync(out_host, outd, 3 * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  int flags = 0;
+  if ((e = cudaMemcpyAsync(&flags, status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  (void)stat_d;
+  out_host[3] = (double)flags;
+  return cudaSuccess;
+}
+
+bsc_status static_fail(bsc_status st, const char* msg) {
+  bsc_set_thread_error(msg);
+  return st;
+}
+
+}  // namespace
+
+extern "C" bsc_status bsc_solve_static(int nu, int nv, int precision, const void* K_dev, const void* b_dev,
+                                       void* x_dev, double rel_tol, int max_iter, void* cuda_stream, int* iters,
+                                       double* rel_res) {
+  char msg[256];
+  if (nu < 5 || nv < 5) return static_fail(BSC_ERR_INVALID_ARG, "bsc_solve_static: nu, nv must be >= 5");
+  if ((long long)nu * nv > (long long)BSC_STATIC_SOLVE_MAX_CP) {
+    snprintf(msg, sizeof(msg), "bsc_solve_static: %d x %d = %lld control points exceed the fixed working set "
+             "of %d control points; use bsc_solve", nu, nv, (long long)nu * nv, BSC_STATIC_SOLVE_MAX_CP);
+    return static_fail(BSC_ERR_INVALID_ARG, msg);
+  }
+  if (precision != BSC_FP64 && precision != BSC_FP32)
+    return static_fail(BSC_ERR_INVALID_ARG, "bsc_solve_static: unknown precision");
+  if (!K_dev || !b_dev || !x_dev) return static_fail(BSC_ERR_INVALID_ARG, "bsc_solve_static: NULL pointer");
+  if ((((uintptr_t)K_dev) | ((uintptr_t)b_dev) | ((uintptr_t)x_dev)) & 15u)
+    return static_fail(BSC_ERR_INVALID_ARG, "bsc_solve_static: pointers must be 16-byte aligned");
+  if (b_dev == x_dev) return static_fail(BSC_ERR_INVALID_ARG, "bsc_solve_static: b and x must not alias");
+  if (!(rel_tol > 0.0)) rel_tol = 1e-8;
+  if (max_iter <= 0) max_iter = 10000;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    snprintf(msg, sizeof(msg), "bsc_solve_static: device query failed: %s", cudaGetErrorString(e));
+    return static_fail(BSC_ERR_CUDA, msg);
+  }
+  void* ptr = nullptr;
+  {
+    // first call on this device: look up the array's device address (with
+    // the device current); later calls reuse it
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      e = cudaGetSymbolAddress(&g_static_ptr[dev], g_solve_scratch);
+      if (e != cudaSuccess) {
+        g_static_ptr[dev] = nullptr;
+        snprintf(msg, sizeof(msg), "bsc_solve_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        return static_fail(BSC_ERR_CUDA, msg);
+      }
+    }
+    ptr = g_static_ptr[dev];
+  }
+  double out[4] = {0, 0, 0, 0};
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  e = precision == BSC_FP64
+          ? static_solve_t<double>(nu, nv, (double*)ptr, K_dev, b_dev, x_dev, rel_tol, max_iter, st, sms, out)
+          : static_solve_t<float>(nu, nv, (double*)ptr, K_dev, b_dev, x_dev, rel_tol, max_iter, st, sms, out);
+  if (e != cudaSuccess) {
+    snprintf(msg, sizeof(msg), "bsc_solve_static: %s", cudaGetErrorString(e));
+    return static_fail(BSC_ERR_CUDA, msg);
+  }
+  if (iters) *iters = (int)out[0];
+  if (rel_res) *rel_res = out[1];
+  const int flags = (int)out[3];
+  if (flags & BSC_STATUS_TIMEOUT_FLAG) return static_fail(BSC_ERR_TIMEOUT, "bsc_solve_static: device wait timed out");
+  if (flags) return static_fail(BSC_ERR_NUMERIC, "bsc_solve_static: non-finite or singular value on the device");
+  if (!(out[1] <= rel_tol)) {
+    snprintf(msg, sizeof(msg), "bsc_solve_static: %d iterations, rel. residual %g", (int)out[0], out[1]);
+    return static_fail(BSC_ERR_NOT_CONVERGED, msg);
+  }
+  return BSC_OK;
+}

@@ -64,6 +64,8 @@ def lib():
         _lib.or_basis9.argtypes = [P, ct.c_double, ct.c_double, I, I, D]
         _lib.or_lumped_mass.argtypes = [P, D]
         _lib.or_span_eval.argtypes = [P, D, D, D, D]
+        _lib.or_span_terms_subset.argtypes = [P, D, I, ct.POINTER(I), I, D, D, D]
+        _lib.or_eval_rows.argtypes = [P, S, D, D, I, ct.POINTER(I), D, D]
         _lib.or_project_psd.argtypes = [I, D, D, D]
         _lib.or_project_psd.restype = I
         _lib.or_eval.argtypes = [P, S, D, D, D, D]
@@ -141,6 +143,29 @@ class Problem:
         H = np.zeros((self.n_spans, 27, 27)) if want_H else None
         lib().or_span_eval(ct.byref(self._p), _dp(C), _dp(E), _dp(g), _dp(H))
         return E, g, H
+
+
+def span_terms_subset(prob, C, spans, project=True):
+    """E, g, H (projected when project) of the selected spans only."""
+    C = _f64(C).reshape(prob.n_cp, 3)
+    sp = np.ascontiguousarray(np.asarray(spans, dtype=np.int32))
+    n = sp.size
+    E, g, H = np.zeros(n), np.zeros((n, 27)), np.zeros((n, 27, 27))
+    lib().or_span_terms_subset(ct.byref(prob._p), _dp(C), n, sp.ctypes.data_as(ct.POINTER(ct.c_int)),
+                               int(bool(project)), _dp(E), _dp(g), _dp(H))
+    return E, g, H
+
+
+def eval_rows(prob, scene, C, Chat, rows):
+    """Gradient entries (n, 3) and stencil rows (n, 25, 3, 3) of selected control points."""
+    C = _f64(C).reshape(prob.n_cp, 3)
+    Chat = C if Chat is None else _f64(Chat).reshape(prob.n_cp, 3)
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32))
+    n = r.size
+    g, K = np.zeros((n, 3)), np.zeros((n, 25, 3, 3))
+    lib().or_eval_rows(ct.byref(prob._p), ct.byref(scene._s), _dp(C), _dp(Chat), n,
+                       r.ctypes.data_as(ct.POINTER(ct.c_int)), _dp(g), _dp(K))
+    return g, K
 
 
 class Scene:

@@ -445,6 +445,46 @@ void or_span_eval(const or_problem* p, const double* C, double* E_span, double* 
   free(E);
 }
 
+/* Selected spans only: points are enumerated as in or_span_eval and those
+ * whose owner span is not selected are skipped. */
+void or_span_terms_subset(const or_problem* p, const double* C, int n, const int* spans, int project,
+                          double* E, double* g, double* H) {
+  int Su = p->nu - 2, Sv = p->nv - 2, Nsp = Su * Sv;
+  int* sel = (int*)malloc(sizeof(int) * Nsp);
+  for (int s = 0; s < Nsp; ++s) sel[s] = -1;
+  for (int k = 0; k < n; ++k) sel[spans[k]] = k;
+  memset(E, 0, sizeof(double) * n);
+  memset(g, 0, sizeof(double) * 27 * (size_t)n);
+  memset(H, 0, sizeof(double) * 729 * (size_t)n);
+  for (int which = 0; which < 2; ++which) {
+    qlist L = {0, 0, 0};
+    build_rule(p, which, &L);
+    for (int k = 0; k < L.n; ++k) {
+      const qpoint* q = &L.pts[k];
+      int j = sel[q->b * Su + q->a];
+      if (j < 0) continue;
+      pgeom G;
+      point_geometry(p, q, &G);
+      double W = q->w * fabs(G.detJ);
+      double Cl[9][3];
+      gather9(p, C, q->a, q->b, Cl);
+      if (which == 0)
+        membrane_point(p, &G, W, Cl, &E[j], g + 27 * (size_t)j, H + 729 * (size_t)j);
+      else
+        bending_point(p, &G, W, Cl, &E[j], g + 27 * (size_t)j, H + 729 * (size_t)j);
+    }
+    free(L.pts);
+  }
+  if (project) {
+    double P[729];
+    for (int j = 0; j < n; ++j) {
+      or_project_psd(27, H + 729 * (size_t)j, P, NULL);
+      memcpy(H + 729 * (size_t)j, P, sizeof(P));
+    }
+  }
+  free(sel);
+}
+
 /* ------------------------------------------------------------------------ */
 /* PSD projection (projected Newton, Sec. 5.1): cyclic Jacobi eigensystem    */
 /* ------------------------------------------------------------------------ */
@@ -604,6 +644,79 @@ double or_eval(const or_problem* p, const or_scene* sc, const double* C, const d
 
 double or_energy(const or_problem* p, const or_scene* sc, const double* C, const double* Chat) {
   return eval_impl(p, sc, C, Chat, NULL, NULL);
+}
+
+/* Rows of eval_impl for selected control points: the spans touching each
+ * row are evaluated (and projected when sc->project), then gathered. */
+void or_eval_rows(const or_problem* p, const or_scene* sc, const double* C, const double* Chat, int n,
+                  const int* rows, double* g, double* K) {
+  int nu = p->nu, nv = p->nv, N = nu * nv, Su = nu - 2, Sv = nv - 2, Nsp = Su * Sv;
+  char* need = (char*)calloc((size_t)Nsp, 1);
+  for (int k = 0; k < n; ++k) {
+    int i = rows[k] % nu, j = rows[k] / nu;
+    for (int b = j - 2; b <= j; ++b)
+      for (int a = i - 2; a <= i; ++a)
+        if (a >= 0 && a < Su && b >= 0 && b < Sv) need[b * Su + a] = 1;
+  }
+  int ns = 0;
+  for (int s = 0; s < Nsp; ++s) ns += need[s];
+  int* list = (int*)malloc(sizeof(int) * (ns ? ns : 1));
+  int* pos = (int*)malloc(sizeof(int) * Nsp);
+  ns = 0;
+  for (int s = 0; s < Nsp; ++s) {
+    pos[s] = need[s] ? ns : -1;
+    if (need[s]) list[ns++] = s;
+  }
+  double* Es = (double*)malloc(sizeof(double) * (ns ? ns : 1));
+  double* gs = (double*)malloc(sizeof(double) * 27 * (size_t)(ns ? ns : 1));
+  double* Hs = (double*)malloc(sizeof(double) * 729 * (size_t)(ns ? ns : 1));
+  or_span_terms_subset(p, C, ns, list, sc->project, Es, gs, Hs);
+  double* m = (double*)malloc(sizeof(double) * N);
+  or_lumped_mass(p, m);
+  char* pin = (char*)calloc((size_t)N, 1);
+  for (int k = 0; k < sc->n_pinned; ++k) pin[sc->pinned[k]] = 1;
+  memset(g, 0, sizeof(double) * 3 * (size_t)n);
+  memset(K, 0, sizeof(double) * 225 * (size_t)n);
+  for (int k = 0; k < n; ++k) {
+    int al = rows[k], i = al % nu, j = al / nu;
+    double* gk = g + 3 * (size_t)k;
+    double* Kk = K + 225 * (size_t)k;
+    for (int b = j - 2; b <= j; ++b)
+      for (int a = i - 2; a <= i; ++a) {
+        if (a < 0 || a >= Su || b < 0 || b >= Sv) continue;
+        int jj = pos[b * Su + a], l = (j - b) * 3 + (i - a);
+        for (int c = 0; c < 3; ++c) gk[c] += gs[27 * (size_t)jj + 3 * l + c];
+        for (int mm = 0; mm < 9; ++mm) {
+          int du = a + mm % 3 - i, dv = b + mm / 3 - j;
+          double* blk = Kk + 9 * slot_of(du, dv);
+          for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d) blk[3 * c + d] += Hs[729 * (size_t)jj + (3 * l + c) * 27 + 3 * mm + d];
+        }
+      }
+    const double* x = C + 3 * al;
+    for (int c = 0; c < 3; ++c) {
+      if (sc->dt > 0.0) {
+        double kk = m[al] / (sc->dt * sc->dt);
+        gk[c] += kk * (x[c] - Chat[3 * al + c]);
+        Kk[9 * slot_of(0, 0) + 4 * c] += kk;
+      }
+      gk[c] -= m[al] * sc->gravity[c];
+    }
+    for (int dv = -2; dv <= 2; ++dv)
+      for (int du = -2; du <= 2; ++du) {
+        int ii = i + du, jj2 = j + dv;
+        if (ii < 0 || ii >= nu || jj2 < 0 || jj2 >= nv) continue;
+        int be = jj2 * nu + ii;
+        if (pin[al] || pin[be]) {
+          double* blk = Kk + 9 * slot_of(du, dv);
+          for (int e = 0; e < 9; ++e) blk[e] = 0.0;
+          if (al == be) blk[0] = blk[4] = blk[8] = 1.0;
+        }
+      }
+    if (pin[al])
+      for (int c = 0; c < 3; ++c) gk[c] = 0.0;
+  }
+  free(need); free(list); free(pos); free(Es); free(gs); free(Hs); free(m); free(pin);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -63,6 +63,16 @@ void or_lumped_mass(const or_problem* p, double* m);
 void or_span_eval(const or_problem* p, const double* C, double* E_span,
                   double* g_span, double* H_span);
 
+/* Span terms of selected spans only (same definitions as or_span_eval):
+ * E[n], g[n][27], H[n][27][27] for spans[0..n); H projected when project. */
+void or_span_terms_subset(const or_problem* p, const double* C, int n, const int* spans, int project,
+                          double* E, double* g, double* H);
+
+/* Gradient entries g[n][3] and stencil rows K[n][25][3][3] of selected
+ * control points (same definition as or_eval). */
+void or_eval_rows(const or_problem* p, const or_scene* sc, const double* C, const double* Chat, int n,
+                  const int* rows, double* g, double* K);
+
 /* PSD projection of one symmetric n x n matrix: V max(Lambda, 0) V^T, with
  * the eigensystem from cyclic Jacobi.  Returns the number of sweeps. */
 int or_project_psd(int n, const double* H, double* P, double* eig_out);

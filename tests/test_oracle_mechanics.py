@@ -256,3 +256,22 @@ def test_plate_deflection_converges_to_navier_solution(orc):
         errs.append(abs(-z - w_exact) / w_exact)
     assert errs[-1] < 0.02, errs
     assert errs[0] > errs[1] > errs[2], errs
+
+
+def test_subset_drivers_match_full_evaluation(orc):
+    """The selected-span and selected-row drivers reproduce the full evaluation."""
+    pat = inputs.config_random_small(17, 9, 8, noise=0.2)
+    p = orc.Problem.from_patch(pat)
+    sc = orc.Scene.from_patch(pat, project=True)
+    E, g, H = p.span_eval(pat.C)
+    spans = [0, 5, 17, 30, 41]
+    Es, gs, Hs = orc.span_terms_subset(p, pat.C, spans, project=False)
+    np.testing.assert_array_equal(Es, E[spans])
+    np.testing.assert_array_equal(Hs, H[spans])
+    _, _, Hp = orc.span_terms_subset(p, pat.C, spans, project=True)
+    assert np.abs(Hp[2] - orc.project_psd(H[17])[0]).max() == 0.0
+    Ef, gf, Kf = orc.evaluate(p, sc, pat.C, pat.Chat)
+    rows = [0, 3, 8, 20, 40, 71]
+    gr, Kr = orc.eval_rows(p, sc, pat.C, pat.Chat, rows)
+    np.testing.assert_allclose(gr, gf[rows], rtol=1e-13, atol=1e-13 * np.abs(gf).max())
+    np.testing.assert_allclose(Kr, Kf[rows], rtol=1e-13, atol=1e-13 * np.abs(Kf).max())

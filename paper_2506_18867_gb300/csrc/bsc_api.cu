@@ -59,6 +59,8 @@ void free_ctx(bsc_ctx* c) {
   for (void* p : c->proj_scratch)
     if (p) cudaFree(p);
   if (c->proj_work) cudaFree(c->proj_work);
+  if (c->proj_span) cudaFree(c->proj_span);
+  if (c->proj_kneg) cudaFree(c->proj_kneg);
   for (int i = 0; i < 2; ++i) {
     if (c->side[i]) cudaStreamDestroy(c->side[i]);
     if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);

@@ -54,7 +54,9 @@ struct bsc_ctx {
   int bucket_off[4];  // host: start of each bucket in bucket_list
   int* nneg;          // [Nsp] negative eigenvalues found per span (diagnostic)
   int proj_grid[3];   // resident grid per class
-  double* proj_scratch[3];  // per-thread slots: Q (9 D) and eigenvectors (n x n)
+  double* proj_scratch[3];  // per-thread slots of the interior phase-2 kernel (cluster eigenvectors)
+  double* proj_span;        // per-span scratch of the interior class
+  int* proj_kneg;           // negative-eigenvalue count per interior span (class order)
   unsigned int* proj_work;  // [3] work counters
   cudaStream_t side[2];     // forked streams for the two small classes
   cudaEvent_t fork_ev, join_ev[2];

@@ -13,15 +13,18 @@
 // proj::project_span (tridiagonalisation, Sturm bisection, inverse
 // iteration).
 //
-// Spans are grouped by D (5, 7, 8).  A block takes BLOCK spans at a time from
-// its class's work counter.  Phase 1 (one thread per span) builds H_r,
-// tridiagonalises it and counts its negative eigenvalues; phase 2 runs in
-// rounds, round r computing eigenpair r of every span that has one, with the
-// (span, r) items compacted onto the block's first threads so that no warp
-// carries masked lanes through the FP64 work (masked lanes cost the FP64 pipe
-// as much as active ones).  Working sets live in interleaved shared memory,
-// the basis and eigenvectors of a span in a per-thread global scratch slot.
-// The three classes run concurrently on forked streams.
+// Interior spans (five derivative vectors, D = 5, n = 15).  A block takes
+// BLOCK spans at a time from a work counter.  Phase 1 (one thread per span)
+// builds H_r, tridiagonalises it and counts its negative eigenvalues.
+// Phase 2a computes every negative eigenvalue of the batch as an independent
+// item spread over the block; phase 2b computes the eigenvectors, one item
+// per cluster of close eigenvalues; phase 2c lets each owner apply its rank-k
+// correction.  Items are spread over all threads, so no warp carries masked
+// lanes through FP64 work (masked lanes cost the FP64 pipe as much as active
+// ones) and no thread waits on another span's eigenvalue count.  Working
+// sets live in interleaved shared memory; basis, eigenvalues, eigenvectors
+// and w vectors in a per-thread global scratch slot.  The border spans run
+// concurrently in k_project_ring on a forked stream.
 #include "bsc_internal.cuh"
 #include "proj_core.cuh"
 
@@ -72,7 +75,7 @@ template <typename T>
 struct SpanH {
   T* H;
   int Nsp, s;
-  __device__ void rank1(double lam, const double (&w)[27]) {
+  __device__ __forceinline__ void rank1(double lam, const double (&w)[27]) {
     T wt[27], lw[27];
 #pragma unroll
     for (int r = 0; r < 27; ++r) {
@@ -97,125 +100,228 @@ struct Smem {
   static constexpr int DOUBLES = NP + 3 * n + 1, FLOATS = 2 * n + 1;
 };
 
-template <typename T, int D, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1)
-    k_project(ProjArgs<T> P, const int* __restrict__ list, int count, double* __restrict__ scratch,
-              unsigned int* __restrict__ work) {
-  constexpr int n = 3 * D, NP = Smem<D>::NP;
+// Per-span scratch of the interior class (global memory, entry-major over
+// the span's position in the class list): reflectors + tau (packed A),
+// scaled tridiagonal (d, e, e^2), basis Q, scale ||T||, eigenvalues, and the
+// span-DOF vectors w of the negative eigenpairs.
+template <int D>
+struct SpanScratch {
+  static constexpr int n = 3 * D, NP = n * (n + 1) / 2;
+  static constexpr int A = 0, R = NP, Q = R + 3 * n, TN = Q + 9 * D, LAM = TN + 1, W = LAM + n, SIZE = W + 27 * n;
+};
+
+// Eigenvalues of a span closer than this (on the tridiagonal scaled to
+// ||T|| <= 1) form a cluster whose eigenvectors are orthogonalised
+// explicitly; farther apart, inverse iteration alone leaves them orthogonal
+// to about eps / gap.
+constexpr double CLUSTER_GAP = 1e-3;
+
+constexpr int P1_BLOCK = 160;  // five warps; packed H_r and R in shared memory
+constexpr int P2_BLOCK = 128;
+
+// Strided view of element type T over the scratch (w vectors, lam w).
+template <typename T>
+struct TView {
+  T* p;
+  int s;
+  __device__ __forceinline__ void set(int i, double v) const { p[(size_t)i * s] = (T)v; }
+  __device__ __forceinline__ T operator[](int i) const { return p[(size_t)i * s]; }
+};
+
+// H -= sum_r lam_r w_r w_r^T for one span in one pass over its 378 packed
+// entries, in the element type (w_r already in T in the scratch).
+template <typename T>
+__device__ __noinline__ void apply_corrections(T* H, int Nsp, int s, proj::View Lam, TView<T> Ws, int kneg) {
+  T lam[32];
+#pragma unroll 1
+  for (int r = 0; r < kneg; ++r) lam[r] = (T)Lam[r];
+  int a = 0, c = 0;
+#pragma unroll 1
+  for (int e = 0; e < H27; ++e) {
+    T acc = T(0);
+#pragma unroll 1
+    for (int r = 0; r < kneg; ++r) acc += lam[r] * Ws[27 * r + a] * Ws[27 * r + c];
+    T* h = H + (size_t)e * Nsp + s;
+    *h -= acc;
+    if (++c == 27) c = ++a;
+  }
+}
+
+// Phase 1: one thread per interior span (uniform work, no barriers).
+template <typename T, int D>
+__global__ void __launch_bounds__(P1_BLOCK, 1)
+    k_proj_p1(ProjArgs<T> P, const int* __restrict__ list, int count, double* __restrict__ sspan,
+              int* __restrict__ kneg_out) {
+  constexpr int n = 3 * D, NP = n * (n + 1) / 2;
+  using SS = SpanScratch<D>;
   extern __shared__ __align__(16) double smd[];
-  double* const Abase = smd;
-  double* const Rbase = smd + (size_t)NP * BLOCK;
-  double* const Tn = smd + (size_t)(NP + 3 * n) * BLOCK;
-  float* const Fbase = reinterpret_cast<float*>(smd + (size_t)Smem<D>::DOUBLES * BLOCK);
-  float* const Lo = Fbase + 2 * n * BLOCK;
-  __shared__ int s_kneg[BLOCK], s_span[BLOCK], s_list[BLOCK], s_wcnt[BLOCK / 32];
-  __shared__ int s_base;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nslots = gridDim.x * BLOCK, slot0 = blockIdx.x * BLOCK;
-  for (;;) {
-    // a batch of BLOCK spans per block, taken from the class's work counter
-    if (tid == 0) s_base = (int)atomicAdd(work, (unsigned)BLOCK);
-    __syncthreads();
-    const int base = s_base;
-    if (base >= count) break;
-    // phase 1 (uniform work): one span per thread
-    const int t = base + tid;
-    int kneg = 0, s = -1;
-    if (t < count) {
-      s = list[t];
-      const int q0 = P.moff[s], b0 = P.boff[s];
-      SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.Nm, P.Nb, P.moff[s + 1] - q0, P.boff[s + 1] - b0,
-                     P.mubd};
-      const proj::View A{Abase + tid, BLOCK}, R{Rbase + tid, BLOCK};
-      const proj::View Qs{scratch + slot0 + tid, nslots};
-      double tn = 0.0;
-      kneg = proj::span_phase1<D>(tab, A, R, Qs, &tn, NEG_REL, RANK_REL);
-      if (kneg < 0) {
-        atomicOr(P.status, BSC_STATUS_NUMERIC_FLAG);
-        kneg = 0;
-      }
-      Tn[tid] = tn;
-#pragma unroll
-      for (int i = 0; i < n; ++i) {
-        Fbase[i * BLOCK + tid] = (float)R[i];
-        Fbase[(n + i) * BLOCK + tid] = (float)R[2 * n + i];
-      }
-      Lo[tid] = -1.0f - 1e-6f;
-      P.nneg[s] = kneg;
+  const proj::View A{smd + threadIdx.x, P1_BLOCK};
+  const proj::View R{smd + (size_t)NP * P1_BLOCK + threadIdx.x, P1_BLOCK};
+  for (int t = blockIdx.x * P1_BLOCK + threadIdx.x; t < count; t += gridDim.x * P1_BLOCK) {
+    const int s = list[t];
+    const int q0 = P.moff[s], b0 = P.boff[s];
+    SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.Nm, P.Nb, P.moff[s + 1] - q0, P.boff[s + 1] - b0, P.mubd};
+    const proj::View Qs{sspan + (size_t)SS::Q * count + t, count};
+    double tn = 0.0;
+    int kneg = proj::span_phase1<D>(tab, A, R, Qs, &tn, NEG_REL, RANK_REL);
+    if (kneg < 0) {
+      atomicOr(P.status, BSC_STATUS_NUMERIC_FLAG);
+      kneg = 0;
     }
-    s_kneg[tid] = kneg;
-    s_span[tid] = s;
-    __syncthreads();
-    // phase 2: round r handles eigenvalue r of every span that has one; the
-    // (span, r) items are compacted onto the first threads of the block
-    for (int r = 0;; ++r) {
-      const bool flag = s_kneg[tid] > r;
-      const unsigned bal = __ballot_sync(0xffffffffu, flag);
-      if (lane == 0) s_wcnt[warp] = __popc(bal);
-      __syncthreads();
-      int off = 0, total = 0;
-#pragma unroll
-      for (int w = 0; w < BLOCK / 32; ++w) {
-        off += (w < warp) ? s_wcnt[w] : 0;
-        total += s_wcnt[w];
-      }
-      if (flag) s_list[off + __popc(bal & ((1u << lane) - 1u))] = tid;
-      __syncthreads();
-      if (total == 0) break;
-      if (tid < total) {
-        const int o = s_list[tid];
-        const proj::View Ao{Abase + o, BLOCK}, Ro{Rbase + o, BLOCK};
-        const proj::View Qo{scratch + slot0 + o, nslots};
-        const proj::View Yo{scratch + (size_t)9 * D * nslots + slot0 + o, nslots};
-        SpanH<T> hs{P.H, P.Nsp, s_span[o]};
-        proj::span_eigpair<D>(Ao, Ro, Qo, Yo, Fbase + o, BLOCK, Lo + o, Tn[o], r, hs, NEG_REL);
-      }
-      __syncthreads();
+    kneg_out[t] = kneg;
+    P.nneg[s] = kneg;
+    if (kneg > 0) {
+#pragma unroll 1
+      for (int e = 0; e < NP; ++e) sspan[(size_t)(SS::A + e) * count + t] = A[e];
+#pragma unroll 1
+      for (int e = 0; e < 3 * n; ++e) sspan[(size_t)(SS::R + e) * count + t] = R[e];
+      sspan[(size_t)SS::TN * count + t] = tn;
     }
   }
 }
 
-template <int D>
-struct Cfg;
-template <> struct Cfg<5> { static constexpr int BLOCK = 128; };
-
-template <int D>
-constexpr size_t smem_bytes() {
-  return (sizeof(double) * Smem<D>::DOUBLES + sizeof(float) * Smem<D>::FLOATS) * (size_t)Cfg<D>::BLOCK;
+// Finds the owner of item i given an exclusive prefix over the block.
+template <int BLOCK>
+__device__ __forceinline__ int owner_of(const int* prefix, int i) {
+  int lo = 0, hi = BLOCK;  // prefix[lo] <= i < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
 }
 
+template <int BLOCK>
+__device__ __forceinline__ void block_prefix(int v, int* prefix, int* wsum) {
+  // exclusive prefix of v over the block into prefix[0..BLOCK], total in prefix[BLOCK]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  int off = 0;
+#pragma unroll
+  for (int w = 0; w < BLOCK / 32; ++w) off += (w < warp) ? wsum[w] : 0;
+  prefix[threadIdx.x] = off + x - v;
+  if (threadIdx.x == BLOCK - 1) prefix[BLOCK] = off + x;
+  __syncthreads();
+}
+
+// Phase 2 over batches of P2_BLOCK consecutive interior spans: (a) every
+// negative eigenvalue is an independent item, (b) every cluster of close
+// eigenvalues is an item that computes its eigenvectors, (c) each owner
+// applies H -= sum lam w w^T to its span.  Items are spread over the whole
+// block, so no warp carries masked lanes through FP64 work (masked lanes
+// cost the FP64 pipe as much as active ones).
 template <typename T, int D>
-cudaError_t run_bucket(bsc_ctx* c, int b, cudaStream_t st) {
-  const int count = c->bucket_off[b + 1] - c->bucket_off[b];
-  if (count <= 0) return cudaSuccess;
-  BSC_COUNT(c, 1);
-  constexpr int BLOCK = Cfg<D>::BLOCK;
+__global__ void __launch_bounds__(P2_BLOCK)
+    k_proj_p2(ProjArgs<T> P, const int* __restrict__ list, int count, const int* __restrict__ kneg_in,
+              double* __restrict__ sspan, double* __restrict__ slots, unsigned int* __restrict__ work) {
+  constexpr int n = 3 * D;
+  using SS = SpanScratch<D>;
+  __shared__ int s_kneg[P2_BLOCK], s_cl[P2_BLOCK], s_pre[P2_BLOCK + 1], s_wsum[P2_BLOCK / 32];
+  __shared__ int s_base;
+  const int tid = threadIdx.x;
+  const int nslots = gridDim.x * P2_BLOCK;
+  const proj::View Ys{slots + blockIdx.x * P2_BLOCK + tid, nslots};
+  auto sv = [&](int t, int off) { return proj::View{sspan + (size_t)off * count + t, count}; };
+  auto wv = [&](int t) { return TView<T>{reinterpret_cast<T*>(sspan + (size_t)SS::W * count) + t, count}; };
+  for (;;) {
+    if (tid == 0) s_base = (int)atomicAdd(work, (unsigned)P2_BLOCK);
+    __syncthreads();
+    const int base = s_base;
+    if (base >= count) break;
+    const int t = base + tid;
+    const int kneg = t < count ? kneg_in[t] : 0;
+    s_kneg[tid] = kneg;
+    // (a) eigenvalues
+    block_prefix<P2_BLOCK>(kneg, s_pre, s_wsum);
+    for (int i = tid; i < s_pre[P2_BLOCK]; i += P2_BLOCK) {
+      const int o = owner_of<P2_BLOCK>(s_pre, i), r = i - s_pre[o], to = base + o;
+      sv(to, SS::LAM)[r] = proj::eigenvalue_reg<n>(sv(to, SS::R), r, NEG_REL);
+    }
+    __syncthreads();
+    // clusters: bit r of s_cl marks an eigenvalue that starts one
+    int ncl = 0;
+    if (kneg > 0) {
+      const proj::View Lam = sv(t, SS::LAM);
+      unsigned mask = 1u;
+      double prev = Lam[0];
+      for (int r = 1; r < kneg; ++r) {
+        const double lr = Lam[r];
+        if (lr - prev > CLUSTER_GAP) mask |= 1u << r;
+        prev = lr;
+      }
+      s_cl[tid] = (int)mask;
+      ncl = __popc(mask);
+    } else {
+      s_cl[tid] = 0;
+    }
+    // (b) eigenvectors, one item per cluster
+    block_prefix<P2_BLOCK>(ncl, s_pre, s_wsum);
+    for (int i = tid; i < s_pre[P2_BLOCK]; i += P2_BLOCK) {
+      const int o = owner_of<P2_BLOCK>(s_pre, i), c = i - s_pre[o], to = base + o;
+      unsigned mm = (unsigned)s_cl[o];
+      for (int z = 0; z < c; ++z) mm &= mm - 1u;  // drop the first c starts
+      const int k0 = __ffs(mm) - 1;
+      const unsigned rest = mm & (mm - 1u);
+      const int k1 = rest ? __ffs(rest) - 1 : s_kneg[o];
+      proj::cluster_vectors_reg<D>(sv(to, SS::R), sv(to, SS::A), sv(to, SS::Q), Ys, sv(to, SS::LAM), wv(to),
+                                   sspan[(size_t)SS::TN * count + to], k0, k1 - k0);
+    }
+    __syncthreads();
+    // (c) the owner applies the rank-k correction to its span
+    if (kneg > 0) apply_corrections<T>(P.H, P.Nsp, list[t], sv(t, SS::LAM), wv(t), kneg);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+ProjArgs<T> proj_args(bsc_ctx* c) {
   ProjArgs<T> P;
   P.Nsp = c->Nsp; P.Nm = c->Nmem; P.Nb = c->Nbd; P.mubd = c->mu_bd;
   P.moff = c->mem_off; P.boff = c->bd_off;
   P.tabm = (const T*)c->tab_mem; P.tabb = (const T*)c->tab_bd;
   P.A = (const T*)c->A_mem; P.H = (T*)c->H_span;
   P.nneg = c->nneg; P.status = c->dstatus;
-  auto k = k_project<T, D, BLOCK>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<D>());
-  if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(c->proj_work + b, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
-  k<<<c->proj_grid[b], BLOCK, smem_bytes<D>(), st>>>(P, c->bucket_list + c->bucket_off[b], count,
-                                                     c->proj_scratch[b], c->proj_work + b);
-  return cudaGetLastError();
+  return P;
 }
+
+constexpr size_t p1_smem() { return sizeof(double) * (size_t)(Smem<5>::NP + 15 * 3) * P1_BLOCK; }
 
 template <typename T>
 cudaError_t run_all(bsc_ctx* c) {
   cudaError_t e;
-  // fork: the border classes (warp-per-span kernel) on a side stream, the
-  // interior class on the context stream; the two co-reside on every SM
+  const int count = c->bucket_off[1] - c->bucket_off[0];
+  const int* list = c->bucket_list + c->bucket_off[0];
+  ProjArgs<T> P = proj_args<T>(c);
+  if (count > 0) {
+    BSC_COUNT(c, 1);
+    auto k1 = k_proj_p1<T, 5>;
+    if ((e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem())) != cudaSuccess)
+      return e;
+    k1<<<c->proj_grid[0], P1_BLOCK, p1_smem(), c->stream>>>(P, list, count, c->proj_span, c->proj_kneg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // fork: the border classes (warp-per-span kernel) on a side stream next to
+  // phase 2, whose blocks leave room for them on every SM
   if ((e = cudaEventRecord(c->fork_ev, c->stream)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(c->side[0], c->fork_ev, 0)) != cudaSuccess) return e;
   if ((e = launch_project_ring(c, c->bucket_off[1], c->bucket_off[3] - c->bucket_off[1], c->proj_work + 1,
                                c->side[0])) != cudaSuccess)
     return e;
-  if ((e = run_bucket<T, 5>(c, 0, c->stream)) != cudaSuccess) return e;
+  if (count > 0) {
+    BSC_COUNT(c, 1);
+    if ((e = cudaMemsetAsync(c->proj_work, 0, sizeof(unsigned int), c->stream)) != cudaSuccess) return e;
+    k_proj_p2<T, 5><<<c->proj_grid[1], P2_BLOCK, 0, c->stream>>>(P, list, count, c->proj_kneg, c->proj_span,
+                                                                  c->proj_scratch[0], c->proj_work);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if ((e = cudaEventRecord(c->join_ev[0], c->side[0])) != cudaSuccess) return e;
   return cudaStreamWaitEvent(c->stream, c->join_ev[0], 0);
 }
@@ -240,35 +346,39 @@ __global__ void k_sum_counts(int n, const double* __restrict__ partial, double* 
   if (threadIdx.x == 0) *out = tot;
 }
 
-template <typename T, int D>
-int resident_grid(int num_sms) {
-  int per_sm = 0;
-  cudaFuncSetAttribute(k_project<T, D, Cfg<D>::BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem_bytes<D>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project<T, D, Cfg<D>::BLOCK>, Cfg<D>::BLOCK,
-                                                smem_bytes<D>());
-  if (per_sm < 1) per_sm = 1;
-  return per_sm * num_sms;
-}
-
 }  // namespace
 
-// Sizes the interior class's grid and scratch slots and loads the border
+// Sizes the interior kernels' grids and scratch and loads the border
 // kernel's constants (called from bsc_create).
 cudaError_t setup_projection(bsc_ctx* c) {
   const int count = c->bucket_off[1] - c->bucket_off[0];
-  const int need = (count + Cfg<5>::BLOCK - 1) / Cfg<5>::BLOCK;
-  int g = c->precision == BSC_FP64 ? resident_grid<double, 5>(c->num_sms) : resident_grid<float, 5>(c->num_sms);
-  if (g > need) g = need;
-  if (g < 1) g = 1;
-  c->proj_grid[0] = g;
-  {
-    const size_t slots = (size_t)g * Cfg<5>::BLOCK;
-    cudaError_t e = cudaMalloc(&c->proj_scratch[0], sizeof(double) * (size_t)(9 * 5 + 15 * 15) * slots);
-    if (e != cudaSuccess) return e;
-    if ((e = setup_projection_ring()) != cudaSuccess) return e;
+  int per1 = 0, per2 = 0;
+  cudaError_t e = c->precision == BSC_FP64
+                      ? cudaFuncSetAttribute(k_proj_p1<double, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem())
+                      : cudaFuncSetAttribute(k_proj_p1<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem());
+  if (e != cudaSuccess) return e;
+  if (c->precision == BSC_FP64) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_proj_p1<double, 5>, P1_BLOCK, p1_smem());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<double, 5>, P2_BLOCK, 0);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_proj_p1<float, 5>, P1_BLOCK, p1_smem());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<float, 5>, P2_BLOCK, 0);
   }
-  cudaError_t e = cudaMalloc(&c->proj_work, sizeof(unsigned int) * 4);
+  per1 = per1 < 1 ? 1 : per1;
+  per2 = per2 < 1 ? 1 : per2;
+  int g1 = per1 * c->num_sms, g2 = per2 * c->num_sms;
+  const int need1 = (count + P1_BLOCK - 1) / P1_BLOCK, need2 = (count + P2_BLOCK - 1) / P2_BLOCK;
+  if (g1 > need1) g1 = need1;
+  if (g2 > need2) g2 = need2;
+  c->proj_grid[0] = g1 < 1 ? 1 : g1;
+  c->proj_grid[1] = g2 < 1 ? 1 : g2;
+  const size_t cnt = count > 0 ? (size_t)count : 1;
+  if ((e = cudaMalloc(&c->proj_span, sizeof(double) * SpanScratch<5>::SIZE * cnt)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->proj_kneg, sizeof(int) * cnt)) != cudaSuccess) return e;
+  const size_t slots = (size_t)c->proj_grid[1] * P2_BLOCK;
+  if ((e = cudaMalloc(&c->proj_scratch[0], sizeof(double) * 15 * 15 * slots)) != cudaSuccess) return e;
+  if ((e = setup_projection_ring()) != cudaSuccess) return e;
+  e = cudaMalloc(&c->proj_work, sizeof(unsigned int) * 4);
   if (e != cudaSuccess) return e;
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking)) != cudaSuccess) return e;

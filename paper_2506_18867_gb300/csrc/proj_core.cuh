@@ -21,6 +21,13 @@
 #define BSC_HD inline
 #endif
 #endif
+// The large phases are separate calls on the GPU, so that each gets its own
+// register allocation instead of one allocation for the whole kernel.
+#ifdef __CUDACC__
+#define BSC_PHASE __host__ __device__ __noinline__
+#else
+#define BSC_PHASE inline
+#endif
 
 namespace proj {
 
@@ -133,7 +140,7 @@ BSC_HD void back_transform(const View& A, double (&x)[n]) {
 // reflectors, Qs the basis, *tn the scale; returns the number of eigenvalues
 // below -neg_rel ||T|| (-1 on a non-finite matrix).
 template <int D, class Tab>
-BSC_HD int span_phase1(const Tab& tab, const View& A, const View& R, const View& Qs, double* tn_out,
+BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, const View& Qs, double* tn_out,
                        double neg_rel, double rank_rel) {
   constexpr int n = 3 * D;
   constexpr int NP = n * (n + 1) / 2;
@@ -332,15 +339,12 @@ BSC_HD int span_phase1(const Tab& tab, const View& A, const View& R, const View&
   return sturm<n>(R, -neg_rel);
 }
 
-// Phase 2: eigenpair k (k-th smallest) of a span whose phase 1 is done:
-// FP32 bracket from *lo32 (raised to the bracket's lower end on return), FP64
-// check and bisection to a 1e-10 bracket, inverse iteration (two solves) with
-// re-orthogonalisation against the span's eigenvectors 0..k-1 in Ys,
-// Rayleigh quotient, back-transformation, w = (Q (x) I3) x, and the rank-one
-// correction H -= lam w w^T.  F holds the FP32 copy of (d, e^2).
-template <int D, class HAcc>
-BSC_HD void span_eigpair(const View& A, const View& R, const View& Qs, const View& Ys, const float* F, int fs,
-                         float* lo32, double tn, int k, HAcc& Hs, double neg_rel) {
+// Phase 2a: eigenvalue k (k-th smallest, scaled) of a span whose phase 1 is
+// done: FP32 bisection on the copy F of (d, e^2) to about 22 bits, the
+// widened bracket checked by two FP64 Sturm counts, then FP64 bisection to a
+// width of 1e-10.  Returns the bracket midpoint.
+template <int D>
+BSC_PHASE double span_eigenvalue(const View& R, const float* F, int fs, int k, double neg_rel) {
   constexpr int n = 3 * D;
   float d32[n], e232[n];
 #pragma unroll
@@ -349,29 +353,39 @@ BSC_HD void span_eigpair(const View& A, const View& R, const View& Qs, const Vie
     e232[i] = F[(n + i) * fs];
   }
   const double lo_all = -1.0 - 1e-12, hi_all = -neg_rel;
-  {
-    // FP32 bracket (about 22 bits), then an FP64 check of the widened bracket
-    float a32 = *lo32, b32 = (float)hi_all;
+  float a32 = -1.0f - 1e-6f, b32 = (float)hi_all;
 #pragma unroll 1
-    for (int it = 0; it < 22; ++it) {
-      const float mid = 0.5f * (a32 + b32);
-      if (sturm32<n>(d32, e232, mid) > k) b32 = mid;
-      else a32 = mid;
-    }
-    *lo32 = a32;
-    double a = fmax((double)a32 - 4e-6, lo_all), b = fmin((double)b32 + 4e-6, hi_all);
-    if (!(sturm<n>(R, a) <= k && sturm<n>(R, b) > k)) {
-      a = lo_all;
-      b = hi_all;
-    }
+  for (int it = 0; it < 22; ++it) {
+    const float mid = 0.5f * (a32 + b32);
+    if (sturm32<n>(d32, e232, mid) > k) b32 = mid;
+    else a32 = mid;
+  }
+  double a = fmax((double)a32 - 4e-6, lo_all), b = fmin((double)b32 + 4e-6, hi_all);
+  if (!(sturm<n>(R, a) <= k && sturm<n>(R, b) > k)) {
+    a = lo_all;
+    b = hi_all;
+  }
 #pragma unroll 1
-    for (int it = 0; it < 40 && b - a > 1e-10; ++it) {
-      const double mid = 0.5 * (a + b);
-      if (sturm<n>(R, mid) > k) b = mid;
-      else a = mid;
-    }
-    const double sig = 0.5 * (a + b);
-    // Gaussian elimination with partial pivoting of T - sig I (one reciprocal a row)
+  for (int it = 0; it < 40 && b - a > 1e-10; ++it) {
+    const double mid = 0.5 * (a + b);
+    if (sturm<n>(R, mid) > k) b = mid;
+    else a = mid;
+  }
+  return 0.5 * (a + b);
+}
+
+// Phase 2b: eigenvectors k0 .. k0+m-1 of a cluster (consecutive eigenvalues
+// closer than the cluster gap), from the shifts in Lam: inverse iteration
+// (two solves) with re-orthogonalisation against the cluster's earlier
+// vectors in Ys, Rayleigh quotient (written back to Lam, unscaled by tn),
+// back-transformation and w = (Q (x) I3) x written to Ws[27 k + .].
+template <int D>
+BSC_PHASE void span_cluster_vectors(const View& A, const View& R, const View& Qs, const View& Ys, const View& Lam,
+                                 const View& Ws, double tn, int k0, int m) {
+  constexpr int n = 3 * D;
+#pragma unroll 1
+  for (int k = k0; k < k0 + m; ++k) {
+    const double sig = Lam[k];
     double u0r[n], u1[n], u2[n], mu[n];
     unsigned sw = 0u;
     {
@@ -382,26 +396,14 @@ BSC_HD void span_eigpair(const View& A, const View& R, const View& Qs, const Vie
         const double a1 = R[i + 1] - sig, e1 = (i + 1 < n - 1) ? R[n + i + 1] : 0.0;
         if (fabs(ei) > fabs(c0)) {
           sw |= 1u << i;
-          const double r = 1.0 / ei;
-          const double m = c0 * r;
-          mu[i] = m;
-          u0r[i] = r;
-          u1[i] = a1;
-          u2[i] = e1;
-          c0 = c1 - m * a1;
-          c1 = c2 - m * e1;
-          c2 = 0.0;
+          const double r = 1.0 / ei, mm = c0 * r;
+          mu[i] = mm; u0r[i] = r; u1[i] = a1; u2[i] = e1;
+          c0 = c1 - mm * a1; c1 = c2 - mm * e1; c2 = 0.0;
         } else {
           if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
-          const double r = 1.0 / c0;
-          const double m = ei * r;
-          mu[i] = m;
-          u0r[i] = r;
-          u1[i] = c1;
-          u2[i] = c2;
-          c0 = a1 - m * c1;
-          c1 = e1 - m * c2;
-          c2 = 0.0;
+          const double r = 1.0 / c0, mm = ei * r;
+          mu[i] = mm; u0r[i] = r; u1[i] = c1; u2[i] = c2;
+          c0 = a1 - mm * c1; c1 = e1 - mm * c2; c2 = 0.0;
         }
       }
       if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
@@ -411,8 +413,10 @@ BSC_HD void span_eigpair(const View& A, const View& R, const View& Qs, const Vie
     double y[n];
 #pragma unroll
     for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.125 * (double)((7 * i + 3 * k) % 5);
+#pragma unroll 1
     for (int it = 0; it < 3; ++it) {
-      for (int j = 0; j < k; ++j) {
+#pragma unroll 1
+      for (int j = k0; j < k; ++j) {
         double dt = 0.0;
 #pragma unroll
         for (int i = 0; i < n; ++i) dt += Ys[j * n + i] * y[i];
@@ -432,10 +436,10 @@ BSC_HD void span_eigpair(const View& A, const View& R, const View& Qs, const Vie
         }
 #pragma unroll
         for (int i = n - 1; i >= 0; --i) {
-          double s = y[i];
-          if (i + 1 < n) s -= u1[i] * y[i + 1];
-          if (i + 2 < n) s -= u2[i] * y[i + 2];
-          y[i] = s * u0r[i];
+          double sacc = y[i];
+          if (i + 1 < n) sacc -= u1[i] * y[i + 1];
+          if (i + 2 < n) sacc -= u2[i] * y[i + 2];
+          y[i] = sacc * u0r[i];
         }
       }
       double nn = 0.0;
@@ -453,11 +457,12 @@ BSC_HD void span_eigpair(const View& A, const View& R, const View& Qs, const Vie
       if (i + 1 < n) ty += R[n + i] * y[i + 1];
       rq += y[i] * ty;
     }
+    if (m > 1) {
 #pragma unroll
-    for (int i = 0; i < n; ++i) Ys[k * n + i] = y[i];
-    const double lam = fmin(rq, 0.0) * tn;
+      for (int i = 0; i < n; ++i) Ys[k * n + i] = y[i];
+    }
+    Lam[k] = fmin(rq, 0.0) * tn;
     back_transform<n>(A, y);
-    double w[27];
 #pragma unroll
     for (int l = 0; l < 9; ++l)
 #pragma unroll
@@ -465,9 +470,237 @@ BSC_HD void span_eigpair(const View& A, const View& R, const View& Qs, const Vie
         double acc = 0.0;
 #pragma unroll
         for (int kk = 0; kk < D; ++kk) acc += Qs[9 * kk + l] * y[3 * kk + c];
-        w[3 * l + c] = acc;
+        Ws[27 * k + 3 * l + c] = acc;
       }
-    Hs.rank1(lam, w);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase-2 items with the tridiagonal in registers (no shared memory needed):
+// the span's scaled (d, e, e^2) are loaded once per item.
+// ---------------------------------------------------------------------------
+
+template <int n>
+BSC_HD int sturm_reg(const double (&d)[n], const double (&e2)[n], double x) {
+  double pm = 1.0, p = d[0] - x;
+  int cnt = sign_of(p);
+#pragma unroll
+  for (int i = 1; i < n; ++i) {
+    double pn = (d[i] - x) * p - e2[i - 1] * pm;
+    if (expo_of(pn) == 0) pn = sign_of(p) ? 1e-300 : -1e-300;
+    cnt += sign_of(pn) ^ sign_of(p);
+    const int ea = expo_of(pn), eb = expo_of(p), mx = ea > eb ? ea : eb;
+    if (mx > 1023 + 500 || mx < 1023 - 500) {
+      const double sc = mx > 1023 ? 0x1p-500 : 0x1p500;
+      pn *= sc;
+      p *= sc;
+    }
+    pm = p;
+    p = pn;
+  }
+  return cnt;
+}
+
+// det(T - x I) from the same three-term recurrence as the Sturm count, with
+// the count; *exact is false when a rescaling step made the value's scale
+// differ from the determinant's (callers then bisect instead).
+template <int n>
+BSC_HD double char_poly(const double (&d)[n], const double (&e2)[n], double x, int* cnt_out, bool* exact) {
+  double pm = 1.0, p = d[0] - x;
+  int cnt = sign_of(p);
+  bool ok = true;
+#pragma unroll
+  for (int i = 1; i < n; ++i) {
+    double pn = (d[i] - x) * p - e2[i - 1] * pm;
+    if (expo_of(pn) == 0) {
+      pn = sign_of(p) ? 1e-300 : -1e-300;
+      ok = false;
+    }
+    cnt += sign_of(pn) ^ sign_of(p);
+    const int ea = expo_of(pn), eb = expo_of(p), mx = ea > eb ? ea : eb;
+    if (mx > 1023 + 500 || mx < 1023 - 500) {
+      const double sc = mx > 1023 ? 0x1p-500 : 0x1p500;
+      pn *= sc;
+      p *= sc;
+      ok = false;
+    }
+    pm = p;
+    p = pn;
+  }
+  *cnt_out = cnt;
+  *exact = ok;
+  return p;
+}
+
+// Eigenvalue k (scaled) of the tridiagonal stored in R (d at R[0..n), e^2 at
+// R[2n..3n)), loaded into registers.  After the FP32 bracket and its FP64
+// check, a bracket that isolates eigenvalue k is refined by the Illinois
+// variant of regula falsi on det(T - x I) (superlinear, bracketing), a
+// bracket holding several eigenvalues by bisection.
+template <int n>
+BSC_PHASE double eigenvalue_reg(const View& R, int k, double neg_rel) {
+  double d[n], e2[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    d[i] = R[i];
+    e2[i] = R[2 * n + i];
+  }
+  float d32[n], e232[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    d32[i] = (float)d[i];
+    e232[i] = (float)e2[i];
+  }
+  const double lo_all = -1.0 - 1e-12, hi_all = -neg_rel;
+  float a32 = -1.0f - 1e-6f, b32 = (float)hi_all;
+#pragma unroll 1
+  for (int it = 0; it < 22; ++it) {
+    const float mid = 0.5f * (a32 + b32);
+    if (sturm32<n>(d32, e232, mid) > k) b32 = mid;
+    else a32 = mid;
+  }
+  double a = fmax((double)a32 - 4e-6, lo_all), b = fmin((double)b32 + 4e-6, hi_all);
+  int ca, cb;
+  bool xa, xb;
+  double fa = char_poly<n>(d, e2, a, &ca, &xa), fb = char_poly<n>(d, e2, b, &cb, &xb);
+  if (!(ca <= k && cb > k)) {
+    a = lo_all;
+    b = hi_all;
+    fa = char_poly<n>(d, e2, a, &ca, &xa);
+    fb = char_poly<n>(d, e2, b, &cb, &xb);
+  }
+  int side = 0;
+#pragma unroll 1
+  for (int it = 0; it < 60 && b - a > 1e-10; ++it) {
+    double x;
+    const bool isolated = ca == k && cb == k + 1 && xa && xb && fa != fb;
+    if (isolated) {
+      x = (a * fb - b * fa) / (fb - fa);
+      if (!(x > a && x < b)) x = 0.5 * (a + b);
+    } else {
+      x = 0.5 * (a + b);
+    }
+    int cx;
+    bool xx;
+    const double fx = char_poly<n>(d, e2, x, &cx, &xx);
+    if (cx > k) {
+      if (isolated && side == -1) fa *= 0.5;  // Illinois: the kept end was kept twice
+      b = x; fb = fx; cb = cx; xb = xx; side = -1;
+    } else {
+      if (isolated && side == 1) fb *= 0.5;
+      a = x; fa = fx; ca = cx; xa = xx; side = 1;
+    }
+    if (isolated && fx == 0.0) return x;
+#ifdef BSC_COUNT_EVALS
+    ++bsc_evals;
+#endif
+  }
+  return 0.5 * (a + b);
+}
+
+// Eigenvectors k0 .. k0+m-1 of a cluster, as span_cluster_vectors, with the
+// tridiagonal (d, e) loaded into registers from R and the reflectors A, basis
+// Q, eigenvalues Lam and output vectors Ws in global memory; Ys is the item's
+// own scratch.
+template <int D, class WView>
+BSC_PHASE void cluster_vectors_reg(const View& R, const View& A, const View& Qs, const View& Ys, const View& Lam,
+                                   const WView& Ws, double tn, int k0, int m) {
+  constexpr int n = 3 * D;
+  double d[n], e[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    d[i] = R[i];
+    e[i] = R[n + i];
+  }
+#pragma unroll 1
+  for (int k = k0; k < k0 + m; ++k) {
+    const double sig = Lam[k];
+    double u0r[n], u1[n], u2[n], mu[n];
+    unsigned sw = 0u;
+    {
+      double c0 = d[0] - sig, c1 = e[0], c2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < n - 1; ++i) {
+        const double ei = e[i];
+        const double a1 = d[i + 1] - sig, e1 = (i + 1 < n - 1) ? e[i + 1] : 0.0;
+        if (fabs(ei) > fabs(c0)) {
+          sw |= 1u << i;
+          const double r = 1.0 / ei, mm = c0 * r;
+          mu[i] = mm; u0r[i] = r; u1[i] = a1; u2[i] = e1;
+          c0 = c1 - mm * a1; c1 = c2 - mm * e1; c2 = 0.0;
+        } else {
+          if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
+          const double r = 1.0 / c0, mm = ei * r;
+          mu[i] = mm; u0r[i] = r; u1[i] = c1; u2[i] = c2;
+          c0 = a1 - mm * c1; c1 = e1 - mm * c2; c2 = 0.0;
+        }
+      }
+      if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
+      u0r[n - 1] = 1.0 / c0;
+      u1[n - 1] = u2[n - 1] = 0.0;
+    }
+    double y[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.125 * (double)((7 * i + 3 * k) % 5);
+#pragma unroll 1
+    for (int it = 0; it < 3; ++it) {
+#pragma unroll 1
+      for (int j = k0; j < k; ++j) {
+        double dt = 0.0;
+#pragma unroll
+        for (int i = 0; i < n; ++i) dt += Ys[(j - k0) * n + i] * y[i];
+#pragma unroll
+        for (int i = 0; i < n; ++i) y[i] -= dt * Ys[(j - k0) * n + i];
+      }
+      if (it < 2) {
+#pragma unroll
+        for (int i = 0; i < n - 1; ++i) {
+          if (sw & (1u << i)) {
+            const double t = y[i];
+            y[i] = y[i + 1];
+            y[i + 1] = t - mu[i] * y[i + 1];
+          } else {
+            y[i + 1] -= mu[i] * y[i];
+          }
+        }
+#pragma unroll
+        for (int i = n - 1; i >= 0; --i) {
+          double sacc = y[i];
+          if (i + 1 < n) sacc -= u1[i] * y[i + 1];
+          if (i + 2 < n) sacc -= u2[i] * y[i + 2];
+          y[i] = sacc * u0r[i];
+        }
+      }
+      double nn = 0.0;
+#pragma unroll
+      for (int i = 0; i < n; ++i) nn += y[i] * y[i];
+      const double inv = 1.0 / sqrt(nn);
+#pragma unroll
+      for (int i = 0; i < n; ++i) y[i] *= inv;
+    }
+    double rq = 0.0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      double ty = d[i] * y[i];
+      if (i > 0) ty += e[i - 1] * y[i - 1];
+      if (i + 1 < n) ty += e[i] * y[i + 1];
+      rq += y[i] * ty;
+    }
+    if (m > 1) {
+#pragma unroll
+      for (int i = 0; i < n; ++i) Ys[(k - k0) * n + i] = y[i];
+    }
+    Lam[k] = fmin(rq, 0.0) * tn;
+    back_transform<n>(A, y);
+#pragma unroll
+    for (int l = 0; l < 9; ++l)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) acc += Qs[9 * kk + l] * y[3 * kk + c];
+        Ws.set(27 * k + 3 * l + c, acc);
+      }
   }
 }
 

@@ -601,10 +601,12 @@ BSC_PHASE double eigenvalue_reg(const View& R, int k, double neg_rel) {
 // Eigenvectors k0 .. k0+m-1 of a cluster, as span_cluster_vectors, with the
 // tridiagonal (d, e) loaded into registers from R and the reflectors A, basis
 // Q, eigenvalues Lam and output vectors Ws in global memory; Ys is the item's
-// own scratch.
+// own scratch.  The LU factors of T - sigma I (multipliers and the three
+// diagonals of U, 4n doubles) live in LU, the thread's slot of an interleaved
+// shared-memory array, which keeps them out of local memory.
 template <int D, class WView>
 BSC_PHASE void cluster_vectors_reg(const View& R, const View& A, const View& Qs, const View& Ys, const View& Lam,
-                                   const WView& Ws, double tn, int k0, int m) {
+                                   const WView& Ws, const View& LU, double tn, int k0, int m) {
   constexpr int n = 3 * D;
   double d[n], e[n];
 #pragma unroll
@@ -612,10 +614,11 @@ BSC_PHASE void cluster_vectors_reg(const View& R, const View& A, const View& Qs,
     d[i] = R[i];
     e[i] = R[n + i];
   }
+  const View mu{LU.p, LU.s}, u0r{LU.p + (long)n * LU.s, LU.s}, u1{LU.p + 2l * n * LU.s, LU.s},
+      u2{LU.p + 3l * n * LU.s, LU.s};
 #pragma unroll 1
   for (int k = k0; k < k0 + m; ++k) {
     const double sig = Lam[k];
-    double u0r[n], u1[n], u2[n], mu[n];
     unsigned sw = 0u;
     {
       double c0 = d[0] - sig, c1 = e[0], c2 = 0.0;

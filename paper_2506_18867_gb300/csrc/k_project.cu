@@ -129,21 +129,31 @@ struct TView {
 };
 
 // H -= sum_r lam_r w_r w_r^T for one span in one pass over its 378 packed
-// entries, in the element type (w_r already in T in the scratch).
+// entries, in the element type (w_r already in T in the scratch).  An
+// interior span has at most n = 15 negative eigenvalues; the unrolled,
+// predicated loops keep lam_r and lam_r w_r[a] of the current row in
+// registers, so only w_r[c] is read per entry.
 template <typename T>
 __device__ __noinline__ void apply_corrections(T* H, int Nsp, int s, proj::View Lam, TView<T> Ws, int kneg) {
-  T lam[32];
+  constexpr int RMAX = 15;
+  T lam[RMAX];
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) lam[r] = r < kneg ? (T)Lam[r] : T(0);
+  int e = 0;
 #pragma unroll 1
-  for (int r = 0; r < kneg; ++r) lam[r] = (T)Lam[r];
-  int a = 0, c = 0;
+  for (int a = 0; a < 27; ++a) {
+    T la[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) la[r] = r < kneg ? lam[r] * Ws[27 * r + a] : T(0);
 #pragma unroll 1
-  for (int e = 0; e < H27; ++e) {
-    T acc = T(0);
-#pragma unroll 1
-    for (int r = 0; r < kneg; ++r) acc += lam[r] * Ws[27 * r + a] * Ws[27 * r + c];
-    T* h = H + (size_t)e * Nsp + s;
-    *h -= acc;
-    if (++c == 27) c = ++a;
+    for (int c = a; c < 27; ++c, ++e) {
+      T acc = T(0);
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (r < kneg) acc += la[r] * Ws[27 * r + c];
+      T* h = H + (size_t)e * Nsp + s;
+      *h -= acc;
+    }
   }
 }
 
@@ -226,9 +236,11 @@ __global__ void __launch_bounds__(P2_BLOCK)
   using SS = SpanScratch<D>;
   __shared__ int s_kneg[P2_BLOCK], s_cl[P2_BLOCK], s_pre[P2_BLOCK + 1], s_wsum[P2_BLOCK / 32];
   __shared__ int s_base;
+  extern __shared__ __align__(16) double s_lu[];  // [4 n][P2_BLOCK]: LU factors of the inverse iteration
   const int tid = threadIdx.x;
   const int nslots = gridDim.x * P2_BLOCK;
   const proj::View Ys{slots + blockIdx.x * P2_BLOCK + tid, nslots};
+  const proj::View LU{s_lu + tid, P2_BLOCK};
   auto sv = [&](int t, int off) { return proj::View{sspan + (size_t)off * count + t, count}; };
   auto wv = [&](int t) { return TView<T>{reinterpret_cast<T*>(sspan + (size_t)SS::W * count) + t, count}; };
   for (;;) {
@@ -271,7 +283,7 @@ __global__ void __launch_bounds__(P2_BLOCK)
       const int k0 = __ffs(mm) - 1;
       const unsigned rest = mm & (mm - 1u);
       const int k1 = rest ? __ffs(rest) - 1 : s_kneg[o];
-      proj::cluster_vectors_reg<D>(sv(to, SS::R), sv(to, SS::A), sv(to, SS::Q), Ys, sv(to, SS::LAM), wv(to),
+      proj::cluster_vectors_reg<D>(sv(to, SS::R), sv(to, SS::A), sv(to, SS::Q), Ys, sv(to, SS::LAM), wv(to), LU,
                                    sspan[(size_t)SS::TN * count + to], k0, k1 - k0);
     }
     __syncthreads();
@@ -293,6 +305,7 @@ ProjArgs<T> proj_args(bsc_ctx* c) {
 }
 
 constexpr size_t p1_smem() { return sizeof(double) * (size_t)(Smem<5>::NP + 15 * 3) * P1_BLOCK; }
+constexpr size_t p2_smem() { return sizeof(double) * (size_t)(4 * 15) * P2_BLOCK; }
 
 template <typename T>
 cudaError_t run_all(bsc_ctx* c) {
@@ -318,8 +331,9 @@ cudaError_t run_all(bsc_ctx* c) {
   if (count > 0) {
     BSC_COUNT(c, 1);
     if ((e = cudaMemsetAsync(c->proj_work, 0, sizeof(unsigned int), c->stream)) != cudaSuccess) return e;
-    k_proj_p2<T, 5><<<c->proj_grid[1], P2_BLOCK, 0, c->stream>>>(P, list, count, c->proj_kneg, c->proj_span,
-                                                                  c->proj_scratch[0], c->proj_work);
+    k_proj_p2<T, 5><<<c->proj_grid[1], P2_BLOCK, p2_smem(), c->stream>>>(P, list, count, c->proj_kneg,
+                                                                          c->proj_span, c->proj_scratch[0],
+                                                                          c->proj_work);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = cudaEventRecord(c->join_ev[0], c->side[0])) != cudaSuccess) return e;
@@ -353,16 +367,25 @@ __global__ void k_sum_counts(int n, const double* __restrict__ partial, double* 
 cudaError_t setup_projection(bsc_ctx* c) {
   const int count = c->bucket_off[1] - c->bucket_off[0];
   int per1 = 0, per2 = 0;
-  cudaError_t e = c->precision == BSC_FP64
-                      ? cudaFuncSetAttribute(k_proj_p1<double, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem())
-                      : cudaFuncSetAttribute(k_proj_p1<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem());
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   if (c->precision == BSC_FP64) {
+    if ((e = cudaFuncSetAttribute(k_proj_p1<double, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)p1_smem())) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_proj_p2<double, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)p2_smem())) != cudaSuccess)
+      return e;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_proj_p1<double, 5>, P1_BLOCK, p1_smem());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<double, 5>, P2_BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<double, 5>, P2_BLOCK, p2_smem());
   } else {
+    if ((e = cudaFuncSetAttribute(k_proj_p1<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)p1_smem())) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_proj_p2<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)p2_smem())) != cudaSuccess)
+      return e;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_proj_p1<float, 5>, P1_BLOCK, p1_smem());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<float, 5>, P2_BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<float, 5>, P2_BLOCK, p2_smem());
   }
   per1 = per1 < 1 ? 1 : per1;
   per2 = per2 < 1 ? 1 : per2;

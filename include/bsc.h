@@ -179,6 +179,93 @@ bsc_status bsc_solve(bsc_ctx* ctx, const void* K_dev, const void* b_dev, void* x
  * Synchronises the stream. */
 bsc_status bsc_newton_step(bsc_ctx* ctx, void* C_dev, const void* Chat_dev, bsc_newton_report* rep);
 
+/* ---- batched patches: many garments in one context ------------------------
+ * A context may hold several independent patches with their own grids,
+ * materials, rest maps, time steps, gravity and pinned sets (the garment
+ * panels of one scene).  Every entry point above then works on all patches
+ * at once - one launch per phase, the PCG as one persistent cooperative
+ * launch whose co-resident blocks are split into one group per patch - and
+ * the patches never interact.
+ *  - Layout: the patches' control points are concatenated in patch order;
+ *    patch p owns entries [cp_offset[p], cp_offset[p+1]) of every plane of a
+ *    control-point vector (3 planes of N = total control points) and of the
+ *    225 planes of K.  Its spans likewise follow in patch order
+ *    (span_offset).  Within a patch the single-patch numbering holds.
+ *  - bsc_energy returns the sum of the patches' energies (added in patch
+ *    order); bsc_solve solves every patch's system to rel_tol (iters =
+ *    the largest count, rel_res = the largest residual); bsc_newton_step
+ *    runs an independent Newton iteration with its own line search per patch
+ *    and reports the aggregate (E0, E1: sums; alpha: smallest; dir_inf,
+ *    pcg_rel_res, pcg_iters, ls_halvings: largest; spans_projected: sum;
+ *    status: the first patch's non-OK status) - bsc_patch_reports gives the
+ *    per-patch reports.
+ *  - A single-patch context is the one-patch case of the same code. */
+
+/* Build a context for `count` patches (1 <= count <= 304, the co-resident
+ * block capacity of the persistent PCG on one GB300).
+ *   grids, materials, options: arrays of count entries (options[p].pinned
+ *   holds patch-local control-point indices); precision, project,
+ *   pcg_rel_tol, pcg_max_iter and max_line_search are taken from
+ *   options[0];  rest_xy: count host pointers, patch p's (nu*nv) x 2 doubles;
+ *   q: the quadrature rules of every patch.  Other arguments as bsc_create. */
+bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double* const* rest_xy,
+                            const bsc_material* materials, const bsc_quadrature* q,
+                            const bsc_options* options, void* cuda_stream, bsc_ctx** out);
+
+/* Patch count and offsets (host arrays of count + 1 ints, either may be NULL). */
+bsc_status bsc_batch_layout(const bsc_ctx* ctx, int* count, int* cp_offset, int* span_offset);
+
+/* Per-patch reports of the last bsc_newton_step (host array of count). */
+bsc_status bsc_patch_reports(const bsc_ctx* ctx, bsc_newton_report* reps);
+
+/* Per-patch incremental potential (host array of count doubles). */
+bsc_status bsc_patch_energies(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, double* E_out);
+
+/* Autotuner.  Span evaluation runs on work items - a patch and either a run
+ * of consecutive spans or a tile of tile_tu x (block / tile_tu) spans - with
+ * one tile width per patch-size class (class k: spans per row < 32, < 64,
+ * < 128, >= 128); width 0 means runs.  bsc_autotune times the Hessian
+ * evaluation of each class present for each candidate width {0, 8, 16, 32}
+ * (CUDA events, best of 3) and keeps the fastest, then assembles K at C,
+ * runs one PCG solve per patch to measure its iteration count, and splits
+ * the PCG's co-resident blocks in proportion to control points x
+ * iterations (bsc_plan_blocks).  C is not modified.  The choices change
+ * only the launch shape and the PCG's reduction grouping, not what is
+ * computed: span terms and K are bitwise the same for every tile width.
+ * out (host, may be NULL) receives the choices and timings. */
+typedef struct bsc_tuning {
+  int tile_tu[4];          /* chosen width per class (-1: class absent) */
+  double tile_ms[4][4];    /* measured ms per class x candidate {0, 8, 16, 32} */
+  int pcg_grid;            /* co-resident blocks of the persistent PCG */
+} bsc_tuning;
+bsc_status bsc_autotune(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, bsc_tuning* out);
+
+/* Set the tile widths by hand (4 entries, each 0, 8, 16 or 32). */
+bsc_status bsc_set_tiles(bsc_ctx* ctx, const int* tile_tu);
+
+/* Current split of the PCG's blocks (host array of count ints). */
+bsc_status bsc_pcg_split(const bsc_ctx* ctx, int* blocks_per_patch);
+
+/* The split rule itself, a pure host function: `total` blocks over `count`
+ * patches with n_cp[p] control points and work estimates work[p] > 0; each
+ * patch gets >= 1 and <= ceil(n_cp / 256) blocks, the rest go one at a time
+ * to the patch with the largest work / blocks (ties to the lower index).
+ * Writes blocks[count]; returns the number handed out, -1 if total < count. */
+int bsc_plan_blocks(int count, const int* n_cp, const double* work, int total, int* blocks);
+
+/* CUDA graph of the Newton iteration.  With on != 0 (the default)
+ * bsc_newton_step captures its launches - evaluation, projection, assembly,
+ * the persistent PCG and the first line-search round - into a CUDA graph
+ * the first time it sees a pair (C_dev, Chat_dev) and replays the graph for
+ * later calls with the same pointers; further line-search rounds, needed
+ * only by patches that reject alpha = 1, are launched directly.  The graph
+ * runs on an internal stream that is ordered after, and before, the
+ * context's stream.  bsc_graph_state (host ints, may be NULL): on = the
+ * setting, captured = 1 while an executable graph is held, replays = graph
+ * launches so far. */
+bsc_status bsc_set_graph(bsc_ctx* ctx, int on);
+bsc_status bsc_graph_state(const bsc_ctx* ctx, int* on, int* captured, long long* replays);
+
 /* ---- inspection entry points (parity tests, profiling) ------------------- */
 
 /* Per-span results of the last evaluation path: E_span (device, Nsp doubles),
@@ -193,7 +280,9 @@ bsc_status bsc_span_terms(bsc_ctx* ctx, const void* C_dev, int project, double* 
  * Returns the point count through count; if out != NULL writes up to cap
  * records of 25 doubles: [u, v, w, owner_a, owner_b, W = w |det J|, then for
  * membrane g[9][2] = dN_l/dX_beta (18 values), for bending L[9] (the
- * Laplacian coefficient of each control point, 9 values)], zero padded. */
+ * Laplacian coefficient of each control point, 9 values)], zero padded,
+ * and record[24] = the owning span's context-wide index (owner_a, owner_b
+ * are patch-local). */
 bsc_status bsc_quadrature_tables(bsc_ctx* ctx, int which, double* out, int cap, int* count);
 
 /* Lumped masses m_alpha (host, N doubles). */

@@ -27,9 +27,13 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5:
 
 # Every entry point declared in include/bsc.h.
 EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc_energy", "bsc_gradient",
-           "bsc_assemble_hessian", "bsc_spmv", "bsc_solve", "bsc_newton_step", "bsc_span_terms",
+           "bsc_assemble_hessian", "bsc_spmv", "bsc_solve", "bsc_newton_step", "bsc_create_batch",
+           "bsc_batch_layout", "bsc_patch_reports", "bsc_patch_energies", "bsc_autotune", "bsc_set_tiles",
+           "bsc_pcg_split", "bsc_plan_blocks", "bsc_set_graph", "bsc_graph_state", "bsc_span_terms",
            "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes", "bsc_set_profiling", "bsc_phase_times",
            "bsc_launch_count", "bsc_projection_stats", "bsc_solve_static")
+
+TILE_CANDIDATES = (0, 8, 16, 32)
 
 STATIC_SOLVE_MAX_CP = 16384  # BSC_STATIC_SOLVE_MAX_CP in include/bsc.h
 
@@ -61,6 +65,14 @@ class NewtonReport(ct.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Tuning(ct.Structure):
+    _fields_ = [("tile_tu", ct.c_int * 4), ("tile_ms", (ct.c_double * 4) * 4), ("pcg_grid", ct.c_int)]
+
+    def as_dict(self):
+        return {"tile_tu": list(self.tile_tu), "tile_ms": [list(r) for r in self.tile_ms],
+                "pcg_grid": self.pcg_grid}
 
 
 class BscError(RuntimeError):
@@ -104,6 +116,18 @@ def load(path: str = LIB_PATH):
     lib.bsc_launch_count.argtypes = [P, ct.POINTER(ct.c_ulonglong)]
     lib.bsc_projection_stats.argtypes = [P, ct.POINTER(I), ct.POINTER(I)]
     lib.bsc_solve_static.argtypes = [I, I, I, V, V, V, D, I, V, ct.POINTER(I), ct.POINTER(D)]
+    lib.bsc_create_batch.argtypes = [I, ct.POINTER(KnotGrid), ct.POINTER(ct.POINTER(ct.c_double)),
+                                     ct.POINTER(Material), ct.POINTER(Quadrature), ct.POINTER(Options), V,
+                                     ct.POINTER(P)]
+    lib.bsc_batch_layout.argtypes = [P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(I)]
+    lib.bsc_patch_reports.argtypes = [P, ct.POINTER(NewtonReport)]
+    lib.bsc_patch_energies.argtypes = [P, V, V, ct.POINTER(D)]
+    lib.bsc_autotune.argtypes = [P, V, V, ct.POINTER(Tuning)]
+    lib.bsc_set_tiles.argtypes = [P, ct.POINTER(I)]
+    lib.bsc_pcg_split.argtypes = [P, ct.POINTER(I)]
+    lib.bsc_plan_blocks.argtypes = [I, ct.POINTER(I), ct.POINTER(D), I, ct.POINTER(I)]
+    lib.bsc_set_graph.argtypes = [P, I]
+    lib.bsc_graph_state.argtypes = [P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(ct.c_longlong)]
     for name in EXPORTS:
         if name not in ("bsc_destroy", "bsc_last_error"):
             getattr(lib, name).restype = I
@@ -116,39 +140,78 @@ def _ptr(t):
 
 
 class Context:
-    """One patch on the GPU (wraps ``bsc_ctx``).  Tensors must be CUDA tensors
-    of the context's dtype, contiguous, in the layouts of include/bsc.h."""
+    """Patches on the GPU (wraps ``bsc_ctx``): one patch from the constructor,
+    several independent patches from :meth:`batch`.  Tensors must be CUDA
+    tensors of the context's dtype, contiguous, in the layouts of
+    include/bsc.h (a batch concatenates its patches' control points)."""
 
     def __init__(self, nu, nv, rest, material, precision=FP64, dt=0.01, gravity=(0.0, -9.81, 0.0),
                  pinned=(), project=True, quadrature=(QUAD_REDUCED, QUAD_REDUCED), pcg_rel_tol=1e-8,
                  pcg_max_iter=10000, max_line_search=30, stream=None):
+        self._create([dict(nu=nu, nv=nv, rest=rest, material=material, dt=dt, gravity=gravity, pinned=pinned)],
+                     precision, project, quadrature, pcg_rel_tol, pcg_max_iter, max_line_search, stream)
+
+    @classmethod
+    def batch(cls, specs, precision=FP64, project=True, quadrature=(QUAD_REDUCED, QUAD_REDUCED), pcg_rel_tol=1e-8,
+              pcg_max_iter=10000, max_line_search=30, stream=None):
+        """Context of several patches; specs: dicts with nu, nv, rest, material,
+        dt, gravity, pinned (patch-local indices)."""
+        self = cls.__new__(cls)
+        self._create(list(specs), precision, project, quadrature, pcg_rel_tol, pcg_max_iter, max_line_search,
+                     stream)
+        return self
+
+    def _create(self, specs, precision, project, quadrature, pcg_rel_tol, pcg_max_iter, max_line_search, stream):
         import torch
         self.torch = torch
         lib = load()
-        self.nu, self.nv, self.N = int(nu), int(nv), int(nu) * int(nv)
-        self.n_spans = (self.nu - 2) * (self.nv - 2)
+        P = len(specs)
+        self.P = P
         self.precision = precision
         self.dtype = torch.float64 if precision == FP64 else torch.float32
-        self._rest = np.ascontiguousarray(np.asarray(rest, dtype=np.float64).reshape(self.N, 2))
-        mu = material.as_tuple() if hasattr(material, "as_tuple") else tuple(material)
-        self._mat = Material(*mu)
-        self._pins = np.ascontiguousarray(np.asarray(pinned, dtype=np.int32).ravel())
-        self._opt = Options(precision, float(dt), (ct.c_double * 3)(*gravity),
-                            self._pins.ctypes.data_as(ct.POINTER(ct.c_int32)), int(self._pins.size),
-                            int(bool(project)), float(pcg_rel_tol), int(pcg_max_iter), int(max_line_search))
+        self._grids = (KnotGrid * P)()
+        self._mats = (Material * P)()
+        self._opts = (Options * P)()
+        self._rests, self._pins = [], []
+        rest_ptrs = (ct.POINTER(ct.c_double) * P)()
+        for p, sp in enumerate(specs):
+            nu, nv = int(sp["nu"]), int(sp["nv"])
+            self._grids[p] = KnotGrid(nu, nv, None, None)
+            r = np.ascontiguousarray(np.asarray(sp["rest"], dtype=np.float64).reshape(nu * nv, 2))
+            self._rests.append(r)
+            rest_ptrs[p] = r.ctypes.data_as(ct.POINTER(ct.c_double))
+            m = sp["material"]
+            self._mats[p] = Material(*(m.as_tuple() if hasattr(m, "as_tuple") else tuple(m)))
+            pins = np.ascontiguousarray(np.asarray(sp.get("pinned", ()), dtype=np.int32).ravel())
+            self._pins.append(pins)
+            self._opts[p] = Options(precision, float(sp.get("dt", 0.01)),
+                                    (ct.c_double * 3)(*sp.get("gravity", (0.0, -9.81, 0.0))),
+                                    pins.ctypes.data_as(ct.POINTER(ct.c_int32)), int(pins.size),
+                                    int(bool(project)), float(pcg_rel_tol), int(pcg_max_iter), int(max_line_search))
         self._quad = Quadrature(*quadrature)
-        self._grid = KnotGrid(self.nu, self.nv, None, None)
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
         h = ct.c_void_p()
-        st = lib.bsc_create(ct.byref(self._grid), self._rest.ctypes.data_as(ct.POINTER(ct.c_double)),
-                            ct.byref(self._mat), ct.byref(self._quad), ct.byref(self._opt),
-                            ct.c_void_p(stream), ct.byref(h))
+        if P == 1:
+            st = lib.bsc_create(ct.byref(self._grids[0]), rest_ptrs[0], ct.byref(self._mats[0]),
+                                ct.byref(self._quad), ct.byref(self._opts[0]), ct.c_void_p(stream), ct.byref(h))
+        else:
+            st = lib.bsc_create_batch(P, self._grids, rest_ptrs, self._mats, ct.byref(self._quad), self._opts,
+                                      ct.c_void_p(stream), ct.byref(h))
         if st != OK:
             raise BscError(st, lib.bsc_last_error(None).decode())
         self._h = h
         self._lib = lib
+        cnt = ct.c_int()
+        cpo = (ct.c_int * (P + 1))()
+        spo = (ct.c_int * (P + 1))()
+        self._check(lib.bsc_batch_layout(h, ct.byref(cnt), cpo, spo))
+        self.cp_offset = np.array(list(cpo), dtype=np.int64)
+        self.span_offset = np.array(list(spo), dtype=np.int64)
+        self.N = int(self.cp_offset[-1])
+        self.n_spans = int(self.span_offset[-1])
+        self.nu, self.nv = int(self._grids[0].nu), int(self._grids[0].nv)
 
     # -- helpers -----------------------------------------------------------
     def _check(self, st):
@@ -273,6 +336,45 @@ class Context:
                                                    b.ctypes.data_as(ct.POINTER(ct.c_int))))
         return a, b
 
+    # -- batches ------------------------------------------------------------
+    def patch_reports(self):
+        reps = (NewtonReport * self.P)()
+        self._check(self._lib.bsc_patch_reports(self._h, reps))
+        return [reps[p] for p in range(self.P)]
+
+    def patch_energies(self, C, Chat=None):
+        out = (ct.c_double * self.P)()
+        self._check(self._lib.bsc_patch_energies(self._h, _ptr(self._vec(C, "C")), _ptr(self._vec(Chat, "Chat")),
+                                                 out))
+        return np.array(list(out))
+
+    def autotune(self, C, Chat=None):
+        t = Tuning()
+        self._check(self._lib.bsc_autotune(self._h, _ptr(self._vec(C, "C")), _ptr(self._vec(Chat, "Chat")),
+                                           ct.byref(t)))
+        return t.as_dict()
+
+    def set_tiles(self, tiles):
+        arr = (ct.c_int * 4)(*[int(t) for t in tiles])
+        self._check(self._lib.bsc_set_tiles(self._h, arr))
+
+    def pcg_split(self):
+        out = (ct.c_int * self.P)()
+        self._check(self._lib.bsc_pcg_split(self._h, out))
+        return list(out)
+
+    def set_graph(self, on=True):
+        self._check(self._lib.bsc_set_graph(self._h, int(bool(on))))
+
+    def graph_state(self):
+        on, cap, rep = ct.c_int(), ct.c_int(), ct.c_longlong()
+        self._check(self._lib.bsc_graph_state(self._h, ct.byref(on), ct.byref(cap), ct.byref(rep)))
+        return {"on": on.value, "captured": cap.value, "replays": rep.value}
+
+    def patch_slice(self, t, p):
+        """Patch p's columns of a (k, N) tensor (a view)."""
+        return t[..., int(self.cp_offset[p]):int(self.cp_offset[p + 1])]
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.bsc_destroy(self._h)
@@ -305,6 +407,24 @@ def solve_static(nu, nv, precision, K, b, x, rel_tol=1e-8, max_iter=10000, strea
     if st != OK:
         raise BscError(st, lib.bsc_last_error(None).decode())
     return it.value, rr.value
+
+
+def plan_blocks(n_cp, work, total):
+    """bsc_plan_blocks: split `total` PCG blocks over patches (pure host code)."""
+    lib = load()
+    n = len(n_cp)
+    a = (ct.c_int * n)(*[int(v) for v in n_cp])
+    w = (ct.c_double * n)(*[float(v) for v in work])
+    out = (ct.c_int * n)()
+    used = lib.bsc_plan_blocks(n, a, w, int(total), out)
+    return used, list(out)
+
+
+def batch_for_patches(patches, precision=FP64, **kw):
+    """Batched context for a list of ``inputs.Patch``."""
+    specs = [dict(nu=p.nu, nv=p.nv, rest=p.rest, material=p.material, dt=p.dt, gravity=p.gravity,
+                  pinned=p.pinned) for p in patches]
+    return Context.batch(specs, precision=precision, **kw)
 
 
 def context_for_patch(patch, precision=FP64, **kw):

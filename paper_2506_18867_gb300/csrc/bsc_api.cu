@@ -4,9 +4,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "bsc_internal.cuh"
 
-int pcg_grid_size(int precision, int num_sms, int N);
+int span_block(int precision);
+void plan_span_items(const bsc_ctx* c, std::vector<SpanItem>& out, int only_class, int tu_override);
 
 namespace {
 
@@ -34,51 +37,176 @@ bsc_status cuda_fail(bsc_ctx* c, cudaError_t e, const char* where) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+bsc_status status_error(bsc_ctx* c, int st, const char* where) {
+  if (st & BSC_STATUS_TIMEOUT_FLAG) return fail(c, BSC_ERR_TIMEOUT, "%s: device wait timed out", where);
+  return fail(c, BSC_ERR_NUMERIC, "%s: non-finite or singular value on the device (flags %d)", where, st);
+}
+
 // Reads and clears the device status word (synchronises the stream).
 bsc_status check_status(bsc_ctx* c, const char* where) {
-  int st = 0;
-  CK(cudaMemcpyAsync(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream), where);
+  CK(cudaMemcpyAsync(c->hflags + 1, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream), where);
   CK(cudaStreamSynchronize(c->stream), where);
+  const int st = c->hflags[1];
   if (st) {
     CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream), where);
-    if (st & BSC_STATUS_TIMEOUT_FLAG) return fail(c, BSC_ERR_TIMEOUT, "%s: device wait timed out", where);
-    return fail(c, BSC_ERR_NUMERIC, "%s: non-finite or singular value on the device (flags %d)", where, st);
+    return status_error(c, st, where);
   }
   return BSC_OK;
 }
 
+void drop_graph(bsc_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_C = c->graph_Chat = nullptr;
+}
+
 void free_ctx(bsc_ctx* c) {
   if (!c) return;
+  drop_graph(c);
   void* ptrs[] = {c->mem_off, c->bd_off, c->tab_mem, c->tab_bd, c->pts_mem, c->pts_bd, c->rest, c->mass,
                   c->pinned, c->bucket_list, c->nneg, c->E_span, c->g_span, c->H_span, c->A_mem, c->K_int,
-                  c->Dinv, c->partials, c->sync, c->dstatus, c->dscalars};
+                  c->Dinv, c->partials, c->sync, c->dstatus, c->dscalars, c->pd, c->cp_patch, c->sp_patch,
+                  c->span_items, c->red_items, c->red_off, c->pcg_blocks, c->pcg_out, c->steps, c->patch_E,
+                  c->pending, c->proj_work, c->proj_span, c->proj_kneg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->vec)
     if (p) cudaFree(p);
   for (void* p : c->proj_scratch)
     if (p) cudaFree(p);
-  if (c->proj_work) cudaFree(c->proj_work);
-  if (c->proj_span) cudaFree(c->proj_span);
-  if (c->proj_kneg) cudaFree(c->proj_kneg);
   for (int i = 0; i < 2; ++i) {
     if (c->side[i]) cudaStreamDestroy(c->side[i]);
     if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
   }
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->gev_in) cudaEventDestroy(c->gev_in);
+  if (c->gev_out) cudaEventDestroy(c->gev_out);
   if (c->hscalars) cudaFreeHost(c->hscalars);
+  if (c->hsteps) cudaFreeHost(c->hsteps);
+  if (c->hflags) cudaFreeHost(c->hflags);
   if (c->profiling)
     for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
+  free(c->hpd);
+  free(c->pcg_weight);
   free(c);
 }
 
+// Phase boundary for bsc_phase_times.  Inside a stream capture a plain
+// record would only become a dependency edge; the external flag makes it an
+// event-record node that the graph replays.
 void mark(bsc_ctx* c, int k) {
-  if (c->profiling) cudaEventRecord(c->ev[k], c->stream);
+  if (!c->profiling) return;
+  if (c->capturing)
+    cudaEventRecordWithFlags(c->ev[k], c->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(c->ev[k], c->stream);
 }
 
 bsc_status eval_path(bsc_ctx* c, const void* C, int want_grad, int want_hess, int project) {
   CK(launch_span_eval(c, C, want_grad, want_hess), "span evaluation");
   if (want_hess && project) CK(launch_project(c), "SPD projection");
+  return BSC_OK;
+}
+
+bsc_status validate_patch(int p, const bsc_knot_grid* g, const double* rest_xy, const bsc_material* m,
+                          const bsc_options* o) {
+  if (!g || !rest_xy || !m || !o) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: NULL argument (patch %d)", p);
+  if (g->nu < 5 || g->nv < 5)
+    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: nu, nv must be >= 5 (patch %d: %d x %d)", p, g->nu,
+                g->nv);
+  if ((long long)g->nu * g->nv > (1ll << 26))
+    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: grid too large (patch %d)", p);
+  for (int ax = 0; ax < 2; ++ax) {
+    const double* kn = ax ? g->knots_v : g->knots_u;
+    const int n = ax ? g->nv : g->nu;
+    if (!kn) continue;
+    for (int k = 0; k < n + 3; ++k) {
+      int want = k - 2;
+      want = want < 0 ? 0 : (want > n - 2 ? n - 2 : want);
+      if (kn[k] != (double)want)
+        return fail(nullptr, BSC_ERR_INVALID_ARG,
+                    "bsc_create: knots must be the open uniform integer vector (patch %d: knot %d of axis %d is %g)",
+                    p, k, ax, kn[k]);
+    }
+  }
+  const double mats[5] = {m->mu_st1, m->mu_st2, m->mu_sh, m->mu_bd, m->rho_area};
+  for (double v : mats)
+    if (!(v >= 0.0) || !isfinite(v))
+      return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: material must be finite, >= 0 (patch %d)", p);
+  const int N = g->nu * g->nv;
+  for (int k = 0; k < 2 * N; ++k)
+    if (!isfinite(rest_xy[k]))
+      return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: rest_xy has a non-finite value (patch %d)", p);
+  if (o->n_pinned < 0 || (o->n_pinned > 0 && !o->pinned))
+    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: bad pinned list (patch %d)", p);
+  for (int k = 0; k < o->n_pinned; ++k)
+    if (o->pinned[k] < 0 || o->pinned[k] >= N)
+      return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: pinned index %d out of range [0, %d) (patch %d)",
+                  o->pinned[k], N, p);
+  if (!isfinite(o->dt) || !isfinite(o->gravity[0]) || !isfinite(o->gravity[1]) || !isfinite(o->gravity[2]))
+    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: dt and gravity must be finite (patch %d)", p);
+  return BSC_OK;
+}
+
+// Everything of one Newton iteration up to and including the first
+// line-search round, and the read-back of the step records: the part a CUDA
+// graph holds.
+cudaError_t enqueue_newton(bsc_ctx* c, void* C, const void* Chat) {
+  cudaError_t e;
+  void *d = c->vec[0], *g = c->vec[5], *trial = c->vec[6], *rhs = c->vec[7];
+  mark(c, 0);
+  if ((e = launch_span_eval(c, C, 1, 1)) != cudaSuccess) return e;
+  mark(c, 1);
+  if (c->project_default && (e = launch_project(c)) != cudaSuccess) return e;
+  mark(c, 2);
+  if ((e = launch_patch_energy(c, C, Chat, c->patch_E)) != cudaSuccess) return e;
+  if ((e = launch_gradient(c, C, Chat, g)) != cudaSuccess) return e;
+  if ((e = launch_assemble(c, c->K_int)) != cudaSuccess) return e;
+  mark(c, 3);
+  if ((e = launch_axpy_trial(c, g, g, -2.0, rhs)) != cudaSuccess) return e;  // rhs = -g
+  if ((e = launch_pcg(c, c->K_int, rhs, d, c->pcg_tol, c->pcg_max_iter)) != cudaSuccess) return e;
+  mark(c, 4);
+  if ((e = launch_step_begin(c, d)) != cudaSuccess) return e;
+  if ((e = launch_ls_round(c, C, Chat, d, trial, C, 0)) != cudaSuccess) return e;
+  mark(c, 5);
+  if ((e = cudaMemcpyAsync(c->hsteps, c->steps, sizeof(PatchStep) * c->P, cudaMemcpyDeviceToHost, c->stream)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(c->hflags, c->pending, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return e;
+  return cudaMemcpyAsync(c->hflags + 1, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+}
+
+// Captures enqueue_newton on the graph stream into an executable graph.
+bsc_status capture_newton(bsc_ctx* c, void* C, const void* Chat) {
+  drop_graph(c);
+  cudaStream_t user = c->stream;
+  c->stream = c->gstream;
+  const unsigned long long before = c->launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e2 = cudaSuccess;
+  if (e == cudaSuccess) {
+    c->capturing = 1;
+    e2 = enqueue_newton(c, C, Chat);
+    c->capturing = 0;
+    e = cudaStreamEndCapture(c->gstream, &graph);
+  }
+  c->stream = user;
+  c->graph_kernels = c->launches - before;
+  c->launches = before;
+  if (e2 != cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    cudaGetLastError();
+    return cuda_fail(c, e, "bsc_newton_step: capturing the CUDA graph");
+  }
+  c->graph_C = C;
+  c->graph_Chat = Chat;
+  c->graph_profiling = c->profiling;
   return BSC_OK;
 }
 
@@ -91,63 +219,65 @@ extern "C" {
 
 const char* bsc_last_error(const bsc_ctx* c) { return c ? c->err : g_create_err; }
 
-bsc_status bsc_create(const bsc_knot_grid* g, const double* rest_xy, const bsc_material* m,
-                      const bsc_quadrature* q, const bsc_options* o, void* stream, bsc_ctx** out) {
+bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double* const* rest_xy,
+                            const bsc_material* mats, const bsc_quadrature* q, const bsc_options* opts,
+                            void* stream, bsc_ctx** out) {
   bsc_ctx* c = nullptr;
   if (!out) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: out is NULL");
   *out = nullptr;
-  if (!g || !rest_xy || !m || !o) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: NULL argument");
-  if (g->nu < 5 || g->nv < 5)
-    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: nu, nv must be >= 5 (got %d x %d)", g->nu, g->nv);
-  if ((long long)g->nu * g->nv > (1ll << 26))
-    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: grid too large");
-  for (int ax = 0; ax < 2; ++ax) {
-    const double* kn = ax ? g->knots_v : g->knots_u;
-    const int n = ax ? g->nv : g->nu;
-    if (!kn) continue;
-    for (int k = 0; k < n + 3; ++k) {
-      int want = k - 2;
-      want = want < 0 ? 0 : (want > n - 2 ? n - 2 : want);
-      if (kn[k] != (double)want)
-        return fail(nullptr, BSC_ERR_INVALID_ARG,
-                    "bsc_create: knots must be the open uniform integer vector (knot %d of axis %d is %g)", k,
-                    ax, kn[k]);
-    }
+  if (count < 1 || count > 304)
+    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: patch count must be in [1, 304] (got %d)", count);
+  if (!grids || !rest_xy || !mats || !opts) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: NULL argument");
+  long long Ntot = 0, Stot = 0;
+  for (int p = 0; p < count; ++p) {
+    bsc_status st = validate_patch(p, &grids[p], rest_xy[p], &mats[p], &opts[p]);
+    if (st != BSC_OK) return st;
+    Ntot += (long long)grids[p].nu * grids[p].nv;
+    Stot += (long long)(grids[p].nu - 2) * (grids[p].nv - 2);
   }
+  if (Ntot > (1ll << 26)) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: too many control points in total");
   const int mem_rule = q ? q->membrane : BSC_QUAD_REDUCED, bend_rule = q ? q->bending : BSC_QUAD_REDUCED;
   for (int r : {mem_rule, bend_rule})
     if (r != BSC_QUAD_REDUCED && r != BSC_QUAD_GAUSS2 && r != BSC_QUAD_GAUSS3)
       return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: unknown quadrature rule %d", r);
+  const bsc_options* o = &opts[0];
   if (o->precision != BSC_FP64 && o->precision != BSC_FP32)
     return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: unknown precision %d", o->precision);
-  const double mats[5] = {m->mu_st1, m->mu_st2, m->mu_sh, m->mu_bd, m->rho_area};
-  for (double v : mats)
-    if (!(v >= 0.0) || !isfinite(v)) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: material must be finite, >= 0");
-  const int N = g->nu * g->nv;
-  for (int k = 0; k < 2 * N; ++k)
-    if (!isfinite(rest_xy[k])) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: rest_xy has a non-finite value");
-  if (o->n_pinned < 0 || (o->n_pinned > 0 && !o->pinned))
-    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: bad pinned list");
-  for (int k = 0; k < o->n_pinned; ++k)
-    if (o->pinned[k] < 0 || o->pinned[k] >= N)
-      return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: pinned index %d out of range [0, %d)", o->pinned[k], N);
-  if (!isfinite(o->dt) || !isfinite(o->gravity[0]) || !isfinite(o->gravity[1]) || !isfinite(o->gravity[2]))
-    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: dt and gravity must be finite");
 
   c = (bsc_ctx*)calloc(1, sizeof(bsc_ctx));
   if (!c) return fail(nullptr, BSC_ERR_OOM, "bsc_create: host allocation failed");
-  c->nu = g->nu; c->nv = g->nv; c->Su = g->nu - 2; c->Sv = g->nv - 2; c->N = N; c->Nsp = c->Su * c->Sv;
+  c->P = count;
+  c->hpd = (PatchDev*)calloc((size_t)count, sizeof(PatchDev));
+  if (!c->hpd) {
+    free_ctx(c);
+    return fail(nullptr, BSC_ERR_OOM, "bsc_create: host allocation failed");
+  }
+  {
+    int cp0 = 0, sp0 = 0;
+    for (int p = 0; p < count; ++p) {
+      PatchDev& d = c->hpd[p];
+      d.nu = grids[p].nu; d.nv = grids[p].nv; d.Su = d.nu - 2; d.Sv = d.nv - 2;
+      d.N = d.nu * d.nv; d.Nsp = d.Su * d.Sv; d.cp0 = cp0; d.sp0 = sp0;
+      d.mu1 = mats[p].mu_st1; d.mu2 = mats[p].mu_st2; d.mush = mats[p].mu_sh; d.mubd = mats[p].mu_bd;
+      d.rho = mats[p].rho_area;
+      d.inv_dt2 = opts[p].dt > 0.0 ? 1.0 / (opts[p].dt * opts[p].dt) : 0.0;
+      for (int k = 0; k < 3; ++k) d.grav[k] = opts[p].gravity[k];
+      cp0 += d.N;
+      sp0 += d.Nsp;
+    }
+  }
+  c->nu = grids[0].nu; c->nv = grids[0].nv; c->Su = c->nu - 2; c->Sv = c->nv - 2;
+  c->N = (int)Ntot; c->Nsp = (int)Stot;
   c->precision = o->precision;
   c->tsize = o->precision == BSC_FP64 ? sizeof(double) : sizeof(float);
-  c->mu_st1 = m->mu_st1; c->mu_st2 = m->mu_st2; c->mu_sh = m->mu_sh; c->mu_bd = m->mu_bd; c->rho = m->rho_area;
   c->mem_rule = mem_rule; c->bend_rule = bend_rule;
-  c->dt = o->dt;
-  for (int k = 0; k < 3; ++k) c->gravity[k] = o->gravity[k];
   c->project_default = o->project;
   c->pcg_tol = o->pcg_rel_tol > 0.0 ? o->pcg_rel_tol : 1e-8;
   c->pcg_max_iter = o->pcg_max_iter > 0 ? o->pcg_max_iter : 10000;
   c->max_ls = o->max_line_search > 0 ? o->max_line_search : 30;
   c->stream = (cudaStream_t)stream;
+  c->use_graph = 1;
+  for (int k = 0; k < TILE_CLASSES; ++k) c->tile_tu[k] = 0;
 
   bsc_status st = BSC_OK;
   cudaError_t e = cudaGetDevice(&c->device);
@@ -164,61 +294,83 @@ bsc_status bsc_create(const bsc_knot_grid* g, const double* rest_xy, const bsc_m
     return fail(nullptr, BSC_ERR_CUDA, "bsc_create: device lacks cooperative launch");
   }
   const size_t ts = c->tsize;
+  const size_t N = (size_t)c->N, Nsp = (size_t)c->Nsp;
   c->red_grid = 2 * c->num_sms;
-  c->pcg_grid = pcg_grid_size(c->precision, c->num_sms, N);
-  const int max_grid = c->red_grid > c->pcg_grid ? c->red_grid : c->pcg_grid;
-#define ALLOC(ptr, bytes)                                     \
-  do {                                                        \
-    e = cudaMalloc((void**)&(ptr), (bytes));                  \
-    if (e != cudaSuccess) {                                   \
+#define ALLOC(ptr, bytes)                                         \
+  do {                                                            \
+    e = cudaMalloc((void**)&(ptr), (bytes));                      \
+    if (e != cudaSuccess) {                                       \
       st = cuda_fail(nullptr, e, "bsc_create: cudaMalloc " #ptr); \
-      free_ctx(c);                                            \
-      return st;                                              \
-    }                                                         \
+      free_ctx(c);                                                \
+      return st;                                                  \
+    }                                                             \
   } while (0)
-  ALLOC(c->rest, sizeof(double) * 2 * (size_t)N);
-  ALLOC(c->mass, sizeof(double) * (size_t)N);
-  ALLOC(c->pinned, (size_t)N);
-  ALLOC(c->nneg, sizeof(int) * (size_t)c->Nsp);
-  ALLOC(c->E_span, sizeof(double) * (size_t)c->Nsp);
-  ALLOC(c->g_span, ts * 27 * (size_t)c->Nsp);
-  ALLOC(c->H_span, ts * H27 * (size_t)c->Nsp);
-  ALLOC(c->K_int, ts * 225 * (size_t)N);
-  ALLOC(c->Dinv, ts * 9 * (size_t)N);
-  for (int k = 0; k < 8; ++k) ALLOC(c->vec[k], ts * 3 * (size_t)N);
-  ALLOC(c->partials, sizeof(double) * 4 * (size_t)max_grid);
-  ALLOC(c->sync, sizeof(unsigned int) * 4);
+#define CREATE_CK(call, what)                       \
+  do {                                              \
+    e = (call);                                     \
+    if (e != cudaSuccess) {                         \
+      st = cuda_fail(nullptr, e, "bsc_create: " what); \
+      free_ctx(c);                                  \
+      return st;                                    \
+    }                                               \
+  } while (0)
+  ALLOC(c->pd, sizeof(PatchDev) * count);
+  ALLOC(c->rest, sizeof(double) * 2 * N);
+  ALLOC(c->mass, sizeof(double) * N);
+  ALLOC(c->pinned, N);
+  ALLOC(c->nneg, sizeof(int) * Nsp);
+  ALLOC(c->E_span, sizeof(double) * Nsp);
+  ALLOC(c->g_span, ts * 27 * Nsp);
+  ALLOC(c->H_span, ts * H27 * Nsp);
+  ALLOC(c->K_int, ts * 225 * N);
+  ALLOC(c->Dinv, ts * 9 * N);
+  for (int k = 0; k < 8; ++k) ALLOC(c->vec[k], ts * 3 * N);
+  ALLOC(c->sync, sizeof(unsigned int) * (2 * (size_t)count + 2));
   ALLOC(c->dstatus, sizeof(int) * 4);
   ALLOC(c->dscalars, sizeof(double) * 16);
-#undef ALLOC
-  e = cudaMallocHost((void**)&c->hscalars, sizeof(double) * 16);
-  if (e != cudaSuccess) {
-    st = cuda_fail(nullptr, e, "bsc_create: cudaMallocHost");
-    free_ctx(c);
-    return st;
-  }
+  ALLOC(c->steps, sizeof(PatchStep) * count);
+  ALLOC(c->patch_E, sizeof(double) * 2 * count);
+  ALLOC(c->pending, sizeof(int) * 4);
+  CREATE_CK(cudaMallocHost((void**)&c->hscalars, sizeof(double) * 16), "cudaMallocHost");
+  CREATE_CK(cudaMallocHost((void**)&c->hsteps, sizeof(PatchStep) * count), "cudaMallocHost");
+  CREATE_CK(cudaMallocHost((void**)&c->hflags, sizeof(int) * 4), "cudaMallocHost");
+  memset(c->hsteps, 0, sizeof(PatchStep) * count);
   // rest coordinates as two planes; pinned mask
-  double* rp = (double*)malloc(sizeof(double) * 2 * (size_t)N);
-  uint8_t* pm = (uint8_t*)calloc((size_t)N, 1);
-  for (int k = 0; k < N; ++k) {
-    rp[k] = rest_xy[2 * k];
-    rp[N + k] = rest_xy[2 * k + 1];
+  {
+    std::vector<double> rp(2 * N);
+    std::vector<uint8_t> pm(N, 0);
+    for (int p = 0; p < count; ++p) {
+      const PatchDev& d = c->hpd[p];
+      for (int k = 0; k < d.N; ++k) {
+        rp[d.cp0 + k] = rest_xy[p][2 * k];
+        rp[N + d.cp0 + k] = rest_xy[p][2 * k + 1];
+      }
+      for (int k = 0; k < opts[p].n_pinned; ++k) pm[d.cp0 + opts[p].pinned[k]] = 1;
+    }
+    CREATE_CK(cudaMemcpy(c->rest, rp.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice), "copy rest");
+    CREATE_CK(cudaMemcpy(c->pinned, pm.data(), N, cudaMemcpyHostToDevice), "copy pinned");
   }
-  for (int k = 0; k < o->n_pinned; ++k) pm[o->pinned[k]] = 1;
-  e = cudaMemcpy(c->rest, rp, sizeof(double) * 2 * (size_t)N, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c->pinned, pm, (size_t)N, cudaMemcpyHostToDevice);
-  free(rp);
-  free(pm);
-  if (e == cudaSuccess) e = cudaMemset(c->sync, 0, sizeof(unsigned int) * 4);
-  if (e == cudaSuccess) e = cudaMemset(c->dstatus, 0, sizeof(int) * 4);
-  if (e == cudaSuccess) e = cudaMemset(c->nneg, 0, sizeof(int) * (size_t)c->Nsp);
-  if (e == cudaSuccess) e = launch_build_tables(c);
-  if (e == cudaSuccess) e = setup_projection(c);
-  if (e != cudaSuccess) {
-    st = cuda_fail(nullptr, e, "bsc_create: building quadrature tables");
-    free_ctx(c);
-    return st;
+  CREATE_CK(cudaMemcpy(c->pd, c->hpd, sizeof(PatchDev) * count, cudaMemcpyHostToDevice), "copy patches");
+  CREATE_CK(cudaMemset(c->sync, 0, sizeof(unsigned int) * (2 * (size_t)count + 2)), "memset");
+  CREATE_CK(cudaMemset(c->dstatus, 0, sizeof(int) * 4), "memset");
+  CREATE_CK(cudaMemset(c->nneg, 0, sizeof(int) * Nsp), "memset");
+  CREATE_CK(cudaMemset(c->steps, 0, sizeof(PatchStep) * count), "memset");
+  CREATE_CK(cudaMemset(c->pending, 0, sizeof(int) * 4), "memset");
+  CREATE_CK(launch_build_tables(c), "building quadrature tables");
+  CREATE_CK(setup_projection(c), "projection set-up");
+  CREATE_CK(setup_span_eval(c), "span evaluation set-up");
+  CREATE_CK(build_span_items(c), "span work items");
+  CREATE_CK(build_red_items(c), "reduction items");
+  CREATE_CK(setup_pcg(c), "PCG set-up (too many patches for the co-resident blocks?)");
+  {
+    const size_t np = (size_t)std::max(std::max(c->red_grid, c->pcg_grid), 2 * c->n_red_items);
+    ALLOC(c->partials, sizeof(double) * 4 * np);
   }
+  CREATE_CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking), "graph stream");
+  CREATE_CK(cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming), "graph events");
+  CREATE_CK(cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming), "graph events");
+#undef ALLOC
+#undef CREATE_CK
   st = check_status(c, "bsc_create");
   if (st != BSC_OK) {
     snprintf(g_create_err, sizeof(g_create_err), "%s (rest map singular?)", c->err);
@@ -230,9 +382,19 @@ bsc_status bsc_create(const bsc_knot_grid* g, const double* rest_xy, const bsc_m
   return BSC_OK;
 }
 
+bsc_status bsc_create(const bsc_knot_grid* g, const double* rest_xy, const bsc_material* m,
+                      const bsc_quadrature* q, const bsc_options* o, void* stream, bsc_ctx** out) {
+  if (!out) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: out is NULL");
+  *out = nullptr;
+  if (!g || !rest_xy || !m || !o) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: NULL argument");
+  const double* rests[1] = {rest_xy};
+  return bsc_create_batch(1, g, rests, m, q, o, stream, out);
+}
+
 void bsc_destroy(bsc_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->gstream);
   free_ctx(c);
 }
 
@@ -251,22 +413,48 @@ bsc_status bsc_sizes(const bsc_ctx* c, int* n_cp, int* n_spans, int* n_mem, int*
   return BSC_OK;
 }
 
+bsc_status bsc_batch_layout(const bsc_ctx* c, int* count, int* cp_offset, int* span_offset) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (count) *count = c->P;
+  for (int p = 0; p <= c->P; ++p) {
+    if (cp_offset) cp_offset[p] = p < c->P ? c->hpd[p].cp0 : c->N;
+    if (span_offset) span_offset[p] = p < c->P ? c->hpd[p].sp0 : c->Nsp;
+  }
+  return BSC_OK;
+}
+
+static bool any_inertia(const bsc_ctx* c) {
+  for (int p = 0; p < c->P; ++p)
+    if (c->hpd[p].inv_dt2 > 0.0) return true;
+  return false;
+}
+
+bsc_status bsc_patch_energies(bsc_ctx* c, const void* C, const void* Chat, double* E_out) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (!C || !E_out || (any_inertia(c) && !Chat)) return fail(c, BSC_ERR_INVALID_ARG, "bsc_energy: NULL argument");
+  if (!aligned16(C) || (Chat && !aligned16(Chat)))
+    return fail(c, BSC_ERR_INVALID_ARG, "bsc_energy: pointers must be 16-byte aligned");
+  CK(launch_span_eval(c, C, 0, 0), "bsc_energy");
+  CK(launch_patch_energy(c, C, Chat, c->patch_E), "bsc_energy");
+  CK(cudaMemcpyAsync(E_out, c->patch_E, sizeof(double) * c->P, cudaMemcpyDeviceToHost, c->stream), "bsc_energy");
+  return check_status(c, "bsc_energy");
+}
+
 bsc_status bsc_energy(bsc_ctx* c, const void* C, const void* Chat, double* E_out) {
   if (!c) return BSC_ERR_INVALID_ARG;
-  if (!C || !E_out || (c->dt > 0.0 && !Chat)) return fail(c, BSC_ERR_INVALID_ARG, "bsc_energy: NULL argument");
-  if (!aligned16(C) || (Chat && !aligned16(Chat))) return fail(c, BSC_ERR_INVALID_ARG, "bsc_energy: pointers must be 16-byte aligned");
-  CK(launch_span_eval(c, C, 0, 0), "bsc_energy");
-  CK(launch_energy(c, C, Chat, c->dscalars), "bsc_energy");
-  CK(cudaMemcpyAsync(c->hscalars, c->dscalars, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "bsc_energy");
-  bsc_status st = check_status(c, "bsc_energy");
+  if (!E_out) return fail(c, BSC_ERR_INVALID_ARG, "bsc_energy: NULL argument");
+  std::vector<double> E(c->P);
+  bsc_status st = bsc_patch_energies(c, C, Chat, E.data());
   if (st != BSC_OK) return st;
-  *E_out = c->hscalars[0];
+  double tot = 0.0;
+  for (int p = 0; p < c->P; ++p) tot += E[p];
+  *E_out = tot;
   return BSC_OK;
 }
 
 bsc_status bsc_gradient(bsc_ctx* c, const void* C, const void* Chat, void* g) {
   if (!c) return BSC_ERR_INVALID_ARG;
-  if (!C || !g || (c->dt > 0.0 && !Chat)) return fail(c, BSC_ERR_INVALID_ARG, "bsc_gradient: NULL argument");
+  if (!C || !g || (any_inertia(c) && !Chat)) return fail(c, BSC_ERR_INVALID_ARG, "bsc_gradient: NULL argument");
   if (!aligned16(C) || !aligned16(g)) return fail(c, BSC_ERR_INVALID_ARG, "bsc_gradient: pointers must be 16-byte aligned");
   bsc_status st = eval_path(c, C, 1, 0, 0);
   if (st != BSC_OK) return st;
@@ -295,105 +483,244 @@ bsc_status bsc_spmv(bsc_ctx* c, const void* K, const void* x, void* y) {
   return BSC_OK;
 }
 
+// Per-patch solves; pcg_out (3 per patch) is left in hscal (host, 3 P).
+static bsc_status solve_all(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit,
+                            std::vector<double>& hout) {
+  CK(launch_pcg(c, K, b, x, tol, maxit), "bsc_solve");
+  hout.resize(3 * (size_t)c->P);
+  CK(cudaMemcpyAsync(hout.data(), c->pcg_out, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToHost, c->stream),
+     "bsc_solve");
+  return check_status(c, "bsc_solve");
+}
+
 bsc_status bsc_solve(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit, int* iters,
                      double* rel_res) {
   if (!c) return BSC_ERR_INVALID_ARG;
   const void* Kd = K ? K : c->K_last;
   if (!Kd || !b || !x) return fail(c, BSC_ERR_INVALID_ARG, "bsc_solve: no matrix or NULL vector");
+  if (b == x) return fail(c, BSC_ERR_INVALID_ARG, "bsc_solve: b and x must not alias");
   if (!(tol > 0.0)) tol = c->pcg_tol;
   if (maxit <= 0) maxit = c->pcg_max_iter;
-  CK(cudaMemsetAsync(c->sync, 0, sizeof(unsigned int) * 4, c->stream), "bsc_solve");
-  CK(launch_pcg(c, Kd, b, x, tol, maxit), "bsc_solve");
-  CK(cudaMemcpyAsync(c->hscalars + 8, c->dscalars + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-     "bsc_solve");
-  bsc_status st = check_status(c, "bsc_solve");
+  std::vector<double> hout;
+  bsc_status st = solve_all(c, Kd, b, x, tol, maxit, hout);
   if (st != BSC_OK) return st;
-  const int it = (int)c->hscalars[8];
+  int it = 0;
+  double rr = 0.0;
+  for (int p = 0; p < c->P; ++p) {
+    it = std::max(it, (int)hout[3 * p]);
+    rr = std::max(rr, hout[3 * p + 1]);
+  }
   if (iters) *iters = it;
-  if (rel_res) *rel_res = c->hscalars[9];
-  if (!(c->hscalars[9] <= tol)) return fail(c, BSC_ERR_NOT_CONVERGED, "bsc_solve: %d iterations, rel. residual %g", it, c->hscalars[9]);
+  if (rel_res) *rel_res = rr;
+  if (!(rr <= tol)) return fail(c, BSC_ERR_NOT_CONVERGED, "bsc_solve: %d iterations, rel. residual %g", it, rr);
   return BSC_OK;
+}
+
+static void fill_report(const bsc_ctx* c, const PatchStep& s, bsc_newton_report& r) {
+  memset(&r, 0, sizeof(r));
+  r.E0 = s.E0;
+  r.E1 = s.E1;
+  r.alpha = s.alpha;
+  r.dir_inf = s.dir_inf;
+  r.pcg_rel_res = s.pcg_res;
+  r.pcg_iters = (int)s.pcg_iters;
+  r.ls_halvings = s.halvings;
+  r.spans_projected = (int)s.spans_projected;
+  if (s.state == -2) r.status = BSC_ERR_NUMERIC;
+  else if (s.state == -1) r.status = BSC_ERR_LINESEARCH;
+  else if (!(s.pcg_res <= c->pcg_tol)) r.status = BSC_ERR_NOT_CONVERGED;
+  else r.status = BSC_OK;
 }
 
 bsc_status bsc_newton_step(bsc_ctx* c, void* C, const void* Chat, bsc_newton_report* rep) {
   if (!c) return BSC_ERR_INVALID_ARG;
-  bsc_newton_report r;
-  memset(&r, 0, sizeof(r));
-  if (!C || (c->dt > 0.0 && !Chat)) return fail(c, BSC_ERR_INVALID_ARG, "bsc_newton_step: NULL argument");
-  if (!aligned16(C) || (Chat && !aligned16(Chat))) return fail(c, BSC_ERR_INVALID_ARG, "bsc_newton_step: pointers must be 16-byte aligned");
-  void *d = c->vec[0], *g = c->vec[5], *trial = c->vec[6];
-  mark(c, 0);
-  CK(launch_span_eval(c, C, 1, 1), "newton: span evaluation");
-  mark(c, 1);
-  if (c->project_default) {
-    CK(launch_project(c), "newton: SPD projection");
-    CK(launch_count_projected(c, c->dscalars + 3), "newton: SPD projection");
-  } else {
-    CK(cudaMemsetAsync(c->dscalars + 3, 0, sizeof(double), c->stream), "newton");
-  }
-  mark(c, 2);
-  bsc_status st = BSC_OK;
-  {
-    CK(launch_energy(c, C, Chat, c->dscalars + 0), "newton: energy");
-    CK(launch_gradient(c, C, Chat, g), "newton: gradient");
-    CK(launch_assemble(c, c->K_int), "newton: assembly");
-    c->K_last = c->K_int;
-    mark(c, 3);
-    // right-hand side -g (into the spare vector), then PCG
-    CK(launch_axpy_trial(c, g, g, -2.0, c->vec[7]), "newton: rhs");
-    int iters = 0;
-    double rr = 0.0;
-    st = bsc_solve(c, c->K_int, c->vec[7], d, c->pcg_tol, c->pcg_max_iter, &iters, &rr);
-    r.pcg_iters = iters;
-    r.pcg_rel_res = rr;
-    mark(c, 4);
-  }
-  if (st == BSC_OK || st == BSC_ERR_NOT_CONVERGED) {
-    bsc_status solve_st = st;
-    CK(launch_absmax(c, d, c->dscalars + 1), "newton: |d|");
-    CK(cudaMemcpyAsync(c->hscalars, c->dscalars, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "newton");
-    st = check_status(c, "bsc_newton_step");
-    if (st == BSC_OK) {
-      r.E0 = c->hscalars[0];
-      r.dir_inf = c->hscalars[1];
-      r.spans_projected = (int)c->hscalars[3];
-      double alpha = 1.0;
-      int h = 0;
-      for (;;) {
-        CK(launch_axpy_trial(c, C, d, alpha, trial), "newton: trial");
-        CK(launch_span_eval(c, trial, 0, 0), "newton: trial energy");
-        CK(launch_energy(c, trial, Chat, c->dscalars + 2), "newton: trial energy");
-        CK(cudaMemcpyAsync(c->hscalars + 2, c->dscalars + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-           "newton");
-        st = check_status(c, "newton: line search");
-        if (st != BSC_OK) break;
-        const double E1 = c->hscalars[2];
-        if (E1 <= r.E0) {
-          CK(launch_copy_vec(c, trial, C), "newton: commit");
-          r.E1 = E1;
-          r.alpha = alpha;
-          r.ls_halvings = h;
-          break;
-        }
-        if (h >= c->max_ls) {
-          r.E1 = E1;
-          r.alpha = 0.0;
-          r.ls_halvings = h;
-          st = fail(c, BSC_ERR_LINESEARCH, "bsc_newton_step: no decrease after %d halvings (E0 %.17g, E1 %.17g)",
-                    h, r.E0, E1);
-          break;
-        }
-        alpha *= 0.5;
-        ++h;
-      }
-      if (st == BSC_OK && solve_st != BSC_OK) st = solve_st;
+  bsc_newton_report agg;
+  memset(&agg, 0, sizeof(agg));
+  if (rep) *rep = agg;
+  if (!C || (any_inertia(c) && !Chat)) return fail(c, BSC_ERR_INVALID_ARG, "bsc_newton_step: NULL argument");
+  if (!aligned16(C) || (Chat && !aligned16(Chat)))
+    return fail(c, BSC_ERR_INVALID_ARG, "bsc_newton_step: pointers must be 16-byte aligned");
+  if (C == Chat) return fail(c, BSC_ERR_INVALID_ARG, "bsc_newton_step: C and Chat must not alias");
+  for (int p = 0; p < c->P; ++p) c->hsteps[p].state = -3;  // not run
+  if (c->use_graph) {
+    if (!c->graph || c->graph_C != C || c->graph_Chat != Chat || c->graph_profiling != c->profiling) {
+      bsc_status st = capture_newton(c, C, Chat);
+      if (st != BSC_OK) return st;
     }
+    CK(cudaEventRecord(c->gev_in, c->stream), "bsc_newton_step");
+    CK(cudaStreamWaitEvent(c->gstream, c->gev_in, 0), "bsc_newton_step");
+    CK(cudaGraphLaunch(c->graph, c->gstream), "bsc_newton_step: graph launch");
+    CK(cudaEventRecord(c->gev_out, c->gstream), "bsc_newton_step");
+    CK(cudaStreamWaitEvent(c->stream, c->gev_out, 0), "bsc_newton_step");
+    c->launches += c->graph_kernels;
+    c->graph_replays += 1;
+  } else {
+    CK(enqueue_newton(c, C, Chat), "bsc_newton_step");
   }
-  mark(c, 5);
-  r.status = st;
-  if (rep) *rep = r;
-  if (st == BSC_OK) CK(cudaStreamSynchronize(c->stream), "bsc_newton_step");
+  CK(cudaStreamSynchronize(c->stream), "bsc_newton_step");
+  c->K_last = c->K_int;
+  // further line-search rounds for the patches that rejected alpha = 1
+  int round = 1;
+  while (c->hflags[0] > 0 && c->hflags[1] == 0 && round <= c->max_ls) {
+    CK(launch_ls_round(c, C, Chat, c->vec[0], c->vec[6], C, round), "bsc_newton_step: line search");
+    CK(cudaMemcpyAsync(c->hflags, c->pending, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "bsc_newton_step");
+    CK(cudaMemcpyAsync(c->hflags + 1, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+       "bsc_newton_step");
+    CK(cudaStreamSynchronize(c->stream), "bsc_newton_step");
+    ++round;
+  }
+  if (round > 1) {
+    CK(cudaMemcpyAsync(c->hsteps, c->steps, sizeof(PatchStep) * c->P, cudaMemcpyDeviceToHost, c->stream),
+       "bsc_newton_step");
+    mark(c, 5);
+    CK(cudaStreamSynchronize(c->stream), "bsc_newton_step");
+  }
+  const int flags = c->hflags[1];
+  if (flags) {
+    CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream), "bsc_newton_step");
+    CK(cudaStreamSynchronize(c->stream), "bsc_newton_step");
+  }
+  // aggregate
+  bsc_status st = BSC_OK;
+  agg.alpha = 1.0;
+  for (int p = 0; p < c->P; ++p) {
+    bsc_newton_report r;
+    fill_report(c, c->hsteps[p], r);
+    agg.E0 += r.E0;
+    agg.E1 += r.E1;
+    agg.alpha = std::min(agg.alpha, r.alpha);
+    agg.dir_inf = std::max(agg.dir_inf, r.dir_inf);
+    agg.pcg_rel_res = std::max(agg.pcg_rel_res, r.pcg_rel_res);
+    agg.pcg_iters = std::max(agg.pcg_iters, r.pcg_iters);
+    agg.ls_halvings = std::max(agg.ls_halvings, r.ls_halvings);
+    agg.spans_projected += r.spans_projected;
+    if (st == BSC_OK && r.status != BSC_OK) st = (bsc_status)r.status;
+  }
+  if (flags) st = status_error(c, flags, "bsc_newton_step");
+  else if (st == BSC_ERR_LINESEARCH) fail(c, st, "bsc_newton_step: no decrease after %d halvings", c->max_ls);
+  else if (st == BSC_ERR_NOT_CONVERGED) fail(c, st, "bsc_newton_step: PCG did not reach the tolerance");
+  else if (st == BSC_ERR_NUMERIC) fail(c, st, "bsc_newton_step: solve failed");
+  agg.status = st;
+  if (rep) *rep = agg;
   return st;
+}
+
+bsc_status bsc_patch_reports(const bsc_ctx* c, bsc_newton_report* reps) {
+  if (!c || !reps) return BSC_ERR_INVALID_ARG;
+  for (int p = 0; p < c->P; ++p) fill_report(c, c->hsteps[p], reps[p]);
+  return BSC_OK;
+}
+
+bsc_status bsc_set_graph(bsc_ctx* c, int on) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  c->use_graph = on ? 1 : 0;
+  if (!on) {
+    CK(cudaStreamSynchronize(c->gstream), "bsc_set_graph");
+    drop_graph(c);
+  }
+  return BSC_OK;
+}
+
+bsc_status bsc_graph_state(const bsc_ctx* c, int* on, int* captured, long long* replays) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (on) *on = c->use_graph;
+  if (captured) *captured = c->graph ? 1 : 0;
+  if (replays) *replays = c->graph_replays;
+  return BSC_OK;
+}
+
+bsc_status bsc_set_tiles(bsc_ctx* c, const int* tu) {
+  if (!c || !tu) return BSC_ERR_INVALID_ARG;
+  const int B = span_block(c->precision);
+  for (int k = 0; k < TILE_CLASSES; ++k)
+    if (!(tu[k] == 0 || tu[k] == 8 || tu[k] == 16 || tu[k] == 32) || (tu[k] > 0 && B % tu[k] != 0))
+      return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_tiles: width %d not in {0, 8, 16, 32}", tu[k]);
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_tiles");
+  for (int k = 0; k < TILE_CLASSES; ++k) c->tile_tu[k] = tu[k];
+  drop_graph(c);
+  CK(build_span_items(c), "bsc_set_tiles");
+  return BSC_OK;
+}
+
+bsc_status bsc_pcg_split(const bsc_ctx* c, int* blocks) {
+  if (!c || !blocks) return BSC_ERR_INVALID_ARG;
+  std::vector<PcgBlock> tab(c->pcg_grid);
+  if (cudaMemcpy(tab.data(), c->pcg_blocks, sizeof(PcgBlock) * c->pcg_grid, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BSC_ERR_CUDA;
+  for (int p = 0; p < c->P; ++p) blocks[p] = 0;
+  for (const PcgBlock& b : tab) blocks[b.p] += 1;
+  return BSC_OK;
+}
+
+bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning* out) {
+  if (!c || !C) return BSC_ERR_INVALID_ARG;
+  if (any_inertia(c) && !Chat) return fail(c, BSC_ERR_INVALID_ARG, "bsc_autotune: NULL argument");
+  bsc_tuning t;
+  memset(&t, 0, sizeof(t));
+  const int cand[4] = {0, 8, 16, 32};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "bsc_autotune");
+  CK(cudaEventCreate(&e1), "bsc_autotune");
+  CK(cudaStreamSynchronize(c->gstream), "bsc_autotune");
+  drop_graph(c);
+  SpanItem* dev_items = nullptr;
+  bsc_status st = BSC_OK;
+  for (int cls = 0; cls < TILE_CLASSES && st == BSC_OK; ++cls) {
+    t.tile_tu[cls] = -1;
+    double best = 1e300;
+    for (int k = 0; k < 4 && st == BSC_OK; ++k) {
+      std::vector<SpanItem> items;
+      plan_span_items(c, items, cls, cand[k]);
+      t.tile_ms[cls][k] = -1.0;
+      if (items.empty()) continue;
+      cudaError_t e = cudaMalloc(&dev_items, sizeof(SpanItem) * items.size());
+      if (e == cudaSuccess)
+        e = cudaMemcpy(dev_items, items.data(), sizeof(SpanItem) * items.size(), cudaMemcpyHostToDevice);
+      float ms = 0.0f, best_rep = 1e30f;
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) e = launch_span_eval_items(c, C, 1, 1, dev_items, (int)items.size(), cand[k]);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best_rep) best_rep = ms;  // the first launch warms up
+      }
+      if (dev_items) cudaFree(dev_items);
+      dev_items = nullptr;
+      if (e != cudaSuccess) {
+        st = cuda_fail(c, e, "bsc_autotune: timing span evaluation");
+        break;
+      }
+      t.tile_ms[cls][k] = best_rep;
+      if (best_rep < best) {
+        best = best_rep;
+        t.tile_tu[cls] = cand[k];
+      }
+    }
+    if (t.tile_tu[cls] >= 0) c->tile_tu[cls] = t.tile_tu[cls];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != BSC_OK) return st;
+  CK(build_span_items(c), "bsc_autotune");
+  // PCG split from measured iteration counts
+  {
+    void *g = c->vec[5], *rhs = c->vec[7], *x = c->vec[0];
+    st = eval_path(c, C, 1, 1, c->project_default);
+    if (st != BSC_OK) return st;
+    CK(launch_gradient(c, C, Chat, g), "bsc_autotune");
+    CK(launch_assemble(c, c->K_int), "bsc_autotune");
+    CK(launch_axpy_trial(c, g, g, -2.0, rhs), "bsc_autotune");
+    std::vector<double> hout;
+    st = solve_all(c, c->K_int, rhs, x, c->pcg_tol, c->pcg_max_iter, hout);
+    if (st != BSC_OK) return st;
+    for (int p = 0; p < c->P; ++p) c->pcg_weight[p] = (double)c->hpd[p].N * std::max(1.0, hout[3 * p]);
+    CK(assign_pcg_blocks(c), "bsc_autotune");
+    c->K_last = c->K_int;
+  }
+  t.pcg_grid = c->pcg_grid;
+  if (out) *out = t;
+  return BSC_OK;
 }
 
 bsc_status bsc_span_terms(bsc_ctx* c, const void* C, int project, double* E_span, void* g_span, void* H_span) {
@@ -419,6 +746,10 @@ bsc_status bsc_quadrature_tables(bsc_ctx* c, int which, double* out, int cap, in
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(tab, which ? c->tab_bd : c->tab_mem, c->tsize * ncol * (size_t)n, cudaMemcpyDeviceToHost,
                         c->stream);
+  std::vector<int> off(c->Nsp + 1);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(off.data(), which ? c->bd_off : c->mem_off, sizeof(int) * (c->Nsp + 1),
+                        cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     free(pts);
@@ -434,6 +765,9 @@ bsc_status bsc_quadrature_tables(bsc_ctx* c, int which, double* out, int cap, in
       r[5 + j] = c->precision == BSC_FP64 ? ((double*)tab)[idx] : (double)((float*)tab)[idx];
     }
   }
+  // owning span (context-wide index) of every record: points are stored span by span
+  for (int s = 0, k = 0; s < c->Nsp && k < m; ++s)
+    for (; k < off[s + 1] && k < m; ++k) out[25 * (size_t)k + 24] = (double)s;
   free(pts);
   free(tab);
   return BSC_OK;
@@ -441,6 +775,8 @@ bsc_status bsc_quadrature_tables(bsc_ctx* c, int which, double* out, int cap, in
 
 bsc_status bsc_set_profiling(bsc_ctx* c, int on) {
   if (!c) return BSC_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_profiling");
+  drop_graph(c);
   if (on && !c->profiling) {
     for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&c->ev[k]), "bsc_set_profiling");
     c->profiling = 1;

@@ -24,18 +24,73 @@ constexpr int H27 = 378;
 constexpr int MAXQ_MEM = 9;
 constexpr int MAXQ_BD = 4;
 
+// One patch of a context as the kernels see it.  A context holds one or
+// more patches; every per-control-point array is one set of planes over the
+// concatenated control points of all patches (patch p owns entries
+// [cp0, cp0 + N) of each plane) and every per-span array likewise over the
+// concatenated spans ([sp0, sp0 + Nsp)).  Within a patch the usual
+// tensor-product numbering holds: control point alpha = j nu + i, span
+// s = b Su + a.
+struct PatchDev {
+  int nu, nv, Su, Sv, N, Nsp, cp0, sp0;
+  double mu1, mu2, mush, mubd, rho, inv_dt2;
+  double grav[3];
+  double pad;
+};
+
+// Work item of the span kernels: patch p, and either a run of consecutive
+// spans starting at local span `first` (tu == 0) or a tu x (BLOCK / tu)
+// tile with origin (a0, b0).
+struct SpanItem {
+  int p, first_or_a0, tu, b0;
+};
+
+// Work item of the per-patch reductions: a chunk [lo, hi) of the patch's
+// spans (kind 0) or control points (kind 1), local indices.
+struct RedItem {
+  int p, kind, lo, hi;
+};
+
+// Block of the persistent PCG: its patch, its rank and the size of the
+// patch's block group, and the global index of the group's first block.
+struct PcgBlock {
+  int p, rank, size, first;
+};
+
+// Per-patch Newton state (device), one record per patch.
+struct PatchStep {
+  double E0, E1, alpha, dir_inf;
+  double pcg_iters, pcg_res, pcg_ok, spans_projected;
+  int state;       // 1 line search pending, 0 accepted, -1 no decrease, -2 aborted
+  int halvings;
+  int accepted_round;
+  int pad;
+};
+
+// Span-tile classes of the autotuner, by the patch's span count per row.
+constexpr int TILE_CLASSES = 4;
+__host__ __device__ __forceinline__ int tile_class_of(int Su) {
+  return Su < 32 ? 0 : (Su < 64 ? 1 : (Su < 128 ? 2 : 3));
+}
+
 struct bsc_ctx {
-  int nu, nv, Su, Sv, N, Nsp;
-  int precision;  // BSC_FP64 / BSC_FP32
-  size_t tsize;   // sizeof(T)
-  double mu_st1, mu_st2, mu_sh, mu_bd, rho;
+  int P;                 // patches
+  int nu, nv, Su, Sv;    // patch 0 (single-patch contexts)
+  int N, Nsp;            // totals over the patches
+  int precision;         // BSC_FP64 / BSC_FP32
+  size_t tsize;          // sizeof(T)
   int mem_rule, bend_rule;
-  double dt, gravity[3];
   int project_default;
   double pcg_tol;
   int pcg_max_iter, max_ls;
   cudaStream_t stream;
   int device, num_sms;
+
+  // patches
+  PatchDev* hpd;         // host copy [P]
+  PatchDev* pd;          // device [P]
+  int* cp_patch;         // [N] patch of every control point
+  int* sp_patch;         // [Nsp] patch of every span
 
   // quadrature tables
   int Nmem, Nbd;
@@ -49,7 +104,7 @@ struct bsc_ctx {
   double* mass;       // [N] FP64 lumped masses
   uint8_t* pinned;    // [N]
 
-  // projection buckets (reduced problem sizes 15, 21, 24)
+  // projection buckets (reduced problem sizes 15, 24, 24)
   int* bucket_list;   // [Nsp] span ids grouped by bucket
   int bucket_off[4];  // host: start of each bucket in bucket_list
   int* nneg;          // [Nsp] negative eigenvalues found per span (diagnostic)
@@ -57,9 +112,18 @@ struct bsc_ctx {
   double* proj_scratch[3];  // per-thread slots of the interior phase-2 kernel (cluster eigenvectors)
   double* proj_span;        // per-span scratch of the interior class
   int* proj_kneg;           // negative-eigenvalue count per interior span (class order)
-  unsigned int* proj_work;  // [3] work counters
-  cudaStream_t side[2];     // forked streams for the two small classes
+  unsigned int* proj_work;  // [4] work counters
+  cudaStream_t side[2];     // forked streams for the border class
   cudaEvent_t fork_ev, join_ev[2];
+
+  // span work items (tile shape per class chosen by the autotuner)
+  int tile_tu[TILE_CLASSES];  // 0 = runs of consecutive spans, else tile width
+  SpanItem* span_items;       // device
+  int n_span_items;
+  // reduction items, grouped by patch: patch p owns [red_off[p], red_off[p+1])
+  RedItem* red_items;         // device
+  int* red_off;               // device [P + 1]
+  int n_red_items;
 
   // span workspace
   double* E_span;     // [Nsp]
@@ -72,13 +136,35 @@ struct bsc_ctx {
   const void* K_last; // last assembled matrix (internal or caller's)
   void* Dinv;         // T [9][N] block-Jacobi preconditioner of K_last
   void* vec[8];       // T [3][N] work vectors: d, r, z, p, q, g, trial C, spare
-  double* partials;   // [4][max_grid] reduction partials
-  unsigned int* sync; // [4] grid barrier state, arrival counters
+  double* partials;   // [4][max(red_grid, pcg_grid, n_red_items)] reduction partials
+  unsigned int* sync; // [2 P + 2] grid-barrier state (count, generation) per patch group
   int* dstatus;       // device status flags (BSC_STATUS_*)
   double* dscalars;   // [16] device scalars
   double* hscalars;   // [16] pinned host scalars
-  int pcg_grid, pcg_block;
+  int pcg_grid;       // co-resident blocks of the persistent PCG
+  PcgBlock* pcg_blocks;  // device [pcg_grid]
+  double* pcg_out;    // device [3 P]: iterations, relative residual, ok
+  double* pcg_weight; // host [P]: work estimate of each patch's solve (autotuned)
   int red_grid;
+
+  // per-patch Newton state
+  PatchStep* steps;   // device [P]
+  PatchStep* hsteps;  // pinned host [P]
+  double* patch_E;    // device [2 P]: energy at C, energy at the trial point
+  int* pending;       // device [1]: patches whose line search is pending
+
+  int* hflags;        // pinned host [4]: pending line searches, status flags
+
+  // CUDA graph of one Newton iteration, for the pointers it was captured with
+  int use_graph;
+  cudaGraphExec_t graph;
+  const void *graph_C, *graph_Chat;
+  int graph_profiling;
+  int capturing;                     // enqueue_newton is being captured
+  unsigned long long graph_kernels;  // kernels per replay
+  long long graph_replays;
+  cudaStream_t gstream;              // the graph's stream
+  cudaEvent_t gev_in, gev_out;       // order gstream after / before the context's stream
 
   // profiling / diagnostics
   unsigned long long launches;  // kernels launched
@@ -95,19 +181,33 @@ struct bsc_ctx {
 // launchers (defined in the .cu files)
 // -------------------------------------------------------------------------
 cudaError_t launch_build_tables(bsc_ctx* c);
-cudaError_t launch_span_eval(bsc_ctx* c, const void* C, int want_grad, int want_hess);
+cudaError_t build_span_items(bsc_ctx* c);
+cudaError_t build_red_items(bsc_ctx* c);
+cudaError_t setup_span_eval(bsc_ctx* c);
+// energy / gradient / Hessian of every span; with a gate, only the spans of
+// the patches whose line search is pending (gate[p].state == 1)
+cudaError_t launch_span_eval(bsc_ctx* c, const void* C, int want_grad, int want_hess,
+                             const PatchStep* gate = nullptr);
+cudaError_t launch_span_eval_items(bsc_ctx* c, const void* C, int want_grad, int want_hess, const SpanItem* items,
+                                   int n_items, int block_tu);
 cudaError_t setup_projection(bsc_ctx* c);
 cudaError_t launch_project(bsc_ctx* c);
-cudaError_t launch_count_projected(bsc_ctx* c, double* dout);
 cudaError_t launch_assemble(bsc_ctx* c, void* K);
 cudaError_t launch_gradient(bsc_ctx* c, const void* C, const void* Chat, void* g);
-cudaError_t launch_energy(bsc_ctx* c, const void* C, const void* Chat, double* dE);
+// per-patch incremental potential into dE[p] (with a gate: pending patches only)
+cudaError_t launch_patch_energy(bsc_ctx* c, const void* C, const void* Chat, double* dE,
+                                const PatchStep* gate = nullptr);
 cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y);
 cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit);
+cudaError_t setup_pcg(bsc_ctx* c);
+cudaError_t assign_pcg_blocks(bsc_ctx* c);
 cudaError_t launch_axpy_trial(bsc_ctx* c, const void* C, const void* d, double alpha, void* out);
 cudaError_t launch_copy_vec(bsc_ctx* c, const void* src, void* dst);
-cudaError_t launch_absmax(bsc_ctx* c, const void* x, double* dout);
 cudaError_t launch_export_span_terms(bsc_ctx* c, void* g_out, void* H_out);
+// Newton step pieces (k_newton.cu)
+cudaError_t launch_step_begin(bsc_ctx* c, const void* d);
+cudaError_t launch_ls_round(bsc_ctx* c, const void* C, const void* Chat, const void* d, void* trial, void* Cout,
+                            int round);
 
 // -------------------------------------------------------------------------
 // device helpers
@@ -153,41 +253,51 @@ __device__ __forceinline__ double block_max(double v, double* sm) {
   return s;
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// wait is bounded: after ~2 s the barrier raises BSC_STATUS_TIMEOUT_FLAG in
-// *status and returns false; callers then leave their loops.
-__device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen,
-                                             int* status) {
+// Barrier over the `nblocks` co-resident blocks that share (count, gen): the
+// whole grid of a cooperative launch, or one patch's block group of the
+// persistent PCG.  The wait is bounded: after ~2 s the barrier raises
+// BSC_STATUS_TIMEOUT_FLAG in *status and returns false (so does every block
+// that sees the flag); callers then leave their loops.
+__device__ __forceinline__ bool group_barrier(unsigned int* count, volatile unsigned int* gen, int* status,
+                                              unsigned int nblocks) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned int g = *gen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(count, 1u);
-    if (arrived == gridDim.x - 1) {
-      *count = 0u;
+    if (nblocks > 1u) {
+      const unsigned int g = *gen;
       __threadfence();
-      atomicAdd((unsigned int*)gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == g) {
-        if (++spins > (1ll << 25)) {  // ~2 s of 64 ns sleeps
-          atomicOr(status, BSC_STATUS_TIMEOUT_FLAG);
-          ok = 0;
-          break;
+      const unsigned int arrived = atomicAdd(count, 1u);
+      if (arrived == nblocks - 1u) {
+        *count = 0u;
+        __threadfence();
+        atomicAdd((unsigned int*)gen, 1u);
+      } else {
+        long long spins = 0;
+        while (*gen == g) {
+          if (++spins > (1ll << 25)) {  // ~2 s of 64 ns sleeps
+            atomicOr(status, BSC_STATUS_TIMEOUT_FLAG);
+            ok = 0;
+            break;
+          }
+          if (*(volatile int*)status & BSC_STATUS_TIMEOUT_FLAG) {
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
         }
-        if (*(volatile int*)status & BSC_STATUS_TIMEOUT_FLAG) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
       }
+      __threadfence();
+    } else if (*(volatile int*)status & BSC_STATUS_TIMEOUT_FLAG) {
+      ok = 0;
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, int* status) {
+  return group_barrier(count, gen, status, gridDim.x);
 }
 
 #endif  // __CUDACC__

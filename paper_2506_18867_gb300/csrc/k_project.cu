@@ -36,7 +36,8 @@ namespace {
 template <typename T>
 struct ProjArgs {
   int Nsp, Nm, Nb;
-  double mubd;
+  const PatchDev* __restrict__ pd;     // bending stiffness of each patch
+  const int* __restrict__ sp_patch;    // patch of each span
   const int* __restrict__ moff;
   const int* __restrict__ boff;
   const T* __restrict__ tabm;
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(P1_BLOCK, 1)
   for (int t = blockIdx.x * P1_BLOCK + threadIdx.x; t < count; t += gridDim.x * P1_BLOCK) {
     const int s = list[t];
     const int q0 = P.moff[s], b0 = P.boff[s];
-    SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.Nm, P.Nb, P.moff[s + 1] - q0, P.boff[s + 1] - b0, P.mubd};
+    SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.Nm, P.Nb, P.moff[s + 1] - q0, P.boff[s + 1] - b0,
+                     P.pd[P.sp_patch[s]].mubd};
     const proj::View Qs{sspan + (size_t)SS::Q * count + t, count};
     double tn = 0.0;
     int kneg = proj::span_phase1<D>(tab, A, R, Qs, &tn, NEG_REL, RANK_REL);
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(P2_BLOCK)
 template <typename T>
 ProjArgs<T> proj_args(bsc_ctx* c) {
   ProjArgs<T> P;
-  P.Nsp = c->Nsp; P.Nm = c->Nmem; P.Nb = c->Nbd; P.mubd = c->mu_bd;
+  P.Nsp = c->Nsp; P.Nm = c->Nmem; P.Nb = c->Nbd; P.pd = c->pd; P.sp_patch = c->sp_patch;
   P.moff = c->mem_off; P.boff = c->bd_off;
   P.tabm = (const T*)c->tab_mem; P.tabb = (const T*)c->tab_bd;
   P.A = (const T*)c->A_mem; P.H = (T*)c->H_span;
@@ -315,9 +317,7 @@ cudaError_t run_all(bsc_ctx* c) {
   ProjArgs<T> P = proj_args<T>(c);
   if (count > 0) {
     BSC_COUNT(c, 1);
-    auto k1 = k_proj_p1<T, 5>;
-    if ((e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem())) != cudaSuccess)
-      return e;
+    auto k1 = k_proj_p1<T, 5>;  // its shared-memory opt-in is set once in setup_projection
     k1<<<c->proj_grid[0], P1_BLOCK, p1_smem(), c->stream>>>(P, list, count, c->proj_span, c->proj_kneg);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -338,26 +338,6 @@ cudaError_t run_all(bsc_ctx* c) {
   }
   if ((e = cudaEventRecord(c->join_ev[0], c->side[0])) != cudaSuccess) return e;
   return cudaStreamWaitEvent(c->stream, c->join_ev[0], 0);
-}
-
-// Number of spans with at least one projected eigenvalue (block counts, then
-// a fixed-order sum over blocks).
-template <int BLOCK>
-__global__ void k_count_projected(int Nsp, const int* __restrict__ nneg, double* __restrict__ partial) {
-  __shared__ double sm[BLOCK / 32];
-  double acc = 0.0;
-  for (int s = blockIdx.x * BLOCK + threadIdx.x; s < Nsp; s += gridDim.x * BLOCK) acc += nneg[s] > 0 ? 1.0 : 0.0;
-  const double tot = block_sum<BLOCK>(acc, sm);
-  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-template <int BLOCK>
-__global__ void k_sum_counts(int n, const double* __restrict__ partial, double* __restrict__ out) {
-  __shared__ double sm[BLOCK / 32];
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < n; k += BLOCK) acc += partial[k];
-  const double tot = block_sum<BLOCK>(acc, sm);
-  if (threadIdx.x == 0) *out = tot;
 }
 
 }  // namespace
@@ -408,13 +388,6 @@ cudaError_t setup_projection(bsc_ctx* c) {
     if ((e = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming)) != cudaSuccess) return e;
   }
   return cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
-}
-
-cudaError_t launch_count_projected(bsc_ctx* c, double* dout) {
-  BSC_COUNT(c, 2);
-  k_count_projected<256><<<c->red_grid, 256, 0, c->stream>>>(c->Nsp, c->nneg, c->partials + 2 * c->red_grid);
-  k_sum_counts<256><<<1, 256, 0, c->stream>>>(c->red_grid, c->partials + 2 * c->red_grid, dout);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_project(bsc_ctx* c) {

@@ -32,7 +32,8 @@ __constant__ double c_helmert[8][9];
 template <typename T>
 struct RingArgs {
   int Nsp, Nm, Nb;
-  double mubd;
+  const PatchDev* __restrict__ pd;     // bending stiffness of each patch
+  const int* __restrict__ sp_patch;    // patch of each span
   const int* __restrict__ moff;
   const int* __restrict__ boff;
   const T* __restrict__ tabm;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
     if (idx >= count) break;
     const int s = list[idx];
     const int q0 = P.moff[s], q1 = P.moff[s + 1], b0 = P.boff[s], b1 = P.boff[s + 1];
+    const double mubd = P.pd[P.sp_patch[s]].mubd;
 
     // ---- column lane of H_r = sum_q (G~ (x) I3) A_q (G~ (x) I3)^T + bending
     double col[RN];
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
       }
     }
     for (int q = b0; q < b1; ++q) {
-      const double WB = (double)P.tabb[q] * P.mubd;
+      const double WB = (double)P.tabb[q] * mubd;
       double Lt[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) Lt[k] = 0.0;
@@ -460,11 +462,11 @@ cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* 
   int g = ring_grid(c->num_sms);
   if (g > need) g = need;
   if (c->precision == BSC_FP64) {
-    RingArgs<double> P{c->Nsp, c->Nmem, c->Nbd, c->mu_bd, c->mem_off, c->bd_off, (const double*)c->tab_mem,
+    RingArgs<double> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const double*)c->tab_mem,
                        (const double*)c->tab_bd, (const double*)c->A_mem, (double*)c->H_span, c->nneg, c->dstatus};
     k_project_ring<double><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work);
   } else {
-    RingArgs<float> P{c->Nsp, c->Nmem, c->Nbd, c->mu_bd, c->mem_off, c->bd_off, (const float*)c->tab_mem,
+    RingArgs<float> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const float*)c->tab_mem,
                       (const float*)c->tab_bd, (const float*)c->A_mem, (float*)c->H_span, c->nneg, c->dstatus};
     k_project_ring<float><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work);
   }

@@ -5,18 +5,23 @@
 // (coalesced across threads) and the neighbours' x through the read-only path.
 //
 // PCG: 3x3 block-Jacobi preconditioned CG in a single persistent cooperative
-// kernel.  Every block owns a fixed slice of control points; the three
+// kernel.  The co-resident blocks are split into one group per patch (the
+// split weighted by each patch's expected work, bsc_plan_blocks); every group
+// runs its patch's CG on its own and leaves when that patch converges.  A
+// group's blocks own fixed slices of the patch's control points; the three
 // reductions per iteration (p.q, r.z, r.r) are FP64, summed per block in a
-// fixed tree and across blocks in block order, so every block computes the
-// same scalars and the result is bitwise reproducible.  Grid barriers are
-// bounded (they raise a timeout flag instead of waiting forever).
-#include <cooperative_groups.h>
+// fixed tree and across the group's blocks in block order, so every block of
+// the group computes the same scalars and the result is bitwise reproducible
+// for a given split.  Group barriers are bounded (they raise a timeout flag
+// instead of waiting forever).
+#include <vector>
 
 #include "bsc_internal.cuh"
 
 namespace {
 
-// Row alpha of y = K x in the element type T (FP32 bulk arithmetic in FP32 mode).
+// Row alpha (patch-local index) of y = K x in the element type T; K and x
+// already point at the patch's first control point, N is the plane stride.
 template <typename T>
 __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T* __restrict__ K,
                                          const T* __restrict__ x, T y[3]) {
@@ -42,12 +47,14 @@ __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T*
 }
 
 template <typename T>
-__global__ void k_spmv(int nu, int nv, const T* __restrict__ K, const T* __restrict__ x, T* __restrict__ y) {
-  const int N = nu * nv;
+__global__ void k_spmv(int N, const PatchDev* __restrict__ pd, const int* __restrict__ cp_patch,
+                       const T* __restrict__ K, const T* __restrict__ x, T* __restrict__ y) {
   const int al = blockIdx.x * blockDim.x + threadIdx.x;
   if (al >= N) return;
+  const PatchDev* pt = pd + cp_patch[al];
+  const int cp0 = __ldg(&pt->cp0);
   T acc[3];
-  spmv_row<T>(nu, nv, N, al, K, x, acc);
+  spmv_row<T>(__ldg(&pt->nu), __ldg(&pt->nv), N, al - cp0, K + cp0, x + cp0, acc);
   y[al] = acc[0];
   y[N + al] = acc[1];
   y[2 * N + al] = acc[2];
@@ -82,8 +89,11 @@ __global__ void k_block_jacobi(int N, const T* __restrict__ K, T* __restrict__ D
 
 template <typename T>
 struct PcgArgs {
-  int nu, nv, N, maxit;
+  int N, maxit;                       // N: plane stride of all vectors
   double tol;
+  const PatchDev* __restrict__ pd;    // nullptr: one nu x nv patch at control point 0
+  const PcgBlock* __restrict__ blocks;  // nullptr: one group of all blocks
+  int nu, nv;                         // the patch when pd == nullptr
   const T* __restrict__ K;
   const T* __restrict__ Dinv;
   const T* __restrict__ b;
@@ -93,15 +103,16 @@ struct PcgArgs {
   T* __restrict__ p;
   T* __restrict__ q;
   double* __restrict__ partial;  // [3][gridDim.x]
-  unsigned int* sync;
+  unsigned int* sync;            // [2 per patch]: barrier count, generation
   int* status;
-  double* out;                   // [0] iterations, [1] relative residual
+  double* out;                   // [3 per patch]: iterations, relative residual, ok
 };
 
+// Sum of part[0..n) in a fixed order (all threads get the result).
 template <int BLOCK>
-__device__ __forceinline__ double grid_sum(const double* part, int G, double* sm) {
+__device__ __forceinline__ double group_sum(const double* part, int n, double* sm) {
   double acc = 0.0;
-  for (int k = threadIdx.x; k < G; k += BLOCK) acc += part[k];
+  for (int k = threadIdx.x; k < n; k += BLOCK) acc += part[k];
   const double s = block_sum<BLOCK>(acc, sm);
   __shared__ double bcast;
   if (threadIdx.x == 0) bcast = s;
@@ -120,24 +131,47 @@ template <typename T, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
   __shared__ double sm[BLOCK / 32];
   const int G = gridDim.x, N = A.N;
-  const int tid = blockIdx.x * BLOCK + threadIdx.x, stride = G * BLOCK;
-  unsigned int* cnt = A.sync;
-  volatile unsigned int* gen = A.sync + 1;
+  int pp = 0, rank = blockIdx.x, gsize = G, gfirst = 0;
+  if (A.blocks) {
+    const PcgBlock bk = A.blocks[blockIdx.x];
+    pp = bk.p; rank = bk.rank; gsize = bk.size; gfirst = bk.first;
+  }
+  int nu = A.nu, nv = A.nv, cp0 = 0;
+  if (A.pd) {
+    nu = A.pd[pp].nu; nv = A.pd[pp].nv; cp0 = A.pd[pp].cp0;
+  }
+  const int Np = nu * nv;
+  const int tid = rank * BLOCK + threadIdx.x, stride = gsize * BLOCK;
+  unsigned int* cnt = A.sync + 2 * pp;
+  volatile unsigned int* gen = A.sync + 2 * pp + 1;
+  const unsigned int nb = (unsigned int)gsize;
+  // the patch's slice of every plane
+  const T* __restrict__ K = A.K + cp0;
+  const T* __restrict__ Dinv = A.Dinv + cp0;
+  const T* __restrict__ bv = A.b + cp0;
+  T* __restrict__ xv = A.x + cp0;
+  T* __restrict__ rv = A.r + cp0;
+  T* __restrict__ zv = A.z + cp0;
+  T* __restrict__ pv = A.p + cp0;
+  T* __restrict__ qv = A.q + cp0;
+  double* const part0 = A.partial + gfirst;
+  double* const part1 = A.partial + G + gfirst;
+  double* const part2 = A.partial + 2 * G + gfirst;
 
   double l_rz = 0.0, l_bb = 0.0;
-  for (int al = tid; al < N; al += stride) {
+  for (int al = tid; al < Np; al += stride) {
     T rr[3], zz[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      A.x[c * N + al] = T(0);
-      rr[c] = A.b[c * N + al];
-      A.r[c * N + al] = rr[c];
+      xv[c * N + al] = T(0);
+      rr[c] = bv[c * N + al];
+      rv[c * N + al] = rr[c];
     }
-    apply_dinv<T>(A.Dinv, N, al, rr, zz);
+    apply_dinv<T>(Dinv, N, al, rr, zz);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      A.z[c * N + al] = zz[c];
-      A.p[c * N + al] = zz[c];
+      zv[c * N + al] = zz[c];
+      pv[c * N + al] = zz[c];
       l_rz += (double)rr[c] * (double)zz[c];
       l_bb += (double)rr[c] * (double)rr[c];
     }
@@ -146,13 +180,13 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
     const double s1 = block_sum<BLOCK>(l_rz, sm);
     const double s2 = block_sum<BLOCK>(l_bb, sm);
     if (threadIdx.x == 0) {
-      A.partial[blockIdx.x] = s1;
-      A.partial[G + blockIdx.x] = s2;
+      part0[rank] = s1;
+      part1[rank] = s2;
     }
   }
-  if (!grid_barrier(cnt, gen, A.status)) return;
-  double rz = grid_sum<BLOCK>(A.partial, G, sm);
-  const double bb = grid_sum<BLOCK>(A.partial + G, G, sm);
+  if (!group_barrier(cnt, gen, A.status, nb)) return;
+  double rz = group_sum<BLOCK>(part0, gsize, sm);
+  const double bb = group_sum<BLOCK>(part1, gsize, sm);
   const double stop2 = A.tol * A.tol * bb;
   int it = 0;
   double rr_glob = bb;
@@ -160,41 +194,41 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
   if (bb > 0.0) {
     for (it = 1; it <= A.maxit; ++it) {
       double l_pq = 0.0;
-      for (int al = tid; al < N; al += stride) {
+      for (int al = tid; al < Np; al += stride) {
         T y[3];
-        spmv_row<T>(A.nu, A.nv, N, al, A.K, A.p, y);
+        spmv_row<T>(nu, nv, N, al, K, pv, y);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          A.q[c * N + al] = y[c];
-          l_pq += (double)A.p[c * N + al] * (double)y[c];
+          qv[c * N + al] = y[c];
+          l_pq += (double)pv[c * N + al] * (double)y[c];
         }
       }
       {
         const double s = block_sum<BLOCK>(l_pq, sm);
-        if (threadIdx.x == 0) A.partial[2 * G + blockIdx.x] = s;
+        if (threadIdx.x == 0) part2[rank] = s;
       }
-      if (!(ok = grid_barrier(cnt, gen, A.status))) break;
-      const double pq = grid_sum<BLOCK>(A.partial + 2 * G, G, sm);
+      if (!(ok = group_barrier(cnt, gen, A.status, nb))) break;
+      const double pq = group_sum<BLOCK>(part2, gsize, sm);
       if (!(pq > 0.0) || !isfinite(pq)) {
-        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(A.status, BSC_STATUS_NUMERIC_FLAG);
+        if (threadIdx.x == 0 && rank == 0) atomicOr(A.status, BSC_STATUS_NUMERIC_FLAG);
         ok = false;
         break;
       }
       const double alpha = rz / pq;
       const T ta = (T)alpha;
       double l_rz2 = 0.0, l_rr = 0.0;
-      for (int al = tid; al < N; al += stride) {
+      for (int al = tid; al < Np; al += stride) {
         T rr[3], zz[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          A.x[c * N + al] += ta * A.p[c * N + al];
-          rr[c] = A.r[c * N + al] - ta * A.q[c * N + al];
-          A.r[c * N + al] = rr[c];
+          xv[c * N + al] += ta * pv[c * N + al];
+          rr[c] = rv[c * N + al] - ta * qv[c * N + al];
+          rv[c * N + al] = rr[c];
         }
-        apply_dinv<T>(A.Dinv, N, al, rr, zz);
+        apply_dinv<T>(Dinv, N, al, rr, zz);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          A.z[c * N + al] = zz[c];
+          zv[c * N + al] = zz[c];
           l_rz2 += (double)rr[c] * (double)zz[c];
           l_rr += (double)rr[c] * (double)rr[c];
         }
@@ -203,27 +237,28 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
         const double s1 = block_sum<BLOCK>(l_rz2, sm);
         const double s2 = block_sum<BLOCK>(l_rr, sm);
         if (threadIdx.x == 0) {
-          A.partial[blockIdx.x] = s1;
-          A.partial[G + blockIdx.x] = s2;
+          part0[rank] = s1;
+          part1[rank] = s2;
         }
       }
-      if (!(ok = grid_barrier(cnt, gen, A.status))) break;
-      const double rz2 = grid_sum<BLOCK>(A.partial, G, sm);
-      rr_glob = grid_sum<BLOCK>(A.partial + G, G, sm);
+      if (!(ok = group_barrier(cnt, gen, A.status, nb))) break;
+      const double rz2 = group_sum<BLOCK>(part0, gsize, sm);
+      rr_glob = group_sum<BLOCK>(part1, gsize, sm);
       if (rr_glob <= stop2 || !isfinite(rr_glob)) break;
       const double beta = rz2 / rz;
       const T tb = (T)beta;
       rz = rz2;
-      for (int al = tid; al < N; al += stride)
+      for (int al = tid; al < Np; al += stride)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) A.p[c * N + al] = A.z[c * N + al] + tb * A.p[c * N + al];
-      if (!(ok = grid_barrier(cnt, gen, A.status))) break;
+        for (int c = 0; c < 3; ++c) pv[c * N + al] = zv[c * N + al] + tb * pv[c * N + al];
+      if (!(ok = group_barrier(cnt, gen, A.status, nb))) break;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    A.out[0] = (double)(it > A.maxit ? A.maxit : it);
-    A.out[1] = bb > 0.0 ? sqrt(rr_glob / bb) : 0.0;
-    A.out[2] = ok ? 1.0 : 0.0;
+  if (rank == 0 && threadIdx.x == 0) {
+    double* o = A.out + 3 * pp;
+    o[0] = (double)(it > A.maxit ? A.maxit : it);
+    o[1] = bb > 0.0 ? sqrt(rr_glob / bb) : 0.0;
+    o[2] = ok ? 1.0 : 0.0;
   }
 }
 
@@ -233,62 +268,123 @@ __global__ void k_axpy(int n, const T* __restrict__ a, const T* __restrict__ d, 
   if (k < n) out[k] = a[k] + (T)alpha * d[k];
 }
 
-template <typename T, int BLOCK>
-__global__ void k_absmax_partials(int n, const T* __restrict__ x, double* __restrict__ partial) {
-  __shared__ double sm[BLOCK / 32];
-  double m = 0.0;
-  for (int k = blockIdx.x * BLOCK + threadIdx.x; k < n; k += gridDim.x * BLOCK) m = fmax(m, fabs((double)x[k]));
-  const double r = block_max<BLOCK>(m, sm);
-  if (threadIdx.x == 0) partial[blockIdx.x] = r;
-}
+constexpr int PCG_BLOCK = 256;
 
-template <int BLOCK>
-__global__ void k_max_partials(int n, const double* __restrict__ partial, double* __restrict__ out) {
-  __shared__ double sm[BLOCK / 32];
-  double m = 0.0;
-  for (int k = threadIdx.x; k < n; k += BLOCK) m = fmax(m, partial[k]);
-  const double r = block_max<BLOCK>(m, sm);
-  if (threadIdx.x == 0) *out = r;
+// Cooperative launch (all blocks co-resident, which the group barriers
+// need) through the extended launch API, so that it can be captured in a
+// CUDA graph.
+template <typename T>
+cudaError_t launch_coop(int grid, PcgArgs<T> A, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(PCG_BLOCK);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg<T, PCG_BLOCK>, A);
 }
 
 template <typename T>
 cudaError_t pcg_t(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit) {
-  constexpr int B = 256;
   const int N = c->N;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->sync, 0, sizeof(unsigned int) * 2 * (size_t)c->P, c->stream)) != cudaSuccess) return e;
   k_block_jacobi<T><<<(N + 255) / 256, 256, 0, c->stream>>>(N, (const T*)K, (T*)c->Dinv, c->dstatus);
   PcgArgs<T> A;
-  A.nu = c->nu; A.nv = c->nv; A.N = N; A.maxit = maxit; A.tol = tol;
+  A.N = N; A.maxit = maxit; A.tol = tol;
+  A.pd = c->pd; A.blocks = c->pcg_blocks; A.nu = c->nu; A.nv = c->nv;
   A.K = (const T*)K; A.Dinv = (const T*)c->Dinv; A.b = (const T*)b; A.x = (T*)x;
   A.r = (T*)c->vec[1]; A.z = (T*)c->vec[2]; A.p = (T*)c->vec[3]; A.q = (T*)c->vec[4];
-  A.partial = c->partials; A.sync = c->sync; A.status = c->dstatus; A.out = c->dscalars + 8;
-  void* args[] = {&A};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg<T, B>, dim3(c->pcg_grid), dim3(B), args, 0, c->stream);
+  A.partial = c->partials; A.sync = c->sync; A.status = c->dstatus; A.out = c->pcg_out;
+  return launch_coop<T>(c->pcg_grid, A, c->stream);
 }
 
 }  // namespace
 
-// Grid size of the persistent PCG kernel: every block must be co-resident.
-int pcg_grid_size(int precision, int num_sms, int N) {
+// Splits `total` co-resident blocks over `count` patches: each patch gets at
+// least one block and at most ceil(n_cp / 256) (a block per 256 control
+// points keeps every thread busy); the rest go one at a time to the patch
+// with the largest work per block (ties to the lower index), which minimises
+// the largest work / blocks.  Returns the number of blocks handed out
+// (<= total), or -1 if total < count.
+extern "C" int bsc_plan_blocks(int count, const int* n_cp, const double* work, int total, int* blocks) {
+  if (count <= 0 || !n_cp || !work || !blocks || total < count) return -1;
+  int used = 0;
+  for (int p = 0; p < count; ++p) {
+    blocks[p] = 1;
+    ++used;
+  }
+  while (used < total) {
+    int best = -1;
+    double bw = -1.0;
+    for (int p = 0; p < count; ++p) {
+      const int cap = (n_cp[p] + PCG_BLOCK - 1) / PCG_BLOCK;
+      if (blocks[p] >= cap) continue;
+      const double w = work[p] / blocks[p];
+      if (w > bw) {
+        bw = w;
+        best = p;
+      }
+    }
+    if (best < 0) break;
+    ++blocks[best];
+    ++used;
+  }
+  return used;
+}
+
+// Grid of the persistent PCG: the co-resident capacity (at most two blocks
+// per SM), capped by what the patches can use; per-patch work estimates
+// start at the control-point counts.
+cudaError_t setup_pcg(bsc_ctx* c) {
   int per_sm = 0;
-  if (precision == BSC_FP64)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<double, 256>, 256, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<float, 256>, 256, 0);
+  cudaError_t e = c->precision == BSC_FP64
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<double, PCG_BLOCK>, PCG_BLOCK, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<float, PCG_BLOCK>, PCG_BLOCK, 0);
+  if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 2) per_sm = 2;
-  int g = num_sms * per_sm;
-  const int need = (N + 255) / 256;
-  if (g > need) g = need < 1 ? 1 : need;
-  return g;
+  const int cap = c->num_sms * per_sm;
+  if (c->P > cap) return cudaErrorInvalidConfiguration;
+  long long need = 0;
+  for (int p = 0; p < c->P; ++p) need += (c->hpd[p].N + PCG_BLOCK - 1) / PCG_BLOCK;
+  c->pcg_grid = (int)(need < cap ? need : cap);
+  c->pcg_weight = (double*)malloc(sizeof(double) * c->P);
+  if (!c->pcg_weight) return cudaErrorMemoryAllocation;
+  for (int p = 0; p < c->P; ++p) c->pcg_weight[p] = (double)c->hpd[p].N;
+  if ((e = cudaMalloc(&c->pcg_blocks, sizeof(PcgBlock) * c->pcg_grid)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->pcg_out, sizeof(double) * 3 * c->P)) != cudaSuccess) return e;
+  return assign_pcg_blocks(c);
+}
+
+// Block table of the persistent PCG from the current work estimates.
+cudaError_t assign_pcg_blocks(bsc_ctx* c) {
+  std::vector<int> ncp(c->P), nb(c->P);
+  for (int p = 0; p < c->P; ++p) ncp[p] = c->hpd[p].N;
+  const int used = bsc_plan_blocks(c->P, ncp.data(), c->pcg_weight, c->pcg_grid, nb.data());
+  if (used != c->pcg_grid) return cudaErrorInvalidConfiguration;
+  std::vector<PcgBlock> tab(c->pcg_grid);
+  int k = 0;
+  for (int p = 0; p < c->P; ++p) {
+    for (int r = 0; r < nb[p]; ++r) tab[k + r] = PcgBlock{p, r, nb[p], k};
+    k += nb[p];
+  }
+  cudaError_t e;
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+  return cudaMemcpy(c->pcg_blocks, tab.data(), sizeof(PcgBlock) * c->pcg_grid, cudaMemcpyHostToDevice);
 }
 
 cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y) {
   BSC_COUNT(c, 1);
   const int B = 256, G = (c->N + B - 1) / B;
   if (c->precision == BSC_FP64)
-    k_spmv<double><<<G, B, 0, c->stream>>>(c->nu, c->nv, (const double*)K, (const double*)x, (double*)y);
+    k_spmv<double><<<G, B, 0, c->stream>>>(c->N, c->pd, c->cp_patch, (const double*)K, (const double*)x, (double*)y);
   else
-    k_spmv<float><<<G, B, 0, c->stream>>>(c->nu, c->nv, (const float*)K, (const float*)x, (float*)y);
+    k_spmv<float><<<G, B, 0, c->stream>>>(c->N, c->pd, c->cp_patch, (const float*)K, (const float*)x, (float*)y);
   return cudaGetLastError();
 }
 
@@ -310,18 +406,6 @@ cudaError_t launch_axpy_trial(bsc_ctx* c, const void* C, const void* d, double a
 
 cudaError_t launch_copy_vec(bsc_ctx* c, const void* src, void* dst) {
   return cudaMemcpyAsync(dst, src, c->tsize * 3 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream);
-}
-
-cudaError_t launch_absmax(bsc_ctx* c, const void* x, double* dout) {
-  BSC_COUNT(c, 2);
-  constexpr int B = 256;
-  const int n = 3 * c->N, G = c->red_grid;
-  if (c->precision == BSC_FP64)
-    k_absmax_partials<double, B><<<G, B, 0, c->stream>>>(n, (const double*)x, c->partials);
-  else
-    k_absmax_partials<float, B><<<G, B, 0, c->stream>>>(n, (const float*)x, c->partials);
-  k_max_partials<B><<<1, B, 0, c->stream>>>(G, c->partials, dout);
-  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -351,7 +435,7 @@ void* g_static_ptr[64];  // device address of g_solve_scratch, per device
 template <typename T>
 cudaError_t static_solve_t(int nu, int nv, double* scratch, const void* K, const void* b, void* x, double tol,
                            int maxit, cudaStream_t st, int num_sms, double* out_host) {
-  constexpr int B = 256;
+  constexpr int B = PCG_BLOCK;
   const int N = nu * nv;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, B>, B, 0);
@@ -379,12 +463,12 @@ cudaError_t static_solve_t(int nu, int nv, double* scratch, const void* K, const
   k_block_jacobi<T><<<(N + 255) / 256, 256, 0, st>>>(N, (const T*)K, Dinv, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   PcgArgs<T> A;
-  A.nu = nu; A.nv = nv; A.N = N; A.maxit = maxit; A.tol = tol;
+  A.N = N; A.maxit = maxit; A.tol = tol;
+  A.pd = nullptr; A.blocks = nullptr; A.nu = nu; A.nv = nv;
   A.K = (const T*)K; A.Dinv = Dinv; A.b = (const T*)b; A.x = (T*)x;
   A.r = r; A.z = z; A.p = p; A.q = q;
   A.partial = partial; A.sync = sync; A.status = status; A.out = outd;
-  void* args[] = {&A};
-  e = cudaLaunchCooperativeKernel((const void*)k_pcg<T, B>, dim3(grid), dim3(B), args, 0, st);
+  e = launch_coop<T>(grid, A, st);
   if (e != cudaSuccess) return e;
   double stat_d = 0.0;
   if ((e = cudaMemcpyAsync(out_host, outd, 3 * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;

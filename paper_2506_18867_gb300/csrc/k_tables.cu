@@ -12,6 +12,8 @@
 // neighbouring addresses.
 #include <math.h>
 
+#include <vector>
+
 #include "bsc_internal.cuh"
 
 namespace {
@@ -114,7 +116,8 @@ __device__ int span_points(int a, int b, int Su, int Sv, int which, int rule, QP
   return n;
 }
 
-__global__ void k_count_points(int Su, int Sv, int mem_rule, int bend_rule, int* cm, int* cb) {
+__global__ void k_count_points(int Su, int Sv, int mem_rule, int bend_rule, int* __restrict__ cm,
+                               int* __restrict__ cb) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= Su * Sv) return;
   QP pts[9];
@@ -123,26 +126,28 @@ __global__ void k_count_points(int Su, int Sv, int mem_rule, int bend_rule, int*
 }
 
 // Rest-map geometry at (u, v) in span (a, b) and the per-point table rows.
+// One patch: nu x nv control points starting at cp0 in the rest planes
+// (stride Ntot), spans starting at sp0 in the offset arrays.
 template <typename T>
-__global__ void k_fill_points(int nu, int nv, const double* __restrict__ rest, int mem_rule,
-                              int bend_rule, double mu_bd, const int* __restrict__ moff,
+__global__ void k_fill_points(int nu, int nv, int cp0, int sp0, int Ntot, const double* __restrict__ rest,
+                              int mem_rule, int bend_rule, const int* __restrict__ moff,
                               const int* __restrict__ boff, int Nm, int Nb, T* __restrict__ tabm,
                               T* __restrict__ tabb, double* __restrict__ ptsm,
                               double* __restrict__ ptsb, int* __restrict__ status) {
-  const int Su = nu - 2, Sv = nv - 2, N = nu * nv;
+  const int Su = nu - 2, Sv = nv - 2;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= Su * Sv) return;
   const int a = s % Su, b = s / Su;
   double X[9][2];
   for (int l = 0; l < 9; ++l) {
-    const int al = (b + l / 3) * nu + a + l % 3;
+    const int al = cp0 + (b + l / 3) * nu + a + l % 3;
     X[l][0] = rest[al];
-    X[l][1] = rest[N + al];
+    X[l][1] = rest[Ntot + al];
   }
   for (int which = 0; which < 2; ++which) {
     QP pts[9];
     const int np = span_points(a, b, Su, Sv, which, which ? bend_rule : mem_rule, pts);
-    const int base = which ? boff[s] : moff[s];
+    const int base = which ? boff[sp0 + s] : moff[sp0 + s];
     for (int k = 0; k < np; ++k) {
       double Nu[3], Du[3], D2u[3], Nv[3], Dv[3], D2v[3];
       span_basis(pts[k].u, a, Su, Nu, Du, D2u);
@@ -203,7 +208,7 @@ __global__ void k_fill_points(int nu, int nv, const double* __restrict__ rest, i
 
 // Lumped mass m_alpha = rho * int N_alpha |det J| du dv, 3x3 Gauss per span,
 // gathered per control point over the (up to 3x3) spans of its support.
-__global__ void k_lumped_mass(int nu, int nv, const double* __restrict__ rest, double rho,
+__global__ void k_lumped_mass(int nu, int nv, int cp0, int Ntot, const double* __restrict__ rest, double rho,
                               double* __restrict__ m) {
   const int Su = nu - 2, Sv = nv - 2, N = nu * nv;
   const int al = blockIdx.x * blockDim.x + threadIdx.x;
@@ -218,9 +223,9 @@ __global__ void k_lumped_mass(int nu, int nv, const double* __restrict__ rest, d
       if (a < 0 || a >= Su) continue;
       double X[9][2];
       for (int l = 0; l < 9; ++l) {
-        const int bl = (b + l / 3) * nu + a + l % 3;
+        const int bl = cp0 + (b + l / 3) * nu + a + l % 3;
         X[l][0] = rest[bl];
-        X[l][1] = rest[N + bl];
+        X[l][1] = rest[Ntot + bl];
       }
       for (int qv = 0; qv < 3; ++qv)
         for (int qu = 0; qu < 3; ++qu) {
@@ -238,85 +243,97 @@ __global__ void k_lumped_mass(int nu, int nv, const double* __restrict__ rest, d
         }
     }
   }
-  m[al] = rho * acc;
+  m[cp0 + al] = rho * acc;
 }
 
 }  // namespace
 
-// Builds tables, offsets, masses and projection buckets.  Host work is the
-// integer bookkeeping (prefix sums of the per-span point counts and the
-// bucketing of spans by reduced problem size); the geometry runs on the GPU.
+// Builds tables, offsets, masses, projection buckets and the patch maps of
+// every patch.  Host work is the integer bookkeeping (prefix sums of the
+// per-span point counts over all patches, the bucketing of spans by reduced
+// problem size); the geometry runs on the GPU, one launch per patch.
 cudaError_t launch_build_tables(bsc_ctx* c) {
   cudaError_t e;
-  const int Nsp = c->Nsp, B = 128, G = (Nsp + B - 1) / B;
+  const int Nsp = c->Nsp, N = c->N, B = 128;
   int *cm = nullptr, *cb = nullptr;
   if ((e = cudaMalloc(&cm, sizeof(int) * Nsp)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&cb, sizeof(int) * Nsp)) != cudaSuccess) { cudaFree(cm); return e; }
-  BSC_COUNT(c, 3);
-  k_count_points<<<G, B, 0, c->stream>>>(c->Su, c->Sv, c->mem_rule, c->bend_rule, cm, cb);
-  int* hcm = (int*)malloc(sizeof(int) * Nsp);
-  int* hcb = (int*)malloc(sizeof(int) * Nsp);
-  int* hmo = (int*)malloc(sizeof(int) * (Nsp + 1));
-  int* hbo = (int*)malloc(sizeof(int) * (Nsp + 1));
-  int* hbl = (int*)malloc(sizeof(int) * Nsp);
-  e = cudaMemcpyAsync(hcm, cm, sizeof(int) * Nsp, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hcb, cb, sizeof(int) * Nsp, cudaMemcpyDeviceToHost, c->stream);
+  for (int p = 0; p < c->P; ++p) {
+    const PatchDev& q = c->hpd[p];
+    BSC_COUNT(c, 1);
+    k_count_points<<<(q.Nsp + B - 1) / B, B, 0, c->stream>>>(q.Su, q.Sv, c->mem_rule, c->bend_rule, cm + q.sp0,
+                                                            cb + q.sp0);
+  }
+  std::vector<int> hcm(Nsp), hcb(Nsp), hmo(Nsp + 1), hbo(Nsp + 1), hbl(Nsp), hsp(Nsp), hcp(N);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hcm.data(), cm, sizeof(int) * Nsp, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hcb.data(), cb, sizeof(int) * Nsp, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(cm);
   cudaFree(cb);
-  if (e != cudaSuccess) goto done;
-  {
-    hmo[0] = hbo[0] = 0;
-    for (int s = 0; s < Nsp; ++s) {
-      hmo[s + 1] = hmo[s] + hcm[s];
-      hbo[s + 1] = hbo[s] + hcb[s];
-    }
-    c->Nmem = hmo[Nsp];
-    c->Nbd = hbo[Nsp];
-    // bucket spans by the dimension of their reduced eigenproblem: the span
-    // Hessian's range lies in span{g_q,beta, L_q} (x) R^3, whose dimension is
-    // at most min(8, 2 n_mem + n_bd) per component (all vectors sum to zero).
-    int nb[3] = {0, 0, 0};
-    for (int s = 0; s < Nsp; ++s) {
-      const int m = 2 * hcm[s] + hcb[s];
-      nb[m <= 5 ? 0 : (m <= 7 ? 1 : 2)]++;
-    }
-    c->bucket_off[0] = 0;
-    c->bucket_off[1] = nb[0];
-    c->bucket_off[2] = nb[0] + nb[1];
-    c->bucket_off[3] = Nsp;
-    int pos[3] = {c->bucket_off[0], c->bucket_off[1], c->bucket_off[2]};
-    for (int s = 0; s < Nsp; ++s) {
-      const int m = 2 * hcm[s] + hcb[s];
-      hbl[pos[m <= 5 ? 0 : (m <= 7 ? 1 : 2)]++] = s;
-    }
-    const size_t ts = c->tsize;
-    if ((e = cudaMalloc(&c->mem_off, sizeof(int) * (Nsp + 1))) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&c->bd_off, sizeof(int) * (Nsp + 1))) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&c->bucket_list, sizeof(int) * Nsp)) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&c->tab_mem, ts * TABM * (size_t)c->Nmem)) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&c->tab_bd, ts * TABB * (size_t)c->Nbd)) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&c->pts_mem, sizeof(double) * 5 * (size_t)c->Nmem)) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&c->pts_bd, sizeof(double) * 5 * (size_t)c->Nbd)) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&c->A_mem, ts * AQ * (size_t)c->Nmem)) != cudaSuccess) goto done;
-    if ((e = cudaMemcpyAsync(c->mem_off, hmo, sizeof(int) * (Nsp + 1), cudaMemcpyHostToDevice, c->stream))) goto done;
-    if ((e = cudaMemcpyAsync(c->bd_off, hbo, sizeof(int) * (Nsp + 1), cudaMemcpyHostToDevice, c->stream))) goto done;
-    if ((e = cudaMemcpyAsync(c->bucket_list, hbl, sizeof(int) * Nsp, cudaMemcpyHostToDevice, c->stream))) goto done;
+  if (e != cudaSuccess) return e;
+  hmo[0] = hbo[0] = 0;
+  for (int s = 0; s < Nsp; ++s) {
+    hmo[s + 1] = hmo[s] + hcm[s];
+    hbo[s + 1] = hbo[s] + hcb[s];
+  }
+  c->Nmem = hmo[Nsp];
+  c->Nbd = hbo[Nsp];
+  // bucket spans by the dimension of their reduced eigenproblem: the span
+  // Hessian's range lies in span{g_q,beta, L_q} (x) R^3, whose dimension is
+  // at most min(8, 2 n_mem + n_bd) per component (all vectors sum to zero).
+  int nb[3] = {0, 0, 0};
+  for (int s = 0; s < Nsp; ++s) {
+    const int m = 2 * hcm[s] + hcb[s];
+    nb[m <= 5 ? 0 : (m <= 7 ? 1 : 2)]++;
+  }
+  c->bucket_off[0] = 0;
+  c->bucket_off[1] = nb[0];
+  c->bucket_off[2] = nb[0] + nb[1];
+  c->bucket_off[3] = Nsp;
+  int pos[3] = {c->bucket_off[0], c->bucket_off[1], c->bucket_off[2]};
+  for (int s = 0; s < Nsp; ++s) {
+    const int m = 2 * hcm[s] + hcb[s];
+    hbl[pos[m <= 5 ? 0 : (m <= 7 ? 1 : 2)]++] = s;
+  }
+  for (int p = 0; p < c->P; ++p) {
+    const PatchDev& q = c->hpd[p];
+    for (int k = 0; k < q.Nsp; ++k) hsp[q.sp0 + k] = p;
+    for (int k = 0; k < q.N; ++k) hcp[q.cp0 + k] = p;
+  }
+  const size_t ts = c->tsize;
+  if ((e = cudaMalloc(&c->mem_off, sizeof(int) * (Nsp + 1))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->bd_off, sizeof(int) * (Nsp + 1))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->bucket_list, sizeof(int) * Nsp)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->sp_patch, sizeof(int) * Nsp)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->cp_patch, sizeof(int) * N)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->tab_mem, ts * TABM * (size_t)c->Nmem)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->tab_bd, ts * TABB * (size_t)c->Nbd)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->pts_mem, sizeof(double) * 5 * (size_t)c->Nmem)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->pts_bd, sizeof(double) * 5 * (size_t)c->Nbd)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->A_mem, ts * AQ * (size_t)c->Nmem)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(c->mem_off, hmo.data(), sizeof(int) * (Nsp + 1), cudaMemcpyHostToDevice))) return e;
+  if ((e = cudaMemcpy(c->bd_off, hbo.data(), sizeof(int) * (Nsp + 1), cudaMemcpyHostToDevice))) return e;
+  if ((e = cudaMemcpy(c->bucket_list, hbl.data(), sizeof(int) * Nsp, cudaMemcpyHostToDevice))) return e;
+  if ((e = cudaMemcpy(c->sp_patch, hsp.data(), sizeof(int) * Nsp, cudaMemcpyHostToDevice))) return e;
+  if ((e = cudaMemcpy(c->cp_patch, hcp.data(), sizeof(int) * N, cudaMemcpyHostToDevice))) return e;
+  for (int p = 0; p < c->P; ++p) {
+    const PatchDev& q = c->hpd[p];
+    const int G = (q.Nsp + B - 1) / B;
+    BSC_COUNT(c, 2);
     if (c->precision == BSC_FP64)
-      k_fill_points<double><<<G, B, 0, c->stream>>>(c->nu, c->nv, c->rest, c->mem_rule, c->bend_rule, c->mu_bd,
-                                                      c->mem_off, c->bd_off, c->Nmem, c->Nbd,
+      k_fill_points<double><<<G, B, 0, c->stream>>>(q.nu, q.nv, q.cp0, q.sp0, N, c->rest, c->mem_rule,
+                                                      c->bend_rule, c->mem_off, c->bd_off, c->Nmem, c->Nbd,
                                                       (double*)c->tab_mem, (double*)c->tab_bd, c->pts_mem,
                                                       c->pts_bd, c->dstatus);
     else
-      k_fill_points<float><<<G, B, 0, c->stream>>>(c->nu, c->nv, c->rest, c->mem_rule, c->bend_rule, c->mu_bd,
-                                                     c->mem_off, c->bd_off, c->Nmem, c->Nbd,
+      k_fill_points<float><<<G, B, 0, c->stream>>>(q.nu, q.nv, q.cp0, q.sp0, N, c->rest, c->mem_rule,
+                                                     c->bend_rule, c->mem_off, c->bd_off, c->Nmem, c->Nbd,
                                                      (float*)c->tab_mem, (float*)c->tab_bd, c->pts_mem,
                                                      c->pts_bd, c->dstatus);
-    k_lumped_mass<<<(c->N + B - 1) / B, B, 0, c->stream>>>(c->nu, c->nv, c->rest, c->rho, c->mass);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    k_lumped_mass<<<(q.N + B - 1) / B, B, 0, c->stream>>>(q.nu, q.nv, q.cp0, N, c->rest, q.rho, c->mass);
   }
-done:
-  free(hcm); free(hcb); free(hmo); free(hbo); free(hbl);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return e;
 }

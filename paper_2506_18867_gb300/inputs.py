@@ -231,6 +231,33 @@ def config_random_small(seed: int, nu: int, nv: int, angle: float | None = None,
                  {"seed": seed, "span_m": span})
 
 
+def config_batch(seed: int = 1, count: int = 64, lo: int = 16, hi: int = 192, span_m: float = 0.01,
+                 sigma: float = 1e-3) -> list:
+    """Batched garments: `count` independent patches.  Per patch: nu and nv
+    independently uniform in [lo, hi] (non-square), E log-uniform in
+    [1e4, 1e6] Pa, Poisson ratio uniform in [0.2, 0.45], h = 1 mm,
+    200 kg/m^2, a rest map rotated by a uniform angle in the plane with 1 cm
+    spans, the drape's perturbation law (sigma = 1 mm per component), the two
+    top corners pinned, gravity -y, dt = 0.01 s."""
+    u = uniform(seed ^ 0xBA7C4, 5 * count)
+    out = []
+    for p in range(count):
+        up = u[5 * p:5 * p + 5]
+        nu = lo + min(int(up[0] * (hi - lo + 1)), hi - lo)
+        nv = lo + min(int(up[1] * (hi - lo + 1)), hi - lo)
+        E = math.exp(math.log(1e4) + up[2] * (math.log(1e6) - math.log(1e4)))
+        pr = 0.2 + 0.25 * up[3]
+        angle = 2.0 * math.pi * up[4]
+        rest = flat_rest(nu, nv, span_m * (nu - 2), span_m * (nv - 2), angle=angle)
+        C = lift(rest)
+        C += sigma * normal(seed * 7919 + 101 + p, C.size).reshape(C.shape)
+        mat = Material.from_engineering(E, pr, 1e-3, 200.0)
+        out.append(Patch(f"garment{p}_{nu}x{nv}", nu, nv, rest, C, C.copy(), mat, 0.01, (0.0, -9.81, 0.0),
+                         corner_pins_top(nu, nv), {"seed": seed, "index": p, "E": E, "poisson": pr,
+                                                   "angle": angle}))
+    return out
+
+
 def crop(patch: Patch, mu: int, mv: int | None = None) -> Patch:
     """The leading mu x mv control points of a patch (same span length, same
     state, pins restricted to the crop): a bounded sample of a large workload."""

@@ -70,6 +70,7 @@ def test_quadrature_tables(case, which):
     o = _sorted_records(np.concatenate([o_pts, o_tab], axis=1))
     assert g.shape[0] == o.shape[0]
     np.testing.assert_array_equal(g[:, 3:5], o[:, 3:5])          # owner spans, exact
+    np.testing.assert_array_equal(g[:, 24], g[:, 4] * (pat.nu - 2) + g[:, 3])  # context-wide span index
     np.testing.assert_allclose(g[:, 0:3], o[:, 0:3], rtol=0, atol=1e-14)
     np.testing.assert_allclose(g[:, 5], o[:, 5], rtol=1e-13)     # W = w |det J|
     ncol = 18 if which == 0 else 9

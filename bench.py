@@ -164,6 +164,26 @@ def dist_setup(args):
     return world, rank, local
 
 
+def reduce_over_ranks(dist, times_ms, spans, device):
+    """Weak scaling across ranks: every rank steps its own workload, so the
+    job's time is the slowest rank's (max of every time) and its work the sum
+    of the ranks' spans.  No data-path collective: only these scalars."""
+    import torch
+    out = dict(times_ms)
+    out["spans"] = spans
+    if dist is None:
+        return out
+    keys = sorted(times_ms)
+    t = torch.tensor([float(times_ms[k]) for k in keys], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(spans)], dtype=torch.float64, device=device)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    for k, v in zip(keys, t.tolist()):
+        out[k] = v
+    out["spans"] = int(n.item())
+    return out
+
+
 def make_context(bsc, pats, prec):
     if len(pats) == 1:
         return bsc.context_for_patch(pats[0], precision=prec, pcg_rel_tol=1e-8)
@@ -285,16 +305,9 @@ def run_gpu(args):
     e2e_step = sum(e2e_ms) / len(e2e_ms)
     tsz = 4 if prec == bsc.FP32 else 8
 
-    # aggregate over ranks (max of times, sum of work)
-    def allmax(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    eval_ms_max, ms_step_max, e2e_max = allmax(eval_ms), allmax(ms_step), allmax(e2e_step)
-    total_spans = Nsp * world
+    agg = reduce_over_ranks(dist, {"eval": eval_ms, "step": ms_step, "e2e": e2e_step}, Nsp, "cuda")
+    eval_ms_max, ms_step_max, e2e_max = agg["eval"], agg["step"], agg["e2e"]
+    total_spans = agg["spans"]
     value = total_spans / (eval_ms_max * 1e-3)
 
     fp64 = None

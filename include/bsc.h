@@ -226,7 +226,9 @@ bsc_status bsc_patch_energies(bsc_ctx* ctx, const void* C_dev, const void* Chat_
  * one tile width per patch-size class (class k: spans per row < 32, < 64,
  * < 128, >= 128); width 0 means runs.  bsc_autotune times the Hessian
  * evaluation of each class present for each candidate width {0, 8, 16, 32}
- * (CUDA events, best of 3) and keeps the fastest, then assembles K at C,
+ * (CUDA events, best of 3) and keeps the fastest, times the SPD projection
+ * of the border spans (at or next to a patch border) by its two paths and
+ * keeps the faster, then assembles K at C,
  * runs one PCG solve per patch to measure its iteration count, and splits
  * the PCG's co-resident blocks in proportion to control points x
  * iterations (bsc_plan_blocks).  C is not modified.  The choices change
@@ -237,11 +239,18 @@ typedef struct bsc_tuning {
   int tile_tu[4];          /* chosen width per class (-1: class absent) */
   double tile_ms[4][4];    /* measured ms per class x candidate {0, 8, 16, 32} */
   int pcg_grid;            /* co-resident blocks of the persistent PCG */
+  int border_path;         /* SPD projection of the border spans: 0 one warp per
+                              span, 1 one thread per span (chosen by time) */
+  double border_ms[2];     /* measured ms of the border projection per path */
 } bsc_tuning;
 bsc_status bsc_autotune(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, bsc_tuning* out);
 
 /* Set the tile widths by hand (4 entries, each 0, 8, 16 or 32). */
 bsc_status bsc_set_tiles(bsc_ctx* ctx, const int* tile_tu);
+
+/* Set the border projection path by hand (0 one warp per span, 1 one thread
+ * per span); both compute the same projection up to rounding. */
+bsc_status bsc_set_border_path(bsc_ctx* ctx, int path);
 
 /* Current split of the PCG's blocks (host array of count ints). */
 bsc_status bsc_pcg_split(const bsc_ctx* ctx, int* blocks_per_patch);

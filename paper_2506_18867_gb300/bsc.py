@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5:
 EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc_energy", "bsc_gradient",
            "bsc_assemble_hessian", "bsc_spmv", "bsc_solve", "bsc_newton_step", "bsc_create_batch",
            "bsc_batch_layout", "bsc_patch_reports", "bsc_patch_energies", "bsc_autotune", "bsc_set_tiles",
+           "bsc_set_border_path",
            "bsc_pcg_split", "bsc_plan_blocks", "bsc_set_graph", "bsc_graph_state", "bsc_span_terms",
            "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes", "bsc_set_profiling", "bsc_phase_times",
            "bsc_launch_count", "bsc_projection_stats", "bsc_solve_static")
@@ -68,11 +69,12 @@ class NewtonReport(ct.Structure):
 
 
 class Tuning(ct.Structure):
-    _fields_ = [("tile_tu", ct.c_int * 4), ("tile_ms", (ct.c_double * 4) * 4), ("pcg_grid", ct.c_int)]
+    _fields_ = [("tile_tu", ct.c_int * 4), ("tile_ms", (ct.c_double * 4) * 4), ("pcg_grid", ct.c_int),
+                ("border_path", ct.c_int), ("border_ms", ct.c_double * 2)]
 
     def as_dict(self):
         return {"tile_tu": list(self.tile_tu), "tile_ms": [list(r) for r in self.tile_ms],
-                "pcg_grid": self.pcg_grid}
+                "pcg_grid": self.pcg_grid, "border_path": self.border_path, "border_ms": list(self.border_ms)}
 
 
 class BscError(RuntimeError):
@@ -125,6 +127,7 @@ def load(path: str = LIB_PATH):
     lib.bsc_autotune.argtypes = [P, V, V, ct.POINTER(Tuning)]
     lib.bsc_set_tiles.argtypes = [P, ct.POINTER(I)]
     lib.bsc_pcg_split.argtypes = [P, ct.POINTER(I)]
+    lib.bsc_set_border_path.argtypes = [P, I]
     lib.bsc_plan_blocks.argtypes = [I, ct.POINTER(I), ct.POINTER(D), I, ct.POINTER(I)]
     lib.bsc_set_graph.argtypes = [P, I]
     lib.bsc_graph_state.argtypes = [P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(ct.c_longlong)]
@@ -357,6 +360,9 @@ class Context:
     def set_tiles(self, tiles):
         arr = (ct.c_int * 4)(*[int(t) for t in tiles])
         self._check(self._lib.bsc_set_tiles(self._h, arr))
+
+    def set_border_path(self, path):
+        self._check(self._lib.bsc_set_border_path(self._h, int(path)))
 
     def pcg_split(self):
         out = (ct.c_int * self.P)()

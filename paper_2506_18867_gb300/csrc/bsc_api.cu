@@ -67,7 +67,7 @@ void free_ctx(bsc_ctx* c) {
                   c->pinned, c->bucket_list, c->nneg, c->E_span, c->g_span, c->H_span, c->A_mem, c->K_int,
                   c->Dinv, c->partials, c->sync, c->dstatus, c->dscalars, c->pd, c->cp_patch, c->sp_patch,
                   c->span_items, c->red_items, c->red_off, c->pcg_blocks, c->pcg_out, c->steps, c->patch_E,
-                  c->pending, c->proj_work, c->proj_span, c->proj_kneg};
+                  c->pending, c->proj_work, c->proj_span[0], c->proj_span[1], c->proj_kneg[0], c->proj_kneg[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->vec)
@@ -642,6 +642,15 @@ bsc_status bsc_set_tiles(bsc_ctx* c, const int* tu) {
   return BSC_OK;
 }
 
+bsc_status bsc_set_border_path(bsc_ctx* c, int path) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (path != 0 && path != 1) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_border_path: path must be 0 or 1");
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_border_path");
+  c->border_path = path;
+  drop_graph(c);
+  return BSC_OK;
+}
+
 bsc_status bsc_pcg_split(const bsc_ctx* c, int* blocks) {
   if (!c || !blocks) return BSC_ERR_INVALID_ARG;
   std::vector<PcgBlock> tab(c->pcg_grid);
@@ -699,6 +708,24 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
     }
     if (t.tile_tu[cls] >= 0) c->tile_tu[cls] = t.tile_tu[cls];
   }
+  // border projection path: time both on freshly evaluated span Hessians
+  for (int path = 0; path < 2 && st == BSC_OK; ++path) {
+    float best_rep = 1e30f, ms = 0.0f;
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      e = launch_span_eval(c, C, 1, 1);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      if (e == cudaSuccess) e = launch_project_border(c, path);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < best_rep) best_rep = ms;
+    }
+    if (e != cudaSuccess) st = cuda_fail(c, e, "bsc_autotune: timing the border projection");
+    t.border_ms[path] = best_rep;
+  }
+  if (st == BSC_OK) c->border_path = t.border_ms[1] < t.border_ms[0] ? 1 : 0;
+  t.border_path = c->border_path;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != BSC_OK) return st;

@@ -104,16 +104,19 @@ struct bsc_ctx {
   double* mass;       // [N] FP64 lumped masses
   uint8_t* pinned;    // [N]
 
-  // projection buckets (reduced problem sizes 15, 24, 24)
+  // projection buckets by the number of derivative vectors m = 2 n_mem + n_bd:
+  // m <= 5, 6..7, >= 8 (reduced problem sizes 15, 24, 24)
   int* bucket_list;   // [Nsp] span ids grouped by bucket
   int bucket_off[4];  // host: start of each bucket in bucket_list
   int* nneg;          // [Nsp] negative eigenvalues found per span (diagnostic)
-  int proj_grid[3];   // resident grid per class
-  double* proj_scratch[3];  // per-thread slots of the interior phase-2 kernel (cluster eigenvectors)
-  double* proj_span;        // per-span scratch of the interior class
-  int* proj_kneg;           // negative-eigenvalue count per interior span (class order)
+  // two span classes: 0 interior (reduced size 15), 1 at or next to the border (24)
+  int proj_grid[2][2];      // resident grid per class and phase
+  double* proj_scratch[2];  // per-thread slots of the phase-2 kernels (cluster eigenvectors)
+  double* proj_span[2];     // per-span scratch of each class
+  int* proj_kneg[2];        // negative-eigenvalue count per span (class order)
   unsigned int* proj_work;  // [4] work counters
-  cudaStream_t side[2];     // forked streams for the border class
+  int border_path;          // 0: one warp per border span, 1: one thread per border span
+  cudaStream_t side[2];     // forked stream of the border class
   cudaEvent_t fork_ev, join_ev[2];
 
   // span work items (tile shape per class chosen by the autotuner)
@@ -192,6 +195,8 @@ cudaError_t launch_span_eval_items(bsc_ctx* c, const void* C, int want_grad, int
                                    int n_items, int block_tu);
 cudaError_t setup_projection(bsc_ctx* c);
 cudaError_t launch_project(bsc_ctx* c);
+// the border class alone by the given path, on the context's stream (autotuner)
+cudaError_t launch_project_border(bsc_ctx* c, int path);
 cudaError_t launch_assemble(bsc_ctx* c, void* K);
 cudaError_t launch_gradient(bsc_ctx* c, const void* C, const void* Chat, void* g);
 // per-patch incremental potential into dE[p] (with a gate: pending patches only)

@@ -31,6 +31,7 @@
 cudaError_t setup_projection_ring();
 cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* work, cudaStream_t st);
 
+
 namespace {
 
 template <typename T>
@@ -117,7 +118,11 @@ struct SpanScratch {
 // to about eps / gap.
 constexpr double CLUSTER_GAP = 1e-3;
 
-constexpr int P1_BLOCK = 160;  // five warps; packed H_r and R in shared memory
+// Threads per block of phase 1 (packed H_r and R of every thread in shared
+// memory: 8 x (NP + 3 n) bytes each) and of phase 2.
+template <int D> struct P1Block;
+template <> struct P1Block<5> { static constexpr int value = 160; };  // 211 KB of shared memory
+template <> struct P1Block<8> { static constexpr int value = 64; };   // 190 KB
 constexpr int P2_BLOCK = 128;
 
 // Strided view of element type T over the scratch (w vectors, lam w).
@@ -130,13 +135,12 @@ struct TView {
 };
 
 // H -= sum_r lam_r w_r w_r^T for one span in one pass over its 378 packed
-// entries, in the element type (w_r already in T in the scratch).  An
-// interior span has at most n = 15 negative eigenvalues; the unrolled,
+// entries, in the element type (w_r already in T in the scratch).  A span
+// has at most RMAX = n negative eigenvalues; the unrolled,
 // predicated loops keep lam_r and lam_r w_r[a] of the current row in
 // registers, so only w_r[c] is read per entry.
-template <typename T>
+template <typename T, int RMAX>
 __device__ __noinline__ void apply_corrections(T* H, int Nsp, int s, proj::View Lam, TView<T> Ws, int kneg) {
-  constexpr int RMAX = 15;
   T lam[RMAX];
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) lam[r] = r < kneg ? (T)Lam[r] : T(0);
@@ -160,15 +164,15 @@ __device__ __noinline__ void apply_corrections(T* H, int Nsp, int s, proj::View 
 
 // Phase 1: one thread per interior span (uniform work, no barriers).
 template <typename T, int D>
-__global__ void __launch_bounds__(P1_BLOCK, 1)
+__global__ void __launch_bounds__(P1Block<D>::value, 1)
     k_proj_p1(ProjArgs<T> P, const int* __restrict__ list, int count, double* __restrict__ sspan,
               int* __restrict__ kneg_out) {
-  constexpr int n = 3 * D, NP = n * (n + 1) / 2;
+  constexpr int n = 3 * D, NP = n * (n + 1) / 2, B1 = P1Block<D>::value;
   using SS = SpanScratch<D>;
   extern __shared__ __align__(16) double smd[];
-  const proj::View A{smd + threadIdx.x, P1_BLOCK};
-  const proj::View R{smd + (size_t)NP * P1_BLOCK + threadIdx.x, P1_BLOCK};
-  for (int t = blockIdx.x * P1_BLOCK + threadIdx.x; t < count; t += gridDim.x * P1_BLOCK) {
+  const proj::View A{smd + threadIdx.x, B1};
+  const proj::View R{smd + (size_t)NP * B1 + threadIdx.x, B1};
+  for (int t = blockIdx.x * B1 + threadIdx.x; t < count; t += gridDim.x * B1) {
     const int s = list[t];
     const int q0 = P.moff[s], b0 = P.boff[s];
     SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.Nm, P.Nb, P.moff[s + 1] - q0, P.boff[s + 1] - b0,
@@ -290,7 +294,7 @@ __global__ void __launch_bounds__(P2_BLOCK)
     }
     __syncthreads();
     // (c) the owner applies the rank-k correction to its span
-    if (kneg > 0) apply_corrections<T>(P.H, P.Nsp, list[t], sv(t, SS::LAM), wv(t), kneg);
+    if (kneg > 0) apply_corrections<T, n>(P.H, P.Nsp, list[t], sv(t, SS::LAM), wv(t), kneg);
     __syncthreads();
   }
 }
@@ -306,83 +310,115 @@ ProjArgs<T> proj_args(bsc_ctx* c) {
   return P;
 }
 
-constexpr size_t p1_smem() { return sizeof(double) * (size_t)(Smem<5>::NP + 15 * 3) * P1_BLOCK; }
-constexpr size_t p2_smem() { return sizeof(double) * (size_t)(4 * 15) * P2_BLOCK; }
+template <int D>
+constexpr size_t p1_smem() { return sizeof(double) * (size_t)(Smem<D>::NP + 3 * Smem<D>::n) * P1Block<D>::value; }
+template <int D>
+constexpr size_t p2_smem() { return sizeof(double) * (size_t)(4 * 3 * D) * P2_BLOCK; }
 
+// Class k of the span lists: 0 = interior spans (five derivative vectors,
+// D = 5), 1 = spans at or next to the border (D = 8).  Phase 1 and phase 2
+// can be issued separately (phase < 0: both).
+template <typename T, int D>
+cudaError_t run_class(bsc_ctx* c, int k, const int* list, int count, cudaStream_t st, int phase = -1) {
+  if (count <= 0) return cudaSuccess;
+  cudaError_t e;
+  ProjArgs<T> P = proj_args<T>(c);
+  if (phase != 1) {
+    BSC_COUNT(c, 1);
+    k_proj_p1<T, D><<<c->proj_grid[k][0], P1Block<D>::value, p1_smem<D>(), st>>>(P, list, count,
+                                                                                   c->proj_span[k], c->proj_kneg[k]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (phase != 0) {
+    BSC_COUNT(c, 1);
+    if ((e = cudaMemsetAsync(c->proj_work + k, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+    k_proj_p2<T, D><<<c->proj_grid[k][1], P2_BLOCK, p2_smem<D>(), st>>>(P, list, count, c->proj_kneg[k],
+                                                                        c->proj_span[k], c->proj_scratch[k],
+                                                                        c->proj_work + k);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// The border class by either path: 0 = one warp per span (k_project_ring,
+// lowest latency per span: best when there are few border spans), 1 = one
+// thread per span through the two phase kernels with D = 8 (highest
+// throughput: best when there are many).
+template <typename T>
+cudaError_t run_border(bsc_ctx* c, int path, cudaStream_t st) {
+  const int first = c->bucket_off[1], count = c->bucket_off[3] - c->bucket_off[1];
+  if (path == 0) return launch_project_ring(c, first, count, c->proj_work + 2, st);
+  return run_class<T, 8>(c, 1, c->bucket_list + first, count, st);
+}
+
+// Both classes.  Phase 1 of the interior class runs alone (one block of
+// 211 KB of shared memory per SM leaves no room for other blocks); then the
+// border class runs on a forked stream next to the interior phase 2.
 template <typename T>
 cudaError_t run_all(bsc_ctx* c) {
   cudaError_t e;
-  const int count = c->bucket_off[1] - c->bucket_off[0];
-  const int* list = c->bucket_list + c->bucket_off[0];
-  ProjArgs<T> P = proj_args<T>(c);
-  if (count > 0) {
-    BSC_COUNT(c, 1);
-    auto k1 = k_proj_p1<T, 5>;  // its shared-memory opt-in is set once in setup_projection
-    k1<<<c->proj_grid[0], P1_BLOCK, p1_smem(), c->stream>>>(P, list, count, c->proj_span, c->proj_kneg);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  // fork: the border classes (warp-per-span kernel) on a side stream next to
-  // phase 2, whose blocks leave room for them on every SM
+  const int* list0 = c->bucket_list + c->bucket_off[0];
+  const int n0 = c->bucket_off[1] - c->bucket_off[0];
+  if ((e = run_class<T, 5>(c, 0, list0, n0, c->stream, 0)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->fork_ev, c->stream)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(c->side[0], c->fork_ev, 0)) != cudaSuccess) return e;
-  if ((e = launch_project_ring(c, c->bucket_off[1], c->bucket_off[3] - c->bucket_off[1], c->proj_work + 1,
-                               c->side[0])) != cudaSuccess)
-    return e;
-  if (count > 0) {
-    BSC_COUNT(c, 1);
-    if ((e = cudaMemsetAsync(c->proj_work, 0, sizeof(unsigned int), c->stream)) != cudaSuccess) return e;
-    k_proj_p2<T, 5><<<c->proj_grid[1], P2_BLOCK, p2_smem(), c->stream>>>(P, list, count, c->proj_kneg,
-                                                                          c->proj_span, c->proj_scratch[0],
-                                                                          c->proj_work);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  if ((e = run_border<T>(c, c->border_path, c->side[0])) != cudaSuccess) return e;
+  if ((e = run_class<T, 5>(c, 0, list0, n0, c->stream, 1)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->join_ev[0], c->side[0])) != cudaSuccess) return e;
   return cudaStreamWaitEvent(c->stream, c->join_ev[0], 0);
 }
 
-}  // namespace
-
-// Sizes the interior kernels' grids and scratch and loads the border
-// kernel's constants (called from bsc_create).
-cudaError_t setup_projection(bsc_ctx* c) {
-  const int count = c->bucket_off[1] - c->bucket_off[0];
-  int per1 = 0, per2 = 0;
+template <typename T, int D>
+cudaError_t setup_class(bsc_ctx* c, int k, int count) {
   cudaError_t e;
-  if (c->precision == BSC_FP64) {
-    if ((e = cudaFuncSetAttribute(k_proj_p1<double, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)p1_smem())) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(k_proj_p2<double, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)p2_smem())) != cudaSuccess)
-      return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_proj_p1<double, 5>, P1_BLOCK, p1_smem());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<double, 5>, P2_BLOCK, p2_smem());
-  } else {
-    if ((e = cudaFuncSetAttribute(k_proj_p1<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)p1_smem())) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(k_proj_p2<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)p2_smem())) != cudaSuccess)
-      return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_proj_p1<float, 5>, P1_BLOCK, p1_smem());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<float, 5>, P2_BLOCK, p2_smem());
-  }
+  if ((e = cudaFuncSetAttribute(k_proj_p1<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)p1_smem<D>())) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_proj_p2<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)p2_smem<D>())) != cudaSuccess)
+    return e;
+  int per1 = 0, per2 = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_proj_p1<T, D>, P1Block<D>::value,
+                                                         p1_smem<D>())) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<T, D>, P2_BLOCK, p2_smem<D>())) !=
+      cudaSuccess)
+    return e;
   per1 = per1 < 1 ? 1 : per1;
   per2 = per2 < 1 ? 1 : per2;
   int g1 = per1 * c->num_sms, g2 = per2 * c->num_sms;
-  const int need1 = (count + P1_BLOCK - 1) / P1_BLOCK, need2 = (count + P2_BLOCK - 1) / P2_BLOCK;
+  const int need1 = (count + P1Block<D>::value - 1) / P1Block<D>::value, need2 = (count + P2_BLOCK - 1) / P2_BLOCK;
   if (g1 > need1) g1 = need1;
   if (g2 > need2) g2 = need2;
-  c->proj_grid[0] = g1 < 1 ? 1 : g1;
-  c->proj_grid[1] = g2 < 1 ? 1 : g2;
+  c->proj_grid[k][0] = g1 < 1 ? 1 : g1;
+  c->proj_grid[k][1] = g2 < 1 ? 1 : g2;
   const size_t cnt = count > 0 ? (size_t)count : 1;
-  if ((e = cudaMalloc(&c->proj_span, sizeof(double) * SpanScratch<5>::SIZE * cnt)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&c->proj_kneg, sizeof(int) * cnt)) != cudaSuccess) return e;
-  const size_t slots = (size_t)c->proj_grid[1] * P2_BLOCK;
-  if ((e = cudaMalloc(&c->proj_scratch[0], sizeof(double) * 15 * 15 * slots)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->proj_span[k], sizeof(double) * SpanScratch<D>::SIZE * cnt)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->proj_kneg[k], sizeof(int) * cnt)) != cudaSuccess) return e;
+  const size_t slots = (size_t)c->proj_grid[k][1] * P2_BLOCK;
+  constexpr int n = 3 * D;
+  return cudaMalloc(&c->proj_scratch[k], sizeof(double) * n * n * slots);
+}
+
+}  // namespace
+
+// Sizes both classes' grids and scratch and creates the side stream
+// (called from bsc_create).
+cudaError_t setup_projection(bsc_ctx* c) {
+  cudaError_t e;
+  const int n0 = c->bucket_off[1] - c->bucket_off[0], n1 = c->bucket_off[3] - c->bucket_off[1];
+  if (c->precision == BSC_FP64) {
+    if ((e = setup_class<double, 5>(c, 0, n0)) != cudaSuccess) return e;
+    if ((e = setup_class<double, 8>(c, 1, n1)) != cudaSuccess) return e;
+  } else {
+    if ((e = setup_class<float, 5>(c, 0, n0)) != cudaSuccess) return e;
+    if ((e = setup_class<float, 8>(c, 1, n1)) != cudaSuccess) return e;
+  }
   if ((e = setup_projection_ring()) != cudaSuccess) return e;
-  e = cudaMalloc(&c->proj_work, sizeof(unsigned int) * 4);
-  if (e != cudaSuccess) return e;
+  // before the autotuner has timed both border paths: warp per span while
+  // the border spans fill the resident warps a few times over at most
+  c->border_path = n1 > 8 * 8 * c->num_sms ? 1 : 0;
+  if ((e = cudaMalloc(&c->proj_work, sizeof(unsigned int) * 4)) != cudaSuccess) return e;
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
     if ((e = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming)) != cudaSuccess) return e;
@@ -393,4 +429,9 @@ cudaError_t setup_projection(bsc_ctx* c) {
 cudaError_t launch_project(bsc_ctx* c) {
   if (c->precision == BSC_FP64) return run_all<double>(c);
   return run_all<float>(c);
+}
+
+cudaError_t launch_project_border(bsc_ctx* c, int path) {
+  if (c->precision == BSC_FP64) return run_border<double>(c, path, c->stream);
+  return run_border<float>(c, path, c->stream);
 }

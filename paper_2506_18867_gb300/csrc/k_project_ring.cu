@@ -1,6 +1,10 @@
 // K3 for the spans at and next to the patch border (more than five
 // derivative vectors: the boundary spans with their 3x3 / 3x2 Gauss rules
-// and the interior spans that own extra knot-line points).
+// and the interior spans that own extra knot-line points), one warp per
+// span: the low-latency path for contexts with few border spans (a large
+// single patch); with many (a batch of small patches) the thread-per-span
+// phase kernels with D = 8 have the higher throughput, and the autotuner
+// picks between the two by timing.
 //
 // Their vectors {g_q,beta, L_b} span the whole 8-dimensional mean-free
 // subspace of R^9 (or a subspace of it), so a fixed orthonormal basis of that

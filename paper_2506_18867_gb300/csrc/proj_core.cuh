@@ -536,7 +536,11 @@ BSC_HD double char_poly(const double (&d)[n], const double (&e2)[n], double x, i
 // R[2n..3n)), loaded into registers.  After the FP32 bracket and its FP64
 // check, a bracket that isolates eigenvalue k is refined by the Illinois
 // variant of regula falsi on det(T - x I) (superlinear, bracketing), a
-// bracket holding several eigenvalues by bisection.
+// bracket holding several eigenvalues by bisection.  Regula falsi stalls
+// when an end of the bracket sits next to a multiple root of det(T - x I)
+// (a padded basis adds a multiple zero eigenvalue): whenever four steps
+// fail to halve the bracket together, the next step bisects, so the
+// bracket shrinks at least by half every five steps.
 template <int n>
 BSC_PHASE double eigenvalue_reg(const View& R, int k, double neg_rel) {
   double d[n], e2[n];
@@ -569,16 +573,21 @@ BSC_PHASE double eigenvalue_reg(const View& R, int k, double neg_rel) {
     fa = char_poly<n>(d, e2, a, &ca, &xa);
     fb = char_poly<n>(d, e2, b, &cb, &xb);
   }
-  int side = 0;
+  int side = 0, win = 0;
+  bool force_bisect = false;
+  double wstart = b - a;
 #pragma unroll 1
-  for (int it = 0; it < 60 && b - a > 1e-10; ++it) {
+  for (int it = 0; it < 120 && b - a > 1e-10; ++it) {
     double x;
-    const bool isolated = ca == k && cb == k + 1 && xa && xb && fa != fb;
+    const bool isolated = ca == k && cb == k + 1 && xa && xb && fa != fb && !force_bisect;
     if (isolated) {
       x = (a * fb - b * fa) / (fb - fa);
       if (!(x > a && x < b)) x = 0.5 * (a + b);
     } else {
       x = 0.5 * (a + b);
+      force_bisect = false;
+      win = 0;
+      wstart = b - a;
     }
     int cx;
     bool xx;
@@ -591,6 +600,11 @@ BSC_PHASE double eigenvalue_reg(const View& R, int k, double neg_rel) {
       a = x; fa = fx; ca = cx; xa = xx; side = 1;
     }
     if (isolated && fx == 0.0) return x;
+    if (isolated && ++win == 4) {  // four regula-falsi steps must at least halve the bracket
+      force_bisect = b - a > 0.5 * wstart;
+      win = 0;
+      wstart = b - a;
+    }
 #ifdef BSC_COUNT_EVALS
     ++bsc_evals;
 #endif

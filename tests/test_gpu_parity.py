@@ -82,11 +82,16 @@ def test_lumped_mass(case):
     assert rel(ctx.lumped_mass(), prob.lumped_mass()) < 1e-13
 
 
-@pytest.mark.parametrize("project", [False, True])
-def test_span_terms_fp64(case, project):
+@pytest.mark.parametrize("project,border_path", [(False, 0), (True, 0), (True, 1)],
+                         ids=["raw", "proj-warp", "proj-thread"])
+def test_span_terms_fp64(case, project, border_path):
+    """Span terms against the oracle; projected by both paths of the border
+    spans (one warp per span, one thread per span)."""
     pat, prob, ctx = case
     C = ctx.to_device(pat.C)
+    ctx.set_border_path(border_path)
     E, g, H = ctx.span_terms(C, project=project)
+    ctx.set_border_path(0)
     oE, og, oH = prob.span_eval(pat.C)
     if project:
         from oracle import project_psd

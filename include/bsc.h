@@ -275,6 +275,55 @@ int bsc_plan_blocks(int count, const int* n_cp, const double* work, int total, i
 bsc_status bsc_set_graph(bsc_ctx* ctx, int on);
 bsc_status bsc_graph_state(const bsc_ctx* ctx, int* on, int* captured, long long* replays);
 
+/* ---- learned preconditioner and flexible CG -------------------------------
+ * A 4-layer 3x3 convolutional network on the control grid of a single-patch
+ * FP32 context (channels 16 -> 32 -> 32 -> 32 -> 16, ReLU after the first
+ * three layers, zero padding), BF16 weights and activations with FP32
+ * accumulation on the tensor cores.  Per control point its 14 input
+ * features are r / s, (D^-1 r) d / s, the diagonal 3x3 block of K / d (six
+ * entries), the pin mask and 1, with s the RMS of r and d the mean
+ * diagonal entry of K; its output y (3 of 16 channels) gives
+ *   z = P(r) = D^-1 r + (s / d) y      (zero at pinned points),
+ * D the 3x3 block diagonal of K.  P(a r) = a P(r) for a > 0, and all-zero
+ * weights give the block-Jacobi preconditioner.
+ * Parameters (FP32, bsc_cnn_param_count() of them) in layer order; per layer
+ * the weights W[dy][dx][c_in][c_out] (dy, dx in {-1, 0, 1}, the offset of
+ * the input pixel (i + dx, j + dy)) then the bias [c_out].
+ * Training minimises the energy-norm error of the preconditioned vector,
+ *   L = (z - x*)^T K (z - x*) / (x*^T K x*),   x* = K^-1 r,
+ * with Adam on the FP32 master parameters.  Errors go to bsc_last_error(ctx). */
+typedef struct bsc_cnn bsc_cnn;
+typedef struct bsc_fcg_report {
+  int fcg_iters;        /* flexible-CG iterations */
+  int pcg_iters;        /* plain PCG iterations after a stall (fallback) */
+  int fell_back;        /* 1 when the flexible CG stalled and PCG finished the solve */
+  double rel_res;       /* final ||b - K x|| / ||b|| (recursive residual) */
+} bsc_fcg_report;
+
+int bsc_cnn_param_count(void);
+bsc_status bsc_cnn_create(bsc_ctx* ctx, bsc_cnn** out);   /* all parameters zero */
+void bsc_cnn_destroy(bsc_cnn* cnn);
+/* host FP32 parameters in; which = 0 parameters / 1 the last gradient out */
+bsc_status bsc_cnn_set_params(bsc_cnn* cnn, const float* params, int count);
+bsc_status bsc_cnn_get_params(bsc_cnn* cnn, float* out, int count, int which);
+/* binds the network to a matrix K_dev (stencil layout; block-Jacobi and the scale d) */
+bsc_status bsc_cnn_prepare(bsc_cnn* cnn, const void* K_dev);
+/* z_dev = P(r_dev) for the prepared matrix (3 planes of N, FP32) */
+bsc_status bsc_cnn_apply(bsc_cnn* cnn, const void* r_dev, void* z_dev);
+/* loss L at (r, x*) and its gradient (kept on the device for the optimizer) */
+bsc_status bsc_cnn_loss_grad(bsc_cnn* cnn, const void* r_dev, const void* xstar_dev, double* loss);
+bsc_status bsc_cnn_adam_step(bsc_cnn* cnn, double lr, double beta1, double beta2, double eps);
+/* activations of the last forward pass as host FP32 [N][channels]: which = 0
+ * features (16), 1..3 layer outputs (32), 4 network output (4: y and a zero) */
+bsc_status bsc_cnn_activations(bsc_cnn* cnn, int which, float* out);
+/* Solve K x = b (x from 0) by flexible CG with z = P(r):
+ *   q = K p, a = p.r / p.q, x += a p, r -= a q, z = P(r), b = -z.q / p.q, p = z + b p,
+ * until ||r|| <= rel_tol ||b||; when the residual has not dropped by 4x in 25
+ * iterations (or a curvature p.q <= 0 appears) plain block-Jacobi PCG finishes
+ * the solve from the current x. */
+bsc_status bsc_solve_fcg(bsc_ctx* ctx, bsc_cnn* cnn, const void* K_dev, const void* b_dev, void* x_dev,
+                         double rel_tol, int max_iter, bsc_fcg_report* rep);
+
 /* ---- inspection entry points (parity tests, profiling) ------------------- */
 
 /* Per-span results of the last evaluation path: E_span (device, Nsp doubles),

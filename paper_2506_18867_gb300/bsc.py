@@ -32,7 +32,9 @@ EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc
            "bsc_set_border_path",
            "bsc_pcg_split", "bsc_plan_blocks", "bsc_set_graph", "bsc_graph_state", "bsc_span_terms",
            "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes", "bsc_set_profiling", "bsc_phase_times",
-           "bsc_launch_count", "bsc_projection_stats", "bsc_solve_static")
+           "bsc_launch_count", "bsc_projection_stats", "bsc_solve_static", "bsc_cnn_param_count",
+           "bsc_cnn_create", "bsc_cnn_destroy", "bsc_cnn_set_params", "bsc_cnn_get_params", "bsc_cnn_prepare",
+           "bsc_cnn_apply", "bsc_cnn_loss_grad", "bsc_cnn_adam_step", "bsc_cnn_activations", "bsc_solve_fcg")
 
 TILE_CANDIDATES = (0, 8, 16, 32)
 
@@ -75,6 +77,13 @@ class Tuning(ct.Structure):
     def as_dict(self):
         return {"tile_tu": list(self.tile_tu), "tile_ms": [list(r) for r in self.tile_ms],
                 "pcg_grid": self.pcg_grid, "border_path": self.border_path, "border_ms": list(self.border_ms)}
+
+
+class FcgReport(ct.Structure):
+    _fields_ = [("fcg_iters", ct.c_int), ("pcg_iters", ct.c_int), ("fell_back", ct.c_int), ("rel_res", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class BscError(RuntimeError):
@@ -130,9 +139,22 @@ def load(path: str = LIB_PATH):
     lib.bsc_set_border_path.argtypes = [P, I]
     lib.bsc_plan_blocks.argtypes = [I, ct.POINTER(I), ct.POINTER(D), I, ct.POINTER(I)]
     lib.bsc_set_graph.argtypes = [P, I]
+    F = ct.POINTER(ct.c_float)
+    lib.bsc_cnn_param_count.argtypes = []
+    lib.bsc_cnn_create.argtypes = [P, ct.POINTER(P)]
+    lib.bsc_cnn_destroy.argtypes = [P]
+    lib.bsc_cnn_destroy.restype = None
+    lib.bsc_cnn_set_params.argtypes = [P, F, I]
+    lib.bsc_cnn_get_params.argtypes = [P, F, I, I]
+    lib.bsc_cnn_prepare.argtypes = [P, V]
+    lib.bsc_cnn_apply.argtypes = [P, V, V]
+    lib.bsc_cnn_loss_grad.argtypes = [P, V, V, ct.POINTER(D)]
+    lib.bsc_cnn_adam_step.argtypes = [P, D, D, D, D]
+    lib.bsc_cnn_activations.argtypes = [P, I, F]
+    lib.bsc_solve_fcg.argtypes = [P, P, V, V, V, D, I, ct.POINTER(FcgReport)]
     lib.bsc_graph_state.argtypes = [P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(ct.c_longlong)]
     for name in EXPORTS:
-        if name not in ("bsc_destroy", "bsc_last_error"):
+        if name not in ("bsc_destroy", "bsc_last_error", "bsc_cnn_destroy"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -413,6 +435,71 @@ def solve_static(nu, nv, precision, K, b, x, rel_tol=1e-8, max_iter=10000, strea
     if st != OK:
         raise BscError(st, lib.bsc_last_error(None).decode())
     return it.value, rr.value
+
+
+class Cnn:
+    """The learned preconditioner of a single-patch FP32 context (wraps bsc_cnn)."""
+
+    def __init__(self, ctx: Context):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        h = ct.c_void_p()
+        ctx._check(self._lib.bsc_cnn_create(ctx._h, ct.byref(h)))
+        self._h = h
+        self.n_params = self._lib.bsc_cnn_param_count()
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+        assert a.size == self.n_params
+        self.ctx._check(self._lib.bsc_cnn_set_params(self._h, a.ctypes.data_as(ct.POINTER(ct.c_float)), a.size))
+
+    def get_params(self, which=0):
+        a = np.zeros(self.n_params, dtype=np.float32)
+        self.ctx._check(self._lib.bsc_cnn_get_params(self._h, a.ctypes.data_as(ct.POINTER(ct.c_float)), a.size,
+                                                     int(which)))
+        return a
+
+    def prepare(self, K):
+        self.ctx._check(self._lib.bsc_cnn_prepare(self._h, _ptr(K)))
+
+    def apply(self, r, out=None):
+        out = self.ctx.new_vec() if out is None else out
+        self.ctx._check(self._lib.bsc_cnn_apply(self._h, _ptr(self.ctx._vec(r, "r")), _ptr(self.ctx._vec(out, "z"))))
+        return out
+
+    def loss_grad(self, r, xstar):
+        L = ct.c_double()
+        self.ctx._check(self._lib.bsc_cnn_loss_grad(self._h, _ptr(self.ctx._vec(r, "r")),
+                                                    _ptr(self.ctx._vec(xstar, "x*")), ct.byref(L)))
+        return L.value
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.ctx._check(self._lib.bsc_cnn_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps)))
+
+    def activations(self, which):
+        ch = {0: 16, 1: 32, 2: 32, 3: 32, 4: 4}[which]
+        a = np.zeros((self.ctx.N, ch), dtype=np.float32)
+        self.ctx._check(self._lib.bsc_cnn_activations(self._h, int(which), a.ctypes.data_as(ct.POINTER(ct.c_float))))
+        return a
+
+    def solve(self, b, K, rel_tol=1e-8, max_iter=10000, out=None):
+        out = self.ctx.new_vec() if out is None else out
+        rep = FcgReport()
+        st = self._lib.bsc_solve_fcg(self.ctx._h, self._h, _ptr(K), _ptr(self.ctx._vec(b, "b")),
+                                     _ptr(self.ctx._vec(out, "x")), float(rel_tol), int(max_iter), ct.byref(rep))
+        self.ctx._check(st)
+        return out, rep.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bsc_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def plan_blocks(n_cp, work, total):

@@ -378,6 +378,17 @@ cudaError_t assign_pcg_blocks(bsc_ctx* c) {
   return cudaMemcpy(c->pcg_blocks, tab.data(), sizeof(PcgBlock) * c->pcg_grid, cudaMemcpyHostToDevice);
 }
 
+// 3x3 block-Jacobi inverses of K into Dinv (9 planes), for callers outside the PCG.
+cudaError_t launch_block_jacobi(bsc_ctx* c, const void* K, void* Dinv) {
+  BSC_COUNT(c, 1);
+  const int G = (c->N + 255) / 256;
+  if (c->precision == BSC_FP64)
+    k_block_jacobi<double><<<G, 256, 0, c->stream>>>(c->N, (const double*)K, (double*)Dinv, c->dstatus);
+  else
+    k_block_jacobi<float><<<G, 256, 0, c->stream>>>(c->N, (const float*)K, (float*)Dinv, c->dstatus);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y) {
   BSC_COUNT(c, 1);
   const int B = 256, G = (c->N + B - 1) / B;

@@ -1,0 +1,137 @@
+"""Learned preconditioner on the GPU against the FP64 NumPy oracle
+(oracle/cnn_oracle.py), through the C ABI.
+
+The GPU keeps activations and back-propagated gradients in BF16 and
+accumulates in FP32 on the tensor cores; the oracle is run with the same BF16
+rounding points (bf16_like=True), so the two differ by FP32 accumulation
+order and the BF16 rounding flips it causes: about 2^-8 relative on the
+elements where a flip happens, norm-wise well under 1e-2.  Grid 40 x 23
+(920 pixels: seven full 128-pixel tiles and a ragged tail of 24).
+"""
+import numpy as np
+import pytest
+
+from oracle import cnn_oracle as co
+from paper_2506_18867_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2506_18867_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2506_18867_gb300 import bsc  # noqa: E402
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def random_params(seed, scale=1.0, last_scale=1.0):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(co.param_count())
+    for l, (ws, shape, bs) in enumerate(co.param_layout()):
+        fan_in = 9 * shape[2]
+        s = scale * (last_scale if l == 3 else 1.0)
+        p[ws] = rng.standard_normal(int(np.prod(shape))) * s * np.sqrt(2.0 / fan_in)
+        p[bs] = rng.standard_normal(bs.stop - bs.start) * 0.05 * s
+    return p.astype(np.float32).astype(np.float64)   # the GPU's FP32 master values
+
+
+@pytest.fixture(scope="module")
+def system():
+    pat = inputs.config_random_small(21, 40, 23, noise=0.05)
+    ctx = bsc.context_for_patch(pat, precision=bsc.FP32, pcg_rel_tol=1e-10)
+    C, Ch = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+    K = ctx.assemble_hessian(C, project=True)
+    r = -ctx.gradient(C, Ch)
+    xs, it, rr = ctx.solve(r, K=K, rel_tol=1e-7)
+    Kh = K.double().cpu().numpy().reshape(25, 3, 3, -1).transpose(3, 0, 1, 2).copy()
+    pin = np.zeros(pat.n_cp, dtype=bool)
+    pin[pat.pinned] = True
+    prep = co.Prepared(pat.nu, pat.nv, Kh, pin)
+    net = bsc.Cnn(ctx)
+    yield pat, ctx, net, K, r, xs, prep
+    net.close()
+    ctx.close()
+
+
+def n3(t):
+    return t.double().cpu().numpy().reshape(3, -1).T.copy()
+
+
+def test_forward_layers_match_oracle(system):
+    pat, ctx, net, K, r, xs, prep = system
+    params = random_params(1)
+    net.set_params(params)
+    net.prepare(K)
+    z = net.apply(r)
+    zo, cache = co.forward(params, prep, n3(r), bf16_like=True)
+    f_gpu = net.activations(0)
+    f_or = cache["acts"][0].reshape(-1, 16)
+    assert rel(f_gpu, f_or) < 4e-3                      # one BF16 rounding of FP32 vs FP64 features
+    errs = []
+    for l in (1, 2, 3):
+        a = net.activations(l)
+        errs.append(rel(a, cache["acts"][l].reshape(-1, 32)))
+    y = net.activations(4)[:, :3]
+    errs.append(rel(y, cache["acts"][4].reshape(-1, 16)[:, :3]))
+    ez = rel(n3(z), zo)
+    print("feature / layer / output rel errors:", rel(f_gpu, f_or), errs, "z:", ez)
+    assert max(errs) < 1e-2 and ez < 1e-2
+
+
+def test_gradients_match_oracle(system):
+    pat, ctx, net, K, r, xs, prep = system
+    params = random_params(2, last_scale=3.0)
+    net.set_params(params)
+    net.prepare(K)
+    L = net.loss_grad(r, xs)
+    g = net.get_params(which=1).astype(np.float64)
+    Lo, go = co.loss_and_grad(params, prep, n3(r), n3(xs), bf16_like=True)
+    assert abs(L - Lo) <= 1e-2 * abs(Lo)
+    for l, (ws, _, bs) in enumerate(co.param_layout()):
+        ew, eb = rel(g[ws], go[ws]), rel(g[bs], go[bs])
+        print(f"layer {l + 1}: weight-gradient rel err {ew:.2e}, bias {eb:.2e}")
+        assert ew < 3e-2 and eb < 3e-2, l
+
+
+def test_zero_weights_reproduce_block_jacobi(system):
+    pat, ctx, net, K, r, xs, prep = system
+    net.set_params(np.zeros(co.param_count()))
+    net.prepare(K)
+    z = n3(net.apply(r))
+    ref = np.einsum("nab,nb->na", np.linalg.inv(prep.diag), n3(r))
+    ref[prep.pin] = 0.0
+    assert rel(z, ref) < 1e-6
+    x, rep = net.solve(r, K, rel_tol=1e-8)
+    _, it, _ = ctx.solve(r, K=K, rel_tol=1e-8)
+    assert rep["fell_back"] == 0 and rep["rel_res"] <= 1e-8
+    assert abs(rep["fcg_iters"] - it) <= 2, (rep, it)
+
+
+def test_fcg_converges_with_a_random_network_or_falls_back(system):
+    pat, ctx, net, K, r, xs, prep = system
+    net.set_params(random_params(3, scale=1.0))
+    x, rep = net.solve(r, K, rel_tol=1e-8)
+    assert rep["rel_res"] <= 1e-8
+    res = n3(ctx.spmv(x, K=K)) - n3(r)
+    assert np.linalg.norm(res) <= 1e-6 * np.linalg.norm(n3(r))
+    print("random network:", rep)
+
+
+def test_adam_steps_reduce_the_loss(system):
+    pat, ctx, net, K, r, xs, prep = system
+    net.set_params(np.zeros(co.param_count()))
+    net.prepare(K)
+    L0 = net.loss_grad(r, xs)
+    for _ in range(30):
+        net.loss_grad(r, xs)
+        net.adam_step(1e-3)
+    L1 = net.loss_grad(r, xs)
+    print("loss", L0, "->", L1)
+    assert L1 < L0

@@ -245,6 +245,11 @@ typedef struct bsc_tuning {
 } bsc_tuning;
 bsc_status bsc_autotune(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, bsc_tuning* out);
 
+/* Replace patch p's material (stiffnesses and density; the lumped masses
+ * are recomputed when the density changes).  Ordered on the context's
+ * stream; synchronises it.  Captured Newton graphs stay valid. */
+bsc_status bsc_set_material(bsc_ctx* ctx, int patch, const bsc_material* m);
+
 /* Set the tile widths by hand (4 entries, each 0, 8, 16 or 32). */
 bsc_status bsc_set_tiles(bsc_ctx* ctx, const int* tile_tu);
 
@@ -277,20 +282,30 @@ bsc_status bsc_graph_state(const bsc_ctx* ctx, int* on, int* captured, long long
 
 /* ---- learned preconditioner and flexible CG -------------------------------
  * A 4-layer 3x3 convolutional network on the control grid of a single-patch
- * FP32 context (channels 16 -> 32 -> 32 -> 32 -> 16, ReLU after the first
+ * FP32 context (channels 32 -> 32 -> 32 -> 32 -> 16, ReLU after the first
  * three layers, zero padding), BF16 weights and activations with FP32
- * accumulation on the tensor cores.  Per control point its 14 input
- * features are r / s, (D^-1 r) d / s, the diagonal 3x3 block of K / d (six
- * entries), the pin mask and 1, with s the RMS of r and d the mean
- * diagonal entry of K; its output y (3 of 16 channels) gives
- *   z = P(r) = D^-1 r + (s / d) y      (zero at pinned points),
- * D the 3x3 block diagonal of K.  P(a r) = a P(r) for a > 0, and all-zero
- * weights give the block-Jacobi preconditioner.
+ * accumulation on the tensor cores.  It reads the matrix and writes a local
+ * linear preconditioner:
+ *   features per control point alpha (32): the diagonal block K_aa / d
+ *     (entries 00 01 02 11 12 22), the traces of the 24 off-diagonal blocks
+ *     / d in slot order, the pin mask and 1 (d = mean diagonal entry of K
+ *     over unpinned points);
+ *   output channels 0..8 (o_t): tap coefficients a_t(alpha) = o_t / (2 (1 +
+ *     sum_s |o_s|)), t = 3 (dy + 1) + (dx + 1) for the neighbour (i + dx,
+ *     j + dy) - sum_t |a_t| < 1/2, so cond(B^T B) <= 9 for any weights;
+ *   M = P L^-T B^T B L^-1 P,  D_aa = L_a L_a^T (Cholesky of each diagonal
+ *     block), (B y)(alpha) = y(alpha) + sum_t a_t(alpha) y(alpha + off_t) for
+ *     each component (zero outside the grid), P zeroing pinned entries.
+ * M is symmetric positive semidefinite for any weights, and all-zero weights
+ * give the block-Jacobi preconditioner.  The network runs once per matrix
+ * (bsc_cnn_prepare); each application of M costs two 9-tap stencils and two
+ * block triangular solves per control point.
  * Parameters (FP32, bsc_cnn_param_count() of them) in layer order; per layer
  * the weights W[dy][dx][c_in][c_out] (dy, dx in {-1, 0, 1}, the offset of
  * the input pixel (i + dx, j + dy)) then the bias [c_out].
- * Training minimises the energy-norm error of the preconditioned vector,
- *   L = (z - x*)^T K (z - x*) / (x*^T K x*),   x* = K^-1 r,
+ * Training minimises the energy-norm error of the preconditioned vector of
+ * pairs (r = K x, x),
+ *   L = (M r - x)^T K (M r - x) / (x^T K x),
  * with Adam on the FP32 master parameters.  Errors go to bsc_last_error(ctx). */
 typedef struct bsc_cnn bsc_cnn;
 typedef struct bsc_fcg_report {
@@ -306,19 +321,22 @@ void bsc_cnn_destroy(bsc_cnn* cnn);
 /* host FP32 parameters in; which = 0 parameters / 1 the last gradient out */
 bsc_status bsc_cnn_set_params(bsc_cnn* cnn, const float* params, int count);
 bsc_status bsc_cnn_get_params(bsc_cnn* cnn, float* out, int count, int which);
-/* binds the network to a matrix K_dev (stencil layout; block-Jacobi and the scale d) */
+/* binds the network to a matrix K_dev (stencil layout): features, block
+ * Cholesky factors, and one forward pass of the network */
 bsc_status bsc_cnn_prepare(bsc_cnn* cnn, const void* K_dev);
-/* z_dev = P(r_dev) for the prepared matrix (3 planes of N, FP32) */
+/* z_dev = M r_dev for the prepared matrix (3 planes of N, FP32) */
 bsc_status bsc_cnn_apply(bsc_cnn* cnn, const void* r_dev, void* z_dev);
-/* loss L at (r, x*) and its gradient (kept on the device for the optimizer) */
+/* loss L at the pair (r, x) (r = K x) with the current weights (the network
+ * is re-run on the prepared matrix) and its gradient (kept on the device for
+ * the optimizer) */
 bsc_status bsc_cnn_loss_grad(bsc_cnn* cnn, const void* r_dev, const void* xstar_dev, double* loss);
 bsc_status bsc_cnn_adam_step(bsc_cnn* cnn, double lr, double beta1, double beta2, double eps);
 /* activations of the last forward pass as host FP32 [N][channels]: which = 0
- * features (16), 1..3 layer outputs (32), 4 network output (4: y and a zero) */
+ * features (32), 1..3 layer outputs (32), 4 network output (16: o_0..o_8 and 7 unused) */
 bsc_status bsc_cnn_activations(bsc_cnn* cnn, int which, float* out);
-/* Solve K x = b (x from 0) by flexible CG with z = P(r):
- *   q = K p, a = p.r / p.q, x += a p, r -= a q, z = P(r), b = -z.q / p.q, p = z + b p,
- * until ||r|| <= rel_tol ||b||; when the residual has not dropped by 4x in 25
+/* Solve K x = b (x from 0) by flexible CG with z = M r (the call prepares the network on K_dev):
+ *   q = K p, a = p.r / p.q, x += a p, r -= a q, z = M r, b = -z.q / p.q, p = z + b p,
+ * until ||r|| <= rel_tol ||b||; when r.r has not dropped by 4x in 24
  * iterations (or a curvature p.q <= 0 appears) plain block-Jacobi PCG finishes
  * the solve from the current x. */
 bsc_status bsc_solve_fcg(bsc_ctx* ctx, bsc_cnn* cnn, const void* K_dev, const void* b_dev, void* x_dev,

@@ -1,34 +1,44 @@
 """Plain FP64 NumPy oracle of the learned preconditioner (TEST INFRASTRUCTURE
 ONLY: imported by tests/ and bench.py's baseline leg, never by the product).
 
-The network is the one the C ABI documents for bsc_cnn_*: four 3x3
-convolutions with zero padding on the nu x nv control grid (channels
-16 -> 32 -> 32 -> 32 -> 16), ReLU after the first three, input features
+What it computes (the C ABI documents the same for bsc_cnn_*):
 
-    r / s,  (D^-1 r) d / s,  diagonal 3x3 block of K / d (6 entries),  pin,  1
+* Matrix features per control point alpha (32 channels): the diagonal 3x3
+  block K_aa / d (six entries: 00 01 02 11 12 22), the traces of the 24
+  off-diagonal blocks K_a,a+(du,dv) / d in slot order, the pin mask and 1,
+  with d = mean diagonal entry of K over unpinned points.
+* A network of four 3x3 convolutions with zero padding on the nu x nv grid
+  (channels 32 -> 32 -> 32 -> 32 -> 16), ReLU after the first three; its
+  first nine output channels o_t give the tap coefficients
+      a_t(alpha) = RHO o_t / (1 + sum_s |o_s|),   RHO = 1/2,
+  t = 3 (dy+1) + (dx+1) for the neighbour (i + dx, j + dy).  The bound
+  sum_t |a_t| < RHO keeps B within RHO of the identity in the infinity norm,
+  so B is invertible and cond(B^T B) <= ((1 + RHO) / (1 - RHO))^2 = 9 for any
+  weights: training cannot reach a nearly singular preconditioner.
+* The preconditioner M = P L^-T B^T B L^-1 P with D_aa = L_a L_a^T the
+  Cholesky factor of every diagonal block, (B y)(alpha) = y(alpha) + sum_t
+  a_t(alpha) y(alpha + off_t) (the same for the three components, zero
+  outside the grid) and P zeroing the pinned entries; z = M r.  M is
+  symmetric positive semidefinite for every a, and a = 0 gives the
+  block-Jacobi preconditioner D^-1 (on the unpinned entries).
+* The loss of a pair (r = K x, x): L = (z - x)^T K (z - x) / (x^T K x).
+* Its gradient by hand-written backpropagation through M and the network;
+  the tests pin it against central finite differences.
 
-with s = RMS of r and d = mean diagonal entry of K over unpinned points, and
-the preconditioned vector z = D^-1 r + (s / d) y (y = output channels 0..2,
-zero at pinned points).  The loss is the energy-norm error of z against the
-exact solve x* = K^-1 r, L = (z - x*)^T K (z - x*) / (x*^T K x*).  The
-backward pass below is written out by hand (chain rule through the combine,
-the convolutions and the ReLUs); the tests pin it against central finite
-differences of the loss.
-
-Arrays: r, z, x* are (N, 3) (control point alpha = j nu + i); K is the
-oracle's stencil (N, 25, 3, 3); parameters are one flat float vector in the
-C ABI's order (per layer W[dy][dx][ci][co], then b[co]).
-
-With bf16=True every tensor the GPU stores in BF16 (features, layer outputs,
-back-propagated gradients) is rounded to BF16 (round to nearest even) at the
-same point, so that GPU and oracle differ only by FP32 accumulation order.
+Arrays: vectors are (N, 3) (alpha = j nu + i), K is the oracle's stencil
+(N, 25, 3, 3), parameters one flat float vector in the C ABI's order (per
+layer W[dy][dx][ci][co], then b[co]).  With bf16_like=True every tensor the
+GPU stores in BF16 (features, layer outputs, back-propagated gradients) is
+rounded to BF16 at the same point.
 """
 from __future__ import annotations
 
 import numpy as np
 
-CH_IN = (16, 32, 32, 32)
+CH_IN = (32, 32, 32, 32)
 CH_OUT = (32, 32, 32, 16)
+TAPS = 9
+RHO = 0.5
 
 
 def param_layout():
@@ -87,8 +97,7 @@ def conv3x3_adjoint(G, W):
     dX = np.zeros((nv, nu, W.shape[2]))
     for dy in range(3):
         for dx in range(3):
-            # output pixel (j, i) received X[j + dy - 1, i + dx - 1]: the input
-            # pixel (j, i) feeds the outputs (j - dy + 1, i - dx + 1)
+            # the input pixel (j, i) feeds the outputs (j - dy + 1, i - dx + 1)
             dX += np.einsum("jid,cd->jic", Gp[2 - dy:2 - dy + nv, 2 - dx:2 - dx + nu], W[dy, dx])
     return dX
 
@@ -105,55 +114,111 @@ def conv3x3_wgrad(X, G):
     return dW, G.sum(axis=(0, 1))
 
 
+def shift(y, nu, nv, dx, dy):
+    """(S y)(j, i) = y(j + dy, i + dx), zero outside.  y: (N, c)."""
+    Y = y.reshape(nv, nu, -1)
+    out = np.zeros_like(Y)
+    js, je = max(0, -dy), nv - max(0, dy)
+    is_, ie = max(0, -dx), nu - max(0, dx)
+    out[js:je, is_:ie] = Y[js + dy:je + dy, is_ + dx:ie + dx]
+    return out.reshape(y.shape)
+
+
+def taps():
+    return [(t % 3 - 1, t // 3 - 1) for t in range(TAPS)]   # (dx, dy) of tap t
+
+
 class Prepared:
-    """The matrix-dependent part: diagonal blocks, their inverses, the scale d."""
+    """The matrix-dependent part: features, block Cholesky factors, the scale d."""
 
     def __init__(self, nu, nv, K, pinned_mask):
         self.nu, self.nv = nu, nv
         K = np.asarray(K, dtype=np.float64).reshape(nu * nv, 25, 3, 3)
         self.K = K
         self.diag = K[:, 12]
-        self.Dinv = np.linalg.inv(self.diag)
         self.pin = np.asarray(pinned_mask, dtype=bool).reshape(-1)
         tr = np.trace(self.diag, axis1=1, axis2=2)[~self.pin]
         self.d = float(tr.sum() / (3 * tr.size)) if tr.size else 1.0
+        self.L = np.linalg.cholesky(self.diag)
+        self.Linv = np.linalg.inv(self.L)
 
-    def features(self, r):
-        r = np.asarray(r, dtype=np.float64).reshape(-1, 3)
-        s = float(np.sqrt((r * r).sum() / r.size))
-        iS = 1.0 / s if s > 0 else 0.0
-        Dr = np.einsum("nab,nb->na", self.Dinv, r)
-        f = np.zeros((r.shape[0], 16))
-        f[:, 0:3] = r * iS
-        f[:, 3:6] = Dr * self.d * iS
+    def features(self):
+        N = self.nu * self.nv
+        f = np.zeros((N, 32))
         g = self.diag / self.d
-        f[:, 6], f[:, 7], f[:, 8] = g[:, 0, 0], g[:, 0, 1], g[:, 0, 2]
-        f[:, 9], f[:, 10], f[:, 11] = g[:, 1, 1], g[:, 1, 2], g[:, 2, 2]
-        f[:, 12] = self.pin.astype(np.float64)
-        f[:, 13] = 1.0
-        return f, s, Dr
+        f[:, 0], f[:, 1], f[:, 2] = g[:, 0, 0], g[:, 0, 1], g[:, 0, 2]
+        f[:, 3], f[:, 4], f[:, 5] = g[:, 1, 1], g[:, 1, 2], g[:, 2, 2]
+        k = 6
+        for slot in range(25):
+            if slot == 12:
+                continue
+            f[:, k] = np.trace(self.K[:, slot], axis1=1, axis2=2) / self.d
+            k += 1
+        f[:, 30] = self.pin.astype(np.float64)
+        f[:, 31] = 1.0
+        return f
 
     def matvec(self, x):
         from oracle import stencil_matvec
         return stencil_matvec(self.nu, self.nv, self.K, x)
 
 
-def forward(params, prep: Prepared, r, bf16_like=False):
-    """z = P(r) and the cache of the forward pass."""
+def network(params, prep: Prepared, bf16_like=False):
+    """Tap coefficients a (N, 9) and the cache of the forward pass."""
     layers = unpack(params)
-    f, s, Dr = prep.features(r)
-    X = _maybe(f, bf16_like).reshape(prep.nv, prep.nu, 16)
+    X = _maybe(prep.features(), bf16_like).reshape(prep.nv, prep.nu, 32)
     acts = [X]
     for l, (W, b) in enumerate(layers):
-        Wl = _maybe(W, bf16_like)
-        Y = conv3x3(acts[-1], Wl, b)
+        Y = conv3x3(acts[-1], _maybe(W, bf16_like), b)
         if l < 3:
             Y = _maybe(np.maximum(Y, 0.0), bf16_like)
         acts.append(Y)
-    y = acts[-1].reshape(-1, 16)[:, :3]
-    z = Dr + (s / prep.d) * y
+    o = acts[-1].reshape(-1, 16)[:, :TAPS]
+    a = bound_taps(o)
+    return a, {"acts": acts, "layers": layers, "o": o}
+
+
+def bound_taps(o):
+    return RHO * o / (1.0 + np.abs(o).sum(axis=1, keepdims=True))
+
+
+def bound_taps_backward(o, da):
+    """d/do of sum_t da_t a_t(o) with a_t = RHO o_t / S, S = 1 + sum |o|."""
+    S = 1.0 + np.abs(o).sum(axis=1, keepdims=True)
+    return RHO * (da / S - np.sign(o) * np.sum(da * o, axis=1, keepdims=True) / S ** 2)
+
+
+def apply_B(a, y, nu, nv):
+    u = y.copy()
+    for t, (dx, dy) in enumerate(taps()):
+        u += a[:, t:t + 1] * shift(y, nu, nv, dx, dy)
+    return u
+
+
+def apply_BT(a, u, nu, nv):
+    v = u.copy()
+    for t, (dx, dy) in enumerate(taps()):
+        v += shift(a[:, t:t + 1] * u, nu, nv, -dx, -dy)
+    return v
+
+
+def precondition(a, prep: Prepared, r):
+    """z = M r with M = P L^-T B^T B L^-1 P, P zeroing the pinned entries; also (y, u, v)."""
+    r = np.array(r, dtype=np.float64).reshape(-1, 3)
+    r[prep.pin] = 0.0
+    y = np.einsum("nab,nb->na", prep.Linv, r)
+    u = apply_B(a, y, prep.nu, prep.nv)
+    v = apply_BT(a, u, prep.nu, prep.nv)
+    z = np.einsum("nba,nb->na", prep.Linv, v)
     z[prep.pin] = 0.0
-    return z, {"acts": acts, "s": s, "Dr": Dr, "layers": layers}
+    return z, (y, u, v)
+
+
+def forward(params, prep: Prepared, r, bf16_like=False):
+    a, cache = network(params, prep, bf16_like)
+    z, yuv = precondition(a, prep, r)
+    cache["a"], cache["yuv"] = a, yuv
+    return z, cache
 
 
 def loss(params, prep: Prepared, r, xstar, bf16_like=False):
@@ -161,6 +226,21 @@ def loss(params, prep: Prepared, r, xstar, bf16_like=False):
     xs = np.asarray(xstar, dtype=np.float64).reshape(-1, 3)
     e = z - xs
     return float(np.sum(e * prep.matvec(e)) / np.sum(xs * prep.matvec(xs)))
+
+
+def tap_gradient(a, prep, yuv, g):
+    """dL/da (N, 9) from dL/dz = g through z = L^-T B^T B L^-1 r."""
+    y, u, _ = yuv
+    nu, nv = prep.nu, prep.nv
+    g = g.copy()
+    g[prep.pin] = 0.0
+    gv = np.einsum("nab,nb->na", prep.Linv, g)        # v -> z = L^-T v
+    gu = apply_B(a, gv, nu, nv)                        # u -> v = B^T u
+    da = np.zeros((nu * nv, TAPS))
+    for t, (dx, dy) in enumerate(taps()):
+        # u = y + sum a_t S_t y  and  v = u + sum S_-t (a_t u)
+        da[:, t] = np.sum(gu * shift(y, nu, nv, dx, dy), axis=1) + np.sum(u * shift(gv, nu, nv, dx, dy), axis=1)
+    return da
 
 
 def loss_and_grad(params, prep: Prepared, r, xstar, bf16_like=False):
@@ -171,19 +251,17 @@ def loss_and_grad(params, prep: Prepared, r, xstar, bf16_like=False):
     Ke = prep.matvec(e)
     xKx = float(np.sum(xs * prep.matvec(xs)))
     L = float(np.sum(e * Ke) / xKx)
-    dz = 2.0 * Ke / xKx                       # dL/dz (K symmetric)
-    dz[prep.pin] = 0.0
+    g = 2.0 * Ke / xKx                                  # dL/dz (K symmetric)
+    da = tap_gradient(cache["a"], prep, cache["yuv"], g)
     dy = np.zeros((prep.nu * prep.nv, 16))
-    dy[:, :3] = (cache["s"] / prep.d) * dz    # z = Dr + (s/d) y
+    dy[:, :TAPS] = bound_taps_backward(cache["o"], da)
     G = _maybe(dy, bf16_like).reshape(prep.nv, prep.nu, 16)
     acts, layers = cache["acts"], cache["layers"]
     grads = [None] * 4
     for l in range(3, -1, -1):
-        dW, db = conv3x3_wgrad(acts[l], G)
-        grads[l] = (dW, db)
+        grads[l] = conv3x3_wgrad(acts[l], G)
         if l > 0:
-            Wl = _maybe(layers[l][0], bf16_like)
-            G = conv3x3_adjoint(G, Wl) * (acts[l] > 0.0)   # through the ReLU of layer l's input
+            G = conv3x3_adjoint(G, _maybe(layers[l][0], bf16_like)) * (acts[l] > 0.0)
             G = _maybe(G, bf16_like)
     flat = np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in grads])
     return L, flat

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5:
 EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc_energy", "bsc_gradient",
            "bsc_assemble_hessian", "bsc_spmv", "bsc_solve", "bsc_newton_step", "bsc_create_batch",
            "bsc_batch_layout", "bsc_patch_reports", "bsc_patch_energies", "bsc_autotune", "bsc_set_tiles",
-           "bsc_set_border_path",
+           "bsc_set_border_path", "bsc_set_material",
            "bsc_pcg_split", "bsc_plan_blocks", "bsc_set_graph", "bsc_graph_state", "bsc_span_terms",
            "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes", "bsc_set_profiling", "bsc_phase_times",
            "bsc_launch_count", "bsc_projection_stats", "bsc_solve_static", "bsc_cnn_param_count",
@@ -137,6 +137,7 @@ def load(path: str = LIB_PATH):
     lib.bsc_set_tiles.argtypes = [P, ct.POINTER(I)]
     lib.bsc_pcg_split.argtypes = [P, ct.POINTER(I)]
     lib.bsc_set_border_path.argtypes = [P, I]
+    lib.bsc_set_material.argtypes = [P, I, ct.POINTER(Material)]
     lib.bsc_plan_blocks.argtypes = [I, ct.POINTER(I), ct.POINTER(D), I, ct.POINTER(I)]
     lib.bsc_set_graph.argtypes = [P, I]
     F = ct.POINTER(ct.c_float)
@@ -288,11 +289,15 @@ class Context:
         self._check(self._lib.bsc_spmv(self._h, _ptr(K), _ptr(self._vec(x, "x")), _ptr(self._vec(out, "y"))))
         return out
 
-    def solve(self, b, K=None, rel_tol=1e-8, max_iter=10000, out=None):
+    def solve(self, b, K=None, rel_tol=1e-8, max_iter=10000, out=None, allow_unconverged=False):
+        """PCG solve; with allow_unconverged the iterate after max_iter is returned
+        instead of raising NOT_CONVERGED."""
         out = self.new_vec() if out is None else out
         it, rr = ct.c_int(), ct.c_double()
-        self._check(self._lib.bsc_solve(self._h, _ptr(K), _ptr(self._vec(b, "b")), _ptr(self._vec(out, "x")),
-                                        float(rel_tol), int(max_iter), ct.byref(it), ct.byref(rr)))
+        st = self._lib.bsc_solve(self._h, _ptr(K), _ptr(self._vec(b, "b")), _ptr(self._vec(out, "x")),
+                                 float(rel_tol), int(max_iter), ct.byref(it), ct.byref(rr))
+        if not (allow_unconverged and st == ERR_NOT_CONVERGED):
+            self._check(st)
         return out, it.value, rr.value
 
     def newton_step(self, C, Chat=None):
@@ -382,6 +387,10 @@ class Context:
     def set_tiles(self, tiles):
         arr = (ct.c_int * 4)(*[int(t) for t in tiles])
         self._check(self._lib.bsc_set_tiles(self._h, arr))
+
+    def set_material(self, material, patch=0):
+        m = Material(*(material.as_tuple() if hasattr(material, "as_tuple") else tuple(material)))
+        self._check(self._lib.bsc_set_material(self._h, int(patch), ct.byref(m)))
 
     def set_border_path(self, path):
         self._check(self._lib.bsc_set_border_path(self._h, int(path)))
@@ -477,7 +486,7 @@ class Cnn:
         self.ctx._check(self._lib.bsc_cnn_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps)))
 
     def activations(self, which):
-        ch = {0: 16, 1: 32, 2: 32, 3: 32, 4: 4}[which]
+        ch = {0: 32, 1: 32, 2: 32, 3: 32, 4: 16}[which]
         a = np.zeros((self.ctx.N, ch), dtype=np.float32)
         self.ctx._check(self._lib.bsc_cnn_activations(self._h, int(which), a.ctypes.data_as(ct.POINTER(ct.c_float))))
         return a

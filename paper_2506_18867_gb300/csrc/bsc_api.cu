@@ -611,6 +611,26 @@ bsc_status bsc_patch_reports(const bsc_ctx* c, bsc_newton_report* reps) {
   return BSC_OK;
 }
 
+bsc_status bsc_set_material(bsc_ctx* c, int p, const bsc_material* m) {
+  if (!c || !m) return BSC_ERR_INVALID_ARG;
+  if (p < 0 || p >= c->P) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_material: patch %d out of range", p);
+  const double v[5] = {m->mu_st1, m->mu_st2, m->mu_sh, m->mu_bd, m->rho_area};
+  for (double x : v)
+    if (!(x >= 0.0) || !isfinite(x)) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_material: material must be finite, >= 0");
+  PatchDev& d = c->hpd[p];
+  const bool rho_changed = d.rho != m->rho_area;
+  d.mu1 = m->mu_st1;
+  d.mu2 = m->mu_st2;
+  d.mush = m->mu_sh;
+  d.mubd = m->mu_bd;
+  d.rho = m->rho_area;
+  // stream-ordered: launches already queued keep the old values
+  CK(cudaMemcpyAsync(c->pd + p, &d, sizeof(PatchDev), cudaMemcpyHostToDevice, c->stream), "bsc_set_material");
+  if (rho_changed) CK(launch_lumped_mass_patch(c, p), "bsc_set_material");
+  CK(cudaStreamSynchronize(c->stream), "bsc_set_material");
+  return BSC_OK;
+}
+
 bsc_status bsc_set_graph(bsc_ctx* c, int on) {
   if (!c) return BSC_ERR_INVALID_ARG;
   c->use_graph = on ? 1 : 0;

@@ -184,6 +184,7 @@ struct bsc_ctx {
 // launchers (defined in the .cu files)
 // -------------------------------------------------------------------------
 cudaError_t launch_build_tables(bsc_ctx* c);
+cudaError_t launch_lumped_mass_patch(bsc_ctx* c, int p);
 cudaError_t build_span_items(bsc_ctx* c);
 cudaError_t build_red_items(bsc_ctx* c);
 cudaError_t setup_span_eval(bsc_ctx* c);

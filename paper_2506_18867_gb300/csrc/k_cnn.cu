@@ -1,15 +1,21 @@
 // K7 / K8: the learned preconditioner - a 4-layer 3x3 convolutional network on
-// the control grid - and the flexible CG that uses it.
+// the control grid that reads the matrix and writes a local linear
+// preconditioner - and the flexible CG that uses it.
 //
-// Network (channels 16 -> 32 -> 32 -> 32 -> 16, ReLU after the first three
-// layers, zero padding at the grid border).  Input features per control
-// point, made dimensionless so that P(a r) = a P(r) for a > 0:
-//   r / s,  (D^-1 r) d / s,  the six entries of the diagonal 3x3 block / d,
-//   the pin mask, and a constant 1 (14 channels, 2 zero pad)
-// with s = RMS of r over the grid and d = mean diagonal entry of K.  The
-// preconditioned vector is z = D^-1 r + (s / d) y, y the first three output
-// channels (zero at pinned points): with zero weights the network reproduces
-// the block-Jacobi preconditioner, and training learns a correction.
+// Input features per control point (32 channels, dimensionless): the diagonal
+// 3x3 block of K / d (six entries), the traces of the 24 off-diagonal blocks
+// / d, the pin mask and 1, d = mean diagonal entry of K.  Network: channels
+// 32 -> 32 -> 32 -> 32 -> 16, ReLU after the first three layers, zero padding
+// at the grid border; output channels 0..8 (o_t) give the tap coefficients
+// a_t(alpha) = RHO o_t / (1 + sum_s |o_s|): sum_t |a_t| < RHO = 1/2, so B
+// stays within 1/2 of the identity and cond(B^T B) <= 9 for any weights.
+// Preconditioner, fixed for a given K:
+//   M = P L^-T B^T B L^-1 P,  D_aa = L_a L_a^T (Cholesky of each diagonal block),
+//   (B y)(alpha) = y(alpha) + sum_t a_t(alpha) y(alpha + off_t),
+// P zeroing the pinned entries.  M is symmetric positive semidefinite for
+// every a, a = 0 is block-Jacobi, and the network runs once per matrix; each
+// CG iteration applies M with two 9-tap stencils and two block triangular
+// solves.
 //
 // Every convolution is an implicit GEMM on the tensor cores (tcgen05, BF16
 // operands, FP32 accumulator in TMEM): a CTA takes 128 consecutive pixels
@@ -19,8 +25,9 @@
 // K = 16 into a TMEM accumulator; the epilogue reads the accumulator back
 // (tcgen05.ld), adds the bias and applies the activation.  The backward pass
 // of the data (gradient w.r.t. a layer's input) is the same kernel on the
-// flipped, transposed weights with the ReLU derivative as epilogue; the
-// weight gradients are reductions over pixels on the CUDA cores.
+// transposed weights gathered at the negated offsets, with the ReLU
+// derivative as epilogue; the weight gradients are reductions over pixels on
+// the CUDA cores.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -34,14 +41,14 @@
 #include "bsc_internal.cuh"
 #include "tc05.cuh"
 
-cudaError_t launch_block_jacobi(bsc_ctx* c, const void* K, void* Dinv);
 
 namespace {
 
 constexpr int NL = 4;
-constexpr int CH_IN[NL] = {16, 32, 32, 32};
+constexpr int CH_IN[NL] = {32, 32, 32, 32};
 constexpr int CH_OUT[NL] = {32, 32, 32, 16};
 constexpr int TILE = 128;
+constexpr float RHO = 0.5f;
 constexpr long long WAIT_LIMIT = 1ll << 25;
 
 constexpr int w_count(int l) { return 9 * CH_IN[l] * CH_OUT[l]; }
@@ -59,7 +66,7 @@ struct ConvArgs {
   const uint8_t* Wb;           // COUT x 9 CIN, BF16, K-major no-swizzle core layout
   const float* bias;           // [COUT] (modes 0, 1)
   const __nv_bfloat16* mask;   // [P][COUT] forward activation whose sign gates the gradient (mode 2)
-  void* Y;                     // [P][COUT] BF16 (modes 0, 2) or [P][4] FP32 (mode 1: channels 0..2)
+  void* Y;                     // [P][COUT] BF16 (modes 0, 2) or FP32 (mode 1)
   int flip;                    // 1: gather at -offset (the transposed convolution)
   int* status;
 };
@@ -155,12 +162,11 @@ __global__ void __launch_bounds__(TILE) k_conv(ConvArgs a) {
     const int p = p0 + tid;
     if (p < a.P) {
       if (MODE == CONV_LINEAR_F32) {
-        float4 o;
-        o.x = v[0] + __ldg(a.bias + 0);
-        o.y = v[1] + __ldg(a.bias + 1);
-        o.z = v[2] + __ldg(a.bias + 2);
-        o.w = 0.0f;
-        reinterpret_cast<float4*>(a.Y)[p] = o;
+        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.Y) + (size_t)p * COUT);
+#pragma unroll
+        for (int c = 0; c < COUT / 4; ++c)
+          dst[c] = make_float4(v[4 * c] + __ldg(a.bias + 4 * c), v[4 * c + 1] + __ldg(a.bias + 4 * c + 1),
+                               v[4 * c + 2] + __ldg(a.bias + 4 * c + 2), v[4 * c + 3] + __ldg(a.bias + 4 * c + 3));
       } else {
         __align__(16) __nv_bfloat16 out[COUT];
         if (MODE == CONV_RELU_BF16) {
@@ -197,65 +203,199 @@ __global__ void __launch_bounds__(TILE) k_conv(ConvArgs a) {
 // features, output, loss
 // ---------------------------------------------------------------------------
 
-// Per control point: diagonal block of K and its block-Jacobi inverse are
-// given; writes the 14 features (BF16, 16 channels).  s = RMS of r, d = mean
-// diagonal entry (both on the device).
-__global__ void k_features(int P, const float* __restrict__ K, const float* __restrict__ Dinv,
-                           const uint8_t* __restrict__ pinned, const float* __restrict__ r,
-                           const double* __restrict__ scales, __nv_bfloat16* __restrict__ X0) {
+// Matrix features (BF16, 32 channels) and the inverse Cholesky factor of the
+// diagonal block (Linv, 6 lower entries 00 10 11 20 21 22) of every control
+// point; d = scales[1].
+__global__ void k_matrix_features(int P, const float* __restrict__ K, const uint8_t* __restrict__ pinned,
+                                  const double* __restrict__ scales, __nv_bfloat16* __restrict__ X0,
+                                  float* __restrict__ Linv, int* __restrict__ status) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  // s = 0 only for r = 0, whose features are then all zero
-  const float is = scales[0] > 0.0 ? (float)(1.0 / scales[0]) : 0.0f, d = (float)scales[1],
-              id = (float)(1.0 / scales[1]);
-  float rr[3], zr[3], f[16];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) rr[c] = r[(size_t)c * P + p];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    zr[c] = Dinv[(size_t)(3 * c) * P + p] * rr[0] + Dinv[(size_t)(3 * c + 1) * P + p] * rr[1] +
-            Dinv[(size_t)(3 * c + 2) * P + p] * rr[2];
-  const int slot = 12;  // du = dv = 0
-  const float k00 = K[(size_t)(slot * 9 + 0) * P + p], k01 = K[(size_t)(slot * 9 + 1) * P + p],
-              k02 = K[(size_t)(slot * 9 + 2) * P + p], k11 = K[(size_t)(slot * 9 + 4) * P + p],
-              k12 = K[(size_t)(slot * 9 + 5) * P + p], k22 = K[(size_t)(slot * 9 + 8) * P + p];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    f[c] = rr[c] * is;
-    f[3 + c] = zr[c] * d * is;
+  const double id = 1.0 / scales[1];
+  float f[32];
+  auto k = [&](int slot, int e) { return K[(size_t)(slot * 9 + e) * P + p]; };
+  const double a00 = k(12, 0), a01 = k(12, 1), a02 = k(12, 2), a11 = k(12, 4), a12 = k(12, 5), a22 = k(12, 8);
+  f[0] = (float)(a00 * id); f[1] = (float)(a01 * id); f[2] = (float)(a02 * id);
+  f[3] = (float)(a11 * id); f[4] = (float)(a12 * id); f[5] = (float)(a22 * id);
+  int c = 6;
+  for (int slot = 0; slot < 25; ++slot) {
+    if (slot == 12) continue;
+    f[c++] = (float)(((double)k(slot, 0) + (double)k(slot, 4) + (double)k(slot, 8)) * id);
   }
-  f[6] = k00 * id; f[7] = k01 * id; f[8] = k02 * id; f[9] = k11 * id; f[10] = k12 * id; f[11] = k22 * id;
-  f[12] = pinned[p] ? 1.0f : 0.0f;
-  f[13] = 1.0f;
-  f[14] = f[15] = 0.0f;
+  f[30] = pinned[p] ? 1.0f : 0.0f;
+  f[31] = 1.0f;
+  __align__(16) __nv_bfloat16 o[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) o[i] = __float2bfloat16_rn(f[i]);
+  uint4* dst = reinterpret_cast<uint4*>(X0 + (size_t)p * 32);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dst[i] = reinterpret_cast<const uint4*>(o)[i];
+  // Cholesky D = L L^T (FP64), then L^-1 (lower triangular)
+  const double l00 = sqrt(a00);
+  const double l10 = a01 / l00, l20 = a02 / l00;
+  const double l11 = sqrt(a11 - l10 * l10);
+  const double l21 = (a12 - l20 * l10) / l11;
+  const double l22 = sqrt(a22 - l20 * l20 - l21 * l21);
+  if (!(l00 > 0.0) || !(l11 > 0.0) || !(l22 > 0.0) || !isfinite(l22)) atomicOr(status, BSC_STATUS_NUMERIC_FLAG);
+  const double i00 = 1.0 / l00, i11 = 1.0 / l11, i22 = 1.0 / l22;
+  const double i10 = -l10 * i00 * i11;
+  const double i21 = -l21 * i11 * i22;
+  const double i20 = -(l20 * i00 + l21 * i10) * i22;
+  float* Li = Linv + (size_t)p * 6;
+  Li[0] = (float)i00; Li[1] = (float)i10; Li[2] = (float)i11; Li[3] = (float)i20; Li[4] = (float)i21; Li[5] = (float)i22;
+}
+
+__device__ __forceinline__ void linv_mul(const float* Li, const float x[3], float y[3]) {
+  y[0] = Li[0] * x[0];
+  y[1] = Li[1] * x[0] + Li[2] * x[1];
+  y[2] = Li[3] * x[0] + Li[4] * x[1] + Li[5] * x[2];
+}
+__device__ __forceinline__ void linvT_mul(const float* Li, const float x[3], float y[3]) {
+  y[0] = Li[0] * x[0] + Li[1] * x[1] + Li[3] * x[2];
+  y[1] = Li[2] * x[1] + Li[4] * x[2];
+  y[2] = Li[5] * x[2];
+}
+
+// a_t = RHO o_t / (1 + sum_s |o_s|) for t < 9 (channels 9..15 zero)
+__global__ void k_bound_taps(int P, const float* __restrict__ O, float* __restrict__ A) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float o[9], S = 1.0f;
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    o[t] = O[(size_t)p * 16 + t];
+    S += fabsf(o[t]);
+  }
+  const float f = RHO / S;
+  float* a = A + (size_t)p * 16;
+#pragma unroll
+  for (int t = 0; t < 9; ++t) a[t] = f * o[t];
+#pragma unroll
+  for (int t = 9; t < 16; ++t) a[t] = 0.0f;
+}
+
+// y = L^-1 P r
+__global__ void k_pc_y(int P, const float* __restrict__ Linv, const uint8_t* __restrict__ pinned,
+                       const float* __restrict__ r, float* __restrict__ y) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float x[3] = {0.0f, 0.0f, 0.0f}, o[3];
+  if (!pinned[p]) {
+    x[0] = r[p]; x[1] = r[(size_t)P + p]; x[2] = r[2 * (size_t)P + p];
+  }
+  linv_mul(Linv + (size_t)p * 6, x, o);
+  y[p] = o[0]; y[(size_t)P + p] = o[1]; y[2 * (size_t)P + p] = o[2];
+}
+
+// u(alpha) = y(alpha) + sum_t a_t(alpha) y(alpha + off_t)   (B y)
+__global__ void k_pc_B(int nu, int nv, const float* __restrict__ A, const float* __restrict__ y,
+                       float* __restrict__ u) {
+  const int P = nu * nv;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int i = p % nu, j = p / nu;
+  const float* ap = A + (size_t)p * 16;
+  float acc[3] = {y[p], y[(size_t)P + p], y[2 * (size_t)P + p]};
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const int ii = i + t % 3 - 1, jj = j + t / 3 - 1;
+    if (ii < 0 || ii >= nu || jj < 0 || jj >= nv) continue;
+    const int q = jj * nu + ii;
+    const float at = ap[t];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] += at * y[(size_t)c * P + q];
+  }
+  u[p] = acc[0]; u[(size_t)P + p] = acc[1]; u[2 * (size_t)P + p] = acc[2];
+}
+
+// z(alpha) = P L^-T (B^T u)(alpha),  (B^T u)(alpha) = u(alpha) + sum_t a_t(alpha - off_t) u(alpha - off_t)
+__global__ void k_pc_BTz(int nu, int nv, const float* __restrict__ A, const float* __restrict__ Linv,
+                         const uint8_t* __restrict__ pinned, const float* __restrict__ u, float* __restrict__ z) {
+  const int P = nu * nv;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  if (pinned[p]) {
+    z[p] = z[(size_t)P + p] = z[2 * (size_t)P + p] = 0.0f;
+    return;
+  }
+  const int i = p % nu, j = p / nu;
+  float v[3] = {u[p], u[(size_t)P + p], u[2 * (size_t)P + p]};
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const int ii = i - (t % 3 - 1), jj = j - (t / 3 - 1);
+    if (ii < 0 || ii >= nu || jj < 0 || jj >= nv) continue;
+    const int q = jj * nu + ii;
+    const float at = A[(size_t)q * 16 + t];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] += at * u[(size_t)c * P + q];
+  }
+  float o[3];
+  linvT_mul(Linv + (size_t)p * 6, v, o);
+  z[p] = o[0]; z[(size_t)P + p] = o[1]; z[2 * (size_t)P + p] = o[2];
+}
+
+// gv = L^-1 P g per control point (the adjoint of z = P L^-T v)
+__global__ void k_pc_gv(int P, const float* __restrict__ Linv, const uint8_t* __restrict__ pinned,
+                        const float* __restrict__ g, float* __restrict__ gv) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float x[3] = {0.0f, 0.0f, 0.0f}, o[3];
+  if (!pinned[p]) {
+    x[0] = g[p]; x[1] = g[(size_t)P + p]; x[2] = g[2 * (size_t)P + p];
+  }
+  linv_mul(Linv + (size_t)p * 6, x, o);
+  gv[p] = o[0]; gv[(size_t)P + p] = o[1]; gv[2 * (size_t)P + p] = o[2];
+}
+
+// dL/da_t(alpha) = gu(alpha) . y(alpha + off_t) + u(alpha) . gv(alpha + off_t), then through the
+// bound a_t = RHO o_t / S (S = 1 + sum |o|): dL/do_s = RHO (da_s / S - sign(o_s) sum_t da_t o_t / S^2),
+// written as the BF16 gradient of the network output.
+__global__ void k_pc_da(int nu, int nv, const float* __restrict__ O, const float* __restrict__ y,
+                        const float* __restrict__ u, const float* __restrict__ gv, const float* __restrict__ gu,
+                        __nv_bfloat16* __restrict__ dy) {
+  const int P = nu * nv;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int i = p % nu, j = p / nu;
   __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(f[c]);
-  uint4* dst = reinterpret_cast<uint4*>(X0 + (size_t)p * 16);
+  for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
+  float gup[3], up[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    gup[c] = gu[(size_t)c * P + p];
+    up[c] = u[(size_t)c * P + p];
+  }
+  float da[9], ov[9], S = 1.0f, dot = 0.0f;
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const int ii = i + t % 3 - 1, jj = j + t / 3 - 1;
+    float s = 0.0f;
+    if (ii >= 0 && ii < nu && jj >= 0 && jj < nv) {
+      const int q = jj * nu + ii;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) s += gup[c] * y[(size_t)c * P + q] + up[c] * gv[(size_t)c * P + q];
+    }
+    da[t] = s;
+    ov[t] = O[(size_t)p * 16 + t];
+    S += fabsf(ov[t]);
+    dot += s * ov[t];
+  }
+  const float iS = 1.0f / S;
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const float sg = ov[t] > 0.0f ? 1.0f : (ov[t] < 0.0f ? -1.0f : 0.0f);
+    o[t] = __float2bfloat16_rn(RHO * (da[t] * iS - sg * dot * iS * iS));
+  }
+  uint4* dst = reinterpret_cast<uint4*>(dy + (size_t)p * 16);
   dst[0] = reinterpret_cast<const uint4*>(o)[0];
   dst[1] = reinterpret_cast<const uint4*>(o)[1];
 }
 
-// z = D^-1 r + (s / d) y (zero at pinned points).
-__global__ void k_combine(int P, const float* __restrict__ Dinv, const uint8_t* __restrict__ pinned,
-                          const float* __restrict__ r, const float4* __restrict__ y,
-                          const double* __restrict__ scales, float* __restrict__ z) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  if (pinned[p]) {
-    z[p] = z[P + p] = z[2 * (size_t)P + p] = 0.0f;
-    return;
-  }
-  const float sd = (float)(scales[0] / scales[1]);
-  const float4 yy = y[p];
-  const float yv[3] = {yy.x, yy.y, yy.z};
-  float rr[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) rr[c] = r[(size_t)c * P + p];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    z[(size_t)c * P + p] = Dinv[(size_t)(3 * c) * P + p] * rr[0] + Dinv[(size_t)(3 * c + 1) * P + p] * rr[1] +
-                           Dinv[(size_t)(3 * c + 2) * P + p] * rr[2] + sd * yv[c];
+// g = 2 K e / (x^T K x) in place (dsc[1] = x^T K x)
+__global__ void k_scale_g(int n, const double* __restrict__ dsc, float* __restrict__ g) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) g[k] = (float)(2.0 * (double)g[k] / dsc[1]);
 }
 
 template <int BLOCK>
@@ -399,25 +539,6 @@ __global__ void k_sub(int n, const float* __restrict__ a, const float* __restric
   if (k < n) out[k] = a[k] - b[k];
 }
 
-// dy4[p][c] = (s / d) * 2 (K e)[c][p] / (x*^T K x*) for c < 3, zero elsewhere and at pins.
-__global__ void k_dy4(int P, const uint8_t* __restrict__ pinned, const float* __restrict__ Ke,
-                      const double* __restrict__ scales, const double* __restrict__ dsc,
-                      __nv_bfloat16* __restrict__ dy4) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  const double f = 2.0 * (scales[0] / scales[1]) / dsc[1];
-  __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
-  if (!pinned[p]) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) o[c] = __float2bfloat16_rn((float)(f * (double)Ke[(size_t)c * P + p]));
-  }
-  uint4* dst = reinterpret_cast<uint4*>(dy4 + (size_t)p * 16);
-  dst[0] = reinterpret_cast<const uint4*>(o)[0];
-  dst[1] = reinterpret_cast<const uint4*>(o)[1];
-}
-
 // Adam on the FP32 master parameters.
 __global__ void k_adam(int n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -445,22 +566,6 @@ __global__ void k_layout(int CIN, int COUT, const float* __restrict__ W, uint8_t
 }
 
 // ---- flexible CG pieces ----------------------------------------------------
-// x += a p, r -= a q with a = dsc[0] / dsc[1] (p.r / p.q)
-__global__ void k_fcg_xr(int n, const double* __restrict__ dsc, const float* __restrict__ p,
-                         const float* __restrict__ q, float* __restrict__ x, float* __restrict__ r) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const float a = (float)(dsc[0] / dsc[1]);
-  x[k] += a * p[k];
-  r[k] -= a * q[k];
-}
-// p = z + b p with b = -dsc[2] / dsc[1] (-(z.q) / p.q)
-__global__ void k_fcg_p(int n, const double* __restrict__ dsc, const float* __restrict__ z, float* __restrict__ p) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const float b = (float)(-dsc[2] / dsc[1]);
-  p[k] = z[k] + b * p[k];
-}
 __global__ void k_copy_f(int n, const float* __restrict__ a, float* __restrict__ b) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) b[k] = a[k];
@@ -468,6 +573,80 @@ __global__ void k_copy_f(int n, const float* __restrict__ a, float* __restrict__
 __global__ void k_add_f(int n, const float* __restrict__ a, float* __restrict__ b) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) b[k] += a[k];
+}
+
+// partial[blk] = a.b and partial[G + blk] = c.d over the block's slice.
+__global__ void __launch_bounds__(RB) k_dot2_partials(int n, const float* __restrict__ a, const float* __restrict__ b,
+                                                      const float* __restrict__ c, const float* __restrict__ d,
+                                                      double* __restrict__ partial) {
+  __shared__ double sm[RB / 32];
+  double s1 = 0.0, s2 = 0.0;
+  for (int k = blockIdx.x * RB + threadIdx.x; k < n; k += gridDim.x * RB) {
+    s1 += (double)a[k] * (double)b[k];
+    s2 += (double)c[k] * (double)d[k];
+  }
+  const double t1 = block_sum<RB>(s1, sm);
+  const double t2 = block_sum<RB>(s2, sm);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = t1;
+    partial[gridDim.x + blockIdx.x] = t2;
+  }
+}
+
+__global__ void __launch_bounds__(RB) k_sum2_to(int n, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sm[RB / 32];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < n; k += RB) {
+    a += partial[k];
+    b += partial[n + k];
+  }
+  const double t1 = block_sum<RB>(a, sm);
+  const double t2 = block_sum<RB>(b, sm);
+  if (threadIdx.x == 0) {
+    out[0] = t1;
+    out[1] = t2;
+  }
+}
+
+// r.r of the flexible CG: dsc[3] = r.r, the feature scale s = RMS of r, and
+// the converged flag (flag[0] = 1, flag[1] = iteration) once r.r <= stop.
+__global__ void __launch_bounds__(RB) k_sum_rr(int n, int P, const double* __restrict__ partial,
+                                               double* __restrict__ dsc, double* __restrict__ scales, double stop,
+                                               int it, int* __restrict__ flag) {
+  __shared__ double sm[RB / 32];
+  double a = 0.0;
+  for (int k = threadIdx.x; k < n; k += RB) a += partial[k];
+  const double t = block_sum<RB>(a, sm);
+  if (threadIdx.x == 0) {
+    dsc[3] = t;
+    scales[0] = sqrt(t / (3.0 * P));
+    if (flag[0] == 0 && (t <= stop || !(dsc[1] > 0.0) || !isfinite(t))) {
+      flag[0] = (t <= stop) ? 1 : 2;  // 2: breakdown (no positive curvature or non-finite)
+      flag[1] = it;
+    }
+  }
+}
+
+// x += a p, r -= a q (a = p.r / p.q) unless the solve has finished.
+__global__ void k_fcg_xr_g(int n, const double* __restrict__ dsc, const int* __restrict__ flag,
+                           const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ x,
+                           float* __restrict__ r) {
+  if (flag[0] || !(dsc[1] > 0.0)) return;  // finished, or no positive curvature (k_sum_rr flags it)
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float a = (float)(dsc[0] / dsc[1]);
+  x[k] += a * p[k];
+  r[k] -= a * q[k];
+}
+
+// p = z + b p (b = -z.q / p.q) unless the solve has finished.
+__global__ void k_fcg_p_g(int n, const double* __restrict__ dsc, const int* __restrict__ flag,
+                          const float* __restrict__ z, float* __restrict__ p) {
+  if (flag[0]) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float b = (float)(-dsc[2] / dsc[1]);
+  p[k] = z[k] + b * p[k];
 }
 
 }  // namespace
@@ -490,16 +669,20 @@ struct bsc_cnn {
   __nv_bfloat16* act[3];       // outputs of layers 1..3
   __nv_bfloat16* g0;           // gradient buffers
   __nv_bfloat16* g1;
-  __nv_bfloat16* dy4;
-  float4* y4;
-  float* Dinv;
+  __nv_bfloat16* dy4;          // gradient of the network output (BF16, 16 channels)
+  float* O;                    // network output o, FP32 [P][16]
+  float* A;                    // bounded tap coefficients a, FP32 [P][16]
+  float* Linv;                 // inverse Cholesky factor of each diagonal block [P][6]
+  float* py;                   // y = L^-1 P r, u = B y of the last application
+  float* pu;
   const float* K;
   double* scales;              // [0] RMS of the residual, [1] mean diagonal entry
   double* dsc;                 // device scalars
   double* hsc;                 // pinned host scalars
   double* red;                 // reduction partials
+  int* flag;                   // [4] flexible CG: converged / breakdown flag, iteration
   float* wpart;                // weight-gradient partials
-  float* vec[6];               // FCG: r, z, p, q, e, spare (3 planes of P)
+  float* vec[8];               // FCG: r, z, p, q, d; training: e, K e, K x (3 planes of P)
   int conv_grid;
   int red_grid;
 };
@@ -536,14 +719,6 @@ cudaError_t conv_setup() {
                               (int)conv_smem<CIN, COUT>());
 }
 
-// s = RMS of r into scales[0]
-cudaError_t rms(bsc_cnn* n, const float* r) {
-  BSC_COUNT(n->c, 2);
-  k_dot_partials<<<n->red_grid, RB, 0, n->c->stream>>>(3 * n->P, r, r, n->red);
-  k_sum_to<<<1, RB, 0, n->c->stream>>>(n->red_grid, n->red, n->scales, 0, 3.0 * n->P);
-  return cudaGetLastError();
-}
-
 cudaError_t dot(bsc_cnn* n, const float* a, const float* b, double* out_slot) {
   BSC_COUNT(n->c, 2);
   k_dot_partials<<<n->red_grid, RB, 0, n->c->stream>>>(3 * n->P, a, b, n->red);
@@ -551,24 +726,32 @@ cudaError_t dot(bsc_cnn* n, const float* a, const float* b, double* out_slot) {
   return cudaGetLastError();
 }
 
-// z = P(r) for the prepared matrix (activations kept for the backward pass)
-cudaError_t cnn_forward(bsc_cnn* n, const float* r, float* z) {
+// Network on the prepared features: tap coefficients A (activations kept
+// for the backward pass).
+cudaError_t cnn_network(bsc_cnn* n) {
   cudaError_t e;
-  const int P = n->P, B = 256, G = (P + B - 1) / B;
-  if ((e = rms(n, r)) != cudaSuccess) return e;
-  BSC_COUNT(n->c, 2);
-  k_features<<<G, B, 0, n->c->stream>>>(P, n->K, n->Dinv, n->c->pinned, r, n->scales, n->X0);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const float* p = n->params;
-  if ((e = conv<16, 32, CONV_RELU_BF16>(n, n->X0, n->Wb[0], p + n->off[0] + w_count(0), nullptr, n->act[0], 0)))
+  if ((e = conv<32, 32, CONV_RELU_BF16>(n, n->X0, n->Wb[0], p + n->off[0] + w_count(0), nullptr, n->act[0], 0)))
     return e;
   if ((e = conv<32, 32, CONV_RELU_BF16>(n, n->act[0], n->Wb[1], p + n->off[1] + w_count(1), nullptr, n->act[1], 0)))
     return e;
   if ((e = conv<32, 32, CONV_RELU_BF16>(n, n->act[1], n->Wb[2], p + n->off[2] + w_count(2), nullptr, n->act[2], 0)))
     return e;
-  if ((e = conv<32, 16, CONV_LINEAR_F32>(n, n->act[2], n->Wb[3], p + n->off[3] + w_count(3), nullptr, n->y4, 0)))
+  if ((e = conv<32, 16, CONV_LINEAR_F32>(n, n->act[2], n->Wb[3], p + n->off[3] + w_count(3), nullptr, n->O, 0)))
     return e;
-  k_combine<<<G, B, 0, n->c->stream>>>(P, n->Dinv, n->c->pinned, r, n->y4, n->scales, z);
+  BSC_COUNT(n->c, 1);
+  k_bound_taps<<<(n->P + 255) / 256, 256, 0, n->c->stream>>>(n->P, n->O, n->A);
+  return cudaGetLastError();
+}
+
+// z = M r = P L^-T B^T B L^-1 P r with the current tap coefficients
+// (y = L^-1 P r and u = B y stay in py, pu).
+cudaError_t precondition(bsc_cnn* n, const float* r, float* z) {
+  const int B = 256, G = (n->P + B - 1) / B;
+  BSC_COUNT(n->c, 3);
+  k_pc_y<<<G, B, 0, n->c->stream>>>(n->P, n->Linv, n->c->pinned, r, n->py);
+  k_pc_B<<<G, B, 0, n->c->stream>>>(n->nu, n->nv, n->A, n->py, n->pu);
+  k_pc_BTz<<<G, B, 0, n->c->stream>>>(n->nu, n->nv, n->A, n->Linv, n->c->pinned, n->pu, z);
   return cudaGetLastError();
 }
 
@@ -581,20 +764,25 @@ cudaError_t wgrad(bsc_cnn* n, int l, const __nv_bfloat16* X, const __nv_bfloat16
   return cudaGetLastError();
 }
 
-// loss = (z - x*)^T K (z - x*) / x*^T K x* and the parameter gradient.
+// loss = (z - x*)^T K (z - x*) / x*^T K x* (z = M r) and the parameter gradient.
 cudaError_t cnn_loss_grad(bsc_cnn* n, const float* r, const float* xs) {
   cudaError_t e;
   const int P = n->P, N3 = 3 * P, B = 256, G3 = (N3 + B - 1) / B, G = (P + B - 1) / B;
-  float *z = n->vec[1], *ev = n->vec[4], *Ke = n->vec[3], *Kx = n->vec[5];
-  if ((e = cnn_forward(n, r, z)) != cudaSuccess) return e;
+  float *z = n->vec[1], *ev = n->vec[5], *Ke = n->vec[6], *Kx = n->vec[7], *gv = n->vec[2], *gu = n->vec[3];
+  if ((e = cnn_network(n)) != cudaSuccess) return e;
+  if ((e = precondition(n, r, z)) != cudaSuccess) return e;
   BSC_COUNT(n->c, 1);
   k_sub<<<G3, B, 0, n->c->stream>>>(N3, z, xs, ev);
   if ((e = launch_spmv(n->c, n->K, ev, Ke)) != cudaSuccess) return e;
   if ((e = launch_spmv(n->c, n->K, xs, Kx)) != cudaSuccess) return e;
   if ((e = dot(n, ev, Ke, n->dsc + 0)) != cudaSuccess) return e;  // e^T K e
   if ((e = dot(n, xs, Kx, n->dsc + 1)) != cudaSuccess) return e;  // x*^T K x*
-  BSC_COUNT(n->c, 1);
-  k_dy4<<<G, B, 0, n->c->stream>>>(P, n->c->pinned, Ke, n->scales, n->dsc, n->dy4);
+  // g = dL/dz = 2 K e / x*^T K x*, then back through z = P L^-T B^T B L^-1 P r
+  BSC_COUNT(n->c, 4);
+  k_scale_g<<<G3, B, 0, n->c->stream>>>(N3, n->dsc, Ke);
+  k_pc_gv<<<G, B, 0, n->c->stream>>>(P, n->Linv, n->c->pinned, Ke, gv);
+  k_pc_B<<<G, B, 0, n->c->stream>>>(n->nu, n->nv, n->A, gv, gu);
+  k_pc_da<<<G, B, 0, n->c->stream>>>(n->nu, n->nv, n->O, n->py, n->pu, gv, gu, n->dy4);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // layer 4
   if ((e = wgrad<32, 16>(n, 3, n->act[2], n->dy4)) != cudaSuccess) return e;
@@ -606,7 +794,7 @@ cudaError_t cnn_loss_grad(bsc_cnn* n, const float* r, const float* xs) {
   if ((e = wgrad<32, 32>(n, 1, n->act[0], n->g1)) != cudaSuccess) return e;
   if ((e = conv<32, 32, CONV_MASK_BF16>(n, n->g1, n->Wt[1], nullptr, n->act[0], n->g0, 1)) != cudaSuccess) return e;
   // layer 1
-  return wgrad<16, 32>(n, 0, n->X0, n->g0);
+  return wgrad<32, 32>(n, 0, n->X0, n->g0);
 }
 
 cudaError_t relayout(bsc_cnn* n) {
@@ -636,7 +824,7 @@ bsc_status cnn_sync(bsc_cnn* n, const char* where) {
 void cnn_free(bsc_cnn* n) {
   if (!n) return;
   void* ptrs[] = {n->params, n->grads, n->adam_m, n->adam_v, n->X0, n->act[0], n->act[1], n->act[2], n->g0,
-                  n->g1, n->dy4, n->y4, n->Dinv, n->scales, n->dsc, n->red, n->wpart};
+                  n->g1, n->dy4, n->O, n->A, n->Linv, n->py, n->pu, n->scales, n->dsc, n->red, n->wpart, n->flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int l = 0; l < NL; ++l) {
@@ -686,26 +874,29 @@ bsc_status bsc_cnn_create(bsc_ctx* c, bsc_cnn** out) {
     CA(n->Wb[l], (size_t)w_count(l) * 2);
     if (l > 0) CA(n->Wt[l], (size_t)w_count(l) * 2);
   }
-  CA(n->X0, P * 16 * 2);
+  CA(n->X0, P * 32 * 2);
   for (int k = 0; k < 3; ++k) CA(n->act[k], P * 32 * 2);
   CA(n->g0, P * 32 * 2);
   CA(n->g1, P * 32 * 2);
   CA(n->dy4, P * 16 * 2);
-  CA(n->y4, P * 16);
-  CA(n->Dinv, P * 9 * 4);
+  CA(n->O, P * 16 * 4);
+  CA(n->A, P * 16 * 4);
+  CA(n->Linv, P * 6 * 4);
+  CA(n->py, 3 * P * 4);
+  CA(n->pu, 3 * P * 4);
   CA(n->scales, 8 * sizeof(double));
   CA(n->dsc, 16 * sizeof(double));
+  CA(n->flag, 4 * sizeof(int));
   n->red_grid = 2 * c->num_sms;
   CA(n->red, 4 * (size_t)n->red_grid * sizeof(double));
   CA(n->wpart, (size_t)((n->P + WG_CHUNK - 1) / WG_CHUNK) * (9 * 32 * 32 + 32) * 4);
-  for (int k = 0; k < 6; ++k) CA(n->vec[k], 3 * P * 4);
+  for (int k = 0; k < 8; ++k) CA(n->vec[k], 3 * P * 4);
 #undef CA
   if (e == cudaSuccess) e = cudaMallocHost((void**)&n->hsc, 16 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(n->params, 0, NP * 4);
   if (e == cudaSuccess) e = cudaMemset(n->adam_m, 0, NP * 4);
   if (e == cudaSuccess) e = cudaMemset(n->adam_v, 0, NP * 4);
   if (e == cudaSuccess) e = cudaMemset(n->grads, 0, NP * 4);
-  if (e == cudaSuccess) e = conv_setup<16, 32, CONV_RELU_BF16>();
   if (e == cudaSuccess) e = conv_setup<32, 32, CONV_RELU_BF16>();
   if (e == cudaSuccess) e = conv_setup<32, 16, CONV_LINEAR_F32>();
   if (e == cudaSuccess) e = conv_setup<16, 32, CONV_MASK_BF16>();
@@ -759,17 +950,19 @@ bsc_status bsc_cnn_get_params(bsc_cnn* n, float* host, int count, int which) {
 bsc_status bsc_cnn_prepare(bsc_cnn* n, const void* K) {
   if (!n || !K) return BSC_ERR_INVALID_ARG;
   n->K = (const float*)K;
-  CKN(launch_block_jacobi(n->c, K, n->Dinv), "bsc_cnn_prepare");
-  BSC_COUNT(n->c, 2);
+  const int B = 256, G = (n->P + B - 1) / B;
+  BSC_COUNT(n->c, 3);
   k_diag_partials<<<n->red_grid, RB, 0, n->c->stream>>>(n->P, n->K, n->c->pinned, n->red);
   k_diag_mean<<<1, RB, 0, n->c->stream>>>(n->red_grid, n->red, n->scales);
+  k_matrix_features<<<G, B, 0, n->c->stream>>>(n->P, n->K, n->c->pinned, n->scales, n->X0, n->Linv, n->c->dstatus);
   CKN(cudaGetLastError(), "bsc_cnn_prepare");
+  CKN(cnn_network(n), "bsc_cnn_prepare");
   return cnn_sync(n, "bsc_cnn_prepare");
 }
 
 bsc_status bsc_cnn_apply(bsc_cnn* n, const void* r, void* z) {
   if (!n || !r || !z || !n->K) return BSC_ERR_INVALID_ARG;
-  CKN(cnn_forward(n, (const float*)r, (float*)z), "bsc_cnn_apply");
+  CKN(precondition(n, (const float*)r, (float*)z), "bsc_cnn_apply");
   return cnn_sync(n, "bsc_cnn_apply");
 }
 
@@ -803,10 +996,10 @@ bsc_status bsc_cnn_activations(bsc_cnn* n, int which, float* host) {
   if (!n || !host || which < 0 || which > 4) return BSC_ERR_INVALID_ARG;
   const size_t P = (size_t)n->P;
   if (which == 4) {
-    CKN(cudaMemcpyAsync(host, n->y4, P * 16, cudaMemcpyDeviceToHost, n->c->stream), "bsc_cnn_activations");
+    CKN(cudaMemcpyAsync(host, n->O, P * 16 * 4, cudaMemcpyDeviceToHost, n->c->stream), "bsc_cnn_activations");
     return cnn_sync(n, "bsc_cnn_activations");
   }
-  const int ch = which == 0 ? 16 : 32;
+  const int ch = 32;
   std::vector<__nv_bfloat16> tmp(P * ch);
   CKN(cudaMemcpyAsync(tmp.data(), which == 0 ? n->X0 : n->act[which - 1], P * ch * 2, cudaMemcpyDeviceToHost,
                       n->c->stream),
@@ -835,7 +1028,7 @@ bsc_status bsc_solve_fcg(bsc_ctx* c, bsc_cnn* n, const void* K, const void* b, v
   BSC_COUNT(c, 1);
   k_copy_f<<<G3, B, 0, s>>>(N3, (const float*)b, r);
   CKN(dot(n, r, r, n->dsc + 4), "bsc_solve_fcg");  // b.b
-  CKN(cnn_forward(n, r, z), "bsc_solve_fcg");
+  CKN(precondition(n, r, z), "bsc_solve_fcg");
   BSC_COUNT(c, 1);
   k_copy_f<<<G3, B, 0, s>>>(N3, z, p);
   CKN(cudaMemcpyAsync(n->hsc + 4, n->dsc + 4, sizeof(double), cudaMemcpyDeviceToHost, s), "bsc_solve_fcg");
@@ -846,37 +1039,47 @@ bsc_status bsc_solve_fcg(bsc_ctx* c, bsc_cnn* n, const void* K, const void* b, v
     return BSC_OK;
   }
   const double stop = tol * tol * bb;
+  CKN(cudaMemsetAsync(n->flag, 0, 4 * sizeof(int), s), "bsc_solve_fcg");
+  // Iterations run without host synchronisation; every CHECK iterations the
+  // host reads r.r and the flag.  After convergence (or breakdown) the
+  // remaining launches of the block leave x and r unchanged.
+  constexpr int CHECK = 4;
   double best = bb, rr = bb;
-  int it = 0, since_best = 0;
-  const int window = 25;
+  int it = 0, since_best = 0, done_it = 0, flag = 0;
+  const int window = 24;
   bool stalled = false;
   for (it = 1; it <= maxit; ++it) {
     CKN(launch_spmv(c, K, p, q), "bsc_solve_fcg");
-    CKN(dot(n, p, r, n->dsc + 0), "bsc_solve_fcg");
-    CKN(dot(n, p, q, n->dsc + 1), "bsc_solve_fcg");
-    BSC_COUNT(c, 1);
-    k_fcg_xr<<<G3, B, 0, s>>>(N3, n->dsc, p, q, xx, r);
-    CKN(dot(n, r, r, n->dsc + 3), "bsc_solve_fcg");
-    CKN(cudaMemcpyAsync(n->hsc, n->dsc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s), "bsc_solve_fcg");
-    if ((st = cnn_sync(n, "bsc_solve_fcg")) != BSC_OK) return st;
-    rr = n->hsc[3];
-    if (!(n->hsc[1] > 0.0) || !isfinite(rr)) {
-      stalled = true;
-      break;
-    }
-    if (rr <= stop) break;
-    if (rr < 0.25 * best) {
-      best = rr;
-      since_best = 0;
-    } else if (++since_best >= window) {
-      stalled = true;  // no halving of the residual norm in `window` iterations
-      break;
-    }
-    CKN(cnn_forward(n, r, z), "bsc_solve_fcg");
+    BSC_COUNT(c, 5);
+    k_dot2_partials<<<n->red_grid, RB, 0, s>>>(N3, p, r, p, q, n->red);
+    k_sum2_to<<<1, RB, 0, s>>>(n->red_grid, n->red, n->dsc);
+    k_fcg_xr_g<<<G3, B, 0, s>>>(N3, n->dsc, n->flag, p, q, xx, r);
+    k_dot_partials<<<n->red_grid, RB, 0, s>>>(N3, r, r, n->red);
+    k_sum_rr<<<1, RB, 0, s>>>(n->red_grid, n->P, n->red, n->dsc, n->scales, stop, it, n->flag);
+    CKN(precondition(n, r, z), "bsc_solve_fcg");
     CKN(dot(n, z, q, n->dsc + 2), "bsc_solve_fcg");
     BSC_COUNT(c, 1);
-    k_fcg_p<<<G3, B, 0, s>>>(N3, n->dsc, z, p);
+    k_fcg_p_g<<<G3, B, 0, s>>>(N3, n->dsc, n->flag, z, p);
+    if (it % CHECK == 0 || it == maxit) {
+      CKN(cudaMemcpyAsync(n->hsc, n->dsc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s), "bsc_solve_fcg");
+      CKN(cudaMemcpyAsync(n->hsc + 8, n->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "bsc_solve_fcg");
+      if ((st = cnn_sync(n, "bsc_solve_fcg")) != BSC_OK) return st;
+      rr = n->hsc[3];
+      const int* hf = reinterpret_cast<const int*>(n->hsc + 8);
+      flag = hf[0];
+      done_it = hf[1];
+      if (flag) break;
+      if (rr < 0.25 * best) {
+        best = rr;
+        since_best = 0;
+      } else if ((since_best += CHECK) >= window) {
+        stalled = true;  // no 4x drop of r.r in `window` iterations
+        break;
+      }
+    }
   }
+  if (flag == 1) it = done_it;
+  if (flag == 2) stalled = true;
   R.fcg_iters = it > maxit ? maxit : it;
   R.rel_res = sqrt(rr / bb);
   if (stalled || !(rr <= stop)) {

@@ -337,3 +337,11 @@ cudaError_t launch_build_tables(bsc_ctx* c) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return e;
 }
+
+// Recomputes the lumped masses of patch p (after a density change).
+cudaError_t launch_lumped_mass_patch(bsc_ctx* c, int p) {
+  const PatchDev& q = c->hpd[p];
+  BSC_COUNT(c, 1);
+  k_lumped_mass<<<(q.N + 127) / 128, 128, 0, c->stream>>>(q.nu, q.nv, q.cp0, c->N, c->rest, q.rho, c->mass);
+  return cudaGetLastError();
+}

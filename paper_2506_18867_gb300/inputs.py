@@ -258,6 +258,26 @@ def config_batch(seed: int = 1, count: int = 64, lo: int = 16, hi: int = 192, sp
     return out
 
 
+def config_learned(seed: int = 1, n: int = 512, size_m: float = 1.0) -> Patch:
+    """Newton system for the learned preconditioner: n x n patch, size_m
+    square, E = 1e5 Pa, nu = 0.3, h = 1 mm, 200 kg/m^2, dt = 0.01 s, gravity
+    -y, the two top corners pinned.  The membrane / bending stiffness ratio
+    mu_st h_span^2 / mu_bd is log-uniform in [1e3, 1e5] (h_span the span
+    length); the state is the rest plus sigma = 1 mm noise and a seeded
+    multi-frequency wrinkle field."""
+    u = uniform(seed ^ 0x1EA4, 2)
+    ratio = math.exp(math.log(1e3) + u[0] * (math.log(1e5) - math.log(1e3)))
+    span = size_m / (n - 2)
+    rest = flat_rest(n, n, size_m, size_m)
+    C = lift(rest)
+    C += 1e-3 * normal(seed * 104729 + 7, C.size).reshape(C.shape)
+    C[:, 2] += wrinkle_field(seed, rest, span, k=6)
+    mat = Material.from_engineering(1e5, 0.3, 1e-3, 200.0)
+    mat.mu_bd = mat.mu_st1 * span * span / ratio
+    return Patch(f"learned{n}", n, n, rest, C, C.copy(), mat, 0.01, (0.0, -9.81, 0.0), corner_pins_top(n, n),
+                 {"seed": seed, "ratio": ratio, "span_m": span})
+
+
 def crop(patch: Patch, mu: int, mv: int | None = None) -> Patch:
     """The leading mu x mv control points of a patch (same span length, same
     state, pins restricted to the crop): a bounded sample of a large workload."""

@@ -1,12 +1,12 @@
 """Learned preconditioner on the GPU against the FP64 NumPy oracle
 (oracle/cnn_oracle.py), through the C ABI.
 
-The GPU keeps activations and back-propagated gradients in BF16 and
-accumulates in FP32 on the tensor cores; the oracle is run with the same BF16
-rounding points (bf16_like=True), so the two differ by FP32 accumulation
-order and the BF16 rounding flips it causes: about 2^-8 relative on the
-elements where a flip happens, norm-wise well under 1e-2.  Grid 40 x 23
-(920 pixels: seven full 128-pixel tiles and a ragged tail of 24).
+The GPU keeps features, activations and back-propagated gradients in BF16
+and accumulates in FP32 on the tensor cores; the oracle is run with the same
+BF16 rounding points (bf16_like=True), so the two differ by FP32 accumulation
+order and the BF16 rounding flips it causes (2^-8 relative on a flipped
+element): norm-wise well under 1e-2.  Grid 40 x 23 (920 pixels: seven full
+128-pixel tiles and a ragged tail of 24).
 """
 import numpy as np
 import pytest
@@ -64,30 +64,42 @@ def n3(t):
     return t.double().cpu().numpy().reshape(3, -1).T.copy()
 
 
-def test_forward_layers_match_oracle(system):
+def test_network_and_preconditioner_match_oracle(system):
     pat, ctx, net, K, r, xs, prep = system
-    params = random_params(1)
+    params = random_params(1, last_scale=0.3)
     net.set_params(params)
     net.prepare(K)
     z = net.apply(r)
     zo, cache = co.forward(params, prep, n3(r), bf16_like=True)
     f_gpu = net.activations(0)
-    f_or = cache["acts"][0].reshape(-1, 16)
-    assert rel(f_gpu, f_or) < 4e-3                      # one BF16 rounding of FP32 vs FP64 features
-    errs = []
-    for l in (1, 2, 3):
-        a = net.activations(l)
-        errs.append(rel(a, cache["acts"][l].reshape(-1, 32)))
-    y = net.activations(4)[:, :3]
-    errs.append(rel(y, cache["acts"][4].reshape(-1, 16)[:, :3]))
+    f_or = cache["acts"][0].reshape(-1, 32)
+    ef = rel(f_gpu, f_or)
+    errs = [rel(net.activations(l), cache["acts"][l].reshape(-1, 32)) for l in (1, 2, 3)]
+    ea = rel(net.activations(4)[:, :9], cache["o"])
     ez = rel(n3(z), zo)
-    print("feature / layer / output rel errors:", rel(f_gpu, f_or), errs, "z:", ez)
-    assert max(errs) < 1e-2 and ez < 1e-2
+    print("features", ef, "layers", errs, "taps", ea, "z", ez)
+    assert ef < 4e-3 and max(errs) < 1e-2 and ea < 1e-2 and ez < 1e-2
+
+
+def test_preconditioner_is_symmetric_on_the_gpu(system):
+    pat, ctx, net, K, r, xs, prep = system
+    net.set_params(random_params(5, last_scale=0.3))
+    net.prepare(K)
+    g = torch.Generator("cuda").manual_seed(9)
+    x = torch.randn((3, ctx.N), device="cuda", generator=g)
+    y = torch.randn((3, ctx.N), device="cuda", generator=g)
+    pins = torch.as_tensor(pat.pinned, device="cuda", dtype=torch.long)
+    x[:, pins] = 0.0
+    y[:, pins] = 0.0
+    Mx, My = net.apply(x.contiguous()), net.apply(y.contiguous())
+    a, b = float((y * Mx).double().sum()), float((x * My).double().sum())
+    assert abs(a - b) <= 1e-5 * max(abs(a), abs(b))
+    assert float((x * Mx).double().sum()) > 0.0
 
 
 def test_gradients_match_oracle(system):
     pat, ctx, net, K, r, xs, prep = system
-    params = random_params(2, last_scale=3.0)
+    params = random_params(2, last_scale=0.3)
     net.set_params(params)
     net.prepare(K)
     L = net.loss_grad(r, xs)
@@ -114,9 +126,9 @@ def test_zero_weights_reproduce_block_jacobi(system):
     assert abs(rep["fcg_iters"] - it) <= 2, (rep, it)
 
 
-def test_fcg_converges_with_a_random_network_or_falls_back(system):
+def test_fcg_converges_with_a_random_network(system):
     pat, ctx, net, K, r, xs, prep = system
-    net.set_params(random_params(3, scale=1.0))
+    net.set_params(random_params(3, last_scale=0.3))
     x, rep = net.solve(r, K, rel_tol=1e-8)
     assert rep["rel_res"] <= 1e-8
     res = n3(ctx.spmv(x, K=K)) - n3(r)
@@ -126,10 +138,11 @@ def test_fcg_converges_with_a_random_network_or_falls_back(system):
 
 def test_adam_steps_reduce_the_loss(system):
     pat, ctx, net, K, r, xs, prep = system
-    net.set_params(np.zeros(co.param_count()))
+    params = random_params(4, scale=0.5, last_scale=0.0)
+    net.set_params(params)
     net.prepare(K)
     L0 = net.loss_grad(r, xs)
-    for _ in range(30):
+    for _ in range(40):
         net.loss_grad(r, xs)
         net.adam_step(1e-3)
     L1 = net.loss_grad(r, xs)

@@ -21,7 +21,9 @@ independent patches (sides uniform in 16..192, per-patch materials and rest
 rotations) stepped together - one launch per phase, the persistent PCG split
 into per-patch block groups, the Newton iteration replayed from a CUDA graph,
 tile shapes from the autotuner.  The default drape line also carries a short
-measurement of that workload under ``batched``.
+measurement of that workload under ``batched``, and under ``learned`` the
+learned preconditioner on held-out 512 x 512 Newton systems (block-Jacobi
+PCG vs flexible CG with the trained network, iterations and ms to 1e-8).
 
 ``--impl reference`` times the oracle itself (the reference arm).
 """
@@ -73,6 +75,7 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-garment sub-measurement")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner sub-measurement")
     return p.parse_args()
 
 
@@ -330,6 +333,9 @@ def run_gpu(args):
     batched = None
     if args.workload != "batch64" and not args.no_batch and prec == bsc.FP32:
         batched = measure_batch(bsc, flush, stream, torch, np, seed=1 + rank)
+    learned = None
+    if args.workload == "drape256" and not args.no_learned and prec == bsc.FP32 and rank == 0:
+        learned = measure_learned(bsc, np)
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
@@ -384,6 +390,7 @@ def run_gpu(args):
                          "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); no FP64 peak in the measured peaks"},
             "fp64": fp64,
             "batched": batched,
+            "learned": learned,
             "cpu_baseline": cpu,
             "clocks": clk,
         }
@@ -413,6 +420,29 @@ def measure_batch(bsc, flush, stream, torch, np, seed=1, steps=3, warmup=2):
            "graph": ctx.graph_state(), "steps": steps}
     ctx.close()
     return out
+
+
+WEIGHTS = os.path.join(ROOT, "paper_2506_18867_gb300", "weights", "cnn_learned512.npz")
+
+
+def measure_learned(bsc, np, seeds=(1_000_000, 1_000_001, 1_000_002, 1_000_003), n=512):
+    """The learned preconditioner on held-out Newton systems of the 512 x 512
+    workload: block-Jacobi PCG vs flexible CG with the trained network, both
+    to 1e-8 (CUDA events around each solve; one warm-up solve each first)."""
+    from paper_2506_18867_gb300 import train_cnn
+    if not os.path.exists(WEIGHTS):
+        return {"unavailable": "no trained weights file"}
+    sy = train_cnn.Systems(n)
+    net = bsc.Cnn(sy.ctx)
+    net.set_params(np.load(WEIGHTS)["params"])
+    train_cnn.evaluate(sy, net, seeds[:1])            # warm-up (graph capture, first launches)
+    rows = train_cnn.evaluate(sy, net, seeds)
+    summ = train_cnn.summarize(rows)
+    net.close()
+    sy.ctx.close()
+    summ.update({"workload": f"learned{n}", "grid": f"{n}x{n}", "rel_tol": 1e-8,
+                 "heldout_seeds": list(seeds), "weights": "paper_2506_18867_gb300/weights/cnn_learned512.npz"})
+    return summ
 
 
 def projection_traffic(workload, fp32):

@@ -148,3 +148,33 @@ def test_adam_steps_reduce_the_loss(system):
     L1 = net.loss_grad(r, xs)
     print("loss", L0, "->", L1)
     assert L1 < L0
+
+
+WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.dirname(
+    __import__("os").path.abspath(__file__))), "paper_2506_18867_gb300", "weights", "cnn_learned512.npz")
+
+
+@pytest.mark.skipif(not __import__("os").path.exists(WEIGHTS), reason="no trained weights")
+def test_trained_network_gains_over_block_jacobi():
+    """The committed network (trained on 512 x 512 Newton systems by
+    paper_2506_18867_gb300.train_cnn) against the method without it, on two
+    held-out systems: fewer CG iterations to 1e-8, same solution."""
+    from paper_2506_18867_gb300 import train_cnn
+    sy = train_cnn.Systems(512)
+    net = bsc.Cnn(sy.ctx)
+    net.set_params(np.load(WEIGHTS)["params"])
+    tot_p = tot_f = 0
+    for seed in (1_000_050, 1_000_051):
+        pat, r = sy.load(seed)
+        x0, it, rr = sy.ctx.solve(r, K=sy.K, rel_tol=1e-8)
+        x1, rep = net.solve(r, sy.K, rel_tol=1e-8)
+        assert rep["rel_res"] <= 1e-8 and rep["fell_back"] == 0
+        res = (sy.ctx.spmv(x1, K=sy.K) - r).double().norm() / r.double().norm()
+        assert float(res) < 1e-6
+        assert float((x1 - x0).double().norm() / x0.double().norm()) < 1e-5
+        print(f"seed {seed} (ratio {pat.meta['ratio']:.3g}): PCG {it} iterations, learned FCG {rep['fcg_iters']}")
+        tot_p += it
+        tot_f += rep["fcg_iters"]
+    assert tot_f < tot_p
+    net.close()
+    sy.ctx.close()

@@ -201,8 +201,8 @@ bsc_status bsc_newton_step(bsc_ctx* ctx, void* C_dev, const void* Chat_dev, bsc_
  *    per-patch reports.
  *  - A single-patch context is the one-patch case of the same code. */
 
-/* Build a context for `count` patches (1 <= count <= 304, the co-resident
- * block capacity of the persistent PCG on one GB300).
+/* Build a context for `count` patches (1 <= count <= 304; more than the
+ * persistent PCG's co-resident block capacity is refused).
  *   grids, materials, options: arrays of count entries (options[p].pinned
  *   holds patch-local control-point indices); precision, project,
  *   pcg_rel_tol, pcg_max_iter and max_line_search are taken from

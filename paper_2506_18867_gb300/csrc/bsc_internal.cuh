@@ -306,4 +306,30 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsig
   return group_barrier(count, gen, status, gridDim.x);
 }
 
+// Row alpha (patch-local index) of y = K x in the element type T; K and x
+// already point at the patch's first control point, N is the plane stride.
+template <typename T>
+__device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T* __restrict__ K,
+                                         const T* __restrict__ x, T y[3]) {
+  const int i = al % nu, j = al / nu;
+  T y0 = T(0), y1 = T(0), y2 = T(0);
+#pragma unroll
+  for (int dv = -2; dv <= 2; ++dv) {
+    const int jb = j + dv;
+    if (jb < 0 || jb >= nv) continue;
+#pragma unroll
+    for (int du = -2; du <= 2; ++du) {
+      const int ib = i + du;
+      if (ib < 0 || ib >= nu) continue;
+      const int slot = (dv + 2) * 5 + (du + 2), be = jb * nu + ib;
+      const T x0 = __ldg(x + be), x1 = __ldg(x + N + be), x2 = __ldg(x + 2 * N + be);
+      const T* Kb = K + (size_t)slot * 9 * N + al;
+      y0 += Kb[0] * x0 + Kb[(size_t)N] * x1 + Kb[(size_t)2 * N] * x2;
+      y1 += Kb[(size_t)3 * N] * x0 + Kb[(size_t)4 * N] * x1 + Kb[(size_t)5 * N] * x2;
+      y2 += Kb[(size_t)6 * N] * x0 + Kb[(size_t)7 * N] * x1 + Kb[(size_t)8 * N] * x2;
+    }
+  }
+  y[0] = y0; y[1] = y1; y[2] = y2;
+}
+
 #endif  // __CUDACC__

@@ -575,78 +575,211 @@ __global__ void k_add_f(int n, const float* __restrict__ a, float* __restrict__ 
   if (k < n) b[k] += a[k];
 }
 
-// partial[blk] = a.b and partial[G + blk] = c.d over the block's slice.
-__global__ void __launch_bounds__(RB) k_dot2_partials(int n, const float* __restrict__ a, const float* __restrict__ b,
-                                                      const float* __restrict__ c, const float* __restrict__ d,
-                                                      double* __restrict__ partial) {
-  __shared__ double sm[RB / 32];
-  double s1 = 0.0, s2 = 0.0;
-  for (int k = blockIdx.x * RB + threadIdx.x; k < n; k += gridDim.x * RB) {
-    s1 += (double)a[k] * (double)b[k];
-    s2 += (double)c[k] * (double)d[k];
-  }
-  const double t1 = block_sum<RB>(s1, sm);
-  const double t2 = block_sum<RB>(s2, sm);
-  if (threadIdx.x == 0) {
-    partial[blockIdx.x] = t1;
-    partial[gridDim.x + blockIdx.x] = t2;
-  }
-}
 
-__global__ void __launch_bounds__(RB) k_sum2_to(int n, const double* __restrict__ partial, double* __restrict__ out) {
-  __shared__ double sm[RB / 32];
-  double a = 0.0, b = 0.0;
-  for (int k = threadIdx.x; k < n; k += RB) {
-    a += partial[k];
-    b += partial[n + k];
-  }
-  const double t1 = block_sum<RB>(a, sm);
-  const double t2 = block_sum<RB>(b, sm);
-  if (threadIdx.x == 0) {
-    out[0] = t1;
-    out[1] = t2;
-  }
-}
 
-// r.r of the flexible CG: dsc[3] = r.r, the feature scale s = RMS of r, and
-// the converged flag (flag[0] = 1, flag[1] = iteration) once r.r <= stop.
-__global__ void __launch_bounds__(RB) k_sum_rr(int n, int P, const double* __restrict__ partial,
-                                               double* __restrict__ dsc, double* __restrict__ scales, double stop,
-                                               int it, int* __restrict__ flag) {
-  __shared__ double sm[RB / 32];
-  double a = 0.0;
-  for (int k = threadIdx.x; k < n; k += RB) a += partial[k];
-  const double t = block_sum<RB>(a, sm);
-  if (threadIdx.x == 0) {
-    dsc[3] = t;
-    scales[0] = sqrt(t / (3.0 * P));
-    if (flag[0] == 0 && (t <= stop || !(dsc[1] > 0.0) || !isfinite(t))) {
-      flag[0] = (t <= stop) ? 1 : 2;  // 2: breakdown (no positive curvature or non-finite)
-      flag[1] = it;
+
+
+
+// ---- the flexible CG with the learned preconditioner as one persistent kernel
+
+struct FcgArgs {
+  int nu, nv, P, maxit, window;
+  double stop;                  // tol^2 b.b
+  const float* __restrict__ K;
+  const float* __restrict__ A;     // bounded taps [P][16]
+  const float* __restrict__ Linv;  // [P][6]
+  const uint8_t* __restrict__ pinned;
+  float *x, *r, *z, *p, *q, *y, *u;
+  double* partial;              // [4][gridDim.x]
+  unsigned int* sync;           // barrier count, generation
+  int* status;
+  double* out;                  // iterations, r.r, state (1 converged, 2 stalled, 3 breakdown, 0 limit)
+};
+
+// From x, r, z = M r, p = z (set up by the caller), per iteration:
+//   q = K p; a = p.r / p.q; x += a p; r -= a q; y = L^-1 P r      (barrier after each reduction)
+//   u = B y; z = P L^-T B^T u; b = -z.q / p.q; p = z + b p
+// with five bounded grid barriers and FP64 reductions in fixed block order.
+// Stops at r.r <= stop, at a breakdown (p.q <= 0 or non-finite), or when r.r
+// has not dropped by 4x in `window` iterations (the caller then falls back).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
+  __shared__ double sm[BLOCK / 32];
+  const int G = gridDim.x, P = F.P, nu = F.nu, nv = F.nv;
+  const int tid = blockIdx.x * BLOCK + threadIdx.x, stride = G * BLOCK;
+  unsigned int* cnt = F.sync;
+  volatile unsigned int* gen = F.sync + 1;
+  double* const part0 = F.partial;
+  double* const part1 = F.partial + G;
+  double* const part2 = F.partial + 2 * G;
+  double* const part3 = F.partial + 3 * G;
+  double best = 0.0, rr = 0.0;
+  int since = 0, state = 0, it = 0;
+  bool ok = true;
+  for (it = 1; it <= F.maxit; ++it) {
+    // 1. q = K p, p.q, p.r
+    double l_pq = 0.0, l_pr = 0.0;
+    for (int al = tid; al < P; al += stride) {
+      float qq[3];
+      spmv_row<float>(nu, nv, P, al, F.K, F.p, qq);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float pc = F.p[(size_t)c * P + al];
+        F.q[(size_t)c * P + al] = qq[c];
+        l_pq += (double)pc * (double)qq[c];
+        l_pr += (double)pc * (double)F.r[(size_t)c * P + al];
+      }
     }
+    {
+      const double a1 = block_sum<BLOCK>(l_pq, sm), a2 = block_sum<BLOCK>(l_pr, sm);
+      if (threadIdx.x == 0) {
+        part0[blockIdx.x] = a1;
+        part1[blockIdx.x] = a2;
+      }
+    }
+    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
+    double pq = 0.0, pr = 0.0;
+    {
+      double s1 = 0.0, s2 = 0.0;
+      for (int k = threadIdx.x; k < G; k += BLOCK) {
+        s1 += part0[k];
+        s2 += part1[k];
+      }
+      pq = block_sum<BLOCK>(s1, sm);
+      pr = block_sum<BLOCK>(s2, sm);
+      __shared__ double b2[2];
+      if (threadIdx.x == 0) {
+        b2[0] = pq;
+        b2[1] = pr;
+      }
+      __syncthreads();
+      pq = b2[0];
+      pr = b2[1];
+    }
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      state = 3;
+      break;
+    }
+    // 2. x += a p, r -= a q, y = L^-1 P r, r.r
+    const float af = (float)(pr / pq);
+    double l_rr = 0.0;
+    for (int al = tid; al < P; al += stride) {
+      float rv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t k = (size_t)c * P + al;
+        F.x[k] += af * F.p[k];
+        rv[c] = F.r[k] - af * F.q[k];
+        F.r[k] = rv[c];
+        l_rr += (double)rv[c] * (double)rv[c];
+      }
+      if (F.pinned[al]) rv[0] = rv[1] = rv[2] = 0.0f;
+      float yv[3];
+      linv_mul(F.Linv + (size_t)al * 6, rv, yv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F.y[(size_t)c * P + al] = yv[c];
+    }
+    {
+      const double a1 = block_sum<BLOCK>(l_rr, sm);
+      if (threadIdx.x == 0) part2[blockIdx.x] = a1;
+    }
+    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
+    {
+      double s1 = 0.0;
+      for (int k = threadIdx.x; k < G; k += BLOCK) s1 += part2[k];
+      rr = block_sum<BLOCK>(s1, sm);
+      __shared__ double b1;
+      if (threadIdx.x == 0) b1 = rr;
+      __syncthreads();
+      rr = b1;
+    }
+    if (!isfinite(rr)) {
+      state = 3;
+      break;
+    }
+    if (rr <= F.stop) {
+      state = 1;
+      break;
+    }
+    if (it == 1 || rr < 0.25 * best) {
+      best = rr;
+      since = 0;
+    } else if (++since >= F.window) {
+      state = 2;
+      break;
+    }
+    // 3. u = B y
+    for (int al = tid; al < P; al += stride) {
+      const int i = al % nu, j = al / nu;
+      const float* ap = F.A + (size_t)al * 16;
+      float acc[3] = {F.y[al], F.y[(size_t)P + al], F.y[2 * (size_t)P + al]};
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int ii = i + t % 3 - 1, jj = j + t / 3 - 1;
+        if (ii < 0 || ii >= nu || jj < 0 || jj >= nv) continue;
+        const int qn = jj * nu + ii;
+        const float at = ap[t];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] += at * F.y[(size_t)c * P + qn];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F.u[(size_t)c * P + al] = acc[c];
+    }
+    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
+    // 4. z = P L^-T B^T u, z.q
+    double l_zq = 0.0;
+    for (int al = tid; al < P; al += stride) {
+      float zv[3] = {0.0f, 0.0f, 0.0f};
+      if (!F.pinned[al]) {
+        const int i = al % nu, j = al / nu;
+        float v[3] = {F.u[al], F.u[(size_t)P + al], F.u[2 * (size_t)P + al]};
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          const int ii = i - (t % 3 - 1), jj = j - (t / 3 - 1);
+          if (ii < 0 || ii >= nu || jj < 0 || jj >= nv) continue;
+          const int qn = jj * nu + ii;
+          const float at = F.A[(size_t)qn * 16 + t];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[c] += at * F.u[(size_t)c * P + qn];
+        }
+        linvT_mul(F.Linv + (size_t)al * 6, v, zv);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        F.z[(size_t)c * P + al] = zv[c];
+        l_zq += (double)zv[c] * (double)F.q[(size_t)c * P + al];
+      }
+    }
+    {
+      const double a1 = block_sum<BLOCK>(l_zq, sm);
+      if (threadIdx.x == 0) part3[blockIdx.x] = a1;
+    }
+    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
+    double zq = 0.0;
+    {
+      double s1 = 0.0;
+      for (int k = threadIdx.x; k < G; k += BLOCK) s1 += part3[k];
+      zq = block_sum<BLOCK>(s1, sm);
+      __shared__ double b1;
+      if (threadIdx.x == 0) b1 = zq;
+      __syncthreads();
+      zq = b1;
+    }
+    // 5. p = z + b p
+    const float bf = (float)(-zq / pq);
+    for (int al = tid; al < P; al += stride)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t k = (size_t)c * P + al;
+        F.p[k] = F.z[k] + bf * F.p[k];
+      }
+    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
   }
-}
-
-// x += a p, r -= a q (a = p.r / p.q) unless the solve has finished.
-__global__ void k_fcg_xr_g(int n, const double* __restrict__ dsc, const int* __restrict__ flag,
-                           const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ x,
-                           float* __restrict__ r) {
-  if (flag[0] || !(dsc[1] > 0.0)) return;  // finished, or no positive curvature (k_sum_rr flags it)
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const float a = (float)(dsc[0] / dsc[1]);
-  x[k] += a * p[k];
-  r[k] -= a * q[k];
-}
-
-// p = z + b p (b = -z.q / p.q) unless the solve has finished.
-__global__ void k_fcg_p_g(int n, const double* __restrict__ dsc, const int* __restrict__ flag,
-                          const float* __restrict__ z, float* __restrict__ p) {
-  if (flag[0]) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const float b = (float)(-dsc[2] / dsc[1]);
-  p[k] = z[k] + b * p[k];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    F.out[0] = (double)(it > F.maxit ? F.maxit : it);
+    F.out[1] = rr;
+    F.out[2] = ok ? (double)state : 3.0;
+  }
 }
 
 }  // namespace
@@ -685,6 +818,10 @@ struct bsc_cnn {
   float* vec[8];               // FCG: r, z, p, q, d; training: e, K e, K x (3 planes of P)
   int conv_grid;
   int red_grid;
+  int fcg_grid;                // co-resident blocks of the persistent flexible CG
+  double* fpart;               // its reduction partials [4][fcg_grid]
+  unsigned int* fsync;         // its barrier words
+  double* fout;                // its results: iterations, r.r, state
 };
 
 namespace {
@@ -834,6 +971,9 @@ void cnn_free(bsc_cnn* n) {
   for (float* v : n->vec)
     if (v) cudaFree(v);
   if (n->hsc) cudaFreeHost(n->hsc);
+  if (n->fsync) cudaFree(n->fsync);
+  if (n->fpart) cudaFree(n->fpart);
+  if (n->fout) cudaFree(n->fout);
   free(n);
 }
 
@@ -893,6 +1033,8 @@ bsc_status bsc_cnn_create(bsc_ctx* c, bsc_cnn** out) {
   for (int k = 0; k < 8; ++k) CA(n->vec[k], 3 * P * 4);
 #undef CA
   if (e == cudaSuccess) e = cudaMallocHost((void**)&n->hsc, 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->fsync, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->fout, 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(n->params, 0, NP * 4);
   if (e == cudaSuccess) e = cudaMemset(n->adam_m, 0, NP * 4);
   if (e == cudaSuccess) e = cudaMemset(n->adam_v, 0, NP * 4);
@@ -913,6 +1055,16 @@ bsc_status bsc_cnn_create(bsc_ctx* c, bsc_cnn** out) {
   per = per < 1 ? 1 : (per > 4 ? 4 : per);
   const int tiles = (n->P + TILE - 1) / TILE;
   n->conv_grid = std::min(tiles, per * c->num_sms);
+  int perf = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf, k_fcg_learned<256>, 256, 0);
+  perf = perf < 1 ? 1 : (perf > 4 ? 4 : perf);
+  n->fcg_grid = std::min((n->P + 255) / 256, perf * c->num_sms);
+  if (n->fcg_grid < 1) n->fcg_grid = 1;
+  if (cudaMalloc((void**)&n->fpart, 4 * sizeof(double) * (size_t)n->fcg_grid) != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "bsc_cnn_create: allocation failed");
+    cnn_free(n);
+    return BSC_ERR_OOM;
+  }
   if (relayout(n) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "bsc_cnn_create: weight layout failed");
     cnn_free(n);
@@ -1021,7 +1173,7 @@ bsc_status bsc_solve_fcg(bsc_ctx* c, bsc_cnn* n, const void* K, const void* b, v
   bsc_status st = bsc_cnn_prepare(n, K);
   if (st != BSC_OK) return st;
   const int N3 = 3 * n->P, B = 256, G3 = (N3 + B - 1) / B;
-  float *r = n->vec[0], *z = n->vec[1], *p = n->vec[2], *q = n->vec[3];
+  float *r = n->vec[0], *z = n->vec[1], *p = n->vec[2];
   float* xx = (float*)x;
   cudaStream_t s = c->stream;
   CKN(cudaMemsetAsync(xx, 0, sizeof(float) * N3, s), "bsc_solve_fcg");
@@ -1039,47 +1191,32 @@ bsc_status bsc_solve_fcg(bsc_ctx* c, bsc_cnn* n, const void* K, const void* b, v
     return BSC_OK;
   }
   const double stop = tol * tol * bb;
-  CKN(cudaMemsetAsync(n->flag, 0, 4 * sizeof(int), s), "bsc_solve_fcg");
-  // Iterations run without host synchronisation; every CHECK iterations the
-  // host reads r.r and the flag.  After convergence (or breakdown) the
-  // remaining launches of the block leave x and r unchanged.
-  constexpr int CHECK = 4;
-  double best = bb, rr = bb;
-  int it = 0, since_best = 0, done_it = 0, flag = 0;
-  const int window = 24;
-  bool stalled = false;
-  for (it = 1; it <= maxit; ++it) {
-    CKN(launch_spmv(c, K, p, q), "bsc_solve_fcg");
-    BSC_COUNT(c, 5);
-    k_dot2_partials<<<n->red_grid, RB, 0, s>>>(N3, p, r, p, q, n->red);
-    k_sum2_to<<<1, RB, 0, s>>>(n->red_grid, n->red, n->dsc);
-    k_fcg_xr_g<<<G3, B, 0, s>>>(N3, n->dsc, n->flag, p, q, xx, r);
-    k_dot_partials<<<n->red_grid, RB, 0, s>>>(N3, r, r, n->red);
-    k_sum_rr<<<1, RB, 0, s>>>(n->red_grid, n->P, n->red, n->dsc, n->scales, stop, it, n->flag);
-    CKN(precondition(n, r, z), "bsc_solve_fcg");
-    CKN(dot(n, z, q, n->dsc + 2), "bsc_solve_fcg");
+  // the iterations: one persistent cooperative kernel
+  FcgArgs F;
+  F.nu = n->nu; F.nv = n->nv; F.P = n->P; F.maxit = maxit; F.window = 24; F.stop = stop;
+  F.K = (const float*)K; F.A = n->A; F.Linv = n->Linv; F.pinned = c->pinned;
+  F.x = xx; F.r = r; F.z = z; F.p = p; F.q = n->vec[3]; F.y = n->py; F.u = n->pu;
+  F.partial = n->fpart; F.sync = n->fsync; F.status = c->dstatus; F.out = n->fout;
+  CKN(cudaMemsetAsync(n->fsync, 0, 4 * sizeof(unsigned int), s), "bsc_solve_fcg");
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n->fcg_grid);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     BSC_COUNT(c, 1);
-    k_fcg_p_g<<<G3, B, 0, s>>>(N3, n->dsc, n->flag, z, p);
-    if (it % CHECK == 0 || it == maxit) {
-      CKN(cudaMemcpyAsync(n->hsc, n->dsc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s), "bsc_solve_fcg");
-      CKN(cudaMemcpyAsync(n->hsc + 8, n->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "bsc_solve_fcg");
-      if ((st = cnn_sync(n, "bsc_solve_fcg")) != BSC_OK) return st;
-      rr = n->hsc[3];
-      const int* hf = reinterpret_cast<const int*>(n->hsc + 8);
-      flag = hf[0];
-      done_it = hf[1];
-      if (flag) break;
-      if (rr < 0.25 * best) {
-        best = rr;
-        since_best = 0;
-      } else if ((since_best += CHECK) >= window) {
-        stalled = true;  // no 4x drop of r.r in `window` iterations
-        break;
-      }
-    }
+    CKN(cudaLaunchKernelEx(&cfg, k_fcg_learned<256>, F), "bsc_solve_fcg");
   }
-  if (flag == 1) it = done_it;
-  if (flag == 2) stalled = true;
+  CKN(cudaMemcpyAsync(n->hsc, n->fout, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "bsc_solve_fcg");
+  if ((st = cnn_sync(n, "bsc_solve_fcg")) != BSC_OK) return st;
+  int it = (int)n->hsc[0];
+  const double rr = n->hsc[1];
+  const int state = (int)n->hsc[2];
+  const bool stalled = state != 1;
   R.fcg_iters = it > maxit ? maxit : it;
   R.rel_res = sqrt(rr / bb);
   if (stalled || !(rr <= stop)) {

@@ -20,32 +20,6 @@
 
 namespace {
 
-// Row alpha (patch-local index) of y = K x in the element type T; K and x
-// already point at the patch's first control point, N is the plane stride.
-template <typename T>
-__device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T* __restrict__ K,
-                                         const T* __restrict__ x, T y[3]) {
-  const int i = al % nu, j = al / nu;
-  T y0 = T(0), y1 = T(0), y2 = T(0);
-#pragma unroll
-  for (int dv = -2; dv <= 2; ++dv) {
-    const int jb = j + dv;
-    if (jb < 0 || jb >= nv) continue;
-#pragma unroll
-    for (int du = -2; du <= 2; ++du) {
-      const int ib = i + du;
-      if (ib < 0 || ib >= nu) continue;
-      const int slot = (dv + 2) * 5 + (du + 2), be = jb * nu + ib;
-      const T x0 = __ldg(x + be), x1 = __ldg(x + N + be), x2 = __ldg(x + 2 * N + be);
-      const T* Kb = K + (size_t)slot * 9 * N + al;
-      y0 += Kb[0] * x0 + Kb[(size_t)N] * x1 + Kb[(size_t)2 * N] * x2;
-      y1 += Kb[(size_t)3 * N] * x0 + Kb[(size_t)4 * N] * x1 + Kb[(size_t)5 * N] * x2;
-      y2 += Kb[(size_t)6 * N] * x0 + Kb[(size_t)7 * N] * x1 + Kb[(size_t)8 * N] * x2;
-    }
-  }
-  y[0] = y0; y[1] = y1; y[2] = y2;
-}
-
 template <typename T>
 __global__ void k_spmv(int N, const PatchDev* __restrict__ pd, const int* __restrict__ cp_patch,
                        const T* __restrict__ K, const T* __restrict__ x, T* __restrict__ y) {
@@ -337,9 +311,10 @@ extern "C" int bsc_plan_blocks(int count, const int* n_cp, const double* work, i
   return used;
 }
 
-// Grid of the persistent PCG: the co-resident capacity (at most two blocks
-// per SM), capped by what the patches can use; per-patch work estimates
-// start at the control-point counts.
+// Grid of the persistent PCG: the co-resident capacity (at most four blocks
+// of 256 threads per SM: the SpMV rows are latency-bound loads, and 1024
+// threads per SM keep enough of them in flight), capped by what the patches
+// can use; per-patch work estimates start at the control-point counts.
 cudaError_t setup_pcg(bsc_ctx* c) {
   int per_sm = 0;
   cudaError_t e = c->precision == BSC_FP64
@@ -347,7 +322,7 @@ cudaError_t setup_pcg(bsc_ctx* c) {
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<float, PCG_BLOCK>, PCG_BLOCK, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2) per_sm = 2;
+  if (per_sm > 4) per_sm = 4;
   const int cap = c->num_sms * per_sm;
   if (c->P > cap) return cudaErrorInvalidConfiguration;
   long long need = 0;

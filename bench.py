@@ -445,10 +445,26 @@ def measure_learned(bsc, np, seeds=(1_000_000, 1_000_001, 1_000_002, 1_000_003),
     return summ
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the projection
+# phase per Newton step, from one ncu capture (profiles/k_project_drape256_fp32.md:
+# k_proj_p1 80.5 MB + k_project_ring 18.3 MB + k_proj_p2 326.1 MB), keyed by a
+# hash of the projection sources it was taken with.
+PROJECTION_TRAFFIC = {("drape256", True): ("57ed2d49a7311e45", 424.9e6)}
+PROJECTION_SOURCES = ("k_project.cu", "proj_core.cuh", "k_project_ring.cu")
+
+
 def projection_traffic(workload, fp32):
-    """DRAM bytes per step of the projection kernels from the committed ncu
-    capture of the drape workload (FP32), or None for other workloads."""
-    return None
+    """The captured DRAM traffic of the projection phase, or None when no
+    capture exists for the workload or the kernels changed since it."""
+    import hashlib
+    rec = PROJECTION_TRAFFIC.get((workload, bool(fp32)))
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for f in PROJECTION_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_18867_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec[1] if h.hexdigest()[:16] == rec[0] else None
 
 
 # --------------------------------------------------------------------------- CPU oracle

@@ -75,6 +75,36 @@ __device__ int sturm64(const double* d, const double* e2, double x) {
   return cnt;
 }
 
+// det(T - x I) of the scaled tridiagonal in shared memory with the Sturm
+// count; *exact is false when a rescaling step made the value's scale differ
+// from the determinant's.
+__device__ __noinline__ double charpoly64(const double* d, const double* e2, double x, int* cnt_out, bool* exact) {
+  double pm = 1.0, p = d[0] - x;
+  int cnt = sgn_d(p);
+  bool ok = true;
+#pragma unroll
+  for (int i = 1; i < RN; ++i) {
+    double pn = (d[i] - x) * p - e2[i - 1] * pm;
+    if (exp_d(pn) == 0) {
+      pn = sgn_d(p) ? 1e-300 : -1e-300;
+      ok = false;
+    }
+    cnt += sgn_d(pn) ^ sgn_d(p);
+    const int ea = exp_d(pn), eb = exp_d(p), mx = ea > eb ? ea : eb;
+    if (mx > 1023 + 500 || mx < 1023 - 500) {
+      const double sc = mx > 1023 ? 0x1p-500 : 0x1p500;
+      pn *= sc;
+      p *= sc;
+      ok = false;
+    }
+    pm = p;
+    p = pn;
+  }
+  *cnt_out = cnt;
+  *exact = ok;
+  return p;
+}
+
 __device__ int sturm32(const float* d, const float* e2, float x) {
   float pm = 1.0f, p = d[0] - x;
   int cnt = sgn_f(p);
@@ -93,6 +123,65 @@ __device__ int sturm32(const float* d, const float* e2, float x) {
     p = pn;
   }
   return cnt;
+}
+
+// Eigenvalue k (scaled) of the tridiagonal in shared memory: FP32 bisection
+// to about 22 bits, the widened bracket checked by two FP64 Sturm counts,
+// then regula falsi (Illinois) on det(T - x I) while the bracket isolates
+// eigenvalue k, bisection otherwise; four steps that fail to halve the
+// bracket force a bisection step (a bracket end next to a multiple root
+// stalls regula falsi).  Own call frame: the kernel body keeps its registers.
+__device__ __noinline__ double ring_eigenvalue(const double* dd, const double* ee2, const float* d32,
+                                               const float* e232, int k) {
+  float a32 = -1.0f - 1e-6f, b32 = (float)(-NEG_REL);
+  for (int it = 0; it < 22; ++it) {
+    const float mid = 0.5f * (a32 + b32);
+    if (sturm32(d32, e232, mid) > k) b32 = mid;
+    else a32 = mid;
+  }
+  double a = fmax((double)a32 - 4e-6, -1.0 - 1e-12), b = fmin((double)b32 + 4e-6, -NEG_REL);
+  int ca, cb;
+  bool xa, xb;
+  double fa = charpoly64(dd, ee2, a, &ca, &xa), fb = charpoly64(dd, ee2, b, &cb, &xb);
+  if (!(ca <= k && cb > k)) {
+    a = -1.0 - 1e-12;
+    b = -NEG_REL;
+    fa = charpoly64(dd, ee2, a, &ca, &xa);
+    fb = charpoly64(dd, ee2, b, &cb, &xb);
+  }
+  int side = 0, win = 0;
+  bool force_bisect = false;
+  double wstart = b - a;
+  for (int it = 0; it < 120 && b - a > 1e-10; ++it) {
+    double x;
+    const bool isolated = ca == k && cb == k + 1 && xa && xb && fa != fb && !force_bisect;
+    if (isolated) {
+      x = (a * fb - b * fa) / (fb - fa);
+      if (!(x > a && x < b)) x = 0.5 * (a + b);
+    } else {
+      x = 0.5 * (a + b);
+      force_bisect = false;
+      win = 0;
+      wstart = b - a;
+    }
+    int cx;
+    bool xx;
+    const double fx = charpoly64(dd, ee2, x, &cx, &xx);
+    if (cx > k) {
+      if (isolated && side == -1) fa *= 0.5;
+      b = x; fb = fx; cb = cx; xb = xx; side = -1;
+    } else {
+      if (isolated && side == 1) fb *= 0.5;
+      a = x; fa = fx; ca = cx; xa = xx; side = 1;
+    }
+    if (isolated && fx == 0.0) return x;
+    if (isolated && ++win == 4) {
+      force_bisect = b - a > 0.5 * wstart;
+      win = 0;
+      wstart = b - a;
+    }
+  }
+  return 0.5 * (a + b);
 }
 
 // Solves (T - sig I) y = y in place by Gaussian elimination with partial
@@ -340,25 +429,7 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
 
     // ---- lane k < kneg: eigenvalue k (FP32 bracket, FP64 check + refinement)
     double sig = 0.0;
-    if (lane < kneg) {
-      float a32 = -1.0f - 1e-6f, b32 = (float)(-NEG_REL);
-      for (int it = 0; it < 22; ++it) {
-        const float mid = 0.5f * (a32 + b32);
-        if (sturm32(s_d32[wp], s_e232[wp], mid) > lane) b32 = mid;
-        else a32 = mid;
-      }
-      double a = fmax((double)a32 - 4e-6, -1.0 - 1e-12), b = fmin((double)b32 + 4e-6, -NEG_REL);
-      if (!(sturm64(dd, ee2, a) <= lane && sturm64(dd, ee2, b) > lane)) {
-        a = -1.0 - 1e-12;
-        b = -NEG_REL;
-      }
-      for (int it = 0; it < 40 && b - a > 1e-10; ++it) {
-        const double mid = 0.5 * (a + b);
-        if (sturm64(dd, ee2, mid) > lane) b = mid;
-        else a = mid;
-      }
-      sig = 0.5 * (a + b);
-    }
+    if (lane < kneg) sig = ring_eigenvalue(dd, ee2, s_d32[wp], s_e232[wp], lane);
     // ---- inverse iteration, two solves, Gram-Schmidt across lanes after each
     double y[RN];
 #pragma unroll

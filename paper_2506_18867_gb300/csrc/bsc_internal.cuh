@@ -109,6 +109,11 @@ struct bsc_ctx {
   int* bucket_list;   // [Nsp] span ids grouped by bucket
   int bucket_off[4];  // host: start of each bucket in bucket_list
   int* nneg;          // [Nsp] negative eigenvalues found per span (diagnostic)
+  // reduced bases of the projection (rest geometry only, computed at create)
+  double* red_g;      // [16][Nmem] g_q,beta of each membrane point in its span's reduced basis
+  double* red_l;      // [8][Nbd] L_q of each bending point in its span's reduced basis
+  double* red_q;      // [45][n interior] orthonormal basis of each interior span (class order)
+  double* helmert;    // device [72]: the border spans' basis (Helmert contrasts)
   // two span classes: 0 interior (reduced size 15), 1 at or next to the border (24)
   int proj_grid[2][2];      // resident grid per class and phase
   double* proj_scratch[2];  // per-thread slots of the phase-2 kernels (cluster eigenvectors)
@@ -308,9 +313,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsig
 
 // Row alpha (patch-local index) of y = K x in the element type T; K and x
 // already point at the patch's first control point, N is the plane stride.
-template <typename T>
-__device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T* __restrict__ K,
-                                         const T* __restrict__ x, T y[3]) {
+// X_RO: x stays unchanged for the whole kernel, so it may go through the
+// non-coherent read-only path; the persistent solvers update their x (the
+// search direction) between grid barriers and read it with plain loads,
+// which the barriers' fences make coherent.
+template <typename T, bool X_RO = false>
+__device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T* __restrict__ K, const T* x,
+                                         T y[3]) {
   const int i = al % nu, j = al / nu;
   T y0 = T(0), y1 = T(0), y2 = T(0);
 #pragma unroll
@@ -322,7 +331,12 @@ __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T*
       const int ib = i + du;
       if (ib < 0 || ib >= nu) continue;
       const int slot = (dv + 2) * 5 + (du + 2), be = jb * nu + ib;
-      const T x0 = __ldg(x + be), x1 = __ldg(x + N + be), x2 = __ldg(x + 2 * N + be);
+      T x0, x1, x2;
+      if (X_RO) {
+        x0 = __ldg(x + be); x1 = __ldg(x + N + be); x2 = __ldg(x + 2 * N + be);
+      } else {
+        x0 = x[be]; x1 = x[N + be]; x2 = x[2 * N + be];
+      }
       const T* Kb = K + (size_t)slot * 9 * N + al;
       y0 += Kb[0] * x0 + Kb[(size_t)N] * x1 + Kb[(size_t)2 * N] * x2;
       y1 += Kb[(size_t)3 * N] * x0 + Kb[(size_t)4 * N] * x1 + Kb[(size_t)5 * N] * x2;

@@ -15,7 +15,10 @@
 //
 // Interior spans (five derivative vectors, D = 5, n = 15).  A block takes
 // BLOCK spans at a time from a work counter.  Phase 1 (one thread per span)
-// builds H_r, tridiagonalises it and counts its negative eigenvalues.
+// builds H_r, tridiagonalises it and counts its negative eigenvalues.  The
+// basis Q and the derivative vectors in it depend on the rest geometry only,
+// so k_reduce_points computes them once per context (Gram-Schmidt for the
+// interior spans, Helmert contrasts for the border spans).
 // Phase 2a computes every negative eigenvalue of the batch as an independent
 // item spread over the block; phase 2b computes the eigenvectors, one item
 // per cluster of close eigenvalues; phase 2c lets each owner apply its rank-k
@@ -47,6 +50,10 @@ struct ProjArgs {
   T* __restrict__ H;
   int* __restrict__ nneg;
   int* __restrict__ status;
+  const double* __restrict__ rg;  // [16][Nm] membrane derivative vectors in the span's reduced basis
+  const double* __restrict__ rl;  // [8][Nb] bending vectors in the span's reduced basis
+  const double* __restrict__ rq;  // the class's bases: [9 D][count] per span, or one 9 x 8 basis
+  int rq_per_span;                // 1: rq holds a basis per span (class order)
 };
 
 // Eigenvalues below -NEG_REL * ||T|| are projected; above that they are
@@ -58,9 +65,11 @@ constexpr double RANK_REL = 1e-13;
 
 template <typename T>
 struct SpanTab {
-  const T* tabm;  // already offset to the span's first membrane point
-  const T* tabb;  // already offset to the span's first bending point
+  const T* tabm;     // already offset to the span's first membrane point
+  const T* tabb;     // already offset to the span's first bending point
   const T* A;
+  const double* rg;  // reduced vectors, offset like tabm / tabb
+  const double* rl;
   int Nm, Nb, nmq, nbq;
   double mubd;
   __device__ int nm() const { return nmq; }
@@ -69,47 +78,30 @@ struct SpanTab {
   __device__ double L(int q, int l) const { return (double)tabb[(1 + l) * Nb + q]; }
   __device__ double wb(int q) const { return (double)tabb[q] * mubd; }
   __device__ double a6(int q, int e) const { return (double)A[e * Nm + q]; }
+  __device__ double gr(int q, int k, int be) const { return rg[(size_t)(2 * k + be) * Nm + q]; }
+  __device__ double lr(int q, int k) const { return rl[(size_t)k * Nb + q]; }
 };
 
-// H <- H - lam w w^T on the packed upper triangle, in the element type: the
-// correction is formed in FP64 and applied in T (FP32 output stays FP32).
-template <typename T>
-struct SpanH {
-  T* H;
-  int Nsp, s;
-  __device__ __forceinline__ void rank1(double lam, const double (&w)[27]) {
-    T wt[27], lw[27];
-#pragma unroll
-    for (int r = 0; r < 27; ++r) {
-      wt[r] = (T)w[r];
-      lw[r] = (T)(lam * w[r]);
-    }
-    T* h = H + s;
-    int e = 0;
-#pragma unroll
-    for (int r = 0; r < 27; ++r)
-#pragma unroll
-      for (int c = r; c < 27; ++c, ++e) h[(size_t)e * Nsp] -= lw[r] * wt[c];
-  }
-};
+// Helmert contrasts q_k = (1, ..., 1, -k, 0, ...) / sqrt(k (k + 1)) (k ones),
+// k = 1..8: an orthonormal basis of the vectors of R^9 that sum to zero, the
+// reduced basis of every border span.
+__device__ double d_helmert[72];
 
-// Shared memory per thread: A (packed H_r, then reflectors), R (3n: basis,
-// then the scaled tridiagonal), the scale ||T||, an FP32 copy of (d, e^2)
-// and the running lower bracket, all interleaved by thread.
+// Shared memory per thread of phase 1: A (packed H_r, then reflectors) and
+// R (3n: the scaled tridiagonal), interleaved by thread.
 template <int D>
 struct Smem {
   static constexpr int n = 3 * D, NP = n * (n + 1) / 2;
-  static constexpr int DOUBLES = NP + 3 * n + 1, FLOATS = 2 * n + 1;
 };
 
-// Per-span scratch of the interior class (global memory, entry-major over
-// the span's position in the class list): reflectors + tau (packed A),
-// scaled tridiagonal (d, e, e^2), basis Q, scale ||T||, eigenvalues, and the
-// span-DOF vectors w of the negative eigenpairs.
+// Per-span scratch of a class (global memory, entry-major over the span's
+// position in the class list): reflectors + tau (packed A), scaled
+// tridiagonal (d, e, e^2), scale ||T||, eigenvalues, and the span-DOF
+// vectors w of the negative eigenpairs.
 template <int D>
 struct SpanScratch {
   static constexpr int n = 3 * D, NP = n * (n + 1) / 2;
-  static constexpr int A = 0, R = NP, Q = R + 3 * n, TN = Q + 9 * D, LAM = TN + 1, W = LAM + n, SIZE = W + 27 * n;
+  static constexpr int A = 0, R = NP, TN = R + 3 * n, LAM = TN + 1, W = LAM + n, SIZE = W + 27 * n;
 };
 
 // Eigenvalues of a span closer than this (on the tridiagonal scaled to
@@ -175,11 +167,10 @@ __global__ void __launch_bounds__(P1Block<D>::value, 1)
   for (int t = blockIdx.x * B1 + threadIdx.x; t < count; t += gridDim.x * B1) {
     const int s = list[t];
     const int q0 = P.moff[s], b0 = P.boff[s];
-    SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.Nm, P.Nb, P.moff[s + 1] - q0, P.boff[s + 1] - b0,
-                     P.pd[P.sp_patch[s]].mubd};
-    const proj::View Qs{sspan + (size_t)SS::Q * count + t, count};
+    SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
+                   P.boff[s + 1] - b0, P.pd[P.sp_patch[s]].mubd};
     double tn = 0.0;
-    int kneg = proj::span_phase1<D>(tab, A, R, Qs, &tn, NEG_REL, RANK_REL);
+    int kneg = proj::span_phase1<D>(tab, A, R, &tn, NEG_REL);
     if (kneg < 0) {
       atomicOr(P.status, BSC_STATUS_NUMERIC_FLAG);
       kneg = 0;
@@ -289,7 +280,9 @@ __global__ void __launch_bounds__(P2_BLOCK)
       const int k0 = __ffs(mm) - 1;
       const unsigned rest = mm & (mm - 1u);
       const int k1 = rest ? __ffs(rest) - 1 : s_kneg[o];
-      proj::cluster_vectors_reg<D>(sv(to, SS::R), sv(to, SS::A), sv(to, SS::Q), Ys, sv(to, SS::LAM), wv(to), LU,
+      const proj::View Qs = P.rq_per_span ? proj::View{const_cast<double*>(P.rq) + to, count}
+                                          : proj::View{const_cast<double*>(P.rq), 1};
+      proj::cluster_vectors_reg<D>(sv(to, SS::R), sv(to, SS::A), Qs, Ys, sv(to, SS::LAM), wv(to), LU,
                                    sspan[(size_t)SS::TN * count + to], k0, k1 - k0);
     }
     __syncthreads();
@@ -300,14 +293,69 @@ __global__ void __launch_bounds__(P2_BLOCK)
 }
 
 template <typename T>
-ProjArgs<T> proj_args(bsc_ctx* c) {
+ProjArgs<T> proj_args(bsc_ctx* c, int k) {
   ProjArgs<T> P;
   P.Nsp = c->Nsp; P.Nm = c->Nmem; P.Nb = c->Nbd; P.pd = c->pd; P.sp_patch = c->sp_patch;
   P.moff = c->mem_off; P.boff = c->bd_off;
   P.tabm = (const T*)c->tab_mem; P.tabb = (const T*)c->tab_bd;
   P.A = (const T*)c->A_mem; P.H = (T*)c->H_span;
   P.nneg = c->nneg; P.status = c->dstatus;
+  P.rg = c->red_g; P.rl = c->red_l;
+  P.rq = k == 0 ? c->red_q : c->helmert;
+  P.rq_per_span = k == 0 ? 1 : 0;
   return P;
+}
+
+// Reduced basis and reduced derivative vectors of every span (thread per
+// position t of the bucket list): interior spans (t < n0) by Gram-Schmidt
+// (basis stored in class order), border spans in the Helmert basis.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_reduce_points(ProjArgs<T> P, const int* __restrict__ list, int n0, int count, double* __restrict__ rq,
+                    double* __restrict__ rg, double* __restrict__ rl) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+    const int s = list[t];
+    const int q0 = P.moff[s], b0 = P.boff[s];
+    const SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, nullptr, nullptr, P.Nm, P.Nb, P.moff[s + 1] - q0,
+                         P.boff[s + 1] - b0, 0.0};
+    double Q[72];
+    int D = 8;
+    if (t < n0) {
+      D = 5;
+      proj::span_basis<5>(tab, proj::View{Q, 1}, RANK_REL);
+      for (int e = 0; e < 45; ++e) rq[(size_t)e * n0 + t] = Q[e];
+    } else {
+      for (int e = 0; e < 72; ++e) Q[e] = d_helmert[e];
+    }
+    for (int q = 0; q < tab.nm(); ++q)
+      for (int k = 0; k < D; ++k) {
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+          a0 += Q[9 * k + l] * tab.g(q, l, 0);
+          a1 += Q[9 * k + l] * tab.g(q, l, 1);
+        }
+        rg[(size_t)(2 * k) * P.Nm + q0 + q] = a0;
+        rg[(size_t)(2 * k + 1) * P.Nm + q0 + q] = a1;
+      }
+    for (int q = 0; q < tab.nb(); ++q)
+      for (int k = 0; k < D; ++k) {
+        double a = 0.0;
+#pragma unroll
+        for (int l = 0; l < 9; ++l) a += Q[9 * k + l] * tab.L(q, l);
+        rl[(size_t)k * P.Nb + b0 + q] = a;
+      }
+  }
+}
+
+template <typename T>
+cudaError_t reduce_points(bsc_ctx* c) {
+  const int count = c->bucket_off[3], n0 = c->bucket_off[1];
+  if (count <= 0) return cudaSuccess;
+  BSC_COUNT(c, 1);
+  k_reduce_points<T><<<(count + 127) / 128, 128, 0, c->stream>>>(proj_args<T>(c, 0), c->bucket_list, n0, count,
+                                                                  c->red_q, c->red_g, c->red_l);
+  return cudaGetLastError();
 }
 
 template <int D>
@@ -322,7 +370,7 @@ template <typename T, int D>
 cudaError_t run_class(bsc_ctx* c, int k, const int* list, int count, cudaStream_t st, int phase = -1) {
   if (count <= 0) return cudaSuccess;
   cudaError_t e;
-  ProjArgs<T> P = proj_args<T>(c);
+  ProjArgs<T> P = proj_args<T>(c, k);
   if (phase != 1) {
     BSC_COUNT(c, 1);
     k_proj_p1<T, D><<<c->proj_grid[k][0], P1Block<D>::value, p1_smem<D>(), st>>>(P, list, count,
@@ -402,18 +450,34 @@ cudaError_t setup_class(bsc_ctx* c, int k, int count) {
 
 }  // namespace
 
-// Sizes both classes' grids and scratch and creates the side stream
-// (called from bsc_create).
+// Sizes both classes' grids and scratch, computes the reduced bases and
+// derivative vectors, and creates the side stream (called from bsc_create,
+// after the quadrature tables).
 cudaError_t setup_projection(bsc_ctx* c) {
   cudaError_t e;
   const int n0 = c->bucket_off[1] - c->bucket_off[0], n1 = c->bucket_off[3] - c->bucket_off[1];
+  {
+    double h[72];
+    for (int k = 0; k < 8; ++k) {
+      const double inv = 1.0 / sqrt((double)(k + 1) * (double)(k + 2));
+      for (int l = 0; l < 9; ++l) h[9 * k + l] = (l <= k ? 1.0 : (l == k + 1 ? -(double)(k + 1) : 0.0)) * inv;
+    }
+    if ((e = cudaMemcpyToSymbol(d_helmert, h, sizeof(h))) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&c->helmert, d_helmert)) != cudaSuccess) return e;
+  }
+  if ((e = cudaMalloc(&c->red_g, sizeof(double) * 16 * (size_t)(c->Nmem > 0 ? c->Nmem : 1))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->red_l, sizeof(double) * 8 * (size_t)(c->Nbd > 0 ? c->Nbd : 1))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->red_q, sizeof(double) * 45 * (size_t)(n0 > 0 ? n0 : 1))) != cudaSuccess) return e;
   if (c->precision == BSC_FP64) {
     if ((e = setup_class<double, 5>(c, 0, n0)) != cudaSuccess) return e;
     if ((e = setup_class<double, 8>(c, 1, n1)) != cudaSuccess) return e;
+    if ((e = reduce_points<double>(c)) != cudaSuccess) return e;
   } else {
     if ((e = setup_class<float, 5>(c, 0, n0)) != cudaSuccess) return e;
     if ((e = setup_class<float, 8>(c, 1, n1)) != cudaSuccess) return e;
+    if ((e = reduce_points<float>(c)) != cudaSuccess) return e;
   }
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
   if ((e = setup_projection_ring()) != cudaSuccess) return e;
   // before the autotuner has timed both border paths: warp per span while
   // the border spans fill the resident warps a few times over at most

@@ -46,6 +46,8 @@ struct RingArgs {
   T* __restrict__ H;
   int* __restrict__ nneg;
   int* __restrict__ status;
+  const double* __restrict__ rg;  // [16][Nm] g_q,beta in the Helmert basis
+  const double* __restrict__ rl;  // [8][Nb] L_q in the Helmert basis
 };
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -54,35 +56,18 @@ __device__ __forceinline__ int sgn_d(double x) { return (unsigned)__double2hiint
 __device__ __forceinline__ int exp_d(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
 __device__ __forceinline__ int sgn_f(float x) { return (unsigned)__float_as_int(x) >> 31; }
 
-// Sturm count (eigenvalues < x) of the scaled tridiagonal in shared memory.
-__device__ int sturm64(const double* d, const double* e2, double x) {
-  double pm = 1.0, p = d[0] - x;
-  int cnt = sgn_d(p);
-#pragma unroll
-  for (int i = 1; i < RN; ++i) {
-    double pn = (d[i] - x) * p - e2[i - 1] * pm;
-    if (exp_d(pn) == 0) pn = sgn_d(p) ? 1e-300 : -1e-300;
-    cnt += sgn_d(pn) ^ sgn_d(p);
-    const int ea = exp_d(pn), eb = exp_d(p), mx = ea > eb ? ea : eb;
-    if (mx > 1023 + 500 || mx < 1023 - 500) {
-      const double sc = mx > 1023 ? 0x1p-500 : 0x1p500;
-      pn *= sc;
-      p *= sc;
-    }
-    pm = p;
-    p = pn;
-  }
-  return cnt;
-}
-
 // det(T - x I) of the scaled tridiagonal in shared memory with the Sturm
-// count; *exact is false when a rescaling step made the value's scale differ
-// from the determinant's.
-__device__ __noinline__ double charpoly64(const double* d, const double* e2, double x, int* cnt_out, bool* exact) {
+// count (eigenvalues < x); *exact is false when a replacement of a zero
+// minor or a rescaling made the value's scale differ from the
+// determinant's.  The recurrence first runs without rescaling, the
+// exponents tracked with integer operations (no predicated FP64
+// instructions); a pair of minors outside [2^-500, 2^500] sends the call to
+// the rescaling pass, which gives the identical result.
+__device__ __noinline__ double charpoly64_scaled(const double* d, const double* e2, double x, int* cnt_out,
+                                                 bool* exact) {
   double pm = 1.0, p = d[0] - x;
   int cnt = sgn_d(p);
   bool ok = true;
-#pragma unroll
   for (int i = 1; i < RN; ++i) {
     double pn = (d[i] - x) * p - e2[i - 1] * pm;
     if (exp_d(pn) == 0) {
@@ -103,6 +88,37 @@ __device__ __noinline__ double charpoly64(const double* d, const double* e2, dou
   *cnt_out = cnt;
   *exact = ok;
   return p;
+}
+
+__device__ __noinline__ double charpoly64(const double* d, const double* e2, double x, int* cnt_out, bool* exact) {
+  double pm = 1.0, p = d[0] - x;
+  int cnt = sgn_d(p), eb = exp_d(p);
+  bool ok = true, in_range = true;
+#pragma unroll
+  for (int i = 1; i < RN; ++i) {
+    double pn = (d[i] - x) * p - e2[i - 1] * pm;
+    const bool z = exp_d(pn) == 0;
+    pn = z ? (sgn_d(p) ? 1e-300 : -1e-300) : pn;
+    ok = ok && !z;
+    cnt += sgn_d(pn) ^ sgn_d(p);
+    const int ea = exp_d(pn), mx = ea > eb ? ea : eb;
+    in_range = in_range && mx <= 1023 + 500 && mx >= 1023 - 500;
+    pm = p;
+    p = pn;
+    eb = ea;
+  }
+  if (!in_range) return charpoly64_scaled(d, e2, x, cnt_out, exact);
+  *cnt_out = cnt;
+  *exact = ok;
+  return p;
+}
+
+// Sturm count (eigenvalues < x) of the scaled tridiagonal in shared memory.
+__device__ int sturm64(const double* d, const double* e2, double x) {
+  int cnt;
+  bool ex;
+  charpoly64(d, e2, x, &cnt, &ex);
+  return cnt;
 }
 
 __device__ int sturm32(const float* d, const float* e2, float x) {
@@ -192,20 +208,17 @@ __device__ void tri_solve(const double* d, const double* e, double sig, double (
 #pragma unroll
   for (int i = 0; i < RN - 1; ++i) {
     const double ei = e[i], a1 = d[i + 1] - sig, e1 = (i + 1 < RN - 1) ? e[i + 1] : 0.0;
-    if (fabs(ei) > fabs(c0)) {
-      const double r = 1.0 / ei, m = c0 * r;
-      u0r[i] = r; u1[i] = a1; u2[i] = e1;
-      const double t = y[i];
-      y[i] = y[i + 1];
-      y[i + 1] = t - m * y[i + 1];
-      c0 = c1 - m * a1; c1 = c2 - m * e1; c2 = 0.0;
-    } else {
-      if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
-      const double r = 1.0 / c0, m = ei * r;
-      u0r[i] = r; u1[i] = c1; u2[i] = c2;
-      y[i + 1] -= m * y[i];
-      c0 = a1 - m * c1; c1 = e1 - m * c2; c2 = 0.0;
-    }
+    // pivot row and eliminated row by selects (no predicated FP64 work)
+    const bool swp = fabs(ei) > fabs(c0);
+    const double g0 = fabs(c0) < 2.3e-16 ? (c0 < 0.0 ? -2.3e-16 : 2.3e-16) : c0;
+    const double t0 = swp ? ei : g0, t1 = swp ? a1 : c1, t2 = swp ? e1 : c2;
+    const double b0 = swp ? c0 : ei, b1 = swp ? c1 : a1, b2 = swp ? c2 : e1;
+    const double r = 1.0 / t0, m = b0 * r;
+    u0r[i] = r; u1[i] = t1; u2[i] = t2;
+    const double ya = swp ? y[i + 1] : y[i], yb = swp ? y[i] : y[i + 1];
+    y[i] = ya;
+    y[i + 1] = yb - m * ya;
+    c0 = b1 - m * t1; c1 = b2 - m * t2; c2 = 0.0;
   }
   if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
   u0r[RN - 1] = 1.0 / c0; u1[RN - 1] = u2[RN - 1] = 0.0;
@@ -277,15 +290,9 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
     for (int q = q0; q < q1; ++q) {
       double gt[8][2];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) gt[k][0] = gt[k][1] = 0.0;
-#pragma unroll
-      for (int l = 0; l < 9; ++l) {
-        const double g0 = (double)P.tabm[(1 + 2 * l) * P.Nm + q], g1 = (double)P.tabm[(2 + 2 * l) * P.Nm + q];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          gt[k][0] += c_helmert[k][l] * g0;
-          gt[k][1] += c_helmert[k][l] * g1;
-        }
+      for (int k = 0; k < 8; ++k) {
+        gt[k][0] = P.rg[(size_t)(2 * k) * P.Nm + q];
+        gt[k][1] = P.rg[(size_t)(2 * k + 1) * P.Nm + q];
       }
       double A6[6][6];
       {
@@ -325,13 +332,7 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
       const double WB = (double)P.tabb[q] * mubd;
       double Lt[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) Lt[k] = 0.0;
-#pragma unroll
-      for (int l = 0; l < 9; ++l) {
-        const double L = (double)P.tabb[(1 + l) * P.Nb + q];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) Lt[k] += c_helmert[k][l] * L;
-      }
+      for (int k = 0; k < 8; ++k) Lt[k] = P.rl[(size_t)k * P.Nb + q];
       double Lk = 0.0;
 #pragma unroll
       for (int k = 0; k < 8; ++k)
@@ -538,11 +539,13 @@ cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* 
   if (g > need) g = need;
   if (c->precision == BSC_FP64) {
     RingArgs<double> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const double*)c->tab_mem,
-                       (const double*)c->tab_bd, (const double*)c->A_mem, (double*)c->H_span, c->nneg, c->dstatus};
+                       (const double*)c->tab_bd, (const double*)c->A_mem, (double*)c->H_span, c->nneg, c->dstatus,
+                       c->red_g, c->red_l};
     k_project_ring<double><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work);
   } else {
     RingArgs<float> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const float*)c->tab_mem,
-                      (const float*)c->tab_bd, (const float*)c->A_mem, (float*)c->H_span, c->nneg, c->dstatus};
+                      (const float*)c->tab_bd, (const float*)c->A_mem, (float*)c->H_span, c->nneg, c->dstatus,
+                      c->red_g, c->red_l};
     k_project_ring<float><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work);
   }
   return cudaGetLastError();

@@ -2,7 +2,8 @@
 //
 // SpMV: y_alpha = sum over the 25 stencil slots of K(alpha, slot) x_beta; one
 // thread per control point reads its 225 matrix entries from 225 planes
-// (coalesced across threads) and the neighbours' x through the read-only path.
+// (coalesced across threads) and the neighbours' x (through the read-only
+// path in the stand-alone SpMV, where x does not change).
 //
 // PCG: 3x3 block-Jacobi preconditioned CG in a single persistent cooperative
 // kernel.  The co-resident blocks are split into one group per patch (the
@@ -28,7 +29,7 @@ __global__ void k_spmv(int N, const PatchDev* __restrict__ pd, const int* __rest
   const PatchDev* pt = pd + cp_patch[al];
   const int cp0 = __ldg(&pt->cp0);
   T acc[3];
-  spmv_row<T>(__ldg(&pt->nu), __ldg(&pt->nv), N, al - cp0, K + cp0, x + cp0, acc);
+  spmv_row<T, true>(__ldg(&pt->nu), __ldg(&pt->nv), N, al - cp0, K + cp0, x + cp0, acc);
   y[al] = acc[0];
   y[N + al] = acc[1];
   y[2 * N + al] = acc[2];

@@ -1,7 +1,7 @@
 // K2: per-span membrane + bending energy, gradient and 27x27 Hessian.
 //
-// One thread per knot span.  Per membrane point (FBW, Eqs. anisotropic
-// invariants and FBW stretching and shearing energy):
+// Per membrane point (FBW, Eqs. anisotropic invariants and FBW stretching
+// and shearing energy):
 //   f_beta = F e_beta = sum_l C_l g_l,beta,   I5(e_b) = |f_b|^2,  I6 = f_1 . f_2
 //   Psi = mu_st1 (|f_1| - 1)^2 + mu_st2 (|f_2| - 1)^2 + mu_sh I6^2
 // with the analytic derivatives w.r.t. (f_1, f_2) chained to the 27 span DOFs
@@ -10,18 +10,38 @@
 //   Psi = mu_bd/2 |sum_l L_l C_l|^2   (quadratic, constant Hessian).
 // The control points of the span are shifted by the span's centre control
 // point before forming f (sum_l g_l = 0), which keeps FP32 strains accurate
-// far from the origin.  Energies accumulate in FP64.  The Hessian is summed
-// in shared memory (interleaved by thread, packed upper triangle) and
-// written as planes; the weighted 6x6 d^2 Psi/df^2 of every membrane point
-// is kept for the FP64 projection.
+// far from the origin.  Energies accumulate in FP64.
 //
-// Blocks take work items: a patch and either a run of BLOCK consecutive
-// spans of it or a tu x (BLOCK / tu) tile of spans, the tile shape chosen per
+// A block evaluates 32 spans (one per lane) with 8 warps, each warp a slice
+// of every span's work.  Phase 1 evaluates the quadrature points (slice k
+// takes the span's points k and k + 8): energy, weighted dPsi/df, the
+// weighted 6x6 d^2 Psi/df^2 (also kept in global memory for the FP64
+// projection) and the point's derivative vectors go to shared memory.
+// Phase 2 sums them into the span terms: slice w owns the 3x3 blocks
+// (l <= m) w, w + 8, ... of the Hessian (five or six of the 45) and
+// gradient row w (slice 7 also row 8), accumulated in registers, so every
+// store is a coalesced 32-span row of an entry plane.  Points come in
+// rounds of ten slots per span (a corner span has nine membrane points and
+// one bending point).
+//
+// Blocks take work items: a patch and either a run of 32 consecutive spans
+// of it or a tu x (32 / tu) tile of spans, the tile shape chosen per
 // patch-size class by the autotuner (bsc_autotune).  All patches of a
 // context are evaluated by one launch.
+//
+// A tile's control-point footprint, (tu + 2) x (tv + 2) points of each of
+// the three coordinate planes, is staged in shared memory by TMA: one box
+// load per plane row from a rank-1 tensor map over the planes, the row's
+// start rounded down to a 16-byte boundary (patch widths are arbitrary, so
+// a 2-D map would violate TMA's stride alignment).  Runs of consecutive
+// spans read their control points from global memory directly.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <vector>
 
 #include "bsc_internal.cuh"
+#include "tc05.cuh"
 
 namespace {
 
@@ -40,183 +60,368 @@ struct SpanArgs {
   T* __restrict__ g;
   T* __restrict__ H;
   T* __restrict__ A;
+  int* __restrict__ status;
 };
+
+// Block shape: SPB spans (lane = span) x SLICES warps.
+constexpr int SPB = 32, SLICES = 8, EVAL_BLOCK = SPB * SLICES;
+// Point slots per span and round, values per slot: membrane g (9 x 2),
+// weighted d^2 Psi/df^2 (packed upper 6x6) and weighted dPsi/df (2 x 3);
+// bending L (9), W mu_bd and the Laplacian sum_l L_l C_l (3).
+constexpr int MAXPT = 10, NV = 45;
+constexpr int V_G = 0, V_A = 18, V_DP = 39;
+constexpr int V_L = 0, V_WB = 9, V_LAP = 10;
+// The 45 3x3 blocks (l <= m) of the span Hessian; slice w owns blocks
+// w + 8 i, i < BPS (six for w < 5, five otherwise).
+constexpr int NBLK = 45, BPS = 6;
+
+// TMA staging of a tile's control points: box width in elements (tile width
+// 32 + 2 halo points + up to 3 elements of alignment slack, rounded to 16
+// bytes), the row pitch in shared memory (128-byte aligned boxes) and the
+// number of rows a block can hold (narrowest tile: 8 spans wide).
+constexpr int TMA_W = 40;
+template <typename T>
+struct CTile {
+  static constexpr int ALIGN = 16 / (int)sizeof(T);
+  static constexpr int PITCH = (int)(((TMA_W * sizeof(T) + 127) / 128) * 128 / sizeof(T));
+};
+constexpr int ROWS = SPB / 8 + 2;
+constexpr long long TMA_WAIT_LIMIT = 1ll << 24;
+
+template <typename T>
+constexpr size_t span_smem() {
+  return 128 + sizeof(T) * 3 * ROWS * CTile<T>::PITCH + 16 + sizeof(T) * MAXPT * NV * SPB +
+         sizeof(double) * MAXPT * SPB;
+}
 
 template <typename T> __device__ __forceinline__ T rsqrt_(T x);
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
 
-template <typename T, bool GRAD, bool HESS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_span_eval(SpanArgs<T> P) {
+// (l, m), l <= m, of block b in row order.
+__device__ __forceinline__ void block_lm(int b, int& l, int& m) {
+  l = 0;
+  int rem = b;
+  while (rem >= 9 - l) {
+    rem -= 9 - l;
+    ++l;
+  }
+  m = l + rem;
+}
+
+template <typename T, bool GRAD, bool HESS>
+__global__ void __launch_bounds__(EVAL_BLOCK, sizeof(T) == 4 ? 2 : 1)
+    k_span_eval(SpanArgs<T> P, const __grid_constant__ CUtensorMap cmap) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* Hs = reinterpret_cast<T*>(smraw);
+  constexpr int PITCH = CTile<T>::PITCH, ALIGN = CTile<T>::ALIGN;
+  const uint32_t pad = (128u - (tc05::smem_u32(smraw) & 127u)) & 127u;
+  T* Ct = reinterpret_cast<T*>(smraw + pad);                 // [3][rows][PITCH] control-point boxes
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Ct + 3 * ROWS * PITCH);
+  T* S = reinterpret_cast<T*>(bar + 2);                      // [MAXPT][NV][SPB] point slots
+  double* Es = reinterpret_cast<double*>(S + MAXPT * NV * SPB);  // [MAXPT][SPB] point energies
   const SpanItem it = P.items[blockIdx.x];
   if (P.gate && P.gate[it.p].state != 1) return;
+  const int j = threadIdx.x & 31, sl = threadIdx.x >> 5;
   const PatchDev* pt = P.pd + it.p;
-  const int Su = __ldg(&pt->Su), nu = __ldg(&pt->nu);
+  const int Su = __ldg(&pt->Su), nu = __ldg(&pt->nu), cp0 = __ldg(&pt->cp0);
   int a, b;
+  bool valid;
   if (it.tu == 0) {
-    const int sl = it.first_or_a0 + threadIdx.x;
-    if (sl >= __ldg(&pt->Nsp)) return;
-    a = sl % Su;
-    b = sl / Su;
+    const int sp = it.first_or_a0 + j;
+    valid = sp < __ldg(&pt->Nsp);
+    a = sp % Su;
+    b = sp / Su;
   } else {
-    a = it.first_or_a0 + threadIdx.x % it.tu;
-    b = it.b0 + threadIdx.x / it.tu;
-    if (a >= Su || b >= __ldg(&pt->Sv)) return;
+    a = it.first_or_a0 + j % it.tu;
+    b = it.b0 + j / it.tu;
+    valid = a < Su && b < __ldg(&pt->Sv);
   }
-  const int s = __ldg(&pt->sp0) + b * Su + a;
-  const T* __restrict__ Cp = P.C + __ldg(&pt->cp0);
+  // tile: stage the footprint rows of the three planes by TMA (block-uniform)
+  const int rows = it.tu > 0 ? SPB / it.tu + 2 : 0;
+  const bool staged = it.tu >= 8 && rows <= ROWS;
+  const int gbase = cp0 + it.b0 * nu + it.first_or_a0;  // plane index of the tile's first control point
+  if (staged) {
+    const int nload = 3 * rows;
+    if (threadIdx.x == 0) {
+      tc05::mbar_init(bar, 1);
+      tc05::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      if (threadIdx.x == 0) tc05::mbar_arrive_expect_tx(bar, (uint32_t)(nload * TMA_W * sizeof(T)));
+      __syncwarp();
+      for (int i = threadIdx.x; i < nload; i += 32) {
+        const int c = i / rows, r = i - c * rows;
+        const int g = c * P.N + gbase + r * nu;
+        tc05::tma_load_1d(Ct + i * PITCH, &cmap, g & ~(ALIGN - 1), bar);
+      }
+    }
+    const bool landed = tc05::mbar_wait(bar, 0, TMA_WAIT_LIMIT);
+    if (__syncthreads_or(!landed)) {  // the whole block leaves together
+      if (threadIdx.x == 0) atomicOr(P.status, BSC_STATUS_TIMEOUT_FLAG);
+      tc05::mbar_wait(bar, 0, TMA_WAIT_LIMIT);  // let the copies in flight land before leaving
+      return;
+    }
+  }
+  const int s = valid ? __ldg(&pt->sp0) + b * Su + a : 0;
+  int q0 = 0, nm = 0, r0 = 0, nb = 0;
+  if (valid) {
+    q0 = P.moff[s];
+    nm = P.moff[s + 1] - q0;
+    r0 = P.boff[s];
+    nb = P.boff[s + 1] - r0;
+  }
+  const int npt = nm + nb;
+  const int mx = __reduce_max_sync(0xffffffffu, npt);  // the same in every warp (lane = span)
   const T mu1 = (T)__ldg(&pt->mu1), mu2 = (T)__ldg(&pt->mu2), mush = (T)__ldg(&pt->mush),
           mubd = (T)__ldg(&pt->mubd);
-  auto HS = [&](int r, int c) -> T& { return Hs[upk(r, c, 27) * BLOCK + threadIdx.x]; };
+  const T* __restrict__ Cp = P.C + cp0;
+  auto SV = [&](int k, int v) -> T& { return S[(k * NV + v) * SPB + j]; };
 
-  // control points relative to the span's centre control point
-  T Cl[9][3];
-  {
-    const int ac = (b + 1) * nu + a + 1;
-    T c0[3];
+  // this slice's Hessian blocks and gradient rows
+  int bl[BPS], bm[BPS];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) c0[c] = Cp[c * P.N + ac];
-#pragma unroll
-    for (int l = 0; l < 9; ++l) {
-      const int al = (b + l / 3) * nu + a + l % 3;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Cl[l][c] = Cp[c * P.N + al] - c0[c];
-    }
+  for (int i = 0; i < BPS; ++i) {
+    bl[i] = bm[i] = 0;
+    if (sl + SLICES * i < NBLK) block_lm(sl + SLICES * i, bl[i], bm[i]);
   }
+  const int nblk = sl + SLICES * (BPS - 1) < NBLK ? BPS : BPS - 1;
+  const int grow1 = sl == SLICES - 1 ? 8 : -1;
+  T acc[BPS][3][3];
+  T gacc[2][3];
+#pragma unroll
+  for (int i = 0; i < BPS; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) acc[i][c][d] = T(0);
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gacc[r][c] = T(0);
   double E = 0.0;
-  T g[27];
-#pragma unroll
-  for (int k = 0; k < 27; ++k) g[k] = T(0);
-  if (HESS) {
-#pragma unroll 1
-    for (int k = 0; k < H27; ++k) Hs[k * BLOCK + threadIdx.x] = T(0);
-  }
 
-  const int q0 = P.moff[s], q1 = P.moff[s + 1];
-  for (int q = q0; q < q1; ++q) {
-    const T W = P.tabm[q];
-    T gq[9][2];
-#pragma unroll
-    for (int l = 0; l < 9; ++l) {
-      gq[l][0] = P.tabm[(1 + 2 * l) * P.Nm + q];
-      gq[l][1] = P.tabm[(2 + 2 * l) * P.Nm + q];
-    }
-    T f[2][3];
-#pragma unroll
-    for (int be = 0; be < 2; ++be)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        T acc = T(0);
-#pragma unroll
-        for (int l = 0; l < 9; ++l) acc += Cl[l][c] * gq[l][be];
-        f[be][c] = acc;
-      }
-    const T I5a = f[0][0] * f[0][0] + f[0][1] * f[0][1] + f[0][2] * f[0][2];
-    const T I5b = f[1][0] * f[1][0] + f[1][1] * f[1][1] + f[1][2] * f[1][2];
-    const T I6 = f[0][0] * f[1][0] + f[0][1] * f[1][1] + f[0][2] * f[1][2];
-    const T r1 = rsqrt_(I5a), r2 = rsqrt_(I5b);  // 1 / |f_b|
-    const T s1 = I5a * r1, s2 = I5b * r2;
-    const T e1 = s1 - T(1), e2 = s2 - T(1);
-    E += (double)W * (double)(mu1 * e1 * e1 + mu2 * e2 * e2 + mush * I6 * I6);
-    // dPsi/df_b = 2 mu_b (1 - 1/|f_b|) f_b + 2 mu_sh I6 f_other
-    const T k1 = T(2) * mu1 * (T(1) - r1), k2 = T(2) * mu2 * (T(1) - r2), ks = T(2) * mush * I6;
-    if (GRAD) {
-      T dP[2][3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        dP[0][c] = W * (k1 * f[0][c] + ks * f[1][c]);
-        dP[1][c] = W * (k2 * f[1][c] + ks * f[0][c]);
-      }
-#pragma unroll
-      for (int l = 0; l < 9; ++l)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) g[3 * l + c] += gq[l][0] * dP[0][c] + gq[l][1] * dP[1][c];
-    }
-    if (HESS) {
-      // weighted d^2 Psi / d f_(b c) d f_(d e), 6x6 with index 3 b + c
-      T A6[6][6];
-      const T c1 = T(2) * mu1 * r1 * r1 * r1, c2 = T(2) * mu2 * r2 * r2 * r2, cs = T(2) * mush;
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const T del = (c == d) ? T(1) : T(0);
-          A6[c][d] = W * (k1 * del + c1 * f[0][c] * f[0][d] + cs * f[1][c] * f[1][d]);
-          A6[3 + c][3 + d] = W * (k2 * del + c2 * f[1][c] * f[1][d] + cs * f[0][c] * f[0][d]);
-          A6[c][3 + d] = W * (cs * f[1][c] * f[0][d] + ks * del);
-          A6[3 + d][c] = A6[c][3 + d];
-        }
-      {
-        int e = 0;
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-          for (int c = r; c < 6; ++c) P.A[(size_t)(e++) * P.Nm + q] = A6[r][c];
-      }
-      // H_(l c)(m d) += sum_{b,d'} g_l,b g_m,d' A6[3b+c][3d'+d]
-#pragma unroll
-      for (int l = 0; l < 9; ++l) {
-        T Tl[3][6];  // Tl[c][k] = sum_b g_l,b A6[3b+c][k]
+  for (int base = 0; base < mx; base += MAXPT) {
+    // ---- phase 1: points base + sl and base + sl + 8 of the span
+#pragma unroll 1
+    for (int k = sl; k < MAXPT; k += SLICES) {
+      const int pi = base + k;
+      if (!valid || pi >= npt) continue;
+      // control points relative to the span's centre control point
+      T Cl[9][3];
+      if (staged) {
+        const int rr = b - it.b0, i0 = a - it.first_or_a0;
+        const T* row[3][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int k = 0; k < 6; ++k) Tl[c][k] = gq[l][0] * A6[c][k] + gq[l][1] * A6[3 + c][k];
+          for (int jj = 0; jj < 3; ++jj) {
+            const int g = c * P.N + gbase + (rr + jj) * nu;
+            row[c][jj] = Ct + (c * rows + rr + jj) * PITCH + (g & (ALIGN - 1)) + i0;
+          }
+        T c0[3];
 #pragma unroll
-        for (int m = l; m < 9; ++m)
+        for (int c = 0; c < 3; ++c) c0[c] = row[c][1][1];
+#pragma unroll
+        for (int l = 0; l < 9; ++l)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Cl[l][c] = row[c][l / 3][l % 3] - c0[c];
+      } else {
+        const int ac = (b + 1) * nu + a + 1;
+        T c0[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) c0[c] = Cp[c * P.N + ac];
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+          const int al = (b + l / 3) * nu + a + l % 3;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Cl[l][c] = Cp[c * P.N + al] - c0[c];
+        }
+      }
+      if (pi < nm) {
+        const int q = q0 + pi;
+        const T W = P.tabm[q];
+        T gq[9][2];
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+          gq[l][0] = P.tabm[(1 + 2 * l) * P.Nm + q];
+          gq[l][1] = P.tabm[(2 + 2 * l) * P.Nm + q];
+        }
+        T f[2][3];
+#pragma unroll
+        for (int be = 0; be < 2; ++be)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            T acc1 = T(0);
+#pragma unroll
+            for (int l = 0; l < 9; ++l) acc1 += Cl[l][c] * gq[l][be];
+            f[be][c] = acc1;
+          }
+        const T I5a = f[0][0] * f[0][0] + f[0][1] * f[0][1] + f[0][2] * f[0][2];
+        const T I5b = f[1][0] * f[1][0] + f[1][1] * f[1][1] + f[1][2] * f[1][2];
+        const T I6 = f[0][0] * f[1][0] + f[0][1] * f[1][1] + f[0][2] * f[1][2];
+        const T r1 = rsqrt_(I5a), r2 = rsqrt_(I5b);  // 1 / |f_b|
+        const T s1 = I5a * r1, s2 = I5b * r2;
+        const T e1 = s1 - T(1), e2 = s2 - T(1);
+        Es[k * SPB + j] = (double)W * (double)(mu1 * e1 * e1 + mu2 * e2 * e2 + mush * I6 * I6);
+        // dPsi/df_b = 2 mu_b (1 - 1/|f_b|) f_b + 2 mu_sh I6 f_other
+        const T k1 = T(2) * mu1 * (T(1) - r1), k2 = T(2) * mu2 * (T(1) - r2), ks = T(2) * mush * I6;
+        if (GRAD || HESS) {
+#pragma unroll
+          for (int l = 0; l < 9; ++l) {
+            SV(k, V_G + 2 * l) = gq[l][0];
+            SV(k, V_G + 2 * l + 1) = gq[l][1];
+          }
+        }
+        if (GRAD) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            SV(k, V_DP + c) = W * (k1 * f[0][c] + ks * f[1][c]);
+            SV(k, V_DP + 3 + c) = W * (k2 * f[1][c] + ks * f[0][c]);
+          }
+        }
+        if (HESS) {
+          // weighted d^2 Psi / d f_(b c) d f_(d e), 6x6 with index 3 b + c
+          T A6[6][6];
+          const T c1 = T(2) * mu1 * r1 * r1 * r1, c2 = T(2) * mu2 * r2 * r2 * r2, cs = T(2) * mush;
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-              if (m == l && d < c) continue;
-              HS(3 * l + c, 3 * m + d) += Tl[c][d] * gq[m][0] + Tl[c][3 + d] * gq[m][1];
+              const T del = (c == d) ? T(1) : T(0);
+              A6[c][d] = W * (k1 * del + c1 * f[0][c] * f[0][d] + cs * f[1][c] * f[1][d]);
+              A6[3 + c][3 + d] = W * (k2 * del + c2 * f[1][c] * f[1][d] + cs * f[0][c] * f[0][d]);
+              A6[c][3 + d] = W * (cs * f[1][c] * f[0][d] + ks * del);
+              A6[3 + d][c] = A6[c][3 + d];
             }
+          int e = 0;
+#pragma unroll
+          for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int c = r; c < 6; ++c, ++e) {
+              SV(k, V_A + e) = A6[r][c];
+              P.A[(size_t)e * P.Nm + q] = A6[r][c];
+            }
+        }
+      } else {
+        const int q = r0 + pi - nm;
+        const T WB = P.tabb[q] * mubd;  // W mu_bd
+        T L[9];
+#pragma unroll
+        for (int l = 0; l < 9; ++l) L[l] = P.tabb[(1 + l) * P.Nb + q];
+        T lap[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T acc1 = T(0);
+#pragma unroll
+          for (int l = 0; l < 9; ++l) acc1 += L[l] * Cl[l][c];
+          lap[c] = acc1;
+        }
+        Es[k * SPB + j] = 0.5 * (double)WB * (double)(lap[0] * lap[0] + lap[1] * lap[1] + lap[2] * lap[2]);
+        if (GRAD || HESS) {
+#pragma unroll
+          for (int l = 0; l < 9; ++l) SV(k, V_L + l) = L[l];
+          SV(k, V_WB) = WB;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) SV(k, V_LAP + c) = lap[c];
+        }
       }
     }
-  }
-
-  const int p0 = P.boff[s], p1 = P.boff[s + 1];
-  for (int q = p0; q < p1; ++q) {
-    const T WB = P.tabb[q] * mubd;  // W mu_bd
-    T L[9];
+    __syncthreads();
+    // ---- phase 2: this slice's blocks and rows, summed over the round's points
+    const int kmax = valid ? min(MAXPT, npt - base) : 0;
+    if (GRAD || HESS) {
+#pragma unroll 1
+      for (int k = 0; k < kmax; ++k) {
+        if (base + k < nm) {
+          if (HESS) {
+            T A[6][6];
+            int e = 0;
 #pragma unroll
-    for (int l = 0; l < 9; ++l) L[l] = P.tabb[(1 + l) * P.Nb + q];
-    T lap[3];
+            for (int r = 0; r < 6; ++r)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T acc = T(0);
+              for (int c = r; c < 6; ++c, ++e) {
+                A[r][c] = SV(k, V_A + e);
+                A[c][r] = A[r][c];
+              }
 #pragma unroll
-      for (int l = 0; l < 9; ++l) acc += L[l] * Cl[l][c];
-      lap[c] = acc;
-    }
-    E += 0.5 * (double)WB * (double)(lap[0] * lap[0] + lap[1] * lap[1] + lap[2] * lap[2]);
-    if (GRAD) {
+            for (int i = 0; i < BPS; ++i) {
+              if (i >= nblk) break;
+              const T gl0 = SV(k, V_G + 2 * bl[i]), gl1 = SV(k, V_G + 2 * bl[i] + 1);
+              const T gm0 = SV(k, V_G + 2 * bm[i]), gm1 = SV(k, V_G + 2 * bm[i] + 1);
+              // H_(l c)(m d) += sum_{beta, delta} g_l,beta g_m,delta A6[3 beta + c][3 delta + d]
 #pragma unroll
-      for (int l = 0; l < 9; ++l)
+              for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) g[3 * l + c] += WB * L[l] * lap[c];
-    }
-    if (HESS) {
+                for (int d = 0; d < 3; ++d) {
+                  const T u = gm0 * A[c][d] + gm1 * A[c][3 + d];
+                  const T v = gm0 * A[3 + c][d] + gm1 * A[3 + c][3 + d];
+                  acc[i][c][d] += gl0 * u + gl1 * v;
+                }
+            }
+          }
+          if (GRAD) {
 #pragma unroll
-      for (int l = 0; l < 9; ++l)
+            for (int r = 0; r < 2; ++r) {
+              const int l = r == 0 ? sl : grow1;
+              if (l < 0) break;
+              const T g0 = SV(k, V_G + 2 * l), g1 = SV(k, V_G + 2 * l + 1);
 #pragma unroll
-        for (int m = l; m < 9; ++m) {
-          const T h = WB * L[l] * L[m];
+              for (int c = 0; c < 3; ++c) gacc[r][c] += g0 * SV(k, V_DP + c) + g1 * SV(k, V_DP + 3 + c);
+            }
+          }
+        } else {
+          const T WB = SV(k, V_WB);
+          if (HESS) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) HS(3 * l + c, 3 * m + c) += h;
+            for (int i = 0; i < BPS; ++i) {
+              if (i >= nblk) break;
+              const T h = WB * SV(k, V_L + bl[i]) * SV(k, V_L + bm[i]);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) acc[i][c][c] += h;
+            }
+          }
+          if (GRAD) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              const int l = r == 0 ? sl : grow1;
+              if (l < 0) break;
+              const T wl = WB * SV(k, V_L + l);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) gacc[r][c] += wl * SV(k, V_LAP + c);
+            }
+          }
         }
+      }
     }
+    if (sl == 0)
+      for (int k = 0; k < kmax; ++k) E += Es[k * SPB + j];
+    if (base + MAXPT < mx) __syncthreads();
   }
 
-  P.E[s] = E;
+  if (!valid) return;
+  if (sl == 0) P.E[s] = E;
   if (GRAD) {
 #pragma unroll
-    for (int k = 0; k < 27; ++k) P.g[(size_t)k * P.Nsp + s] = g[k];
+    for (int r = 0; r < 2; ++r) {
+      const int l = r == 0 ? sl : grow1;
+      if (l < 0) break;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) P.g[(size_t)(3 * l + c) * P.Nsp + s] = gacc[r][c];
+    }
   }
   if (HESS) {
-#pragma unroll 1
-    for (int k = 0; k < H27; ++k) P.H[(size_t)k * P.Nsp + s] = Hs[k * BLOCK + threadIdx.x];
+#pragma unroll
+    for (int i = 0; i < BPS; ++i) {
+      if (i >= nblk) break;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (bl[i] == bm[i] && d < c) continue;
+          P.H[(size_t)upk(3 * bl[i] + c, 3 * bm[i] + d, 27) * P.Nsp + s] = acc[i][c][d];
+        }
+    }
   }
 }
 
@@ -229,37 +434,72 @@ SpanArgs<T> make_args(bsc_ctx* c, const void* C, const SpanItem* items, const Pa
   P.moff = c->mem_off; P.boff = c->bd_off;
   P.tabm = (const T*)c->tab_mem; P.tabb = (const T*)c->tab_bd;
   P.E = c->E_span; P.g = (T*)c->g_span; P.H = (T*)c->H_span; P.A = (T*)c->A_mem;
+  P.status = c->dstatus;
   return P;
 }
 
-template <typename T, int BLOCK>
+// Rank-1 tiled tensor map over the three coordinate planes of C (3 N
+// elements from a 16-byte aligned base), box TMA_W elements, zero fill past
+// the end.  The encoder comes from the driver through the runtime.
+template <typename T>
+cudaError_t planes_map(CUtensorMap* m, const void* C, int N) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  if ((reinterpret_cast<uintptr_t>(C) & 15u) != 0 || 3ll * N >= (1ll << 31)) return cudaErrorInvalidValue;
+  const cuuint64_t dim[1] = {(cuuint64_t)3 * (cuuint64_t)N};
+  const cuuint64_t stride[1] = {0};  // rank 1: no strides
+  const cuuint32_t box[1] = {(cuuint32_t)TMA_W}, estride[1] = {1};
+  const CUresult r = encode(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 1,
+                            const_cast<void*>(C), dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename T>
 cudaError_t run(bsc_ctx* c, const void* C, int want_grad, int want_hess, const SpanItem* items, int n_items,
                 const PatchStep* gate) {
   if (n_items <= 0) return cudaSuccess;
   SpanArgs<T> P = make_args<T>(c, C, items, gate);
+  CUtensorMap m;
+  cudaError_t e = planes_map<T>(&m, C, c->N);
+  if (e != cudaSuccess) return e;
   if (want_hess)
-    k_span_eval<T, true, true, BLOCK><<<n_items, BLOCK, sizeof(T) * H27 * BLOCK, c->stream>>>(P);
+    k_span_eval<T, true, true><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
   else if (want_grad)
-    k_span_eval<T, true, false, BLOCK><<<n_items, BLOCK, 0, c->stream>>>(P);
+    k_span_eval<T, true, false><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
   else
-    k_span_eval<T, false, false, BLOCK><<<n_items, BLOCK, 0, c->stream>>>(P);
+    k_span_eval<T, false, false><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
   return cudaGetLastError();
 }
 
-constexpr int BLOCK64 = 64, BLOCK32 = 128;
+template <typename T>
+cudaError_t set_smem() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_span_eval<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)span_smem<T>())) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_span_eval<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)span_smem<T>())) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_span_eval<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)span_smem<T>());
+}
 
 }  // namespace
 
-int span_block(int precision) { return precision == BSC_FP64 ? BLOCK64 : BLOCK32; }
+int span_block(int) { return SPB; }
 
-// The Hessian variant keeps its 27x27 accumulator in shared memory (378
-// entries per thread): opt in to more than 48 KB once per context.
+// The point slots exceed 48 KB of shared memory: opt in once per context.
 cudaError_t setup_span_eval(bsc_ctx* c) {
-  if (c->precision == BSC_FP64)
-    return cudaFuncSetAttribute(k_span_eval<double, true, true, BLOCK64>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * H27 * BLOCK64));
-  return cudaFuncSetAttribute(k_span_eval<float, true, true, BLOCK32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(float) * H27 * BLOCK32));
+  return c->precision == BSC_FP64 ? set_smem<double>() : set_smem<float>();
 }
 
 // Work items of every patch (or of one size class) with the tile shape of
@@ -303,13 +543,12 @@ cudaError_t build_span_items(bsc_ctx* c) {
 cudaError_t launch_span_eval_items(bsc_ctx* c, const void* C, int want_grad, int want_hess, const SpanItem* items,
                                    int n_items, int) {
   BSC_COUNT(c, 1);
-  if (c->precision == BSC_FP64) return run<double, BLOCK64>(c, C, want_grad, want_hess, items, n_items, nullptr);
-  return run<float, BLOCK32>(c, C, want_grad, want_hess, items, n_items, nullptr);
+  if (c->precision == BSC_FP64) return run<double>(c, C, want_grad, want_hess, items, n_items, nullptr);
+  return run<float>(c, C, want_grad, want_hess, items, n_items, nullptr);
 }
 
 cudaError_t launch_span_eval(bsc_ctx* c, const void* C, int want_grad, int want_hess, const PatchStep* gate) {
   BSC_COUNT(c, 1);
-  if (c->precision == BSC_FP64)
-    return run<double, BLOCK64>(c, C, want_grad, want_hess, c->span_items, c->n_span_items, gate);
-  return run<float, BLOCK32>(c, C, want_grad, want_hess, c->span_items, c->n_span_items, gate);
+  if (c->precision == BSC_FP64) return run<double>(c, C, want_grad, want_hess, c->span_items, c->n_span_items, gate);
+  return run<float>(c, C, want_grad, want_hess, c->span_items, c->n_span_items, gate);
 }

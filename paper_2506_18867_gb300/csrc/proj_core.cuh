@@ -2,11 +2,12 @@
 // one GPU thread per span with a small on-chip working set:
 //   A  packed lower triangle of the reduced Hessian (3D x 3D), then the
 //      Householder vectors, with tau_k kept in the freed diagonal slot;
-//   R  3n doubles: first the orthonormal basis Q (9 x D), then the scaled
-//      tridiagonal (d, e, e^2);
-//   Qs, Ys  per-thread scratch slots (global memory): the basis Q for the
-//      final mapping and the eigenvectors found so far (for
-//      re-orthogonalisation inside clusters).
+//   R  3n doubles: the scaled tridiagonal (d, e, e^2);
+//   Qs  the span's orthonormal basis Q (9 x D) of its derivative vectors,
+//      and the derivative vectors in that basis, computed once per context
+//      from the rest geometry (span_basis, by the caller);
+//   Ys  per-thread scratch slot (global memory): the eigenvectors found so
+//      far (for re-orthogonalisation inside clusters).
 // The span Hessian in HBM is corrected in place, P = H - sum lam w w^T over
 // the negative eigenpairs.  __host__ __device__ so the same code runs on the
 // host for checks.
@@ -59,29 +60,88 @@ BSC_HD int expo_of(double x) {
 #endif
 }
 
-// Eigenvalues of the scaled tridiagonal below x (signs of the leading
-// principal minors of T - x I; Sylvester's law of inertia).  d at R[0..n),
-// e^2 at R[2n..3n).  Minors are kept in range by exact power-of-two scaling.
-template <int n>
-BSC_HD int sturm(const View& R, double x) {
-  double pm = 1.0, p = R[0] - x;
+// det(T - x I) of a scaled tridiagonal (d[0..n), e^2[0..n-1)) by the
+// three-term recurrence of the leading principal minors, with the Sturm
+// count (sign changes of the minors = eigenvalues below x, by Sylvester's
+// law of inertia).  An exact zero minor is replaced by a tiny value of the
+// sign opposite to its predecessor.  The recurrence is homogeneous in
+// (p_i, p_i-1): char_poly_scaled rescales the pair by a power of two
+// whenever the larger of the two leaves [2^-500, 2^500].  *exact is false
+// when a replacement or a rescaling made the value's scale differ from the
+// determinant's.
+template <int n, class DA, class EA>
+BSC_PHASE double char_poly_scaled(const DA& d, const EA& e2, double x, int* cnt_out, bool* exact) {
+  double pm = 1.0, p = d[0] - x;
   int cnt = sign_of(p);
-#pragma unroll
+  bool ok = true;
+#pragma unroll 1
   for (int i = 1; i < n; ++i) {
-    double pn = (R[i] - x) * p - R[2 * n + i - 1] * pm;
-    if (expo_of(pn) == 0) pn = sign_of(p) ? 1e-300 : -1e-300;  // exact zero: sign opposite to p
+    double pn = (d[i] - x) * p - e2[i - 1] * pm;
+    if (expo_of(pn) == 0) {
+      pn = sign_of(p) ? 1e-300 : -1e-300;
+      ok = false;
+    }
     cnt += sign_of(pn) ^ sign_of(p);
-    // the recurrence is homogeneous in (p_i, p_i-1): rescale the pair by a power
-    // of two when the larger of the two leaves [2^-500, 2^500]
     const int ea = expo_of(pn), eb = expo_of(p), mx = ea > eb ? ea : eb;
     if (mx > 1023 + 500 || mx < 1023 - 500) {
       const double sc = mx > 1023 ? 0x1p-500 : 0x1p500;
       pn *= sc;
       p *= sc;
+      ok = false;
     }
     pm = p;
     p = pn;
   }
+  *cnt_out = cnt;
+  *exact = ok;
+  return p;
+}
+
+// The same value and count.  With ||T|| <= 1 the minors of the sizes used
+// here (n <= 24) stay far inside that range, so this pass runs the
+// recurrence without rescaling and tracks the exponents with integer
+// operations only; the rare pair that leaves the range sends the call to
+// char_poly_scaled, which then gives the identical result.  No FP64
+// instruction is predicated (a predicated FP64 instruction occupies the
+// FP64 pipe like an executed one).
+template <int n, class DA, class EA>
+BSC_HD double char_poly(const DA& d, const EA& e2, double x, int* cnt_out, bool* exact) {
+  double pm = 1.0, p = d[0] - x;
+  int cnt = sign_of(p), eb = expo_of(p);
+  bool ok = true, in_range = true;
+#pragma unroll
+  for (int i = 1; i < n; ++i) {
+    double pn = (d[i] - x) * p - e2[i - 1] * pm;
+    const bool z = expo_of(pn) == 0;
+    pn = z ? (sign_of(p) ? 1e-300 : -1e-300) : pn;
+    ok = ok && !z;
+    cnt += sign_of(pn) ^ sign_of(p);
+    const int ea = expo_of(pn), mx = ea > eb ? ea : eb;
+    in_range = in_range && mx <= 1023 + 500 && mx >= 1023 - 500;
+    pm = p;
+    p = pn;
+    eb = ea;
+  }
+  if (!in_range) return char_poly_scaled<n>(d, e2, x, cnt_out, exact);
+  *cnt_out = cnt;
+  *exact = ok;
+  return p;
+}
+
+// Offset accessor of a strided view (e^2 of the tridiagonal kept in R).
+struct ViewAt {
+  View v;
+  int o;
+  BSC_HD double operator[](int i) const { return v[o + i]; }
+};
+
+// Eigenvalues of the scaled tridiagonal below x; d at R[0..n), e^2 at
+// R[2n..3n).
+template <int n>
+BSC_HD int sturm(const View& R, double x) {
+  int cnt;
+  bool ex;
+  char_poly<n>(ViewAt{R, 0}, ViewAt{R, 2 * n}, x, &cnt, &ex);
   return cnt;
 }
 
@@ -134,21 +194,14 @@ BSC_HD void back_transform(const View& A, double (&x)[n]) {
   }
 }
 
-// Phase 1 of a span: basis, reduced Hessian, tridiagonal form, inertia.
-// Tab: nm(), nb(), g(q, l, beta), L(q, l), wb(q) = W mu_bd, a6(q, e) (packed
-// upper 6x6).  On return R holds the scaled tridiagonal (d, e, e^2), A the
-// reflectors, Qs the basis, *tn the scale; returns the number of eigenvalues
-// below -neg_rel ||T|| (-1 on a non-finite matrix).
-template <int D, class Tab>
-BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, const View& Qs, double* tn_out,
-                       double neg_rel, double rank_rel) {
-  constexpr int n = 3 * D;
-  constexpr int NP = n * (n + 1) / 2;
-#pragma unroll 1
-  for (int k = 0; k < NP; ++k) A[k] = 0.0;
-
-  // 1. orthonormal basis Q (rows of R) of the span of the derivative vectors,
-  //    with the constant vector removed (it lies in the kernel of every one)
+// Orthonormal basis Q (rows Q[9 k + l], k < D) of the span of a span's
+// derivative vectors {g_q,beta, L_b} with the constant vector removed (it
+// lies in the kernel of every one): modified Gram-Schmidt with one
+// re-orthogonalisation pass; a candidate whose residual is below rank_rel of
+// its norm is dependent and skipped, unused rows are zero.  Depends on the
+// rest geometry only.  Returns the rank.
+template <int D, class Tab, class QView>
+BSC_HD int span_basis(const Tab& tab, const QView& Q, double rank_rel) {
   int d = 0;
   const int nm = tab.nm(), nb = tab.nb(), nvec = 2 * nm + nb;
   for (int iv = 0; iv < nvec; ++iv) {
@@ -178,9 +231,9 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, const Vi
         if (k >= d) break;
         double dt = 0.0;
 #pragma unroll
-        for (int l = 0; l < 9; ++l) dt += R[9 * k + l] * v[l];
+        for (int l = 0; l < 9; ++l) dt += Q[9 * k + l] * v[l];
 #pragma unroll
-        for (int l = 0; l < 9; ++l) v[l] -= dt * R[9 * k + l];
+        for (int l = 0; l < 9; ++l) v[l] -= dt * Q[9 * k + l];
       }
     double n1 = 0.0;
 #pragma unroll
@@ -188,27 +241,36 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, const Vi
     if (n1 <= rank_rel * rank_rel * n0) continue;
     const double inv = 1.0 / sqrt(n1);
 #pragma unroll
-    for (int l = 0; l < 9; ++l) R[9 * d + l] = v[l] * inv;
+    for (int l = 0; l < 9; ++l) Q[9 * d + l] = v[l] * inv;
     ++d;
   }
   for (int k = d; k < D; ++k)
 #pragma unroll
-    for (int l = 0; l < 9; ++l) R[9 * k + l] = 0.0;
+    for (int l = 0; l < 9; ++l) Q[9 * k + l] = 0.0;
+  return d;
+}
 
-  // 2. reduced Hessian, lower triangle, index 3k + c
+// Phase 1 of a span: reduced Hessian, tridiagonal form, inertia.
+// Tab: nm(), nb(), wb(q) = W mu_bd, a6(q, e) (packed upper 6x6), gr(q, k,
+// beta) and lr(q, k): the derivative vectors g_q,beta and L_q in the span's
+// reduced basis.  On return R holds the scaled tridiagonal (d, e, e^2), A
+// the reflectors, *tn the scale; returns the number of eigenvalues below
+// -neg_rel ||T|| (-1 on a non-finite matrix).
+template <int D, class Tab>
+BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* tn_out, double neg_rel) {
+  constexpr int n = 3 * D;
+  constexpr int NP = n * (n + 1) / 2;
+#pragma unroll 1
+  for (int k = 0; k < NP; ++k) A[k] = 0.0;
+  const int nm = tab.nm(), nb = tab.nb();
+
+  // 1. reduced Hessian, lower triangle, index 3k + c
   for (int q = 0; q < nm; ++q) {
     double gr[D][2];
 #pragma unroll
-    for (int k = 0; k < D; ++k) gr[k][0] = gr[k][1] = 0.0;
-#pragma unroll
-    for (int l = 0; l < 9; ++l) {
-      const double g0 = tab.g(q, l, 0), g1 = tab.g(q, l, 1);
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const double qk = R[9 * k + l];
-        gr[k][0] += qk * g0;
-        gr[k][1] += qk * g1;
-      }
+    for (int k = 0; k < D; ++k) {
+      gr[k][0] = tab.gr(q, k, 0);
+      gr[k][1] = tab.gr(q, k, 1);
     }
     double A6[6][6];
     {
@@ -243,13 +305,7 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, const Vi
     const double WB = tab.wb(q);
     double Lr[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) Lr[k] = 0.0;
-#pragma unroll
-    for (int l = 0; l < 9; ++l) {
-      const double L = tab.L(q, l);
-#pragma unroll
-      for (int k = 0; k < D; ++k) Lr[k] += R[9 * k + l] * L;
-    }
+    for (int k = 0; k < D; ++k) Lr[k] = tab.lr(q, k);
 #pragma unroll
     for (int k = 0; k < D; ++k)
 #pragma unroll
@@ -259,11 +315,7 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, const Vi
         for (int c = 0; c < 3; ++c) A[lp(3 * k + c, 3 * k2 + c)] += h;
       }
   }
-  // keep Q for the final mapping
-#pragma unroll
-  for (int k = 0; k < 9 * D; ++k) Qs[k] = R[k];
-
-  // 3. Householder tridiagonalisation: d -> R[0..n), e -> R[n..2n); the
+  // 2. Householder tridiagonalisation: d -> R[0..n), e -> R[n..2n); the
   //    reflector v_k stays in column k of A, p = tau A v in R[2n..3n).
   //    Operands come from shared memory: the FP64 pipe, not the loads, is
   //    the limit, and no per-thread arrays compete for registers.
@@ -319,7 +371,7 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, const Vi
   R[n - 1] = A[lp(n - 1, n - 1)];
   R[2 * n - 1] = 0.0;
 
-  // 4. scale to ||T|| <= 1; e^2 -> R[2n..3n)
+  // 3. scale to ||T|| <= 1; e^2 -> R[2n..3n)
   double tn = 0.0;
 #pragma unroll
   for (int i = 0; i < n; ++i) {
@@ -339,198 +391,10 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, const Vi
   return sturm<n>(R, -neg_rel);
 }
 
-// Phase 2a: eigenvalue k (k-th smallest, scaled) of a span whose phase 1 is
-// done: FP32 bisection on the copy F of (d, e^2) to about 22 bits, the
-// widened bracket checked by two FP64 Sturm counts, then FP64 bisection to a
-// width of 1e-10.  Returns the bracket midpoint.
-template <int D>
-BSC_PHASE double span_eigenvalue(const View& R, const float* F, int fs, int k, double neg_rel) {
-  constexpr int n = 3 * D;
-  float d32[n], e232[n];
-#pragma unroll
-  for (int i = 0; i < n; ++i) {
-    d32[i] = F[i * fs];
-    e232[i] = F[(n + i) * fs];
-  }
-  const double lo_all = -1.0 - 1e-12, hi_all = -neg_rel;
-  float a32 = -1.0f - 1e-6f, b32 = (float)hi_all;
-#pragma unroll 1
-  for (int it = 0; it < 22; ++it) {
-    const float mid = 0.5f * (a32 + b32);
-    if (sturm32<n>(d32, e232, mid) > k) b32 = mid;
-    else a32 = mid;
-  }
-  double a = fmax((double)a32 - 4e-6, lo_all), b = fmin((double)b32 + 4e-6, hi_all);
-  if (!(sturm<n>(R, a) <= k && sturm<n>(R, b) > k)) {
-    a = lo_all;
-    b = hi_all;
-  }
-#pragma unroll 1
-  for (int it = 0; it < 40 && b - a > 1e-10; ++it) {
-    const double mid = 0.5 * (a + b);
-    if (sturm<n>(R, mid) > k) b = mid;
-    else a = mid;
-  }
-  return 0.5 * (a + b);
-}
-
-// Phase 2b: eigenvectors k0 .. k0+m-1 of a cluster (consecutive eigenvalues
-// closer than the cluster gap), from the shifts in Lam: inverse iteration
-// (two solves) with re-orthogonalisation against the cluster's earlier
-// vectors in Ys, Rayleigh quotient (written back to Lam, unscaled by tn),
-// back-transformation and w = (Q (x) I3) x written to Ws[27 k + .].
-template <int D>
-BSC_PHASE void span_cluster_vectors(const View& A, const View& R, const View& Qs, const View& Ys, const View& Lam,
-                                 const View& Ws, double tn, int k0, int m) {
-  constexpr int n = 3 * D;
-#pragma unroll 1
-  for (int k = k0; k < k0 + m; ++k) {
-    const double sig = Lam[k];
-    double u0r[n], u1[n], u2[n], mu[n];
-    unsigned sw = 0u;
-    {
-      double c0 = R[0] - sig, c1 = R[n], c2 = 0.0;
-#pragma unroll
-      for (int i = 0; i < n - 1; ++i) {
-        const double ei = R[n + i];
-        const double a1 = R[i + 1] - sig, e1 = (i + 1 < n - 1) ? R[n + i + 1] : 0.0;
-        if (fabs(ei) > fabs(c0)) {
-          sw |= 1u << i;
-          const double r = 1.0 / ei, mm = c0 * r;
-          mu[i] = mm; u0r[i] = r; u1[i] = a1; u2[i] = e1;
-          c0 = c1 - mm * a1; c1 = c2 - mm * e1; c2 = 0.0;
-        } else {
-          if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
-          const double r = 1.0 / c0, mm = ei * r;
-          mu[i] = mm; u0r[i] = r; u1[i] = c1; u2[i] = c2;
-          c0 = a1 - mm * c1; c1 = e1 - mm * c2; c2 = 0.0;
-        }
-      }
-      if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
-      u0r[n - 1] = 1.0 / c0;
-      u1[n - 1] = u2[n - 1] = 0.0;
-    }
-    double y[n];
-#pragma unroll
-    for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.125 * (double)((7 * i + 3 * k) % 5);
-#pragma unroll 1
-    for (int it = 0; it < 3; ++it) {
-#pragma unroll 1
-      for (int j = k0; j < k; ++j) {
-        double dt = 0.0;
-#pragma unroll
-        for (int i = 0; i < n; ++i) dt += Ys[j * n + i] * y[i];
-#pragma unroll
-        for (int i = 0; i < n; ++i) y[i] -= dt * Ys[j * n + i];
-      }
-      if (it < 2) {
-#pragma unroll
-        for (int i = 0; i < n - 1; ++i) {
-          if (sw & (1u << i)) {
-            const double t = y[i];
-            y[i] = y[i + 1];
-            y[i + 1] = t - mu[i] * y[i + 1];
-          } else {
-            y[i + 1] -= mu[i] * y[i];
-          }
-        }
-#pragma unroll
-        for (int i = n - 1; i >= 0; --i) {
-          double sacc = y[i];
-          if (i + 1 < n) sacc -= u1[i] * y[i + 1];
-          if (i + 2 < n) sacc -= u2[i] * y[i + 2];
-          y[i] = sacc * u0r[i];
-        }
-      }
-      double nn = 0.0;
-#pragma unroll
-      for (int i = 0; i < n; ++i) nn += y[i] * y[i];
-      const double inv = 1.0 / sqrt(nn);
-#pragma unroll
-      for (int i = 0; i < n; ++i) y[i] *= inv;
-    }
-    double rq = 0.0;
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-      double ty = R[i] * y[i];
-      if (i > 0) ty += R[n + i - 1] * y[i - 1];
-      if (i + 1 < n) ty += R[n + i] * y[i + 1];
-      rq += y[i] * ty;
-    }
-    if (m > 1) {
-#pragma unroll
-      for (int i = 0; i < n; ++i) Ys[k * n + i] = y[i];
-    }
-    Lam[k] = fmin(rq, 0.0) * tn;
-    back_transform<n>(A, y);
-#pragma unroll
-    for (int l = 0; l < 9; ++l)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        double acc = 0.0;
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) acc += Qs[9 * kk + l] * y[3 * kk + c];
-        Ws[27 * k + 3 * l + c] = acc;
-      }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Phase-2 items with the tridiagonal in registers (no shared memory needed):
 // the span's scaled (d, e, e^2) are loaded once per item.
 // ---------------------------------------------------------------------------
-
-template <int n>
-BSC_HD int sturm_reg(const double (&d)[n], const double (&e2)[n], double x) {
-  double pm = 1.0, p = d[0] - x;
-  int cnt = sign_of(p);
-#pragma unroll
-  for (int i = 1; i < n; ++i) {
-    double pn = (d[i] - x) * p - e2[i - 1] * pm;
-    if (expo_of(pn) == 0) pn = sign_of(p) ? 1e-300 : -1e-300;
-    cnt += sign_of(pn) ^ sign_of(p);
-    const int ea = expo_of(pn), eb = expo_of(p), mx = ea > eb ? ea : eb;
-    if (mx > 1023 + 500 || mx < 1023 - 500) {
-      const double sc = mx > 1023 ? 0x1p-500 : 0x1p500;
-      pn *= sc;
-      p *= sc;
-    }
-    pm = p;
-    p = pn;
-  }
-  return cnt;
-}
-
-// det(T - x I) from the same three-term recurrence as the Sturm count, with
-// the count; *exact is false when a rescaling step made the value's scale
-// differ from the determinant's (callers then bisect instead).
-template <int n>
-BSC_HD double char_poly(const double (&d)[n], const double (&e2)[n], double x, int* cnt_out, bool* exact) {
-  double pm = 1.0, p = d[0] - x;
-  int cnt = sign_of(p);
-  bool ok = true;
-#pragma unroll
-  for (int i = 1; i < n; ++i) {
-    double pn = (d[i] - x) * p - e2[i - 1] * pm;
-    if (expo_of(pn) == 0) {
-      pn = sign_of(p) ? 1e-300 : -1e-300;
-      ok = false;
-    }
-    cnt += sign_of(pn) ^ sign_of(p);
-    const int ea = expo_of(pn), eb = expo_of(p), mx = ea > eb ? ea : eb;
-    if (mx > 1023 + 500 || mx < 1023 - 500) {
-      const double sc = mx > 1023 ? 0x1p-500 : 0x1p500;
-      pn *= sc;
-      p *= sc;
-      ok = false;
-    }
-    pm = p;
-    p = pn;
-  }
-  *cnt_out = cnt;
-  *exact = ok;
-  return p;
-}
 
 // Eigenvalue k (scaled) of the tridiagonal stored in R (d at R[0..n), e^2 at
 // R[2n..3n)), loaded into registers.  After the FP32 bracket and its FP64
@@ -612,10 +476,14 @@ BSC_PHASE double eigenvalue_reg(const View& R, int k, double neg_rel) {
   return 0.5 * (a + b);
 }
 
-// Eigenvectors k0 .. k0+m-1 of a cluster, as span_cluster_vectors, with the
-// tridiagonal (d, e) loaded into registers from R and the reflectors A, basis
-// Q, eigenvalues Lam and output vectors Ws in global memory; Ys is the item's
-// own scratch.  The LU factors of T - sigma I (multipliers and the three
+// Eigenvectors k0 .. k0+m-1 of a cluster (consecutive eigenvalues closer
+// than the cluster gap), from the shifts in Lam: inverse iteration (two
+// solves) with re-orthogonalisation against the cluster's earlier vectors in
+// Ys, Rayleigh quotient (written back to Lam, unscaled by tn),
+// back-transformation and w = (Q (x) I3) x written to Ws[27 k + .].  The
+// tridiagonal (d, e) is loaded into registers from R; the reflectors A,
+// basis Q, eigenvalues Lam and output vectors Ws are in global memory; Ys is
+// the item's own scratch.  The LU factors of T - sigma I (multipliers and the three
 // diagonals of U, 4n doubles) live in LU, the thread's slot of an interleaved
 // shared-memory array, which keeps them out of local memory.
 template <int D, class WView>
@@ -635,22 +503,22 @@ BSC_PHASE void cluster_vectors_reg(const View& R, const View& A, const View& Qs,
     const double sig = Lam[k];
     unsigned sw = 0u;
     {
+      // Gaussian elimination of T - sig I with partial pivoting between
+      // the current row (c0, c1, c2) and the next (e_i, a1, e1); the rows
+      // are chosen by selects, so both alternatives cost no FP64 work.
       double c0 = d[0] - sig, c1 = e[0], c2 = 0.0;
 #pragma unroll
       for (int i = 0; i < n - 1; ++i) {
         const double ei = e[i];
         const double a1 = d[i + 1] - sig, e1 = (i + 1 < n - 1) ? e[i + 1] : 0.0;
-        if (fabs(ei) > fabs(c0)) {
-          sw |= 1u << i;
-          const double r = 1.0 / ei, mm = c0 * r;
-          mu[i] = mm; u0r[i] = r; u1[i] = a1; u2[i] = e1;
-          c0 = c1 - mm * a1; c1 = c2 - mm * e1; c2 = 0.0;
-        } else {
-          if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
-          const double r = 1.0 / c0, mm = ei * r;
-          mu[i] = mm; u0r[i] = r; u1[i] = c1; u2[i] = c2;
-          c0 = a1 - mm * c1; c1 = e1 - mm * c2; c2 = 0.0;
-        }
+        const bool swp = fabs(ei) > fabs(c0);
+        const double g0 = fabs(c0) < 2.3e-16 ? (c0 < 0.0 ? -2.3e-16 : 2.3e-16) : c0;
+        const double t0 = swp ? ei : g0, t1 = swp ? a1 : c1, t2 = swp ? e1 : c2;  // pivot row
+        const double b0 = swp ? c0 : ei, b1 = swp ? c1 : a1, b2 = swp ? c2 : e1;  // eliminated row
+        const double r = 1.0 / t0, mm = b0 * r;
+        sw |= (unsigned)swp << i;
+        mu[i] = mm; u0r[i] = r; u1[i] = t1; u2[i] = t2;
+        c0 = b1 - mm * t1; c1 = b2 - mm * t2; c2 = 0.0;
       }
       if (fabs(c0) < 2.3e-16) c0 = c0 < 0.0 ? -2.3e-16 : 2.3e-16;
       u0r[n - 1] = 1.0 / c0;
@@ -672,13 +540,10 @@ BSC_PHASE void cluster_vectors_reg(const View& R, const View& A, const View& Qs,
       if (it < 2) {
 #pragma unroll
         for (int i = 0; i < n - 1; ++i) {
-          if (sw & (1u << i)) {
-            const double t = y[i];
-            y[i] = y[i + 1];
-            y[i + 1] = t - mu[i] * y[i + 1];
-          } else {
-            y[i + 1] -= mu[i] * y[i];
-          }
+          const bool swp = (sw >> i) & 1u;
+          const double ya = swp ? y[i + 1] : y[i], yb = swp ? y[i] : y[i + 1];
+          y[i] = ya;
+          y[i + 1] = yb - mu[i] * ya;
         }
 #pragma unroll
         for (int i = n - 1; i >= 0; --i) {

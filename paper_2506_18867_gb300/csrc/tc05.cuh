@@ -1,7 +1,8 @@
 // Blackwell (sm_103a) tensor-core primitives as inline PTX: tensor memory
 // (TMEM) allocation, tcgen05.mma with shared-memory matrix descriptors,
-// completion through an mbarrier, tcgen05.ld of the accumulator, and the
-// 16-byte asynchronous global -> shared copies that stage the operands.
+// completion through an mbarrier, tcgen05.ld of the accumulator, the
+// 16-byte asynchronous global -> shared copies that stage the operands, and
+// TMA (cp.async.bulk.tensor) box loads.
 //
 // Operand layout used by every caller: K-major, no swizzle.  A tile of R rows
 // (M or N dimension) by K columns of 16-bit elements is stored as 8 x 8
@@ -112,6 +113,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long 
     if (i > 64) __nanosleep(32);
   }
   return false;
+}
+
+// Arrives once on the mbarrier and adds `bytes` to the transaction count the
+// current phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+
+// ---- TMA ----------------------------------------------------------------------
+// One box of a rank-1 tiled tensor map, starting at element x, into shared
+// memory (128-byte aligned destination); completion is counted in bytes on
+// the mbarrier.  x * element size must be a multiple of 16 bytes; parts of the
+// box past the tensor's extent read as zero.
+__device__ __forceinline__ void tma_load_1d(void* smem_dst, const void* tmap, int x, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(tmap), "r"(x), "r"(smem_u32(mbar))
+      : "memory");
 }
 
 // ---- TMEM -> registers ------------------------------------------------------

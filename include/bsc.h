@@ -228,7 +228,8 @@ bsc_status bsc_patch_energies(bsc_ctx* ctx, const void* C_dev, const void* Chat_
  * evaluation of each class present for each candidate width {0, 8, 16, 32}
  * (CUDA events, best of 3) and keeps the fastest, times the SPD projection
  * of the border spans (at or next to a patch border) by its two paths and
- * keeps the faster, then assembles K at C,
+ * keeps the faster, likewise the two occupancy variants of the interior
+ * projection's eigenpair phase, then assembles K at C,
  * runs one PCG solve per patch to measure its iteration count, and splits
  * the PCG's co-resident blocks in proportion to control points x
  * iterations (bsc_plan_blocks).  C is not modified.  The choices change
@@ -242,6 +243,9 @@ typedef struct bsc_tuning {
   int border_path;         /* SPD projection of the border spans: 0 one warp per
                               span, 1 one thread per span (chosen by time) */
   double border_ms[2];     /* measured ms of the border projection per path */
+  int p2_variant;          /* phase 2 of the interior projection: 0 two, 1 three
+                              resident blocks per SM (fewer registers; chosen by time) */
+  double p2_ms[2];         /* measured ms of that phase per variant */
 } bsc_tuning;
 bsc_status bsc_autotune(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, bsc_tuning* out);
 
@@ -256,6 +260,10 @@ bsc_status bsc_set_tiles(bsc_ctx* ctx, const int* tile_tu);
 /* Set the border projection path by hand (0 one warp per span, 1 one thread
  * per span); both compute the same projection up to rounding. */
 bsc_status bsc_set_border_path(bsc_ctx* ctx, int path);
+
+/* Set the occupancy variant of the interior projection's eigenpair phase by
+ * hand (0 or 1, see bsc_tuning); both compute bitwise the same result. */
+bsc_status bsc_set_p2_variant(bsc_ctx* ctx, int variant);
 
 /* Current split of the PCG's blocks (host array of count ints). */
 bsc_status bsc_pcg_split(const bsc_ctx* ctx, int* blocks_per_patch);

@@ -663,6 +663,15 @@ bsc_status bsc_set_tiles(bsc_ctx* c, const int* tu) {
   return BSC_OK;
 }
 
+bsc_status bsc_set_p2_variant(bsc_ctx* c, int v) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (v != 0 && v != 1) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_p2_variant: variant must be 0 or 1");
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_p2_variant");
+  c->p2_variant = v;
+  drop_graph(c);
+  return BSC_OK;
+}
+
 bsc_status bsc_set_border_path(bsc_ctx* c, int path) {
   if (!c) return BSC_ERR_INVALID_ARG;
   if (path != 0 && path != 1) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_border_path: path must be 0 or 1");
@@ -747,6 +756,26 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
   }
   if (st == BSC_OK) c->border_path = t.border_ms[1] < t.border_ms[0] ? 1 : 0;
   t.border_path = c->border_path;
+  // interior phase-2 occupancy variant: both timed on the same phase-1 output
+  if (st == BSC_OK) {
+    cudaError_t e = launch_span_eval(c, C, 1, 1);
+    if (e == cudaSuccess) e = launch_project_interior(c, 0);
+    for (int v = 0; v < 2; ++v) t.p2_ms[v] = 1e30;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+      for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        float ms = 0.0f;
+        c->p2_variant = v;
+        e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) e = launch_project_interior(c, 1);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && ms < t.p2_ms[v]) t.p2_ms[v] = ms;  // the first round warms up
+      }
+    if (e != cudaSuccess) st = cuda_fail(c, e, "bsc_autotune: timing the interior projection");
+    c->p2_variant = t.p2_ms[1] < t.p2_ms[0] ? 1 : 0;
+  }
+  t.p2_variant = c->p2_variant;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != BSC_OK) return st;

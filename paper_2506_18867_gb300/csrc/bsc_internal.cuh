@@ -116,6 +116,8 @@ struct bsc_ctx {
   double* helmert;    // device [72]: the border spans' basis (Helmert contrasts)
   // two span classes: 0 interior (reduced size 15), 1 at or next to the border (24)
   int proj_grid[2][2];      // resident grid per class and phase
+  int p2_grid[2][2];        // resident grid of phase 2 per class and occupancy variant
+  int p2_variant;           // interior phase-2 variant (autotuned)
   double* proj_scratch[2];  // per-thread slots of the phase-2 kernels (cluster eigenvectors)
   double* proj_span[2];     // per-span scratch of each class
   int* proj_kneg[2];        // negative-eigenvalue count per span (class order)
@@ -203,6 +205,7 @@ cudaError_t setup_projection(bsc_ctx* c);
 cudaError_t launch_project(bsc_ctx* c);
 // the border class alone by the given path, on the context's stream (autotuner)
 cudaError_t launch_project_border(bsc_ctx* c, int path);
+cudaError_t launch_project_interior(bsc_ctx* c, int phase);
 cudaError_t launch_assemble(bsc_ctx* c, void* K);
 cudaError_t launch_gradient(bsc_ctx* c, const void* C, const void* Chat, void* g);
 // per-patch incremental potential into dE[p] (with a gate: pending patches only)

@@ -219,14 +219,19 @@ __device__ __forceinline__ void block_prefix(int v, int* prefix, int* wsum) {
   __syncthreads();
 }
 
+// Phase-2 occupancy variants: MINB resident blocks per SM (2: no register
+// limit below 255; 3: 168 registers, a little spilling in the eigenvector
+// item).  The autotuner keeps the faster for the interior class.
+constexpr int P2_MINB[2] = {2, 3};
+
 // Phase 2 over batches of P2_BLOCK consecutive interior spans: (a) every
 // negative eigenvalue is an independent item, (b) every cluster of close
 // eigenvalues is an item that computes its eigenvectors, (c) each owner
 // applies H -= sum lam w w^T to its span.  Items are spread over the whole
 // block, so no warp carries masked lanes through FP64 work (masked lanes
 // cost the FP64 pipe as much as active ones).
-template <typename T, int D>
-__global__ void __launch_bounds__(P2_BLOCK)
+template <typename T, int D, int MINB>
+__global__ void __launch_bounds__(P2_BLOCK, MINB)
     k_proj_p2(ProjArgs<T> P, const int* __restrict__ list, int count, const int* __restrict__ kneg_in,
               double* __restrict__ sspan, double* __restrict__ slots, unsigned int* __restrict__ work) {
   constexpr int n = 3 * D;
@@ -380,9 +385,13 @@ cudaError_t run_class(bsc_ctx* c, int k, const int* list, int count, cudaStream_
   if (phase != 0) {
     BSC_COUNT(c, 1);
     if ((e = cudaMemsetAsync(c->proj_work + k, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
-    k_proj_p2<T, D><<<c->proj_grid[k][1], P2_BLOCK, p2_smem<D>(), st>>>(P, list, count, c->proj_kneg[k],
-                                                                        c->proj_span[k], c->proj_scratch[k],
-                                                                        c->proj_work + k);
+    const int v = k == 0 ? c->p2_variant : 0;
+    if (v == 0)
+      k_proj_p2<T, D, P2_MINB[0]><<<c->p2_grid[k][0], P2_BLOCK, p2_smem<D>(), st>>>(
+          P, list, count, c->proj_kneg[k], c->proj_span[k], c->proj_scratch[k], c->proj_work + k);
+    else
+      k_proj_p2<T, D, P2_MINB[1]><<<c->p2_grid[k][1], P2_BLOCK, p2_smem<D>(), st>>>(
+          P, list, count, c->proj_kneg[k], c->proj_span[k], c->proj_scratch[k], c->proj_work + k);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -416,34 +425,46 @@ cudaError_t run_all(bsc_ctx* c) {
   return cudaStreamWaitEvent(c->stream, c->join_ev[0], 0);
 }
 
+template <typename T, int D, int MINB>
+cudaError_t p2_grid_of(bsc_ctx* c, int count, int* grid) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_proj_p2<T, D, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)p2_smem<D>())) != cudaSuccess)
+    return e;
+  int per = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_proj_p2<T, D, MINB>, P2_BLOCK, p2_smem<D>())) !=
+      cudaSuccess)
+    return e;
+  per = per < 1 ? 1 : per;
+  int g = per * c->num_sms;
+  const int need = (count + P2_BLOCK - 1) / P2_BLOCK;
+  if (g > need) g = need;
+  *grid = g < 1 ? 1 : g;
+  return cudaSuccess;
+}
+
 template <typename T, int D>
 cudaError_t setup_class(bsc_ctx* c, int k, int count) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_proj_p1<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)p1_smem<D>())) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_proj_p2<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)p2_smem<D>())) != cudaSuccess)
-    return e;
-  int per1 = 0, per2 = 0;
+  int per1 = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_proj_p1<T, D>, P1Block<D>::value,
                                                          p1_smem<D>())) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_proj_p2<T, D>, P2_BLOCK, p2_smem<D>())) !=
-      cudaSuccess)
-    return e;
   per1 = per1 < 1 ? 1 : per1;
-  per2 = per2 < 1 ? 1 : per2;
-  int g1 = per1 * c->num_sms, g2 = per2 * c->num_sms;
-  const int need1 = (count + P1Block<D>::value - 1) / P1Block<D>::value, need2 = (count + P2_BLOCK - 1) / P2_BLOCK;
+  int g1 = per1 * c->num_sms;
+  const int need1 = (count + P1Block<D>::value - 1) / P1Block<D>::value;
   if (g1 > need1) g1 = need1;
-  if (g2 > need2) g2 = need2;
   c->proj_grid[k][0] = g1 < 1 ? 1 : g1;
-  c->proj_grid[k][1] = g2 < 1 ? 1 : g2;
+  if ((e = p2_grid_of<T, D, P2_MINB[0]>(c, count, &c->p2_grid[k][0])) != cudaSuccess) return e;
+  if ((e = p2_grid_of<T, D, P2_MINB[1]>(c, count, &c->p2_grid[k][1])) != cudaSuccess) return e;
+  const int g2 = c->p2_grid[k][0] > c->p2_grid[k][1] ? c->p2_grid[k][0] : c->p2_grid[k][1];
   const size_t cnt = count > 0 ? (size_t)count : 1;
   if ((e = cudaMalloc(&c->proj_span[k], sizeof(double) * SpanScratch<D>::SIZE * cnt)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->proj_kneg[k], sizeof(int) * cnt)) != cudaSuccess) return e;
-  const size_t slots = (size_t)c->proj_grid[k][1] * P2_BLOCK;
+  const size_t slots = (size_t)g2 * P2_BLOCK;
   constexpr int n = 3 * D;
   return cudaMalloc(&c->proj_scratch[k], sizeof(double) * n * n * slots);
 }
@@ -493,6 +514,15 @@ cudaError_t setup_projection(bsc_ctx* c) {
 cudaError_t launch_project(bsc_ctx* c) {
   if (c->precision == BSC_FP64) return run_all<double>(c);
   return run_all<float>(c);
+}
+
+// The interior class's phase 1 or phase 2 alone (phase 0 / 1), on the
+// context's stream: the autotuner times phase 2 per variant.
+cudaError_t launch_project_interior(bsc_ctx* c, int phase) {
+  const int* list0 = c->bucket_list + c->bucket_off[0];
+  const int n0 = c->bucket_off[1] - c->bucket_off[0];
+  if (c->precision == BSC_FP64) return run_class<double, 5>(c, 0, list0, n0, c->stream, phase);
+  return run_class<float, 5>(c, 0, list0, n0, c->stream, phase);
 }
 
 cudaError_t launch_project_border(bsc_ctx* c, int path) {

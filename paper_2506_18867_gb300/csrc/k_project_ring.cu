@@ -60,9 +60,9 @@ __device__ __forceinline__ int sgn_f(float x) { return (unsigned)__float_as_int(
 // count (eigenvalues < x); *exact is false when a replacement of a zero
 // minor or a rescaling made the value's scale differ from the
 // determinant's.  The recurrence first runs without rescaling, the
-// exponents tracked with integer operations (no predicated FP64
-// instructions); a pair of minors outside [2^-500, 2^500] sends the call to
-// the rescaling pass, which gives the identical result.
+// exponents tracked with integer operations (three FP64 operations per
+// step); a pair of minors outside [2^-500, 2^500] sends the call to the
+// rescaling pass, which gives the identical result.
 __device__ __noinline__ double charpoly64_scaled(const double* d, const double* e2, double x, int* cnt_out,
                                                  bool* exact) {
   double pm = 1.0, p = d[0] - x;
@@ -208,7 +208,7 @@ __device__ void tri_solve(const double* d, const double* e, double sig, double (
 #pragma unroll
   for (int i = 0; i < RN - 1; ++i) {
     const double ei = e[i], a1 = d[i + 1] - sig, e1 = (i + 1 < RN - 1) ? e[i + 1] : 0.0;
-    // pivot row and eliminated row by selects (no predicated FP64 work)
+    // pivot row and eliminated row chosen by selects: one reciprocal per step
     const bool swp = fabs(ei) > fabs(c0);
     const double g0 = fabs(c0) < 2.3e-16 ? (c0 < 0.0 ? -2.3e-16 : 2.3e-16) : c0;
     const double t0 = swp ? ei : g0, t1 = swp ? a1 : c1, t2 = swp ? e1 : c2;

@@ -69,14 +69,15 @@ BSC_HD int expo_of(double x) {
 // whenever the larger of the two leaves [2^-500, 2^500].  *exact is false
 // when a replacement or a rescaling made the value's scale differ from the
 // determinant's.
-template <int n, class DA, class EA>
-BSC_PHASE double char_poly_scaled(const DA& d, const EA& e2, double x, int* cnt_out, bool* exact) {
+template <int n>
+BSC_PHASE double char_poly_scaled(const double* d, int ds, const double* e2, int es, double x, int* cnt_out,
+                                  bool* exact) {
   double pm = 1.0, p = d[0] - x;
   int cnt = sign_of(p);
   bool ok = true;
 #pragma unroll 1
   for (int i = 1; i < n; ++i) {
-    double pn = (d[i] - x) * p - e2[i - 1] * pm;
+    double pn = (d[(long)i * ds] - x) * p - e2[(long)(i - 1) * es] * pm;
     if (expo_of(pn) == 0) {
       pn = sign_of(p) ? 1e-300 : -1e-300;
       ok = false;
@@ -101,9 +102,8 @@ BSC_PHASE double char_poly_scaled(const DA& d, const EA& e2, double x, int* cnt_
 // here (n <= 24) stay far inside that range, so this pass runs the
 // recurrence without rescaling and tracks the exponents with integer
 // operations only; the rare pair that leaves the range sends the call to
-// char_poly_scaled, which then gives the identical result.  No FP64
-// instruction is predicated (a predicated FP64 instruction occupies the
-// FP64 pipe like an executed one).
+// char_poly_scaled, which then gives the identical result.  Each step is
+// three FP64 operations; the rescaling multiplications leave the loop.
 template <int n, class DA, class EA>
 BSC_HD double char_poly(const DA& d, const EA& e2, double x, int* cnt_out, bool* exact) {
   double pm = 1.0, p = d[0] - x;
@@ -122,7 +122,16 @@ BSC_HD double char_poly(const DA& d, const EA& e2, double x, int* cnt_out, bool*
     p = pn;
     eb = ea;
   }
-  if (!in_range) return char_poly_scaled<n>(d, e2, x, cnt_out, exact);
+  if (!in_range) {
+    // rare: copy the operands out (the fast pass keeps them in registers)
+    double buf[2 * n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      buf[i] = d[i];
+      buf[n + i] = e2[i];
+    }
+    return char_poly_scaled<n>(buf, 1, buf + n, 1, x, cnt_out, exact);
+  }
   *cnt_out = cnt;
   *exact = ok;
   return p;
@@ -505,7 +514,7 @@ BSC_PHASE void cluster_vectors_reg(const View& R, const View& A, const View& Qs,
     {
       // Gaussian elimination of T - sig I with partial pivoting between
       // the current row (c0, c1, c2) and the next (e_i, a1, e1); the rows
-      // are chosen by selects, so both alternatives cost no FP64 work.
+      // are chosen by selects: one reciprocal per step whichever is taken.
       double c0 = d[0] - sig, c1 = e[0], c2 = 0.0;
 #pragma unroll
       for (int i = 0; i < n - 1; ++i) {

@@ -227,6 +227,15 @@ def test_autotune_choices(pair):
             assert t["tile_tu"][k] == -1
     split = batch.pcg_split()
     assert sum(split) == t["pcg_grid"] and min(split) >= 1
+    assert t["p2_variant"] in (0, 1) and all(ms > 0 for ms in t["p2_ms"])
+    # both occupancy variants of the projection's eigenpair phase: bitwise the same
+    outs = []
+    for v in (0, 1):
+        batch.set_p2_variant(v)
+        E, g, H = batch.span_terms(C, project=True)
+        outs.append(H.cpu())
+    assert torch.equal(outs[0], outs[1])
+    batch.set_p2_variant(t["p2_variant"])
     batch.set_tiles((0, 0, 0, 0))
 
 

@@ -127,31 +127,57 @@ struct TView {
 };
 
 // H -= sum_r lam_r w_r w_r^T for one span in one pass over its 378 packed
-// entries, in the element type (w_r already in T in the scratch).  A span
-// has at most RMAX = n negative eigenvalues; the unrolled,
-// predicated loops keep lam_r and lam_r w_r[a] of the current row in
-// registers, so only w_r[c] is read per entry.
-template <typename T, int RMAX>
-__device__ __noinline__ void apply_corrections(T* H, int Nsp, int s, proj::View Lam, TView<T> Ws, int kneg) {
-  T lam[RMAX];
+// entries, in the element type (w_r already in T in the scratch), for
+// kneg <= RM negative eigenvalues.  The unrolled, predicated loops keep
+// lam_r and lam_r w_r[a] of the current row a in registers.  Each row goes in
+// chunks of CH entries whose H values are all loaded before any is updated,
+// so a thread keeps CH reads of H in flight (the update is bound by the
+// latency of these reads, not by arithmetic).
+template <typename T, int RM>
+__device__ __noinline__ void apply_corrections_rm(T* __restrict__ H, int Nsp, int s, proj::View Lam, TView<T> Ws,
+                                                  int kneg) {
+  constexpr int CH = 8;
+  const T* __restrict__ W = Ws.p;
+  const size_t ws = (size_t)Ws.s;
+  T lam[RM];
 #pragma unroll
-  for (int r = 0; r < RMAX; ++r) lam[r] = r < kneg ? (T)Lam[r] : T(0);
+  for (int r = 0; r < RM; ++r) lam[r] = r < kneg ? (T)Lam[r] : T(0);
   int e = 0;
 #pragma unroll 1
   for (int a = 0; a < 27; ++a) {
-    T la[RMAX];
+    T la[RM];
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) la[r] = r < kneg ? lam[r] * Ws[27 * r + a] : T(0);
+    for (int r = 0; r < RM; ++r) la[r] = r < kneg ? lam[r] * W[(27 * r + a) * ws] : T(0);
 #pragma unroll 1
-    for (int c = a; c < 27; ++c, ++e) {
-      T acc = T(0);
+    for (int c0 = a; c0 < 27; c0 += CH) {
+      const int m = 27 - c0 < CH ? 27 - c0 : CH;
+      // every read of the chunk is issued before any of its writes
+      T h[CH], w[RM][CH];
 #pragma unroll
-      for (int r = 0; r < RMAX; ++r)
-        if (r < kneg) acc += la[r] * Ws[27 * r + c];
-      T* h = H + (size_t)e * Nsp + s;
-      *h -= acc;
+      for (int u = 0; u < CH; ++u) {
+        h[u] = u < m ? H[(size_t)(e + u) * Nsp + s] : T(0);
+#pragma unroll
+        for (int r = 0; r < RM; ++r) w[r][u] = (u < m && r < kneg) ? W[(27 * r + c0 + u) * ws] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        T acc = T(0);
+#pragma unroll
+        for (int r = 0; r < RM; ++r) acc += la[r] * w[r][u];
+        if (u < m) H[(size_t)(e + u) * Nsp + s] = h[u] - acc;
+      }
+      e += m;
     }
   }
+}
+
+// Dispatch on the count: most spans have at most four negative eigenvalues,
+// and a smaller unrolled bound keeps the loads of a chunk in registers.
+template <typename T, int RMAX>
+__device__ __forceinline__ void apply_corrections(T* H, int Nsp, int s, proj::View Lam, TView<T> Ws, int kneg) {
+  if (kneg <= 4) apply_corrections_rm<T, 4>(H, Nsp, s, Lam, Ws, kneg);
+  else if (kneg <= 8) apply_corrections_rm<T, 8>(H, Nsp, s, Lam, Ws, kneg);
+  else apply_corrections_rm<T, RMAX>(H, Nsp, s, Lam, Ws, kneg);
 }
 
 // Phase 1: one thread per interior span (uniform work, no barriers).
@@ -253,6 +279,21 @@ __global__ void __launch_bounds__(P2_BLOCK, MINB)
     const int t = base + tid;
     const int kneg = t < count ? kneg_in[t] : 0;
     s_kneg[tid] = kneg;
+    {
+      // (c) reads and rewrites the 378 entry planes over this batch's spans
+      // (ascending span ids): start pulling them into L2 now, so that the
+      // update waits on L2 rather than on HBM
+      const int last = base + P2_BLOCK - 1 < count ? base + P2_BLOCK - 1 : count - 1;
+      const size_t s0 = (size_t)list[base], s1 = (size_t)list[last];
+      const bool dense = s1 >= s0 && s1 - s0 < 2 * P2_BLOCK;  // scattered batches (border spans) are skipped
+      for (int e = tid; dense && e < H27; e += P2_BLOCK) {
+        const char* b0 = reinterpret_cast<const char*>(P.H + (size_t)e * P.Nsp + s0);
+        const char* b1 = reinterpret_cast<const char*>(P.H + (size_t)e * P.Nsp + s1);
+        for (const char* q = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(b0) & ~uintptr_t(127));
+             q <= b1; q += 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+      }
+    }
     // (a) eigenvalues
     block_prefix<P2_BLOCK>(kneg, s_pre, s_wsum);
     for (int i = tid; i < s_pre[P2_BLOCK]; i += P2_BLOCK) {

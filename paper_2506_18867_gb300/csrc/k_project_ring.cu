@@ -121,6 +121,9 @@ __device__ int sturm64(const double* d, const double* e2, double x) {
   return cnt;
 }
 
+// FP32 count on the copy of the tridiagonal: with ||T|| <= 1 the minors stay
+// below (1 + sqrt 2)^24 < 2e9, so only a pair near underflow (next to the
+// exact zero eigenvalues of a rank-deficient span) is rescaled.
 __device__ int sturm32(const float* d, const float* e2, float x) {
   float pm = 1.0f, p = d[0] - x;
   int cnt = sgn_f(p);
@@ -129,11 +132,9 @@ __device__ int sturm32(const float* d, const float* e2, float x) {
     float pn = (d[i] - x) * p - e2[i - 1] * pm;
     if (pn == 0.0f) pn = sgn_f(p) ? 1e-30f : -1e-30f;
     cnt += sgn_f(pn) ^ sgn_f(p);
-    const float mx = fmaxf(fabsf(pn), fabsf(p));
-    if (mx > 1e30f || mx < 1e-30f) {
-      const float sc = mx > 1.0f ? 1e-30f : 1e30f;
-      pn *= sc;
-      p *= sc;
+    if (fmaxf(fabsf(pn), fabsf(p)) < 1e-30f) {  // a pair near underflow (a multiple root nearby)
+      pn *= 1e30f;
+      p *= 1e30f;
     }
     pm = p;
     p = pn;
@@ -141,8 +142,9 @@ __device__ int sturm32(const float* d, const float* e2, float x) {
   return cnt;
 }
 
-// Eigenvalue k (scaled) of the tridiagonal in shared memory: FP32 bisection
-// to about 22 bits, the widened bracket checked by two FP64 Sturm counts,
+// Eigenvalue k (scaled) of the tridiagonal in shared memory: FP32
+// quadrisection to about 22 bits (three independent counts per step), the
+// widened bracket checked by two FP64 Sturm counts,
 // then regula falsi (Illinois) on det(T - x I) while the bracket isolates
 // eigenvalue k, bisection otherwise; four steps that fail to halve the
 // bracket force a bisection step (a bracket end next to a multiple root
@@ -150,10 +152,21 @@ __device__ int sturm32(const float* d, const float* e2, float x) {
 __device__ __noinline__ double ring_eigenvalue(const double* dd, const double* ee2, const float* d32,
                                                const float* e232, int k) {
   float a32 = -1.0f - 1e-6f, b32 = (float)(-NEG_REL);
-  for (int it = 0; it < 22; ++it) {
-    const float mid = 0.5f * (a32 + b32);
-    if (sturm32(d32, e232, mid) > k) b32 = mid;
-    else a32 = mid;
+  for (int it = 0; it < 11; ++it) {
+    const float h = 0.25f * (b32 - a32);
+    const float m1 = a32 + h, m2 = a32 + 2.0f * h, m3 = a32 + 3.0f * h;
+    const bool c1 = sturm32(d32, e232, m1) > k, c2 = sturm32(d32, e232, m2) > k, c3 = sturm32(d32, e232, m3) > k;
+    if (c1) {
+      b32 = m1;
+    } else if (c2) {
+      a32 = m1;
+      b32 = m2;
+    } else if (c3) {
+      a32 = m2;
+      b32 = m3;
+    } else {
+      a32 = m3;
+    }
   }
   double a = fmax((double)a32 - 4e-6, -1.0 - 1e-12), b = fmin((double)b32 + 4e-6, -NEG_REL);
   int ca, cb;

@@ -21,18 +21,37 @@
 
 namespace {
 
+// Stand-alone SpMV: one thread per (output component c, control point):
+// it reads the 75 entries of row c of the point's 25 blocks (coalesced over
+// consecutive points) and the neighbours' x through the read-only path.
+// Three threads per point keep three times as many independent K reads in
+// flight as one thread per point would.
 template <typename T>
-__global__ void k_spmv(int N, const PatchDev* __restrict__ pd, const int* __restrict__ cp_patch,
-                       const T* __restrict__ K, const T* __restrict__ x, T* __restrict__ y) {
-  const int al = blockIdx.x * blockDim.x + threadIdx.x;
-  if (al >= N) return;
+__global__ void __launch_bounds__(256) k_spmv(int N, const PatchDev* __restrict__ pd, const int* __restrict__ cp_patch,
+                                              const T* __restrict__ K, const T* __restrict__ x, T* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * N) return;
+  const int c = t / N, al = t - c * N;
   const PatchDev* pt = pd + cp_patch[al];
-  const int cp0 = __ldg(&pt->cp0);
-  T acc[3];
-  spmv_row<T, true>(__ldg(&pt->nu), __ldg(&pt->nv), N, al - cp0, K + cp0, x + cp0, acc);
-  y[al] = acc[0];
-  y[N + al] = acc[1];
-  y[2 * N + al] = acc[2];
+  const int cp0 = __ldg(&pt->cp0), nu = __ldg(&pt->nu), nv = __ldg(&pt->nv);
+  const int a = al - cp0, i = a % nu, j = a / nu;
+  const T* __restrict__ Kp = K + cp0;
+  const T* __restrict__ xp = x + cp0;
+  T acc = T(0);
+#pragma unroll
+  for (int dv = -2; dv <= 2; ++dv) {
+    const int jb = j + dv;
+    if (jb < 0 || jb >= nv) continue;
+#pragma unroll
+    for (int du = -2; du <= 2; ++du) {
+      const int ib = i + du;
+      if (ib < 0 || ib >= nu) continue;
+      const int slot = (dv + 2) * 5 + (du + 2), be = jb * nu + ib;
+      const T* Kb = Kp + (size_t)(slot * 9 + 3 * c) * N + a;
+      acc += Kb[0] * __ldg(xp + be) + Kb[(size_t)N] * __ldg(xp + N + be) + Kb[(size_t)2 * N] * __ldg(xp + 2 * N + be);
+    }
+  }
+  y[(size_t)c * N + al] = acc;
 }
 
 // Inverse of each 3x3 diagonal block (adjugate / determinant, FP64).
@@ -367,7 +386,7 @@ cudaError_t launch_block_jacobi(bsc_ctx* c, const void* K, void* Dinv) {
 
 cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y) {
   BSC_COUNT(c, 1);
-  const int B = 256, G = (c->N + B - 1) / B;
+  const int B = 256, G = (3 * c->N + B - 1) / B;
   if (c->precision == BSC_FP64)
     k_spmv<double><<<G, B, 0, c->stream>>>(c->N, c->pd, c->cp_patch, (const double*)K, (const double*)x, (double*)y);
   else

@@ -158,7 +158,10 @@ BSC_HD int sturm(const View& R, double x) {
 // is 64x the FP64 one, so the bracket of each eigenvalue is narrowed here
 // first and only validated and refined in FP64.  The FP32 count is exact for
 // a tridiagonal within a few FP32 ulps of T, so its brackets are widened
-// before the FP64 check.
+// before the FP64 check.  With ||T|| <= 1 and n <= 24 the minors stay below
+// (1 + sqrt 2)^24 < 2e9, so only a pair near underflow (next to a multiple
+// root, e.g. the exact zero eigenvalues of a rank-deficient span) is
+// rescaled.
 BSC_HD int sign_of_f(float x) {
 #ifdef __CUDA_ARCH__
   return (unsigned)__float_as_int(x) >> 31;
@@ -176,16 +179,41 @@ BSC_HD int sturm32(const float (&d)[n], const float (&e2)[n], float x) {
     float pn = (d[i] - x) * p - e2[i - 1] * pm;
     if (pn == 0.0f) pn = sign_of_f(p) ? 1e-30f : -1e-30f;
     cnt += sign_of_f(pn) ^ sign_of_f(p);
-    const float mx = fmaxf(fabsf(pn), fabsf(p));
-    if (mx > 1e30f || mx < 1e-30f) {
-      const float sc = mx > 1.0f ? 1e-30f : 1e30f;
-      pn *= sc;
-      p *= sc;
+    if (fmaxf(fabsf(pn), fabsf(p)) < 1e-30f) {  // a pair near underflow (a multiple root nearby)
+      pn *= 1e30f;
+      p *= 1e30f;
     }
     pm = p;
     p = pn;
   }
   return cnt;
+}
+
+// FP32 bracket of eigenvalue k in [*a, *b] to 2^-22 of its width by
+// quadrisection: each step counts at the three quarter points, which are
+// independent (three dependent chains in flight instead of one).
+template <int n>
+BSC_HD void bracket32(const float (&d)[n], const float (&e2)[n], int k, float* a, float* b) {
+  float lo = *a, hi = *b;
+#pragma unroll 1
+  for (int it = 0; it < 11; ++it) {
+    const float h = 0.25f * (hi - lo);
+    const float m1 = lo + h, m2 = lo + 2.0f * h, m3 = lo + 3.0f * h;
+    const bool c1 = sturm32<n>(d, e2, m1) > k, c2 = sturm32<n>(d, e2, m2) > k, c3 = sturm32<n>(d, e2, m3) > k;
+    if (c1) {
+      hi = m1;
+    } else if (c2) {
+      lo = m1;
+      hi = m2;
+    } else if (c3) {
+      lo = m2;
+      hi = m3;
+    } else {
+      lo = m3;
+    }
+  }
+  *a = lo;
+  *b = hi;
 }
 
 // Householder vectors in A(i, k), i > k; tau_k in A(k, k).  x <- H_0 ... H_{n-3} x.
@@ -430,12 +458,7 @@ BSC_PHASE double eigenvalue_reg(const View& R, int k, double neg_rel) {
   }
   const double lo_all = -1.0 - 1e-12, hi_all = -neg_rel;
   float a32 = -1.0f - 1e-6f, b32 = (float)hi_all;
-#pragma unroll 1
-  for (int it = 0; it < 22; ++it) {
-    const float mid = 0.5f * (a32 + b32);
-    if (sturm32<n>(d32, e232, mid) > k) b32 = mid;
-    else a32 = mid;
-  }
+  bracket32<n>(d32, e232, k, &a32, &b32);
   double a = fmax((double)a32 - 4e-6, lo_all), b = fmin((double)b32 + 4e-6, hi_all);
   int ca, cb;
   bool xa, xb;
@@ -536,8 +559,13 @@ BSC_PHASE void cluster_vectors_reg(const View& R, const View& A, const View& Qs,
     double y[n];
 #pragma unroll
     for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.125 * (double)((7 * i + 3 * k) % 5);
+    // a vector of its own (m == 1) needs no re-orthogonalisation: two
+    // solves, one normalisation (the solves grow |y| by at most 1/2.3e-16
+    // each, far inside the FP64 range); a cluster re-orthogonalises and
+    // normalises after each solve and once more after the last
+    const int passes = m > 1 ? 3 : 2;
 #pragma unroll 1
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < passes; ++it) {
 #pragma unroll 1
       for (int j = k0; j < k; ++j) {
         double dt = 0.0;
@@ -562,6 +590,7 @@ BSC_PHASE void cluster_vectors_reg(const View& R, const View& A, const View& Qs,
           y[i] = sacc * u0r[i];
         }
       }
+      if (m == 1 && it == 0) continue;
       double nn = 0.0;
 #pragma unroll
       for (int i = 0; i < n; ++i) nn += y[i] * y[i];

@@ -227,8 +227,8 @@ bsc_status bsc_patch_energies(bsc_ctx* ctx, const void* C_dev, const void* Chat_
  * < 128, >= 128); width 0 means runs.  bsc_autotune times the Hessian
  * evaluation of each class present for each candidate width {0, 8, 16, 32}
  * (CUDA events, best of 3) and keeps the fastest, times the SPD projection
- * of the border spans (at or next to a patch border) by its two paths and
- * keeps the faster, likewise the two occupancy variants of the interior
+ * (interior and border spans together) with each of the three paths of
+ * the border spans (at or next to a patch border) and keeps the fastest, likewise the two occupancy variants of the interior
  * projection's eigenpair phase, then assembles K at C,
  * runs one PCG solve per patch to measure its iteration count, and splits
  * the PCG's co-resident blocks in proportion to control points x
@@ -241,8 +241,10 @@ typedef struct bsc_tuning {
   double tile_ms[4][4];    /* measured ms per class x candidate {0, 8, 16, 32} */
   int pcg_grid;            /* co-resident blocks of the persistent PCG */
   int border_path;         /* SPD projection of the border spans: 0 one warp per
-                              span, 1 one thread per span (chosen by time) */
-  double border_ms[2];     /* measured ms of the border projection per path */
+                              span, 1 one thread per span, 2 one warp per span
+                              to the tridiagonal form, then one thread per
+                              eigenpair (chosen by time) */
+  double border_ms[3];     /* measured ms of the whole projection per border path */
   int p2_variant;          /* phase 2 of the interior projection: 0 two, 1 three
                               resident blocks per SM (fewer registers; chosen by time) */
   double p2_ms[2];         /* measured ms of that phase per variant */
@@ -257,8 +259,8 @@ bsc_status bsc_set_material(bsc_ctx* ctx, int patch, const bsc_material* m);
 /* Set the tile widths by hand (4 entries, each 0, 8, 16 or 32). */
 bsc_status bsc_set_tiles(bsc_ctx* ctx, const int* tile_tu);
 
-/* Set the border projection path by hand (0 one warp per span, 1 one thread
- * per span); both compute the same projection up to rounding. */
+/* Set the border projection path by hand (0, 1 or 2, see bsc_tuning); all
+ * compute the same projection up to rounding. */
 bsc_status bsc_set_border_path(bsc_ctx* ctx, int path);
 
 /* Set the occupancy variant of the interior projection's eigenpair phase by

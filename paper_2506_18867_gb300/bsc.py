@@ -72,7 +72,7 @@ class NewtonReport(ct.Structure):
 
 class Tuning(ct.Structure):
     _fields_ = [("tile_tu", ct.c_int * 4), ("tile_ms", (ct.c_double * 4) * 4), ("pcg_grid", ct.c_int),
-                ("border_path", ct.c_int), ("border_ms", ct.c_double * 2), ("p2_variant", ct.c_int),
+                ("border_path", ct.c_int), ("border_ms", ct.c_double * 3), ("p2_variant", ct.c_int),
                 ("p2_ms", ct.c_double * 2)]
 
     def as_dict(self):

@@ -674,7 +674,7 @@ bsc_status bsc_set_p2_variant(bsc_ctx* c, int v) {
 
 bsc_status bsc_set_border_path(bsc_ctx* c, int path) {
   if (!c) return BSC_ERR_INVALID_ARG;
-  if (path != 0 && path != 1) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_border_path: path must be 0 or 1");
+  if (path < 0 || path > 2) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_border_path: path must be 0, 1 or 2");
   CK(cudaStreamSynchronize(c->gstream), "bsc_set_border_path");
   c->border_path = path;
   drop_graph(c);
@@ -738,23 +738,31 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
     }
     if (t.tile_tu[cls] >= 0) c->tile_tu[cls] = t.tile_tu[cls];
   }
-  // border projection path: time both on freshly evaluated span Hessians
-  for (int path = 0; path < 2 && st == BSC_OK; ++path) {
+  // border projection path: time the whole projection (the border class
+  // runs beside the interior phase 2 and competes with it for the FP64
+  // pipes) with each path, on freshly evaluated span Hessians
+  for (int path = 0; path < 3 && st == BSC_OK; ++path) {
     float best_rep = 1e30f, ms = 0.0f;
     cudaError_t e = cudaSuccess;
+    c->border_path = path;
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
       e = launch_span_eval(c, C, 1, 1);
       if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-      if (e == cudaSuccess) e = launch_project_border(c, path);
+      if (e == cudaSuccess) e = launch_project(c);
       if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
       if (rep > 0 && ms < best_rep) best_rep = ms;
     }
-    if (e != cudaSuccess) st = cuda_fail(c, e, "bsc_autotune: timing the border projection");
+    if (e != cudaSuccess) st = cuda_fail(c, e, "bsc_autotune: timing the projection");
     t.border_ms[path] = best_rep;
   }
-  if (st == BSC_OK) c->border_path = t.border_ms[1] < t.border_ms[0] ? 1 : 0;
+  if (st == BSC_OK) {
+    int best = 0;
+    for (int path = 1; path < 3; ++path)
+      if (t.border_ms[path] < t.border_ms[best]) best = path;
+    c->border_path = best;
+  }
   t.border_path = c->border_path;
   // interior phase-2 occupancy variant: both timed on the same phase-1 output
   if (st == BSC_OK) {

@@ -21,18 +21,20 @@
 // interior spans, Helmert contrasts for the border spans).
 // Phase 2a computes every negative eigenvalue of the batch as an independent
 // item spread over the block; phase 2b computes the eigenvectors, one item
-// per cluster of close eigenvalues; phase 2c lets each owner apply its rank-k
-// correction.  Items are spread over all threads, so no warp carries masked
-// lanes through FP64 work (masked lanes cost the FP64 pipe as much as active
-// ones) and no thread waits on another span's eigenvalue count.  Working
-// sets live in interleaved shared memory; basis, eigenvalues, eigenvectors
-// and w vectors in a per-thread global scratch slot.  The border spans run
-// concurrently in k_project_ring on a forked stream.
+// per cluster of close eigenvalues.  Items are spread over all threads, so
+// no warp carries masked lanes through FP64 work (masked lanes cost the FP64
+// pipe as much as active ones) and no thread waits on another span's
+// eigenvalue count.  Phase 3 applies the rank-k corrections of all spans in
+// one fully parallel read-modify-write of the Hessian planes.  Working sets
+// live in interleaved shared memory; eigenvalues, eigenvectors and w vectors
+// in the class scratch.  The border spans run concurrently on a forked
+// stream (k_project_ring, or the phase kernels with D = 8).
 #include "bsc_internal.cuh"
 #include "proj_core.cuh"
 
 cudaError_t setup_projection_ring();
-cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* work, cudaStream_t st);
+cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* work, cudaStream_t st, bool p1only,
+                                double* sspan, int* kneg);
 
 
 namespace {
@@ -126,58 +128,51 @@ struct TView {
   __device__ __forceinline__ T operator[](int i) const { return p[(size_t)i * s]; }
 };
 
-// H -= sum_r lam_r w_r w_r^T for one span in one pass over its 378 packed
-// entries, in the element type (w_r already in T in the scratch), for
-// kneg <= RM negative eigenvalues.  The unrolled, predicated loops keep
-// lam_r and lam_r w_r[a] of the current row a in registers.  Each row goes in
-// chunks of CH entries whose H values are all loaded before any is updated,
-// so a thread keeps CH reads of H in flight (the update is bound by the
-// latency of these reads, not by arithmetic).
-template <typename T, int RM>
-__device__ __noinline__ void apply_corrections_rm(T* __restrict__ H, int Nsp, int s, proj::View Lam, TView<T> Ws,
-                                                  int kneg) {
-  constexpr int CH = 8;
-  const T* __restrict__ W = Ws.p;
-  const size_t ws = (size_t)Ws.s;
-  T lam[RM];
+// Phase 3: H -= sum_r lam_r w_r w_r^T for every span of a class, one thread
+// per (row a of the packed upper triangle, span position): lam_r w_r[a] in
+// registers, then the row's entries (a, c), c >= a, four at a time with their
+// reads of H and w issued together.  Consecutive threads take consecutive
+// spans of a row, so every access is coalesced; the update is a parallel
+// read-modify-write of the Hessian planes, bound by HBM.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_proj_corr(int count, int Nsp, const int* __restrict__ list, const int* __restrict__ kneg_in,
+                const double* __restrict__ lam, const T* __restrict__ W, T* __restrict__ H) {
+  constexpr int RM = 8;  // negative eigenvalues kept in registers (more go through the loop below)
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 27ll * count) return;
+  const int a = (int)(t / count), pos = (int)(t - (long long)a * count);
+  const int kneg = kneg_in[pos];
+  if (kneg == 0) return;
+  const size_t cs = (size_t)count;
+  const int s = list[pos];
+  T la[RM];
 #pragma unroll
-  for (int r = 0; r < RM; ++r) lam[r] = r < kneg ? (T)Lam[r] : T(0);
-  int e = 0;
+  for (int r = 0; r < RM; ++r) la[r] = r < kneg ? (T)lam[r * cs + pos] * W[(27 * r + a) * cs + pos] : T(0);
+  T* __restrict__ h = H + s;
+  const int e0 = a * 27 - (a * (a - 1)) / 2;  // packed index of (a, a)
 #pragma unroll 1
-  for (int a = 0; a < 27; ++a) {
-    T la[RM];
+  for (int c0 = a; c0 < 27; c0 += 4) {
+    T hv[4], acc[4];
 #pragma unroll
-    for (int r = 0; r < RM; ++r) la[r] = r < kneg ? lam[r] * W[(27 * r + a) * ws] : T(0);
-#pragma unroll 1
-    for (int c0 = a; c0 < 27; c0 += CH) {
-      const int m = 27 - c0 < CH ? 27 - c0 : CH;
-      // every read of the chunk is issued before any of its writes
-      T h[CH], w[RM][CH];
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      hv[u] = c < 27 ? h[(size_t)(e0 + c - a) * Nsp] : T(0);
+      acc[u] = T(0);
 #pragma unroll
-      for (int u = 0; u < CH; ++u) {
-        h[u] = u < m ? H[(size_t)(e + u) * Nsp + s] : T(0);
-#pragma unroll
-        for (int r = 0; r < RM; ++r) w[r][u] = (u < m && r < kneg) ? W[(27 * r + c0 + u) * ws] : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < CH; ++u) {
-        T acc = T(0);
-#pragma unroll
-        for (int r = 0; r < RM; ++r) acc += la[r] * w[r][u];
-        if (u < m) H[(size_t)(e + u) * Nsp + s] = h[u] - acc;
-      }
-      e += m;
+      for (int r = 0; r < RM; ++r)
+        if (r < kneg && c < 27) acc[u] += la[r] * W[(27 * r + c) * cs + pos];
     }
+    for (int r = RM; r < kneg; ++r) {  // rare: more than RM negative eigenvalues
+      const T lr = (T)lam[r * cs + pos] * W[(27 * r + a) * cs + pos];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c0 + u < 27) acc[u] += lr * W[(27 * r + c0 + u) * cs + pos];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (c0 + u < 27) h[(size_t)(e0 + c0 + u - a) * Nsp] = hv[u] - acc[u];
   }
-}
-
-// Dispatch on the count: most spans have at most four negative eigenvalues,
-// and a smaller unrolled bound keeps the loads of a chunk in registers.
-template <typename T, int RMAX>
-__device__ __forceinline__ void apply_corrections(T* H, int Nsp, int s, proj::View Lam, TView<T> Ws, int kneg) {
-  if (kneg <= 4) apply_corrections_rm<T, 4>(H, Nsp, s, Lam, Ws, kneg);
-  else if (kneg <= 8) apply_corrections_rm<T, 8>(H, Nsp, s, Lam, Ws, kneg);
-  else apply_corrections_rm<T, RMAX>(H, Nsp, s, Lam, Ws, kneg);
 }
 
 // Phase 1: one thread per interior span (uniform work, no barriers).
@@ -250,12 +245,13 @@ __device__ __forceinline__ void block_prefix(int v, int* prefix, int* wsum) {
 // item).  The autotuner keeps the faster for the interior class.
 constexpr int P2_MINB[2] = {2, 3};
 
-// Phase 2 over batches of P2_BLOCK consecutive interior spans: (a) every
+// Phase 2 over batches of P2_BLOCK consecutive spans of a class: (a) every
 // negative eigenvalue is an independent item, (b) every cluster of close
-// eigenvalues is an item that computes its eigenvectors, (c) each owner
-// applies H -= sum lam w w^T to its span.  Items are spread over the whole
-// block, so no warp carries masked lanes through FP64 work (masked lanes
-// cost the FP64 pipe as much as active ones).
+// eigenvalues is an item that computes its eigenvectors; the eigenvalues and
+// w vectors go to the class scratch, and phase 3 (k_proj_corr) applies
+// H -= sum lam w w^T.  Items are spread over the whole block, so no warp
+// carries masked lanes through FP64 work (masked lanes cost the FP64 pipe as
+// much as active ones).
 template <typename T, int D, int MINB>
 __global__ void __launch_bounds__(P2_BLOCK, MINB)
     k_proj_p2(ProjArgs<T> P, const int* __restrict__ list, int count, const int* __restrict__ kneg_in,
@@ -279,21 +275,6 @@ __global__ void __launch_bounds__(P2_BLOCK, MINB)
     const int t = base + tid;
     const int kneg = t < count ? kneg_in[t] : 0;
     s_kneg[tid] = kneg;
-    {
-      // (c) reads and rewrites the 378 entry planes over this batch's spans
-      // (ascending span ids): start pulling them into L2 now, so that the
-      // update waits on L2 rather than on HBM
-      const int last = base + P2_BLOCK - 1 < count ? base + P2_BLOCK - 1 : count - 1;
-      const size_t s0 = (size_t)list[base], s1 = (size_t)list[last];
-      const bool dense = s1 >= s0 && s1 - s0 < 2 * P2_BLOCK;  // scattered batches (border spans) are skipped
-      for (int e = tid; dense && e < H27; e += P2_BLOCK) {
-        const char* b0 = reinterpret_cast<const char*>(P.H + (size_t)e * P.Nsp + s0);
-        const char* b1 = reinterpret_cast<const char*>(P.H + (size_t)e * P.Nsp + s1);
-        for (const char* q = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(b0) & ~uintptr_t(127));
-             q <= b1; q += 128)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
-      }
-    }
     // (a) eigenvalues
     block_prefix<P2_BLOCK>(kneg, s_pre, s_wsum);
     for (int i = tid; i < s_pre[P2_BLOCK]; i += P2_BLOCK) {
@@ -331,9 +312,6 @@ __global__ void __launch_bounds__(P2_BLOCK, MINB)
       proj::cluster_vectors_reg<D>(sv(to, SS::R), sv(to, SS::A), Qs, Ys, sv(to, SS::LAM), wv(to), LU,
                                    sspan[(size_t)SS::TN * count + to], k0, k1 - k0);
     }
-    __syncthreads();
-    // (c) the owner applies the rank-k correction to its span
-    if (kneg > 0) apply_corrections<T, n>(P.H, P.Nsp, list[t], sv(t, SS::LAM), wv(t), kneg);
     __syncthreads();
   }
 }
@@ -434,18 +412,34 @@ cudaError_t run_class(bsc_ctx* c, int k, const int* list, int count, cudaStream_
       k_proj_p2<T, D, P2_MINB[1]><<<c->p2_grid[k][1], P2_BLOCK, p2_smem<D>(), st>>>(
           P, list, count, c->proj_kneg[k], c->proj_span[k], c->proj_scratch[k], c->proj_work + k);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    BSC_COUNT(c, 1);
+    using SS = SpanScratch<D>;
+    const double* sp = c->proj_span[k];
+    const long long nthreads = 27ll * count;
+    k_proj_corr<T><<<(unsigned)((nthreads + 255) / 256), 256, 0, st>>>(
+        count, c->Nsp, list, c->proj_kneg[k], sp + (size_t)SS::LAM * count,
+        reinterpret_cast<const T*>(sp + (size_t)SS::W * count), (T*)c->H_span);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// The border class by either path: 0 = one warp per span (k_project_ring,
-// lowest latency per span: best when there are few border spans), 1 = one
-// thread per span through the two phase kernels with D = 8 (highest
-// throughput: best when there are many).
+// The border class by one of three paths: 0 = one warp per span
+// (k_project_ring, lowest latency per span: best when there are few border
+// spans), 1 = one thread per span through the two phase kernels with D = 8
+// (highest throughput: best when there are many), 2 = the warp-per-span
+// tridiagonalisation followed by the thread-per-item eigenpair phase (lanes
+// busy in both halves).
 template <typename T>
 cudaError_t run_border(bsc_ctx* c, int path, cudaStream_t st) {
   const int first = c->bucket_off[1], count = c->bucket_off[3] - c->bucket_off[1];
-  if (path == 0) return launch_project_ring(c, first, count, c->proj_work + 2, st);
+  static_assert(SpanScratch<8>::R == 300 && SpanScratch<8>::TN == 372, "ring phase-1 layout");
+  if (path == 0) return launch_project_ring(c, first, count, c->proj_work + 2, st, false, nullptr, nullptr);
+  if (path == 2) {
+    cudaError_t e = launch_project_ring(c, first, count, c->proj_work + 2, st, true, c->proj_span[1], c->proj_kneg[1]);
+    if (e != cudaSuccess) return e;
+    return run_class<T, 8>(c, 1, c->bucket_list + first, count, st, 1);
+  }
   return run_class<T, 8>(c, 1, c->bucket_list + first, count, st);
 }
 

@@ -273,9 +273,20 @@ __device__ void warp_mgs(double (&y)[RN], int lane, int kneg) {
 // (row, column) of packed upper-triangle entry e of a 27 x 27 matrix
 __constant__ unsigned char c_row[H27], c_col[H27];
 
-template <typename T>
+// Phase-1 output of a span for the thread-per-item eigenpair kernel (the
+// class scratch of k_proj_p2 with D = 8, entry-major over the span's
+// position in the class list): packed reflectors with tau on the diagonal,
+// the scaled tridiagonal (d, e, e^2), the scale, and the count.
+struct RingP1Out {
+  double* A;    // [300][count]
+  double* R;    // [72][count]
+  double* TN;   // [count]
+  int* kneg;    // [count]
+};
+
+template <typename T, bool P1ONLY>
 __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const int* __restrict__ list, int count,
-                                                         unsigned int* __restrict__ work) {
+                                                         unsigned int* __restrict__ work, RingP1Out out) {
   constexpr int WARPS = RBLOCK / 32;
   __shared__ double s_refl[WARPS][RN][RN];  // reflector k in column k (rows k+1..), tau_k at [k][k]
   __shared__ double s_d[WARPS][RN], s_e[WARPS][RN], s_e2[WARPS][RN];
@@ -423,8 +434,10 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
     if (!(tn > 0.0) || !isfinite(tn)) {
       if (lane == 0) {
         P.nneg[s] = 0;
+        if (P1ONLY) out.kneg[idx] = 0;
         if (!isfinite(tn)) atomicOr(P.status, BSC_STATUS_NUMERIC_FLAG);
       }
+      __syncwarp();
       continue;
     }
     const double itn = 1.0 / tn;
@@ -439,6 +452,25 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
     __syncwarp();
     const int kneg = sturm64(dd, ee2, -NEG_REL);
     if (lane == 0) P.nneg[s] = kneg;
+    if (P1ONLY) {
+      // hand the span to the eigenpair items: reflectors k <= RN - 3 (the
+      // back-transformation uses no others), tridiagonal, scale, count
+      if (lane == 0) out.kneg[idx] = kneg;
+      if (kneg > 0) {
+        for (int q = lane; q < RN * RN; q += 32) {
+          const int i = q / RN, k = q - i * RN;
+          if (k <= RN - 3 && i >= k) out.A[(size_t)(i * (i + 1) / 2 + k) * count + idx] = refl[i * RN + k];
+        }
+        if (lane < RN) {
+          out.R[(size_t)lane * count + idx] = dd[lane];
+          out.R[(size_t)(RN + lane) * count + idx] = ee[lane];
+          out.R[(size_t)(2 * RN + lane) * count + idx] = ee2[lane];
+        }
+        if (lane == 0) out.TN[idx] = tn;
+      }
+      __syncwarp();
+      continue;
+    }
     if (kneg == 0) continue;
 
     // ---- lane k < kneg: eigenvalue k (FP32 bracket, FP64 check + refinement)
@@ -542,7 +574,11 @@ cudaError_t setup_projection_ring() {
 
 int ring_grid(int num_sms) { return 2 * num_sms; }
 
-cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* work, cudaStream_t st) {
+// Border class, one warp per span.  p1only: stop after the tridiagonal form
+// and hand each span to k_proj_p2<T, 8> through its class scratch (sspan,
+// laid out as reflectors [300], tridiagonal [72], scale [1]) and kneg.
+cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* work, cudaStream_t st, bool p1only,
+                                double* sspan, int* kneg) {
   if (count <= 0) return cudaSuccess;
   BSC_COUNT(c, 1);
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
@@ -550,16 +586,24 @@ cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* 
   const int need = (count + RBLOCK / 32 - 1) / (RBLOCK / 32);
   int g = ring_grid(c->num_sms);
   if (g > need) g = need;
+  const size_t cnt = (size_t)count;
+  RingP1Out out{sspan, sspan ? sspan + 300 * cnt : nullptr, sspan ? sspan + 372 * cnt : nullptr, kneg};
   if (c->precision == BSC_FP64) {
     RingArgs<double> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const double*)c->tab_mem,
                        (const double*)c->tab_bd, (const double*)c->A_mem, (double*)c->H_span, c->nneg, c->dstatus,
                        c->red_g, c->red_l};
-    k_project_ring<double><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work);
+    if (p1only)
+      k_project_ring<double, true><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work, out);
+    else
+      k_project_ring<double, false><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work, out);
   } else {
     RingArgs<float> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const float*)c->tab_mem,
                       (const float*)c->tab_bd, (const float*)c->A_mem, (float*)c->H_span, c->nneg, c->dstatus,
                       c->red_g, c->red_l};
-    k_project_ring<float><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work);
+    if (p1only)
+      k_project_ring<float, true><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work, out);
+    else
+      k_project_ring<float, false><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work, out);
   }
   return cudaGetLastError();
 }

@@ -82,11 +82,12 @@ def test_lumped_mass(case):
     assert rel(ctx.lumped_mass(), prob.lumped_mass()) < 1e-13
 
 
-@pytest.mark.parametrize("project,border_path", [(False, 0), (True, 0), (True, 1)],
-                         ids=["raw", "proj-warp", "proj-thread"])
+@pytest.mark.parametrize("project,border_path", [(False, 0), (True, 0), (True, 1), (True, 2)],
+                         ids=["raw", "proj-warp", "proj-thread", "proj-warp-items"])
 def test_span_terms_fp64(case, project, border_path):
-    """Span terms against the oracle; projected by both paths of the border
-    spans (one warp per span, one thread per span)."""
+    """Span terms against the oracle; projected by every path of the border
+    spans (one warp per span; one thread per span; one warp per span to the
+    tridiagonal form, then one thread per eigenpair)."""
     pat, prob, ctx = case
     C = ctx.to_device(pat.C)
     ctx.set_border_path(border_path)

@@ -240,19 +240,24 @@ __device__ __forceinline__ void block_prefix(int v, int* prefix, int* wsum) {
   __syncthreads();
 }
 
+// Spans per phase-2 batch: the whole block for the interior class; a quarter
+// for the border class, whose few spans (a thousand or two in a large patch)
+// would otherwise fill only a few blocks with several items per thread.
+__host__ __device__ constexpr int p2_spans(int D) { return D == 5 ? P2_BLOCK : P2_BLOCK / 4; }
+
 // Phase-2 occupancy variants: MINB resident blocks per SM (2: no register
 // limit below 255; 3: 168 registers, a little spilling in the eigenvector
 // item).  The autotuner keeps the faster for the interior class.
 constexpr int P2_MINB[2] = {2, 3};
 
-// Phase 2 over batches of P2_BLOCK consecutive spans of a class: (a) every
+// Phase 2 over batches of SB consecutive spans of a class: (a) every
 // negative eigenvalue is an independent item, (b) every cluster of close
 // eigenvalues is an item that computes its eigenvectors; the eigenvalues and
 // w vectors go to the class scratch, and phase 3 (k_proj_corr) applies
 // H -= sum lam w w^T.  Items are spread over the whole block, so no warp
 // carries masked lanes through FP64 work (masked lanes cost the FP64 pipe as
 // much as active ones).
-template <typename T, int D, int MINB>
+template <typename T, int D, int MINB, int SB = p2_spans(D)>
 __global__ void __launch_bounds__(P2_BLOCK, MINB)
     k_proj_p2(ProjArgs<T> P, const int* __restrict__ list, int count, const int* __restrict__ kneg_in,
               double* __restrict__ sspan, double* __restrict__ slots, unsigned int* __restrict__ work) {
@@ -268,12 +273,12 @@ __global__ void __launch_bounds__(P2_BLOCK, MINB)
   auto sv = [&](int t, int off) { return proj::View{sspan + (size_t)off * count + t, count}; };
   auto wv = [&](int t) { return TView<T>{reinterpret_cast<T*>(sspan + (size_t)SS::W * count) + t, count}; };
   for (;;) {
-    if (tid == 0) s_base = (int)atomicAdd(work, (unsigned)P2_BLOCK);
+    if (tid == 0) s_base = (int)atomicAdd(work, (unsigned)SB);
     __syncthreads();
     const int base = s_base;
     if (base >= count) break;
     const int t = base + tid;
-    const int kneg = t < count ? kneg_in[t] : 0;
+    const int kneg = (tid < SB && t < count) ? kneg_in[t] : 0;
     s_kneg[tid] = kneg;
     // (a) eigenvalues
     block_prefix<P2_BLOCK>(kneg, s_pre, s_wsum);
@@ -472,7 +477,7 @@ cudaError_t p2_grid_of(bsc_ctx* c, int count, int* grid) {
     return e;
   per = per < 1 ? 1 : per;
   int g = per * c->num_sms;
-  const int need = (count + P2_BLOCK - 1) / P2_BLOCK;
+  const int need = (count + p2_spans(D) - 1) / p2_spans(D);
   if (g > need) g = need;
   *grid = g < 1 ? 1 : g;
   return cudaSuccess;

@@ -134,23 +134,22 @@ class ClockSampler:
 # --------------------------------------------------------------------------- flop model
 
 def projection_flops(nred, nneg, nm, nb):
-    """Algorithmic FP64 flops of the SPD projection of one span as implemented:
-    basis orthonormalisation (interior spans), reduced Hessian formation,
-    Householder tridiagonalisation (4/3 n^3), the inertia count, and per
-    negative eigenvalue: the FP64 check of its FP32 bracket and the
-    regula-falsi refinement (5 characteristic-polynomial evaluations of 4 n
-    flops on average), the pivoted LU and two solves of the shifted
-    tridiagonal, the Rayleigh quotient, the back-transformation (2 n^2), the
-    mapping to span DOFs and the rank-one update of the 378 packed entries
-    (FP32 bracketing and FP32 updates are not counted)."""
+    """Algorithmic FP64 flops of the SPD projection of one span per Newton
+    iteration as implemented: reduced Hessian formation from the reduced
+    derivative vectors (the span's orthonormal basis and the vectors in it
+    depend on the rest geometry only and are computed once per context, so
+    they are not counted), Householder tridiagonalisation (4/3 n^3), the
+    inertia count, and per negative eigenvalue: the FP64 check of its FP32
+    bracket and the regula-falsi refinement (5 characteristic-polynomial
+    evaluations of 4 n flops on average), the pivoted LU and two solves of
+    the shifted tridiagonal, the Rayleigh quotient, the back-transformation
+    (2 n^2), the mapping to span DOFs and the rank-one update of the 378
+    packed entries (FP32 bracketing and FP32 updates are not counted)."""
     n = nred
     D = n // 3
-    m = 2 * nm + nb
     f = 0.0
-    if n == 15:
-        f += m * (27 + 2 * 2 * 18 * D / 2)             # mean removal, norm, two MGS passes (mean rank D/2)
-    f += nm * 2 * (18 * D + 36 * D + 9 * D * (D + 1))  # g~, T_k, reduced blocks per membrane point
-    f += nb * (18 * D + 2 * D * (D + 1))               # L~ and blocks per bending point
+    f += nm * 2 * (36 * D + 9 * D * (D + 1))           # T_k, reduced blocks per membrane point
+    f += nb * (2 * D * (D + 1))                        # blocks per bending point
     f += 4.0 * n ** 3 / 3.0 + 4 * n                    # tridiagonalisation, scaling
     f += 4 * n                                         # inertia count at -tau
     if nneg:

@@ -448,18 +448,22 @@ cudaError_t run_border(bsc_ctx* c, int path, cudaStream_t st) {
   return run_class<T, 8>(c, 1, c->bucket_list + first, count, st);
 }
 
-// Both classes.  Phase 1 of the interior class runs alone (one block of
-// 211 KB of shared memory per SM leaves no room for other blocks); then the
-// border class runs on a forked stream next to the interior phase 2.
+// Both classes.  The border class runs on a forked stream.  Its warp-per-span
+// kernel (paths 0 and 2) fits beside the interior phase 1 (one block of 211 KB
+// of shared memory per SM leaves room for one-warp blocks), so it is forked
+// before that phase; the thread-per-span kernels (path 1) do not fit and are
+// forked after it, next to the interior phase 2.
 template <typename T>
 cudaError_t run_all(bsc_ctx* c) {
   cudaError_t e;
   const int* list0 = c->bucket_list + c->bucket_off[0];
   const int n0 = c->bucket_off[1] - c->bucket_off[0];
-  if ((e = run_class<T, 5>(c, 0, list0, n0, c->stream, 0)) != cudaSuccess) return e;
+  const bool early = c->border_path != 1;
+  if (!early && (e = run_class<T, 5>(c, 0, list0, n0, c->stream, 0)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->fork_ev, c->stream)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(c->side[0], c->fork_ev, 0)) != cudaSuccess) return e;
   if ((e = run_border<T>(c, c->border_path, c->side[0])) != cudaSuccess) return e;
+  if (early && (e = run_class<T, 5>(c, 0, list0, n0, c->stream, 0)) != cudaSuccess) return e;
   if ((e = run_class<T, 5>(c, 0, list0, n0, c->stream, 1)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->join_ev[0], c->side[0])) != cudaSuccess) return e;
   return cudaStreamWaitEvent(c->stream, c->join_ev[0], 0);

@@ -26,7 +26,8 @@
 namespace {
 
 constexpr int RN = 24;         // reduced size 3 x 8
-constexpr int RBLOCK = 128;    // four warps (spans) per block
+constexpr int RBLOCK = 32;     // one warp (span) per block: 5.6 KB of shared memory, so blocks fit beside the
+                                // interior phase 1 (211 KB per SM) and the border class can start with it
 constexpr double NEG_REL = 1e-14;
 
 // Helmert contrasts: q_k = (1, ..., 1, -k, 0, ...) / sqrt(k (k + 1)), k = 1..8
@@ -572,7 +573,10 @@ cudaError_t setup_projection_ring() {
   return cudaMemcpyToSymbol(c_col, cc, sizeof(cc));
 }
 
-int ring_grid(int num_sms) { return 2 * num_sms; }
+// Three one-warp blocks per SM: with the interior phase 1's block (211 KB of
+// shared memory, 160 threads x 254 registers) they fill an SM's 228 KB of
+// shared memory and 64 K registers, so both kernels run side by side.
+int ring_grid(int num_sms) { return 3 * num_sms; }
 
 // Border class, one warp per span.  p1only: stop after the tridiagonal form
 // and hand each span to k_proj_p2<T, 8> through its class scratch (sspan,

@@ -316,11 +316,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsig
 
 // Row alpha (patch-local index) of y = K x in the element type T; K and x
 // already point at the patch's first control point, N is the plane stride.
-// X_RO: x stays unchanged for the whole kernel, so it may go through the
-// non-coherent read-only path; the persistent solvers update their x (the
-// search direction) between grid barriers and read it with plain loads,
-// which the barriers' fences make coherent.
-template <typename T, bool X_RO = false>
+// X_MODE 1: x stays unchanged for the whole kernel, so it may go through the
+// non-coherent read-only path.  The persistent solvers update their x (the
+// search direction) between grid barriers: 0 reads it with plain loads, which
+// the barriers' fences make coherent; 2 reads it from L2 (ld.global.cg),
+// which is coherent without relying on L1 invalidation.
+template <typename T, int X_MODE = 0>
 __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T* __restrict__ K, const T* x,
                                          T y[3]) {
   const int i = al % nu, j = al / nu;
@@ -335,8 +336,10 @@ __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T*
       if (ib < 0 || ib >= nu) continue;
       const int slot = (dv + 2) * 5 + (du + 2), be = jb * nu + ib;
       T x0, x1, x2;
-      if (X_RO) {
+      if (X_MODE == 1) {
         x0 = __ldg(x + be); x1 = __ldg(x + N + be); x2 = __ldg(x + 2 * N + be);
+      } else if (X_MODE == 2) {
+        x0 = __ldcg(x + be); x1 = __ldcg(x + N + be); x2 = __ldcg(x + 2 * N + be);
       } else {
         x0 = x[be]; x1 = x[N + be]; x2 = x[2 * N + be];
       }

@@ -130,8 +130,8 @@ struct TView {
 
 // Phase 3: H -= sum_r lam_r w_r w_r^T for every span of a class, one thread
 // per (row a of the packed upper triangle, span position): lam_r w_r[a] in
-// registers, then the row's entries (a, c), c >= a, four at a time with their
-// reads of H and w issued together.  Consecutive threads take consecutive
+// registers, then the row's entries (a, c), c >= a, eight at a time with
+// their reads of H and w issued together.  Consecutive threads take consecutive
 // spans of a row, so every access is coalesced; the update is a parallel
 // read-modify-write of the Hessian planes, bound by HBM.
 template <typename T>
@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(256)
     k_proj_corr(int count, int Nsp, const int* __restrict__ list, const int* __restrict__ kneg_in,
                 const double* __restrict__ lam, const T* __restrict__ W, T* __restrict__ H) {
   constexpr int RM = 8;  // negative eigenvalues kept in registers (more go through the loop below)
+  constexpr int CW = 8;  // entries of a row per step
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 27ll * count) return;
   const int a = (int)(t / count), pos = (int)(t - (long long)a * count);
@@ -152,10 +153,10 @@ __global__ void __launch_bounds__(256)
   T* __restrict__ h = H + s;
   const int e0 = a * 27 - (a * (a - 1)) / 2;  // packed index of (a, a)
 #pragma unroll 1
-  for (int c0 = a; c0 < 27; c0 += 4) {
-    T hv[4], acc[4];
+  for (int c0 = a; c0 < 27; c0 += CW) {
+    T hv[CW], acc[CW];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < CW; ++u) {
       const int c = c0 + u;
       hv[u] = c < 27 ? h[(size_t)(e0 + c - a) * Nsp] : T(0);
       acc[u] = T(0);
@@ -166,11 +167,11 @@ __global__ void __launch_bounds__(256)
     for (int r = RM; r < kneg; ++r) {  // rare: more than RM negative eigenvalues
       const T lr = (T)lam[r * cs + pos] * W[(27 * r + a) * cs + pos];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < CW; ++u)
         if (c0 + u < 27) acc[u] += lr * W[(27 * r + c0 + u) * cs + pos];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < CW; ++u)
       if (c0 + u < 27) h[(size_t)(e0 + c0 + u - a) * Nsp] = hv[u] - acc[u];
   }
 }

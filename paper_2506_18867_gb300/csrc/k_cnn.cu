@@ -720,7 +720,7 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
         const int qn = jj * nu + ii;
         const float at = ap[t];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] += at * F.y[(size_t)c * P + qn];
+        for (int c = 0; c < 3; ++c) acc[c] += at * __ldcg(F.y + (size_t)c * P + qn);  // neighbours' y: via L2
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) F.u[(size_t)c * P + al] = acc[c];
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
           const int qn = jj * nu + ii;
           const float at = F.A[(size_t)qn * 16 + t];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) v[c] += at * F.u[(size_t)c * P + qn];
+          for (int c = 0; c < 3; ++c) v[c] += at * __ldcg(F.u + (size_t)c * P + qn);  // neighbours' u: via L2
         }
         linvT_mul(F.Linv + (size_t)al * 6, v, zv);
       }

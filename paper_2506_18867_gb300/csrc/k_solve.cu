@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
       double l_pq = 0.0;
       for (int al = tid; al < Np; al += stride) {
         T y[3];
-        spmv_row<T>(nu, nv, N, al, K, pv, y);
+        spmv_row<T>(nu, nv, N, al, K, pv, y);  // plain loads of the neighbours' p (measured faster here than via L2)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           qv[c * N + al] = y[c];

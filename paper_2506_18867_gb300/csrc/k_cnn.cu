@@ -850,10 +850,15 @@ cudaError_t conv(bsc_cnn* n, const __nv_bfloat16* X, const uint8_t* W, const flo
   return cudaGetLastError();
 }
 
+// The largest shared-memory carveout, so that two CTAs (2 x 92 KB of tiles)
+// share an SM: one CTA's gather and epilogue overlap the other's MMAs.
 template <int CIN, int COUT, int MODE>
 cudaError_t conv_setup() {
-  return cudaFuncSetAttribute(k_conv<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)conv_smem<CIN, COUT>());
+  cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)conv_smem<CIN, COUT>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_conv<CIN, COUT, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
 }
 
 cudaError_t dot(bsc_cnn* n, const float* a, const float* b, double* out_slot) {
@@ -1048,13 +1053,11 @@ bsc_status bsc_cnn_create(bsc_ctx* c, bsc_cnn** out) {
     cnn_free(n);
     return e == cudaErrorMemoryAllocation ? BSC_ERR_OOM : BSC_ERR_CUDA;
   }
-  // persistent conv CTAs: as many as fit (two per SM with the 92 KB tiles)
-  int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv<32, 32, CONV_RELU_BF16>, TILE,
-                                                conv_smem<32, 32>());
-  per = per < 1 ? 1 : (per > 4 ? 4 : per);
+  // persistent conv CTAs: two per SM (2 x 92 KB of tiles with the largest
+  // shared-memory carveout, 2 x 32 TMEM columns); a CTA that does not fit
+  // simply starts later (no CTA waits on another)
   const int tiles = (n->P + TILE - 1) / TILE;
-  n->conv_grid = std::min(tiles, per * c->num_sms);
+  n->conv_grid = std::min(tiles, 2 * c->num_sms);
   int perf = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf, k_fcg_learned<256>, 256, 0);
   perf = perf < 1 ? 1 : (perf > 4 ? 4 : perf);

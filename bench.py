@@ -416,7 +416,7 @@ def measure_batch(bsc, flush, stream, torch, np, seed=1, steps=3, warmup=2):
            "eval_assembly_ms": eval_ms, "phases_ms": {k: v / steps for k, v in phases.items()},
            "launches_per_step": launches / steps, "max_pcg_iters": reports[-1]["pcg_iters"],
            "max_ls_halvings": reports[-1]["ls_halvings"], "tile_tu": tuning["tile_tu"],
-           "graph": ctx.graph_state(), "steps": steps}
+           "autotune": tuning, "graph": ctx.graph_state(), "steps": steps}
     ctx.close()
     return out
 

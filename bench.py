@@ -384,7 +384,7 @@ def run_gpu(args):
             "roofline": {"kernel": "SPD projection (k_proj_p1, k_proj_p2, k_project_ring: FP64)",
                          "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                         "traffic": projection_traffic(args.workload, prec == bsc.FP32),
+                         "traffic": projection_traffic(args.workload, prec == bsc.FP32, tuning),
                          "algorithmic_flops_per_step": flops, "launch_ms": proj_ms,
                          "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); no FP64 peak in the measured peaks"},
             "fp64": fp64,
@@ -445,25 +445,34 @@ def measure_learned(bsc, np, seeds=(1_000_000, 1_000_001, 1_000_002, 1_000_003),
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the projection
-# phase per Newton step, from one ncu capture (profiles/k_project_drape256_fp32.md:
-# k_proj_p1 80.5 MB + k_project_ring 18.3 MB + k_proj_p2 326.1 MB), keyed by a
-# hash of the projection sources it was taken with.
-PROJECTION_TRAFFIC = {("drape256", True): ("57ed2d49a7311e45", 424.9e6)}
+# phase per Newton step, from one metrics-only ncu capture of the drape bench
+# (profiles/k_project_drape256_fp32.md), keyed by the autotuner's border path and
+# phase-2 variant and by a hash of the projection sources it was taken with.
+#   path 2, variant 0: ring<1> 3.8 + p1<5> 54.8 + p2<5,2> 150.9 + corr 180.3
+#                      + p2<8> 6.9 + corr 16.1 MB
+#   path 1, variant 0: p1<5> 54.8 + p1<8> 3.7 + p2<8> 6.9 + corr 16.1
+#                      + p2<5,2> 150.9 + corr 180.3 MB
+#   path 0, variant 1: ring<0> 18.6 + p1<5> 55.2 + p2<5,3> 183.5 + corr 180.2 MB
+PROJECTION_TRAFFIC_HASH = "85a309a31ce15230"
+PROJECTION_TRAFFIC = {("drape256", True, 2, 0): 412.7e6,
+                      ("drape256", True, 1, 0): 412.6e6,
+                      ("drape256", True, 0, 1): 437.5e6}
 PROJECTION_SOURCES = ("k_project.cu", "proj_core.cuh", "k_project_ring.cu")
 
 
-def projection_traffic(workload, fp32):
-    """The captured DRAM traffic of the projection phase, or None when no
-    capture exists for the workload or the kernels changed since it."""
+def projection_traffic(workload, fp32, tuning):
+    """The captured DRAM traffic of the projection phase for the autotuner's
+    choices, or None when no capture exists for them or the kernels changed
+    since it."""
     import hashlib
-    rec = PROJECTION_TRAFFIC.get((workload, bool(fp32)))
+    rec = PROJECTION_TRAFFIC.get((workload, bool(fp32), tuning.get("border_path"), tuning.get("p2_variant")))
     if rec is None:
         return None
     h = hashlib.sha256()
     for f in PROJECTION_SOURCES:
         with open(os.path.join(ROOT, "paper_2506_18867_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return rec[1] if h.hexdigest()[:16] == rec[0] else None
+    return rec if h.hexdigest()[:16] == PROJECTION_TRAFFIC_HASH else None
 
 
 # --------------------------------------------------------------------------- CPU oracle

@@ -76,6 +76,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-garment sub-measurement")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner sub-measurement")
+    p.add_argument("--no-point", action="store_true", help="skip the per-point projection sub-measurement")
     return p.parse_args()
 
 
@@ -335,6 +336,10 @@ def run_gpu(args):
     learned = None
     if args.workload == "drape256" and not args.no_learned and prec == bsc.FP32 and rank == 0:
         learned = measure_learned(bsc, np)
+    point = None
+    if len(pats) == 1 and not args.no_point and rank == 0:
+        point = measure_point_projection(bsc, pats[0], prec, ctx, C0, Chat, K, args.warmup, ms_step, flush, stream,
+                                         torch)
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
@@ -390,6 +395,7 @@ def run_gpu(args):
             "fp64": fp64,
             "batched": batched,
             "learned": learned,
+            "point_projection": point,
             "cpu_baseline": cpu,
             "clocks": clk,
         }
@@ -398,6 +404,57 @@ def run_gpu(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def newton_to_convergence(ctx, C, C0, Chat, dt, stream, torch, tol=1e-2, max_iter=30):
+    """Newton iterations of one time step from C0 until ||d||_inf / dt < tol
+    (the paper's stopping rule, Sec. 6): iterations and device ms."""
+    C.copy_(C0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    it = 0
+    for it in range(1, max_iter + 1):
+        rep = ctx.newton_step(C, Chat)
+        if rep.status != 0 or rep.dir_inf / dt < tol:
+            break
+    ev1.record(stream)
+    ev1.synchronize()
+    return {"iterations": it, "ms": ev0.elapsed_time(ev1), "status": rep.status,
+            "dir_inf_over_dt": rep.dir_inf / dt}
+
+
+def measure_point_projection(bsc, pat, prec, ctx_span, C0, Chat, steps, warmup, span_ms, flush, stream, torch):
+    """The same workload with the per-point closed-form projection of the FBW
+    terms (BSC_PROJECT_POINT) instead of the FP64 span projection: Newton-step
+    time, and Newton iterations to convergence for both projections."""
+    ctx = bsc.context_for_patch(pat, precision=prec, project=bsc.PROJECT_POINT, pcg_rel_tol=1e-8)
+    ctx.set_profiling(True)
+    ctx.autotune(C0, Chat)
+    C = C0.clone()
+    ms, ph, reps, launches = time_newton(ctx, C, C0, Chat, steps, warmup, flush, stream, torch)
+    step_ms = sum(ms) / steps
+    eval_ms = (ph["span_eval"] + ph["project"] + ph["assemble"]) / steps
+    conv = {"point": newton_to_convergence(ctx, C, C0, Chat, pat.dt, stream, torch),
+            "span": newton_to_convergence(ctx_span, C, C0, Chat, pat.dt, stream, torch)}
+    ctx.close()
+    # the paper's ablation baseline (Sec. 6.5, case A): 2x2 Gauss on the
+    # interior spans, same projection, same state
+    ctx = bsc.context_for_patch(pat, precision=prec, project=bsc.PROJECT_POINT, pcg_rel_tol=1e-8,
+                                quadrature=(bsc.QUAD_STANDARD, bsc.QUAD_STANDARD))
+    ctx.set_profiling(True)
+    ctx.autotune(C0, Chat)
+    ms_a, ph_a, reps_a, _ = time_newton(ctx, C, C0, Chat, steps, warmup, flush, stream, torch)
+    pts = lambda c: (len(c.quadrature_tables(0)), len(c.quadrature_tables(1)))  # noqa: E731
+    ablation = {"quadrature": "2x2 Gauss on interior spans, reduced placements on boundary spans",
+                "newton_step_ms": sum(ms_a) / steps, "phases_ms": {k: v / steps for k, v in ph_a.items()},
+                "pcg_iters": reps_a[-1]["pcg_iters"], "points_membrane_bending": pts(ctx),
+                "to_convergence": newton_to_convergence(ctx, C, C0, Chat, pat.dt, stream, torch)}
+    ctx.close()
+    return {"newton_step_ms": step_ms, "eval_assembly_ms": eval_ms, "spans_per_s": ctx_span.n_spans / (eval_ms * 1e-3),
+            "phases_ms": {k: v / steps for k, v in ph.items()}, "pcg_iters": reps[-1]["pcg_iters"],
+            "newton_step_speedup_vs_span_projection": span_ms / step_ms, "gpu_launches_per_step": launches / steps,
+            "points_membrane_bending": pts(ctx_span), "to_convergence": conv,
+            "stop_rule": "||d||_inf / dt < 1e-2 m/s", "ablation_standard_2x2": ablation}
 
 
 def measure_batch(bsc, flush, stream, torch, np, seed=1, steps=3, warmup=2):

@@ -60,9 +60,22 @@ enum { BSC_FP64 = 0, BSC_FP32 = 1 };
 /* Quadrature rules: the paper's reduced rules (Sec. 4.1 membrane: dual-grid
  * alternating 1x2 / 2x1 Gauss in the interior, 3x3 corner spans, 3x2 / 2x3
  * side spans; Sec. 4.2 bending: one point per boundary span centre and per
- * interior knot intersection, Fig. 3), or full per-span Gauss rules used by
- * the paper's ablation (Sec. 6.5) and by tests. */
-enum { BSC_QUAD_REDUCED = 0, BSC_QUAD_GAUSS2 = 2, BSC_QUAD_GAUSS3 = 3 };
+ * interior knot intersection, Fig. 3); the baseline of the paper's ablation
+ * (Sec. 6.5, case A): 2x2 Gauss on every interior span for both energies,
+ * with the reduced rules' boundary-span placements (BSC_QUAD_STANDARD); or
+ * full per-span Gauss rules everywhere, used by tests. */
+enum { BSC_QUAD_REDUCED = 0, BSC_QUAD_GAUSS2 = 2, BSC_QUAD_GAUSS3 = 3, BSC_QUAD_STANDARD = 4 };
+
+/* PSD projection of the elastic Hessian (projected Newton, Sec. 5.1):
+ * NONE  - the Hessian as it is (indefinite in compression);
+ * SPAN  - each span's summed membrane + bending 27x27 Hessian replaced by
+ *         V max(Lambda, 0) V^T, computed in FP64;
+ * POINT - at every membrane quadrature point each FBW term's Hessian w.r.t.
+ *         (f_1, f_2) (the two stretch terms and the shear term of Sec. 4.1)
+ *         replaced by its PSD projection in closed form before the chain
+ *         rule, the eigenanalysis FBW admits; the bending Hessian is PSD
+ *         already.  Computed in the precision T of the span evaluation. */
+enum { BSC_PROJECT_NONE = 0, BSC_PROJECT_SPAN = 1, BSC_PROJECT_POINT = 2 };
 
 /* Knot grid (Sec. 3.1.2).  knots_u / knots_v may be NULL; if given they must
  * hold the open uniform integer knot vector of length nu+3 / nv+3. */
@@ -94,7 +107,7 @@ typedef struct bsc_options {
   double gravity[3];    /* m/s^2; body force m_alpha * gravity */
   const int32_t* pinned; /* host array of Dirichlet control points (copied) */
   int n_pinned;
-  int project;          /* default PSD projection flag for bsc_newton_step */
+  int project;          /* BSC_PROJECT_*: the projection bsc_newton_step uses */
   double pcg_rel_tol;   /* PCG stops when ||r|| <= tol * ||b|| (<= 0: 1e-8) */
   int pcg_max_iter;     /* <= 0: 10000 */
   int max_line_search;  /* halvings of alpha before BSC_ERR_LINESEARCH (<= 0: 30) */
@@ -109,7 +122,8 @@ typedef struct bsc_newton_report {
   int pcg_iters;
   int ls_halvings;
   int status;           /* bsc_status of the step */
-  int spans_projected;  /* spans whose Hessian had a negative eigenvalue */
+  int spans_projected;  /* spans whose Hessian had a negative eigenvalue
+                           (BSC_PROJECT_SPAN; 0 otherwise) */
 } bsc_newton_report;
 
 typedef struct bsc_ctx bsc_ctx;
@@ -152,12 +166,12 @@ bsc_status bsc_energy(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, dou
 bsc_status bsc_gradient(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, void* g_dev);
 
 /* Global Hessian of E(C): sum over spans of the 27x27 span Hessian (projected
- * to PSD when project != 0: V max(Lambda, 0) V^T of the span's summed
- * membrane + bending Hessian, computed in FP64), gathered into the 5x5 block
+ * to PSD per project, one of BSC_PROJECT_*), gathered into the 5x5 block
  * stencil in a fixed order without atomics, plus m/dt^2 I on the diagonal;
  * rows and columns of pinned control points are replaced by the identity.
  * K_dev: device, 225 planes of N (T), or NULL to keep K inside the context.
- * The context remembers the matrix for bsc_spmv / bsc_solve. */
+ * The context remembers the matrix for bsc_spmv / bsc_solve.  A project
+ * value outside BSC_PROJECT_* returns BSC_ERR_INVALID_ARG. */
 bsc_status bsc_assemble_hessian(bsc_ctx* ctx, const void* C_dev, int project, void* K_dev);
 
 /* y = K x with K_dev (NULL = the last matrix assembled by this context).
@@ -356,7 +370,7 @@ bsc_status bsc_solve_fcg(bsc_ctx* ctx, bsc_cnn* cnn, const void* K_dev, const vo
 
 /* Per-span results of the last evaluation path: E_span (device, Nsp doubles),
  * g_span (device, Nsp x 27 T, row-major [span][3*l + c]) and H_span (device,
- * Nsp x 27 x 27 T, row-major) at C, projected when project != 0.  Span
+ * Nsp x 27 x 27 T, row-major) at C, projected per project (BSC_PROJECT_*).  Span
  * s = b*(nu-2) + a; local control point l = lj*3 + li.  Any output may be
  * NULL. */
 bsc_status bsc_span_terms(bsc_ctx* ctx, const void* C_dev, int project, double* E_span,

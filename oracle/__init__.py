@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bsc_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
-RULE_REDUCED, RULE_GAUSS2, RULE_GAUSS3 = 0, 2, 3
+RULE_REDUCED, RULE_GAUSS2, RULE_GAUSS3, RULE_STANDARD = 0, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -64,6 +64,8 @@ def lib():
         _lib.or_basis9.argtypes = [P, ct.c_double, ct.c_double, I, I, D]
         _lib.or_lumped_mass.argtypes = [P, D]
         _lib.or_span_eval.argtypes = [P, D, D, D, D]
+        _lib.or_span_eval_projected.argtypes = [P, D, ct.c_int, D, D, D]
+        _lib.or_fbw_hessian6.argtypes = [P, D, I, D]
         _lib.or_span_terms_subset.argtypes = [P, D, I, ct.POINTER(I), I, D, D, D]
         _lib.or_eval_rows.argtypes = [P, S, D, D, I, ct.POINTER(I), D, D]
         _lib.or_project_psd.argtypes = [I, D, D, D]
@@ -144,15 +146,44 @@ class Problem:
         lib().or_span_eval(ct.byref(self._p), _dp(C), _dp(E), _dp(g), _dp(H))
         return E, g, H
 
+    def fbw_hessian6(self, f1, f2, point_project=False):
+        """6x6 d^2 Psi / d(f_1, f_2)^2 of the FBW density with this problem's
+        material; with point_project each term's Hessian is projected first."""
+        f6 = np.ascontiguousarray(np.concatenate([_f64(f1).ravel(), _f64(f2).ravel()]))
+        A6 = np.zeros((6, 6))
+        lib().or_fbw_hessian6(ct.byref(self._p), _dp(f6), int(bool(point_project)), _dp(A6))
+        return A6
+
+    def span_eval_projected(self, C, project, want_g=True, want_H=True):
+        """span_eval with the Hessians projected per project (see _project_mode)."""
+        C = _f64(C).reshape(self.n_cp, 3)
+        E = np.zeros(self.n_spans)
+        g = np.zeros((self.n_spans, 27)) if want_g else None
+        H = np.zeros((self.n_spans, 27, 27)) if want_H else None
+        lib().or_span_eval_projected(ct.byref(self._p), _dp(C), _project_mode(project), _dp(E), _dp(g), _dp(H))
+        return E, g, H
+
+
+PROJECT_NONE, PROJECT_SPAN, PROJECT_POINT = 0, 1, 2
+
+
+def _project_mode(project):
+    """True/False or one of PROJECT_*: True means the per-span projection."""
+    if project is True or project is False:
+        return int(project)
+    if project not in (PROJECT_NONE, PROJECT_SPAN, PROJECT_POINT):
+        raise ValueError(f"project must be a bool or one of PROJECT_*, got {project!r}")
+    return int(project)
+
 
 def span_terms_subset(prob, C, spans, project=True):
-    """E, g, H (projected when project) of the selected spans only."""
+    """E, g, H (projected per project, see _project_mode) of the selected spans only."""
     C = _f64(C).reshape(prob.n_cp, 3)
     sp = np.ascontiguousarray(np.asarray(spans, dtype=np.int32))
     n = sp.size
     E, g, H = np.zeros(n), np.zeros((n, 27)), np.zeros((n, 27, 27))
     lib().or_span_terms_subset(ct.byref(prob._p), _dp(C), n, sp.ctypes.data_as(ct.POINTER(ct.c_int)),
-                               int(bool(project)), _dp(E), _dp(g), _dp(H))
+                               _project_mode(project), _dp(E), _dp(g), _dp(H))
     return E, g, H
 
 
@@ -173,7 +204,7 @@ class Scene:
         self.pinned = np.ascontiguousarray(np.asarray(pinned, dtype=np.int32).ravel())
         self._s = _Scene(float(dt), (ct.c_double * 3)(*gravity),
                          self.pinned.ctypes.data_as(ct.POINTER(ct.c_int)), int(self.pinned.size),
-                         int(bool(project)))
+                         _project_mode(project))
 
     @classmethod
     def from_patch(cls, patch, project=True, static=False):

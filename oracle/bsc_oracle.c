@@ -23,7 +23,11 @@
  *      boundary, 2 along it (Fig. 3 red / blue reference cells);
  *   R6 lumped mass integrates rho * N_alpha with 3x3 Gauss per span;
  *   R7 projection clamps the eigenvalues of each span's summed 27x27
- *      elastic Hessian at zero;
+ *      elastic Hessian at zero (OR_PROJECT_SPAN); the per-point variant
+ *      (OR_PROJECT_POINT) clamps, at every membrane point, the eigenvalues
+ *      of each FBW term's own Hessian w.r.t. (f_1, f_2) separately (the two
+ *      stretch terms and the shear term), then applies the chain rule; the
+ *      bending Hessian is PSD by construction and is kept;
  *   R8 Dirichlet control points are eliminated: zero rows/columns, identity
  *      diagonal block, zero gradient;
  *   R9 line search accepts plain decrease E(C + alpha d) <= E(C).
@@ -175,6 +179,12 @@ static void build_rule(const or_problem* p, int which, qlist* L) {
       else
         qpush(L, a + 0.5, b + 0.5, 1.0, a, b); /* span centre */
     }
+  if (rule == OR_RULE_STANDARD) {
+    /* Sec. 6.5 case A: standard 2x2 Gauss on every interior span */
+    for (int b = 1; b < Sv - 1; ++b)
+      for (int a = 1; a < Su - 1; ++a) push_gauss_span(L, a, b, 2, 2);
+    return;
+  }
   /* Interior region [1, Su-1] x [1, Sv-1]: dual-grid cells centred on knots
    * (k_u, k_v), edges at k +- 1/2, clipped to the region. */
   double d = 0.5 / sqrt(3.0);
@@ -350,9 +360,53 @@ static void gather9(const or_problem* p, const double* C, int a, int b, double C
   }
 }
 
-/* Adds W * Psi_membrane and its derivatives w.r.t. the 27 span DOFs. */
+/* Adds the PSD projection of the symmetric 6x6 T to A (both row-major). */
+static void add_projected6(const double* T, double* A) {
+  double P[36];
+  or_project_psd(6, T, P, NULL);
+  for (int i = 0; i < 36; ++i) A[i] += P[i];
+}
+
+/* d^2 Psi / df_beta,c df_delta,d of the FBW density (row/column index
+ * 3 beta + c) as the sum of the three terms' Hessians, each projected to PSD
+ * first when ptproj. */
+static void fbw_hessian6(const or_problem* p, double f[2][3], int ptproj, double* A6) {
+  double I5a = f[0][0] * f[0][0] + f[0][1] * f[0][1] + f[0][2] * f[0][2];
+  double I5b = f[1][0] * f[1][0] + f[1][1] * f[1][1] + f[1][2] * f[1][2];
+  double I6 = f[0][0] * f[1][0] + f[0][1] * f[1][1] + f[0][2] * f[1][2];
+  double s1 = sqrt(I5a), s2 = sqrt(I5b);
+  double Hst1[6][6], Hst2[6][6], Hsh[6][6];
+  memset(Hst1, 0, sizeof(Hst1));
+  memset(Hst2, 0, sizeof(Hst2));
+  for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d) {
+      double del = (c == d) ? 1.0 : 0.0;
+      Hst1[c][d] = 2.0 * p->mu_st1 * ((1.0 - 1.0 / s1) * del + f[0][c] * f[0][d] / (s1 * s1 * s1));
+      Hst2[3 + c][3 + d] = 2.0 * p->mu_st2 * ((1.0 - 1.0 / s2) * del + f[1][c] * f[1][d] / (s2 * s2 * s2));
+      Hsh[c][d] = 2.0 * p->mu_sh * f[1][c] * f[1][d];
+      Hsh[3 + c][3 + d] = 2.0 * p->mu_sh * f[0][c] * f[0][d];
+      Hsh[c][3 + d] = 2.0 * p->mu_sh * (f[1][c] * f[0][d] + I6 * del);
+      Hsh[3 + c][d] = 2.0 * p->mu_sh * (f[0][c] * f[1][d] + I6 * del);
+    }
+  memset(A6, 0, sizeof(double) * 36);
+  if (ptproj) {
+    add_projected6(&Hst1[0][0], A6);
+    add_projected6(&Hst2[0][0], A6);
+    add_projected6(&Hsh[0][0], A6);
+  } else {
+    for (int i = 0; i < 36; ++i) A6[i] = (&Hst1[0][0])[i] + (&Hst2[0][0])[i] + (&Hsh[0][0])[i];
+  }
+}
+
+void or_fbw_hessian6(const or_problem* p, const double* f6, int ptproj, double* A6) {
+  double f[2][3] = {{f6[0], f6[1], f6[2]}, {f6[3], f6[4], f6[5]}};
+  fbw_hessian6(p, f, ptproj, A6);
+}
+
+/* Adds W * Psi_membrane and its derivatives w.r.t. the 27 span DOFs.  With
+ * ptproj the Hessian of each FBW term is projected before the chain rule. */
 static void membrane_point(const or_problem* p, const pgeom* G, double W, double Cl[9][3],
-                           double* E, double* g27, double* H27) {
+                           double* E, double* g27, double* H27, int ptproj) {
   double f[2][3] = {{0, 0, 0}, {0, 0, 0}}; /* f_beta = F e_beta */
   for (int beta = 0; beta < 2; ++beta)
     for (int c = 0; c < 3; ++c)
@@ -375,18 +429,13 @@ static void membrane_point(const or_problem* p, const pgeom* G, double W, double
       for (int c = 0; c < 3; ++c)
         g27[3 * l + c] += W * (G->g[l][0] * dP[0][c] + G->g[l][1] * dP[1][c]);
   if (!H27) return;
-  /* d^2 Psi / df_beta,c df_delta,d */
+  double A6[36];
+  fbw_hessian6(p, f, ptproj, A6);
   double A[2][3][2][3];
-  for (int c = 0; c < 3; ++c)
-    for (int d = 0; d < 3; ++d) {
-      double del = (c == d) ? 1.0 : 0.0;
-      A[0][c][0][d] = 2.0 * p->mu_st1 * ((1.0 - 1.0 / s1) * del + f[0][c] * f[0][d] / (s1 * s1 * s1)) +
-                      2.0 * p->mu_sh * f[1][c] * f[1][d];
-      A[1][c][1][d] = 2.0 * p->mu_st2 * ((1.0 - 1.0 / s2) * del + f[1][c] * f[1][d] / (s2 * s2 * s2)) +
-                      2.0 * p->mu_sh * f[0][c] * f[0][d];
-      A[0][c][1][d] = 2.0 * p->mu_sh * (f[1][c] * f[0][d] + I6 * del);
-      A[1][c][0][d] = 2.0 * p->mu_sh * (f[0][c] * f[1][d] + I6 * del);
-    }
+  for (int be = 0; be < 2; ++be)
+    for (int c = 0; c < 3; ++c)
+      for (int de = 0; de < 2; ++de)
+        for (int d = 0; d < 3; ++d) A[be][c][de][d] = A6[(3 * be + c) * 6 + 3 * de + d];
   /* chain rule: H_(l c)(m d) = sum_{beta, delta} g_l,beta g_m,delta A */
   for (int l = 0; l < 9; ++l)
     for (int c = 0; c < 3; ++c)
@@ -415,8 +464,8 @@ static void bending_point(const or_problem* p, const pgeom* G, double W, double 
         for (int c = 0; c < 3; ++c) H27[(3 * l + c) * 27 + 3 * m + c] += W * p->mu_bd * G->L[l] * G->L[m];
 }
 
-void or_span_eval(const or_problem* p, const double* C, double* E_span, double* g_span,
-                  double* H_span) {
+static void span_eval_impl(const or_problem* p, const double* C, int ptproj, double* E_span, double* g_span,
+                           double* H_span) {
   int Su = p->nu - 2, Sv = p->nv - 2, Nsp = Su * Sv;
   double* E = (double*)calloc((size_t)Nsp, sizeof(double));
   if (g_span) memset(g_span, 0, sizeof(double) * 27 * (size_t)Nsp);
@@ -435,7 +484,7 @@ void or_span_eval(const or_problem* p, const double* C, double* E_span, double* 
       double* g27 = g_span ? g_span + 27 * (size_t)s : NULL;
       double* H27 = H_span ? H_span + 729 * (size_t)s : NULL;
       if (which == 0)
-        membrane_point(p, &G, W, Cl, &E[s], g27, H27);
+        membrane_point(p, &G, W, Cl, &E[s], g27, H27, ptproj);
       else
         bending_point(p, &G, W, Cl, &E[s], g27, H27);
     }
@@ -443,6 +492,24 @@ void or_span_eval(const or_problem* p, const double* C, double* E_span, double* 
   }
   if (E_span) memcpy(E_span, E, sizeof(double) * (size_t)Nsp);
   free(E);
+}
+
+void or_span_eval(const or_problem* p, const double* C, double* E_span, double* g_span,
+                  double* H_span) {
+  span_eval_impl(p, C, 0, E_span, g_span, H_span);
+}
+
+void or_span_eval_projected(const or_problem* p, const double* C, int project, double* E_span,
+                            double* g_span, double* H_span) {
+  int Nsp = (p->nu - 2) * (p->nv - 2);
+  span_eval_impl(p, C, project == OR_PROJECT_POINT, E_span, g_span, H_span);
+  if (project == OR_PROJECT_SPAN && H_span) {
+    double P[729];
+    for (int s = 0; s < Nsp; ++s) {
+      or_project_psd(27, H_span + 729 * (size_t)s, P, NULL);
+      memcpy(H_span + 729 * (size_t)s, P, sizeof(P));
+    }
+  }
 }
 
 /* Selected spans only: points are enumerated as in or_span_eval and those
@@ -469,13 +536,14 @@ void or_span_terms_subset(const or_problem* p, const double* C, int n, const int
       double Cl[9][3];
       gather9(p, C, q->a, q->b, Cl);
       if (which == 0)
-        membrane_point(p, &G, W, Cl, &E[j], g + 27 * (size_t)j, H + 729 * (size_t)j);
+        membrane_point(p, &G, W, Cl, &E[j], g + 27 * (size_t)j, H + 729 * (size_t)j,
+                       project == OR_PROJECT_POINT);
       else
         bending_point(p, &G, W, Cl, &E[j], g + 27 * (size_t)j, H + 729 * (size_t)j);
     }
     free(L.pts);
   }
-  if (project) {
+  if (project == OR_PROJECT_SPAN) {
     double P[729];
     for (int j = 0; j < n; ++j) {
       or_project_psd(27, H + 729 * (size_t)j, P, NULL);
@@ -560,7 +628,7 @@ static double eval_impl(const or_problem* p, const or_scene* sc, const double* C
   double* E_s = (double*)malloc(sizeof(double) * Nsp);
   double* g_s = grad ? (double*)malloc(sizeof(double) * 27 * (size_t)Nsp) : NULL;
   double* H_s = K ? (double*)malloc(sizeof(double) * 729 * (size_t)Nsp) : NULL;
-  or_span_eval(p, C, E_s, g_s, H_s);
+  span_eval_impl(p, C, sc->project == OR_PROJECT_POINT, E_s, g_s, H_s);
   double* m = (double*)malloc(sizeof(double) * N);
   or_lumped_mass(p, m);
 
@@ -572,7 +640,7 @@ static double eval_impl(const or_problem* p, const or_scene* sc, const double* C
   for (int s = 0; s < Nsp; ++s) {
     int a = s % Su, b = s / Su;
     if (K) {
-      if (sc->project)
+      if (sc->project == OR_PROJECT_SPAN)
         or_project_psd(27, H_s + 729 * (size_t)s, P, NULL);
       else
         memcpy(P, H_s + 729 * (size_t)s, sizeof(P));

@@ -22,7 +22,11 @@
 extern "C" {
 #endif
 
-enum { OR_RULE_REDUCED = 0, OR_RULE_GAUSS2 = 2, OR_RULE_GAUSS3 = 3 };
+/* Quadrature rules: the reduced rules of Sec. 4.1 / 4.2 (Fig. 3); 2x2 or
+ * 3x3 Gauss on every span; or the ablation baseline of Sec. 6.5 (case A):
+ * 2x2 Gauss on interior spans for both energies, the reduced rules'
+ * placements on the boundary spans. */
+enum { OR_RULE_REDUCED = 0, OR_RULE_GAUSS2 = 2, OR_RULE_GAUSS3 = 3, OR_RULE_STANDARD = 4 };
 
 typedef struct {
   int nu, nv;
@@ -36,8 +40,14 @@ typedef struct {
   double gravity[3];
   const int* pinned;    /* control-point indices fixed by Dirichlet conditions */
   int n_pinned;
-  int project;          /* 1: per-span PSD projection of the elastic Hessian */
+  int project;          /* OR_PROJECT_*: PSD projection of the elastic Hessian */
 } or_scene;
+
+/* Projection of the elastic Hessian (projected Newton, Sec. 5.1): none; per
+ * span (eigenvalues of the summed 27x27 span Hessian clamped at 0); or per
+ * membrane point and FBW term (Sec. 4.1: each stretch term's and the shear
+ * term's Hessian w.r.t. (f_1, f_2) clamped separately before the chain rule). */
+enum { OR_PROJECT_NONE = 0, OR_PROJECT_SPAN = 1, OR_PROJECT_POINT = 2 };
 
 /* Quadrature points (Sec. 4.1 reduced membrane rule, Sec. 4.2 one-point
  * bending rule, Fig. 3).  which = 0 membrane, 1 bending.  Record layout:
@@ -63,8 +73,18 @@ void or_lumped_mass(const or_problem* p, double* m);
 void or_span_eval(const or_problem* p, const double* C, double* E_span,
                   double* g_span, double* H_span);
 
+/* d^2 Psi / d f d f of the FBW density at one point (Sec. 4.1), f6 = (f_1,
+ * f_2), A6 row-major 6x6 with index 3 beta + c, with the material of p; with
+ * ptproj each term's Hessian is projected to PSD before they are summed. */
+void or_fbw_hessian6(const or_problem* p, const double* f6, int ptproj, double* A6);
+
+/* or_span_eval with the Hessian projected per project (OR_PROJECT_*). */
+void or_span_eval_projected(const or_problem* p, const double* C, int project, double* E_span,
+                            double* g_span, double* H_span);
+
 /* Span terms of selected spans only (same definitions as or_span_eval):
- * E[n], g[n][27], H[n][27][27] for spans[0..n); H projected when project. */
+ * E[n], g[n][27], H[n][27][27] for spans[0..n); H projected per project
+ * (OR_PROJECT_*). */
 void or_span_terms_subset(const or_problem* p, const double* C, int n, const int* spans, int project,
                           double* E, double* g, double* H);
 

@@ -20,7 +20,17 @@ LIB_PATH = os.path.join(_HERE, "libbsc.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_NOT_CONVERGED, ERR_LINESEARCH, ERR_TIMEOUT = range(8)
 FP64, FP32 = 0, 1
-QUAD_REDUCED, QUAD_GAUSS2, QUAD_GAUSS3 = 0, 2, 3
+QUAD_REDUCED, QUAD_GAUSS2, QUAD_GAUSS3, QUAD_STANDARD = 0, 2, 3, 4
+PROJECT_NONE, PROJECT_SPAN, PROJECT_POINT = 0, 1, 2
+
+
+def _project(project):
+    """True / False (per-span projection or none) or one of PROJECT_*."""
+    if project is True or project is False:
+        return int(project)
+    if project not in (PROJECT_NONE, PROJECT_SPAN, PROJECT_POINT):
+        raise ValueError(f"project must be a bool or one of PROJECT_*, got {project!r}")
+    return int(project)
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5: "NOT_CONVERGED",
                 6: "LINESEARCH", 7: "TIMEOUT"}
@@ -216,7 +226,7 @@ class Context:
             self._opts[p] = Options(precision, float(sp.get("dt", 0.01)),
                                     (ct.c_double * 3)(*sp.get("gravity", (0.0, -9.81, 0.0))),
                                     pins.ctypes.data_as(ct.POINTER(ct.c_int32)), int(pins.size),
-                                    int(bool(project)), float(pcg_rel_tol), int(pcg_max_iter), int(max_line_search))
+                                    _project(project), float(pcg_rel_tol), int(pcg_max_iter), int(max_line_search))
         self._quad = Quadrature(*quadrature)
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
@@ -280,10 +290,10 @@ class Context:
 
     def assemble_hessian(self, C, project=True, out=None, internal=False):
         if internal:
-            self._check(self._lib.bsc_assemble_hessian(self._h, _ptr(self._vec(C, "C")), int(bool(project)), None))
+            self._check(self._lib.bsc_assemble_hessian(self._h, _ptr(self._vec(C, "C")), _project(project), None))
             return None
         out = self.new_matrix() if out is None else out
-        self._check(self._lib.bsc_assemble_hessian(self._h, _ptr(self._vec(C, "C")), int(bool(project)),
+        self._check(self._lib.bsc_assemble_hessian(self._h, _ptr(self._vec(C, "C")), _project(project),
                                                    _ptr(out)))
         return out
 
@@ -322,7 +332,7 @@ class Context:
         E = t.zeros(self.n_spans, dtype=t.float64, device="cuda")
         g = t.zeros((self.n_spans, 27), dtype=self.dtype, device="cuda")
         H = t.zeros((self.n_spans, 27, 27), dtype=self.dtype, device="cuda")
-        self._check(self._lib.bsc_span_terms(self._h, _ptr(self._vec(C, "C")), int(bool(project)), _ptr(E),
+        self._check(self._lib.bsc_span_terms(self._h, _ptr(self._vec(C, "C")), _project(project), _ptr(E),
                                              _ptr(g), _ptr(H)))
         return E, g, H
 

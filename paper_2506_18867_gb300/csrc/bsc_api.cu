@@ -105,8 +105,10 @@ void mark(bsc_ctx* c, int k) {
 }
 
 bsc_status eval_path(bsc_ctx* c, const void* C, int want_grad, int want_hess, int project) {
-  CK(launch_span_eval(c, C, want_grad, want_hess), "span evaluation");
-  if (want_hess && project) CK(launch_project(c), "SPD projection");
+  if (project < BSC_PROJECT_NONE || project > BSC_PROJECT_POINT)
+    return fail(c, BSC_ERR_INVALID_ARG, "project must be one of BSC_PROJECT_* (got %d)", project);
+  CK(launch_span_eval(c, C, want_grad, hess_mode(want_hess, project)), "span evaluation");
+  if (want_hess && project == BSC_PROJECT_SPAN) CK(launch_project(c), "SPD projection");
   return BSC_OK;
 }
 
@@ -139,6 +141,8 @@ bsc_status validate_patch(int p, const bsc_knot_grid* g, const double* rest_xy, 
   for (int k = 0; k < 2 * N; ++k)
     if (!isfinite(rest_xy[k]))
       return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: rest_xy has a non-finite value (patch %d)", p);
+  if (o->project < BSC_PROJECT_NONE || o->project > BSC_PROJECT_POINT)
+    return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: project must be one of BSC_PROJECT_* (patch %d)", p);
   if (o->n_pinned < 0 || (o->n_pinned > 0 && !o->pinned))
     return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: bad pinned list (patch %d)", p);
   for (int k = 0; k < o->n_pinned; ++k)
@@ -157,9 +161,9 @@ cudaError_t enqueue_newton(bsc_ctx* c, void* C, const void* Chat) {
   cudaError_t e;
   void *d = c->vec[0], *g = c->vec[5], *trial = c->vec[6], *rhs = c->vec[7];
   mark(c, 0);
-  if ((e = launch_span_eval(c, C, 1, 1)) != cudaSuccess) return e;
+  if ((e = launch_span_eval(c, C, 1, hess_mode(1, c->project_default))) != cudaSuccess) return e;
   mark(c, 1);
-  if (c->project_default && (e = launch_project(c)) != cudaSuccess) return e;
+  if (c->project_default == BSC_PROJECT_SPAN && (e = launch_project(c)) != cudaSuccess) return e;
   mark(c, 2);
   if ((e = launch_patch_energy(c, C, Chat, c->patch_E)) != cudaSuccess) return e;
   if ((e = launch_gradient(c, C, Chat, g)) != cudaSuccess) return e;
@@ -239,7 +243,7 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
   if (Ntot > (1ll << 26)) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: too many control points in total");
   const int mem_rule = q ? q->membrane : BSC_QUAD_REDUCED, bend_rule = q ? q->bending : BSC_QUAD_REDUCED;
   for (int r : {mem_rule, bend_rule})
-    if (r != BSC_QUAD_REDUCED && r != BSC_QUAD_GAUSS2 && r != BSC_QUAD_GAUSS3)
+    if (r != BSC_QUAD_REDUCED && r != BSC_QUAD_GAUSS2 && r != BSC_QUAD_GAUSS3 && r != BSC_QUAD_STANDARD)
       return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: unknown quadrature rule %d", r);
   const bsc_options* o = &opts[0];
   if (o->precision != BSC_FP64 && o->precision != BSC_FP32)

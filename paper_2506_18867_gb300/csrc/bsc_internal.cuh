@@ -195,6 +195,11 @@ cudaError_t launch_lumped_mass_patch(bsc_ctx* c, int p);
 cudaError_t build_span_items(bsc_ctx* c);
 cudaError_t build_red_items(bsc_ctx* c);
 cudaError_t setup_span_eval(bsc_ctx* c);
+// want_hess of launch_span_eval: 0 no Hessian, 1 the Hessian as it is, 2 with
+// the per-point closed-form projection of the FBW terms (BSC_PROJECT_POINT)
+inline int hess_mode(int want_hess, int project) {
+  return want_hess ? (project == BSC_PROJECT_POINT ? 2 : 1) : 0;
+}
 // energy / gradient / Hessian of every span; with a gate, only the spans of
 // the patches whose line search is pending (gate[p].state == 1)
 cudaError_t launch_span_eval(bsc_ctx* c, const void* C, int want_grad, int want_hess,

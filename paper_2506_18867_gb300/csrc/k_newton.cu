@@ -143,7 +143,7 @@ cudaError_t launch_step_begin(bsc_ctx* c, const void* d) {
     k_step_items<float><<<c->n_red_items, SB, 0, c->stream>>>(c->N, c->n_red_items, c->red_items, c->pd, c->nneg,
                                                               (const float*)d, c->partials);
   k_step_begin<<<c->P, SB, 0, c->stream>>>(c->n_red_items, c->red_off, c->partials, c->patch_E, c->pcg_out,
-                                           c->project_default, c->steps, c->dstatus);
+                                           c->project_default == BSC_PROJECT_SPAN, c->steps, c->dstatus);
   return cudaGetLastError();
 }
 

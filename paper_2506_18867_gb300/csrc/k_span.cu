@@ -15,8 +15,10 @@
 // A block evaluates 32 spans (one per lane) with 8 warps, each warp a slice
 // of every span's work.  Phase 1 evaluates the quadrature points (slice k
 // takes the span's points k and k + 8): energy, weighted dPsi/df, the
-// weighted 6x6 d^2 Psi/df^2 (also kept in global memory for the FP64
-// projection) and the point's derivative vectors go to shared memory.
+// weighted 6x6 d^2 Psi/df^2 (also kept in global memory for the FP64 span
+// projection; under the per-point projection each FBW term's part is
+// projected in closed form first, see membrane_hessian6) and the point's
+// derivative vectors go to shared memory.
 // Phase 2 sums them into the span terms: slice w owns the 3x3 blocks
 // (l <= m) w, w + 8, ... of the Hessian (five or six of the 45) and
 // gradient row w (slice 7 also row 8), accumulated in registers, so every
@@ -109,7 +111,82 @@ __device__ __forceinline__ void block_lm(int b, int& l, int& m) {
   m = l + rem;
 }
 
-template <typename T, bool GRAD, bool HESS>
+// Weighted 6x6 d^2 Psi / d f_(b c) d f_(d e) of one membrane point (index
+// 3 b + c), either as it is or, with PP, with each FBW term's Hessian
+// replaced by its PSD projection (BSC_PROJECT_POINT).  k_b = 2 mu_b (1 - r_b)
+// and ks = 2 mu_sh I6 are the gradient coefficients, r_b = 1 / |f_b|.
+//
+// Stretch term b, 2 mu_b [(1 - r) I + r^3 f f^T]: eigenvalue 2 mu_b along f
+// and 2 mu_b (1 - r) twice across it; when |f| < 1 the second is clamped to
+// 0, which leaves 2 mu_b r^2 f f^T.
+//
+// Shear term, 2 mu_sh [g g^T + I6 A] with g = (f_2; f_1) and A = [0 I; I 0].
+// A is +1 on the vectors (x; x) and -1 on (x; -x); u = f_1 + f_2 and
+// w = f_2 - f_1 are the parts of g in the two halves (|g_+|^2 = |u|^2 / 2,
+// |g_-|^2 = |w|^2 / 2, and |g_+|^2 - |g_-|^2 = 2 I6).  Hence the spectrum:
+//   +I6 on (x; x) with x perpendicular to u (two vectors),
+//   -I6 on (x; -x) with x perpendicular to w (two vectors),
+//   and the 2x2 block [[|g+|^2 + I6, |g+||g-|], [|g+||g-|, |g-|^2 - I6]] on
+//   span(g_+, g_-): trace I5a + I5b, determinant -3 I6^2, so one eigenvalue
+//   lam = (tr + sqrt(tr^2 + 12 I6^2)) / 2 >= 0 and one <= 0.
+// The projection keeps max(I6, 0) and max(-I6, 0) on the first two families
+// and lam v v^T with v = al g_+ + be g_- from the 2x2 eigenvector, written
+// without dividing by |g_+| or |g_-| (al, be >= 0 below).
+template <typename T, bool PP>
+__device__ __forceinline__ void membrane_hessian6(const T f[2][3], T I5a, T I5b, T I6, T r1, T r2, T k1, T k2,
+                                                  T ks, T mu1, T mu2, T mush, T W, T A6[6][6]) {
+  T c1 = T(2) * mu1 * r1 * r1 * r1, c2 = T(2) * mu2 * r2 * r2 * r2;
+  const T cs = T(2) * mush;
+  if (!PP) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T del = (c == d) ? T(1) : T(0);
+        A6[c][d] = W * (k1 * del + c1 * f[0][c] * f[0][d] + cs * f[1][c] * f[1][d]);
+        A6[3 + c][3 + d] = W * (k2 * del + c2 * f[1][c] * f[1][d] + cs * f[0][c] * f[0][d]);
+        A6[c][3 + d] = W * (cs * f[1][c] * f[0][d] + ks * del);
+        A6[3 + d][c] = A6[c][3 + d];
+      }
+    return;
+  }
+  if (r1 > T(1)) { k1 = T(0); c1 = T(2) * mu1 * r1 * r1; }
+  if (r2 > T(1)) { k2 = T(0); c2 = T(2) * mu2 * r2 * r2; }
+  T u[3], w[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    u[c] = f[0][c] + f[1][c];
+    w[c] = f[1][c] - f[0][c];
+  }
+  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2], ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  const T tr = I5a + I5b, sq = sqrt(tr * tr + T(12) * I6 * I6), lam = T(0.5) * (tr + sq);
+  const bool pos = I6 >= T(0);
+  const T al = pos ? T(2) * I6 + T(0.5) * sq : T(0.5) * ww;
+  const T be = pos ? T(0.5) * uu : T(0.5) * sq - T(2) * I6;
+  const T vv = T(0.5) * (al * al * uu + be * be * ww);  // |v|^2
+  const T kv = vv > T(0) ? lam / vv : T(0);
+  const T sp = pos ? I6 : T(0), sm = pos ? T(0) : -I6;
+  const T iu = sp > T(0) ? T(1) / uu : T(0), iw = sm > T(0) ? T(1) / ww : T(0);
+  T pv[3], qv[3];  // v = (p; q)
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    pv[c] = T(0.5) * (al * u[c] + be * w[c]);
+    qv[c] = T(0.5) * (al * u[c] - be * w[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T del = (c == d) ? T(1) : T(0);
+      const T Pu = T(0.5) * sp * (del - u[c] * u[d] * iu), Pw = T(0.5) * sm * (del - w[c] * w[d] * iw);
+      A6[c][d] = W * (k1 * del + c1 * f[0][c] * f[0][d] + cs * (kv * pv[c] * pv[d] + Pu + Pw));
+      A6[3 + c][3 + d] = W * (k2 * del + c2 * f[1][c] * f[1][d] + cs * (kv * qv[c] * qv[d] + Pu + Pw));
+      A6[c][3 + d] = W * cs * (kv * pv[c] * qv[d] + Pu - Pw);
+      A6[3 + d][c] = A6[c][3 + d];
+    }
+}
+
+template <typename T, bool GRAD, bool HESS, bool PP>
 __global__ void __launch_bounds__(EVAL_BLOCK, sizeof(T) == 4 ? 2 : 1)
     k_span_eval(SpanArgs<T> P, const __grid_constant__ CUtensorMap cmap) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -283,24 +360,14 @@ __global__ void __launch_bounds__(EVAL_BLOCK, sizeof(T) == 4 ? 2 : 1)
         if (HESS) {
           // weighted d^2 Psi / d f_(b c) d f_(d e), 6x6 with index 3 b + c
           T A6[6][6];
-          const T c1 = T(2) * mu1 * r1 * r1 * r1, c2 = T(2) * mu2 * r2 * r2 * r2, cs = T(2) * mush;
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              const T del = (c == d) ? T(1) : T(0);
-              A6[c][d] = W * (k1 * del + c1 * f[0][c] * f[0][d] + cs * f[1][c] * f[1][d]);
-              A6[3 + c][3 + d] = W * (k2 * del + c2 * f[1][c] * f[1][d] + cs * f[0][c] * f[0][d]);
-              A6[c][3 + d] = W * (cs * f[1][c] * f[0][d] + ks * del);
-              A6[3 + d][c] = A6[c][3 + d];
-            }
+          membrane_hessian6<T, PP>(f, I5a, I5b, I6, r1, r2, k1, k2, ks, mu1, mu2, mush, W, A6);
           int e = 0;
 #pragma unroll
           for (int r = 0; r < 6; ++r)
 #pragma unroll
             for (int c = r; c < 6; ++c, ++e) {
               SV(k, V_A + e) = A6[r][c];
-              P.A[(size_t)e * P.Nm + q] = A6[r][c];
+              if (!PP) P.A[(size_t)e * P.Nm + q] = A6[r][c];  // input of the span projection
             }
         }
       } else {
@@ -471,26 +538,32 @@ cudaError_t run(bsc_ctx* c, const void* C, int want_grad, int want_hess, const S
   CUtensorMap m;
   cudaError_t e = planes_map<T>(&m, C, c->N);
   if (e != cudaSuccess) return e;
-  if (want_hess)
-    k_span_eval<T, true, true><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
+  if (want_hess == 2)
+    k_span_eval<T, true, true, true><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
+  else if (want_hess)
+    k_span_eval<T, true, true, false><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
   else if (want_grad)
-    k_span_eval<T, true, false><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
+    k_span_eval<T, true, false, false><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
   else
-    k_span_eval<T, false, false><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
+    k_span_eval<T, false, false, false><<<n_items, EVAL_BLOCK, span_smem<T>(), c->stream>>>(P, m);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t set_smem() {
+  const int bytes = (int)span_smem<T>();
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_span_eval<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)span_smem<T>())) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_span_eval<T, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_span_eval<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)span_smem<T>())) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_span_eval<T, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(k_span_eval<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)span_smem<T>());
+  if ((e = cudaFuncSetAttribute(k_span_eval<T, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_span_eval<T, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
 }
 
 }  // namespace

@@ -82,6 +82,10 @@ __device__ int span_points(int a, int b, int Su, int Sv, int which, int rule, QP
     else out[n++] = QP{a + 0.5, b + 0.5, 1.0};
     return n;
   }
+  if (rule == BSC_QUAD_STANDARD) {  // ablation baseline: 2x2 Gauss per interior span
+    gauss_span(2, 2);
+    return n;
+  }
   // Interior span: candidate dual cells centred on knots (ku, kv) with
   // ku in {a, a+1}, kv in {b, b+1}; keep the points this span owns.  A point
   // on knot line k belongs to span clamp(k, 1, S-2); otherwise to floor.

@@ -162,7 +162,7 @@ def test_deterministic_bitwise(case):
     assert torch.equal(g1, ctx.gradient(C, ctx.to_device(pat.Chat)))
 
 
-@pytest.mark.parametrize("rule", [2, 3])
+@pytest.mark.parametrize("rule", [2, 3, 4])
 def test_full_gauss_rules(orc, rule):
     pat = inputs.config_random_small(8, 9, 11, noise=0.1)
     prob = orc.Problem.from_patch(pat, mem_rule=rule, bend_rule=rule)

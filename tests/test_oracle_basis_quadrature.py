@@ -202,6 +202,33 @@ def test_gauss_rules(orc):
     assert abs((loc2[:, 2] * loc2[:, 0] ** 3).sum() - 0.25) < 1e-14
 
 
+@pytest.mark.parametrize("nu,nv", [(5, 5), (7, 9), (12, 10)])
+def test_standard_rule_of_the_ablation(orc, nu, nv):
+    """Sec. 6.5 case A: 2x2 Gauss on every interior span for both energies,
+    the reduced rules' placements on the boundary spans."""
+    Su, Sv = nu - 2, nv - 2
+    red = _prob(orc, nu, nv)
+    std = _prob(orc, nu, nv, mem_rule=orc.RULE_STANDARD, bend_rule=orc.RULE_STANDARD)
+    for which in (0, 1):
+        qr, qs = red.quad_points(which), std.quad_points(which)
+        ring_r = (qr[:, 3] == 0) | (qr[:, 3] == Su - 1) | (qr[:, 4] == 0) | (qr[:, 4] == Sv - 1)
+        ring_s = (qs[:, 3] == 0) | (qs[:, 3] == Su - 1) | (qs[:, 4] == 0) | (qs[:, 4] == Sv - 1)
+        key = lambda q: sorted(tuple(round(float(x), 12) for x in row) for row in q[:, :5])  # noqa: E731
+        assert key(qs[ring_s]) == key(qr[ring_r])
+        inner = qs[~ring_s]
+        assert len(inner) == 4 * (Su - 2) * (Sv - 2)
+        assert abs(qs[:, 2].sum() - Su * Sv) < 1e-10
+        for a in range(1, Su - 1):
+            for b in range(1, Sv - 1):
+                loc = inner[(inner[:, 3] == a) & (inner[:, 4] == b)]
+                t, r = loc[:, 0] - a, loc[:, 1] - b
+                assert len(loc) == 4 and abs(loc[:, 2].sum() - 1.0) < 1e-14
+                # the 2-point rule integrates t^3 and t^3 r^3 exactly, not t^4
+                assert abs((loc[:, 2] * t ** 3).sum() - 0.25) < 1e-14
+                assert abs((loc[:, 2] * t ** 3 * r ** 3).sum() - 1 / 16) < 1e-14
+                assert abs((loc[:, 2] * t ** 4).sum() - 0.2) > 1e-3
+
+
 # ---------------------------------------------------------------- geometry
 
 def test_affine_rest_geometry(orc):

@@ -30,7 +30,7 @@ def _rot(rng):
     return q
 
 
-@pytest.mark.parametrize("rule", [0, 2, 3])
+@pytest.mark.parametrize("rule", [0, 2, 3, 4])
 def test_affine_deformation_exact_energy(orc, rule):
     """phi = A X + b is reproduced exactly; energy = Psi(A) * area for any rule."""
     rng = np.random.default_rng(3)

@@ -262,6 +262,10 @@ typedef struct bsc_tuning {
   int p2_variant;          /* phase 2 of the interior projection: 0 two, 1 three
                               resident blocks per SM (fewer registers; chosen by time) */
   double p2_ms[2];         /* measured ms of that phase per variant */
+  int pcg_grid_cand[4];    /* PCG grids tried: a block per two SMs, one and two
+                              per SM, a thread per control point (each clamped
+                              to [patches, usable blocks]) */
+  double pcg_ms[4];        /* measured ms of the solve per candidate (-1: duplicate) */
 } bsc_tuning;
 bsc_status bsc_autotune(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, bsc_tuning* out);
 
@@ -269,6 +273,13 @@ bsc_status bsc_autotune(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, b
  * are recomputed when the density changes).  Ordered on the context's
  * stream; synchronises it.  Captured Newton graphs stay valid. */
 bsc_status bsc_set_material(bsc_ctx* ctx, int patch, const bsc_material* m);
+
+/* Set the grid of the persistent PCG by hand: grid in [number of patches,
+ * usable blocks] (usable: the co-resident capacity, at most one block per 256
+ * control points of each patch; BSC_ERR_INVALID_ARG otherwise); the blocks
+ * are split over the patches by the current work estimates.  Results are
+ * independent of the grid up to the order of the FP64 reductions. */
+bsc_status bsc_set_pcg_grid(bsc_ctx* ctx, int grid);
 
 /* Set the tile widths by hand (4 entries, each 0, 8, 16 or 32). */
 bsc_status bsc_set_tiles(bsc_ctx* ctx, const int* tile_tu);

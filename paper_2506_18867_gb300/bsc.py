@@ -39,7 +39,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5:
 EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc_energy", "bsc_gradient",
            "bsc_assemble_hessian", "bsc_spmv", "bsc_solve", "bsc_newton_step", "bsc_create_batch",
            "bsc_batch_layout", "bsc_patch_reports", "bsc_patch_energies", "bsc_autotune", "bsc_set_tiles",
-           "bsc_set_border_path", "bsc_set_p2_variant", "bsc_set_material",
+           "bsc_set_border_path", "bsc_set_p2_variant", "bsc_set_pcg_grid", "bsc_set_material",
            "bsc_pcg_split", "bsc_plan_blocks", "bsc_set_graph", "bsc_graph_state", "bsc_span_terms",
            "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes", "bsc_set_profiling", "bsc_phase_times",
            "bsc_launch_count", "bsc_projection_stats", "bsc_solve_static", "bsc_cnn_param_count",
@@ -83,12 +83,13 @@ class NewtonReport(ct.Structure):
 class Tuning(ct.Structure):
     _fields_ = [("tile_tu", ct.c_int * 4), ("tile_ms", (ct.c_double * 4) * 4), ("pcg_grid", ct.c_int),
                 ("border_path", ct.c_int), ("border_ms", ct.c_double * 3), ("p2_variant", ct.c_int),
-                ("p2_ms", ct.c_double * 2)]
+                ("p2_ms", ct.c_double * 2), ("pcg_grid_cand", ct.c_int * 4), ("pcg_ms", ct.c_double * 4)]
 
     def as_dict(self):
         return {"tile_tu": list(self.tile_tu), "tile_ms": [list(r) for r in self.tile_ms],
                 "pcg_grid": self.pcg_grid, "border_path": self.border_path, "border_ms": list(self.border_ms),
-                "p2_variant": self.p2_variant, "p2_ms": list(self.p2_ms)}
+                "p2_variant": self.p2_variant, "p2_ms": list(self.p2_ms),
+                "pcg_grid_cand": list(self.pcg_grid_cand), "pcg_ms": list(self.pcg_ms)}
 
 
 class FcgReport(ct.Structure):
@@ -150,6 +151,7 @@ def load(path: str = LIB_PATH):
     lib.bsc_pcg_split.argtypes = [P, ct.POINTER(I)]
     lib.bsc_set_border_path.argtypes = [P, I]
     lib.bsc_set_p2_variant.argtypes = [P, I]
+    lib.bsc_set_pcg_grid.argtypes = [P, I]
     lib.bsc_set_material.argtypes = [P, I, ct.POINTER(Material)]
     lib.bsc_plan_blocks.argtypes = [I, ct.POINTER(I), ct.POINTER(D), I, ct.POINTER(I)]
     lib.bsc_set_graph.argtypes = [P, I]
@@ -412,6 +414,10 @@ class Context:
         """Occupancy variant (0 or 1) of the interior projection's eigenpair
         phase; both give bitwise the same result."""
         self._check(self._lib.bsc_set_p2_variant(self._h, int(variant)))
+
+    def set_pcg_grid(self, grid):
+        """Blocks of the persistent PCG, in [patches, usable blocks]."""
+        self._check(self._lib.bsc_set_pcg_grid(self._h, int(grid)))
 
     def pcg_split(self):
         out = (ct.c_int * self.P)()

@@ -368,7 +368,7 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
   CREATE_CK(build_red_items(c), "reduction items");
   CREATE_CK(setup_pcg(c), "PCG set-up (too many patches for the co-resident blocks?)");
   {
-    const size_t np = (size_t)std::max(std::max(c->red_grid, c->pcg_grid), 2 * c->n_red_items);
+    const size_t np = (size_t)std::max(std::max(c->red_grid, c->pcg_cap), 2 * c->n_red_items);
     ALLOC(c->partials, sizeof(double) * 4 * np);
   }
   CREATE_CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking), "graph stream");
@@ -685,6 +685,16 @@ bsc_status bsc_set_border_path(bsc_ctx* c, int path) {
   return BSC_OK;
 }
 
+bsc_status bsc_set_pcg_grid(bsc_ctx* c, int grid) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (grid < c->P || grid > c->pcg_need)
+    return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_pcg_grid: grid must be in [%d, %d]", c->P, c->pcg_need);
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_pcg_grid");
+  CK(set_pcg_grid(c, grid), "bsc_set_pcg_grid");
+  drop_graph(c);
+  return BSC_OK;
+}
+
 bsc_status bsc_pcg_split(const bsc_ctx* c, int* blocks) {
   if (!c || !blocks) return BSC_ERR_INVALID_ARG;
   std::vector<PcgBlock> tab(c->pcg_grid);
@@ -806,6 +816,40 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
     for (int p = 0; p < c->P; ++p) c->pcg_weight[p] = (double)c->hpd[p].N * std::max(1.0, hout[3 * p]);
     CK(assign_pcg_blocks(c), "bsc_autotune");
     c->K_last = c->K_int;
+    // grid of the persistent PCG: a block per two SMs, one or two per SM, or
+    // a thread per control point (at most the co-resident capacity), timed
+    const int cand[4] = {c->num_sms / 2, c->num_sms, 2 * c->num_sms, c->pcg_need};
+    cudaEvent_t a0, a1;
+    CK(cudaEventCreate(&a0), "bsc_autotune");
+    CK(cudaEventCreate(&a1), "bsc_autotune");
+    int best = -1;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+      int g = std::min(std::max(cand[k], c->P), c->pcg_need);
+      t.pcg_grid_cand[k] = g;
+      t.pcg_ms[k] = -1.0;
+      bool dup = false;
+      for (int j = 0; j < k; ++j) dup = dup || t.pcg_grid_cand[j] == g;
+      if (dup) continue;
+      e = set_pcg_grid(c, g);
+      float ms = 0.0f, best_rep = 1e30f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(a0, c->stream);
+        if (e == cudaSuccess) e = launch_pcg(c, c->K_int, rhs, x, c->pcg_tol, c->pcg_max_iter);
+        if (e == cudaSuccess) e = cudaEventRecord(a1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(a1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a0, a1);
+        if (rep > 0 && ms < best_rep) best_rep = ms;  // the first solve warms up
+      }
+      t.pcg_ms[k] = best_rep;
+      if (best < 0 || best_rep < t.pcg_ms[best]) best = k;
+    }
+    cudaEventDestroy(a0);
+    cudaEventDestroy(a1);
+    if (e == cudaSuccess && best >= 0) e = set_pcg_grid(c, t.pcg_grid_cand[best]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "bsc_autotune: timing the PCG grid");
+    st = check_status(c, "bsc_autotune: timing the PCG grid");
+    if (st != BSC_OK) return st;
   }
   t.pcg_grid = c->pcg_grid;
   if (out) *out = t;

@@ -152,6 +152,8 @@ struct bsc_ctx {
   double* dscalars;   // [16] device scalars
   double* hscalars;   // [16] pinned host scalars
   int pcg_grid;       // co-resident blocks of the persistent PCG
+  int pcg_cap;        // co-resident capacity (pcg_blocks and partials are sized for it)
+  int pcg_need;       // most blocks the patches can use (a thread per control point), <= pcg_cap
   PcgBlock* pcg_blocks;  // device [pcg_grid]
   double* pcg_out;    // device [3 P]: iterations, relative residual, ok
   double* pcg_weight; // host [P]: work estimate of each patch's solve (autotuned)
@@ -220,6 +222,8 @@ cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y);
 cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit);
 cudaError_t setup_pcg(bsc_ctx* c);
 cudaError_t assign_pcg_blocks(bsc_ctx* c);
+// Sets the PCG grid (clamped to [patches, capacity]) and re-plans the groups.
+cudaError_t set_pcg_grid(bsc_ctx* c, int grid);
 cudaError_t launch_axpy_trial(bsc_ctx* c, const void* C, const void* d, double alpha, void* out);
 cudaError_t launch_copy_vec(bsc_ctx* c, const void* src, void* dst);
 cudaError_t launch_export_span_terms(bsc_ctx* c, void* g_out, void* H_out);

@@ -347,12 +347,21 @@ cudaError_t setup_pcg(bsc_ctx* c) {
   if (c->P > cap) return cudaErrorInvalidConfiguration;
   long long need = 0;
   for (int p = 0; p < c->P; ++p) need += (c->hpd[p].N + PCG_BLOCK - 1) / PCG_BLOCK;
-  c->pcg_grid = (int)(need < cap ? need : cap);
+  c->pcg_cap = cap;
+  c->pcg_need = (int)(need < cap ? need : cap);
+  c->pcg_grid = c->pcg_need;
   c->pcg_weight = (double*)malloc(sizeof(double) * c->P);
   if (!c->pcg_weight) return cudaErrorMemoryAllocation;
   for (int p = 0; p < c->P; ++p) c->pcg_weight[p] = (double)c->hpd[p].N;
-  if ((e = cudaMalloc(&c->pcg_blocks, sizeof(PcgBlock) * c->pcg_grid)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->pcg_blocks, sizeof(PcgBlock) * cap)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->pcg_out, sizeof(double) * 3 * c->P)) != cudaSuccess) return e;
+  return assign_pcg_blocks(c);
+}
+
+cudaError_t set_pcg_grid(bsc_ctx* c, int grid) {
+  if (grid < c->P) grid = c->P;
+  if (grid > c->pcg_need) grid = c->pcg_need;
+  c->pcg_grid = grid;
   return assign_pcg_blocks(c);
 }
 

@@ -237,6 +237,26 @@ def test_autotune_choices(pair):
     assert torch.equal(outs[0], outs[1])
     batch.set_p2_variant(t["p2_variant"])
     batch.set_tiles((0, 0, 0, 0))
+    # PCG grid: the chosen candidate is the fastest measured one; every grid
+    # solves the same system to the same tolerance
+    ms = [m for m in t["pcg_ms"] if m >= 0]
+    assert t["pcg_grid"] in t["pcg_grid_cand"] and min(ms) == t["pcg_ms"][t["pcg_grid_cand"].index(t["pcg_grid"])]
+    K = batch.assemble_hessian(C, project=True)
+    b = -batch.gradient(C, Ch)
+    fp64 = batch.dtype == torch.float64
+    tol = 1e-10 if fp64 else 1e-6
+    sols = []
+    for gsz in sorted(set(t["pcg_grid_cand"])):
+        batch.set_pcg_grid(gsz)
+        assert sum(batch.pcg_split()) == gsz
+        x, it, rr = batch.solve(b, K=K, rel_tol=tol)
+        assert rr <= tol
+        sols.append(x.double().cpu())
+    for x in sols[1:]:
+        assert float((x - sols[0]).norm() / sols[0].norm()) < (1e-7 if fp64 else 1e-3)
+    with pytest.raises(bsc.BscError):
+        batch.set_pcg_grid(len(pats) - 1)
+    batch.set_pcg_grid(t["pcg_grid"])
 
 
 def test_batch64_workload(orc):

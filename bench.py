@@ -503,7 +503,7 @@ def measure_learned(bsc, np, seeds=(1_000_000, 1_000_001, 1_000_002, 1_000_003),
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the projection
 # phase per Newton step, from one metrics-only ncu capture of the drape bench
-# (profiles/k_project_drape256_fp32.md), keyed by the autotuner's border path and
+# (dram__bytes_* of every projection launch of one step), keyed by the autotuner's border path and
 # phase-2 variant and by a hash of the projection sources it was taken with.
 #   path 2, variant 0: ring<1> 3.8 + p1<5> 54.8 + p2<5,2> 150.9 + corr 180.3
 #                      + p2<8> 6.9 + corr 16.1 MB

@@ -77,6 +77,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched-garment sub-measurement")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner sub-measurement")
     p.add_argument("--no-point", action="store_true", help="skip the per-point projection sub-measurement")
+    p.add_argument("--no-sweep", action="store_true", help="skip the 1024x1024 precision sweep sub-measurement")
     return p.parse_args()
 
 
@@ -336,6 +337,9 @@ def run_gpu(args):
     learned = None
     if args.workload == "drape256" and not args.no_learned and prec == bsc.FP32 and rank == 0:
         learned = measure_learned(bsc, np)
+    sweep = None
+    if args.workload == "drape256" and not args.no_sweep and rank == 0:
+        sweep = measure_sweep(bsc, torch)
     point = None
     if len(pats) == 1 and not args.no_point and rank == 0:
         point = measure_point_projection(bsc, pats[0], prec, ctx, C0, Chat, K, args.warmup, ms_step, flush, stream,
@@ -396,6 +400,7 @@ def run_gpu(args):
             "batched": batched,
             "learned": learned,
             "point_projection": point,
+            "precision_sweep": sweep,
             "cpu_baseline": cpu,
             "clocks": clk,
         }
@@ -404,6 +409,61 @@ def run_gpu(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def hbm_peak_gbs():
+    """The measured copy bandwidth of the GB300s, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def measure_sweep(bsc, torch, n=1024, spmvs=50):
+    """The 1024 x 1024 wrinkle field (1,044,484 spans) in FP32 and FP64: energy,
+    gradient and the projected Hessian (span evaluation + FP64 projection +
+    assembly), one call each after a warm-up call, then 50 SpMVs with that K.
+    K (225 entries per control point) is far larger than L2, so every product
+    streams it from HBM; the algorithmic bytes of one product are K + x + y."""
+    pat = inputs.config_wrinkle(1, n)
+    peak, src = hbm_peak_gbs()
+    out = {"workload": f"wrinkle{n}", "spans": (n - 2) * (n - 2), "control_points": n * n, "spmvs": spmvs}
+    for prec, name in ((bsc.FP32, "fp32"), (bsc.FP64, "fp64")):
+        ctx = bsc.context_for_patch(pat, precision=prec, pcg_rel_tol=1e-8)
+        C, Ch = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+        ctx.energy(C, Ch)
+        ctx.gradient(C, Ch)
+        K = ctx.assemble_hessian(C, project=True)
+        x = torch.randn((3, ctx.N), dtype=ctx.dtype, device="cuda", generator=torch.Generator("cuda").manual_seed(9))
+        y = ctx.new_vec()
+        ctx.spmv(x, K=K, out=y)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record()
+        ctx.energy(C, Ch)
+        ev[1].record()
+        ctx.gradient(C, Ch, out=y)
+        ev[2].record()
+        ctx.assemble_hessian(C, project=True, out=K)
+        ev[3].record()
+        for _ in range(spmvs):
+            ctx.spmv(x, K=K, out=y)
+        ev[4].record()
+        ev[4].synchronize()
+        spmv_ms = ev[3].elapsed_time(ev[4]) / spmvs
+        tsz = 4 if prec == bsc.FP32 else 8
+        nbytes = ctx.N * tsz * (225 + 3 + 3)
+        gbs = nbytes / (spmv_ms * 1e-3) / 1e9
+        hess_ms = ev[2].elapsed_time(ev[3])
+        out[name] = {"energy_ms": ev[0].elapsed_time(ev[1]), "gradient_ms": ev[1].elapsed_time(ev[2]),
+                     "hessian_ms": hess_ms, "hessian_spans_per_s": out["spans"] / (hess_ms * 1e-3),
+                     "spmv_ms": spmv_ms, "spmv_bytes": nbytes, "spmv_gbs": gbs, "spmv_frac_of_hbm": gbs / peak}
+        ctx.close()
+        del K, x, y, C, Ch
+    out["hbm_peak_gbs"] = peak
+    out["hbm_peak_source"] = src
+    return out
 
 
 def newton_to_convergence(ctx, C, C0, Chat, dt, stream, torch, tol=1e-2, max_iter=30):

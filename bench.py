@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner sub-measurement")
     p.add_argument("--no-point", action="store_true", help="skip the per-point projection sub-measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the 1024x1024 precision sweep sub-measurement")
+    p.add_argument("--no-trajectory", action="store_true",
+                   help="skip the 20-time-step drape trajectories (mu_bd sweep, FP32 vs FP64)")
     return p.parse_args()
 
 
@@ -340,6 +342,9 @@ def run_gpu(args):
     sweep = None
     if args.workload == "drape256" and not args.no_sweep and rank == 0:
         sweep = measure_sweep(bsc, torch)
+    trajectory = None
+    if args.workload == "drape256" and not args.no_trajectory and rank == 0:
+        trajectory = measure_trajectories(bsc, torch)
     point = None
     if len(pats) == 1 and not args.no_point and rank == 0:
         point = measure_point_projection(bsc, pats[0], prec, ctx, C0, Chat, K, args.warmup, ms_step, flush, stream,
@@ -401,6 +406,7 @@ def run_gpu(args):
             "learned": learned,
             "point_projection": point,
             "precision_sweep": sweep,
+            "trajectories": trajectory,
             "cpu_baseline": cpu,
             "clocks": clk,
         }
@@ -463,6 +469,73 @@ def measure_sweep(bsc, torch, n=1024, spmvs=50):
         del K, x, y, C, Ch
     out["hbm_peak_gbs"] = peak
     out["hbm_peak_source"] = src
+    return out
+
+
+def drape_trajectory(bsc, torch, pat, prec, steps, tol=1e-2, max_newton=30):
+    """`steps` implicit-Euler time steps of the drape from rest velocity:
+    Chat = C + dt v, Newton iterations until ||d||_inf / dt < tol, then
+    v = (C - C_prev) / dt.  Device time of the whole trajectory (CUDA
+    events), Newton and PCG iteration counts, and the final positions."""
+    ctx = bsc.context_for_patch(pat, precision=prec, pcg_rel_tol=1e-8)
+    C = ctx.to_device(pat.C)
+    ctx.autotune(C, C)
+    v = torch.zeros_like(C)
+    C_prev, Chat = torch.empty_like(C), torch.empty_like(C)  # fixed buffers: the captured graph stays valid
+    newton, pcg, worst = 0, 0, 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # warm-up outside the timed region: the vector operations' first launches and the
+    # capture of the Newton graph on these buffers; then back to the initial state
+    C_prev.copy_(C)
+    torch.add(C, v, alpha=pat.dt, out=Chat)
+    ctx.newton_step(C, Chat)
+    torch.sub(C, C_prev, out=v)
+    v.div_(pat.dt)
+    C.copy_(C_prev)
+    v.zero_()
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(steps):
+        C_prev.copy_(C)
+        torch.add(C, v, alpha=pat.dt, out=Chat)
+        for _ in range(max_newton):
+            rep = ctx.newton_step(C, Chat)
+            newton += 1
+            pcg += rep.pcg_iters
+            if rep.status != 0 or rep.dir_inf / pat.dt < tol:
+                break
+        worst = max(worst, rep.dir_inf / pat.dt)
+        torch.sub(C, C_prev, out=v)
+        v.div_(pat.dt)
+    ev1.record()
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    final = C.double().cpu()
+    ctx.close()
+    return {"time_steps": steps, "newton_iterations": newton, "pcg_iterations": pcg, "ms": ms,
+            "ms_per_time_step": ms / steps, "ms_per_newton_iteration": ms / newton,
+            "last_dir_inf_over_dt_max": worst}, final
+
+
+def measure_trajectories(bsc, torch, steps=20):
+    """The drape over 20 time steps (dt = 0.01 s) for mu_bd = 1e-6, 1e-5 and
+    1e-4 N m in FP32 bulk, and for 1e-5 also in FP64; the FP32 trajectory's
+    final positions against the FP64 one's (the FP64 path holds the oracle's
+    1e-12 parity), relative to the cloth width."""
+    out = {"workload": "drape256", "stop_rule": "||d||_inf / dt < 1e-2 m/s per time step", "runs": {}}
+    finals = {}
+    for mu_bd in (1e-6, 1e-5, 1e-4):
+        pat = inputs.config_drape(1, 256, mu_bd)
+        for prec, name in ((bsc.FP32, "fp32"), (bsc.FP64, "fp64")):
+            if prec == bsc.FP64 and mu_bd != 1e-5:
+                continue
+            rec, final = drape_trajectory(bsc, torch, pat, prec, steps)
+            out["runs"][f"mu_bd={mu_bd:g} {name}"] = rec
+            finals[(mu_bd, name)] = final
+        if mu_bd == 1e-5:
+            width = float((pat.rest.max(axis=0) - pat.rest.min(axis=0)).max())
+            d = (finals[(mu_bd, "fp32")] - finals[(mu_bd, "fp64")]).abs().max().item()
+            out["fp32_vs_fp64_final_max_abs_over_width"] = d / width
     return out
 
 

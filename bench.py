@@ -695,7 +695,29 @@ def cpu_baseline(args, pats, m=160, budget_spans=25000):
     spans = sum(p.n_spans for p in sample)
     return {"value": spans / secs, "unit": "spans/s", "cores": 1, "kind": "oracle",
             "sample": f"E+grad+projected Hessian+stencil assembly of {what}, FP64, one thread",
-            "seconds": secs}
+            "seconds": secs, "all_cores": _oracle_all_cores(orc, pats[0])}
+
+
+def _oracle_all_cores(orc, pat, m=96):
+    """The same oracle evaluation on every host core at once: one thread per
+    core, each evaluating its own copy of a leading m x m crop (the ctypes
+    calls release the GIL, and the oracle keeps no global state)."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = os.cpu_count() or 1
+    crop = inputs.crop(pat, min(m, pat.nu), min(m, pat.nv))
+
+    def work(_):
+        prob = orc.Problem.from_patch(crop)
+        sc = orc.Scene.from_patch(crop, project=True)
+        orc.evaluate(prob, sc, crop.C.copy(), crop.Chat.copy())
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(n) as ex:
+        list(ex.map(work, range(n)))
+    wall = time.perf_counter() - t0
+    return {"value": n * crop.n_spans / wall, "unit": "spans/s", "cores": n, "seconds": wall,
+            "sample": f"{n} concurrent evaluations of the leading {crop.nu}x{crop.nv} control points "
+                      f"({crop.n_spans} spans each), one per thread"}
 
 
 def run_reference(args):

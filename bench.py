@@ -608,6 +608,16 @@ def measure_batch(bsc, flush, stream, torch, np, seed=1, steps=3, warmup=2):
            "max_ls_halvings": reports[-1]["ls_halvings"], "tile_tu": tuning["tile_tu"],
            "autotune": tuning, "graph": ctx.graph_state(), "steps": steps}
     ctx.close()
+    # the same batch with the per-point projection of the FBW terms
+    ctx = bsc.batch_for_patches(pats, precision=bsc.FP32, pcg_rel_tol=1e-8, project=bsc.PROJECT_POINT)
+    ctx.set_profiling(True)
+    ctx.autotune(C0, Chat)
+    C = C0.clone()
+    step_ms, phases, reports, _ = time_newton(ctx, C, C0, Chat, steps, warmup, flush, stream, torch)
+    out["point_projection"] = {"newton_step_ms": sum(step_ms) / steps,
+                               "phases_ms": {k: v / steps for k, v in phases.items()},
+                               "max_pcg_iters": reports[-1]["pcg_iters"]}
+    ctx.close()
     return out
 
 

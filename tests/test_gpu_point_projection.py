@@ -166,3 +166,32 @@ def test_drape_full_size_point(orc, precision):
     bound = 1e-12 if precision == bsc.FP64 else 2e-5
     assert eH < bound and eK < bound
     assert rep.status == 0 and rep.E1 <= rep.E0 and rep.pcg_rel_res <= 1e-8 and rep.spans_projected == 0
+
+
+def test_batch_point_projection_bitwise(orc):
+    """A batch of uneven patches under the per-point projection: span terms
+    and K bitwise equal to one context per patch; every patch's Newton step
+    succeeds."""
+    pats = [inputs.config_random_small(11 + k, nu, nv, noise=0.2)
+            for k, (nu, nv) in enumerate([(7, 9), (12, 6), (5, 5), (20, 14)])]
+    batch = bsc.batch_for_patches(pats, precision=bsc.FP64, project=POINT)
+    try:
+        out = np.zeros((3, batch.N))
+        for p, pat in enumerate(pats):
+            out[:, batch.cp_offset[p]:batch.cp_offset[p + 1]] = pat.C.T
+        C = torch.from_numpy(out).to(device="cuda", dtype=batch.dtype).contiguous()
+        _, _, H = batch.span_terms(C, project=POINT)
+        K = batch.assemble_hessian(C, project=POINT)
+        for p, pat in enumerate(pats):
+            with bsc.context_for_patch(pat, precision=bsc.FP64, project=POINT) as one:
+                C1 = one.to_device(pat.C)
+                _, _, H1 = one.span_terms(C1, project=POINT)
+                K1 = one.assemble_hessian(C1, project=POINT)
+                a, b = int(batch.span_offset[p]), int(batch.span_offset[p + 1])
+                assert torch.equal(H[a:b], H1), p
+                assert torch.equal(batch.patch_slice(K, p), K1), p
+        rep = batch.newton_step(C, C.clone())
+        assert rep.status == 0 and rep.spans_projected == 0
+        assert all(r.status == 0 for r in batch.patch_reports())
+    finally:
+        batch.close()

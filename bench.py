@@ -400,7 +400,10 @@ def run_gpu(args):
                          "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                          "traffic": projection_traffic(args.workload, prec == bsc.FP32, tuning),
                          "algorithmic_flops_per_step": flops, "launch_ms": proj_ms,
-                         "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); no FP64 peak in the measured peaks"},
+                         "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); no FP64 peak in the measured peaks",
+                         "executed": projection_executed(args.workload, prec == bsc.FP32, tuning, proj_ms,
+                                                         clk.get("sm_mhz") or 2070.0,
+                                                         torch.cuda.get_device_properties(local).multi_processor_count)},
             "fp64": fp64,
             "batched": batched,
             "learned": learned,
@@ -658,6 +661,23 @@ PROJECTION_TRAFFIC = {("drape256", True, 2, 0): 412.7e6,
                       ("drape256", True, 1, 0): 412.6e6,
                       ("drape256", True, 0, 1): 437.5e6}
 PROJECTION_SOURCES = ("k_project.cu", "proj_core.cuh", "k_project_ring.cu")
+# Executed FP64 work of the projection kernels of one drape step (border path 2,
+# phase-2 variant 0), from the same kind of capture with the metrics
+# sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum and
+# sm__pipe_fp64_cycles_active.sum: FLOPs (DADD + DMUL + 2 DFMA) and FP64-pipe
+# cycles summed over the SMs.
+PROJECTION_EXECUTED = {("drape256", True, 2, 0): (938.5e6, 403.6e6)}
+
+
+def projection_executed(workload, fp32, tuning, launch_ms, sm_mhz, num_sms):
+    """Executed FP64 FLOP/s of the projection and the busy fraction of the SMs'
+    FP64 pipes over its live time, from the captured counts, or None."""
+    rec = PROJECTION_EXECUTED.get((workload, bool(fp32), tuning.get("border_path"), tuning.get("p2_variant")))
+    if rec is None or projection_traffic(workload, fp32, tuning) is None:
+        return None
+    flops, cycles = rec
+    return {"executed_flops_per_step": flops, "executed_tflops": flops / (launch_ms * 1e-3) / 1e12,
+            "fp64_pipe_busy": cycles / (num_sms * launch_ms * 1e-3 * sm_mhz * 1e6)}
 
 
 def projection_traffic(workload, fp32, tuning):

@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
 #pragma unroll
         for (int k = 0; k < 8; ++k)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) col[3 * k + c] += gt[k][0] * t[0][c] + gt[k][1] * t[1][c];
+          for (int c = 0; c < 3; ++c)  // two FMAs into the accumulator
+            col[3 * k + c] = fma(gt[k][1], t[1][c], fma(gt[k][0], t[0][c], col[3 * k + c]));
       }
     }
     for (int q = b0; q < b1; ++q) {
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
       for (int i = k + 1; i < RN; ++i) w[i] = shfl(wj, i);
       if (act) {
 #pragma unroll
-        for (int i = k + 1; i < RN; ++i) col[i] -= v[i] * wj + w[i] * vj;
+        for (int i = k + 1; i < RN; ++i) col[i] = fma(-w[i], vj, fma(-v[i], wj, col[i]));  // two FMAs
       }
     }
     if (lane == RN - 2) {

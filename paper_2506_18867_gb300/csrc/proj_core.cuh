@@ -334,7 +334,10 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* 
 #pragma unroll
           for (int dd = 0; dd < 3; ++dd) {
             if (k2 == k && dd > c) continue;
-            A[lp(3 * k + c, 3 * k2 + dd)] += Tk[c][dd] * gr[k2][0] + Tk[c][3 + dd] * gr[k2][1];
+            // two FMAs into the accumulator (a separate product and sum would
+            // cost the FP64 pipe a DMUL and a DADD more per entry)
+            const int ix = lp(3 * k + c, 3 * k2 + dd);
+            A[ix] = fma(Tk[c][3 + dd], gr[k2][1], fma(Tk[c][dd], gr[k2][0], A[ix]));
           }
     }
   }
@@ -344,13 +347,16 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* 
 #pragma unroll
     for (int k = 0; k < D; ++k) Lr[k] = tab.lr(q, k);
 #pragma unroll
-    for (int k = 0; k < D; ++k)
+    for (int k = 0; k < D; ++k) {
+      const double wl = WB * Lr[k];
 #pragma unroll
-      for (int k2 = 0; k2 <= k; ++k2) {
-        const double h = WB * Lr[k] * Lr[k2];
+      for (int k2 = 0; k2 <= k; ++k2)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) A[lp(3 * k + c, 3 * k2 + c)] += h;
-      }
+        for (int c = 0; c < 3; ++c) {
+          const int ix = lp(3 * k + c, 3 * k2 + c);
+          A[ix] = fma(wl, Lr[k2], A[ix]);
+        }
+    }
   }
   // 2. Householder tridiagonalisation: d -> R[0..n), e -> R[n..2n); the
   //    reflector v_k stays in column k of A, p = tau A v in R[2n..3n).
@@ -400,7 +406,8 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* 
       const double vi = A[i * (i + 1) / 2 + k], wi = R[2 * n + i];
       const int ri = i * (i + 1) / 2;
 #pragma unroll 1
-      for (int j = k + 1; j <= i; ++j) A[ri + j] -= vi * R[2 * n + j] + wi * A[j * (j + 1) / 2 + k];
+      for (int j = k + 1; j <= i; ++j)  // A -= v w^T + w v^T as two FMAs per entry
+        A[ri + j] = fma(-wi, A[j * (j + 1) / 2 + k], fma(-vi, R[2 * n + j], A[ri + j]));
     }
   }
   R[n - 2] = A[lp(n - 2, n - 2)];

@@ -651,22 +651,21 @@ def measure_learned(bsc, np, seeds=(1_000_000, 1_000_001, 1_000_002, 1_000_003),
 # phase per Newton step, from one metrics-only ncu capture of the drape bench
 # (dram__bytes_* of every projection launch of one step), keyed by the autotuner's border path and
 # phase-2 variant and by a hash of the projection sources it was taken with.
-#   path 2, variant 0: ring<1> 3.8 + p1<5> 54.8 + p2<5,2> 150.9 + corr 180.3
-#                      + p2<8> 6.9 + corr 16.1 MB
-#   path 1, variant 0: p1<5> 54.8 + p1<8> 3.7 + p2<8> 6.9 + corr 16.1
-#                      + p2<5,2> 150.9 + corr 180.3 MB
-#   path 0, variant 1: ring<0> 18.6 + p1<5> 55.2 + p2<5,3> 183.5 + corr 180.2 MB
-PROJECTION_TRAFFIC_HASH = "85a309a31ce15230"
-PROJECTION_TRAFFIC = {("drape256", True, 2, 0): 412.7e6,
-                      ("drape256", True, 1, 0): 412.6e6,
-                      ("drape256", True, 0, 1): 437.5e6}
+#   path 2, variant 0: ring<1> 3.7 + p2<8> 6.9 + corr 16.1 + p1<5> 57.5
+#                      + p2<5,2> 153.8 + corr 183.1 MB
+#   path 1, variant 0: p1<5> + p1<8> + p2<8> + corr + p2<5,2> + corr, 421.4 MB
+#   path 0, variant 0: ring<0> + p1<5> + p2<5,2> + corr, 413.1 MB
+PROJECTION_TRAFFIC_HASH = "6496be87f21c3bc4"
+PROJECTION_TRAFFIC = {("drape256", True, 2, 0): 421.2e6,
+                      ("drape256", True, 1, 0): 421.4e6,
+                      ("drape256", True, 0, 0): 413.1e6}
 PROJECTION_SOURCES = ("k_project.cu", "proj_core.cuh", "k_project_ring.cu")
 # Executed FP64 work of the projection kernels of one drape step (border path 2,
 # phase-2 variant 0), from the same kind of capture with the metrics
 # sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum and
 # sm__pipe_fp64_cycles_active.sum: FLOPs (DADD + DMUL + 2 DFMA) and FP64-pipe
 # cycles summed over the SMs.
-PROJECTION_EXECUTED = {("drape256", True, 2, 0): (938.5e6, 403.6e6)}
+PROJECTION_EXECUTED = {("drape256", True, 2, 0): (938.5e6, 367.4e6)}
 
 
 def projection_executed(workload, fp32, tuning, launch_ms, sm_mhz, num_sms):

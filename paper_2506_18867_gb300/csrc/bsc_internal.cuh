@@ -330,7 +330,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsig
 // search direction) between grid barriers: 0 reads it with plain loads, which
 // the barriers' fences make coherent; 2 reads it from L2 (ld.global.cg),
 // which is coherent without relying on L1 invalidation.
-template <typename T, int X_MODE = 0>
+// FUSED: each row accumulates by three FMAs per block (fewest instructions:
+// faster in the persistent PCG, and in FP64, where the FP64 pipe bounds the
+// product); otherwise a product, an FMA and an add per block, which the
+// learned flexible CG runs faster (measured).
+template <typename T, int X_MODE = 0, bool FUSED = true>
 __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T* __restrict__ K, const T* x,
                                          T y[3]) {
   const int i = al % nu, j = al / nu;
@@ -353,9 +357,15 @@ __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T*
         x0 = x[be]; x1 = x[N + be]; x2 = x[2 * N + be];
       }
       const T* Kb = K + (size_t)slot * 9 * N + al;
-      y0 += Kb[0] * x0 + Kb[(size_t)N] * x1 + Kb[(size_t)2 * N] * x2;
-      y1 += Kb[(size_t)3 * N] * x0 + Kb[(size_t)4 * N] * x1 + Kb[(size_t)5 * N] * x2;
-      y2 += Kb[(size_t)6 * N] * x0 + Kb[(size_t)7 * N] * x1 + Kb[(size_t)8 * N] * x2;
+      if (FUSED) {
+        y0 = fma(Kb[(size_t)2 * N], x2, fma(Kb[(size_t)N], x1, fma(Kb[0], x0, y0)));
+        y1 = fma(Kb[(size_t)5 * N], x2, fma(Kb[(size_t)4 * N], x1, fma(Kb[(size_t)3 * N], x0, y1)));
+        y2 = fma(Kb[(size_t)8 * N], x2, fma(Kb[(size_t)7 * N], x1, fma(Kb[(size_t)6 * N], x0, y2)));
+      } else {
+        y0 += Kb[0] * x0 + Kb[(size_t)N] * x1 + Kb[(size_t)2 * N] * x2;
+        y1 += Kb[(size_t)3 * N] * x0 + Kb[(size_t)4 * N] * x1 + Kb[(size_t)5 * N] * x2;
+        y2 += Kb[(size_t)6 * N] * x0 + Kb[(size_t)7 * N] * x1 + Kb[(size_t)8 * N] * x2;
+      }
     }
   }
   y[0] = y0; y[1] = y1; y[2] = y2;

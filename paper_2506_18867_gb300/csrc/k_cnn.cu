@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
     double l_pq = 0.0, l_pr = 0.0;
     for (int al = tid; al < P; al += stride) {
       float qq[3];
-      spmv_row<float, 2>(nu, nv, P, al, F.K, F.p, qq);
+      spmv_row<float, 2, false>(nu, nv, P, al, F.K, F.p, qq);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float pc = F.p[(size_t)c * P + al];

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK, sizeof(T) == 4 ? 2 : 1)
                 for (int d = 0; d < 3; ++d) {
                   const T u = gm0 * A[c][d] + gm1 * A[c][3 + d];
                   const T v = gm0 * A[3 + c][d] + gm1 * A[3 + c][3 + d];
-                  acc[i][c][d] += gl0 * u + gl1 * v;
+                  acc[i][c][d] = fma(gl1, v, fma(gl0, u, acc[i][c][d]));  // two FMAs, no separate product and add
                 }
             }
           }
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK, sizeof(T) == 4 ? 2 : 1)
               if (l < 0) break;
               const T g0 = SV(k, V_G + 2 * l), g1 = SV(k, V_G + 2 * l + 1);
 #pragma unroll
-              for (int c = 0; c < 3; ++c) gacc[r][c] += g0 * SV(k, V_DP + c) + g1 * SV(k, V_DP + 3 + c);
+              for (int c = 0; c < 3; ++c) gacc[r][c] = fma(g1, SV(k, V_DP + 3 + c), fma(g0, SV(k, V_DP + c), gacc[r][c]));
             }
           }
         } else {

@@ -172,6 +172,27 @@ def test_full_gauss_rules(orc, rule):
         assert rel(g.cpu().numpy(), og) < 1e-12 and rel(H.cpu().numpy(), oH) < 1e-12
 
 
+@pytest.mark.parametrize("rule", [3, 4])
+def test_gauss_rules_projected(orc, rule):
+    """Projected span terms under the full 3x3 Gauss rule and the ablation rule
+    (2x2 Gauss on interior spans): every interior span then falls in the 24x24
+    class; both projections against the oracle."""
+    from oracle import project_psd
+    pat = inputs.config_random_small(9, 9, 8, noise=0.2)
+    prob = orc.Problem.from_patch(pat, mem_rule=rule, bend_rule=rule)
+    _, _, oH = prob.span_eval(pat.C)
+    oHs = np.stack([project_psd(h)[0] for h in oH])
+    _, _, oHp = prob.span_eval_projected(pat.C, orc.PROJECT_POINT)
+    with bsc.context_for_patch(pat, precision=bsc.FP64, quadrature=(rule, rule)) as ctx:
+        C = ctx.to_device(pat.C)
+        for path in (0, 1, 2):
+            ctx.set_border_path(path)
+            _, _, H = ctx.span_terms(C, project=bsc.PROJECT_SPAN)
+            assert rel(H.cpu().numpy(), oHs) < 1e-12, path
+        _, _, H = ctx.span_terms(C, project=bsc.PROJECT_POINT)
+        assert rel(H.cpu().numpy(), oHp) < 1e-12
+
+
 def test_fp32_errors_against_oracle(orc):
     """FP32 span evaluation / assembly with the FP64 projection: error stated."""
     pat = inputs.config_square(1, 32)

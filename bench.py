@@ -316,8 +316,10 @@ def run_gpu(args):
     total_spans = agg["spans"]
     value = total_spans / (eval_ms_max * 1e-3)
 
+    # The sub-measurements below run in single-GPU runs only: a multi-GPU run
+    # times the replicated step and holds its GPUs no longer than that.
     fp64 = None
-    if not args.no_fp64 and prec == bsc.FP32 and rank == 0:
+    if not args.no_fp64 and prec == bsc.FP32 and world == 1:
         ctx64 = make_context(bsc, pats, bsc.FP64)
         ctx64.set_profiling(True)
         C64_0 = C0.double()
@@ -334,19 +336,19 @@ def run_gpu(args):
         del C64, C64_0, Chat64
 
     batched = None
-    if args.workload != "batch64" and not args.no_batch and prec == bsc.FP32:
+    if args.workload != "batch64" and not args.no_batch and prec == bsc.FP32 and world == 1:
         batched = measure_batch(bsc, flush, stream, torch, np, seed=1 + rank)
     learned = None
-    if args.workload == "drape256" and not args.no_learned and prec == bsc.FP32 and rank == 0:
+    if args.workload == "drape256" and not args.no_learned and prec == bsc.FP32 and world == 1:
         learned = measure_learned(bsc, np)
     sweep = None
-    if args.workload == "drape256" and not args.no_sweep and rank == 0:
+    if args.workload == "drape256" and not args.no_sweep and world == 1:
         sweep = measure_sweep(bsc, torch)
     trajectory = None
-    if args.workload == "drape256" and not args.no_trajectory and rank == 0:
+    if args.workload == "drape256" and not args.no_trajectory and world == 1:
         trajectory = measure_trajectories(bsc, torch)
     point = None
-    if len(pats) == 1 and not args.no_point and rank == 0:
+    if len(pats) == 1 and not args.no_point and world == 1:
         point = measure_point_projection(bsc, pats[0], prec, ctx, C0, Chat, K, args.warmup, ms_step, flush, stream,
                                          torch)
 

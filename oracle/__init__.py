@@ -81,6 +81,8 @@ def lib():
         _lib.or_solve_pcg.restype = I
         _lib.or_newton_step.argtypes = [P, S, D, D, I, ct.c_double, I, ct.POINTER(NewtonReport)]
         _lib.or_newton_step.restype = I
+        _lib.or_line_search.argtypes = [P, S, D, D, D, ct.c_double, I, D, ct.POINTER(NewtonReport)]
+        _lib.or_line_search.restype = I
     return _lib
 
 
@@ -269,6 +271,20 @@ def newton_step(prob: Problem, scene: Scene, C, Chat=None, solver=0, pcg_tol=1e-
     lib().or_newton_step(ct.byref(prob._p), ct.byref(scene._s), _dp(C), _dp(Chat), int(solver),
                          float(pcg_tol), int(max_halvings), ct.byref(rep))
     return C, rep
+
+
+def line_search(prob: Problem, scene: Scene, C, Chat, d, max_halvings=30):
+    """The oracle's backtracking along direction d from C; returns (C_new, status, report)."""
+    C = _f64(C).reshape(prob.n_cp, 3).copy()
+    Chat = C.copy() if Chat is None else _f64(Chat).reshape(prob.n_cp, 3)
+    d = _f64(d).reshape(prob.n_cp, 3)
+    E0 = energy(prob, scene, C, Chat)
+    work = np.zeros_like(C)
+    rep = NewtonReport()
+    st = lib().or_line_search(ct.byref(prob._p), ct.byref(scene._s), _dp(C), _dp(Chat), _dp(d), float(E0),
+                              int(max_halvings), _dp(work), ct.byref(rep))
+    rep.E0 = E0
+    return C, st, rep
 
 
 def stencil_to_dense(nu, nv, K) -> np.ndarray:

@@ -955,25 +955,40 @@ int or_newton_step(const or_problem* p, const or_scene* sc, double* C, const dou
   rep->grad_inf = ginf;
   rep->dir_inf = dinf;
   int status = st;
-  if (st == 0) {
-    double alpha = 1.0;
-    int h = 0;
-    for (;;) {
-      for (int i = 0; i < n; ++i) Ct[i] = C[i] + alpha * dC[i];
-      double E1 = or_energy(p, sc, Ct, Chat);
-      if (E1 <= E0) {
-        memcpy(C, Ct, sizeof(double) * n);
-        rep->E1 = E1;
-        rep->alpha = alpha;
-        rep->ls_halvings = h;
-        break;
-      }
-      if (h == max_halvings) { status = -3; rep->E1 = E1; rep->alpha = 0.0; rep->ls_halvings = h; break; }
-      alpha *= 0.5;
-      ++h;
-    }
-  }
+  if (st == 0) status = or_line_search(p, sc, C, Chat, dC, E0, max_halvings, Ct, rep);
   rep->status = status;
   free(g); free(K); free(rhs); free(dC); free(Ct);
   return status;
+}
+
+/* Backtracking along dC from C, whose energy is E0 (Sec. 5.1: the step
+ * length starts at 1 and is halved until the incremental potential does not
+ * increase, plain decrease without an Armijo constant): C <- C + alpha dC
+ * for the first alpha in 1, 1/2, 1/4, ... with E(C + alpha dC) <= E0; after
+ * max_halvings halvings without one, C is left unchanged and -3 returned.
+ * Ct: caller's workspace of 3N doubles.  Fills E1, alpha, ls_halvings. */
+int or_line_search(const or_problem* p, const or_scene* sc, double* C, const double* Chat, const double* dC,
+                   double E0, int max_halvings, double* Ct, or_newton_report* rep) {
+  const int n = 3 * p->nu * p->nv;
+  double alpha = 1.0;
+  int h = 0;
+  for (;;) {
+    for (int i = 0; i < n; ++i) Ct[i] = C[i] + alpha * dC[i];
+    double E1 = or_energy(p, sc, Ct, Chat);
+    if (E1 <= E0) {
+      memcpy(C, Ct, sizeof(double) * n);
+      rep->E1 = E1;
+      rep->alpha = alpha;
+      rep->ls_halvings = h;
+      return 0;
+    }
+    if (h == max_halvings) {
+      rep->E1 = E1;
+      rep->alpha = 0.0;
+      rep->ls_halvings = h;
+      return -3;
+    }
+    alpha *= 0.5;
+    ++h;
+  }
 }

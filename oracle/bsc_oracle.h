@@ -131,6 +131,13 @@ int or_newton_step(const or_problem* p, const or_scene* sc, double* C,
                    const double* Chat, int solver, double pcg_tol,
                    int max_halvings, or_newton_report* rep);
 
+/* The backtracking line search of or_newton_step on its own, along a given
+ * direction dC from C (energy E0): C <- C + alpha dC for the first alpha in
+ * 1, 1/2, ... with E(C + alpha dC) <= E0 (returns 0), or C unchanged and -3
+ * after max_halvings halvings.  Ct: workspace of 3N doubles. */
+int or_line_search(const or_problem* p, const or_scene* sc, double* C, const double* Chat, const double* dC,
+                   double E0, int max_halvings, double* Ct, or_newton_report* rep);
+
 #ifdef __cplusplus
 }
 #endif

@@ -231,6 +231,40 @@ def test_newton_on_quadratic_problem_converges_in_one_step(orc):
     assert np.abs(g1).max() <= 1e-10 * rep.grad_inf
 
 
+def test_line_search_backtracking_branch(orc):
+    """Sec. 5.1 backtracking (plain decrease, no Armijo constant): on a noisy
+    state whose full Newton step increases the incremental potential, the
+    oracle takes the first alpha in 1, 1/2, 1/4, ... at which the energy has
+    not increased, with the energies evaluated here step by step; along an
+    uphill direction (d = +g, so E(C + alpha d) > E(C) for every small alpha)
+    it gives up after 30 halvings and leaves C unchanged; and it stops at
+    the halving limit it is given."""
+    pat = inputs.config_random_small(16, 14, 12, noise=0.3)
+    prob = orc.Problem.from_patch(pat)
+    sc = orc.Scene.from_patch(pat, project=True)
+    E0, g, K = orc.evaluate(prob, sc, pat.C, pat.Chat)
+    d = orc.solve_banded(pat.nu, pat.nv, K, -g)
+    alphas = [0.5 ** k for k in range(31)]
+    Es = [orc.energy(prob, sc, pat.C + a * d, pat.Chat) for a in alphas]
+    first = next(k for k, E in enumerate(Es) if E <= E0)
+    assert first >= 1 and Es[0] > E0            # the full step overshoots here
+    assert all(E > E0 for E in Es[:first])
+    C1, st, rep = orc.line_search(prob, sc, pat.C, pat.Chat, d)
+    assert st == 0 and rep.ls_halvings == first and rep.alpha == alphas[first]
+    assert rep.E1 == Es[first] and rep.E1 <= E0
+    np.testing.assert_array_equal(C1, pat.C + alphas[first] * d)
+    Cn, rn = orc.newton_step(prob, sc, pat.C, pat.Chat, solver=0)
+    assert rn.status == 0 and rn.ls_halvings == first and rn.alpha == alphas[first]
+    np.testing.assert_array_equal(Cn, C1)
+    # a non-descent direction: uphill along the gradient
+    assert all(orc.energy(prob, sc, pat.C + a * g, pat.Chat) > E0 for a in alphas)
+    C2, st2, rep2 = orc.line_search(prob, sc, pat.C, pat.Chat, g)
+    assert st2 == -3 and rep2.ls_halvings == 30 and rep2.alpha == 0.0
+    np.testing.assert_array_equal(C2, pat.C)
+    _, rep3 = orc.newton_step(prob, sc, pat.C, pat.Chat, solver=0, max_halvings=first - 1)
+    assert rep3.status == -3 and rep3.ls_halvings == first - 1
+
+
 def test_plate_deflection_converges_to_navier_solution(orc):
     """Sec. 6.2 bending benchmark: simply supported plate, bending only, uniform
     load B; the maximum deflection approaches 0.048744 B a^4 (1-nu^2)/(E h^3)

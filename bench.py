@@ -2,7 +2,8 @@
 """Benchmark of the GB300 B-spline cloth hot path.
 
 One timed step = one projected-Newton iteration (``bsc_newton_step``) of the
-256 x 256 drape workload in FP32 bulk precision: span evaluation (E, g, 27x27
+largest single-GPU workload, the 1024 x 1024 wrinkle field (1,048,576 control
+points, 1,044,484 spans) in FP32 bulk precision: span evaluation (E, g, 27x27
 H), FP64 SPD projection, gather assembly, PCG solve to 1e-8 and the
 backtracking line search.  Reported:
 
@@ -20,10 +21,12 @@ backtracking line search.  Reported:
 independent patches (sides uniform in 16..192, per-patch materials and rest
 rotations) stepped together - one launch per phase, the persistent PCG split
 into per-patch block groups, the Newton iteration replayed from a CUDA graph,
-tile shapes from the autotuner.  The default drape line also carries a short
-measurement of that workload under ``batched``, and under ``learned`` the
+tile shapes from the autotuner; ``--workload drape256`` the 256 x 256 drape.
+The default line also carries short measurements of the drape under
+``drape256``, of the batch under ``batched``, and under ``learned`` the
 learned preconditioner on held-out 512 x 512 Newton systems (block-Jacobi
-PCG vs flexible CG with the trained network, iterations and ms to 1e-8).
+PCG vs flexible CG with the trained network: iterations and ms to 1e-8 per
+solve, and ms per Newton step with each solver).
 
 ``--impl reference`` times the oracle itself (the reference arm).
 """
@@ -46,7 +49,11 @@ if ROOT not in sys.path:
 from paper_2506_18867_gb300 import inputs  # noqa: E402
 
 METRIC = "spans/s (E+grad+Hessian+assembly) and Newton-step ms"
-FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300 (no FP64 entry in the measured peaks)
+# FP64 peak of a GB300 (no FP64 entry in the measured peaks): 152 SMs x 2 DFMA
+# per clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s, NVIDIA's nominal 1.25; a
+# throughput microbenchmark of independent DFMA chains measured 1.0 TFLOP/s
+FP64_PEAK_TFLOPS = 1.25
+FP64_DFMA_MEASURED_TFLOPS = 1.0
 
 WORKLOADS = {
     # name: (builder of the list of patches, description)
@@ -55,8 +62,14 @@ WORKLOADS = {
                  "sigma = 1 mm noise, u = 0 edge pinned, dt = 0.01 s"),
     "square32": (lambda seed: [inputs.config_square(seed, 32)],
                  "square, 32x32 control points (900 spans), 1 m x 1 m, two top corners pinned"),
+    "wrinkle512": (lambda seed: [inputs.config_wrinkle(seed, 512, 2.0)],
+                   "the wrinkle field on 512x512 control points (261,121 spans), 2 m x 2 m, same span length "
+                   "and material as wrinkle1024: the size the profiles are captured at"),
     "wrinkle1024": (lambda seed: [inputs.config_wrinkle(seed, 1024)],
-                    "precision sweep, 1024x1024 control points (1,044,484 spans), 4 m x 4 m wrinkle field"),
+                    "precision-sweep patch, 1024x1024 control points (1,048,576 cp, 1,044,484 spans), 4 m x 4 m, "
+                    "seeded multi-frequency wrinkle field (8 sinusoids, wavelengths 4-64 spans, amplitudes 1-5 mm), "
+                    "E = 1e5 Pa, nu = 0.3, h = 1 mm, 200 kg/m^2, two top corners pinned, gravity -z, "
+                    "dt = 0.01 s"),
     "batch64": (lambda seed: inputs.config_batch(seed, 64),
                 "batched garments: 64 independent patches, nu and nv uniform in [16, 192], E log-uniform in "
                 "[1e4, 1e6] Pa, Poisson ratio uniform in [0.2, 0.45], random rest rotations, 1 cm spans, "
@@ -70,11 +83,12 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="bsc", choices=["bsc", "reference"])
-    p.add_argument("--workload", default="drape256", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="wrinkle1024", choices=sorted(WORKLOADS))
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-garment sub-measurement")
+    p.add_argument("--no-drape", action="store_true", help="skip the 256x256 drape sub-measurement")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner sub-measurement")
     p.add_argument("--no-point", action="store_true", help="skip the per-point projection sub-measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the 1024x1024 precision sweep sub-measurement")
@@ -137,7 +151,19 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- flop model
 
-def projection_flops(nred, nneg, nm, nb):
+def ldlt_flops(n):
+    """The FP64 PSD test of a reduced Hessian of size n: the infinity norm
+    (n^2 absolute values summed), the shift, and the right-looking LDL^T with
+    one reciprocal, n - k - 1 multipliers and (n - k - 1)(n - k) / 2 FMAs
+    (2 flops each) per pivot k."""
+    f = n * n + n
+    for k in range(n):
+        m = n - k - 1
+        f += 1 + m + m * (m + 1)
+    return f
+
+
+def projection_flops(nred, nneg, nm, nb, psd=False):
     """Algorithmic FP64 flops of the SPD projection of one span per Newton
     iteration as implemented: reduced Hessian formation from the reduced
     derivative vectors (the span's orthonormal basis and the vectors in it
@@ -148,12 +174,19 @@ def projection_flops(nred, nneg, nm, nb):
     evaluations of 4 n flops on average), the pivoted LU and two solves of
     the shifted tridiagonal, the Rayleigh quotient, the back-transformation
     (2 n^2), the mapping to span DOFs and the rank-one update of the 378
-    packed entries (FP32 bracketing and FP32 updates are not counted)."""
+    packed entries (FP32 bracketing and FP32 updates are not counted).
+    With the PSD test (interior spans, psd=True) every span pays the
+    formation and the LDL^T test, and only the spans with a projected
+    eigenvalue go on to the formation again and the eigendecomposition."""
     n = nred
     D = n // 3
+    form = nm * 2 * (36 * D + 9 * D * (D + 1)) + nb * (2 * D * (D + 1))  # T_k and blocks per point
     f = 0.0
-    f += nm * 2 * (36 * D + 9 * D * (D + 1))           # T_k, reduced blocks per membrane point
-    f += nb * (2 * D * (D + 1))                        # blocks per bending point
+    if psd and n == 15:
+        f += form + ldlt_flops(n)
+        if not nneg:
+            return f
+    f += form
     f += 4.0 * n ** 3 / 3.0 + 4 * n                    # tridiagonalisation, scaling
     f += 4 * n                                         # inertia count at -tau
     if nneg:
@@ -287,8 +320,9 @@ def run_gpu(args):
     nm = np.bincount(ctx.quadrature_tables(0)[:, 24].astype(np.int64), minlength=Nsp)
     nb = np.bincount(ctx.quadrature_tables(1)[:, 24].astype(np.int64), minlength=Nsp)
     flops = 0.0
+    psd = bool(tuning.get("psd_test"))
     for s_ in range(Nsp):
-        flops += projection_flops(int(nred[s_]), int(nneg[s_]), int(nm[s_]), int(nb[s_]))
+        flops += projection_flops(int(nred[s_]), int(nneg[s_]), int(nm[s_]), int(nb[s_]), psd)
     achieved_tflops = flops / (proj_ms * 1e-3) / 1e12
 
     # e2e: the same Newton step through the C ABI from pinned host buffers
@@ -335,17 +369,20 @@ def run_gpu(args):
         ctx64.close()
         del C64, C64_0, Chat64
 
+    drape = None
+    if args.workload != "drape256" and not args.no_drape and prec == bsc.FP32 and world == 1:
+        drape = measure_drape(bsc, flush, stream, torch, np, K, args.warmup)
     batched = None
     if args.workload != "batch64" and not args.no_batch and prec == bsc.FP32 and world == 1:
         batched = measure_batch(bsc, flush, stream, torch, np, seed=1 + rank)
     learned = None
-    if args.workload == "drape256" and not args.no_learned and prec == bsc.FP32 and world == 1:
-        learned = measure_learned(bsc, np)
+    if args.workload != "batch64" and not args.no_learned and prec == bsc.FP32 and world == 1:
+        learned = measure_learned(bsc, np, torch, flush)
     sweep = None
-    if args.workload == "drape256" and not args.no_sweep and world == 1:
+    if args.workload != "batch64" and not args.no_sweep and world == 1:
         sweep = measure_sweep(bsc, torch)
     trajectory = None
-    if args.workload == "drape256" and not args.no_trajectory and world == 1:
+    if args.workload != "batch64" and not args.no_trajectory and world == 1:
         trajectory = measure_trajectories(bsc, torch)
     point = None
     if len(pats) == 1 and not args.no_point and world == 1:
@@ -402,11 +439,17 @@ def run_gpu(args):
                          "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                          "traffic": projection_traffic(args.workload, prec == bsc.FP32, tuning),
                          "algorithmic_flops_per_step": flops, "launch_ms": proj_ms,
-                         "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); no FP64 peak in the measured peaks",
+                         "peak_source": "GB300 FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x "
+                                        "2.07 GHz = 1.26 TFLOP/s (nominal 1.25); no FP64 entry in the measured peaks",
+                         "frac_of_dfma_microbenchmark": achieved_tflops / FP64_DFMA_MEASURED_TFLOPS,
+                         "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of the projection launches "
+                                           "of one step (ncu capture summarised in profiles/), null when no capture "
+                                           "of the current kernels exists for this workload",
                          "executed": projection_executed(args.workload, prec == bsc.FP32, tuning, proj_ms,
                                                          clk.get("sm_mhz") or 2070.0,
                                                          torch.cuda.get_device_properties(local).multi_processor_count)},
             "fp64": fp64,
+            "drape256": drape,
             "batched": batched,
             "learned": learned,
             "point_projection": point,
@@ -595,6 +638,39 @@ def measure_point_projection(bsc, pat, prec, ctx_span, C0, Chat, steps, warmup, 
             "stop_rule": "||d||_inf / dt < 1e-2 m/s", "ablation_standard_2x2": ablation}
 
 
+def measure_drape(bsc, flush, stream, torch, np, steps, warmup):
+    """The 256 x 256 drape (65,536 cp, 64,516 spans) in FP32 bulk and in FP64:
+    Newton-step ms, phases, spans/s of the evaluation + assembly phase."""
+    pat = WORKLOADS["drape256"][0](1)[0]
+    out = {"workload": "drape256", "spans": pat.n_spans, "control_points": pat.n_cp}
+    for prec, name, k in ((bsc.FP32, "fp32", steps), (bsc.FP64, "fp64", max(2, steps // 3))):
+        ctx = bsc.context_for_patch(pat, precision=prec, pcg_rel_tol=1e-8)
+        ctx.set_profiling(True)
+        C0, Chat = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+        C = C0.clone()
+        tuning = ctx.autotune(C0, Chat)
+        ms, ph, reps, launches = time_newton(ctx, C, C0, Chat, k, warmup, flush, stream, torch)
+        ev = (ph["span_eval"] + ph["project"] + ph["assemble"]) / k
+        out[name] = {"newton_step_ms": sum(ms) / k, "eval_assembly_ms": ev, "spans_per_s": pat.n_spans / (ev * 1e-3),
+                     "phases_ms": {kk: v / k for kk, v in ph.items()}, "pcg_iters": reps[-1]["pcg_iters"],
+                     "launches_per_step": launches / k, "steps": k, "autotune": tuning}
+        if prec == bsc.FP32:
+            nneg, nred = ctx.projection_stats()
+            nm = np.bincount(ctx.quadrature_tables(0)[:, 24].astype(np.int64), minlength=pat.n_spans)
+            nb = np.bincount(ctx.quadrature_tables(1)[:, 24].astype(np.int64), minlength=pat.n_spans)
+            psd = bool(tuning.get("psd_test"))
+            fl = sum(projection_flops(int(nred[i]), int(nneg[i]), int(nm[i]), int(nb[i]), psd)
+                     for i in range(pat.n_spans))
+            pms = ph["project"] / k
+            out[name]["projection"] = {"ms": pms, "algorithmic_flops": fl,
+                                       "tflops": fl / (pms * 1e-3) / 1e12,
+                                       "frac_of_nominal_fp64": fl / (pms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                                       "traffic": projection_traffic("drape256", True, tuning)}
+        ctx.close()
+    out["newton_step_speedup_fp32_vs_fp64"] = out["fp64"]["newton_step_ms"] / out["fp32"]["newton_step_ms"]
+    return out
+
+
 def measure_batch(bsc, flush, stream, torch, np, seed=1, steps=3, warmup=2):
     """Short measurement of the batched-garment workload (FP32, autotuned, graph)."""
     pats = WORKLOADS["batch64"][0](seed)
@@ -629,10 +705,12 @@ def measure_batch(bsc, flush, stream, torch, np, seed=1, steps=3, warmup=2):
 WEIGHTS = os.path.join(ROOT, "paper_2506_18867_gb300", "weights", "cnn_learned512.npz")
 
 
-def measure_learned(bsc, np, seeds=(1_000_000, 1_000_001, 1_000_002, 1_000_003), n=512):
+def measure_learned(bsc, np, torch, flush, seeds=(1_000_000, 1_000_001, 1_000_002, 1_000_003), n=512, steps=3):
     """The learned preconditioner on held-out Newton systems of the 512 x 512
     workload: block-Jacobi PCG vs flexible CG with the trained network, both
-    to 1e-8 (CUDA events around each solve; one warm-up solve each first)."""
+    to 1e-8 (CUDA events around each solve; one warm-up solve each first);
+    then whole Newton steps of the same held-out states with each solver
+    (graph replay, the step from the same state every time, L2 flushed)."""
     from paper_2506_18867_gb300 import train_cnn
     if not os.path.exists(WEIGHTS):
         return {"unavailable": "no trained weights file"}
@@ -642,6 +720,31 @@ def measure_learned(bsc, np, seeds=(1_000_000, 1_000_001, 1_000_002, 1_000_003),
     train_cnn.evaluate(sy, net, seeds[:1])            # warm-up (graph capture, first launches)
     rows = train_cnn.evaluate(sy, net, seeds)
     summ = train_cnn.summarize(rows)
+    ctx = sy.ctx
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    newton = {"pcg": [], "learned": []}
+    for s in seeds:
+        pat = inputs.config_learned(s, n)
+        ctx.set_material(pat.material)
+        C0, Chat = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+        C = C0.clone()
+        for name, solver in (("pcg", None), ("learned", net)):
+            ctx.set_learned_solver(solver)
+            ms, ph, reps, _ = time_newton(ctx, C, C0, Chat, steps, 1, flush, stream, torch)
+            newton[name].append({"seed": int(s), "newton_step_ms": sum(ms) / steps, "solve_ms": ph["solve"] / steps,
+                                 "iters": reps[-1]["pcg_iters"], "fcg_iters": reps[-1]["fcg_iters"],
+                                 "fell_back": reps[-1]["fell_back"], "alpha": reps[-1]["alpha"]})
+    ctx.set_learned_solver(None)
+    mean = lambda rows, k: float(np.mean([r[k] for r in rows]))  # noqa: E731
+    summ["newton_step"] = {
+        "pcg_ms_mean": mean(newton["pcg"], "newton_step_ms"), "learned_ms_mean": mean(newton["learned"], "newton_step_ms"),
+        "pcg_solve_ms_mean": mean(newton["pcg"], "solve_ms"),
+        "learned_solve_ms_mean": mean(newton["learned"], "solve_ms"),
+        "pcg_iters_mean": mean(newton["pcg"], "iters"), "learned_iters_mean": mean(newton["learned"], "iters"),
+        "step_time_ratio_pcg_over_learned": mean(newton["pcg"], "newton_step_ms") / mean(newton["learned"],
+                                                                                        "newton_step_ms"),
+        "rows": newton}
     net.close()
     sy.ctx.close()
     summ.update({"workload": f"learned{n}", "grid": f"{n}x{n}", "rel_tol": 1e-8,

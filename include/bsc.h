@@ -124,6 +124,10 @@ typedef struct bsc_newton_report {
   int status;           /* bsc_status of the step */
   int spans_projected;  /* spans whose Hessian had a negative eigenvalue
                            (BSC_PROJECT_SPAN; 0 otherwise) */
+  int fcg_iters;        /* with a learned solver (bsc_set_learned_solver): the
+                           flexible-CG iterations, which pcg_iters includes; 0 otherwise */
+  int fell_back;        /* 1 when the learned solve stalled and block-Jacobi
+                           PCG finished it */
 } bsc_newton_report;
 
 typedef struct bsc_ctx bsc_ctx;
@@ -266,6 +270,10 @@ typedef struct bsc_tuning {
                               per SM, a thread per control point (each clamped
                               to [patches, usable blocks]) */
   double pcg_ms[4];        /* measured ms of the solve per candidate (-1: duplicate) */
+  int pcg_form;            /* PCG form chosen at that grid (see bsc_set_pcg_form) */
+  double pcg_form_ms[2];   /* measured ms of the solve per form (1e30: did not converge) */
+  int psd_test;            /* PSD test before the interior eigendecomposition (bsc_set_psd_test) */
+  double psd_ms[2];        /* measured ms of the whole projection without / with it */
 } bsc_tuning;
 bsc_status bsc_autotune(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, bsc_tuning* out);
 
@@ -291,6 +299,29 @@ bsc_status bsc_set_border_path(bsc_ctx* ctx, int path);
 /* Set the occupancy variant of the interior projection's eigenpair phase by
  * hand (0 or 1, see bsc_tuning); both compute bitwise the same result. */
 bsc_status bsc_set_p2_variant(bsc_ctx* ctx, int variant);
+
+/* PSD test of the SPD projection (BSC_PROJECT_SPAN): with on != 0 (the
+ * default) every interior span's reduced Hessian H_r first goes through an
+ * FP64 LDL^T factorisation of H_r + tau I, tau = 1e-14 ||H_r||_inf; a span
+ * whose pivots are all positive has no eigenvalue below -tau and keeps its
+ * Hessian, and only the spans that fail go on to the eigendecomposition
+ * (gathered into one list, so that the eigendecomposition runs with full
+ * warps).  The projected matrix is the same either way up to eigenvalues
+ * of size tau.  The test pays off when few spans need projecting (a cloth
+ * near equilibrium) and costs about a fifth of the eigendecomposition when
+ * most do; bsc_autotune keeps the faster setting for the state it is given. */
+bsc_status bsc_set_psd_test(bsc_ctx* ctx, int on);
+
+/* Form of the persistent block-Jacobi PCG (the same iterates up to rounding):
+ * 0 - the textbook recurrences, three group barriers per iteration (one
+ *     per reduction, one before the product reads the new direction);
+ * 1 - the pipelined recurrences of Ghysels & Vanroose (2014), which carry
+ *     K u and M K u so that an iteration's three dot products form in one
+ *     pass behind a single group barrier, at the cost of six more vectors
+ *     and a recursively updated residual that drifts a little further from
+ *     b - K x.
+ * bsc_autotune picks the faster of the two for the context; the default is 0. */
+bsc_status bsc_set_pcg_form(bsc_ctx* ctx, int form);
 
 /* Current split of the PCG's blocks (host array of count ints). */
 bsc_status bsc_pcg_split(const bsc_ctx* ctx, int* blocks_per_patch);
@@ -376,6 +407,33 @@ bsc_status bsc_cnn_activations(bsc_cnn* cnn, int which, float* out);
  * the solve from the current x. */
 bsc_status bsc_solve_fcg(bsc_ctx* ctx, bsc_cnn* cnn, const void* K_dev, const void* b_dev, void* x_dev,
                          double rel_tol, int max_iter, bsc_fcg_report* rep);
+
+/* Linear solver of bsc_newton_step.  With cnn != NULL (a network created on
+ * this single-patch FP32 context) every Newton step solves K d = -g by the
+ * flexible CG of bsc_solve_fcg - the network runs once on the step's K, the
+ * flexible CG iterates with z = M r, and block-Jacobi PCG finishes the solve
+ * from the current iterate when it stalls - to the same relative residual
+ * (options.pcg_rel_tol), inside the step's CUDA graph.  cnn == NULL returns
+ * to plain block-Jacobi PCG.  The report's pcg_iters then counts both
+ * solvers' iterations, fcg_iters the flexible CG's, fell_back the fallback.
+ * This is the learned preconditioner on the Newton path of Sec. 5.1 (the
+ * paper solves with a direct Cholesky factorisation instead).  Destroying the
+ * network detaches it. */
+bsc_status bsc_set_learned_solver(bsc_ctx* ctx, bsc_cnn* cnn);
+
+/* Stall window of the flexible CG (iterations in which r.r must drop by 4x
+ * before the solve falls back to PCG; default 24, range [1, 100000]). */
+bsc_status bsc_cnn_set_stall_window(bsc_cnn* cnn, int window);
+
+/* Bounded device waits of the context's persistent solvers (the group
+ * barriers of the PCG and of the learned flexible CG): spins = sleeps of
+ * about 64 ns before a barrier gives up, raises BSC_ERR_TIMEOUT and returns
+ * (default 2^25, about 2 s; range [1, 2^40]).  extra_blocks (0 or 1) makes
+ * every barrier wait for that many blocks beyond those launched, so that no
+ * barrier can complete: a test hook for the timeout path, which needs no
+ * fault.  Normal use leaves it 0.  The solvers' results are undefined after a
+ * timeout; the context stays usable. */
+bsc_status bsc_set_wait_limit(bsc_ctx* ctx, long long spins, int extra_blocks);
 
 /* ---- inspection entry points (parity tests, profiling) ------------------- */
 

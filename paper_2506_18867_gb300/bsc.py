@@ -44,7 +44,9 @@ EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc
            "bsc_quadrature_tables", "bsc_lumped_mass", "bsc_sizes", "bsc_set_profiling", "bsc_phase_times",
            "bsc_launch_count", "bsc_projection_stats", "bsc_solve_static", "bsc_cnn_param_count",
            "bsc_cnn_create", "bsc_cnn_destroy", "bsc_cnn_set_params", "bsc_cnn_get_params", "bsc_cnn_prepare",
-           "bsc_cnn_apply", "bsc_cnn_loss_grad", "bsc_cnn_adam_step", "bsc_cnn_activations", "bsc_solve_fcg")
+           "bsc_cnn_apply", "bsc_cnn_loss_grad", "bsc_cnn_adam_step", "bsc_cnn_activations", "bsc_solve_fcg",
+           "bsc_set_learned_solver", "bsc_cnn_set_stall_window", "bsc_set_wait_limit", "bsc_set_pcg_form",
+           "bsc_set_psd_test")
 
 TILE_CANDIDATES = (0, 8, 16, 32)
 
@@ -74,7 +76,8 @@ class Options(ct.Structure):
 class NewtonReport(ct.Structure):
     _fields_ = [("E0", ct.c_double), ("E1", ct.c_double), ("alpha", ct.c_double), ("dir_inf", ct.c_double),
                 ("pcg_rel_res", ct.c_double), ("pcg_iters", ct.c_int), ("ls_halvings", ct.c_int),
-                ("status", ct.c_int), ("spans_projected", ct.c_int)]
+                ("status", ct.c_int), ("spans_projected", ct.c_int), ("fcg_iters", ct.c_int),
+                ("fell_back", ct.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,13 +86,17 @@ class NewtonReport(ct.Structure):
 class Tuning(ct.Structure):
     _fields_ = [("tile_tu", ct.c_int * 4), ("tile_ms", (ct.c_double * 4) * 4), ("pcg_grid", ct.c_int),
                 ("border_path", ct.c_int), ("border_ms", ct.c_double * 3), ("p2_variant", ct.c_int),
-                ("p2_ms", ct.c_double * 2), ("pcg_grid_cand", ct.c_int * 4), ("pcg_ms", ct.c_double * 4)]
+                ("p2_ms", ct.c_double * 2), ("pcg_grid_cand", ct.c_int * 4), ("pcg_ms", ct.c_double * 4),
+                ("pcg_form", ct.c_int), ("pcg_form_ms", ct.c_double * 2), ("psd_test", ct.c_int),
+                ("psd_ms", ct.c_double * 2)]
 
     def as_dict(self):
         return {"tile_tu": list(self.tile_tu), "tile_ms": [list(r) for r in self.tile_ms],
                 "pcg_grid": self.pcg_grid, "border_path": self.border_path, "border_ms": list(self.border_ms),
                 "p2_variant": self.p2_variant, "p2_ms": list(self.p2_ms),
-                "pcg_grid_cand": list(self.pcg_grid_cand), "pcg_ms": list(self.pcg_ms)}
+                "pcg_grid_cand": list(self.pcg_grid_cand), "pcg_ms": list(self.pcg_ms),
+                "pcg_form": self.pcg_form, "pcg_form_ms": list(self.pcg_form_ms),
+                "psd_test": self.psd_test, "psd_ms": list(self.psd_ms)}
 
 
 class FcgReport(ct.Structure):
@@ -169,6 +176,11 @@ def load(path: str = LIB_PATH):
     lib.bsc_cnn_activations.argtypes = [P, I, F]
     lib.bsc_solve_fcg.argtypes = [P, P, V, V, V, D, I, ct.POINTER(FcgReport)]
     lib.bsc_graph_state.argtypes = [P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(ct.c_longlong)]
+    lib.bsc_set_learned_solver.argtypes = [P, P]
+    lib.bsc_cnn_set_stall_window.argtypes = [P, I]
+    lib.bsc_set_wait_limit.argtypes = [P, ct.c_longlong, I]
+    lib.bsc_set_pcg_form.argtypes = [P, I]
+    lib.bsc_set_psd_test.argtypes = [P, I]
     for name in EXPORTS:
         if name not in ("bsc_destroy", "bsc_last_error", "bsc_cnn_destroy"):
             getattr(lib, name).restype = I
@@ -419,6 +431,14 @@ class Context:
         """Blocks of the persistent PCG, in [patches, usable blocks]."""
         self._check(self._lib.bsc_set_pcg_grid(self._h, int(grid)))
 
+    def set_psd_test(self, on=True):
+        """FP64 LDL^T PSD test before the interior spans' eigendecomposition."""
+        self._check(self._lib.bsc_set_psd_test(self._h, int(bool(on))))
+
+    def set_pcg_form(self, form):
+        """PCG form: 0 three group barriers per iteration, 1 the pipelined recurrences with one."""
+        self._check(self._lib.bsc_set_pcg_form(self._h, int(form)))
+
     def pcg_split(self):
         out = (ct.c_int * self.P)()
         self._check(self._lib.bsc_pcg_split(self._h, out))
@@ -431,6 +451,16 @@ class Context:
         on, cap, rep = ct.c_int(), ct.c_int(), ct.c_longlong()
         self._check(self._lib.bsc_graph_state(self._h, ct.byref(on), ct.byref(cap), ct.byref(rep)))
         return {"on": on.value, "captured": cap.value, "replays": rep.value}
+
+    def set_learned_solver(self, cnn):
+        """Newton steps solve with the learned flexible CG of `cnn` (a Cnn of this
+        context), PCG as fallback; None returns to plain PCG."""
+        self._check(self._lib.bsc_set_learned_solver(self._h, None if cnn is None else cnn._h))
+
+    def set_wait_limit(self, spins, extra_blocks=0):
+        """Spin limit of the persistent solvers' bounded barriers; extra_blocks > 0
+        makes every barrier wait out its limit (tests of the timeout path)."""
+        self._check(self._lib.bsc_set_wait_limit(self._h, int(spins), int(extra_blocks)))
 
     def patch_slice(self, t, p):
         """Patch p's columns of a (k, N) tensor (a view)."""
@@ -514,6 +544,18 @@ class Cnn:
         a = np.zeros((self.ctx.N, ch), dtype=np.float32)
         self.ctx._check(self._lib.bsc_cnn_activations(self._h, int(which), a.ctypes.data_as(ct.POINTER(ct.c_float))))
         return a
+
+    def set_stall_window(self, window):
+        """Iterations in which r.r must drop by 4x before the flexible CG falls back to PCG."""
+        self.ctx._check(self._lib.bsc_cnn_set_stall_window(self._h, int(window)))
+
+    def solve_status(self, b, K, rel_tol=1e-8, max_iter=10000, out=None):
+        """Like solve but returns (status, x, report) instead of raising."""
+        out = self.ctx.new_vec() if out is None else out
+        rep = FcgReport()
+        st = self._lib.bsc_solve_fcg(self.ctx._h, self._h, _ptr(K), _ptr(self.ctx._vec(b, "b")),
+                                     _ptr(self.ctx._vec(out, "x")), float(rel_tol), int(max_iter), ct.byref(rep))
+        return st, out, rep.as_dict()
 
     def solve(self, b, K, rel_tol=1e-8, max_iter=10000, out=None):
         out = self.ctx.new_vec() if out is None else out

@@ -68,12 +68,14 @@ void free_ctx(bsc_ctx* c) {
                   c->Dinv, c->partials, c->sync, c->dstatus, c->dscalars, c->pd, c->cp_patch, c->sp_patch,
                   c->span_items, c->red_items, c->red_off, c->pcg_blocks, c->pcg_out, c->steps, c->patch_E,
                   c->pending, c->proj_work, c->proj_span[0], c->proj_span[1], c->proj_kneg[0], c->proj_kneg[1],
-                  c->red_g, c->red_l, c->red_q};
+                  c->red_g, c->red_l, c->red_q, c->fcg_rec, c->proj_cnt, c->proj_sel};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->vec)
     if (p) cudaFree(p);
   for (void* p : c->proj_scratch)
+    if (p) cudaFree(p);
+  for (void* p : c->pcg_pipe)
     if (p) cudaFree(p);
   for (int i = 0; i < 2; ++i) {
     if (c->side[i]) cudaStreamDestroy(c->side[i]);
@@ -170,7 +172,11 @@ cudaError_t enqueue_newton(bsc_ctx* c, void* C, const void* Chat) {
   if ((e = launch_assemble(c, c->K_int)) != cudaSuccess) return e;
   mark(c, 3);
   if ((e = launch_axpy_trial(c, g, g, -2.0, rhs)) != cudaSuccess) return e;  // rhs = -g
-  if ((e = launch_pcg(c, c->K_int, rhs, d, c->pcg_tol, c->pcg_max_iter)) != cudaSuccess) return e;
+  if (c->solver_cnn)
+    e = enqueue_learned_solve(c, c->solver_cnn, c->K_int, rhs, d, c->pcg_tol, c->pcg_max_iter);
+  else
+    e = launch_pcg(c, c->K_int, rhs, d, c->pcg_tol, c->pcg_max_iter);
+  if (e != cudaSuccess) return e;
   mark(c, 4);
   if ((e = launch_step_begin(c, d)) != cudaSuccess) return e;
   if ((e = launch_ls_round(c, C, Chat, d, trial, C, 0)) != cudaSuccess) return e;
@@ -282,6 +288,9 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
   c->max_ls = o->max_line_search > 0 ? o->max_line_search : 30;
   c->stream = (cudaStream_t)stream;
   c->use_graph = 1;
+  c->wait_limit = kWaitLimitDefault;
+  c->barrier_extra = 0u;
+  c->solver_cnn = nullptr;
   for (int k = 0; k < TILE_CLASSES; ++k) c->tile_tu[k] = 0;
 
   bsc_status st = BSC_OK;
@@ -336,6 +345,7 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
   ALLOC(c->steps, sizeof(PatchStep) * count);
   ALLOC(c->patch_E, sizeof(double) * 2 * count);
   ALLOC(c->pending, sizeof(int) * 4);
+  ALLOC(c->fcg_rec, sizeof(double) * 2 * count);
   CREATE_CK(cudaMallocHost((void**)&c->hscalars, sizeof(double) * 16), "cudaMallocHost");
   CREATE_CK(cudaMallocHost((void**)&c->hsteps, sizeof(PatchStep) * count), "cudaMallocHost");
   CREATE_CK(cudaMallocHost((void**)&c->hflags, sizeof(int) * 4), "cudaMallocHost");
@@ -361,6 +371,7 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
   CREATE_CK(cudaMemset(c->nneg, 0, sizeof(int) * Nsp), "memset");
   CREATE_CK(cudaMemset(c->steps, 0, sizeof(PatchStep) * count), "memset");
   CREATE_CK(cudaMemset(c->pending, 0, sizeof(int) * 4), "memset");
+  CREATE_CK(cudaMemset(c->fcg_rec, 0, sizeof(double) * 2 * count), "memset");
   CREATE_CK(launch_build_tables(c), "building quadrature tables");
   CREATE_CK(setup_projection(c), "projection set-up");
   CREATE_CK(setup_span_eval(c), "span evaluation set-up");
@@ -531,6 +542,8 @@ static void fill_report(const bsc_ctx* c, const PatchStep& s, bsc_newton_report&
   r.pcg_iters = (int)s.pcg_iters;
   r.ls_halvings = s.halvings;
   r.spans_projected = (int)s.spans_projected;
+  r.fcg_iters = (int)s.fcg_iters;
+  r.fell_back = s.fell_back != 0.0 ? 1 : 0;
   if (s.state == -2) r.status = BSC_ERR_NUMERIC;
   else if (s.state == -1) r.status = BSC_ERR_LINESEARCH;
   else if (!(s.pcg_res <= c->pcg_tol)) r.status = BSC_ERR_NOT_CONVERGED;
@@ -599,6 +612,8 @@ bsc_status bsc_newton_step(bsc_ctx* c, void* C, const void* Chat, bsc_newton_rep
     agg.pcg_iters = std::max(agg.pcg_iters, r.pcg_iters);
     agg.ls_halvings = std::max(agg.ls_halvings, r.ls_halvings);
     agg.spans_projected += r.spans_projected;
+    agg.fcg_iters = std::max(agg.fcg_iters, r.fcg_iters);
+    agg.fell_back = std::max(agg.fell_back, r.fell_back);
     if (st == BSC_OK && r.status != BSC_OK) st = (bsc_status)r.status;
   }
   if (flags) st = status_error(c, flags, "bsc_newton_step");
@@ -633,6 +648,26 @@ bsc_status bsc_set_material(bsc_ctx* c, int p, const bsc_material* m) {
   CK(cudaMemcpyAsync(c->pd + p, &d, sizeof(PatchDev), cudaMemcpyHostToDevice, c->stream), "bsc_set_material");
   if (rho_changed) CK(launch_lumped_mass_patch(c, p), "bsc_set_material");
   CK(cudaStreamSynchronize(c->stream), "bsc_set_material");
+  return BSC_OK;
+}
+
+bsc_status bsc_set_learned_solver(bsc_ctx* c, bsc_cnn* n) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (n && c->P != 1) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_learned_solver: single-patch contexts only");
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_learned_solver");
+  c->solver_cnn = n;
+  drop_graph(c);
+  return BSC_OK;
+}
+
+bsc_status bsc_set_wait_limit(bsc_ctx* c, long long spins, int extra_blocks) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (spins < 1 || spins > (1ll << 40) || extra_blocks < 0 || extra_blocks > 1)
+    return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_wait_limit: spins must be in [1, 2^40], extra_blocks 0 or 1");
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_wait_limit");
+  c->wait_limit = spins;
+  c->barrier_extra = (unsigned int)extra_blocks;
+  drop_graph(c);
   return BSC_OK;
 }
 
@@ -695,6 +730,23 @@ bsc_status bsc_set_pcg_grid(bsc_ctx* c, int grid) {
   return BSC_OK;
 }
 
+bsc_status bsc_set_psd_test(bsc_ctx* c, int on) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_psd_test");
+  c->proj_psd = on ? 1 : 0;
+  drop_graph(c);
+  return BSC_OK;
+}
+
+bsc_status bsc_set_pcg_form(bsc_ctx* c, int form) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (form != 0 && form != 1) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_pcg_form: form must be 0 or 1");
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_pcg_form");
+  c->pcg_form = form;
+  drop_graph(c);
+  return BSC_OK;
+}
+
 bsc_status bsc_pcg_split(const bsc_ctx* c, int* blocks) {
   if (!c || !blocks) return BSC_ERR_INVALID_ARG;
   std::vector<PcgBlock> tab(c->pcg_grid);
@@ -752,6 +804,26 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
     }
     if (t.tile_tu[cls] >= 0) c->tile_tu[cls] = t.tile_tu[cls];
   }
+  // the PSD test before the interior eigendecomposition: on or off, whole
+  // projection timed on freshly evaluated span Hessians
+  for (int on = 0; on < 2 && st == BSC_OK; ++on) {
+    float best_rep = 1e30f, ms = 0.0f;
+    cudaError_t e = cudaSuccess;
+    c->proj_psd = on;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      e = launch_span_eval(c, C, 1, 1);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      if (e == cudaSuccess) e = launch_project(c);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < best_rep) best_rep = ms;
+    }
+    if (e != cudaSuccess) st = cuda_fail(c, e, "bsc_autotune: timing the PSD test");
+    t.psd_ms[on] = best_rep;
+  }
+  c->proj_psd = t.psd_ms[1] <= t.psd_ms[0] ? 1 : 0;
+  t.psd_test = c->proj_psd;
   // border projection path: time the whole projection (the border class
   // runs beside the interior phase 2 and competes with it for the FP64
   // pipes) with each path, on freshly evaluated span Hessians
@@ -844,14 +916,52 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
       t.pcg_ms[k] = best_rep;
       if (best < 0 || best_rep < t.pcg_ms[best]) best = k;
     }
+    if (e == cudaSuccess && best >= 0) e = set_pcg_grid(c, t.pcg_grid_cand[best]);
+    // the PCG's form at that grid: three group barriers per iteration, or the
+    // pipelined recurrences with one
+    const int form0 = c->pcg_form;
+    for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
+      c->pcg_form = f;
+      float ms = 0.0f, best_rep = 1e30f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(a0, c->stream);
+        if (e == cudaSuccess) e = launch_pcg(c, c->K_int, rhs, x, c->pcg_tol, c->pcg_max_iter);
+        if (e == cudaSuccess) e = cudaEventRecord(a1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(a1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a0, a1);
+        if (rep > 0 && ms < best_rep) best_rep = ms;
+      }
+      t.pcg_form_ms[f] = best_rep;
+      if (e == cudaSuccess) {
+        // a form that did not reach the tolerance, or broke down (the
+        // pipelined recurrences can lose (r, M r) > 0 in FP32), does not
+        // count; its status flag is cleared
+        std::vector<double> o(3 * (size_t)c->P);
+        int flags = 0;
+        e = cudaMemcpy(o.data(), c->pcg_out, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&flags, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && flags) e = cudaMemset(c->dstatus, 0, sizeof(int));
+        if (flags) t.pcg_form_ms[f] = 1e30;
+        for (int p = 0; p < c->P && e == cudaSuccess; ++p)
+          if (!(o[3 * p + 1] <= c->pcg_tol) || !(o[3 * p + 2] > 0.0)) t.pcg_form_ms[f] = 1e30;
+        if (f == 0 && flags) {
+          // the three-barrier form itself failed: report it as before
+          int fl = flags;
+          cudaEventDestroy(a0);
+          cudaEventDestroy(a1);
+          return status_error(c, fl, "bsc_autotune: timing the PCG grid");
+        }
+      }
+    }
+    c->pcg_form = e == cudaSuccess ? (t.pcg_form_ms[1] < t.pcg_form_ms[0] ? 1 : 0) : form0;
     cudaEventDestroy(a0);
     cudaEventDestroy(a1);
-    if (e == cudaSuccess && best >= 0) e = set_pcg_grid(c, t.pcg_grid_cand[best]);
     if (e != cudaSuccess) return cuda_fail(c, e, "bsc_autotune: timing the PCG grid");
     st = check_status(c, "bsc_autotune: timing the PCG grid");
     if (st != BSC_OK) return st;
   }
   t.pcg_grid = c->pcg_grid;
+  t.pcg_form = c->pcg_form;
   if (out) *out = t;
   return BSC_OK;
 }

@@ -61,6 +61,7 @@ struct PcgBlock {
 struct PatchStep {
   double E0, E1, alpha, dir_inf;
   double pcg_iters, pcg_res, pcg_ok, spans_projected;
+  double fcg_iters, fell_back;  // learned solver: flexible-CG iterations, PCG fallback taken
   int state;       // 1 line search pending, 0 accepted, -1 no decrease, -2 aborted
   int halvings;
   int accepted_round;
@@ -122,6 +123,10 @@ struct bsc_ctx {
   double* proj_span[2];     // per-span scratch of each class
   int* proj_kneg[2];        // negative-eigenvalue count per span (class order)
   unsigned int* proj_work;  // [4] work counters
+  int* proj_cnt;            // device [4]: class sizes (interior, border), spans failing the PSD test
+  int* proj_sel;            // device [interior spans]: class positions of the spans failing the PSD test
+  int proj_psd;             // interior class: FP64 LDL^T PSD test first (autotuned)
+  int p0_grid;              // resident grid of the PSD test
   int border_path;          // 0: one warp per border span, 1: one thread per border span
   cudaStream_t side[2];     // forked stream of the border class
   cudaEvent_t fork_ev, join_ev[2];
@@ -157,6 +162,8 @@ struct bsc_ctx {
   PcgBlock* pcg_blocks;  // device [pcg_grid]
   double* pcg_out;    // device [3 P]: iterations, relative residual, ok
   double* pcg_weight; // host [P]: work estimate of each patch's solve (autotuned)
+  int pcg_form;       // 0: three group barriers per iteration, 1: the pipelined form with one (autotuned)
+  void* pcg_pipe[6];  // T [3][N] vectors of the pipelined form: u, w, m (two buffers), s, z
   int red_grid;
 
   // per-patch Newton state
@@ -166,6 +173,17 @@ struct bsc_ctx {
   int* pending;       // device [1]: patches whose line search is pending
 
   int* hflags;        // pinned host [4]: pending line searches, status flags
+
+  // linear solver of the Newton step: block-Jacobi PCG, or (solver_cnn set) the
+  // learned flexible CG with PCG as fallback; fcg_rec (device [2 P]) holds the
+  // flexible CG's iterations and fallback flag of the last learned solve
+  struct bsc_cnn* solver_cnn;
+  double* fcg_rec;
+  // bounded device waits of the persistent solvers: spin limit, and blocks
+  // their barriers expect beyond the launched ones (0; > 0 only to test the
+  // timeout path, see bsc_set_wait_limit)
+  long long wait_limit;
+  unsigned int barrier_extra;
 
   // CUDA graph of one Newton iteration, for the pointers it was captured with
   int use_graph;
@@ -220,6 +238,18 @@ cudaError_t launch_patch_energy(bsc_ctx* c, const void* C, const void* Chat, dou
                                 const PatchStep* gate = nullptr);
 cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y);
 cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit);
+// PCG as the fallback of a learned flexible-CG solve: it reads that solve's
+// result record (iterations, r.r, state) and b.b on the device, returns at
+// once (x = 0) when the flexible CG converged, and otherwise solves K x = b
+// to min(1/2, tol sqrt(b.b / r.r)), the tolerance that finishes the solve.
+cudaError_t launch_pcg_fallback(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit,
+                                const double* fcg_out, const double* bb);
+// The learned flexible CG of the context's solver network (k_cnn.cu): every
+// launch of one solve of K x = b (single-patch FP32 contexts), graph-capturable,
+// PCG fallback included; leaves the combined result in pcg_out (iterations of
+// both solvers, relative residual, ok) and the flexible CG's record in fcg_rec.
+cudaError_t enqueue_learned_solve(bsc_ctx* c, struct bsc_cnn* n, const void* K, const void* b, void* x, double tol,
+                                  int maxit);
 cudaError_t setup_pcg(bsc_ctx* c);
 cudaError_t assign_pcg_blocks(bsc_ctx* c);
 // Sets the PCG grid (clamped to [patches, capacity]) and re-plans the groups.
@@ -276,13 +306,16 @@ __device__ __forceinline__ double block_max(double v, double* sm) {
   return s;
 }
 
+// Spins of 64 ns sleeps a bounded device wait gives up after by default (~2 s).
+constexpr long long kWaitLimitDefault = 1ll << 25;
+
 // Barrier over the `nblocks` co-resident blocks that share (count, gen): the
 // whole grid of a cooperative launch, or one patch's block group of the
-// persistent PCG.  The wait is bounded: after ~2 s the barrier raises
+// persistent PCG.  The wait is bounded: after `limit` spins the barrier raises
 // BSC_STATUS_TIMEOUT_FLAG in *status and returns false (so does every block
 // that sees the flag); callers then leave their loops.
 __device__ __forceinline__ bool group_barrier(unsigned int* count, volatile unsigned int* gen, int* status,
-                                              unsigned int nblocks) {
+                                              unsigned int nblocks, long long limit = kWaitLimitDefault) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -298,7 +331,7 @@ __device__ __forceinline__ bool group_barrier(unsigned int* count, volatile unsi
       } else {
         long long spins = 0;
         while (*gen == g) {
-          if (++spins > (1ll << 25)) {  // ~2 s of 64 ns sleeps
+          if (++spins > limit) {
             atomicOr(status, BSC_STATUS_TIMEOUT_FLAG);
             ok = 0;
             break;
@@ -319,8 +352,9 @@ __device__ __forceinline__ bool group_barrier(unsigned int* count, volatile unsi
   return ok != 0;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, int* status) {
-  return group_barrier(count, gen, status, gridDim.x);
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, int* status,
+                                             long long limit = kWaitLimitDefault, unsigned int extra = 0u) {
+  return group_barrier(count, gen, status, gridDim.x + extra, limit);
 }
 
 // Row alpha (patch-local index) of y = K x in the element type T; K and x

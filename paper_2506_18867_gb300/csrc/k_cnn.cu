@@ -584,7 +584,10 @@ __global__ void k_add_f(int n, const float* __restrict__ a, float* __restrict__ 
 
 struct FcgArgs {
   int nu, nv, P, maxit, window;
-  double stop;                  // tol^2 b.b
+  double tol2;                  // tol^2: the solve stops at r.r <= tol^2 b.b
+  const double* bb;             // b.b (device, computed by the set-up launches)
+  long long wait_limit;         // spins of the bounded grid barriers
+  unsigned int extra;           // blocks the barriers expect beyond the grid (0; > 0 only in tests)
   const float* __restrict__ K;
   const float* __restrict__ A;     // bounded taps [P][16]
   const float* __restrict__ Linv;  // [P][6]
@@ -613,9 +616,21 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
   double* const part1 = F.partial + G;
   double* const part2 = F.partial + 2 * G;
   double* const part3 = F.partial + 3 * G;
-  double best = 0.0, rr = 0.0;
+  double best = 0.0, rr = -1.0;  // r.r < 0: not computed yet (r = b)
   int since = 0, state = 0, it = 0;
   bool ok = true;
+  const double bb = *F.bb, stop = F.tol2 * bb;
+  const long long lim = F.wait_limit;
+  const unsigned int extra = F.extra;
+  if (!(bb > 0.0)) {
+    // b = 0: x = 0 is the solution
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      F.out[0] = 0.0;
+      F.out[1] = 0.0;
+      F.out[2] = 1.0;
+    }
+    return;
+  }
   for (it = 1; it <= F.maxit; ++it) {
     // 1. q = K p, p.q, p.r
     double l_pq = 0.0, l_pr = 0.0;
@@ -637,7 +652,7 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
         part1[blockIdx.x] = a2;
       }
     }
-    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
+    if (!(ok = grid_barrier(cnt, gen, F.status, lim, extra))) break;
     double pq = 0.0, pr = 0.0;
     {
       double s1 = 0.0, s2 = 0.0;
@@ -683,7 +698,7 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
       const double a1 = block_sum<BLOCK>(l_rr, sm);
       if (threadIdx.x == 0) part2[blockIdx.x] = a1;
     }
-    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
+    if (!(ok = grid_barrier(cnt, gen, F.status, lim, extra))) break;
     {
       double s1 = 0.0;
       for (int k = threadIdx.x; k < G; k += BLOCK) s1 += part2[k];
@@ -697,7 +712,7 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
       state = 3;
       break;
     }
-    if (rr <= F.stop) {
+    if (rr <= stop) {
       state = 1;
       break;
     }
@@ -725,7 +740,7 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) F.u[(size_t)c * P + al] = acc[c];
     }
-    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
+    if (!(ok = grid_barrier(cnt, gen, F.status, lim, extra))) break;
     // 4. z = P L^-T B^T u, z.q
     double l_zq = 0.0;
     for (int al = tid; al < P; al += stride) {
@@ -754,7 +769,7 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
       const double a1 = block_sum<BLOCK>(l_zq, sm);
       if (threadIdx.x == 0) part3[blockIdx.x] = a1;
     }
-    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
+    if (!(ok = grid_barrier(cnt, gen, F.status, lim, extra))) break;
     double zq = 0.0;
     {
       double s1 = 0.0;
@@ -773,12 +788,37 @@ __global__ void __launch_bounds__(BLOCK) k_fcg_learned(FcgArgs F) {
         const size_t k = (size_t)c * P + al;
         F.p[k] = F.z[k] + bf * F.p[k];
       }
-    if (!(ok = grid_barrier(cnt, gen, F.status))) break;
+    if (!(ok = grid_barrier(cnt, gen, F.status, lim, extra))) break;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     F.out[0] = (double)(it > F.maxit ? F.maxit : it);
-    F.out[1] = rr;
+    F.out[1] = rr >= 0.0 ? rr : bb;  // a solve that stopped before its first r.r keeps r = b
     F.out[2] = ok ? (double)state : 3.0;
+  }
+}
+
+// Completes a learned solve after its PCG fallback (which solved K d = r for
+// the flexible CG's remaining residual r, or returned d = 0 when the flexible
+// CG had converged): x += d where the fallback ran; one thread writes the
+// combined record (iterations of both solvers, relative residual, ok) to the
+// PCG's result slot that the Newton step reads, and the flexible CG's
+// iterations and fallback flag to rec.
+__global__ void k_fcg_finish(int n3, const double* __restrict__ fout, const double* __restrict__ bbp,
+                             double* __restrict__ pcg_out, const float* __restrict__ d, float* __restrict__ x,
+                             double* __restrict__ rec) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool fell = fout[2] != 1.0;
+  if (fell && k < n3) x[k] += d[k];
+  if (k == 0) {
+    const double bb = *bbp, rr = fout[1];
+    const double fres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    const double pit = fell ? pcg_out[0] : 0.0, pres = fell ? pcg_out[1] : 1.0;
+    const double pok = fell ? pcg_out[2] : 1.0;
+    pcg_out[0] = fout[0] + pit;
+    pcg_out[1] = fell ? pres * fres : fres;
+    pcg_out[2] = pok;
+    rec[0] = fout[0];
+    rec[1] = fell ? 1.0 : 0.0;
   }
 }
 
@@ -822,6 +862,7 @@ struct bsc_cnn {
   double* fpart;               // its reduction partials [4][fcg_grid]
   unsigned int* fsync;         // its barrier words
   double* fout;                // its results: iterations, r.r, state
+  int window;                  // stall window of the flexible CG (iterations)
 };
 
 namespace {
@@ -895,6 +936,21 @@ cudaError_t precondition(bsc_cnn* n, const float* r, float* z) {
   k_pc_B<<<G, B, 0, n->c->stream>>>(n->nu, n->nv, n->A, n->py, n->pu);
   k_pc_BTz<<<G, B, 0, n->c->stream>>>(n->nu, n->nv, n->A, n->Linv, n->c->pinned, n->pu, z);
   return cudaGetLastError();
+}
+
+// Features of the matrix K (diagonal blocks, off-diagonal traces, pin mask),
+// the Cholesky factors of the diagonal blocks and one forward pass of the
+// network: everything that depends on K alone.
+cudaError_t prepare_network(bsc_cnn* n, const void* K) {
+  n->K = (const float*)K;
+  const int B = 256, G = (n->P + B - 1) / B;
+  BSC_COUNT(n->c, 3);
+  k_diag_partials<<<n->red_grid, RB, 0, n->c->stream>>>(n->P, n->K, n->c->pinned, n->red);
+  k_diag_mean<<<1, RB, 0, n->c->stream>>>(n->red_grid, n->red, n->scales);
+  k_matrix_features<<<G, B, 0, n->c->stream>>>(n->P, n->K, n->c->pinned, n->scales, n->X0, n->Linv, n->c->dstatus);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cnn_network(n);
 }
 
 template <int CIN, int COUT>
@@ -984,6 +1040,52 @@ void cnn_free(bsc_cnn* n) {
 
 }  // namespace
 
+// Every launch of one learned solve of K x = b: network on K, x = 0, r = b,
+// b.b, z = M r, p = z, the persistent flexible CG, the PCG fallback (a no-op
+// when the flexible CG converged) and the completion.  No host synchronisation,
+// so a CUDA graph can hold it.
+cudaError_t enqueue_learned_solve(bsc_ctx* c, bsc_cnn* n, const void* K, const void* b, void* x, double tol,
+                                  int maxit) {
+  cudaError_t e;
+  const int N3 = 3 * n->P, B = 256, G3 = (N3 + B - 1) / B;
+  float *r = n->vec[0], *z = n->vec[1], *p = n->vec[2], *d = n->vec[4];
+  float* xx = (float*)x;
+  cudaStream_t s = c->stream;
+  if ((e = prepare_network(n, K)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(xx, 0, sizeof(float) * N3, s)) != cudaSuccess) return e;
+  BSC_COUNT(c, 1);
+  k_copy_f<<<G3, B, 0, s>>>(N3, (const float*)b, r);
+  if ((e = dot(n, r, r, n->dsc + 4)) != cudaSuccess) return e;  // b.b
+  if ((e = precondition(n, r, z)) != cudaSuccess) return e;
+  BSC_COUNT(c, 1);
+  k_copy_f<<<G3, B, 0, s>>>(N3, z, p);
+  FcgArgs F;
+  F.nu = n->nu; F.nv = n->nv; F.P = n->P; F.maxit = maxit; F.window = n->window;
+  F.tol2 = tol * tol; F.bb = n->dsc + 4; F.wait_limit = c->wait_limit; F.extra = c->barrier_extra;
+  F.K = (const float*)K; F.A = n->A; F.Linv = n->Linv; F.pinned = c->pinned;
+  F.x = xx; F.r = r; F.z = z; F.p = p; F.q = n->vec[3]; F.y = n->py; F.u = n->pu;
+  F.partial = n->fpart; F.sync = n->fsync; F.status = c->dstatus; F.out = n->fout;
+  if ((e = cudaMemsetAsync(n->fsync, 0, 4 * sizeof(unsigned int), s)) != cudaSuccess) return e;
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n->fcg_grid);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BSC_COUNT(c, 1);
+    if ((e = cudaLaunchKernelEx(&cfg, k_fcg_learned<256>, F)) != cudaSuccess) return e;
+  }
+  // the fallback: block-Jacobi PCG on the remaining residual r, into d
+  if ((e = launch_pcg_fallback(c, K, r, d, tol, maxit, n->fout, n->dsc + 4)) != cudaSuccess) return e;
+  BSC_COUNT(c, 1);
+  k_fcg_finish<<<G3, B, 0, s>>>(N3, n->fout, n->dsc + 4, c->pcg_out, d, xx, c->fcg_rec);
+  return cudaGetLastError();
+}
+
 extern "C" {
 
 int bsc_cnn_param_count(void) { return param_total(); }
@@ -999,6 +1101,7 @@ bsc_status bsc_cnn_create(bsc_ctx* c, bsc_cnn** out) {
   bsc_cnn* n = (bsc_cnn*)calloc(1, sizeof(bsc_cnn));
   if (!n) return BSC_ERR_OOM;
   n->c = c;
+  n->window = 24;
   n->P = c->N;
   n->nu = c->nu;
   n->nv = c->nv;
@@ -1079,6 +1182,7 @@ bsc_status bsc_cnn_create(bsc_ctx* c, bsc_cnn** out) {
 
 void bsc_cnn_destroy(bsc_cnn* n) {
   if (!n) return;
+  if (n->c->solver_cnn == n) bsc_set_learned_solver(n->c, nullptr);  // the context's Newton step goes back to PCG
   cudaStreamSynchronize(n->c->stream);
   cnn_free(n);
 }
@@ -1104,15 +1208,15 @@ bsc_status bsc_cnn_get_params(bsc_cnn* n, float* host, int count, int which) {
 
 bsc_status bsc_cnn_prepare(bsc_cnn* n, const void* K) {
   if (!n || !K) return BSC_ERR_INVALID_ARG;
-  n->K = (const float*)K;
-  const int B = 256, G = (n->P + B - 1) / B;
-  BSC_COUNT(n->c, 3);
-  k_diag_partials<<<n->red_grid, RB, 0, n->c->stream>>>(n->P, n->K, n->c->pinned, n->red);
-  k_diag_mean<<<1, RB, 0, n->c->stream>>>(n->red_grid, n->red, n->scales);
-  k_matrix_features<<<G, B, 0, n->c->stream>>>(n->P, n->K, n->c->pinned, n->scales, n->X0, n->Linv, n->c->dstatus);
-  CKN(cudaGetLastError(), "bsc_cnn_prepare");
-  CKN(cnn_network(n), "bsc_cnn_prepare");
+  CKN(prepare_network(n, K), "bsc_cnn_prepare");
   return cnn_sync(n, "bsc_cnn_prepare");
+}
+
+bsc_status bsc_cnn_set_stall_window(bsc_cnn* n, int window) {
+  if (!n) return BSC_ERR_INVALID_ARG;
+  if (window < 1 || window > 100000) return cnn_fail(n, BSC_ERR_INVALID_ARG, "bsc_cnn_set_stall_window: window must be in [1, 100000]");
+  n->window = window;
+  return BSC_OK;
 }
 
 bsc_status bsc_cnn_apply(bsc_cnn* n, const void* r, void* z) {
@@ -1168,75 +1272,22 @@ bsc_status bsc_cnn_activations(bsc_cnn* n, int which, float* host) {
 bsc_status bsc_solve_fcg(bsc_ctx* c, bsc_cnn* n, const void* K, const void* b, void* x, double tol, int maxit,
                          bsc_fcg_report* rep) {
   if (!c || !n || n->c != c || !K || !b || !x) return BSC_ERR_INVALID_ARG;
+  if (b == x) return cnn_fail(n, BSC_ERR_INVALID_ARG, "bsc_solve_fcg: b and x must not alias");
   if (!(tol > 0.0)) tol = c->pcg_tol;
   if (maxit <= 0) maxit = c->pcg_max_iter;
   bsc_fcg_report R;
   memset(&R, 0, sizeof(R));
   if (rep) *rep = R;
-  bsc_status st = bsc_cnn_prepare(n, K);
+  CKN(enqueue_learned_solve(c, n, K, b, x, tol, maxit), "bsc_solve_fcg");
+  CKN(cudaMemcpyAsync(n->hsc, c->pcg_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "bsc_solve_fcg");
+  CKN(cudaMemcpyAsync(n->hsc + 4, c->fcg_rec, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+      "bsc_solve_fcg");
+  bsc_status st = cnn_sync(n, "bsc_solve_fcg");
   if (st != BSC_OK) return st;
-  const int N3 = 3 * n->P, B = 256, G3 = (N3 + B - 1) / B;
-  float *r = n->vec[0], *z = n->vec[1], *p = n->vec[2];
-  float* xx = (float*)x;
-  cudaStream_t s = c->stream;
-  CKN(cudaMemsetAsync(xx, 0, sizeof(float) * N3, s), "bsc_solve_fcg");
-  BSC_COUNT(c, 1);
-  k_copy_f<<<G3, B, 0, s>>>(N3, (const float*)b, r);
-  CKN(dot(n, r, r, n->dsc + 4), "bsc_solve_fcg");  // b.b
-  CKN(precondition(n, r, z), "bsc_solve_fcg");
-  BSC_COUNT(c, 1);
-  k_copy_f<<<G3, B, 0, s>>>(N3, z, p);
-  CKN(cudaMemcpyAsync(n->hsc + 4, n->dsc + 4, sizeof(double), cudaMemcpyDeviceToHost, s), "bsc_solve_fcg");
-  if ((st = cnn_sync(n, "bsc_solve_fcg")) != BSC_OK) return st;
-  const double bb = n->hsc[4];
-  if (!(bb > 0.0)) {
-    if (rep) *rep = R;
-    return BSC_OK;
-  }
-  const double stop = tol * tol * bb;
-  // the iterations: one persistent cooperative kernel
-  FcgArgs F;
-  F.nu = n->nu; F.nv = n->nv; F.P = n->P; F.maxit = maxit; F.window = 24; F.stop = stop;
-  F.K = (const float*)K; F.A = n->A; F.Linv = n->Linv; F.pinned = c->pinned;
-  F.x = xx; F.r = r; F.z = z; F.p = p; F.q = n->vec[3]; F.y = n->py; F.u = n->pu;
-  F.partial = n->fpart; F.sync = n->fsync; F.status = c->dstatus; F.out = n->fout;
-  CKN(cudaMemsetAsync(n->fsync, 0, 4 * sizeof(unsigned int), s), "bsc_solve_fcg");
-  {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)n->fcg_grid);
-    cfg.blockDim = dim3(256);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    BSC_COUNT(c, 1);
-    CKN(cudaLaunchKernelEx(&cfg, k_fcg_learned<256>, F), "bsc_solve_fcg");
-  }
-  CKN(cudaMemcpyAsync(n->hsc, n->fout, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "bsc_solve_fcg");
-  if ((st = cnn_sync(n, "bsc_solve_fcg")) != BSC_OK) return st;
-  int it = (int)n->hsc[0];
-  const double rr = n->hsc[1];
-  const int state = (int)n->hsc[2];
-  const bool stalled = state != 1;
-  R.fcg_iters = it > maxit ? maxit : it;
-  R.rel_res = sqrt(rr / bb);
-  if (stalled || !(rr <= stop)) {
-    // fallback: plain block-Jacobi PCG on the remaining residual, x += d
-    R.fell_back = 1;
-    const double tol2 = sqrt(stop / (rr > 0.0 ? rr : stop));
-    float* d = n->vec[4];
-    int pit = 0;
-    double prr = 0.0;
-    st = bsc_solve(c, K, r, d, tol2 < 1.0 ? tol2 : 0.5, maxit, &pit, &prr);
-    if (st != BSC_OK && st != BSC_ERR_NOT_CONVERGED) return st;
-    BSC_COUNT(c, 1);
-    k_add_f<<<G3, B, 0, s>>>(N3, d, xx);
-    R.pcg_iters = pit;
-    R.rel_res = prr * sqrt(rr / bb);
-    CKN(cudaStreamSynchronize(s), "bsc_solve_fcg");
-  }
+  R.fcg_iters = (int)n->hsc[4];
+  R.fell_back = n->hsc[5] != 0.0 ? 1 : 0;
+  R.pcg_iters = (int)n->hsc[0] - R.fcg_iters;
+  R.rel_res = n->hsc[1];
   if (rep) *rep = R;
   if (!(R.rel_res <= tol)) {
     snprintf(c->err, sizeof(c->err), "bsc_solve_fcg: %d + %d iterations, rel. residual %g", R.fcg_iters,

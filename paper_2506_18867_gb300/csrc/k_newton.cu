@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(SB) k_step_items(int N, int n_items, const Red
 __global__ void __launch_bounds__(SB) k_step_begin(int n_items, const int* __restrict__ red_off,
                                                    const double* __restrict__ partial, const double* __restrict__ E0,
                                                    const double* __restrict__ pcg_out, int project,
+                                                   const double* __restrict__ fcg_rec,
                                                    PatchStep* __restrict__ steps, const int* __restrict__ status) {
   __shared__ double sm[SB / 32];
   const int p = blockIdx.x;
@@ -66,6 +67,8 @@ __global__ void __launch_bounds__(SB) k_step_begin(int n_items, const int* __res
     st.pcg_res = pcg_out[3 * p + 1];
     st.pcg_ok = pcg_out[3 * p + 2];
     st.spans_projected = project ? c_tot : 0.0;
+    st.fcg_iters = fcg_rec ? fcg_rec[2 * p] : 0.0;
+    st.fell_back = fcg_rec ? fcg_rec[2 * p + 1] : 0.0;
     const int flags = *(volatile const int*)status;
     st.state = (flags & (BSC_STATUS_TIMEOUT_FLAG | BSC_STATUS_NUMERIC_FLAG)) || !(st.pcg_ok > 0.0) ? -2 : 1;
     st.halvings = 0;
@@ -143,7 +146,8 @@ cudaError_t launch_step_begin(bsc_ctx* c, const void* d) {
     k_step_items<float><<<c->n_red_items, SB, 0, c->stream>>>(c->N, c->n_red_items, c->red_items, c->pd, c->nneg,
                                                               (const float*)d, c->partials);
   k_step_begin<<<c->P, SB, 0, c->stream>>>(c->n_red_items, c->red_off, c->partials, c->patch_E, c->pcg_out,
-                                           c->project_default == BSC_PROJECT_SPAN, c->steps, c->dstatus);
+                                           c->project_default == BSC_PROJECT_SPAN,
+                                           c->solver_cnn ? c->fcg_rec : nullptr, c->steps, c->dstatus);
   return cudaGetLastError();
 }
 

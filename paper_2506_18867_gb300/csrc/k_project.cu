@@ -136,17 +136,19 @@ struct TView {
 // read-modify-write of the Hessian planes, bound by HBM.
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_proj_corr(int count, int Nsp, const int* __restrict__ list, const int* __restrict__ kneg_in,
-                const double* __restrict__ lam, const T* __restrict__ W, T* __restrict__ H) {
+    k_proj_corr(const int* __restrict__ cnt, int cs_, int Nsp, const int* __restrict__ list,
+                const int* __restrict__ sel, const int* __restrict__ kneg_in, const double* __restrict__ lam,
+                const T* __restrict__ W, T* __restrict__ H) {
   constexpr int RM = 8;  // negative eigenvalues kept in registers (more go through the loop below)
   constexpr int CW = 8;  // entries of a row per step
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 27ll * count) return;
+  const int count = *cnt;
+  const size_t cs = (size_t)cs_;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 27ll * count;
+       t += (long long)gridDim.x * blockDim.x) {
   const int a = (int)(t / count), pos = (int)(t - (long long)a * count);
   const int kneg = kneg_in[pos];
-  if (kneg == 0) return;
-  const size_t cs = (size_t)count;
-  const int s = list[pos];
+  if (kneg == 0) continue;
+  const int s = list[sel ? sel[pos] : pos];
   T la[RM];
 #pragma unroll
   for (int r = 0; r < RM; ++r) la[r] = r < kneg ? (T)lam[r * cs + pos] * W[(27 * r + a) * cs + pos] : T(0);
@@ -174,20 +176,27 @@ __global__ void __launch_bounds__(256)
     for (int u = 0; u < CW; ++u)
       if (c0 + u < 27) h[(size_t)(e0 + c0 + u - a) * Nsp] = hv[u] - acc[u];
   }
+  }
 }
 
+template <int BLOCK>
+__device__ __forceinline__ void block_prefix(int v, int* prefix, int* wsum);
+
 // Phase 1: one thread per interior span (uniform work, no barriers).
+// The spans are list[sel[t]] for t < *cnt (sel == nullptr: list[t]); the
+// scratch is indexed by t with stride cs (the class size).
 template <typename T, int D>
 __global__ void __launch_bounds__(P1Block<D>::value, 1)
-    k_proj_p1(ProjArgs<T> P, const int* __restrict__ list, int count, double* __restrict__ sspan,
-              int* __restrict__ kneg_out) {
+    k_proj_p1(ProjArgs<T> P, const int* __restrict__ list, const int* __restrict__ sel, const int* __restrict__ cnt,
+              int cs, double* __restrict__ sspan, int* __restrict__ kneg_out) {
   constexpr int n = 3 * D, NP = n * (n + 1) / 2, B1 = P1Block<D>::value;
   using SS = SpanScratch<D>;
   extern __shared__ __align__(16) double smd[];
   const proj::View A{smd + threadIdx.x, B1};
   const proj::View R{smd + (size_t)NP * B1 + threadIdx.x, B1};
+  const int count = *cnt;
   for (int t = blockIdx.x * B1 + threadIdx.x; t < count; t += gridDim.x * B1) {
-    const int s = list[t];
+    const int s = list[sel ? sel[t] : t];
     const int q0 = P.moff[s], b0 = P.boff[s];
     SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
                    P.boff[s + 1] - b0, P.pd[P.sp_patch[s]].mubd};
@@ -201,11 +210,48 @@ __global__ void __launch_bounds__(P1Block<D>::value, 1)
     P.nneg[s] = kneg;
     if (kneg > 0) {
 #pragma unroll 1
-      for (int e = 0; e < NP; ++e) sspan[(size_t)(SS::A + e) * count + t] = A[e];
+      for (int e = 0; e < NP; ++e) sspan[(size_t)(SS::A + e) * cs + t] = A[e];
 #pragma unroll 1
-      for (int e = 0; e < 3 * n; ++e) sspan[(size_t)(SS::R + e) * count + t] = R[e];
-      sspan[(size_t)SS::TN * count + t] = tn;
+      for (int e = 0; e < 3 * n; ++e) sspan[(size_t)(SS::R + e) * cs + t] = R[e];
+      sspan[(size_t)SS::TN * cs + t] = tn;
     }
+  }
+}
+
+// Phase 0 (the PSD test, interior spans): one thread per span forms H_r and
+// runs the FP64 LDL^T test of proj::ldlt_psd.  Spans that pass keep their
+// Hessian (nneg = 0); the class positions of the others are appended to
+// sel_out (block by block: the order of the blocks' groups varies from run
+// to run, the per-span results do not), and the later phases run on that
+// list only, so no warp carries the eigendecomposition of one span while
+// its other lanes idle.
+template <int D> struct P0Block;
+template <> struct P0Block<5> { static constexpr int value = 224; };  // 224 x 120 doubles = 210 KB
+template <typename T, int D>
+__global__ void __launch_bounds__(P0Block<D>::value, 1)
+    k_proj_p0(ProjArgs<T> P, const int* __restrict__ list, int count, int* __restrict__ sel_out,
+              int* __restrict__ sel_count) {
+  constexpr int B0 = P0Block<D>::value;
+  extern __shared__ __align__(16) double smd[];
+  __shared__ int s_pre[B0 + 1], s_wsum[B0 / 32], s_base;
+  const proj::View A{smd + threadIdx.x, B0};
+  for (int chunk = blockIdx.x; chunk * B0 < count; chunk += gridDim.x) {
+    const int t = chunk * B0 + threadIdx.x;
+    int fail = 0;
+    if (t < count) {
+      const int s = list[t];
+      const int q0 = P.moff[s], b0 = P.boff[s];
+      SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
+                     P.boff[s + 1] - b0, P.pd[P.sp_patch[s]].mubd};
+      proj::span_form<D>(tab, A);
+      fail = proj::ldlt_psd<D>(A, NEG_REL) ? 0 : 1;
+      if (!fail) P.nneg[s] = 0;
+    }
+    block_prefix<B0>(fail, s_pre, s_wsum);
+    if (threadIdx.x == 0) s_base = s_pre[B0] > 0 ? (int)atomicAdd(sel_count, s_pre[B0]) : 0;
+    __syncthreads();
+    if (fail) sel_out[s_base + s_pre[threadIdx.x]] = t;
+    __syncthreads();
   }
 }
 
@@ -260,10 +306,12 @@ constexpr int P2_MINB[2] = {2, 3};
 // much as active ones).
 template <typename T, int D, int MINB, int SB = p2_spans(D)>
 __global__ void __launch_bounds__(P2_BLOCK, MINB)
-    k_proj_p2(ProjArgs<T> P, const int* __restrict__ list, int count, const int* __restrict__ kneg_in,
-              double* __restrict__ sspan, double* __restrict__ slots, unsigned int* __restrict__ work) {
+    k_proj_p2(ProjArgs<T> P, const int* __restrict__ list, const int* __restrict__ sel, const int* __restrict__ cnt,
+              int cs, const int* __restrict__ kneg_in, double* __restrict__ sspan, double* __restrict__ slots,
+              unsigned int* __restrict__ work) {
   constexpr int n = 3 * D;
   using SS = SpanScratch<D>;
+  const int count = *cnt;
   __shared__ int s_kneg[P2_BLOCK], s_cl[P2_BLOCK], s_pre[P2_BLOCK + 1], s_wsum[P2_BLOCK / 32];
   __shared__ int s_base;
   extern __shared__ __align__(16) double s_lu[];  // [4 n][P2_BLOCK]: LU factors of the inverse iteration
@@ -271,8 +319,8 @@ __global__ void __launch_bounds__(P2_BLOCK, MINB)
   const int nslots = gridDim.x * P2_BLOCK;
   const proj::View Ys{slots + blockIdx.x * P2_BLOCK + tid, nslots};
   const proj::View LU{s_lu + tid, P2_BLOCK};
-  auto sv = [&](int t, int off) { return proj::View{sspan + (size_t)off * count + t, count}; };
-  auto wv = [&](int t) { return TView<T>{reinterpret_cast<T*>(sspan + (size_t)SS::W * count) + t, count}; };
+  auto sv = [&](int t, int off) { return proj::View{sspan + (size_t)off * cs + t, cs}; };
+  auto wv = [&](int t) { return TView<T>{reinterpret_cast<T*>(sspan + (size_t)SS::W * cs) + t, cs}; };
   for (;;) {
     if (tid == 0) s_base = (int)atomicAdd(work, (unsigned)SB);
     __syncthreads();
@@ -313,10 +361,11 @@ __global__ void __launch_bounds__(P2_BLOCK, MINB)
       const int k0 = __ffs(mm) - 1;
       const unsigned rest = mm & (mm - 1u);
       const int k1 = rest ? __ffs(rest) - 1 : s_kneg[o];
-      const proj::View Qs = P.rq_per_span ? proj::View{const_cast<double*>(P.rq) + to, count}
+      const int tc = sel ? sel[to] : to;  // the span's position in its class (its basis)
+      const proj::View Qs = P.rq_per_span ? proj::View{const_cast<double*>(P.rq) + tc, cs}
                                           : proj::View{const_cast<double*>(P.rq), 1};
       proj::cluster_vectors_reg<D>(sv(to, SS::R), sv(to, SS::A), Qs, Ys, sv(to, SS::LAM), wv(to), LU,
-                                   sspan[(size_t)SS::TN * count + to], k0, k1 - k0);
+                                   sspan[(size_t)SS::TN * cs + to], k0, k1 - k0);
     }
     __syncthreads();
   }
@@ -396,14 +445,34 @@ constexpr size_t p2_smem() { return sizeof(double) * (size_t)(4 * 3 * D) * P2_BL
 // Class k of the span lists: 0 = interior spans (five derivative vectors,
 // D = 5), 1 = spans at or next to the border (D = 8).  Phase 1 and phase 2
 // can be issued separately (phase < 0: both).
+template <int D>
+constexpr size_t p0_smem() { return sizeof(double) * (size_t)Smem<D>::NP * P0Block<D>::value; }
+
+// Class k of the span lists: 0 = interior spans (five derivative vectors,
+// D = 5), 1 = spans at or next to the border (D = 8).  Phase 1 and phase 2
+// can be issued separately (phase < 0: both).  With the PSD test (interior
+// class, c->proj_psd), phase 0 runs first and the later phases run on the
+// spans that failed it.
 template <typename T, int D>
 cudaError_t run_class(bsc_ctx* c, int k, const int* list, int count, cudaStream_t st, int phase = -1) {
   if (count <= 0) return cudaSuccess;
   cudaError_t e;
   ProjArgs<T> P = proj_args<T>(c, k);
+  const bool psd = k == 0 && c->proj_psd;
+  const int* sel = psd ? c->proj_sel : nullptr;
+  const int* cnt = c->proj_cnt + (psd ? 2 : k);
   if (phase != 1) {
+    if (psd) {
+      if constexpr (D == 5) {
+        if ((e = cudaMemsetAsync(c->proj_cnt + 2, 0, sizeof(int), st)) != cudaSuccess) return e;
+        BSC_COUNT(c, 1);
+        k_proj_p0<T, D><<<c->p0_grid, P0Block<D>::value, p0_smem<D>(), st>>>(P, list, count, c->proj_sel,
+                                                                            c->proj_cnt + 2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
+    }
     BSC_COUNT(c, 1);
-    k_proj_p1<T, D><<<c->proj_grid[k][0], P1Block<D>::value, p1_smem<D>(), st>>>(P, list, count,
+    k_proj_p1<T, D><<<c->proj_grid[k][0], P1Block<D>::value, p1_smem<D>(), st>>>(P, list, sel, cnt, count,
                                                                                    c->proj_span[k], c->proj_kneg[k]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -413,18 +482,21 @@ cudaError_t run_class(bsc_ctx* c, int k, const int* list, int count, cudaStream_
     const int v = k == 0 ? c->p2_variant : 0;
     if (v == 0)
       k_proj_p2<T, D, P2_MINB[0]><<<c->p2_grid[k][0], P2_BLOCK, p2_smem<D>(), st>>>(
-          P, list, count, c->proj_kneg[k], c->proj_span[k], c->proj_scratch[k], c->proj_work + k);
+          P, list, sel, cnt, count, c->proj_kneg[k], c->proj_span[k], c->proj_scratch[k], c->proj_work + k);
     else
       k_proj_p2<T, D, P2_MINB[1]><<<c->p2_grid[k][1], P2_BLOCK, p2_smem<D>(), st>>>(
-          P, list, count, c->proj_kneg[k], c->proj_span[k], c->proj_scratch[k], c->proj_work + k);
+          P, list, sel, cnt, count, c->proj_kneg[k], c->proj_span[k], c->proj_scratch[k], c->proj_work + k);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     BSC_COUNT(c, 1);
     using SS = SpanScratch<D>;
     const double* sp = c->proj_span[k];
     const long long nthreads = 27ll * count;
-    k_proj_corr<T><<<(unsigned)((nthreads + 255) / 256), 256, 0, st>>>(
-        count, c->Nsp, list, c->proj_kneg[k], sp + (size_t)SS::LAM * count,
-        reinterpret_cast<const T*>(sp + (size_t)SS::W * count), (T*)c->H_span);
+    long long blocks = (nthreads + 255) / 256;
+    if (blocks > 32ll * c->num_sms) blocks = 32ll * c->num_sms;  // grid-stride beyond that
+    k_proj_corr<T><<<(unsigned)blocks, 256, 0, st>>>(cnt, count, c->Nsp, list, sel, c->proj_kneg[k],
+                                                     sp + (size_t)SS::LAM * count,
+                                                     reinterpret_cast<const T*>(sp + (size_t)SS::W * count),
+                                                     (T*)c->H_span);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -491,6 +563,21 @@ cudaError_t p2_grid_of(bsc_ctx* c, int count, int* grid) {
 template <typename T, int D>
 cudaError_t setup_class(bsc_ctx* c, int k, int count) {
   cudaError_t e;
+  if constexpr (D == 5) {
+    if ((e = cudaFuncSetAttribute(k_proj_p0<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)p0_smem<D>())) != cudaSuccess)
+      return e;
+    int per0 = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per0, k_proj_p0<T, D>, P0Block<D>::value,
+                                                           p0_smem<D>())) != cudaSuccess)
+      return e;
+    per0 = per0 < 1 ? 1 : per0;
+    int g0 = per0 * c->num_sms;
+    const int need0 = (count + P0Block<D>::value - 1) / P0Block<D>::value;
+    if (g0 > need0) g0 = need0;
+    c->p0_grid = g0 < 1 ? 1 : g0;
+    if ((e = cudaMalloc(&c->proj_sel, sizeof(int) * (size_t)(count > 0 ? count : 1))) != cudaSuccess) return e;
+  }
   if ((e = cudaFuncSetAttribute(k_proj_p1<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)p1_smem<D>())) != cudaSuccess)
     return e;
@@ -549,6 +636,14 @@ cudaError_t setup_projection(bsc_ctx* c) {
   // the border spans fill the resident warps a few times over at most
   c->border_path = n1 > 8 * 8 * c->num_sms ? 1 : 0;
   if ((e = cudaMalloc(&c->proj_work, sizeof(unsigned int) * 4)) != cudaSuccess) return e;
+  {
+    // the class sizes as device counts (the phase kernels read their span
+    // count from the device: the PSD test's compacted count, or these)
+    const int h[4] = {n0, n1, 0, 0};
+    if ((e = cudaMalloc(&c->proj_cnt, sizeof(int) * 4)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(c->proj_cnt, h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  }
+  c->proj_psd = 1;
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
     if ((e = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming)) != cudaSuccess) return e;

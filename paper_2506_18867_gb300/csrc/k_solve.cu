@@ -110,6 +110,10 @@ struct PcgArgs {
   unsigned int* sync;            // [2 per patch]: barrier count, generation
   int* status;
   double* out;                   // [3 per patch]: iterations, relative residual, ok
+  long long wait_limit;          // spins of the bounded group barriers
+  unsigned int extra;            // blocks the barriers expect beyond the group (0; > 0 only in tests)
+  const double* gate;            // fallback of a learned solve: its (iterations, r.r, state), else nullptr
+  const double* gate_bb;         //   and its b.b
 };
 
 // Sum of part[0..n) in a fixed order (all threads get the result).
@@ -148,7 +152,28 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
   const int tid = rank * BLOCK + threadIdx.x, stride = gsize * BLOCK;
   unsigned int* cnt = A.sync + 2 * pp;
   volatile unsigned int* gen = A.sync + 2 * pp + 1;
-  const unsigned int nb = (unsigned int)gsize;
+  const unsigned int nb = (unsigned int)gsize + A.extra;
+  const long long lim = A.wait_limit;
+  double tol = A.tol;
+  if (A.gate) {
+    // fallback of a learned flexible CG: nothing to do when it converged
+    // (state 1); otherwise finish its remaining residual b
+    const double state = A.gate[2], rr0 = A.gate[1], bb0 = *A.gate_bb;
+    if (state == 1.0) {
+      for (int al = tid; al < Np; al += stride)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A.x[cp0 + c * N + al] = T(0);
+      if (rank == 0 && threadIdx.x == 0) {
+        double* o = A.out + 3 * pp;
+        o[0] = 0.0;
+        o[1] = 0.0;
+        o[2] = 1.0;
+      }
+      return;
+    }
+    const double t = rr0 > 0.0 ? A.tol * sqrt(bb0 / rr0) : 0.5;
+    tol = t < 0.5 ? t : 0.5;
+  }
   // the patch's slice of every plane
   const T* __restrict__ K = A.K + cp0;
   const T* __restrict__ Dinv = A.Dinv + cp0;
@@ -188,10 +213,18 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
       part1[rank] = s2;
     }
   }
-  if (!group_barrier(cnt, gen, A.status, nb)) return;
+  if (!group_barrier(cnt, gen, A.status, nb, lim)) {
+    if (rank == 0 && threadIdx.x == 0) {
+      double* o = A.out + 3 * pp;
+      o[0] = 0.0;
+      o[1] = 1.0;
+      o[2] = 0.0;
+    }
+    return;
+  }
   double rz = group_sum<BLOCK>(part0, gsize, sm);
   const double bb = group_sum<BLOCK>(part1, gsize, sm);
-  const double stop2 = A.tol * A.tol * bb;
+  const double stop2 = tol * tol * bb;
   int it = 0;
   double rr_glob = bb;
   bool ok = true;
@@ -211,7 +244,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
         const double s = block_sum<BLOCK>(l_pq, sm);
         if (threadIdx.x == 0) part2[rank] = s;
       }
-      if (!(ok = group_barrier(cnt, gen, A.status, nb))) break;
+      if (!(ok = group_barrier(cnt, gen, A.status, nb, lim))) break;
       const double pq = group_sum<BLOCK>(part2, gsize, sm);
       if (!(pq > 0.0) || !isfinite(pq)) {
         if (threadIdx.x == 0 && rank == 0) atomicOr(A.status, BSC_STATUS_NUMERIC_FLAG);
@@ -245,7 +278,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
           part1[rank] = s2;
         }
       }
-      if (!(ok = group_barrier(cnt, gen, A.status, nb))) break;
+      if (!(ok = group_barrier(cnt, gen, A.status, nb, lim))) break;
       const double rz2 = group_sum<BLOCK>(part0, gsize, sm);
       rr_glob = group_sum<BLOCK>(part1, gsize, sm);
       if (rr_glob <= stop2 || !isfinite(rr_glob)) break;
@@ -255,11 +288,223 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
       for (int al = tid; al < Np; al += stride)
 #pragma unroll
         for (int c = 0; c < 3; ++c) pv[c * N + al] = zv[c * N + al] + tb * pv[c * N + al];
-      if (!(ok = group_barrier(cnt, gen, A.status, nb))) break;
+      if (!(ok = group_barrier(cnt, gen, A.status, nb, lim))) break;
     }
   }
   if (rank == 0 && threadIdx.x == 0) {
     double* o = A.out + 3 * pp;
+    o[0] = (double)(it > A.maxit ? A.maxit : it);
+    o[1] = bb > 0.0 ? sqrt(rr_glob / bb) : 0.0;
+    o[2] = ok ? 1.0 : 0.0;
+  }
+}
+
+// The pipelined form of the same block-Jacobi PCG (Ghysels & Vanroose 2014,
+// "Hiding global synchronization latency in the preconditioned conjugate
+// gradient algorithm"): with u = M r, w = K u, m = M w, n = K m carried by
+// recurrences, the three dot products of an iteration, (r, u), (w, u) and
+// (r, r), are formed in one pass and need one group barrier, which also
+// publishes m for the next product.  Per iteration and row:
+//   n = K m;  z = n + b z;  q = m + b q;  s = w + b s;  p = u + b p;
+//   x += a p;  r -= a s;  u -= a q;  w -= a z;  m' = M w  (into the other m buffer)
+// with b = g / g_old, a = g / (d - b g / a_old), g = (r, u), d = (w, u).
+// m is double-buffered: the rows of a group read their neighbours' m while
+// other rows already write the next one.  Mathematically the iterates are
+// those of k_pcg; rounding differs (the recurrences drift from the true
+// residual a little faster).  Two barriers set up u and w; then one per
+// iteration instead of three.
+template <typename T>
+struct PipeVecs {
+  T* __restrict__ u;
+  T* __restrict__ w;
+  T* __restrict__ m0;
+  T* __restrict__ m1;
+  T* __restrict__ s;
+  T* __restrict__ z2;   // z of the recurrences (K m carried)
+};
+
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_pcg_pipe(PcgArgs<T> A, PipeVecs<T> V) {
+  __shared__ double sm[BLOCK / 32];
+  const int G = gridDim.x, N = A.N;
+  int pp = 0, rank = blockIdx.x, gsize = G, gfirst = 0;
+  if (A.blocks) {
+    const PcgBlock bk = A.blocks[blockIdx.x];
+    pp = bk.p; rank = bk.rank; gsize = bk.size; gfirst = bk.first;
+  }
+  int nu = A.nu, nv = A.nv, cp0 = 0;
+  if (A.pd) {
+    nu = A.pd[pp].nu; nv = A.pd[pp].nv; cp0 = A.pd[pp].cp0;
+  }
+  const int Np = nu * nv;
+  const int tid = rank * BLOCK + threadIdx.x, stride = gsize * BLOCK;
+  unsigned int* cnt = A.sync + 2 * pp;
+  volatile unsigned int* gen = A.sync + 2 * pp + 1;
+  const unsigned int nb = (unsigned int)gsize + A.extra;
+  const long long lim = A.wait_limit;
+  double tol = A.tol;
+  if (A.gate) {
+    const double state = A.gate[2], rr0 = A.gate[1], bb0 = *A.gate_bb;
+    if (state == 1.0) {
+      for (int al = tid; al < Np; al += stride)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A.x[cp0 + c * N + al] = T(0);
+      if (rank == 0 && threadIdx.x == 0) {
+        double* o = A.out + 3 * pp;
+        o[0] = 0.0;
+        o[1] = 0.0;
+        o[2] = 1.0;
+      }
+      return;
+    }
+    const double t = rr0 > 0.0 ? A.tol * sqrt(bb0 / rr0) : 0.5;
+    tol = t < 0.5 ? t : 0.5;
+  }
+  const T* __restrict__ K = A.K + cp0;
+  const T* __restrict__ Dinv = A.Dinv + cp0;
+  const T* __restrict__ bv = A.b + cp0;
+  T* __restrict__ xv = A.x + cp0;
+  T* __restrict__ rv = A.r + cp0;
+  T* __restrict__ pv = A.p + cp0;
+  T* __restrict__ qv = A.q + cp0;
+  T* __restrict__ uv = V.u + cp0;
+  T* __restrict__ wv = V.w + cp0;
+  T* __restrict__ sv = V.s + cp0;
+  T* __restrict__ zv = V.z2 + cp0;
+  T* mb[2] = {V.m0 + cp0, V.m1 + cp0};
+  double* const part0 = A.partial + gfirst;
+  double* const part1 = A.partial + G + gfirst;
+  double* const part2 = A.partial + 2 * G + gfirst;
+  double* const o = A.out + 3 * pp;
+  auto fail_out = [&]() {
+    if (rank == 0 && threadIdx.x == 0) {
+      o[0] = 0.0;
+      o[1] = 1.0;
+      o[2] = 0.0;
+    }
+  };
+
+  // x = 0, r = b, u = M r; the recurrence vectors start at zero
+  for (int al = tid; al < Np; al += stride) {
+    T rr[3], uu[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      xv[c * N + al] = T(0);
+      pv[c * N + al] = T(0);
+      qv[c * N + al] = T(0);
+      sv[c * N + al] = T(0);
+      zv[c * N + al] = T(0);
+      rr[c] = bv[c * N + al];
+      rv[c * N + al] = rr[c];
+    }
+    apply_dinv<T>(Dinv, N, al, rr, uu);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) uv[c * N + al] = uu[c];
+  }
+  if (!group_barrier(cnt, gen, A.status, nb, lim)) {
+    fail_out();
+    return;
+  }
+  // w = K u, m = M w, and the first dot products
+  {
+    double l_g = 0.0, l_d = 0.0, l_r = 0.0;
+    for (int al = tid; al < Np; al += stride) {
+      T ww[3], mm[3];
+      spmv_row<T>(nu, nv, N, al, K, uv, ww);
+      apply_dinv<T>(Dinv, N, al, ww, mm);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        wv[c * N + al] = ww[c];
+        mb[0][c * N + al] = mm[c];
+        const double r_ = (double)rv[c * N + al], u_ = (double)uv[c * N + al];
+        l_g += r_ * u_;
+        l_d += (double)ww[c] * u_;
+        l_r += r_ * r_;
+      }
+    }
+    const double s1 = block_sum<BLOCK>(l_g, sm), s2 = block_sum<BLOCK>(l_d, sm), s3 = block_sum<BLOCK>(l_r, sm);
+    if (threadIdx.x == 0) {
+      part0[rank] = s1;
+      part1[rank] = s2;
+      part2[rank] = s3;
+    }
+  }
+  if (!group_barrier(cnt, gen, A.status, nb, lim)) {
+    fail_out();
+    return;
+  }
+  double gam = group_sum<BLOCK>(part0, gsize, sm);
+  double del = group_sum<BLOCK>(part1, gsize, sm);
+  const double bb = group_sum<BLOCK>(part2, gsize, sm);
+  const double stop2 = tol * tol * bb;
+  double rr_glob = bb, gam_old = 1.0, alpha_old = 1.0;
+  int it = 0, cur = 0;
+  bool ok = true;
+  if (bb > 0.0) {
+    for (it = 1; it <= A.maxit; ++it) {
+      double beta = 0.0, den = del;
+      if (it > 1) {
+        beta = gam / gam_old;
+        den = del - beta * gam / alpha_old;
+      }
+      if (!(den > 0.0) || !isfinite(den) || !(gam > 0.0)) {
+        if (threadIdx.x == 0 && rank == 0) atomicOr(A.status, BSC_STATUS_NUMERIC_FLAG);
+        ok = false;
+        break;
+      }
+      const double alpha = gam / den;
+      const T ta = (T)alpha, tb = (T)beta;
+      const T* __restrict__ mc = mb[cur];
+      T* __restrict__ mn = mb[cur ^ 1];
+      double l_g = 0.0, l_d = 0.0, l_r = 0.0;
+      for (int al = tid; al < Np; al += stride) {
+        T nn[3];
+        spmv_row<T>(nu, nv, N, al, K, mc, nn);
+        T ww[3], uu[3], rr_[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int k = c * N + al;
+          const T z_ = nn[c] + tb * zv[k];
+          const T q_ = mc[k] + tb * qv[k];
+          const T s_ = wv[k] + tb * sv[k];
+          const T p_ = uv[k] + tb * pv[k];
+          zv[k] = z_; qv[k] = q_; sv[k] = s_; pv[k] = p_;
+          xv[k] += ta * p_;
+          rr_[c] = rv[k] - ta * s_;
+          uu[c] = uv[k] - ta * q_;
+          ww[c] = wv[k] - ta * z_;
+          rv[k] = rr_[c]; uv[k] = uu[c]; wv[k] = ww[c];
+        }
+        T mm[3];
+        apply_dinv<T>(Dinv, N, al, ww, mm);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          mn[c * N + al] = mm[c];
+          l_g += (double)rr_[c] * (double)uu[c];
+          l_d += (double)ww[c] * (double)uu[c];
+          l_r += (double)rr_[c] * (double)rr_[c];
+        }
+      }
+      {
+        const double s1 = block_sum<BLOCK>(l_g, sm), s2 = block_sum<BLOCK>(l_d, sm),
+                     s3 = block_sum<BLOCK>(l_r, sm);
+        if (threadIdx.x == 0) {
+          part0[rank] = s1;
+          part1[rank] = s2;
+          part2[rank] = s3;
+        }
+      }
+      if (!(ok = group_barrier(cnt, gen, A.status, nb, lim))) break;
+      gam_old = gam;
+      alpha_old = alpha;
+      gam = group_sum<BLOCK>(part0, gsize, sm);
+      del = group_sum<BLOCK>(part1, gsize, sm);
+      rr_glob = group_sum<BLOCK>(part2, gsize, sm);
+      cur ^= 1;
+      if (rr_glob <= stop2 || !isfinite(rr_glob)) break;
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) {
     o[0] = (double)(it > A.maxit ? A.maxit : it);
     o[1] = bb > 0.0 ? sqrt(rr_glob / bb) : 0.0;
     o[2] = ok ? 1.0 : 0.0;
@@ -278,22 +523,36 @@ constexpr int PCG_BLOCK = 256;
 // need) through the extended launch API, so that it can be captured in a
 // CUDA graph.
 template <typename T>
-cudaError_t launch_coop(int grid, PcgArgs<T> A, cudaStream_t st) {
+cudaLaunchConfig_t coop_config(int grid, cudaStream_t st, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(PCG_BLOCK);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <typename T>
+cudaError_t launch_coop(int grid, PcgArgs<T> A, cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = coop_config<T>(grid, st, attr);
   return cudaLaunchKernelEx(&cfg, k_pcg<T, PCG_BLOCK>, A);
 }
 
 template <typename T>
-cudaError_t pcg_t(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit) {
+cudaError_t launch_coop_pipe(int grid, PcgArgs<T> A, PipeVecs<T> V, cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = coop_config<T>(grid, st, attr);
+  return cudaLaunchKernelEx(&cfg, k_pcg_pipe<T, PCG_BLOCK>, A, V);
+}
+
+template <typename T>
+cudaError_t pcg_t(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit,
+                  const double* gate = nullptr, const double* gate_bb = nullptr) {
   const int N = c->N;
   cudaError_t e;
   if ((e = cudaMemsetAsync(c->sync, 0, sizeof(unsigned int) * 2 * (size_t)c->P, c->stream)) != cudaSuccess) return e;
@@ -304,6 +563,14 @@ cudaError_t pcg_t(bsc_ctx* c, const void* K, const void* b, void* x, double tol,
   A.K = (const T*)K; A.Dinv = (const T*)c->Dinv; A.b = (const T*)b; A.x = (T*)x;
   A.r = (T*)c->vec[1]; A.z = (T*)c->vec[2]; A.p = (T*)c->vec[3]; A.q = (T*)c->vec[4];
   A.partial = c->partials; A.sync = c->sync; A.status = c->dstatus; A.out = c->pcg_out;
+  A.wait_limit = c->wait_limit; A.extra = c->barrier_extra;
+  A.gate = gate; A.gate_bb = gate_bb;
+  if (c->pcg_form == 1) {
+    PipeVecs<T> V;
+    V.u = (T*)c->pcg_pipe[0]; V.w = (T*)c->pcg_pipe[1]; V.m0 = (T*)c->pcg_pipe[2]; V.m1 = (T*)c->pcg_pipe[3];
+    V.s = (T*)c->pcg_pipe[4]; V.z2 = (T*)c->pcg_pipe[5];
+    return launch_coop_pipe<T>(c->pcg_grid, A, V, c->stream);
+  }
   return launch_coop<T>(c->pcg_grid, A, c->stream);
 }
 
@@ -346,11 +613,17 @@ extern "C" int bsc_plan_blocks(int count, const int* n_cp, const double* work, i
 // threads per SM keep enough of them in flight), capped by what the patches
 // can use; per-patch work estimates start at the control-point counts.
 cudaError_t setup_pcg(bsc_ctx* c) {
-  int per_sm = 0;
+  int per_sm = 0, per_pipe = 0;
   cudaError_t e = c->precision == BSC_FP64
                       ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<double, PCG_BLOCK>, PCG_BLOCK, 0)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<float, PCG_BLOCK>, PCG_BLOCK, 0);
   if (e != cudaSuccess) return e;
+  e = c->precision == BSC_FP64
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_pipe, k_pcg_pipe<double, PCG_BLOCK>, PCG_BLOCK, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_pipe, k_pcg_pipe<float, PCG_BLOCK>, PCG_BLOCK, 0);
+  if (e != cudaSuccess) return e;
+  // one grid serves both forms: the co-resident capacity of the more demanding one
+  if (per_pipe < per_sm) per_sm = per_pipe;
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 4) per_sm = 4;
   const int cap = c->num_sms * per_sm;
@@ -365,6 +638,9 @@ cudaError_t setup_pcg(bsc_ctx* c) {
   for (int p = 0; p < c->P; ++p) c->pcg_weight[p] = (double)c->hpd[p].N;
   if ((e = cudaMalloc(&c->pcg_blocks, sizeof(PcgBlock) * cap)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->pcg_out, sizeof(double) * 3 * c->P)) != cudaSuccess) return e;
+  for (int k = 0; k < 6; ++k)
+    if ((e = cudaMalloc(&c->pcg_pipe[k], c->tsize * 3 * (size_t)c->N)) != cudaSuccess) return e;
+  c->pcg_form = 0;
   return assign_pcg_blocks(c);
 }
 
@@ -417,6 +693,13 @@ cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double
   BSC_COUNT(c, 2);
   if (c->precision == BSC_FP64) return pcg_t<double>(c, K, b, x, tol, maxit);
   return pcg_t<float>(c, K, b, x, tol, maxit);
+}
+
+cudaError_t launch_pcg_fallback(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit,
+                                const double* fcg_out, const double* bb) {
+  BSC_COUNT(c, 2);
+  if (c->precision == BSC_FP64) return pcg_t<double>(c, K, b, x, tol, maxit, fcg_out, bb);
+  return pcg_t<float>(c, K, b, x, tol, maxit, fcg_out, bb);
 }
 
 cudaError_t launch_axpy_trial(bsc_ctx* c, const void* C, const void* d, double alpha, void* out) {
@@ -483,8 +766,9 @@ cudaError_t static_solve_t(int nu, int nv, double* scratch, const void* K, const
   unsigned int* sync = reinterpret_cast<unsigned int*>(tail);  // 4 words
   int* status = reinterpret_cast<int*>(tail + 2);                // 1 word
   double* outd = tail + 4;                                        // 3 doubles
-  // the barrier words and the status must start at zero on every call
-  if ((e = cudaMemsetAsync(tail, 0, 4 * sizeof(double), st)) != cudaSuccess) return e;
+  // the barrier words, the status and the result scalars start at zero on
+  // every call (a solve that stops early must not report the last call's results)
+  if ((e = cudaMemsetAsync(tail, 0, 7 * sizeof(double), st)) != cudaSuccess) return e;
   k_block_jacobi<T><<<(N + 255) / 256, 256, 0, st>>>(N, (const T*)K, Dinv, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   PcgArgs<T> A;
@@ -493,14 +777,13 @@ cudaError_t static_solve_t(int nu, int nv, double* scratch, const void* K, const
   A.K = (const T*)K; A.Dinv = Dinv; A.b = (const T*)b; A.x = (T*)x;
   A.r = r; A.z = z; A.p = p; A.q = q;
   A.partial = partial; A.sync = sync; A.status = status; A.out = outd;
+  A.wait_limit = kWaitLimitDefault; A.extra = 0u; A.gate = nullptr; A.gate_bb = nullptr;
   e = launch_coop<T>(grid, A, st);
   if (e != cudaSuccess) return e;
-  double stat_d = 0.0;
   if ((e = cudaMemcpyAsync(out_host, outd, 3 * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
   int flags = 0;
   if ((e = cudaMemcpyAsync(&flags, status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-  (void)stat_d;
   out_host[3] = (double)flags;
   return cudaSuccess;
 }

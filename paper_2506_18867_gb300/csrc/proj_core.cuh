@@ -287,14 +287,12 @@ BSC_HD int span_basis(const Tab& tab, const QView& Q, double rank_rel) {
   return d;
 }
 
-// Phase 1 of a span: reduced Hessian, tridiagonal form, inertia.
-// Tab: nm(), nb(), wb(q) = W mu_bd, a6(q, e) (packed upper 6x6), gr(q, k,
-// beta) and lr(q, k): the derivative vectors g_q,beta and L_q in the span's
-// reduced basis.  On return R holds the scaled tridiagonal (d, e, e^2), A
-// the reflectors, *tn the scale; returns the number of eigenvalues below
-// -neg_rel ||T|| (-1 on a non-finite matrix).
+// The reduced Hessian H_r of a span into A (packed lower triangle, index
+// 3k + c for reduced vector k and component c).  Tab: nm(), nb(), wb(q) =
+// W mu_bd, a6(q, e) (packed upper 6x6), gr(q, k, beta) and lr(q, k): the
+// derivative vectors g_q,beta and L_q in the span's reduced basis.
 template <int D, class Tab>
-BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* tn_out, double neg_rel) {
+BSC_PHASE void span_form(const Tab& tab, const View& A) {
   constexpr int n = 3 * D;
   constexpr int NP = n * (n + 1) / 2;
 #pragma unroll 1
@@ -358,6 +356,61 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* 
         }
     }
   }
+}
+
+// The PSD test that precedes the eigendecomposition: an LDL^T factorisation
+// of H_r + tau I in FP64, tau = neg_rel ||H_r||_inf, in place in A.  Every
+// pivot positive means H_r + tau I is positive definite (the factorisation's
+// backward error, about n eps ||H_r||, is several times smaller than tau),
+// so no eigenvalue of H_r lies below -tau and the span needs no projection.
+// A non-positive or non-finite pivot fails the test; the span then goes
+// through the eigendecomposition, which decides (with its own threshold on
+// the same scale) which eigenvalues to clamp.  Destroys A.  Returns true
+// when the test passes.
+template <int D>
+BSC_PHASE bool ldlt_psd(const View& A, double neg_rel) {
+  constexpr int n = 3 * D;
+  double nrm = 0.0;
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    double r = 0.0;
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) r += fabs(A[lp(i, j)]);
+    nrm = fmax(nrm, r);
+  }
+  if (!(nrm > 0.0)) return nrm == 0.0;  // the zero matrix is PSD; NaN fails
+  const double tau = neg_rel * nrm;
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) A[lp(i, i)] += tau;
+  // right-looking LDL^T: A(i, j) -= l_ik A(j, k) over the trailing block,
+  // l_ik = A(i, k) / d_k; the multipliers are not kept
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    const double dk = A[lp(k, k)];
+    if (!(dk > 0.0) || !isfinite(dk)) return false;
+    const double r = 1.0 / dk;
+#pragma unroll 1
+    for (int i = k + 1; i < n; ++i) {
+      const int ri = i * (i + 1) / 2;
+      const double l = A[ri + k] * r;
+#pragma unroll 1
+      for (int j = k + 1; j <= i; ++j) A[ri + j] = fma(-l, A[j * (j + 1) / 2 + k], A[ri + j]);
+    }
+  }
+  return true;
+}
+
+// Phase 1 of a span: reduced Hessian (span_form), then span_tridiag.
+template <int D, class Tab>
+BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* tn_out, double neg_rel);
+
+// Tridiagonal form and inertia of the reduced Hessian in A.  On return R
+// holds the scaled tridiagonal (d, e, e^2), A the reflectors, *tn the
+// scale; returns the number of eigenvalues below -neg_rel ||T|| (-1 on a
+// non-finite matrix).
+template <int D>
+BSC_PHASE int span_tridiag(const View& A, const View& R, double* tn_out, double neg_rel) {
+  constexpr int n = 3 * D;
   // 2. Householder tridiagonalisation: d -> R[0..n), e -> R[n..2n); the
   //    reflector v_k stays in column k of A, p = tau A v in R[2n..3n).
   //    Operands come from shared memory: the FP64 pipe, not the loads, is
@@ -433,6 +486,12 @@ BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* 
     R[2 * n + i] = es * es;
   }
   return sturm<n>(R, -neg_rel);
+}
+
+template <int D, class Tab>
+BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* tn_out, double neg_rel) {
+  span_form<D>(tab, A);
+  return span_tridiag<D>(A, R, tn_out, neg_rel);
 }
 
 // ---------------------------------------------------------------------------

@@ -278,6 +278,99 @@ def config_learned(seed: int = 1, n: int = 512, size_m: float = 1.0) -> Patch:
                  {"seed": seed, "ratio": ratio, "span_m": span})
 
 
+def distorted_rest(kind: str, param: float, nu: int, nv: int, size_m: float = 1.0) -> np.ndarray:
+    """Rest control points of the three distortion families of the paper's
+    non-rectangular-domain study (Sec. 6): Greville-placed control points of
+    the unit square mapped to
+      "aspect"  a size x (param * size) rectangle (aspect ratio 1:param);
+      "skew"    a parallelogram with interior angle param degrees at the
+                origin (sides of length size);
+      "bend"    the unit square whose v = max edge is pulled inwards at its
+                middle so that the control polygon of that edge turns with
+                interior angle param degrees (v scaled linearly between the
+                straight bottom edge and the bent top edge)."""
+    gu, gv = greville(nu) / (nu - 2), greville(nv) / (nv - 2)
+    U, V = np.meshgrid(gu, gv)          # (nv, nu): control point (i, j) at [j, i]
+    if kind == "aspect":
+        X, Y = U * size_m, V * size_m * param
+    elif kind == "skew":
+        th = math.radians(param)
+        X, Y = (U + V * math.cos(th)) * size_m, V * math.sin(th) * size_m
+    elif kind == "bend":
+        h = 0.5 * math.tan(math.radians(180.0 - param) / 2.0)
+        top = 1.0 - h * (1.0 - np.abs(2.0 * U - 1.0))
+        X, Y = U * size_m, V * top * size_m
+    else:
+        raise ValueError(kind)
+    return np.stack([X.ravel(), Y.ravel()], axis=1)
+
+
+def config_distorted(kind: str, param: float, nu: int = 24, nv: int = 24, seed: int = 1) -> Patch:
+    """A cloth state on a distorted rest domain (distorted_rest): a smooth,
+    non-affine deformation of it (2 % stretch along X1, 1 % shear, an in-plane
+    ripple and an out-of-plane bulge of 3 % of the extent) plus seeded noise
+    of 1e-3 span; E = 1e5 Pa, nu = 0.3, h = 1 mm, 200 kg/m^2, dt = 0.01 s,
+    gravity -z, corners of the v = 0 edge pinned."""
+    rest = distorted_rest(kind, param, nu, nv)
+    lo, hi = rest.min(axis=0), rest.max(axis=0)
+    L = hi - lo
+    Xn = (rest - lo) / L
+    C = np.zeros((rest.shape[0], 3))
+    C[:, 0] = 1.02 * rest[:, 0] + 0.01 * rest[:, 1]
+    C[:, 1] = 0.99 * rest[:, 1] + 0.005 * L.min() * np.sin(2.0 * math.pi * Xn[:, 0])
+    C[:, 2] = 0.03 * L.min() * np.sin(math.pi * Xn[:, 0]) * np.sin(math.pi * Xn[:, 1])
+    span = min(L[0] / (nu - 2), L[1] / (nv - 2))
+    C += 1e-3 * span * normal(seed, C.size).reshape(C.shape)
+    mat = Material.from_engineering(1e5, 0.3, 1e-3, 200.0)
+    pins = np.array([0, nu - 1], dtype=np.int32)
+    return Patch(f"{kind}{param:g}", nu, nv, rest, C, C.copy(), mat, 0.01, (0.0, 0.0, -9.81), pins,
+                 {"seed": seed, "kind": kind, "param": param, "span_m": span})
+
+
+def synthetic_stencil(seed: int, nu: int, nv: int, pinned=(), coupling: float = 0.15) -> np.ndarray:
+    """A seeded symmetric positive definite matrix in the 5 x 5 block-stencil
+    shape of the global Hessian, (N, 25, 3, 3) with slot = (dv + 2) * 5 + (du + 2):
+    normal off-diagonal 3 x 3 blocks of scale `coupling` for every neighbour pair
+    (block (beta, alpha) the transpose of block (alpha, beta)), diagonal blocks
+    A A^T / 3 + (1 + the row's absolute off-diagonal sum) I, so the matrix is
+    strictly diagonally dominant; rows and columns of pinned control points
+    are replaced by the identity.  Input for tests of solvers and of the
+    learned preconditioner that need no cloth state."""
+    N = nu * nv
+    K = np.zeros((N, 25, 3, 3))
+    j, i = np.divmod(np.arange(N), nu)
+    k = 0
+    for dv in range(-2, 3):
+        for du in range(-2, 3):
+            s = (dv + 2) * 5 + (du + 2)
+            if s <= 12:
+                continue
+            B = coupling * normal(seed, 9 * N, offset=9 * N * k).reshape(N, 3, 3)
+            k += 1
+            ok = (i + du >= 0) & (i + du < nu) & (j + dv >= 0) & (j + dv < nv)
+            a = np.nonzero(ok)[0]
+            b = a + dv * nu + du
+            K[a, s] = B[a]
+            K[b, 24 - s] = np.transpose(B[a], (0, 2, 1))
+    A = normal(seed ^ 0xD1A6, 9 * N).reshape(N, 3, 3)
+    off = np.abs(K).sum(axis=(1, 3)) - np.abs(K[:, 12]).sum(axis=2)   # (N, 3) row sums
+    D = np.einsum("nab,ncb->nac", A, A) / 3.0
+    D += (1.0 + off.max(axis=1))[:, None, None] * np.eye(3)[None]
+    K[:, 12] = D
+    pins = np.asarray(pinned, dtype=np.int64).ravel()
+    if pins.size:
+        pj, pi = np.divmod(pins, nu)
+        for dv in range(-2, 3):
+            for du in range(-2, 3):
+                s = (dv + 2) * 5 + (du + 2)
+                ok = (pi + du >= 0) & (pi + du < nu) & (pj + dv >= 0) & (pj + dv < nv)
+                q = pins[ok] + dv * nu + du
+                K[pins[ok], s] = 0.0
+                K[q, 24 - s] = 0.0
+        K[pins, 12] = np.eye(3)[None]
+    return K
+
+
 def crop(patch: Patch, mu: int, mv: int | None = None) -> Patch:
     """The leading mu x mv control points of a patch (same span length, same
     state, pins restricted to the crop): a bounded sample of a large workload."""

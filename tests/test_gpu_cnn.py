@@ -3,14 +3,26 @@
 
 The GPU keeps features, activations and back-propagated gradients in BF16
 and accumulates in FP32 on the tensor cores; the oracle is run with the same
-BF16 rounding points (bf16_like=True), so the two differ by FP32 accumulation
-order and the BF16 rounding flips it causes (2^-8 relative on a flipped
-element): norm-wise well under 1e-2.  Grid 40 x 23 (920 pixels: seven full
-128-pixel tiles and a ragged tail of 24).
+BF16 rounding points (bf16_like=True), so the two differ only by FP32
+accumulation order and the BF16 rounding flips it causes (2^-8 relative on
+a flipped element), and the ReLU masks those flips can change.  Measured
+norm-wise errors on the 40 x 23 system: at most 2e-5 on layer outputs, taps
+and z, 2e-5 on the loss, 4e-5 on the weight and bias gradients of layers 3
+and 4 and 5.5e-4 on those of layers 1 and 2, which sit two and three BF16
+back-propagation steps deep.  Bounds: 3e-3 on layers, taps and z, 1e-3 on
+the loss and on the gradients of layers 3 and 4, 2e-3 on those of layers 1
+and 2.
+
+The systems are seeded synthetic SPD matrices in the stencil layout
+(inputs.synthetic_stencil), x* seeded normal and r = K x* from the oracle's
+stencil product: no input of the oracle comes from the GPU.  Grids: 40 x 23
+(920 pixels: seven full 128-pixel tiles and a ragged tail of 24) and the
+training size 512 x 512 (2048 tiles).
 """
 import numpy as np
 import pytest
 
+import oracle
 from oracle import cnn_oracle as co
 from paper_2506_18867_gb300 import inputs
 
@@ -24,6 +36,9 @@ from paper_2506_18867_gb300 import build as _build  # noqa: E402
 
 _build.build()
 from paper_2506_18867_gb300 import bsc  # noqa: E402
+
+B_LAYER, B_GRAD = 3e-3, 1e-3
+B_GRAD_LAYER = (2e-3, 2e-3, 1e-3, 1e-3)   # per layer: the first two are deeper in the BF16 backward pass
 
 
 def rel(a, b):
@@ -42,18 +57,27 @@ def random_params(seed, scale=1.0, last_scale=1.0):
     return p.astype(np.float32).astype(np.float64)   # the GPU's FP32 master values
 
 
+def make_system(pat, seed):
+    """Context of the patch's grid and pins (FP32), a synthetic SPD stencil
+    matrix with the same pins, x* and r = K x* (oracle product)."""
+    nu, nv = pat.nu, pat.nv
+    Kh = inputs.synthetic_stencil(seed, nu, nv, pinned=pat.pinned)
+    pin = np.zeros(nu * nv, dtype=bool)
+    pin[pat.pinned] = True
+    xs_h = inputs.normal(seed + 1, 3 * nu * nv).reshape(nu * nv, 3)
+    xs_h[pin] = 0.0
+    r_h = oracle.stencil_matvec(nu, nv, Kh, xs_h)
+    ctx = bsc.context_for_patch(pat, precision=bsc.FP32, pcg_rel_tol=1e-10)
+    K = torch.as_tensor(np.ascontiguousarray(Kh.reshape(nu * nv, 225).T), dtype=torch.float32, device="cuda")
+    r, xs = ctx.to_device(r_h), ctx.to_device(xs_h)
+    prep = co.Prepared(nu, nv, Kh, pin)
+    return ctx, K, r, xs, prep
+
+
 @pytest.fixture(scope="module")
 def system():
     pat = inputs.config_random_small(21, 40, 23, noise=0.05)
-    ctx = bsc.context_for_patch(pat, precision=bsc.FP32, pcg_rel_tol=1e-10)
-    C, Ch = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
-    K = ctx.assemble_hessian(C, project=True)
-    r = -ctx.gradient(C, Ch)
-    xs, it, rr = ctx.solve(r, K=K, rel_tol=1e-7)
-    Kh = K.double().cpu().numpy().reshape(25, 3, 3, -1).transpose(3, 0, 1, 2).copy()
-    pin = np.zeros(pat.n_cp, dtype=bool)
-    pin[pat.pinned] = True
-    prep = co.Prepared(pat.nu, pat.nv, Kh, pin)
+    ctx, K, r, xs, prep = make_system(pat, 5)
     net = bsc.Cnn(ctx)
     yield pat, ctx, net, K, r, xs, prep
     net.close()
@@ -78,7 +102,7 @@ def test_network_and_preconditioner_match_oracle(system):
     ea = rel(net.activations(4)[:, :9], cache["o"])
     ez = rel(n3(z), zo)
     print("features", ef, "layers", errs, "taps", ea, "z", ez)
-    assert ef < 4e-3 and max(errs) < 1e-2 and ea < 1e-2 and ez < 1e-2
+    assert ef < 1e-3 and max(errs) < B_LAYER and ea < B_LAYER and ez < B_LAYER
 
 
 def test_preconditioner_is_symmetric_on_the_gpu(system):
@@ -105,11 +129,12 @@ def test_gradients_match_oracle(system):
     L = net.loss_grad(r, xs)
     g = net.get_params(which=1).astype(np.float64)
     Lo, go = co.loss_and_grad(params, prep, n3(r), n3(xs), bf16_like=True)
-    assert abs(L - Lo) <= 1e-2 * abs(Lo)
+    print(f"loss {L:.6e} vs oracle {Lo:.6e}: rel err {abs(L - Lo) / abs(Lo):.2e}")
+    assert abs(L - Lo) <= B_GRAD * abs(Lo)
     for l, (ws, _, bs) in enumerate(co.param_layout()):
         ew, eb = rel(g[ws], go[ws]), rel(g[bs], go[bs])
         print(f"layer {l + 1}: weight-gradient rel err {ew:.2e}, bias {eb:.2e}")
-        assert ew < 3e-2 and eb < 3e-2, l
+        assert ew < B_GRAD_LAYER[l] and eb < B_GRAD_LAYER[l], l
 
 
 def test_zero_weights_reproduce_block_jacobi(system):
@@ -134,6 +159,64 @@ def test_fcg_converges_with_a_random_network(system):
     res = n3(ctx.spmv(x, K=K)) - n3(r)
     assert np.linalg.norm(res) <= 1e-6 * np.linalg.norm(n3(r))
     print("random network:", rep)
+
+
+def test_forced_stall_falls_back_to_pcg(system):
+    """A stall window of one iteration makes the flexible CG hand over to
+    block-Jacobi PCG as soon as r.r fails to drop by 4x in one iteration, on
+    the patch's own Newton system (projected K, r = -g), which needs tens of
+    iterations: the fallback must finish the solve to the same tolerance and
+    the same solution as PCG alone."""
+    pat, ctx, net, _, _, _, _ = system
+    C, Ch = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+    K = ctx.assemble_hessian(C, project=True)
+    r = -ctx.gradient(C, Ch)
+    x_pcg, it_pcg, _ = ctx.solve(r, K=K, rel_tol=1e-8)
+    net.set_params(random_params(3, last_scale=0.3))
+    net.set_stall_window(1)
+    try:
+        x, rep = net.solve(r, K, rel_tol=1e-8)
+    finally:
+        net.set_stall_window(24)
+    print("forced stall:", rep, "PCG alone:", it_pcg)
+    assert rep["fell_back"] == 1 and rep["pcg_iters"] > 0 and rep["fcg_iters"] >= 1
+    assert rep["rel_res"] <= 1e-8
+    res = n3(ctx.spmv(x, K=K)) - n3(r)
+    assert np.linalg.norm(res) <= 1e-6 * np.linalg.norm(n3(r))
+    assert rel(n3(x), n3(x_pcg)) < 1e-5
+
+
+def test_cnn_parity_at_training_size():
+    """512 x 512 (the training size): features, every layer output, the taps
+    and z, the loss and every layer's weight and bias gradients against the
+    oracle over all 262,144 pixels."""
+    pat = inputs.config_learned(1, 512)
+    ctx, K, r, xs, prep = make_system(pat, 11)
+    net = bsc.Cnn(ctx)
+    try:
+        params = random_params(7, last_scale=0.3)
+        net.set_params(params)
+        net.prepare(K)
+        z = net.apply(r)
+        zo, cache = co.forward(params, prep, n3(r), bf16_like=True)
+        ef = rel(net.activations(0), cache["acts"][0].reshape(-1, 32))
+        errs = [rel(net.activations(l), cache["acts"][l].reshape(-1, 32)) for l in (1, 2, 3)]
+        ea = rel(net.activations(4)[:, :9], cache["o"])
+        ez = rel(n3(z), zo)
+        L = net.loss_grad(r, xs)
+        g = net.get_params(which=1).astype(np.float64)
+        Lo, go = co.loss_and_grad(params, prep, n3(r), n3(xs), bf16_like=True)
+        eL = abs(L - Lo) / abs(Lo)
+        eg = [(rel(g[ws], go[ws]), rel(g[bs], go[bs])) for ws, _, bs in co.param_layout()]
+        print(f"512x512: features {ef:.2e}, layers {[f'{e:.2e}' for e in errs]}, taps {ea:.2e}, z {ez:.2e}, "
+              f"loss {eL:.2e}, gradients {[(f'{a:.2e}', f'{b:.2e}') for a, b in eg]}")
+        assert ef < 1e-3 and max(errs) < B_LAYER and ea < B_LAYER and ez < B_LAYER
+        assert eL < B_GRAD
+        for l, (ew, eb) in enumerate(eg):
+            assert ew < B_GRAD_LAYER[l] and eb < B_GRAD_LAYER[l], l
+    finally:
+        net.close()
+        ctx.close()
 
 
 def test_adam_steps_reduce_the_loss(system):

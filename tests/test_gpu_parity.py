@@ -44,6 +44,10 @@ CASES = [
     ("rand6x9", lambda: inputs.config_random_small(3, 6, 9, noise=0.2)),
     ("rand13x7_curved", lambda: inputs.config_random_small(4, 13, 7, curved=0.6, noise=0.1)),
     ("rand40x23", lambda: inputs.config_random_small(5, 40, 23, noise=0.05)),
+    # non-rectangular rest domains (Sec. 6): the most distorted case of each family
+    ("aspect10", lambda: inputs.config_distorted("aspect", 10, 24, 24)),
+    ("skew30", lambda: inputs.config_distorted("skew", 30, 24, 24)),
+    ("bend105", lambda: inputs.config_distorted("bend", 105, 24, 24)),
 ]
 
 
@@ -136,6 +140,61 @@ def test_spmv_and_solve_fp64(case, orc):
     want = orc.solve_banded(pat.nu, pat.nv, oK, b) if pat.n_cp <= 4096 else orc.solve_pcg(
         pat.nu, pat.nv, oK, b, 1e-14)[0]
     assert rel(to_n3(xs), want) < 1e-10
+
+
+def test_psd_test_changes_nothing(case, orc):
+    """The FP64 LDL^T PSD test before the eigendecomposition skips the spans
+    with no eigenvalue below -1e-14 ||H_r||: projected span Hessians with and
+    without it agree to 1e-13 and both match the oracle's Jacobi projection;
+    the spans it lets through are those without a projected eigenvalue (up
+    to spans whose smallest eigenvalue lies within the thresholds' band)."""
+    pat, prob, ctx = case
+    C = ctx.to_device(pat.C)
+    ctx.set_psd_test(False)
+    E0, g0, H0 = ctx.span_terms(C, project=True)
+    nneg0, _ = ctx.projection_stats()
+    ctx.set_psd_test(True)
+    E1, g1, H1 = ctx.span_terms(C, project=True)
+    nneg1, _ = ctx.projection_stats()
+    _, _, oH = prob.span_eval_projected(pat.C, True)
+    H0h, H1h = H0.double().cpu().numpy(), H1.double().cpu().numpy()
+    print(f"{pat.name}: {int((nneg0 > 0).sum())} of {pat.n_spans} spans projected; with / without the test "
+          f"{rel(H1h, H0h):.1e}")
+    assert rel(H1h, H0h) < 1e-13 and rel(H1h, oH) < 1e-12
+    # the two decisions use thresholds of the same size on different norms:
+    # only spans whose smallest eigenvalue sits within that band may differ
+    assert int(((nneg0 > 0) != (nneg1 > 0)).sum()) <= max(1, pat.n_spans // 1000)
+
+
+def test_pipelined_pcg_fp64(case, orc):
+    """The pipelined PCG form (one group barrier per iteration) reaches the
+    same solution as the oracle's direct solve, and its Newton step the
+    oracle's positions, at the bounds of the three-barrier form."""
+    pat, prob, ctx = case
+    sc = orc.Scene.from_patch(pat, project=True)
+    _, og, oK = orc.evaluate(prob, sc, pat.C, pat.Chat)
+    C, Ch = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+    Kd = ctx.assemble_hessian(C, project=True)
+    b = -og
+    _, it0, _ = ctx.solve(ctx.to_device(b), K=Kd, rel_tol=1e-13)
+    ctx.set_pcg_form(1)
+    try:
+        xs, it, rr = ctx.solve(ctx.to_device(b), K=Kd, rel_tol=1e-13)
+        assert rr <= 1e-13 and it > 0
+        want = orc.solve_banded(pat.nu, pat.nv, oK, b) if pat.n_cp <= 4096 else orc.solve_pcg(
+            pat.nu, pat.nv, oK, b, 1e-14)[0]
+        e = rel(to_n3(xs), want)
+        true_res = rel(orc.stencil_matvec(pat.nu, pat.nv, oK, to_n3(xs)), b)
+        print(f"{pat.name}: pipelined PCG {it} iterations (three-barrier form {it0}), solution {e:.2e}, "
+              f"true residual {true_res:.2e}")
+        assert e < 1e-10 and true_res < 1e-11
+        oC, orep = orc.newton_step(prob, sc, pat.C, pat.Chat, solver=0 if pat.n_cp <= 4096 else 1, pcg_tol=1e-14)
+        rep = ctx.newton_step(C, Ch)
+        assert rep.status == 0 and rep.alpha == orep.alpha
+        width = np.ptp(pat.rest, axis=0).max()
+        assert np.abs(to_n3(C) - oC).max() <= 1e-10 * width
+    finally:
+        ctx.set_pcg_form(0)
 
 
 def test_newton_step_fp64(case, orc):

@@ -2,9 +2,10 @@
 multi-frequency wrinkle field): energy, gradient, the assembled Hessian and
 50 SpMVs on the GPU in FP64 and in FP32, each against the FP64 oracle.
 
-The energy and the gradient are compared over the whole patch; the Hessian
-on sampled stencil rows (corners, edges, interior), which the oracle
-computes one by one; each SpMV y = K x (random x) on the same rows, against
+The energy and the gradient are compared over the whole patch; the Hessian,
+raw and with the per-span SPD projection the Newton step uses, on sampled
+stencil rows (corners, edges, interior), which the oracle computes one by
+one; each SpMV y = K x (random x) on the same rows, against
 the oracle's rows of K applied to x in FP64.  The errors are printed per
 result; the bounds are 1e-12 relative for FP64 and, for FP32, the bounds of
 the drape parity tests, except the FP32 gradient: at this near-equilibrium
@@ -50,7 +51,8 @@ def sweep(orc):
     oE = orc.energy(prob, scene, pat.C, pat.Chat)
     _, og, _ = orc.evaluate(prob, scene, pat.C, pat.Chat, want_K=False)
     _, oK = orc.eval_rows(prob, scene, pat.C, pat.Chat, rows)
-    return pat, rows, oE, og, oK
+    _, oKp = orc.eval_rows(prob, orc.Scene.from_patch(pat, project=True), pat.C, pat.Chat, rows)
+    return pat, rows, oE, og, oK, oKp
 
 
 def neighbour_index(n, rows):
@@ -68,7 +70,7 @@ def neighbour_index(n, rows):
 
 @pytest.mark.parametrize("precision", [bsc.FP64, bsc.FP32], ids=["fp64", "fp32"])
 def test_precision_sweep_1024(sweep, precision):
-    pat, rows, oE, og, oK = sweep
+    pat, rows, oE, og, oK, oKp = sweep
     nb = neighbour_index(N_SIDE, rows.astype(np.int64))
     valid = nb >= 0
     dt = torch.float64 if precision == bsc.FP64 else torch.float32
@@ -88,11 +90,15 @@ def test_precision_sweep_1024(sweep, precision):
             xn = np.where(valid[..., None], xh[np.where(valid, nb, 0)], 0.0)  # (rows, 25, 3)
             yo = np.einsum("rsab,rsb->ra", oK, xn)
             e_spmv.append(rel(y, yo))
-    eE, eg, eK = abs(E - oE) / abs(oE), rel(g, og), rel(Kr, oK)
+        del K
+        Kp = ctx.assemble_hessian(C, project=True)
+        Kpr = Kp[:, ri].double().cpu().numpy().reshape(25, 3, 3, -1).transpose(3, 0, 1, 2)
+        del Kp
+    eE, eg, eK, eKp = abs(E - oE) / abs(oE), rel(g, og), rel(Kr, oK), rel(Kpr, oKp)
     name = "FP64" if precision == bsc.FP64 else "FP32"
-    print(f"{name} 1024x1024: energy {eE:.2e}, gradient {eg:.2e}, {rows.size} Hessian rows {eK:.2e}, "
-          f"{N_SPMV} SpMVs max {max(e_spmv):.2e} (mean {np.mean(e_spmv):.2e})")
+    print(f"{name} 1024x1024: energy {eE:.2e}, gradient {eg:.2e}, {rows.size} Hessian rows {eK:.2e} "
+          f"(projected {eKp:.2e}), {N_SPMV} SpMVs max {max(e_spmv):.2e} (mean {np.mean(e_spmv):.2e})")
     if precision == bsc.FP64:
-        assert eE < 1e-12 and eg < 1e-12 and eK < 1e-12 and max(e_spmv) < 1e-12
+        assert eE < 1e-12 and eg < 1e-12 and eK < 1e-12 and eKp < 1e-12 and max(e_spmv) < 1e-12
     else:
-        assert eE < 1e-6 and eg < 5e-4 and eK < 2e-5 and max(e_spmv) < 2e-5
+        assert eE < 1e-6 and eg < 5e-4 and eK < 2e-5 and eKp < 2e-5 and max(e_spmv) < 2e-5

@@ -204,9 +204,10 @@ def dist_setup(args):
 
 
 def reduce_over_ranks(dist, times_ms, spans, device):
-    """Weak scaling across ranks: every rank steps its own workload, so the
-    job's time is the slowest rank's (max of every time) and its work the sum
-    of the ranks' spans.  No data-path collective: only these scalars."""
+    """Across ranks (replicas, or the patches of one batch split over them):
+    every rank steps its own patches, so the job's time is the slowest rank's
+    (max of every time) and its work the sum of the ranks' spans.  No
+    data-path collective: only these scalars."""
     import torch
     out = dict(times_ms)
     out["spans"] = spans
@@ -289,7 +290,13 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     builder, desc = WORKLOADS[args.workload]
-    pats = builder(1 + rank)
+    partitioned = args.workload == "batch64" and world > 1
+    if partitioned:
+        # one batch of garments split over the ranks (no exchange): strong scaling
+        from paper_2506_18867_gb300 import partition
+        _, pats = partition.rank_patches(builder(1), rank, world)
+    else:
+        pats = builder(1 + rank)
     prec = bsc.FP32 if args.precision == "fp32" else bsc.FP64
     ctx = make_context(bsc, pats, prec)
     ctx.set_profiling(True)
@@ -402,9 +409,46 @@ def run_gpu(args):
                "pcg_rel_tol": 1e-8, "l2": "flushed (256 MB write) before every timed step",
                "step": "one projected-Newton iteration (bsc_newton_step, CUDA-graph replay) from the same "
                        "seeded state",
-               "replicas": "one independent workload per GPU (seed 1 + rank)"}
+               "ranks": ("the 64 patches of one batch split over the ranks by the longest-processing-time "
+                         "rule on span counts, no exchange" if partitioned else
+                         "one independent workload per GPU (seed 1 + rank)")}
         if len(pats) == 1:
             cfg.update(nu=pats[0].nu, nv=pats[0].nv)
+        # the linear solve: the persistent PCG streams K once per iteration
+        # (HBM-bound at this size); algorithmic bytes per iteration and
+        # control point: the stencil K (225 entries) plus the SpMV's x and y
+        # and five vector passes (11 vectors of 3 components), in T
+        pcg_ms = phases["solve"] / K
+        iters = sum(r["pcg_iters"] for r in reports) / len(reports)
+        pcg_bytes = iters * Ncp * tsz * (225 + 6 + 15)
+        hbm, hbm_src = hbm_peak_gbs()
+        pcg_gbs = pcg_bytes / (pcg_ms * 1e-3) / 1e9
+        roof_pcg = {"kernel": "persistent block-Jacobi PCG (k_pcg or k_pcg_pipe)", "bound": "hbm",
+                    "achieved": pcg_gbs, "peak": hbm, "unit": "GB/s", "frac": pcg_gbs / hbm,
+                    "traffic": pcg_traffic(args.workload, prec == bsc.FP32, tuning, iters),
+                    "algorithmic_bytes_per_launch": pcg_bytes, "iterations": iters,
+                    "bytes_per_cp_per_iteration": tsz * (225 + 6 + 15), "launch_ms": pcg_ms,
+                    "launch_ms_source": "solve phase of bsc_phase_times (rhs, block-Jacobi inverses and the PCG "
+                                        "launch, CUDA events on the launching stream)",
+                    "peak_source": hbm_src,
+                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one k_pcg launch of the "
+                                      "512x512 wrinkle field (profiles/k_pcg_wrinkle512_fp32.md), scaled by control "
+                                      "points x iterations to this launch; null once the kernel changed"}
+        roof_proj = {"kernel": "SPD projection (k_proj_p0, k_proj_p1, k_proj_p2, k_proj_corr, k_project_ring: FP64)",
+                     "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                     "traffic": projection_traffic(args.workload, prec == bsc.FP32, tuning),
+                     "algorithmic_flops_per_step": flops, "launch_ms": proj_ms,
+                     "peak_source": "GB300 FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x "
+                                    "2.07 GHz = 1.26 TFLOP/s (nominal 1.25); no FP64 entry in the measured peaks",
+                     "frac_of_dfma_microbenchmark": achieved_tflops / FP64_DFMA_MEASURED_TFLOPS,
+                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of the projection launches "
+                                       "of one step (ncu capture summarised in profiles/), null when no capture "
+                                       "of the current kernels exists for this workload",
+                     "executed": projection_executed(args.workload, prec == bsc.FP32, tuning, proj_ms,
+                                             clk.get("sm_mhz") or 2070.0,
+                                             torch.cuda.get_device_properties(local).multi_processor_count)}
+        roof_main = roof_pcg if pcg_ms >= proj_ms else roof_proj
         line = {
             "metric": METRIC,
             "value": value,
@@ -414,7 +458,7 @@ def run_gpu(args):
             "warmup": args.warmup,
             "ms_per_step": ms_step_max,
             "higher_is_better": True,
-            "scaling": "weak",
+            "scaling": "strong" if partitioned else "weak",
             "vs_baseline": None,
             "dtype": "f32" if prec == bsc.FP32 else "f64",
             "data": "synthetic",
@@ -434,20 +478,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": 3 * Ncp * tsz},
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / K,
-            "roofline": {"kernel": "SPD projection (k_proj_p1, k_proj_p2, k_project_ring: FP64)",
-                         "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                         "traffic": projection_traffic(args.workload, prec == bsc.FP32, tuning),
-                         "algorithmic_flops_per_step": flops, "launch_ms": proj_ms,
-                         "peak_source": "GB300 FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x "
-                                        "2.07 GHz = 1.26 TFLOP/s (nominal 1.25); no FP64 entry in the measured peaks",
-                         "frac_of_dfma_microbenchmark": achieved_tflops / FP64_DFMA_MEASURED_TFLOPS,
-                         "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of the projection launches "
-                                           "of one step (ncu capture summarised in profiles/), null when no capture "
-                                           "of the current kernels exists for this workload",
-                         "executed": projection_executed(args.workload, prec == bsc.FP32, tuning, proj_ms,
-                                                         clk.get("sm_mhz") or 2070.0,
-                                                         torch.cuda.get_device_properties(local).multi_processor_count)},
+            "roofline": roof_main,
+            "rooflines": {"pcg": roof_pcg, "projection": roof_proj},
             "fp64": fp64,
             "drape256": drape,
             "batched": batched,
@@ -782,6 +814,28 @@ def projection_executed(workload, fp32, tuning, launch_ms, sm_mhz, num_sms):
     flops, cycles = rec
     return {"executed_flops_per_step": flops, "executed_tflops": flops / (launch_ms * 1e-3) / 1e12,
             "fp64_pipe_busy": cycles / (num_sms * launch_ms * 1e-3 * sm_mhz * 1e6)}
+
+
+# DRAM bytes (read + write) of one k_pcg launch (three-barrier form, FP32) on
+# the 512x512 wrinkle field, 32 iterations: 8.169 GB read + 0.501 GB written
+# (profiles/k_pcg_wrinkle512_fp32.md), i.e. 1033.6 B per control point and
+# iteration; it scales with both where K (0.9 KB per control point) does not
+# fit the 129 MB L2, so from 512x512 up.  Keyed by a hash of the solver source.
+PCG_TRAFFIC_PER_CP_ITER = 8.670e9 / (32 * 262144)
+PCG_TRAFFIC_HASH = "1b3224fedab2fe37"
+PCG_TRAFFIC_WORKLOADS = ("wrinkle512", "wrinkle1024")
+
+
+def pcg_traffic(workload, fp32, tuning, iters):
+    import hashlib
+    if workload not in PCG_TRAFFIC_WORKLOADS or not fp32 or tuning.get("pcg_form") != 0:
+        return None
+    with open(os.path.join(ROOT, "paper_2506_18867_gb300", "csrc", "k_solve.cu"), "rb") as fh:
+        h = hashlib.sha256(fh.read()).hexdigest()[:16]
+    if h != PCG_TRAFFIC_HASH:
+        return None
+    n = {"wrinkle512": 512 * 512, "wrinkle1024": 1024 * 1024}[workload]
+    return PCG_TRAFFIC_PER_CP_ITER * n * iters
 
 
 def projection_traffic(workload, fp32, tuning):

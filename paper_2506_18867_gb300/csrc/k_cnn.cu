@@ -26,8 +26,9 @@
 // (tcgen05.ld), adds the bias and applies the activation.  The backward pass
 // of the data (gradient w.r.t. a layer's input) is the same kernel on the
 // transposed weights gathered at the negated offsets, with the ReLU
-// derivative as epilogue; the weight gradients are reductions over pixels on
-// the CUDA cores.
+// derivative as epilogue; the weight gradients are one more contraction on
+// the tensor cores, over the pixels (k_wgrad), reduced across CTAs in a fixed
+// order.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -469,59 +470,140 @@ __global__ void __launch_bounds__(RB) k_diag_mean(int n, const double* __restric
 namespace {
 
 // ---------------------------------------------------------------------------
-// backward: weight gradients (CUDA cores), loss, optimizer, weight layouts
+// backward: weight gradients on the tensor cores, loss, optimizer, layouts
 // ---------------------------------------------------------------------------
-constexpr int WG_CHUNK = 1024;  // pixels per CTA of the weight-gradient reduction
-constexpr int WG_PB = 16;       // pixels staged per step
+constexpr int WG_CHUNK = 1024;                       // pixels per CTA (one partial sum per CTA)
+constexpr int WG_KC = 64;                            // pixels per MMA step (K of one staging)
+constexpr uint32_t WG_TILE_BYTES = 128u * WG_KC * 2;  // one 128-row A tile, K-major BF16
 
-// partial[blk][o] = sum over the block's pixels of X[p + off(tap)][ci] dY[p][co]
-// (o = (tap CIN + ci) COUT + co), then the bias gradient sum dY[p][co].
+template <int COUT>
+constexpr size_t wgrad_smem() { return 3 * (size_t)WG_TILE_BYTES + (size_t)COUT * WG_KC * 2; }
+
+// partial[blk][o] = sum over the block's pixels p of X[p + off(tap)][ci] dY[p][co]
+// (o = (tap CIN + ci) COUT + co), then the bias gradient sum_p dY[p][co] at
+// o = 9 CIN COUT + co.  One contraction over the pixels:
+//   D (rows (tap, ci) and one row for the bias, N = COUT) = A B^T,
+//   A[(tap, ci)][p] = X[p + off(tap)][ci] (zero outside the grid), a row of
+//   ones, B[co][p] = dY[p][co],
+// with BF16 operands staged transposed (pixels contiguous, K-major) in shared
+// memory by the threads, three 128-row tiles of tcgen05.mma (M = 128, N =
+// COUT, K = 16) accumulating in FP32 in TMEM over the CTA's pixels, and a
+// tcgen05.ld epilogue.  The CTAs' partial sums are reduced in block order by
+// k_wgrad_reduce, so the gradient is deterministic.  Bounded mbarrier waits.
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) k_wgrad(int nu, int nv, int P, const __nv_bfloat16* __restrict__ X,
-                                               const __nv_bfloat16* __restrict__ dY, float* __restrict__ partial) {
-  constexpr int NO = 9 * CIN * COUT, PER = (NO + 255) / 256;
-  __shared__ float sx[WG_PB][9 * CIN];
-  __shared__ float sy[WG_PB][COUT];
-  const int tid = threadIdx.x;
-  float acc[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) acc[k] = 0.0f;
-  float bacc = 0.0f;
+__global__ void __launch_bounds__(128) k_wgrad(int nu, int nv, int P, const __nv_bfloat16* __restrict__ X,
+                                               const __nv_bfloat16* __restrict__ dY, float* __restrict__ partial,
+                                               int* status) {
+  static_assert(9 * CIN + 1 <= 3 * 128 && CIN % 8 == 0 && COUT % 16 == 0 && 3 * COUT <= 128, "shapes");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + 3 * WG_TILE_BYTES;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr uint32_t IDESC = tc05::idesc_bf16_f32(128, COUT);
+  constexpr int NO = 9 * CIN * COUT, G8 = CIN / 8, ONES = 9 * CIN;
+  constexpr uint32_t SBO = (WG_KC / 8) * 128;
+  auto a_at = [&](int m, int k) {
+    return reinterpret_cast<__nv_bfloat16*>(sA + (m >> 7) * WG_TILE_BYTES + tc05::kmajor_offset(m & 127, k, WG_KC));
+  };
+  // the padding rows stay zero; the bias row is all ones
+  for (int i = tid; i < (int)(3 * WG_TILE_BYTES / 16); i += 128) reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  for (int k = tid; k < WG_KC; k += 128) *a_at(ONES, k) = __float2bfloat16_rn(1.0f);
+  if (warp == 0) {
+    tc05::tmem_alloc(&tmem_base, 128);
+    tc05::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc05::mbar_init(&mbar, 1);
+    tc05::fence_mbar_init();
+  }
+  tc05::fence_before_sync();
+  __syncthreads();
+  tc05::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  uint32_t phase = 0;
+  bool failed = false, first = true;
   const int lo = blockIdx.x * WG_CHUNK, hi = min(P, lo + WG_CHUNK);
-  for (int base = lo; base < hi; base += WG_PB) {
-    for (int idx = tid; idx < WG_PB * 9 * CIN; idx += 256) {
-      const int pix = idx / (9 * CIN), rem = idx - pix * 9 * CIN, tap = rem / CIN, ci = rem - tap * CIN;
-      const int p = base + pix;
-      float v = 0.0f;
+  for (int base = lo; base < hi && !failed; base += WG_KC) {
+    // A: item (pixel k, tap, 8-channel group g): 16 bytes of X scattered to 8 rows
+    for (int it = tid; it < WG_KC * 9 * G8; it += 128) {
+      const int k = it % WG_KC, rest = it / WG_KC, g = rest % G8, tap = rest / G8;
+      const int p = base + k;
+      uint4 v = make_uint4(0, 0, 0, 0);
       if (p < hi) {
         const int i = p % nu + (tap % 3 - 1), j = p / nu + (tap / 3 - 1);
-        if (i >= 0 && i < nu && j >= 0 && j < nv) v = __bfloat162float(X[(size_t)(j * nu + i) * CIN + ci]);
+        if (i >= 0 && i < nu && j >= 0 && j < nv)
+          v = *reinterpret_cast<const uint4*>(X + (size_t)(j * nu + i) * CIN + 8 * g);
       }
-      sx[pix][rem] = v;
-    }
-    for (int idx = tid; idx < WG_PB * COUT; idx += 256) {
-      const int pix = idx / COUT, co = idx - pix * COUT, p = base + pix;
-      sy[pix][co] = p < hi ? __bfloat162float(dY[(size_t)p * COUT + co]) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int pix = 0; pix < WG_PB; ++pix) {
+      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
 #pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const int o = tid + 256 * k;
-        if (o < NO) acc[k] += sx[pix][o / COUT] * sy[pix][o % COUT];
+      for (int q = 0; q < 8; ++q) *a_at(tap * CIN + 8 * g + q, k) = e[q];
+    }
+    // B: item (pixel k, 8-channel group g) of dY
+    for (int it = tid; it < WG_KC * (COUT / 8); it += 128) {
+      const int k = it % WG_KC, g = it / WG_KC, p = base + k;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (p < hi) v = *reinterpret_cast<const uint4*>(dY + (size_t)p * COUT + 8 * g);
+      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<__nv_bfloat16*>(sB + tc05::kmajor_offset(8 * g + q, k, WG_KC)) = e[q];
+    }
+    tc05::fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc05::fence_after_sync();
+      const uint32_t a0 = tc05::smem_u32(sA), b0 = tc05::smem_u32(sB);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int k16 = 0; k16 < WG_KC / 16; ++k16) {
+          const uint64_t ad = tc05::smem_desc(a0 + t * WG_TILE_BYTES + k16 * 256, 128, SBO);
+          const uint64_t bd = tc05::smem_desc(b0 + k16 * 256, 128, SBO);
+          tc05::mma_bf16(tmem + (uint32_t)(t * COUT), ad, bd, IDESC, (!first || k16 > 0) ? 1u : 0u);
+        }
+      tc05::mma_commit(&mbar);
+    }
+    first = false;
+    const bool ok = tc05::mbar_wait(&mbar, phase, WAIT_LIMIT);
+    failed = __syncthreads_or(!ok) != 0;
+    if (failed) {
+      if (tid == 0) atomicOr(status, BSC_STATUS_TIMEOUT_FLAG);
+      break;
+    }
+    phase ^= 1u;
+    tc05::fence_after_sync();  // the next staging overwrites the operands the MMAs read
+  }
+  if (failed) {
+    tc05::mbar_wait(&mbar, phase, WAIT_LIMIT);  // a bounded chance for an MMA in flight
+  } else {
+    float* out = partial + (size_t)blockIdx.x * (NO + COUT);
+#pragma unroll 1
+    for (int t = 0; t < 3; ++t) {
+      float v[COUT];
+#pragma unroll
+      for (int h = 0; h < COUT / 16; ++h) {
+        float t16[16];
+        tc05::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * COUT + 16 * h), t16);
+        tc05::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[16 * h + i] = t16[i];
       }
-      if (tid < COUT) bacc += sy[pix][tid];
-    }
-    __syncthreads();
-  }
-  float* out = partial + (size_t)blockIdx.x * (NO + COUT);
+      const int m = t * 128 + tid;
+      if (m < ONES) {
 #pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int o = tid + 256 * k;
-    if (o < NO) out[o] = acc[k];
+        for (int co = 0; co < COUT; ++co) out[m * COUT + co] = v[co];
+      } else if (m == ONES) {
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) out[NO + co] = v[co];
+      }
+    }
   }
-  if (tid < COUT) out[NO + tid] = bacc;
+  tc05::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc05::tmem_dealloc(tmem, 128);
 }
 
 // grad[o] = sum over blocks of partial[b][o], in block order.
@@ -957,7 +1039,8 @@ template <int CIN, int COUT>
 cudaError_t wgrad(bsc_cnn* n, int l, const __nv_bfloat16* X, const __nv_bfloat16* dY) {
   const int nblk = (n->P + WG_CHUNK - 1) / WG_CHUNK, NO1 = 9 * CIN * COUT + COUT;
   BSC_COUNT(n->c, 2);
-  k_wgrad<CIN, COUT><<<nblk, 256, 0, n->c->stream>>>(n->nu, n->nv, n->P, X, dY, n->wpart);
+  k_wgrad<CIN, COUT><<<nblk, 128, wgrad_smem<COUT>(), n->c->stream>>>(n->nu, n->nv, n->P, X, dY, n->wpart,
+                                                                      n->c->dstatus);
   k_wgrad_reduce<<<(NO1 + 255) / 256, 256, 0, n->c->stream>>>(nblk, NO1, n->wpart, n->grads + n->off[l]);
   return cudaGetLastError();
 }
@@ -1151,6 +1234,10 @@ bsc_status bsc_cnn_create(bsc_ctx* c, bsc_cnn** out) {
   if (e == cudaSuccess) e = conv_setup<32, 16, CONV_LINEAR_F32>();
   if (e == cudaSuccess) e = conv_setup<16, 32, CONV_MASK_BF16>();
   if (e == cudaSuccess) e = conv_setup<32, 32, CONV_MASK_BF16>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_wgrad<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_smem<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_wgrad<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_smem<16>());
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "bsc_cnn_create: %s", cudaGetErrorString(e));
     cnn_free(n);

@@ -359,27 +359,23 @@ BSC_PHASE void span_form(const Tab& tab, const View& A) {
 }
 
 // The PSD test that precedes the eigendecomposition: an LDL^T factorisation
-// of H_r + tau I in FP64, tau = neg_rel ||H_r||_inf, in place in A.  Every
-// pivot positive means H_r + tau I is positive definite (the factorisation's
-// backward error, about n eps ||H_r||, is several times smaller than tau),
-// so no eigenvalue of H_r lies below -tau and the span needs no projection.
-// A non-positive or non-finite pivot fails the test; the span then goes
-// through the eigendecomposition, which decides (with its own threshold on
-// the same scale) which eigenvalues to clamp.  Destroys A.  Returns true
-// when the test passes.
+// of H_r + tau I in FP64, tau = neg_rel tr(H_r) / n, in place in A.  For a
+// PSD matrix tr / n lies between ||H_r||_2 / n and ||H_r||_2, so tau is at
+// most the eigendecomposition's own threshold (neg_rel on the same scale).
+// Every pivot positive means H_r + tau I is positive definite (the
+// factorisation's backward error, about n eps ||H_r||, is below tau), so no
+// eigenvalue of H_r lies below -tau and the span needs no projection.  A
+// non-positive trace, or a non-positive or non-finite pivot, fails the test;
+// the span then goes through the eigendecomposition, which decides which
+// eigenvalues to clamp.  Destroys A.  Returns true when the test passes.
 template <int D>
 BSC_PHASE bool ldlt_psd(const View& A, double neg_rel) {
   constexpr int n = 3 * D;
-  double nrm = 0.0;
-#pragma unroll 1
-  for (int i = 0; i < n; ++i) {
-    double r = 0.0;
-#pragma unroll 1
-    for (int j = 0; j < n; ++j) r += fabs(A[lp(i, j)]);
-    nrm = fmax(nrm, r);
-  }
-  if (!(nrm > 0.0)) return nrm == 0.0;  // the zero matrix is PSD; NaN fails
-  const double tau = neg_rel * nrm;
+  double tr = 0.0;
+#pragma unroll
+  for (int i = 0; i < n; ++i) tr += A[lp(i, i)];
+  if (!(tr > 0.0) || !isfinite(tr)) return false;
+  const double tau = neg_rel * tr * (1.0 / n);
 #pragma unroll 1
   for (int i = 0; i < n; ++i) A[lp(i, i)] += tau;
   // right-looking LDL^T: A(i, j) -= l_ik A(j, k) over the trailing block,

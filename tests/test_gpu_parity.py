@@ -170,6 +170,7 @@ def test_pipelined_pcg_fp64(case, orc):
     """The pipelined PCG form (one group barrier per iteration) reaches the
     same solution as the oracle's direct solve, and its Newton step the
     oracle's positions, at the bounds of the three-barrier form."""
+    form = 1
     pat, prob, ctx = case
     sc = orc.Scene.from_patch(pat, project=True)
     _, og, oK = orc.evaluate(prob, sc, pat.C, pat.Chat)
@@ -177,7 +178,7 @@ def test_pipelined_pcg_fp64(case, orc):
     Kd = ctx.assemble_hessian(C, project=True)
     b = -og
     _, it0, _ = ctx.solve(ctx.to_device(b), K=Kd, rel_tol=1e-13)
-    ctx.set_pcg_form(1)
+    ctx.set_pcg_form(form)
     try:
         xs, it, rr = ctx.solve(ctx.to_device(b), K=Kd, rel_tol=1e-13)
         assert rr <= 1e-13 and it > 0
@@ -185,7 +186,7 @@ def test_pipelined_pcg_fp64(case, orc):
             pat.nu, pat.nv, oK, b, 1e-14)[0]
         e = rel(to_n3(xs), want)
         true_res = rel(orc.stencil_matvec(pat.nu, pat.nv, oK, to_n3(xs)), b)
-        print(f"{pat.name}: pipelined PCG {it} iterations (three-barrier form {it0}), solution {e:.2e}, "
+        print(f"{pat.name}: PCG form {form} {it} iterations (three-barrier form {it0}), solution {e:.2e}, "
               f"true residual {true_res:.2e}")
         assert e < 1e-10 and true_res < 1e-11
         oC, orep = orc.newton_step(prob, sc, pat.C, pat.Chat, solver=0 if pat.n_cp <= 4096 else 1, pcg_tol=1e-14)

@@ -89,6 +89,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-garment sub-measurement")
     p.add_argument("--no-drape", action="store_true", help="skip the 256x256 drape sub-measurement")
+    p.add_argument("--no-contact", action="store_true", help="skip the drape-on-a-sphere contact sub-measurement")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner sub-measurement")
     p.add_argument("--no-point", action="store_true", help="skip the per-point projection sub-measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the 1024x1024 precision sweep sub-measurement")
@@ -379,6 +380,9 @@ def run_gpu(args):
     drape = None
     if args.workload != "drape256" and not args.no_drape and prec == bsc.FP32 and world == 1:
         drape = measure_drape(bsc, flush, stream, torch, np, K, args.warmup)
+    contact = None
+    if args.workload != "batch64" and not args.no_contact and prec == bsc.FP32 and world == 1:
+        contact = measure_contact(bsc, flush, stream, torch, np)
     batched = None
     if args.workload != "batch64" and not args.no_batch and prec == bsc.FP32 and world == 1:
         batched = measure_batch(bsc, flush, stream, torch, np, seed=1 + rank)
@@ -482,6 +486,7 @@ def run_gpu(args):
             "rooflines": {"pcg": roof_pcg, "projection": roof_proj},
             "fp64": fp64,
             "drape256": drape,
+            "contact": contact,
             "batched": batched,
             "learned": learned,
             "point_projection": point,
@@ -700,6 +705,34 @@ def measure_drape(bsc, flush, stream, torch, np, steps, warmup):
                                        "traffic": projection_traffic("drape256", True, tuning)}
         ctx.close()
     out["newton_step_speedup_fp32_vs_fp64"] = out["fp64"]["newton_step_ms"] / out["fp32"]["newton_step_ms"]
+    return out
+
+
+def measure_contact(bsc, flush, stream, torch, np, steps=5, warmup=2):
+    """The drape (256x256, FP32) resting on a sphere (radius 0.4 m, 9,216
+    triangles) 4 mm below its centre, IPC barrier with dhat = 1 cm, kappa =
+    1e3 Pa, contact mesh of about twice the control points: Newton-step ms
+    with and without the contact term, from the same state."""
+    pat = inputs.config_drape(1, 256, 1e-5)
+    V, T = inputs.sphere_obstacle((1.0, 1.0, -0.404), 0.4, 48, 96)
+    out = {"workload": "drape256 on a sphere", "obstacle_triangles": int(len(T)), "dhat_m": 0.01,
+           "kappa_pa": 1e3}
+    for name, with_contact in (("without", False), ("with", True)):
+        ctx = bsc.context_for_patch(pat, precision=bsc.FP32, pcg_rel_tol=1e-8)
+        ctx.set_profiling(True)
+        if with_contact:
+            ctx.contact_attach(V, T, 0.01, 1e3)
+        C0, Chat = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+        C = C0.clone()
+        ctx.autotune(C0, Chat)
+        ms, ph, reps, launches = time_newton(ctx, C, C0, Chat, steps, warmup, flush, stream, torch)
+        rec = {"newton_step_ms": sum(ms) / steps, "phases_ms": {k: v / steps for k, v in ph.items()},
+               "alpha": reps[-1]["alpha"], "pcg_iters": reps[-1]["pcg_iters"], "launches_per_step": launches / steps}
+        if with_contact:
+            rec.update(ctx.contact_stats())
+        out[name] = rec
+        ctx.close()
+    out["contact_overhead_ms"] = out["with"]["newton_step_ms"] - out["without"]["newton_step_ms"]
     return out
 
 

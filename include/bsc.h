@@ -435,6 +435,48 @@ bsc_status bsc_cnn_set_stall_window(bsc_cnn* cnn, int window);
  * timeout; the context stays usable. */
 bsc_status bsc_set_wait_limit(bsc_ctx* ctx, long long spins, int extra_blocks);
 
+/* ---- contact with a static obstacle (Sec. 4.3) ----------------------------
+ * A triangle mesh embedded in the B-spline surface of a single-patch context
+ * meets a static obstacle triangle mesh through the log barrier of
+ * incremental potential contact.
+ *  - Contact mesh: mu x mv vertices at parametric points u_i = S_u i /
+ *    (mu - 1), v_j = S_v j / (mv - 1) (vertex k = j mu + i), each moving with
+ *    the nine control points of its span, x_k = sum_l N_l(u, v) C_l (Eq. trig
+ *    mesh node from control points); cells split into two triangles along
+ *    alternating diagonals; weight A_k = a third of the rest areas of its
+ *    triangles.  mu, mv <= 0 choose about twice the control points in all
+ *    (sqrt(2) (n - 1) + 1 per side).
+ *  - Potential: kappa sum_k A_k sum beta(d / dhat), beta(x) = -(x - 1)^2 ln x
+ *    for 0 < x < 1, over the (vertex, obstacle triangle) pairs closer than
+ *    dhat [m]; a pair whose closest point lies on an edge or a corner counts
+ *    once, for the lowest-index triangle holding that feature.  kappa [Pa].
+ *  - Every energy, gradient and Hessian of the context then includes it:
+ *    per pair the gradient and the PSD projection of the Hessian w.r.t. the
+ *    vertex (kappa A beta'' / dhat^2 u u^T, u the unit vector from the
+ *    closest point), chained onto the span's control points (Eq. gradient and
+ *    hessian of contact barrier) and gathered into the stencil with the
+ *    elastic terms (after their projection).
+ *  - bsc_newton_step starts its line search at min(1, step bound): the
+ *    largest step that keeps every vertex at least 0.1 of its distance from
+ *    every obstacle triangle it could reach, from the convexity of the
+ *    distance along the step.
+ *  - No self-contact of the cloth, no edge-edge or obstacle-vertex-cloth-
+ *    triangle pairs, no friction.
+ *   obs_xyz  host, n_obs_vertices x 3 doubles [m];  obs_tris  host,
+ *            n_obs_tris x 3 vertex indices (distinct, in range).
+ * Copies everything; BSC_ERR_INVALID_ARG on bad input; replaces an earlier
+ * obstacle.  Drops the captured Newton graph. */
+bsc_status bsc_contact_attach(bsc_ctx* ctx, const double* obs_xyz, int n_obs_vertices, const int32_t* obs_tris,
+                              int n_obs_tris, int mu, int mv, double dhat, double kappa);
+bsc_status bsc_contact_detach(bsc_ctx* ctx);
+/* Contact-mesh vertex positions at C (host, nvert x 3 doubles; cap >= nvert),
+ * or only the count with x_out == NULL. */
+bsc_status bsc_contact_vertices(bsc_ctx* ctx, const void* C_dev, double* x_out, int cap, int* nvert);
+/* The line search's step bound of direction D_dev (3 planes of N) from C_dev. */
+bsc_status bsc_contact_step_bound(bsc_ctx* ctx, const void* C_dev, const void* D_dev, double* alpha);
+/* Contact-mesh vertex count and pairs counted by the last evaluation. */
+bsc_status bsc_contact_stats(bsc_ctx* ctx, int* nvert, int* npairs);
+
 /* ---- inspection entry points (parity tests, profiling) ------------------- */
 
 /* Per-span results of the last evaluation path: E_span (device, Nsp doubles),

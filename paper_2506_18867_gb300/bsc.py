@@ -46,7 +46,8 @@ EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc
            "bsc_cnn_create", "bsc_cnn_destroy", "bsc_cnn_set_params", "bsc_cnn_get_params", "bsc_cnn_prepare",
            "bsc_cnn_apply", "bsc_cnn_loss_grad", "bsc_cnn_adam_step", "bsc_cnn_activations", "bsc_solve_fcg",
            "bsc_set_learned_solver", "bsc_cnn_set_stall_window", "bsc_set_wait_limit", "bsc_set_pcg_form",
-           "bsc_set_psd_test")
+           "bsc_set_psd_test", "bsc_contact_attach", "bsc_contact_detach", "bsc_contact_vertices",
+           "bsc_contact_step_bound", "bsc_contact_stats")
 
 TILE_CANDIDATES = (0, 8, 16, 32)
 
@@ -181,6 +182,11 @@ def load(path: str = LIB_PATH):
     lib.bsc_set_wait_limit.argtypes = [P, ct.c_longlong, I]
     lib.bsc_set_pcg_form.argtypes = [P, I]
     lib.bsc_set_psd_test.argtypes = [P, I]
+    lib.bsc_contact_attach.argtypes = [P, ct.POINTER(D), I, ct.POINTER(ct.c_int32), I, I, I, D, D]
+    lib.bsc_contact_detach.argtypes = [P]
+    lib.bsc_contact_vertices.argtypes = [P, V, ct.POINTER(D), I, ct.POINTER(I)]
+    lib.bsc_contact_step_bound.argtypes = [P, V, V, ct.POINTER(D)]
+    lib.bsc_contact_stats.argtypes = [P, ct.POINTER(I), ct.POINTER(I)]
     for name in EXPORTS:
         if name not in ("bsc_destroy", "bsc_last_error", "bsc_cnn_destroy"):
             getattr(lib, name).restype = I
@@ -430,6 +436,39 @@ class Context:
     def set_pcg_grid(self, grid):
         """Blocks of the persistent PCG, in [patches, usable blocks]."""
         self._check(self._lib.bsc_set_pcg_grid(self._h, int(grid)))
+
+    # -- contact with a static obstacle ---------------------------------------
+    def contact_attach(self, vertices, triangles, dhat, kappa, mu=0, mv=0):
+        """Obstacle triangle mesh (vertices (n, 3), triangles (m, 3)); contact
+        mesh of mu x mv vertices (0: about twice the control points)."""
+        V = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64).reshape(-1, 3))
+        T = np.ascontiguousarray(np.asarray(triangles, dtype=np.int32).reshape(-1, 3))
+        self._check(self._lib.bsc_contact_attach(self._h, V.ctypes.data_as(ct.POINTER(ct.c_double)), V.shape[0],
+                                                 T.ctypes.data_as(ct.POINTER(ct.c_int32)), T.shape[0], int(mu),
+                                                 int(mv), float(dhat), float(kappa)))
+
+    def contact_detach(self):
+        self._check(self._lib.bsc_contact_detach(self._h))
+
+    def contact_vertices(self, C):
+        n = ct.c_int()
+        self._check(self._lib.bsc_contact_vertices(self._h, None, None, 0, ct.byref(n)))
+        out = np.zeros((n.value, 3))
+        self._check(self._lib.bsc_contact_vertices(self._h, _ptr(self._vec(C, "C")),
+                                                   out.ctypes.data_as(ct.POINTER(ct.c_double)), n.value,
+                                                   ct.byref(n)))
+        return out
+
+    def contact_step_bound(self, C, D):
+        a = ct.c_double()
+        self._check(self._lib.bsc_contact_step_bound(self._h, _ptr(self._vec(C, "C")), _ptr(self._vec(D, "D")),
+                                                     ct.byref(a)))
+        return a.value
+
+    def contact_stats(self):
+        n, p = ct.c_int(), ct.c_int()
+        self._check(self._lib.bsc_contact_stats(self._h, ct.byref(n), ct.byref(p)))
+        return {"vertices": n.value, "pairs": p.value}
 
     def set_psd_test(self, on=True):
         """FP64 LDL^T PSD test before the interior spans' eigendecomposition."""

@@ -63,6 +63,7 @@ void drop_graph(bsc_ctx* c) {
 void free_ctx(bsc_ctx* c) {
   if (!c) return;
   drop_graph(c);
+  contact_destroy(c);
   void* ptrs[] = {c->mem_off, c->bd_off, c->tab_mem, c->tab_bd, c->pts_mem, c->pts_bd, c->rest, c->mass,
                   c->pinned, c->bucket_list, c->nneg, c->E_span, c->g_span, c->H_span, c->A_mem, c->K_int,
                   c->Dinv, c->partials, c->sync, c->dstatus, c->dscalars, c->pd, c->cp_patch, c->sp_patch,
@@ -111,6 +112,7 @@ bsc_status eval_path(bsc_ctx* c, const void* C, int want_grad, int want_hess, in
     return fail(c, BSC_ERR_INVALID_ARG, "project must be one of BSC_PROJECT_* (got %d)", project);
   CK(launch_span_eval(c, C, want_grad, hess_mode(want_hess, project)), "span evaluation");
   if (want_hess && project == BSC_PROJECT_SPAN) CK(launch_project(c), "SPD projection");
+  CK(contact_add(c, C, want_grad, want_hess, nullptr), "contact");
   return BSC_OK;
 }
 
@@ -167,6 +169,7 @@ cudaError_t enqueue_newton(bsc_ctx* c, void* C, const void* Chat) {
   mark(c, 1);
   if (c->project_default == BSC_PROJECT_SPAN && (e = launch_project(c)) != cudaSuccess) return e;
   mark(c, 2);
+  if ((e = contact_add(c, C, 1, 1, nullptr)) != cudaSuccess) return e;
   if ((e = launch_patch_energy(c, C, Chat, c->patch_E)) != cudaSuccess) return e;
   if ((e = launch_gradient(c, C, Chat, g)) != cudaSuccess) return e;
   if ((e = launch_assemble(c, c->K_int)) != cudaSuccess) return e;
@@ -178,6 +181,7 @@ cudaError_t enqueue_newton(bsc_ctx* c, void* C, const void* Chat) {
     e = launch_pcg(c, c->K_int, rhs, d, c->pcg_tol, c->pcg_max_iter);
   if (e != cudaSuccess) return e;
   mark(c, 4);
+  if ((e = contact_step_bound(c, C, d)) != cudaSuccess) return e;  // the line search starts at the step bound
   if ((e = launch_step_begin(c, d)) != cudaSuccess) return e;
   if ((e = launch_ls_round(c, C, Chat, d, trial, C, 0)) != cudaSuccess) return e;
   mark(c, 5);
@@ -222,6 +226,9 @@ bsc_status capture_newton(bsc_ctx* c, void* C, const void* Chat) {
 }
 
 }  // namespace
+
+// Drops the captured Newton graph (after a change of what it launches).
+void bsc_drop_graph(bsc_ctx* c) { drop_graph(c); }
 
 // Message of a failed context-free call, read back through bsc_last_error(NULL).
 void bsc_set_thread_error(const char* msg) { snprintf(g_create_err, sizeof(g_create_err), "%s", msg); }
@@ -291,6 +298,7 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
   c->wait_limit = kWaitLimitDefault;
   c->barrier_extra = 0u;
   c->solver_cnn = nullptr;
+  c->contact = nullptr;
   for (int k = 0; k < TILE_CLASSES; ++k) c->tile_tu[k] = 0;
 
   bsc_status st = BSC_OK;
@@ -451,6 +459,7 @@ bsc_status bsc_patch_energies(bsc_ctx* c, const void* C, const void* Chat, doubl
   if (!aligned16(C) || (Chat && !aligned16(Chat)))
     return fail(c, BSC_ERR_INVALID_ARG, "bsc_energy: pointers must be 16-byte aligned");
   CK(launch_span_eval(c, C, 0, 0), "bsc_energy");
+  CK(contact_add(c, C, 0, 0, nullptr), "bsc_energy");
   CK(launch_patch_energy(c, C, Chat, c->patch_E), "bsc_energy");
   CK(cudaMemcpyAsync(E_out, c->patch_E, sizeof(double) * c->P, cudaMemcpyDeviceToHost, c->stream), "bsc_energy");
   return check_status(c, "bsc_energy");

@@ -179,6 +179,8 @@ struct bsc_ctx {
   // flexible CG's iterations and fallback flag of the last learned solve
   struct bsc_cnn* solver_cnn;
   double* fcg_rec;
+  // contact with a static obstacle (bsc_contact_attach), or nullptr
+  struct bsc_contact* contact;
   // bounded device waits of the persistent solvers: spin limit, and blocks
   // their barriers expect beyond the launched ones (0; > 0 only to test the
   // timeout path, see bsc_set_wait_limit)
@@ -257,6 +259,14 @@ cudaError_t set_pcg_grid(bsc_ctx* c, int grid);
 cudaError_t launch_axpy_trial(bsc_ctx* c, const void* C, const void* d, double alpha, void* out);
 cudaError_t launch_copy_vec(bsc_ctx* c, const void* src, void* dst);
 cudaError_t launch_export_span_terms(bsc_ctx* c, void* g_out, void* H_out);
+// contact (k_contact.cu): terms at C added to the span arrays after the
+// elastic projection; the step bound of a direction into the contact record;
+// release with the context
+cudaError_t contact_add(bsc_ctx* c, const void* C, int add_g, int add_h, const PatchStep* gate);
+cudaError_t contact_step_bound(bsc_ctx* c, const void* C, const void* D);
+void contact_destroy(bsc_ctx* c);
+// the step bound on the device (nullptr without contact)
+const double* contact_bound_ptr(const bsc_ctx* c);
 // Newton step pieces (k_newton.cu)
 cudaError_t launch_step_begin(bsc_ctx* c, const void* d);
 cudaError_t launch_ls_round(bsc_ctx* c, const void* C, const void* Chat, const void* d, void* trial, void* Cout,

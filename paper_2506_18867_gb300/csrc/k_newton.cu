@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(SB) k_step_begin(int n_items, const int* __res
                                                    const double* __restrict__ partial, const double* __restrict__ E0,
                                                    const double* __restrict__ pcg_out, int project,
                                                    const double* __restrict__ fcg_rec,
+                                                   const double* __restrict__ alpha0,
                                                    PatchStep* __restrict__ steps, const int* __restrict__ status) {
   __shared__ double sm[SB / 32];
   const int p = blockIdx.x;
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(SB) k_step_begin(int n_items, const int* __res
     PatchStep st;
     st.E0 = E0[p];
     st.E1 = 0.0;
-    st.alpha = 1.0;
+    st.alpha = alpha0 ? fmin(1.0, *alpha0) : 1.0;  // contact: the conservative step bound
     st.dir_inf = m_tot;
     st.pcg_iters = pcg_out[3 * p];
     st.pcg_res = pcg_out[3 * p + 1];
@@ -147,7 +148,8 @@ cudaError_t launch_step_begin(bsc_ctx* c, const void* d) {
                                                               (const float*)d, c->partials);
   k_step_begin<<<c->P, SB, 0, c->stream>>>(c->n_red_items, c->red_off, c->partials, c->patch_E, c->pcg_out,
                                            c->project_default == BSC_PROJECT_SPAN,
-                                           c->solver_cnn ? c->fcg_rec : nullptr, c->steps, c->dstatus);
+                                           c->solver_cnn ? c->fcg_rec : nullptr, contact_bound_ptr(c), c->steps,
+                                           c->dstatus);
   return cudaGetLastError();
 }
 
@@ -164,6 +166,7 @@ cudaError_t launch_ls_round(bsc_ctx* c, const void* C, const void* Chat, const v
                                               (float*)trial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_span_eval(c, trial, 0, 0, c->steps)) != cudaSuccess) return e;
+  if ((e = contact_add(c, trial, 0, 0, c->steps)) != cudaSuccess) return e;
   if ((e = launch_patch_energy(c, trial, Chat, c->patch_E + c->P, c->steps)) != cudaSuccess) return e;
   BSC_COUNT(c, 2);
   k_ls_accept<<<1, SB, 0, c->stream>>>(c->P, c->steps, c->patch_E + c->P, c->max_ls, round, c->dstatus, c->pending);

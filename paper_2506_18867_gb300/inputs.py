@@ -327,6 +327,59 @@ def config_distorted(kind: str, param: float, nu: int = 24, nv: int = 24, seed: 
                  {"seed": seed, "kind": kind, "param": param, "span_m": span})
 
 
+def pyramid_obstacle(cx=0.25, cy=0.25, apex_z=-0.004, base_z=-0.03, half=0.2):
+    """A square pyramid (apex up) as a static obstacle triangle mesh: 5
+    vertices, the 4 side faces.  Returns (vertices (5, 3), triangles (4, 3))."""
+    V = np.array([(cx - half, cy - half, base_z), (cx + half, cy - half, base_z), (cx + half, cy + half, base_z),
+                  (cx - half, cy + half, base_z), (cx, cy, apex_z)])
+    T = np.array([(0, 1, 4), (1, 2, 4), (2, 3, 4), (3, 0, 4)], dtype=np.int32)
+    return V, T
+
+
+def sphere_obstacle(center, radius, n_lat=24, n_lon=48):
+    """A UV sphere as a static obstacle triangle mesh (vertices, triangles)."""
+    cx, cy, cz = center
+    V = [(cx, cy, cz + radius)]
+    for i in range(1, n_lat):
+        th = math.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2.0 * math.pi * j / n_lon
+            V.append((cx + radius * math.sin(th) * math.cos(ph), cy + radius * math.sin(th) * math.sin(ph),
+                      cz + radius * math.cos(th)))
+    V.append((cx, cy, cz - radius))
+    T = []
+    for j in range(n_lon):
+        T.append((0, 1 + j, 1 + (j + 1) % n_lon))
+    for i in range(n_lat - 2):
+        r0, r1 = 1 + i * n_lon, 1 + (i + 1) * n_lon
+        for j in range(n_lon):
+            a, b = r0 + j, r0 + (j + 1) % n_lon
+            c, d = r1 + j, r1 + (j + 1) % n_lon
+            T += [(a, c, b), (b, c, d)]
+    last = len(V) - 1
+    r0 = 1 + (n_lat - 2) * n_lon
+    for j in range(n_lon):
+        T.append((r0 + j, last, r0 + (j + 1) % n_lon))
+    return np.array(V), np.array(T, dtype=np.int32)
+
+
+def config_contact(seed: int = 2, n: int = 11, size_m: float = 0.5) -> Patch:
+    """A cloth patch just above the apex of a pyramid obstacle
+    (pyramid_obstacle): n x n control points, size_m square, height 6 mm
+    with a 4 mm standing wave and seeded 1 mm noise, E = 1e5 Pa, nu = 0.3,
+    h = 1 mm, 200 kg/m^2, dt = 0.01 s, gravity -z, corners of the v = 0 edge
+    pinned.  Contact parameters in meta: dhat = 0.02 m, kappa = 1e3 Pa."""
+    rest = flat_rest(n, n, size_m, size_m)
+    C = lift(rest)
+    X = rest
+    C[:, 2] = 0.006 + 0.004 * np.sin(2 * math.pi * X[:, 0] / size_m) * np.cos(2 * math.pi * X[:, 1] / size_m)
+    C += 1e-3 * normal(seed, C.size).reshape(C.shape)
+    mat = Material.from_engineering(1e5, 0.3, 1e-3, 200.0)
+    pins = np.array([0, n - 1], dtype=np.int32)
+    return Patch(f"contact{n}", n, n, rest, C, C.copy(), mat, 0.01, (0.0, 0.0, -9.81), pins,
+                 {"seed": seed, "dhat": 0.02, "kappa": 1e3})
+
+
 def synthetic_stencil(seed: int, nu: int, nv: int, pinned=(), coupling: float = 0.15) -> np.ndarray:
     """A seeded symmetric positive definite matrix in the 5 x 5 block-stencil
     shape of the global Hessian, (N, 25, 3, 3) with slot = (dv + 2) * 5 + (du + 2):

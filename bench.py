@@ -84,6 +84,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="bsc", choices=["bsc", "reference"])
     p.add_argument("--workload", default="wrinkle1024", choices=sorted(WORKLOADS))
+    p.add_argument("--k-layout", default="symmetric", choices=("symmetric", "full"),
+                   help="layout of the Newton step's matrix (bsc_set_k_storage; symmetric is the library default)")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -301,6 +303,7 @@ def run_gpu(args):
     prec = bsc.FP32 if args.precision == "fp32" else bsc.FP64
     ctx = make_context(bsc, pats, prec)
     ctx.set_profiling(True)
+    ctx.set_k_storage(args.k_layout == "symmetric")
     Nsp, Ncp = ctx.n_spans, ctx.N
     C0 = stacked(ctx, [p.C for p in pats], torch, np).to(device="cuda", dtype=ctx.dtype)
     Chat = stacked(ctx, [p.Chat for p in pats], torch, np).to(device="cuda", dtype=ctx.dtype)
@@ -420,18 +423,23 @@ def run_gpu(args):
             cfg.update(nu=pats[0].nu, nv=pats[0].nv)
         # the linear solve: the persistent PCG streams K once per iteration
         # (HBM-bound at this size); algorithmic bytes per iteration and
-        # control point: the stencil K (225 entries) plus the SpMV's x and y
-        # and five vector passes (11 vectors of 3 components), in T
+        # control point: the stencil K as the Newton step stores it (13
+        # blocks of the symmetric layout = 117 entries, the default; 225 in
+        # the full one) plus the SpMV's x and y and five vector passes (11
+        # vectors of 3 components), in T
         pcg_ms = phases["solve"] / K
         iters = sum(r["pcg_iters"] for r in reports) / len(reports)
-        pcg_bytes = iters * Ncp * tsz * (225 + 6 + 15)
+        k_sym = args.k_layout == "symmetric"
+        k_entries = 117 if k_sym else 225
+        pcg_bytes = iters * Ncp * tsz * (k_entries + 6 + 15)
         hbm, hbm_src = hbm_peak_gbs()
         pcg_gbs = pcg_bytes / (pcg_ms * 1e-3) / 1e9
         roof_pcg = {"kernel": "persistent block-Jacobi PCG (k_pcg or k_pcg_pipe)", "bound": "hbm",
                     "achieved": pcg_gbs, "peak": hbm, "unit": "GB/s", "frac": pcg_gbs / hbm,
                     "traffic": pcg_traffic(args.workload, prec == bsc.FP32, tuning, iters),
                     "algorithmic_bytes_per_launch": pcg_bytes, "iterations": iters,
-                    "bytes_per_cp_per_iteration": tsz * (225 + 6 + 15), "launch_ms": pcg_ms,
+                    "bytes_per_cp_per_iteration": tsz * (k_entries + 6 + 15),
+                    "k_layout": "symmetric (13 blocks)" if k_sym else "full (25 blocks)", "launch_ms": pcg_ms,
                     "launch_ms_source": "solve phase of bsc_phase_times (rhs, block-Jacobi inverses and the PCG "
                                         "launch, CUDA events on the launching stream)",
                     "peak_source": hbm_src,

@@ -271,7 +271,7 @@ typedef struct bsc_tuning {
                               to [patches, usable blocks]) */
   double pcg_ms[4];        /* measured ms of the solve per candidate (-1: duplicate) */
   int pcg_form;            /* PCG form chosen at that grid (see bsc_set_pcg_form) */
-  double pcg_form_ms[2];   /* measured ms of the solve per form (1e30: did not converge) */
+  double pcg_form_ms[3];   /* measured ms of the solve per form (1e30: did not converge) */
   int psd_test;            /* PSD test before the interior eigendecomposition (bsc_set_psd_test) */
   double psd_ms[2];        /* measured ms of the whole projection without / with it */
 } bsc_tuning;
@@ -301,8 +301,9 @@ bsc_status bsc_set_border_path(bsc_ctx* ctx, int path);
 bsc_status bsc_set_p2_variant(bsc_ctx* ctx, int variant);
 
 /* PSD test of the SPD projection (BSC_PROJECT_SPAN): with on != 0 (the
- * default) every interior span's reduced Hessian H_r first goes through an
- * FP64 LDL^T factorisation of H_r + tau I, tau = 1e-14 ||H_r||_inf; a span
+ * default) every interior span's reduced Hessian H_r (order n) first goes
+ * through an FP64 LDL^T factorisation of H_r + tau I, tau = 1e-14 tr(H_r) / n
+ * (a span with tr(H_r) <= 0 fails outright); a span
  * whose pivots are all positive has no eigenvalue below -tau and keeps its
  * Hessian, and only the spans that fail go on to the eigendecomposition
  * (gathered into one list, so that the eigendecomposition runs with full
@@ -319,9 +320,29 @@ bsc_status bsc_set_psd_test(bsc_ctx* ctx, int on);
  *     K u and M K u so that an iteration's three dot products form in one
  *     pass behind a single group barrier, at the cost of six more vectors
  *     and a recursively updated residual that drifts a little further from
- *     b - K x.
- * bsc_autotune picks the faster of the two for the context; the default is 0. */
+ *     b - K x;
+ * 2 - two passes and two group barriers per iteration: since K p = K z +
+ *     beta K p_old, the product pass forms K z and updates q = K z + beta q
+ *     and p = z + beta p in place, and the direction needs no pass of its
+ *     own (q is carried by a recurrence, like r).
+ * bsc_autotune picks the fastest form that reaches the tolerance; the
+ * default is 0. */
 bsc_status bsc_set_pcg_form(bsc_ctx* ctx, int form);
+
+/* Layout of the matrix the Newton step assembles and its block-Jacobi PCG
+ * reads (bsc_newton_step, bsc_autotune): symmetric != 0 (the default) keeps
+ * only the diagonal block and the 12 blocks that couple a control point to
+ * the neighbours after it (dv > 0, or dv = 0 and du > 0) - 13 slots, plane
+ * (s' * 9 + 3 r + c) with s' = stencil slot - 12 - and reads each block
+ * before a row as the transpose of the neighbour's (K is symmetric: the
+ * gathers of (alpha, beta) and (beta, alpha) add the same span entries in the
+ * same order).  The product accumulates the same entries in the same order
+ * as with the full 25 slots, so both layouts give the same Newton step bit
+ * for bit, with half the matrix bytes to write and to stream per PCG
+ * iteration.  The learned solver always uses the full layout.  After a
+ * Newton step, bsc_spmv and bsc_solve with K_dev NULL use its matrix in
+ * whichever layout it has; bsc_assemble_hessian always writes the full one. */
+bsc_status bsc_set_k_storage(bsc_ctx* ctx, int symmetric);
 
 /* Current split of the PCG's blocks (host array of count ints). */
 bsc_status bsc_pcg_split(const bsc_ctx* ctx, int* blocks_per_patch);
@@ -548,6 +569,87 @@ bsc_status bsc_projection_stats(bsc_ctx* ctx, int* nneg, int* nred);
 #define BSC_STATIC_SOLVE_MAX_CP 16384
 bsc_status bsc_solve_static(int nu, int nv, int precision, const void* K_dev, const void* b_dev, void* x_dev,
                             double rel_tol, int max_iter, void* cuda_stream, int* iters, double* rel_res);
+
+/* ---- strip decomposition of one patch over ranks ----------------------------
+ * A patch too large for one GPU splits into strips of whole control-point
+ * rows (v direction), one per rank.  Rank r owns the rows [own0, own1) and
+ * holds a window of them plus two halo rows on each side (clipped to the
+ * grid): rows [row0, row1), row0 = own0 - min(2, own0), row1 = own1 +
+ * min(2, nv - own1).  The spans touching an owned row (span b covers rows
+ * b .. b + 2) all lie in the window, so with the halo rows of C current the
+ * window's gradient and Hessian rows of its owned rows are exactly the
+ * patch's, bit for bit (same spans, same gather order).  A span belongs to
+ * the rank owning its middle row b + 1.
+ *
+ * One Newton iteration then needs these exchanges between neighbouring
+ * ranks: the halo rows of the search direction p before every product
+ * y = K p (the product reads p two rows beyond the owned ones), the halo rows
+ * of the solution d before the line search, and sums over ranks of per-row
+ * partial sums (the PCG's dot products, the energy of a trial point).  The
+ * calls below return those partial sums one per owned row, each computed
+ * from that row alone in a fixed order; adding them up in the global row
+ * order (after an all-gather) gives every decomposition of a patch - one
+ * window of all rows included - the same sums bit for bit.  The exchanges
+ * and the all-gather are the caller's (host copies, NCCL, gloo ...): no
+ * kernel here waits for another rank. */
+typedef struct {
+  int row0, row1;  /* global control-point rows held: [row0, row1) */
+  int own0, own1;  /* global rows owned: [own0, own1), own0 < own1 */
+} bsc_window;
+
+/* Context of one strip window of the patch (g, rest_xy, m, q, o as for
+ * bsc_create, describing the WHOLE patch; the pinned list holds whole-patch
+ * indices).  Vectors of the window (C, Chat, g, d, ...) are 3 planes of
+ * nu * (row1 - row0) values, local row k being global row row0 + k; K holds
+ * 225 planes of that length.  Every single-patch call works on it
+ * (bsc_gradient, bsc_assemble_hessian, bsc_spmv: rows outside [own0, own1)
+ * hold partial sums and are to be ignored; bsc_energy: the owned span rows'
+ * and owned control points' share of the incremental potential), except the
+ * ones that solve over the whole window (bsc_newton_step, bsc_solve,
+ * bsc_autotune) and contact, which return BSC_ERR_INVALID_ARG.
+ * Errors: BSC_ERR_INVALID_ARG for a window other than the one defined above
+ * or fewer than 3 rows, otherwise as bsc_create. */
+bsc_status bsc_create_window(const bsc_knot_grid* g, const double* rest_xy, const bsc_material* m,
+                             const bsc_quadrature* q, const bsc_options* o, const bsc_window* w,
+                             void* cuda_stream, bsc_ctx** out);
+
+/* Per-row partial sums of the incremental potential at C (Eq. incremental
+ * potential): out[0 .. ns) the energies of the owned span rows (global
+ * rows max(own0 - 1, 0) .. min(own1 - 1, nv - 2) - 1, each the sum of its
+ * spans' energies), then out[ns .. ns + (own1 - own0)) the inertia and
+ * gravity terms of the owned control-point rows.  *count = ns + own1 - own0;
+ * cap is out's length (out may be NULL to query the count).  Synchronises
+ * the context's stream. */
+bsc_status bsc_window_energy_rows(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, double* out, int cap,
+                                  int* count);
+
+/* Block-Jacobi PCG of K d = -g over the ranks, one step at a time (Sec. 5.1
+ * solve; the iteration of bsc_solve with the reductions left to the caller).
+ * x_dev, p_dev: caller-owned window vectors (3 planes) that hold the solution
+ * and the search direction from bsc_window_pcg_begin to the end of the solve;
+ * the caller fills p's halo rows from the neighbours (their owned rows)
+ * before each bsc_window_pcg_product, and reads x's owned rows at the end.
+ * Each call works on the owned rows only and writes per-owned-row partial
+ * sums to rows (host, n = own1 - own0 per quantity), then synchronises the
+ * context's stream.
+ *   begin:     block-Jacobi inverses of K; x = 0, r = -g, z = M^-1 r, p = z;
+ *              rows[0..n) = r.z, rows[n..2n) = r.r
+ *   product:   q = K p; rows[0..n) = p.q
+ *   update:    x += alpha p, r -= alpha q, z = M^-1 r; rows = r.z, then r.r
+ *   direction: p = z + beta p (no sums)
+ * With rz, pq, rr the sums over all rows: alpha = rz / pq, beta = rz_new /
+ * rz; stop when rr <= tol^2 rr_0.  K_dev is the window's assembled Hessian
+ * (bsc_assemble_hessian). */
+bsc_status bsc_window_pcg_begin(bsc_ctx* ctx, const void* K_dev, const void* g_dev, void* x_dev, void* p_dev,
+                                double* rows);
+bsc_status bsc_window_pcg_product(bsc_ctx* ctx, const void* K_dev, double* rows);
+bsc_status bsc_window_pcg_update(bsc_ctx* ctx, double alpha, double* rows);
+bsc_status bsc_window_pcg_direction(bsc_ctx* ctx, double beta);
+
+/* out = a + alpha d over all of the context's vector entries (3 planes of
+ * N): the trial point C + alpha d of a line search.  Device pointers of the
+ * context's element type; out may alias a. */
+bsc_status bsc_axpy(bsc_ctx* ctx, const void* a_dev, const void* d_dev, double alpha, void* out_dev);
 
 #ifdef __cplusplus
 }

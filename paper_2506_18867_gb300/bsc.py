@@ -47,11 +47,17 @@ EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc
            "bsc_cnn_apply", "bsc_cnn_loss_grad", "bsc_cnn_adam_step", "bsc_cnn_activations", "bsc_solve_fcg",
            "bsc_set_learned_solver", "bsc_cnn_set_stall_window", "bsc_set_wait_limit", "bsc_set_pcg_form",
            "bsc_set_psd_test", "bsc_contact_attach", "bsc_contact_detach", "bsc_contact_vertices",
-           "bsc_contact_step_bound", "bsc_contact_stats")
+           "bsc_contact_step_bound", "bsc_contact_stats", "bsc_create_window", "bsc_window_energy_rows",
+           "bsc_window_pcg_begin", "bsc_window_pcg_product", "bsc_window_pcg_update", "bsc_window_pcg_direction",
+           "bsc_axpy", "bsc_set_k_storage")
 
 TILE_CANDIDATES = (0, 8, 16, 32)
 
 STATIC_SOLVE_MAX_CP = 16384  # BSC_STATIC_SOLVE_MAX_CP in include/bsc.h
+
+
+class Window(ct.Structure):
+    _fields_ = [("row0", ct.c_int), ("row1", ct.c_int), ("own0", ct.c_int), ("own1", ct.c_int)]
 
 
 class KnotGrid(ct.Structure):
@@ -88,7 +94,7 @@ class Tuning(ct.Structure):
     _fields_ = [("tile_tu", ct.c_int * 4), ("tile_ms", (ct.c_double * 4) * 4), ("pcg_grid", ct.c_int),
                 ("border_path", ct.c_int), ("border_ms", ct.c_double * 3), ("p2_variant", ct.c_int),
                 ("p2_ms", ct.c_double * 2), ("pcg_grid_cand", ct.c_int * 4), ("pcg_ms", ct.c_double * 4),
-                ("pcg_form", ct.c_int), ("pcg_form_ms", ct.c_double * 2), ("psd_test", ct.c_int),
+                ("pcg_form", ct.c_int), ("pcg_form_ms", ct.c_double * 3), ("psd_test", ct.c_int),
                 ("psd_ms", ct.c_double * 2)]
 
     def as_dict(self):
@@ -187,6 +193,16 @@ def load(path: str = LIB_PATH):
     lib.bsc_contact_vertices.argtypes = [P, V, ct.POINTER(D), I, ct.POINTER(I)]
     lib.bsc_contact_step_bound.argtypes = [P, V, V, ct.POINTER(D)]
     lib.bsc_contact_stats.argtypes = [P, ct.POINTER(I), ct.POINTER(I)]
+    lib.bsc_create_window.argtypes = [ct.POINTER(KnotGrid), ct.POINTER(D), ct.POINTER(Material),
+                                      ct.POINTER(Quadrature), ct.POINTER(Options), ct.POINTER(Window), V,
+                                      ct.POINTER(P)]
+    lib.bsc_window_energy_rows.argtypes = [P, V, V, ct.POINTER(D), I, ct.POINTER(I)]
+    lib.bsc_window_pcg_begin.argtypes = [P, V, V, V, V, ct.POINTER(D)]
+    lib.bsc_window_pcg_product.argtypes = [P, V, ct.POINTER(D)]
+    lib.bsc_window_pcg_update.argtypes = [P, D, ct.POINTER(D)]
+    lib.bsc_window_pcg_direction.argtypes = [P, D]
+    lib.bsc_axpy.argtypes = [P, V, V, D, V]
+    lib.bsc_set_k_storage.argtypes = [P, I]
     for name in EXPORTS:
         if name not in ("bsc_destroy", "bsc_last_error", "bsc_cnn_destroy"):
             getattr(lib, name).restype = I
@@ -206,9 +222,12 @@ class Context:
 
     def __init__(self, nu, nv, rest, material, precision=FP64, dt=0.01, gravity=(0.0, -9.81, 0.0),
                  pinned=(), project=True, quadrature=(QUAD_REDUCED, QUAD_REDUCED), pcg_rel_tol=1e-8,
-                 pcg_max_iter=10000, max_line_search=30, stream=None):
+                 pcg_max_iter=10000, max_line_search=30, stream=None, window=None):
+        """window: (row0, row1, own0, own1) for a strip window of the patch
+        (bsc_create_window); nu, nv, rest and pinned then describe the whole
+        patch."""
         self._create([dict(nu=nu, nv=nv, rest=rest, material=material, dt=dt, gravity=gravity, pinned=pinned)],
-                     precision, project, quadrature, pcg_rel_tol, pcg_max_iter, max_line_search, stream)
+                     precision, project, quadrature, pcg_rel_tol, pcg_max_iter, max_line_search, stream, window)
 
     @classmethod
     def batch(cls, specs, precision=FP64, project=True, quadrature=(QUAD_REDUCED, QUAD_REDUCED), pcg_rel_tol=1e-8,
@@ -220,7 +239,8 @@ class Context:
                      stream)
         return self
 
-    def _create(self, specs, precision, project, quadrature, pcg_rel_tol, pcg_max_iter, max_line_search, stream):
+    def _create(self, specs, precision, project, quadrature, pcg_rel_tol, pcg_max_iter, max_line_search, stream,
+                window=None):
         import torch
         self.torch = torch
         lib = load()
@@ -252,7 +272,14 @@ class Context:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
         h = ct.c_void_p()
-        if P == 1:
+        self.window = None
+        if window is not None:
+            self._win = Window(*(int(v) for v in window))
+            self.window = tuple(int(v) for v in window)
+            st = lib.bsc_create_window(ct.byref(self._grids[0]), rest_ptrs[0], ct.byref(self._mats[0]),
+                                       ct.byref(self._quad), ct.byref(self._opts[0]), ct.byref(self._win),
+                                       ct.c_void_p(stream), ct.byref(h))
+        elif P == 1:
             st = lib.bsc_create(ct.byref(self._grids[0]), rest_ptrs[0], ct.byref(self._mats[0]),
                                 ct.byref(self._quad), ct.byref(self._opts[0]), ct.c_void_p(stream), ct.byref(h))
         else:
@@ -271,6 +298,8 @@ class Context:
         self.N = int(self.cp_offset[-1])
         self.n_spans = int(self.span_offset[-1])
         self.nu, self.nv = int(self._grids[0].nu), int(self._grids[0].nv)
+        if window is not None:
+            self.nv = self.N // self.nu   # the window's rows
 
     # -- helpers -----------------------------------------------------------
     def _check(self, st):
@@ -283,6 +312,11 @@ class Context:
         if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.numel() == 3 * self.N):
             raise ValueError(f"{name}: expected a contiguous CUDA {self.dtype} tensor with 3*N elements")
         return t
+
+    def _mat(self, K):
+        if not (K.is_cuda and K.dtype == self.dtype and K.is_contiguous() and K.numel() == 225 * self.N):
+            raise ValueError(f"K: expected a contiguous CUDA {self.dtype} tensor with 225*N elements")
+        return K
 
     def new_vec(self):
         return self.torch.zeros((3, self.N), dtype=self.dtype, device="cuda")
@@ -475,8 +509,68 @@ class Context:
         self._check(self._lib.bsc_set_psd_test(self._h, int(bool(on))))
 
     def set_pcg_form(self, form):
-        """PCG form: 0 three group barriers per iteration, 1 the pipelined recurrences with one."""
+        """PCG form: 0 three group barriers per iteration, 1 the pipelined
+        recurrences with one, 2 two passes with two (q = K z + beta q)."""
         self._check(self._lib.bsc_set_pcg_form(self._h, int(form)))
+
+    # -- strip windows (bsc_create_window) ----------------------------------
+    def _n_own(self):
+        if self.window is None:
+            raise ValueError("not a strip window context")
+        return self.window[3] - self.window[2]
+
+    def energy_rows(self, C, Chat=None):
+        """Per-row partial energies of a strip window: (owned span rows, owned
+        control-point rows), host float64 arrays."""
+        own = self._n_own()
+        n = ct.c_int()
+        self._check(self._lib.bsc_window_energy_rows(self._h, None, None, None, 0, ct.byref(n)))
+        out = np.zeros(n.value)
+        self._check(self._lib.bsc_window_energy_rows(self._h, _ptr(self._vec(C, "C")), _ptr(self._vec(Chat, "Chat")),
+                                                     out.ctypes.data_as(ct.POINTER(ct.c_double)), n.value,
+                                                     ct.byref(n)))
+        return out[:n.value - own], out[n.value - own:]
+
+    def pcg_begin(self, K, g, x, p):
+        """Strip PCG of K d = -g: x = 0, p = z = M^-1 r; returns the owned rows'
+        partial sums (r.z, r.r) as a (2, rows) array.  x and p stay in use
+        until the solve ends."""
+        rows = np.zeros((2, self._n_own()))
+        self._win_xp = (x, p)
+        self._check(self._lib.bsc_window_pcg_begin(self._h, _ptr(self._mat(K)), _ptr(self._vec(g, "g")),
+                                                   _ptr(self._vec(x, "x")), _ptr(self._vec(p, "p")),
+                                                   rows.ctypes.data_as(ct.POINTER(ct.c_double))))
+        return rows
+
+    def pcg_product(self, K):
+        """q = K p on the owned rows (p's halo rows current); partial sums p.q."""
+        rows = np.zeros(self._n_own())
+        self._check(self._lib.bsc_window_pcg_product(self._h, _ptr(self._mat(K)),
+                                                     rows.ctypes.data_as(ct.POINTER(ct.c_double))))
+        return rows
+
+    def pcg_update(self, alpha):
+        """x += alpha p, r -= alpha q, z = M^-1 r; partial sums (r.z, r.r)."""
+        rows = np.zeros((2, self._n_own()))
+        self._check(self._lib.bsc_window_pcg_update(self._h, float(alpha),
+                                                    rows.ctypes.data_as(ct.POINTER(ct.c_double))))
+        return rows
+
+    def pcg_direction(self, beta):
+        """p = z + beta p on the owned rows."""
+        self._check(self._lib.bsc_window_pcg_direction(self._h, float(beta)))
+
+    def axpy(self, a, d, alpha, out=None):
+        """out = a + alpha d (a new tensor unless out is given)."""
+        if out is None:
+            out = self.new_vec()
+        self._check(self._lib.bsc_axpy(self._h, _ptr(self._vec(a, "a")), _ptr(self._vec(d, "d")), float(alpha),
+                                       _ptr(self._vec(out, "out"))))
+        return out
+
+    def set_k_storage(self, symmetric):
+        """Layout of the Newton step's matrix: symmetric (13 slots, the default) or full (25)."""
+        self._check(self._lib.bsc_set_k_storage(self._h, int(bool(symmetric))))
 
     def pcg_split(self):
         out = (ct.c_int * self.P)()
@@ -635,7 +729,8 @@ def batch_for_patches(patches, precision=FP64, **kw):
 
 
 def context_for_patch(patch, precision=FP64, **kw):
-    """Context for an ``inputs.Patch`` (rest, material, scene)."""
+    """Context for an ``inputs.Patch`` (rest, material, scene); window=(row0,
+    row1, own0, own1) gives a strip window of it."""
     kw.setdefault("dt", patch.dt)
     kw.setdefault("gravity", patch.gravity)
     kw.setdefault("pinned", patch.pinned)

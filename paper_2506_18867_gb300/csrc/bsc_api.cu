@@ -12,8 +12,8 @@ int span_block(int precision);
 void plan_span_items(const bsc_ctx* c, std::vector<SpanItem>& out, int only_class, int tu_override);
 
 namespace {
-
 thread_local char g_create_err[512] = "";
+}  // namespace
 
 bsc_status fail(bsc_ctx* c, bsc_status st, const char* fmt, ...) {
   char* buf = c ? c->err : g_create_err;
@@ -53,6 +53,8 @@ bsc_status check_status(bsc_ctx* c, const char* where) {
   }
   return BSC_OK;
 }
+
+namespace {
 
 void drop_graph(bsc_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -158,6 +160,10 @@ bsc_status validate_patch(int p, const bsc_knot_grid* g, const double* rest_xy, 
   return BSC_OK;
 }
 
+// Layout of the Newton step's own matrix: symmetric unless switched off or
+// the learned solver (whose network reads the full stencil) is set.
+int newton_sym(const bsc_ctx* c) { return c->k_sym && !c->solver_cnn ? 1 : 0; }
+
 // Everything of one Newton iteration up to and including the first
 // line-search round, and the read-back of the step records: the part a CUDA
 // graph holds.
@@ -172,13 +178,16 @@ cudaError_t enqueue_newton(bsc_ctx* c, void* C, const void* Chat) {
   if ((e = contact_add(c, C, 1, 1, nullptr)) != cudaSuccess) return e;
   if ((e = launch_patch_energy(c, C, Chat, c->patch_E)) != cudaSuccess) return e;
   if ((e = launch_gradient(c, C, Chat, g)) != cudaSuccess) return e;
-  if ((e = launch_assemble(c, c->K_int)) != cudaSuccess) return e;
+  // the block-Jacobi PCG reads K in the symmetric layout (half the bytes);
+  // the learned solver's network reads the full stencil
+  const int sym = newton_sym(c);
+  if ((e = launch_assemble(c, c->K_int, sym)) != cudaSuccess) return e;
   mark(c, 3);
   if ((e = launch_axpy_trial(c, g, g, -2.0, rhs)) != cudaSuccess) return e;  // rhs = -g
   if (c->solver_cnn)
     e = enqueue_learned_solve(c, c->solver_cnn, c->K_int, rhs, d, c->pcg_tol, c->pcg_max_iter);
   else
-    e = launch_pcg(c, c->K_int, rhs, d, c->pcg_tol, c->pcg_max_iter);
+    e = launch_pcg(c, c->K_int, rhs, d, c->pcg_tol, c->pcg_max_iter, sym);
   if (e != cudaSuccess) return e;
   mark(c, 4);
   if ((e = contact_step_bound(c, C, d)) != cudaSuccess) return e;  // the line search starts at the step bound
@@ -237,9 +246,20 @@ extern "C" {
 
 const char* bsc_last_error(const bsc_ctx* c) { return c ? c->err : g_create_err; }
 
-bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double* const* rest_xy,
-                            const bsc_material* mats, const bsc_quadrature* q, const bsc_options* opts,
-                            void* stream, bsc_ctx** out) {
+}  // extern "C"
+
+// A strip window of one patch: the global rows held and owned, and the
+// patch's global span-row count.
+struct WinSpec {
+  int row0, row1, own0, own1, SvG;
+};
+
+// Creates a context of `count` patches, or (win != nullptr, count == 1) of
+// the strip window `win` whose grid, rest coordinates and pinned list are
+// already the window's own (validated by the caller).
+static bsc_status create_ctx(int count, const bsc_knot_grid* grids, const double* const* rest_xy,
+                             const bsc_material* mats, const bsc_quadrature* q, const bsc_options* opts,
+                             void* stream, bsc_ctx** out, const WinSpec* win) {
   bsc_ctx* c = nullptr;
   if (!out) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: out is NULL");
   *out = nullptr;
@@ -248,8 +268,10 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
   if (!grids || !rest_xy || !mats || !opts) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create: NULL argument");
   long long Ntot = 0, Stot = 0;
   for (int p = 0; p < count; ++p) {
-    bsc_status st = validate_patch(p, &grids[p], rest_xy[p], &mats[p], &opts[p]);
-    if (st != BSC_OK) return st;
+    if (!win) {
+      bsc_status st = validate_patch(p, &grids[p], rest_xy[p], &mats[p], &opts[p]);
+      if (st != BSC_OK) return st;
+    }
     Ntot += (long long)grids[p].nu * grids[p].nv;
     Stot += (long long)(grids[p].nu - 2) * (grids[p].nv - 2);
   }
@@ -276,6 +298,8 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
       PatchDev& d = c->hpd[p];
       d.nu = grids[p].nu; d.nv = grids[p].nv; d.Su = d.nu - 2; d.Sv = d.nv - 2;
       d.N = d.nu * d.nv; d.Nsp = d.Su * d.Sv; d.cp0 = cp0; d.sp0 = sp0;
+      d.vb0 = win ? win->row0 : 0;
+      d.SvG = win ? win->SvG : d.Sv;
       d.mu1 = mats[p].mu_st1; d.mu2 = mats[p].mu_st2; d.mush = mats[p].mu_sh; d.mubd = mats[p].mu_bd;
       d.rho = mats[p].rho_area;
       d.inv_dt2 = opts[p].dt > 0.0 ? 1.0 / (opts[p].dt * opts[p].dt) : 0.0;
@@ -299,6 +323,12 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
   c->barrier_extra = 0u;
   c->solver_cnn = nullptr;
   c->contact = nullptr;
+  c->is_window = win ? 1 : 0;
+  if (win) {
+    c->win_row0 = win->row0; c->win_row1 = win->row1;
+    c->win_own0 = win->own0; c->win_own1 = win->own1;
+  }
+  c->win_x = c->win_p = nullptr;
   for (int k = 0; k < TILE_CLASSES; ++k) c->tile_tu[k] = 0;
 
   bsc_status st = BSC_OK;
@@ -402,8 +432,52 @@ bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double*
     return st;
   }
   c->K_last = nullptr;
+  c->K_last_sym = 0;
+  c->k_sym = 1;
   *out = c;
   return BSC_OK;
+}
+
+extern "C" {
+
+bsc_status bsc_create_batch(int count, const bsc_knot_grid* grids, const double* const* rest_xy,
+                            const bsc_material* mats, const bsc_quadrature* q, const bsc_options* opts,
+                            void* stream, bsc_ctx** out) {
+  return create_ctx(count, grids, rest_xy, mats, q, opts, stream, out, nullptr);
+}
+
+bsc_status bsc_create_window(const bsc_knot_grid* g, const double* rest_xy, const bsc_material* m,
+                             const bsc_quadrature* q, const bsc_options* o, const bsc_window* w, void* stream,
+                             bsc_ctx** out) {
+  if (!out) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create_window: out is NULL");
+  *out = nullptr;
+  if (!w) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create_window: NULL window");
+  bsc_status st = validate_patch(0, g, rest_xy, m, o);
+  if (st != BSC_OK) return st;
+  const int nu = g->nu, nv = g->nv;
+  const int r0 = w->row0, r1 = w->row1, o0 = w->own0, o1 = w->own1;
+  const int h0 = o0 < 2 ? o0 : 2, h1 = nv - o1 < 2 ? nv - o1 : 2;
+  if (!(0 <= o0 && o0 < o1 && o1 <= nv) || r0 != o0 - h0 || r1 != o1 + h1)
+    return fail(nullptr, BSC_ERR_INVALID_ARG,
+                "bsc_create_window: need 0 <= own0 < own1 <= nv and halos of two rows clipped to the grid "
+                "(row0 = own0 - min(2, own0), row1 = own1 + min(2, nv - own1)); got rows [%d, %d), owned [%d, %d), "
+                "nv = %d", r0, r1, o0, o1, nv);
+  if (r1 - r0 < 3) return fail(nullptr, BSC_ERR_INVALID_ARG, "bsc_create_window: a window needs 3 rows or more");
+  const int nw = r1 - r0;
+  std::vector<double> rest((size_t)2 * nu * nw);
+  for (size_t k = 0; k < (size_t)2 * nu * nw; ++k) rest[k] = rest_xy[(size_t)2 * nu * r0 + k];
+  std::vector<int32_t> pin;
+  for (int k = 0; k < o->n_pinned; ++k)
+    if (o->pinned[k] >= nu * r0 && o->pinned[k] < nu * r1) pin.push_back(o->pinned[k] - nu * r0);
+  bsc_knot_grid lg = *g;
+  lg.nv = nw;
+  lg.knots_v = nullptr;  // the window's span rows follow the global knots (PatchDev::vb0, SvG)
+  bsc_options lo = *o;
+  lo.n_pinned = (int)pin.size();
+  lo.pinned = pin.empty() ? nullptr : pin.data();
+  const double* rests[1] = {rest.data()};
+  const WinSpec ws{r0, r1, o0, o1, nv - 2};
+  return create_ctx(1, &lg, rests, m, q, &lo, stream, out, &ws);
 }
 
 bsc_status bsc_create(const bsc_knot_grid* g, const double* rest_xy, const bsc_material* m,
@@ -496,6 +570,7 @@ bsc_status bsc_assemble_hessian(bsc_ctx* c, const void* C, int project, void* K)
   if (st != BSC_OK) return st;
   CK(launch_assemble(c, Kd), "bsc_assemble_hessian");
   c->K_last = Kd;
+  c->K_last_sym = 0;
   return BSC_OK;
 }
 
@@ -504,14 +579,14 @@ bsc_status bsc_spmv(bsc_ctx* c, const void* K, const void* x, void* y) {
   const void* Kd = K ? K : c->K_last;
   if (!Kd || !x || !y) return fail(c, BSC_ERR_INVALID_ARG, "bsc_spmv: no matrix or NULL vector");
   if (x == y) return fail(c, BSC_ERR_INVALID_ARG, "bsc_spmv: x and y must not alias");
-  CK(launch_spmv(c, Kd, x, y), "bsc_spmv");
+  CK(launch_spmv(c, Kd, x, y, K ? 0 : c->K_last_sym), "bsc_spmv");
   return BSC_OK;
 }
 
 // Per-patch solves; pcg_out (3 per patch) is left in hscal (host, 3 P).
 static bsc_status solve_all(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit,
-                            std::vector<double>& hout) {
-  CK(launch_pcg(c, K, b, x, tol, maxit), "bsc_solve");
+                            std::vector<double>& hout, int sym = 0) {
+  CK(launch_pcg(c, K, b, x, tol, maxit, sym), "bsc_solve");
   hout.resize(3 * (size_t)c->P);
   CK(cudaMemcpyAsync(hout.data(), c->pcg_out, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToHost, c->stream),
      "bsc_solve");
@@ -521,13 +596,14 @@ static bsc_status solve_all(bsc_ctx* c, const void* K, const void* b, void* x, d
 bsc_status bsc_solve(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit, int* iters,
                      double* rel_res) {
   if (!c) return BSC_ERR_INVALID_ARG;
+  if (c->is_window) return fail(c, BSC_ERR_INVALID_ARG, "bsc_solve: a strip window solves with bsc_window_pcg_*");
   const void* Kd = K ? K : c->K_last;
   if (!Kd || !b || !x) return fail(c, BSC_ERR_INVALID_ARG, "bsc_solve: no matrix or NULL vector");
   if (b == x) return fail(c, BSC_ERR_INVALID_ARG, "bsc_solve: b and x must not alias");
   if (!(tol > 0.0)) tol = c->pcg_tol;
   if (maxit <= 0) maxit = c->pcg_max_iter;
   std::vector<double> hout;
-  bsc_status st = solve_all(c, Kd, b, x, tol, maxit, hout);
+  bsc_status st = solve_all(c, Kd, b, x, tol, maxit, hout, K ? 0 : c->K_last_sym);
   if (st != BSC_OK) return st;
   int it = 0;
   double rr = 0.0;
@@ -561,6 +637,8 @@ static void fill_report(const bsc_ctx* c, const PatchStep& s, bsc_newton_report&
 
 bsc_status bsc_newton_step(bsc_ctx* c, void* C, const void* Chat, bsc_newton_report* rep) {
   if (!c) return BSC_ERR_INVALID_ARG;
+  if (c->is_window)
+    return fail(c, BSC_ERR_INVALID_ARG, "bsc_newton_step: a strip window steps with its ranks (bsc_window_pcg_*)");
   bsc_newton_report agg;
   memset(&agg, 0, sizeof(agg));
   if (rep) *rep = agg;
@@ -586,6 +664,7 @@ bsc_status bsc_newton_step(bsc_ctx* c, void* C, const void* Chat, bsc_newton_rep
   }
   CK(cudaStreamSynchronize(c->stream), "bsc_newton_step");
   c->K_last = c->K_int;
+  c->K_last_sym = newton_sym(c);
   // further line-search rounds for the patches that rejected alpha = 1
   int round = 1;
   while (c->hflags[0] > 0 && c->hflags[1] == 0 && round <= c->max_ls) {
@@ -662,7 +741,8 @@ bsc_status bsc_set_material(bsc_ctx* c, int p, const bsc_material* m) {
 
 bsc_status bsc_set_learned_solver(bsc_ctx* c, bsc_cnn* n) {
   if (!c) return BSC_ERR_INVALID_ARG;
-  if (n && c->P != 1) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_learned_solver: single-patch contexts only");
+  if (n && (c->P != 1 || c->is_window))
+    return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_learned_solver: single-patch contexts only (no strip windows)");
   CK(cudaStreamSynchronize(c->gstream), "bsc_set_learned_solver");
   c->solver_cnn = n;
   drop_graph(c);
@@ -749,9 +829,17 @@ bsc_status bsc_set_psd_test(bsc_ctx* c, int on) {
 
 bsc_status bsc_set_pcg_form(bsc_ctx* c, int form) {
   if (!c) return BSC_ERR_INVALID_ARG;
-  if (form != 0 && form != 1) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_pcg_form: form must be 0 or 1");
+  if (form < 0 || form > 2) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_pcg_form: form must be 0, 1 or 2");
   CK(cudaStreamSynchronize(c->gstream), "bsc_set_pcg_form");
   c->pcg_form = form;
+  drop_graph(c);
+  return BSC_OK;
+}
+
+bsc_status bsc_set_k_storage(bsc_ctx* c, int symmetric) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_k_storage");
+  c->k_sym = symmetric ? 1 : 0;
   drop_graph(c);
   return BSC_OK;
 }
@@ -768,6 +856,7 @@ bsc_status bsc_pcg_split(const bsc_ctx* c, int* blocks) {
 
 bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning* out) {
   if (!c || !C) return BSC_ERR_INVALID_ARG;
+  if (c->is_window) return fail(c, BSC_ERR_INVALID_ARG, "bsc_autotune: not for strip windows");
   if (any_inertia(c) && !Chat) return fail(c, BSC_ERR_INVALID_ARG, "bsc_autotune: NULL argument");
   bsc_tuning t;
   memset(&t, 0, sizeof(t));
@@ -889,14 +978,16 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
     st = eval_path(c, C, 1, 1, c->project_default);
     if (st != BSC_OK) return st;
     CK(launch_gradient(c, C, Chat, g), "bsc_autotune");
-    CK(launch_assemble(c, c->K_int), "bsc_autotune");
+    const int sym = newton_sym(c);  // the Newton step's own layout
+    CK(launch_assemble(c, c->K_int, sym), "bsc_autotune");
     CK(launch_axpy_trial(c, g, g, -2.0, rhs), "bsc_autotune");
     std::vector<double> hout;
-    st = solve_all(c, c->K_int, rhs, x, c->pcg_tol, c->pcg_max_iter, hout);
+    st = solve_all(c, c->K_int, rhs, x, c->pcg_tol, c->pcg_max_iter, hout, sym);
     if (st != BSC_OK) return st;
     for (int p = 0; p < c->P; ++p) c->pcg_weight[p] = (double)c->hpd[p].N * std::max(1.0, hout[3 * p]);
     CK(assign_pcg_blocks(c), "bsc_autotune");
     c->K_last = c->K_int;
+    c->K_last_sym = sym;
     // grid of the persistent PCG: a block per two SMs, one or two per SM, or
     // a thread per control point (at most the co-resident capacity), timed
     const int cand[4] = {c->num_sms / 2, c->num_sms, 2 * c->num_sms, c->pcg_need};
@@ -916,7 +1007,7 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
       float ms = 0.0f, best_rep = 1e30f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         e = cudaEventRecord(a0, c->stream);
-        if (e == cudaSuccess) e = launch_pcg(c, c->K_int, rhs, x, c->pcg_tol, c->pcg_max_iter);
+        if (e == cudaSuccess) e = launch_pcg(c, c->K_int, rhs, x, c->pcg_tol, c->pcg_max_iter, sym);
         if (e == cudaSuccess) e = cudaEventRecord(a1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(a1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a0, a1);
@@ -926,15 +1017,15 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
       if (best < 0 || best_rep < t.pcg_ms[best]) best = k;
     }
     if (e == cudaSuccess && best >= 0) e = set_pcg_grid(c, t.pcg_grid_cand[best]);
-    // the PCG's form at that grid: three group barriers per iteration, or the
-    // pipelined recurrences with one
+    // the PCG's form at that grid: three group barriers per iteration, the
+    // pipelined recurrences with one, or two passes with two
     const int form0 = c->pcg_form;
-    for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
+    for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
       c->pcg_form = f;
       float ms = 0.0f, best_rep = 1e30f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         e = cudaEventRecord(a0, c->stream);
-        if (e == cudaSuccess) e = launch_pcg(c, c->K_int, rhs, x, c->pcg_tol, c->pcg_max_iter);
+        if (e == cudaSuccess) e = launch_pcg(c, c->K_int, rhs, x, c->pcg_tol, c->pcg_max_iter, sym);
         if (e == cudaSuccess) e = cudaEventRecord(a1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(a1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a0, a1);
@@ -962,7 +1053,14 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
         }
       }
     }
-    c->pcg_form = e == cudaSuccess ? (t.pcg_form_ms[1] < t.pcg_form_ms[0] ? 1 : 0) : form0;
+    if (e == cudaSuccess) {
+      int fb = 0;
+      for (int f = 1; f < 3; ++f)
+        if (t.pcg_form_ms[f] < t.pcg_form_ms[fb]) fb = f;
+      c->pcg_form = fb;
+    } else {
+      c->pcg_form = form0;
+    }
     cudaEventDestroy(a0);
     cudaEventDestroy(a1);
     if (e != cudaSuccess) return cuda_fail(c, e, "bsc_autotune: timing the PCG grid");

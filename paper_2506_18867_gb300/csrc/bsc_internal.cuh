@@ -31,8 +31,13 @@ constexpr int MAXQ_BD = 4;
 // concatenated spans ([sp0, sp0 + Nsp)).  Within a patch the usual
 // tensor-product numbering holds: control point alpha = j nu + i, span
 // s = b Su + a.
+// One patch of a context.  A strip window of a larger patch (bsc_create_window)
+// holds the control-point rows [vb0, vb0 + nv) of a patch with SvG span rows:
+// its spans are the global span rows vb0 .. vb0 + Sv - 1, and the quadrature
+// rule and knots follow the global row (vb0 = 0, SvG = Sv for a whole patch).
 struct PatchDev {
   int nu, nv, Su, Sv, N, Nsp, cp0, sp0;
+  int vb0, SvG;
   double mu1, mu2, mush, mubd, rho, inv_dt2;
   double grav[3];
   double pad;
@@ -149,6 +154,8 @@ struct bsc_ctx {
   // global objects
   void* K_int;        // T [225][N]
   const void* K_last; // last assembled matrix (internal or caller's)
+  int K_last_sym;     // K_last in the symmetric layout (13 slots; the Newton step's own matrix)
+  int k_sym;          // the Newton step assembles and solves in the symmetric layout (default 1)
   void* Dinv;         // T [9][N] block-Jacobi preconditioner of K_last
   void* vec[8];       // T [3][N] work vectors: d, r, z, p, q, g, trial C, spare
   double* partials;   // [4][max(red_grid, pcg_grid, n_red_items)] reduction partials
@@ -181,6 +188,12 @@ struct bsc_ctx {
   double* fcg_rec;
   // contact with a static obstacle (bsc_contact_attach), or nullptr
   struct bsc_contact* contact;
+  // strip window (bsc_create_window): 1, the global rows [win_row0, win_row1)
+  // held and [win_own0, win_own1) owned; the caller's solution and direction
+  // planes of the strip PCG
+  int is_window;
+  int win_row0, win_row1, win_own0, win_own1;
+  void *win_x, *win_p;
   // bounded device waits of the persistent solvers: spin limit, and blocks
   // their barriers expect beyond the launched ones (0; > 0 only to test the
   // timeout path, see bsc_set_wait_limit)
@@ -233,13 +246,14 @@ cudaError_t launch_project(bsc_ctx* c);
 // the border class alone by the given path, on the context's stream (autotuner)
 cudaError_t launch_project_border(bsc_ctx* c, int path);
 cudaError_t launch_project_interior(bsc_ctx* c, int phase);
-cudaError_t launch_assemble(bsc_ctx* c, void* K);
+cudaError_t launch_assemble(bsc_ctx* c, void* K, int sym = 0);
 cudaError_t launch_gradient(bsc_ctx* c, const void* C, const void* Chat, void* g);
 // per-patch incremental potential into dE[p] (with a gate: pending patches only)
 cudaError_t launch_patch_energy(bsc_ctx* c, const void* C, const void* Chat, double* dE,
                                 const PatchStep* gate = nullptr);
-cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y);
-cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit);
+// sym: K in the symmetric stencil layout (13 slots, see spmv_row_sym)
+cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y, int sym = 0);
+cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit, int sym = 0);
 // PCG as the fallback of a learned flexible-CG solve: it reads that solve's
 // result record (iterations, r.r, state) and b.b on the device, returns at
 // once (x = 0) when the flexible CG converged, and otherwise solves K x = b
@@ -267,6 +281,12 @@ cudaError_t contact_step_bound(bsc_ctx* c, const void* C, const void* D);
 void contact_destroy(bsc_ctx* c);
 // the step bound on the device (nullptr without contact)
 const double* contact_bound_ptr(const bsc_ctx* c);
+// error helpers of the C ABI (bsc_api.cu): message into the context (or the
+// thread's create message), CUDA error, status word read-back and clear
+bsc_status fail(bsc_ctx* c, bsc_status st, const char* fmt, ...);
+bsc_status cuda_fail(bsc_ctx* c, cudaError_t e, const char* where);
+bsc_status check_status(bsc_ctx* c, const char* where);
+bool aligned16(const void* p);
 // Newton step pieces (k_newton.cu)
 cudaError_t launch_step_begin(bsc_ctx* c, const void* d);
 cudaError_t launch_ls_round(bsc_ctx* c, const void* C, const void* Chat, const void* d, void* trial, void* Cout,
@@ -367,6 +387,41 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsig
   return group_barrier(count, gen, status, gridDim.x + extra, limit);
 }
 
+// z = D r with D the 3x3 block (9 planes, stride N) of control point al.
+template <typename T>
+__device__ __forceinline__ void apply_dinv(const T* __restrict__ Dinv, int N, int al, const T r[3], T z[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    z[c] = Dinv[(3 * c) * N + al] * r[0] + Dinv[(3 * c + 1) * N + al] * r[1] + Dinv[(3 * c + 2) * N + al] * r[2];
+}
+
+// Inverse of control point al's 3x3 diagonal block of K (stencil slot 12) by
+// adjugate / determinant in FP64 into Dinv; a singular or non-finite block
+// raises the NUMERIC flag.
+template <typename T>
+__device__ __forceinline__ void block_jacobi_at(int N, int al, const T* __restrict__ K, T* __restrict__ Dinv,
+                                                int* status, int slot = 12 /* du = dv = 0 */) {
+  double a[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) a[k] = (double)K[(size_t)(slot * 9 + k) * N + al];
+  const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+  const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  if (!(fabs(det) > 0.0) || !isfinite(det)) atomicOr(status, BSC_STATUS_NUMERIC_FLAG);
+  const double id = 1.0 / det;
+  double b[9];
+  b[0] = c00 * id;
+  b[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+  b[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+  b[3] = c01 * id;
+  b[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+  b[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+  b[6] = c02 * id;
+  b[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+  b[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Dinv[(size_t)k * N + al] = (T)b[k];
+}
+
 // Row alpha (patch-local index) of y = K x in the element type T; K and x
 // already point at the patch's first control point, N is the plane stride.
 // X_MODE 1: x stays unchanged for the whole kernel, so it may go through the
@@ -410,6 +465,54 @@ __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T*
         y1 += Kb[(size_t)3 * N] * x0 + Kb[(size_t)4 * N] * x1 + Kb[(size_t)5 * N] * x2;
         y2 += Kb[(size_t)6 * N] * x0 + Kb[(size_t)7 * N] * x1 + Kb[(size_t)8 * N] * x2;
       }
+    }
+  }
+  y[0] = y0; y[1] = y1; y[2] = y2;
+}
+
+// Row alpha of y = K x with K in the symmetric stencil layout: 13 slots, the
+// diagonal block and the 12 blocks coupling alpha to the neighbours after it
+// (dv > 0, or dv = 0 and du > 0), slot s' = stencil slot - 12, plane
+// (s' * 9 + 3 r + c).  A block before alpha is the transpose of the
+// neighbour's block after it, B(alpha, beta) = B(beta, alpha)^T, read from
+// the neighbour's row (consecutive alpha read consecutive beta).  Entries and
+// accumulation order are those of spmv_row, so both layouts give the same
+// product bit for bit; K is read once per product instead of twice.
+template <typename T, int X_MODE = 0>
+__device__ __forceinline__ void spmv_row_sym(int nu, int nv, int N, int al, const T* __restrict__ K, const T* x,
+                                             T y[3]) {
+  const int i = al % nu, j = al / nu;
+  T y0 = T(0), y1 = T(0), y2 = T(0);
+#pragma unroll
+  for (int dv = -2; dv <= 2; ++dv) {
+    const int jb = j + dv;
+    if (jb < 0 || jb >= nv) continue;
+#pragma unroll
+    for (int du = -2; du <= 2; ++du) {
+      const int ib = i + du;
+      if (ib < 0 || ib >= nu) continue;
+      const int slot = (dv + 2) * 5 + (du + 2), be = jb * nu + ib;
+      T x0, x1, x2;
+      if (X_MODE == 1) {
+        x0 = __ldg(x + be); x1 = __ldg(x + N + be); x2 = __ldg(x + 2 * N + be);
+      } else {
+        x0 = x[be]; x1 = x[N + be]; x2 = x[2 * N + be];
+      }
+      T k[9];
+      if (slot >= 12) {
+        const T* Kb = K + (size_t)(slot - 12) * 9 * N + al;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) k[e] = Kb[(size_t)e * N];
+      } else {
+        const T* Kb = K + (size_t)(12 - slot) * 9 * N + be;  // the neighbour's slot 24 - slot, transposed
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) k[3 * r + c] = Kb[(size_t)(3 * c + r) * N];
+      }
+      y0 = fma(k[2], x2, fma(k[1], x1, fma(k[0], x0, y0)));
+      y1 = fma(k[5], x2, fma(k[4], x1, fma(k[3], x0, y1)));
+      y2 = fma(k[8], x2, fma(k[7], x1, fma(k[6], x0, y2)));
     }
   }
   y[0] = y0; y[1] = y1; y[2] = y2;

@@ -22,13 +22,18 @@
 
 namespace {
 
-template <typename T>
+// SYM: only the diagonal block and the 12 blocks after it (stencil slots
+// 12..24), written as slots 0..12 of the symmetric layout; the blocks before
+// a row are the transposes of its neighbours' (the gathers of (alpha, beta)
+// and (beta, alpha) add the same span entries in the same order).
+template <typename T, bool SYM>
 __global__ void k_assemble(int N, int Nsp, const PatchDev* __restrict__ pd, const int* __restrict__ cp_patch,
                            const T* __restrict__ H, const double* __restrict__ mass,
                            const uint8_t* __restrict__ pinned, T* __restrict__ K) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 25ll * N) return;
-  const int slot = (int)(t / N), al = (int)(t - (long long)slot * N);
+  if (t >= (SYM ? 13ll : 25ll) * N) return;
+  const int s_out = (int)(t / N), al = (int)(t - (long long)s_out * N);
+  const int slot = SYM ? s_out + 12 : s_out;
   const PatchDev* pt = pd + cp_patch[al];
   const int nu = __ldg(&pt->nu), nv = __ldg(&pt->nv), Su = nu - 2, Sv = nv - 2;
   const int cp0 = __ldg(&pt->cp0), sp0 = __ldg(&pt->sp0);
@@ -64,7 +69,7 @@ __global__ void k_assemble(int N, int Nsp, const PatchDev* __restrict__ pd, cons
     }
   }
 #pragma unroll
-  for (int k = 0; k < 9; ++k) K[(size_t)(slot * 9 + k) * N + al] = blk[k];
+  for (int k = 0; k < 9; ++k) K[(size_t)(s_out * 9 + k) * N + al] = blk[k];
 }
 
 template <typename T>
@@ -179,12 +184,24 @@ __global__ void k_export_span(int Nsp, const T* __restrict__ gs, const T* __rest
 // of RED_CHUNK, grouped by patch.
 constexpr int RED_CHUNK = 2048;
 
+// A strip window (one patch) instead has one item per owned row: the span
+// rows whose middle control-point row it owns, then its owned control-point
+// rows.  A row's partial sum then depends on the row alone, not on the
+// window, so the ranks of a decomposition can add them up in the global row
+// order and all decompositions of a patch agree bit for bit.
 cudaError_t build_red_items(bsc_ctx* c) {
   std::vector<RedItem> items;
   std::vector<int> off(c->P + 1);
   for (int p = 0; p < c->P; ++p) {
     off[p] = (int)items.size();
     const PatchDev& q = c->hpd[p];
+    if (c->is_window) {
+      const int r0 = c->win_row0;
+      const int b0 = std::max(c->win_own0 - 1, 0), b1 = std::min(c->win_own1 - 1, q.SvG);
+      for (int b = b0; b < b1; ++b) items.push_back(RedItem{p, 0, (b - r0) * q.Su, (b - r0 + 1) * q.Su});
+      for (int j = c->win_own0; j < c->win_own1; ++j) items.push_back(RedItem{p, 1, (j - r0) * q.nu, (j - r0 + 1) * q.nu});
+      continue;
+    }
     for (int lo = 0; lo < q.Nsp; lo += RED_CHUNK) items.push_back(RedItem{p, 0, lo, std::min(lo + RED_CHUNK, q.Nsp)});
     for (int lo = 0; lo < q.N; lo += RED_CHUNK) items.push_back(RedItem{p, 1, lo, std::min(lo + RED_CHUNK, q.N)});
   }
@@ -199,16 +216,29 @@ cudaError_t build_red_items(bsc_ctx* c) {
   return cudaMemcpy(c->red_off, off.data(), sizeof(int) * (c->P + 1), cudaMemcpyHostToDevice);
 }
 
-cudaError_t launch_assemble(bsc_ctx* c, void* K) {
+cudaError_t launch_assemble(bsc_ctx* c, void* K, int sym) {
   BSC_COUNT(c, 1);
   const int B = 256;
-  const long long G = (25ll * c->N + B - 1) / B;
-  if (c->precision == BSC_FP64)
-    k_assemble<double><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch, (const double*)c->H_span,
-                                                        c->mass, c->pinned, (double*)K);
-  else
-    k_assemble<float><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch, (const float*)c->H_span,
-                                                       c->mass, c->pinned, (float*)K);
+  const long long G = ((sym ? 13ll : 25ll) * c->N + B - 1) / B;
+  if (c->precision == BSC_FP64) {
+    if (sym)
+      k_assemble<double, true><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch,
+                                                                 (const double*)c->H_span, c->mass, c->pinned,
+                                                                 (double*)K);
+    else
+      k_assemble<double, false><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch,
+                                                                  (const double*)c->H_span, c->mass, c->pinned,
+                                                                  (double*)K);
+  } else {
+    if (sym)
+      k_assemble<float, true><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch,
+                                                                (const float*)c->H_span, c->mass, c->pinned,
+                                                                (float*)K);
+    else
+      k_assemble<float, false><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch,
+                                                                 (const float*)c->H_span, c->mass, c->pinned,
+                                                                 (float*)K);
+  }
   return cudaGetLastError();
 }
 

@@ -1360,6 +1360,7 @@ bsc_status bsc_solve_fcg(bsc_ctx* c, bsc_cnn* n, const void* K, const void* b, v
                          bsc_fcg_report* rep) {
   if (!c || !n || n->c != c || !K || !b || !x) return BSC_ERR_INVALID_ARG;
   if (b == x) return cnn_fail(n, BSC_ERR_INVALID_ARG, "bsc_solve_fcg: b and x must not alias");
+  if (c->is_window) return cnn_fail(n, BSC_ERR_INVALID_ARG, "bsc_solve_fcg: not for strip windows");
   if (!(tol > 0.0)) tol = c->pcg_tol;
   if (maxit <= 0) maxit = c->pcg_max_iter;
   bsc_fcg_report R;

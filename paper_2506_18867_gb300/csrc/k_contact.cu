@@ -473,7 +473,8 @@ extern "C" {
 bsc_status bsc_contact_attach(bsc_ctx* c, const double* obs_xyz, int nvo, const int32_t* tris, int nto, int mu,
                               int mv, double dhat, double kappa) {
   if (!c) return BSC_ERR_INVALID_ARG;
-  if (c->P != 1) return cfail(c, BSC_ERR_INVALID_ARG, "bsc_contact_attach: single-patch contexts only");
+  if (c->P != 1 || c->is_window)
+    return cfail(c, BSC_ERR_INVALID_ARG, "bsc_contact_attach: single-patch contexts only (no strip windows)");
   if (!obs_xyz || !tris || nvo < 3 || nto < 1)
     return cfail(c, BSC_ERR_INVALID_ARG, "bsc_contact_attach: the obstacle needs >= 3 vertices and >= 1 triangle");
   if (!(dhat > 0.0) || !isfinite(dhat) || !(kappa >= 0.0) || !isfinite(kappa))

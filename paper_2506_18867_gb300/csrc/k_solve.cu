@@ -15,6 +15,7 @@
 // the group computes the same scalars and the result is bitwise reproducible
 // for a given split.  Group barriers are bounded (they raise a timeout flag
 // instead of waiting forever).
+#include <algorithm>
 #include <vector>
 
 #include "bsc_internal.cuh"
@@ -64,31 +65,28 @@ __global__ void __launch_bounds__(256) k_spmv(int N, const PatchDev* __restrict_
   y[(size_t)c * N + al] = acc0 + acc1 + acc2;
 }
 
-// Inverse of each 3x3 diagonal block (adjugate / determinant, FP64).
+// Stand-alone SpMV with K in the symmetric layout: a thread per control point.
 template <typename T>
-__global__ void k_block_jacobi(int N, const T* __restrict__ K, T* __restrict__ Dinv, int* status) {
+__global__ void __launch_bounds__(256) k_spmv_sym(int N, const PatchDev* __restrict__ pd,
+                                                  const int* __restrict__ cp_patch, const T* __restrict__ K,
+                                                  const T* __restrict__ x, T* __restrict__ y) {
   const int al = blockIdx.x * blockDim.x + threadIdx.x;
   if (al >= N) return;
-  const int slot = 12;  // du = dv = 0
-  double a[9];
+  const PatchDev* pt = pd + cp_patch[al];
+  const int cp0 = __ldg(&pt->cp0), nu = __ldg(&pt->nu), nv = __ldg(&pt->nv);
+  T o[3];
+  spmv_row_sym<T, 1>(nu, nv, N, al - cp0, K + cp0, x + cp0, o);
 #pragma unroll
-  for (int k = 0; k < 9; ++k) a[k] = (double)K[(size_t)(slot * 9 + k) * N + al];
-  const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
-  const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-  if (!(fabs(det) > 0.0) || !isfinite(det)) atomicOr(status, BSC_STATUS_NUMERIC_FLAG);
-  const double id = 1.0 / det;
-  double b[9];
-  b[0] = c00 * id;
-  b[1] = (a[2] * a[7] - a[1] * a[8]) * id;
-  b[2] = (a[1] * a[5] - a[2] * a[4]) * id;
-  b[3] = c01 * id;
-  b[4] = (a[0] * a[8] - a[2] * a[6]) * id;
-  b[5] = (a[2] * a[3] - a[0] * a[5]) * id;
-  b[6] = c02 * id;
-  b[7] = (a[1] * a[6] - a[0] * a[7]) * id;
-  b[8] = (a[0] * a[4] - a[1] * a[3]) * id;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) Dinv[(size_t)k * N + al] = (T)b[k];
+  for (int c = 0; c < 3; ++c) y[(size_t)c * N + al] = o[c];
+}
+
+// Inverse of each 3x3 diagonal block (adjugate / determinant, FP64); slot:
+// the diagonal block's slot (12 in the full layout, 0 in the symmetric one).
+template <typename T>
+__global__ void k_block_jacobi(int N, const T* __restrict__ K, T* __restrict__ Dinv, int* status, int slot) {
+  const int al = blockIdx.x * blockDim.x + threadIdx.x;
+  if (al >= N) return;
+  block_jacobi_at<T>(N, al, K, Dinv, status, slot);
 }
 
 template <typename T>
@@ -128,14 +126,14 @@ __device__ __forceinline__ double group_sum(const double* part, int n, double* s
   return bcast;
 }
 
-template <typename T>
-__device__ __forceinline__ void apply_dinv(const T* __restrict__ Dinv, int N, int al, const T r[3], T z[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    z[c] = Dinv[(3 * c) * N + al] * r[0] + Dinv[(3 * c + 1) * N + al] * r[1] + Dinv[(3 * c + 2) * N + al] * r[2];
-}
-
-template <typename T, int BLOCK>
+// FORM 0: three passes and group barriers per iteration (q = K p; x, r, z;
+// p = z + beta p).  FORM 2: two, by linearity of the product: the first pass
+// forms w = K z and updates q = w + beta q and p = z + beta p in place (q
+// stays K p up to rounding), the second updates x, r, z; the direction no
+// longer needs a pass and a barrier of its own.  Same iterates in exact
+// arithmetic; q is carried by a recurrence, as r is in both forms.
+// SYM: K in the symmetric layout (spmv_row_sym; the same products).
+template <typename T, int BLOCK, int FORM, bool SYM>
 __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
   __shared__ double sm[BLOCK / 32];
   const int G = gridDim.x, N = A.N;
@@ -200,7 +198,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       zv[c * N + al] = zz[c];
-      pv[c * N + al] = zz[c];
+      pv[c * N + al] = FORM == 2 ? T(0) : zz[c];
+      if (FORM == 2) qv[c * N + al] = T(0);
       l_rz += (double)rr[c] * (double)zz[c];
       l_bb += (double)rr[c] * (double)rr[c];
     }
@@ -226,18 +225,38 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
   const double bb = group_sum<BLOCK>(part1, gsize, sm);
   const double stop2 = tol * tol * bb;
   int it = 0;
-  double rr_glob = bb;
+  double rr_glob = bb, beta = 0.0;
   bool ok = true;
   if (bb > 0.0) {
     for (it = 1; it <= A.maxit; ++it) {
       double l_pq = 0.0;
-      for (int al = tid; al < Np; al += stride) {
-        T y[3];
-        spmv_row<T>(nu, nv, N, al, K, pv, y);  // plain loads of the neighbours' p (measured faster here than via L2)
+      if (FORM == 2) {
+        const T tb = (T)beta;
+        for (int al = tid; al < Np; al += stride) {
+          T y[3];
+          if (SYM) spmv_row_sym<T>(nu, nv, N, al, K, zv, y);
+          else spmv_row<T>(nu, nv, N, al, K, zv, y);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          qv[c * N + al] = y[c];
-          l_pq += (double)pv[c * N + al] * (double)y[c];
+          for (int c = 0; c < 3; ++c) {
+            const int k = c * N + al;
+            const T q_ = y[c] + tb * qv[k];
+            const T p_ = zv[k] + tb * pv[k];
+            qv[k] = q_;
+            pv[k] = p_;
+            l_pq += (double)p_ * (double)q_;
+          }
+        }
+      } else {
+        for (int al = tid; al < Np; al += stride) {
+          T y[3];
+          // plain loads of the neighbours' p (measured faster here than via L2)
+          if (SYM) spmv_row_sym<T>(nu, nv, N, al, K, pv, y);
+          else spmv_row<T>(nu, nv, N, al, K, pv, y);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            qv[c * N + al] = y[c];
+            l_pq += (double)pv[c * N + al] * (double)y[c];
+          }
         }
       }
       {
@@ -282,13 +301,15 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
       const double rz2 = group_sum<BLOCK>(part0, gsize, sm);
       rr_glob = group_sum<BLOCK>(part1, gsize, sm);
       if (rr_glob <= stop2 || !isfinite(rr_glob)) break;
-      const double beta = rz2 / rz;
-      const T tb = (T)beta;
+      beta = rz2 / rz;
       rz = rz2;
-      for (int al = tid; al < Np; al += stride)
+      if (FORM == 0) {
+        const T tb = (T)beta;
+        for (int al = tid; al < Np; al += stride)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) pv[c * N + al] = zv[c * N + al] + tb * pv[c * N + al];
-      if (!(ok = group_barrier(cnt, gen, A.status, nb, lim))) break;
+          for (int c = 0; c < 3; ++c) pv[c * N + al] = zv[c * N + al] + tb * pv[c * N + al];
+        if (!(ok = group_barrier(cnt, gen, A.status, nb, lim))) break;
+      }
     }
   }
   if (rank == 0 && threadIdx.x == 0) {
@@ -323,8 +344,10 @@ struct PipeVecs {
   T* __restrict__ z2;   // z of the recurrences (K m carried)
 };
 
-template <typename T, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_pcg_pipe(PcgArgs<T> A, PipeVecs<T> V) {
+// Register-capped to the four blocks of 256 per SM of the other forms: all
+// forms share one grid, the co-resident capacity of the most demanding.
+template <typename T, int BLOCK, bool SYM>
+__global__ void __launch_bounds__(BLOCK, 4) k_pcg_pipe(PcgArgs<T> A, PipeVecs<T> V) {
   __shared__ double sm[BLOCK / 32];
   const int G = gridDim.x, N = A.N;
   int pp = 0, rank = blockIdx.x, gsize = G, gfirst = 0;
@@ -410,7 +433,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_pipe(PcgArgs<T> A, PipeVecs<T> V)
     double l_g = 0.0, l_d = 0.0, l_r = 0.0;
     for (int al = tid; al < Np; al += stride) {
       T ww[3], mm[3];
-      spmv_row<T>(nu, nv, N, al, K, uv, ww);
+      if (SYM) spmv_row_sym<T>(nu, nv, N, al, K, uv, ww);
+      else spmv_row<T>(nu, nv, N, al, K, uv, ww);
       apply_dinv<T>(Dinv, N, al, ww, mm);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -459,7 +483,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_pipe(PcgArgs<T> A, PipeVecs<T> V)
       double l_g = 0.0, l_d = 0.0, l_r = 0.0;
       for (int al = tid; al < Np; al += stride) {
         T nn[3];
-        spmv_row<T>(nu, nv, N, al, K, mc, nn);
+        if (SYM) spmv_row_sym<T>(nu, nv, N, al, K, mc, nn);
+        else spmv_row<T>(nu, nv, N, al, K, mc, nn);
         T ww[3], uu[3], rr_[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -537,26 +562,31 @@ cudaLaunchConfig_t coop_config(int grid, cudaStream_t st, cudaLaunchAttribute* a
 }
 
 template <typename T>
-cudaError_t launch_coop(int grid, PcgArgs<T> A, cudaStream_t st) {
+cudaError_t launch_coop(int grid, PcgArgs<T> A, cudaStream_t st, int form = 0, int sym = 0) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = coop_config<T>(grid, st, attr);
-  return cudaLaunchKernelEx(&cfg, k_pcg<T, PCG_BLOCK>, A);
+  if (form == 2)
+    return sym ? cudaLaunchKernelEx(&cfg, k_pcg<T, PCG_BLOCK, 2, true>, A)
+               : cudaLaunchKernelEx(&cfg, k_pcg<T, PCG_BLOCK, 2, false>, A);
+  return sym ? cudaLaunchKernelEx(&cfg, k_pcg<T, PCG_BLOCK, 0, true>, A)
+             : cudaLaunchKernelEx(&cfg, k_pcg<T, PCG_BLOCK, 0, false>, A);
 }
 
 template <typename T>
-cudaError_t launch_coop_pipe(int grid, PcgArgs<T> A, PipeVecs<T> V, cudaStream_t st) {
+cudaError_t launch_coop_pipe(int grid, PcgArgs<T> A, PipeVecs<T> V, cudaStream_t st, int sym = 0) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = coop_config<T>(grid, st, attr);
-  return cudaLaunchKernelEx(&cfg, k_pcg_pipe<T, PCG_BLOCK>, A, V);
+  return sym ? cudaLaunchKernelEx(&cfg, k_pcg_pipe<T, PCG_BLOCK, true>, A, V)
+             : cudaLaunchKernelEx(&cfg, k_pcg_pipe<T, PCG_BLOCK, false>, A, V);
 }
 
 template <typename T>
-cudaError_t pcg_t(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit,
+cudaError_t pcg_t(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit, int sym,
                   const double* gate = nullptr, const double* gate_bb = nullptr) {
   const int N = c->N;
   cudaError_t e;
   if ((e = cudaMemsetAsync(c->sync, 0, sizeof(unsigned int) * 2 * (size_t)c->P, c->stream)) != cudaSuccess) return e;
-  k_block_jacobi<T><<<(N + 255) / 256, 256, 0, c->stream>>>(N, (const T*)K, (T*)c->Dinv, c->dstatus);
+  k_block_jacobi<T><<<(N + 255) / 256, 256, 0, c->stream>>>(N, (const T*)K, (T*)c->Dinv, c->dstatus, sym ? 0 : 12);
   PcgArgs<T> A;
   A.N = N; A.maxit = maxit; A.tol = tol;
   A.pd = c->pd; A.blocks = c->pcg_blocks; A.nu = c->nu; A.nv = c->nv;
@@ -569,9 +599,9 @@ cudaError_t pcg_t(bsc_ctx* c, const void* K, const void* b, void* x, double tol,
     PipeVecs<T> V;
     V.u = (T*)c->pcg_pipe[0]; V.w = (T*)c->pcg_pipe[1]; V.m0 = (T*)c->pcg_pipe[2]; V.m1 = (T*)c->pcg_pipe[3];
     V.s = (T*)c->pcg_pipe[4]; V.z2 = (T*)c->pcg_pipe[5];
-    return launch_coop_pipe<T>(c->pcg_grid, A, V, c->stream);
+    return launch_coop_pipe<T>(c->pcg_grid, A, V, c->stream, sym);
   }
-  return launch_coop<T>(c->pcg_grid, A, c->stream);
+  return launch_coop<T>(c->pcg_grid, A, c->stream, c->pcg_form, sym);
 }
 
 }  // namespace
@@ -612,18 +642,26 @@ extern "C" int bsc_plan_blocks(int count, const int* n_cp, const double* work, i
 // of 256 threads per SM: the SpMV rows are latency-bound loads, and 1024
 // threads per SM keep enough of them in flight), capped by what the patches
 // can use; per-patch work estimates start at the control-point counts.
+template <typename T>
+cudaError_t pcg_occupancy(int* per_sm) {
+  const void* fns[6] = {(const void*)k_pcg<T, PCG_BLOCK, 0, false>, (const void*)k_pcg<T, PCG_BLOCK, 2, false>,
+                        (const void*)k_pcg<T, PCG_BLOCK, 0, true>,  (const void*)k_pcg<T, PCG_BLOCK, 2, true>,
+                        (const void*)k_pcg_pipe<T, PCG_BLOCK, false>, (const void*)k_pcg_pipe<T, PCG_BLOCK, true>};
+  cudaError_t e = cudaSuccess;
+  *per_sm = 1 << 30;
+  for (const void* f : fns) {
+    int n = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, PCG_BLOCK, 0)) != cudaSuccess) return e;
+    *per_sm = std::min(*per_sm, n);
+  }
+  return e;
+}
+
 cudaError_t setup_pcg(bsc_ctx* c) {
-  int per_sm = 0, per_pipe = 0;
-  cudaError_t e = c->precision == BSC_FP64
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<double, PCG_BLOCK>, PCG_BLOCK, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<float, PCG_BLOCK>, PCG_BLOCK, 0);
+  int per_sm = 0;
+  // one grid serves every form: the co-resident capacity of the most demanding one
+  cudaError_t e = c->precision == BSC_FP64 ? pcg_occupancy<double>(&per_sm) : pcg_occupancy<float>(&per_sm);
   if (e != cudaSuccess) return e;
-  e = c->precision == BSC_FP64
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_pipe, k_pcg_pipe<double, PCG_BLOCK>, PCG_BLOCK, 0)
-          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_pipe, k_pcg_pipe<float, PCG_BLOCK>, PCG_BLOCK, 0);
-  if (e != cudaSuccess) return e;
-  // one grid serves both forms: the co-resident capacity of the more demanding one
-  if (per_pipe < per_sm) per_sm = per_pipe;
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 4) per_sm = 4;
   const int cap = c->num_sms * per_sm;
@@ -673,14 +711,24 @@ cudaError_t launch_block_jacobi(bsc_ctx* c, const void* K, void* Dinv) {
   BSC_COUNT(c, 1);
   const int G = (c->N + 255) / 256;
   if (c->precision == BSC_FP64)
-    k_block_jacobi<double><<<G, 256, 0, c->stream>>>(c->N, (const double*)K, (double*)Dinv, c->dstatus);
+    k_block_jacobi<double><<<G, 256, 0, c->stream>>>(c->N, (const double*)K, (double*)Dinv, c->dstatus, 12);
   else
-    k_block_jacobi<float><<<G, 256, 0, c->stream>>>(c->N, (const float*)K, (float*)Dinv, c->dstatus);
+    k_block_jacobi<float><<<G, 256, 0, c->stream>>>(c->N, (const float*)K, (float*)Dinv, c->dstatus, 12);
   return cudaGetLastError();
 }
 
-cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y) {
+cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y, int sym) {
   BSC_COUNT(c, 1);
+  if (sym) {
+    const int G = (c->N + 255) / 256;
+    if (c->precision == BSC_FP64)
+      k_spmv_sym<double><<<G, 256, 0, c->stream>>>(c->N, c->pd, c->cp_patch, (const double*)K, (const double*)x,
+                                                   (double*)y);
+    else
+      k_spmv_sym<float><<<G, 256, 0, c->stream>>>(c->N, c->pd, c->cp_patch, (const float*)K, (const float*)x,
+                                                  (float*)y);
+    return cudaGetLastError();
+  }
   const int B = 256, G = (3 * c->N + B - 1) / B;
   if (c->precision == BSC_FP64)
     k_spmv<double><<<G, B, 0, c->stream>>>(c->N, c->pd, c->cp_patch, (const double*)K, (const double*)x, (double*)y);
@@ -689,17 +737,17 @@ cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit) {
+cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit, int sym) {
   BSC_COUNT(c, 2);
-  if (c->precision == BSC_FP64) return pcg_t<double>(c, K, b, x, tol, maxit);
-  return pcg_t<float>(c, K, b, x, tol, maxit);
+  if (c->precision == BSC_FP64) return pcg_t<double>(c, K, b, x, tol, maxit, sym);
+  return pcg_t<float>(c, K, b, x, tol, maxit, sym);
 }
 
 cudaError_t launch_pcg_fallback(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit,
                                 const double* fcg_out, const double* bb) {
   BSC_COUNT(c, 2);
-  if (c->precision == BSC_FP64) return pcg_t<double>(c, K, b, x, tol, maxit, fcg_out, bb);
-  return pcg_t<float>(c, K, b, x, tol, maxit, fcg_out, bb);
+  if (c->precision == BSC_FP64) return pcg_t<double>(c, K, b, x, tol, maxit, 0, fcg_out, bb);
+  return pcg_t<float>(c, K, b, x, tol, maxit, 0, fcg_out, bb);
 }
 
 cudaError_t launch_axpy_trial(bsc_ctx* c, const void* C, const void* d, double alpha, void* out) {
@@ -746,7 +794,7 @@ cudaError_t static_solve_t(int nu, int nv, double* scratch, const void* K, const
   constexpr int B = PCG_BLOCK;
   const int N = nu * nv;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, B>, B, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, B, 0, false>, B, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 2) per_sm = 2;
@@ -769,7 +817,7 @@ cudaError_t static_solve_t(int nu, int nv, double* scratch, const void* K, const
   // the barrier words, the status and the result scalars start at zero on
   // every call (a solve that stops early must not report the last call's results)
   if ((e = cudaMemsetAsync(tail, 0, 7 * sizeof(double), st)) != cudaSuccess) return e;
-  k_block_jacobi<T><<<(N + 255) / 256, 256, 0, st>>>(N, (const T*)K, Dinv, status);
+  k_block_jacobi<T><<<(N + 255) / 256, 256, 0, st>>>(N, (const T*)K, Dinv, status, 12);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   PcgArgs<T> A;
   A.N = N; A.maxit = maxit; A.tol = tol;

@@ -120,28 +120,32 @@ __device__ int span_points(int a, int b, int Su, int Sv, int which, int rule, QP
   return n;
 }
 
-__global__ void k_count_points(int Su, int Sv, int mem_rule, int bend_rule, int* __restrict__ cm,
+// Sv local span rows starting at global span row vb0 of SvG (a strip window;
+// vb0 = 0, SvG = Sv for a whole patch).
+__global__ void k_count_points(int Su, int Sv, int vb0, int SvG, int mem_rule, int bend_rule, int* __restrict__ cm,
                                int* __restrict__ cb) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= Su * Sv) return;
   QP pts[9];
-  cm[s] = span_points(s % Su, s / Su, Su, Sv, 0, mem_rule, pts);
-  cb[s] = span_points(s % Su, s / Su, Su, Sv, 1, bend_rule, pts);
+  cm[s] = span_points(s % Su, s / Su + vb0, Su, SvG, 0, mem_rule, pts);
+  cb[s] = span_points(s % Su, s / Su + vb0, Su, SvG, 1, bend_rule, pts);
 }
 
 // Rest-map geometry at (u, v) in span (a, b) and the per-point table rows.
 // One patch: nu x nv control points starting at cp0 in the rest planes
-// (stride Ntot), spans starting at sp0 in the offset arrays.
+// (stride Ntot), spans starting at sp0 in the offset arrays; local span row b
+// is the global row b + vb0 of SvG (the v coordinates stored are global, the
+// owner span indices local).
 template <typename T>
-__global__ void k_fill_points(int nu, int nv, int cp0, int sp0, int Ntot, const double* __restrict__ rest,
-                              int mem_rule, int bend_rule, const int* __restrict__ moff,
-                              const int* __restrict__ boff, int Nm, int Nb, T* __restrict__ tabm,
-                              T* __restrict__ tabb, double* __restrict__ ptsm,
+__global__ void k_fill_points(int nu, int nv, int vb0, int SvG, int cp0, int sp0, int Ntot,
+                              const double* __restrict__ rest, int mem_rule, int bend_rule,
+                              const int* __restrict__ moff, const int* __restrict__ boff, int Nm, int Nb,
+                              T* __restrict__ tabm, T* __restrict__ tabb, double* __restrict__ ptsm,
                               double* __restrict__ ptsb, int* __restrict__ status) {
   const int Su = nu - 2, Sv = nv - 2;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= Su * Sv) return;
-  const int a = s % Su, b = s / Su;
+  const int a = s % Su, b = s / Su, bg = b + vb0;
   double X[9][2];
   for (int l = 0; l < 9; ++l) {
     const int al = cp0 + (b + l / 3) * nu + a + l % 3;
@@ -150,12 +154,12 @@ __global__ void k_fill_points(int nu, int nv, int cp0, int sp0, int Ntot, const 
   }
   for (int which = 0; which < 2; ++which) {
     QP pts[9];
-    const int np = span_points(a, b, Su, Sv, which, which ? bend_rule : mem_rule, pts);
+    const int np = span_points(a, bg, Su, SvG, which, which ? bend_rule : mem_rule, pts);
     const int base = which ? boff[sp0 + s] : moff[sp0 + s];
     for (int k = 0; k < np; ++k) {
       double Nu[3], Du[3], D2u[3], Nv[3], Dv[3], D2v[3];
       span_basis(pts[k].u, a, Su, Nu, Du, D2u);
-      span_basis(pts[k].v, b, Sv, Nv, Dv, D2v);
+      span_basis(pts[k].v, bg, SvG, Nv, Dv, D2v);
       // dX/du, dX/dv and second derivatives of the rest map
       double Xu[2] = {0, 0}, Xv[2] = {0, 0}, Xuu[2] = {0, 0}, Xuv[2] = {0, 0}, Xvv[2] = {0, 0};
       double Nl_u[9], Nl_v[9], Nl_uu[9], Nl_uv[9], Nl_vv[9];
@@ -211,9 +215,10 @@ __global__ void k_fill_points(int nu, int nv, int cp0, int sp0, int Ntot, const 
 }
 
 // Lumped mass m_alpha = rho * int N_alpha |det J| du dv, 3x3 Gauss per span,
-// gathered per control point over the (up to 3x3) spans of its support.
-__global__ void k_lumped_mass(int nu, int nv, int cp0, int Ntot, const double* __restrict__ rest, double rho,
-                              double* __restrict__ m) {
+// gathered per control point over the (up to 3x3) spans of its support that
+// the context holds (all of them but on a strip window's outer halo rows).
+__global__ void k_lumped_mass(int nu, int nv, int vb0, int SvG, int cp0, int Ntot, const double* __restrict__ rest,
+                              double rho, double* __restrict__ m) {
   const int Su = nu - 2, Sv = nv - 2, N = nu * nv;
   const int al = blockIdx.x * blockDim.x + threadIdx.x;
   if (al >= N) return;
@@ -235,7 +240,7 @@ __global__ void k_lumped_mass(int nu, int nv, int cp0, int Ntot, const double* _
         for (int qu = 0; qu < 3; ++qu) {
           double Nu[3], Du[3], D2u[3], Nv[3], Dv[3], D2v[3];
           span_basis(a + gx[qu], a, Su, Nu, Du, D2u);
-          span_basis(b + gx[qv], b, Sv, Nv, Dv, D2v);
+          span_basis(b + vb0 + gx[qv], b + vb0, SvG, Nv, Dv, D2v);
           double Xu0 = 0, Xu1 = 0, Xv0 = 0, Xv1 = 0;
           for (int l = 0; l < 9; ++l) {
             const double nu_ = Du[l % 3] * Nv[l / 3], nv_ = Nu[l % 3] * Dv[l / 3];
@@ -265,8 +270,8 @@ cudaError_t launch_build_tables(bsc_ctx* c) {
   for (int p = 0; p < c->P; ++p) {
     const PatchDev& q = c->hpd[p];
     BSC_COUNT(c, 1);
-    k_count_points<<<(q.Nsp + B - 1) / B, B, 0, c->stream>>>(q.Su, q.Sv, c->mem_rule, c->bend_rule, cm + q.sp0,
-                                                            cb + q.sp0);
+    k_count_points<<<(q.Nsp + B - 1) / B, B, 0, c->stream>>>(q.Su, q.Sv, q.vb0, q.SvG, c->mem_rule, c->bend_rule,
+                                                            cm + q.sp0, cb + q.sp0);
   }
   std::vector<int> hcm(Nsp), hcb(Nsp), hmo(Nsp + 1), hbo(Nsp + 1), hbl(Nsp), hsp(Nsp), hcp(N);
   e = cudaGetLastError();
@@ -326,16 +331,17 @@ cudaError_t launch_build_tables(bsc_ctx* c) {
     const int G = (q.Nsp + B - 1) / B;
     BSC_COUNT(c, 2);
     if (c->precision == BSC_FP64)
-      k_fill_points<double><<<G, B, 0, c->stream>>>(q.nu, q.nv, q.cp0, q.sp0, N, c->rest, c->mem_rule,
+      k_fill_points<double><<<G, B, 0, c->stream>>>(q.nu, q.nv, q.vb0, q.SvG, q.cp0, q.sp0, N, c->rest, c->mem_rule,
                                                       c->bend_rule, c->mem_off, c->bd_off, c->Nmem, c->Nbd,
                                                       (double*)c->tab_mem, (double*)c->tab_bd, c->pts_mem,
                                                       c->pts_bd, c->dstatus);
     else
-      k_fill_points<float><<<G, B, 0, c->stream>>>(q.nu, q.nv, q.cp0, q.sp0, N, c->rest, c->mem_rule,
+      k_fill_points<float><<<G, B, 0, c->stream>>>(q.nu, q.nv, q.vb0, q.SvG, q.cp0, q.sp0, N, c->rest, c->mem_rule,
                                                      c->bend_rule, c->mem_off, c->bd_off, c->Nmem, c->Nbd,
                                                      (float*)c->tab_mem, (float*)c->tab_bd, c->pts_mem,
                                                      c->pts_bd, c->dstatus);
-    k_lumped_mass<<<(q.N + B - 1) / B, B, 0, c->stream>>>(q.nu, q.nv, q.cp0, N, c->rest, q.rho, c->mass);
+    k_lumped_mass<<<(q.N + B - 1) / B, B, 0, c->stream>>>(q.nu, q.nv, q.vb0, q.SvG, q.cp0, N, c->rest, q.rho,
+                                                           c->mass);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -346,6 +352,7 @@ cudaError_t launch_build_tables(bsc_ctx* c) {
 cudaError_t launch_lumped_mass_patch(bsc_ctx* c, int p) {
   const PatchDev& q = c->hpd[p];
   BSC_COUNT(c, 1);
-  k_lumped_mass<<<(q.N + 127) / 128, 128, 0, c->stream>>>(q.nu, q.nv, q.cp0, c->N, c->rest, q.rho, c->mass);
+  k_lumped_mass<<<(q.N + 127) / 128, 128, 0, c->stream>>>(q.nu, q.nv, q.vb0, q.SvG, q.cp0, c->N, c->rest, q.rho,
+                                                          c->mass);
   return cudaGetLastError();
 }

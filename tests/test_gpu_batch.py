@@ -165,6 +165,45 @@ def test_pipelined_pcg_batch_matches_three_barrier_form(pair):
         assert rel(patch_vec(batch, x1, p), patch_vec(batch, x0, p)) < (1e-9 if tol < 1e-9 else 1e-4), p
 
 
+def test_two_pass_pcg_batch_matches_three_barrier_form(pair):
+    """The two-pass PCG form (q = K z + beta q carried by a recurrence) on the
+    uneven batch, FP64 and FP32: every patch reaches the tolerance and the
+    solutions agree with the three-barrier form's to it."""
+    pats, batch, _ = pair
+    tol = 1e-12 if batch.precision == bsc.FP64 else 1e-6
+    C = batch_tensor(batch, [p.C for p in pats])
+    Ch = batch_tensor(batch, [p.Chat for p in pats])
+    K = batch.assemble_hessian(C, project=True)
+    b = -batch.gradient(C, Ch)
+    x0, it0, rr0 = batch.solve(b, K=K, rel_tol=tol)
+    batch.set_pcg_form(2)
+    try:
+        x2, it2, rr2 = batch.solve(b, K=K, rel_tol=tol)
+    finally:
+        batch.set_pcg_form(0)
+    worst = max(rel(patch_vec(batch, x2, p), patch_vec(batch, x0, p)) for p in range(len(pats)))
+    print(f"batch solve: three-barrier {it0} iterations, two-pass {it2}; largest relative difference {worst:.2e}")
+    assert rr2 <= tol
+    assert worst < (1e-9 if batch.precision == bsc.FP64 else 1e-4)
+
+
+def test_symmetric_storage_same_batch_step(pair):
+    """The batch's Newton step with the symmetric and with the full matrix
+    layout: bitwise the same positions and per-patch reports (FP64, FP32)."""
+    pats, batch, _ = pair
+    res = []
+    try:
+        for sym in (False, True):
+            batch.set_k_storage(sym)
+            C = batch_tensor(batch, [p.C for p in pats])
+            batch.newton_step(C, batch_tensor(batch, [p.Chat for p in pats]))
+            res.append((C, [r.as_dict() for r in batch.patch_reports()]))
+    finally:
+        batch.set_k_storage(True)
+    assert torch.equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1]
+
+
 def test_newton_step_against_oracle(orc):
     """FP64 batch: every patch's Newton step against the oracle's (banded
     Cholesky solve), including the line-search halvings."""
@@ -256,7 +295,7 @@ def test_autotune_choices(pair):
     assert sum(split) == t["pcg_grid"] and min(split) >= 1
     assert t["p2_variant"] in (0, 1) and all(ms > 0 for ms in t["p2_ms"])
     assert t["psd_test"] in (0, 1) and all(ms > 0 for ms in t["psd_ms"])
-    assert t["pcg_form"] in (0, 1) and min(t["pcg_form_ms"]) == t["pcg_form_ms"][t["pcg_form"]]
+    assert t["pcg_form"] in (0, 1, 2) and min(t["pcg_form_ms"]) == t["pcg_form_ms"][t["pcg_form"]]
     # both occupancy variants of the projection's eigenpair phase: bitwise the same
     outs = []
     for v in (0, 1):

@@ -166,11 +166,12 @@ def test_psd_test_changes_nothing(case, orc):
     assert int(((nneg0 > 0) != (nneg1 > 0)).sum()) <= max(1, pat.n_spans // 1000)
 
 
-def test_pipelined_pcg_fp64(case, orc):
-    """The pipelined PCG form (one group barrier per iteration) reaches the
-    same solution as the oracle's direct solve, and its Newton step the
-    oracle's positions, at the bounds of the three-barrier form."""
-    form = 1
+@pytest.mark.parametrize("form", [1, 2], ids=["pipelined", "two_pass"])
+def test_pcg_forms_fp64(case, orc, form):
+    """The pipelined PCG form (one group barrier per iteration) and the
+    two-pass form (q = K z + beta q) reach the same solution as the oracle's
+    direct solve, and their Newton steps the oracle's positions, at the
+    bounds of the three-barrier form."""
     pat, prob, ctx = case
     sc = orc.Scene.from_patch(pat, project=True)
     _, og, oK = orc.evaluate(prob, sc, pat.C, pat.Chat)
@@ -196,6 +197,34 @@ def test_pipelined_pcg_fp64(case, orc):
         assert np.abs(to_n3(C) - oC).max() <= 1e-10 * width
     finally:
         ctx.set_pcg_form(0)
+
+
+def test_symmetric_storage_same_newton_step(case):
+    """The Newton step's matrix in the symmetric layout (13 slots, the
+    default) and in the full one (25) give the same step bit for bit: the
+    product reads the same entries in the same order.  After the step, a
+    product with the step's own matrix (K = None) equals one with the full
+    matrix assembled at the same state, up to the stand-alone full-layout
+    product's own accumulation order (three FMA chains per row)."""
+    pat, prob, ctx = case
+    out = {}
+    try:
+        for sym in (False, True):
+            ctx.set_k_storage(sym)
+            C = ctx.to_device(pat.C)
+            rep = ctx.newton_step(C, ctx.to_device(pat.Chat))
+            out[sym] = (C, rep.as_dict())
+        x = ctx.to_device(np.random.default_rng(7).standard_normal((pat.n_cp, 3)))
+        y_sym = ctx.spmv(x)            # the last Newton step's matrix (symmetric layout)
+        Kf = ctx.assemble_hessian(ctx.to_device(pat.C), project=True)
+        y_full = ctx.spmv(x, K=Kf)
+    finally:
+        ctx.set_k_storage(True)
+    assert torch.equal(out[False][0], out[True][0])
+    assert out[False][1] == out[True][1]
+    e = (torch.linalg.norm(y_sym - y_full) / torch.linalg.norm(y_full)).item()
+    print(f"{pat.name}: product with the step's symmetric matrix vs the full one: {e:.1e}")
+    assert e < 1e-14
 
 
 def test_newton_step_fp64(case, orc):

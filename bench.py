@@ -166,7 +166,7 @@ def ldlt_flops(n):
     return f
 
 
-def projection_flops(nred, nneg, nm, nb, psd=False):
+def projection_flops(nred, nneg, nm, nb, psd=False, open_frac=1.0, border_psd=False):
     """Algorithmic FP64 flops of the SPD projection of one span per Newton
     iteration as implemented: reduced Hessian formation from the reduced
     derivative vectors (the span's orthonormal basis and the vectors in it
@@ -178,14 +178,22 @@ def projection_flops(nred, nneg, nm, nb, psd=False):
     the shifted tridiagonal, the Rayleigh quotient, the back-transformation
     (2 n^2), the mapping to span DOFs and the rank-one update of the 378
     packed entries (FP32 bracketing and FP32 updates are not counted).
-    With the PSD test (interior spans, psd=True) every span pays the
-    formation and the LDL^T test, and only the spans with a projected
-    eigenvalue go on to the formation again and the eigendecomposition."""
+    With the PSD test (interior spans, psd=True) a span pays the formation
+    and the LDL^T test in FP64 with probability open_frac (the share of the
+    interior spans the FP32 certificate leaves open; 1 without it - the
+    certificate's own work is FP32 and not counted), and only the spans with
+    a projected eigenvalue go on to the formation again and the
+    eigendecomposition.  Border spans (n = 24) pay the FP64 test when it
+    runs on them (border_psd: border path 1 with the test on)."""
     n = nred
     D = n // 3
     form = nm * 2 * (36 * D + 9 * D * (D + 1)) + nb * (2 * D * (D + 1))  # T_k and blocks per point
     f = 0.0
     if psd and n == 15:
+        f += open_frac * (form + ldlt_flops(n))
+        if not nneg:
+            return f
+    if border_psd and n == 24:
         f += form + ldlt_flops(n)
         if not nneg:
             return f
@@ -332,8 +340,11 @@ def run_gpu(args):
     nb = np.bincount(ctx.quadrature_tables(1)[:, 24].astype(np.int64), minlength=Nsp)
     flops = 0.0
     psd = bool(tuning.get("psd_test"))
+    psd_counts = ctx.psd_counts()   # interior spans, FP64-tested, eigendecomposed
+    open_frac = psd_counts[1] / max(psd_counts[0], 1)
     for s_ in range(Nsp):
-        flops += projection_flops(int(nred[s_]), int(nneg[s_]), int(nm[s_]), int(nb[s_]), psd)
+        flops += projection_flops(int(nred[s_]), int(nneg[s_]), int(nm[s_]), int(nb[s_]), psd, open_frac,
+                                  psd and tuning.get("border_path") == 1)
     achieved_tflops = flops / (proj_ms * 1e-3) / 1e12
 
     # e2e: the same Newton step through the C ABI from pinned host buffers
@@ -436,17 +447,21 @@ def run_gpu(args):
         pcg_gbs = pcg_bytes / (pcg_ms * 1e-3) / 1e9
         roof_pcg = {"kernel": "persistent block-Jacobi PCG (k_pcg or k_pcg_pipe)", "bound": "hbm",
                     "achieved": pcg_gbs, "peak": hbm, "unit": "GB/s", "frac": pcg_gbs / hbm,
-                    "traffic": pcg_traffic(args.workload, prec == bsc.FP32, tuning, iters),
+                    "traffic": pcg_traffic(args.workload, prec == bsc.FP32, tuning, iters, k_sym),
                     "algorithmic_bytes_per_launch": pcg_bytes, "iterations": iters,
                     "bytes_per_cp_per_iteration": tsz * (k_entries + 6 + 15),
                     "k_layout": "symmetric (13 blocks)" if k_sym else "full (25 blocks)", "launch_ms": pcg_ms,
                     "launch_ms_source": "solve phase of bsc_phase_times (rhs, block-Jacobi inverses and the PCG "
                                         "launch, CUDA events on the launching stream)",
                     "peak_source": hbm_src,
-                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one k_pcg launch of the "
-                                      "512x512 wrinkle field (profiles/k_pcg_wrinkle512_fp32.md), scaled by control "
-                                      "points x iterations to this launch; null once the kernel changed"}
-        roof_proj = {"kernel": "SPD projection (k_proj_p0, k_proj_p1, k_proj_p2, k_proj_corr, k_project_ring: FP64)",
+                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one k_pcg launch (two-pass "
+                                      "form, symmetric layout) of the 512x512 wrinkle field "
+                                      "(profiles/k_pcg_wrinkle512_fp32.md), scaled by control points x iterations "
+                                      "to this launch; null for another form or layout, or once the kernel changed"}
+        roof_proj = {"kernel": "SPD projection (k_proj_pf: FP32 certificate; k_proj_p0, k_proj_p1, k_proj_p2, "
+                               "k_proj_corr, k_project_ring: FP64)",
+                     "psd_counts": {"interior_spans": psd_counts[0], "fp64_tested": psd_counts[1],
+                                    "eigendecomposed": psd_counts[2], "mode": tuning.get("psd_test")},
                      "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                      "traffic": projection_traffic(args.workload, prec == bsc.FP32, tuning),
@@ -704,7 +719,9 @@ def measure_drape(bsc, flush, stream, torch, np, steps, warmup):
             nm = np.bincount(ctx.quadrature_tables(0)[:, 24].astype(np.int64), minlength=pat.n_spans)
             nb = np.bincount(ctx.quadrature_tables(1)[:, 24].astype(np.int64), minlength=pat.n_spans)
             psd = bool(tuning.get("psd_test"))
-            fl = sum(projection_flops(int(nred[i]), int(nneg[i]), int(nm[i]), int(nb[i]), psd)
+            pc = ctx.psd_counts()
+            fl = sum(projection_flops(int(nred[i]), int(nneg[i]), int(nm[i]), int(nb[i]), psd,
+                                      pc[1] / max(pc[0], 1), psd and tuning.get("border_path") == 1)
                      for i in range(pat.n_spans))
             pms = ph["project"] / k
             out[name]["projection"] = {"ms": pms, "algorithmic_flops": fl,
@@ -857,19 +874,21 @@ def projection_executed(workload, fp32, tuning, launch_ms, sm_mhz, num_sms):
             "fp64_pipe_busy": cycles / (num_sms * launch_ms * 1e-3 * sm_mhz * 1e6)}
 
 
-# DRAM bytes (read + write) of one k_pcg launch (three-barrier form, FP32) on
-# the 512x512 wrinkle field, 32 iterations: 8.169 GB read + 0.501 GB written
-# (profiles/k_pcg_wrinkle512_fp32.md), i.e. 1033.6 B per control point and
-# iteration; it scales with both where K (0.9 KB per control point) does not
-# fit the 129 MB L2, so from 512x512 up.  Keyed by a hash of the solver source.
-PCG_TRAFFIC_PER_CP_ITER = 8.670e9 / (32 * 262144)
-PCG_TRAFFIC_HASH = "1b3224fedab2fe37"
+# DRAM bytes (read + write) of one k_pcg launch (two-pass form, symmetric
+# matrix layout, FP32) on the 512x512 wrinkle field, 32 iterations: 3.999 GB
+# read + 0.452 GB written (profiles/k_pcg_wrinkle512_fp32.md), i.e. 530.6 B
+# per control point and iteration; it scales with both where K (0.47 KB per
+# control point) does not fit the 129 MB L2, so from 512x512 up.  Keyed by a
+# hash of the solver source, the form and the layout.
+PCG_TRAFFIC_PER_CP_ITER = 4.451e9 / (32 * 262144)
+PCG_TRAFFIC_HASH = "ddd6b7a6ebab236b"
+PCG_TRAFFIC_FORM = 2
 PCG_TRAFFIC_WORKLOADS = ("wrinkle512", "wrinkle1024")
 
 
-def pcg_traffic(workload, fp32, tuning, iters):
+def pcg_traffic(workload, fp32, tuning, iters, k_sym=True):
     import hashlib
-    if workload not in PCG_TRAFFIC_WORKLOADS or not fp32 or tuning.get("pcg_form") != 0:
+    if workload not in PCG_TRAFFIC_WORKLOADS or not fp32 or tuning.get("pcg_form") != PCG_TRAFFIC_FORM or not k_sym:
         return None
     with open(os.path.join(ROOT, "paper_2506_18867_gb300", "csrc", "k_solve.cu"), "rb") as fh:
         h = hashlib.sha256(fh.read()).hexdigest()[:16]

@@ -272,8 +272,8 @@ typedef struct bsc_tuning {
   double pcg_ms[4];        /* measured ms of the solve per candidate (-1: duplicate) */
   int pcg_form;            /* PCG form chosen at that grid (see bsc_set_pcg_form) */
   double pcg_form_ms[3];   /* measured ms of the solve per form (1e30: did not converge) */
-  int psd_test;            /* PSD test before the interior eigendecomposition (bsc_set_psd_test) */
-  double psd_ms[2];        /* measured ms of the whole projection without / with it */
+  int psd_test;            /* PSD test mode before the interior eigendecomposition (bsc_set_psd_test) */
+  double psd_ms[3];        /* measured ms of the whole projection in modes 0, 1, 2 */
 } bsc_tuning;
 bsc_status bsc_autotune(bsc_ctx* ctx, const void* C_dev, const void* Chat_dev, bsc_tuning* out);
 
@@ -300,18 +300,32 @@ bsc_status bsc_set_border_path(bsc_ctx* ctx, int path);
  * hand (0 or 1, see bsc_tuning); both compute bitwise the same result. */
 bsc_status bsc_set_p2_variant(bsc_ctx* ctx, int variant);
 
-/* PSD test of the SPD projection (BSC_PROJECT_SPAN): with on != 0 (the
- * default) every interior span's reduced Hessian H_r (order n) first goes
- * through an FP64 LDL^T factorisation of H_r + tau I, tau = 1e-14 tr(H_r) / n
- * (a span with tr(H_r) <= 0 fails outright); a span
- * whose pivots are all positive has no eigenvalue below -tau and keeps its
- * Hessian, and only the spans that fail go on to the eigendecomposition
- * (gathered into one list, so that the eigendecomposition runs with full
- * warps).  The projected matrix is the same either way up to eigenvalues
- * of size tau.  The test pays off when few spans need projecting (a cloth
- * near equilibrium) and costs about a fifth of the eigendecomposition when
- * most do; bsc_autotune keeps the faster setting for the state it is given. */
-bsc_status bsc_set_psd_test(bsc_ctx* ctx, int on);
+/* PSD test of the SPD projection (BSC_PROJECT_SPAN), mode:
+ * 0 - every interior span goes through the eigendecomposition;
+ * 1 - every interior span's reduced Hessian H_r (order n) first goes
+ *     through an FP64 LDL^T factorisation of H_r + tau I, tau = 1e-14
+ *     tr(H_r) / n (a span with tr(H_r) <= 0 fails outright); a span whose
+ *     pivots are all positive has no eigenvalue below -tau and keeps its
+ *     Hessian, and only the spans that fail go on to the eigendecomposition
+ *     (gathered into one list, so that it runs with full warps);
+ * 2 (the default) - before that, an FP32 certificate: H_r formed and
+ *     Cholesky-factored in FP32 with a shift sigma that bounds the rounding
+ *     of both (a few 1e-6 of tr(H_r) and of the size of H_r's terms); a
+ *     factorisation that completes proves H_r positive definite with every
+ *     eigenvalue above sigma / 2, so the span keeps its Hessian without the
+ *     FP64 test, which would have passed it too.  Only the spans the
+ *     certificate leaves open go through the FP64 test.
+ * The projected matrix is the same in modes 1 and 2 bit for bit, and the
+ * same as in mode 0 up to eigenvalues of size tau.  bsc_autotune keeps the
+ * fastest mode for the state it is given.  Errors: BSC_ERR_INVALID_ARG for
+ * another mode. */
+bsc_status bsc_set_psd_test(bsc_ctx* ctx, int mode);
+
+/* Span counts of the last interior projection (host array of 3 ints): the
+ * interior spans, those the FP64 PSD test ran on (all of them in mode 1,
+ * the certificate's open ones in mode 2, none in mode 0) and those that went
+ * on to the eigendecomposition. */
+bsc_status bsc_psd_counts(bsc_ctx* ctx, int* out);
 
 /* Form of the persistent block-Jacobi PCG (the same iterates up to rounding):
  * 0 - the textbook recurrences, three group barriers per iteration (one

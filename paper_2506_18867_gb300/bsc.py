@@ -49,7 +49,7 @@ EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc
            "bsc_set_psd_test", "bsc_contact_attach", "bsc_contact_detach", "bsc_contact_vertices",
            "bsc_contact_step_bound", "bsc_contact_stats", "bsc_create_window", "bsc_window_energy_rows",
            "bsc_window_pcg_begin", "bsc_window_pcg_product", "bsc_window_pcg_update", "bsc_window_pcg_direction",
-           "bsc_axpy", "bsc_set_k_storage")
+           "bsc_axpy", "bsc_set_k_storage", "bsc_psd_counts")
 
 TILE_CANDIDATES = (0, 8, 16, 32)
 
@@ -95,7 +95,7 @@ class Tuning(ct.Structure):
                 ("border_path", ct.c_int), ("border_ms", ct.c_double * 3), ("p2_variant", ct.c_int),
                 ("p2_ms", ct.c_double * 2), ("pcg_grid_cand", ct.c_int * 4), ("pcg_ms", ct.c_double * 4),
                 ("pcg_form", ct.c_int), ("pcg_form_ms", ct.c_double * 3), ("psd_test", ct.c_int),
-                ("psd_ms", ct.c_double * 2)]
+                ("psd_ms", ct.c_double * 3)]
 
     def as_dict(self):
         return {"tile_tu": list(self.tile_tu), "tile_ms": [list(r) for r in self.tile_ms],
@@ -203,6 +203,7 @@ def load(path: str = LIB_PATH):
     lib.bsc_window_pcg_direction.argtypes = [P, D]
     lib.bsc_axpy.argtypes = [P, V, V, D, V]
     lib.bsc_set_k_storage.argtypes = [P, I]
+    lib.bsc_psd_counts.argtypes = [P, ct.POINTER(I)]
     for name in EXPORTS:
         if name not in ("bsc_destroy", "bsc_last_error", "bsc_cnn_destroy"):
             getattr(lib, name).restype = I
@@ -504,9 +505,16 @@ class Context:
         self._check(self._lib.bsc_contact_stats(self._h, ct.byref(n), ct.byref(p)))
         return {"vertices": n.value, "pairs": p.value}
 
-    def set_psd_test(self, on=True):
-        """FP64 LDL^T PSD test before the interior spans' eigendecomposition."""
-        self._check(self._lib.bsc_set_psd_test(self._h, int(bool(on))))
+    def set_psd_test(self, mode=2):
+        """PSD test before the interior spans' eigendecomposition: 0 / False
+        none, 1 / True the FP64 LDL^T test, 2 the FP32 certificate first."""
+        self._check(self._lib.bsc_set_psd_test(self._h, int(mode)))
+
+    def psd_counts(self):
+        """(interior spans, spans the FP64 test ran on, spans eigendecomposed) of the last projection."""
+        out = (ct.c_int * 3)()
+        self._check(self._lib.bsc_psd_counts(self._h, out))
+        return tuple(out)
 
     def set_pcg_form(self, form):
         """PCG form: 0 three group barriers per iteration, 1 the pipelined

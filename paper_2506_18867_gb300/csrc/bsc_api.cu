@@ -71,7 +71,7 @@ void free_ctx(bsc_ctx* c) {
                   c->Dinv, c->partials, c->sync, c->dstatus, c->dscalars, c->pd, c->cp_patch, c->sp_patch,
                   c->span_items, c->red_items, c->red_off, c->pcg_blocks, c->pcg_out, c->steps, c->patch_E,
                   c->pending, c->proj_work, c->proj_span[0], c->proj_span[1], c->proj_kneg[0], c->proj_kneg[1],
-                  c->red_g, c->red_l, c->red_q, c->fcg_rec, c->proj_cnt, c->proj_sel};
+                  c->red_g, c->red_l, c->red_q, c->fcg_rec, c->proj_cnt, c->proj_sel, c->proj_pre, c->proj_sel1};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->vec)
@@ -819,11 +819,23 @@ bsc_status bsc_set_pcg_grid(bsc_ctx* c, int grid) {
   return BSC_OK;
 }
 
-bsc_status bsc_set_psd_test(bsc_ctx* c, int on) {
+bsc_status bsc_set_psd_test(bsc_ctx* c, int mode) {
   if (!c) return BSC_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 2) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_psd_test: mode must be 0, 1 or 2");
   CK(cudaStreamSynchronize(c->gstream), "bsc_set_psd_test");
-  c->proj_psd = on ? 1 : 0;
+  c->proj_psd = mode;
   drop_graph(c);
+  return BSC_OK;
+}
+
+bsc_status bsc_psd_counts(bsc_ctx* c, int* out) {
+  if (!c || !out) return BSC_ERR_INVALID_ARG;
+  int h[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h, c->proj_cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "bsc_psd_counts");
+  CK(cudaStreamSynchronize(c->stream), "bsc_psd_counts");
+  out[0] = h[0];
+  out[1] = c->proj_psd == 2 ? h[3] : (c->proj_psd == 1 ? h[0] : 0);
+  out[2] = c->proj_psd ? h[2] : h[0];
   return BSC_OK;
 }
 
@@ -902,9 +914,10 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
     }
     if (t.tile_tu[cls] >= 0) c->tile_tu[cls] = t.tile_tu[cls];
   }
-  // the PSD test before the interior eigendecomposition: on or off, whole
-  // projection timed on freshly evaluated span Hessians
-  for (int on = 0; on < 2 && st == BSC_OK; ++on) {
+  // the PSD test before the interior eigendecomposition: off, FP64 alone,
+  // or the FP32 certificate first; whole projection timed on freshly
+  // evaluated span Hessians
+  for (int on = 0; on < 3 && st == BSC_OK; ++on) {
     float best_rep = 1e30f, ms = 0.0f;
     cudaError_t e = cudaSuccess;
     c->proj_psd = on;
@@ -920,7 +933,12 @@ bsc_status bsc_autotune(bsc_ctx* c, const void* C, const void* Chat, bsc_tuning*
     if (e != cudaSuccess) st = cuda_fail(c, e, "bsc_autotune: timing the PSD test");
     t.psd_ms[on] = best_rep;
   }
-  c->proj_psd = t.psd_ms[1] <= t.psd_ms[0] ? 1 : 0;
+  {
+    int best = 2;  // the certificate first, unless another mode is measurably faster
+    for (int m = 0; m < 2; ++m)
+      if (t.psd_ms[m] < t.psd_ms[best]) best = m;
+    c->proj_psd = best;
+  }
   t.psd_test = c->proj_psd;
   // border projection path: time the whole projection (the border class
   // runs beside the interior phase 2 and competes with it for the FP64

@@ -128,10 +128,16 @@ struct bsc_ctx {
   double* proj_span[2];     // per-span scratch of each class
   int* proj_kneg[2];        // negative-eigenvalue count per span (class order)
   unsigned int* proj_work;  // [4] work counters
-  int* proj_cnt;            // device [4]: class sizes (interior, border), spans failing the PSD test
+  int* proj_cnt;            // device [6]: class sizes (interior, border); interior spans failing the PSD
+                            // test, left open by the certificate; border spans failing the test
   int* proj_sel;            // device [interior spans]: class positions of the spans failing the PSD test
-  int proj_psd;             // interior class: FP64 LDL^T PSD test first (autotuned)
+  int proj_psd;             // interior class: 0 no PSD test, 1 the FP64 LDL^T test first, 2 an FP32
+                            // certificate of positive definiteness, then the FP64 test on the rest (autotuned)
+  int* proj_pre;            // device [interior spans]: class positions the FP32 certificate left open
+  int* proj_sel1;           // device [border spans]: class positions failing the border's FP64 test (path 1)
+  int p0_grid1;             // resident grid of the border's PSD test
   int p0_grid;              // resident grid of the PSD test
+  int pf_grid;              // resident grid of the FP32 certificate
   int border_path;          // 0: one warp per border span, 1: one thread per border span
   cudaStream_t side[2];     // forked stream of the border class
   cudaEvent_t fork_ev, join_ev[2];

@@ -218,8 +218,167 @@ __global__ void __launch_bounds__(P1Block<D>::value, 1)
   }
 }
 
-// Phase 0 (the PSD test, interior spans): one thread per span forms H_r and
-// runs the FP64 LDL^T test of proj::ldlt_psd.  Spans that pass keep their
+// Phase 0a (interior spans): an FP32 certificate of positive definiteness.
+// With u = 2^-24 and gamma_k = k u / (1 - k u):
+//  - forming H_r in FP32 errs in every entry by at most gamma_16 times the
+//    sum of the absolute values of the entry's three-factor terms: a term
+//    meets at most 3 roundings of its inputs (to FP32), 2 in T_k, and one per
+//    accumulation into the entry, 2 n_mem + n_bd <= 5 in the interior class
+//    (spans with more return "open"); the Frobenius norm of those absolute
+//    sums is at most
+//      S = sum_q 3 ||g_q||^2 ||A6_q||_F + sum_b 3 W_b ||L_b||^2
+//    (|M^T A M| <= |M|^T |A| |M| entrywise, ||M||_F^2 = 3 ||g_q||^2), so
+//    ||H_r - Â||_2 <= gamma_16 S;
+//  - an LDL^T factorisation in FP32 (multipliers by a correctly rounded
+//    reciprocal of the pivot, then a product: two roundings) that ends with
+//    every pivot positive is Gaussian elimination with computed factors L and
+//    U, L U = X + F, |F| <= gamma_{n+1} |L| |U| (Higham, Accuracy and
+//    Stability of Numerical Algorithms, 2nd ed., Thm. 9.3, one rounding more
+//    per multiplier), and U = D L^T entrywise up to 1 + theta, |theta| <=
+//    gamma_2; so X = L D L^T + E with |E| <= gamma_{n+4} |L| D |L^T|, and
+//    ||E||_2 <= gamma_{n+4} tr(L D L^T) <= 2 gamma_{n+4} tr(X).
+// Factoring X = Â - sigma I with sigma = 2.2 (2 gamma_{n+4} tr Â + gamma_16 S)
+// (the factor covers the rounding of the shift, of tr Â and of S): if every
+// pivot is positive, H_r = L D L^T + sigma I - E + (H_r - Â) has every
+// eigenvalue above sigma / 2 > 0.  Such a span has no negative eigenvalue, and the FP64 test,
+// whose margin is 1e-14 tr / n, would pass it as well: taking the
+// certificate instead changes no span's result.  The spans it cannot decide
+// (their class positions appended to pre_out) go on to the FP64 test.
+constexpr int PF_BLOCK = 128;
+
+// The certificate with H_r in registers: every loop over matrix indices is
+// unrolled, so each packed entry is a register and the factorisation runs
+// without memory traffic (the open spans' class positions go out through
+// shared-memory prefix sums only).
+template <int D, class Tab>
+__device__ __forceinline__ bool certify_pd_f32(const Tab& tab) {
+  constexpr int n = 3 * D, NP = n * (n + 1) / 2;
+  constexpr float u = 5.9604644775390625e-8f;  // 2^-24
+  constexpr float g_n4 = (n + 4) * u / (1.0f - (n + 4) * u), g_16 = 16 * u / (1.0f - 16 * u);
+  float A[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) A[k] = 0.0f;
+  const int nm = tab.nm(), nb = tab.nb();
+  if (2 * nm + nb > D) return false;  // outside the rounding count above
+  float S = 0.0f;
+#pragma unroll 1
+  for (int q = 0; q < nm; ++q) {
+    float gr[D][2], g2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        gr[k][b] = (float)tab.gr(q, k, b);
+        g2 = fmaf(gr[k][b], gr[k][b], g2);
+      }
+    float A6[6][6], a2 = 0.0f;
+    {
+      int e = 0;
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c) {
+          const float v = (float)tab.a6(q, e++);
+          A6[r][c] = v;
+          A6[c][r] = v;
+          a2 = fmaf(r == c ? v : 2.0f * v, v, a2);
+        }
+    }
+    S = fmaf(3.0f * g2, __fsqrt_ru(a2), S);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float Tk[3][6];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) Tk[c][j] = fmaf(gr[k][1], A6[3 + c][j], gr[k][0] * A6[c][j]);
+#pragma unroll
+      for (int k2 = 0; k2 <= k; ++k2)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int dd = 0; dd < 3; ++dd) {
+            if (k2 == k && dd > c) continue;
+            float& a = A[proj::lp(3 * k + c, 3 * k2 + dd)];
+            a = fmaf(Tk[c][3 + dd], gr[k2][1], fmaf(Tk[c][dd], gr[k2][0], a));
+          }
+    }
+  }
+#pragma unroll 1
+  for (int q = 0; q < nb; ++q) {
+    const float WB = (float)tab.wb(q);
+    float Lr[D], l2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      Lr[k] = (float)tab.lr(q, k);
+      l2 = fmaf(Lr[k], Lr[k], l2);
+    }
+    S = fmaf(3.0f * fabsf(WB), l2, S);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float wl = WB * Lr[k];
+#pragma unroll
+      for (int k2 = 0; k2 <= k; ++k2)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float& a = A[proj::lp(3 * k + c, 3 * k2 + c)];
+          a = fmaf(wl, Lr[k2], a);
+        }
+    }
+  }
+  float tr = 0.0f;
+#pragma unroll
+  for (int i = 0; i < n; ++i) tr += A[proj::lp(i, i)];
+  if (!(tr > 0.0f) || !isfinite(tr) || !isfinite(S)) return false;
+  const float sigma = 2.2f * (2.0f * g_n4 * tr + g_16 * S);
+#pragma unroll
+  for (int i = 0; i < n; ++i) A[proj::lp(i, i)] -= sigma;
+  // right-looking LDL^T on the packed lower triangle: a(i, j) -= l_ik a(j, k),
+  // l_ik = a(i, k) / d_k; the multipliers are not kept
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    const float d = A[proj::lp(k, k)];
+    ok = ok && (d > 0.0f) && isfinite(d);
+    const float r = __frcp_rn(d);
+#pragma unroll
+    for (int i = k + 1; i < n; ++i) {
+      const float l = A[proj::lp(i, k)] * r;
+#pragma unroll
+      for (int j = k + 1; j <= i; ++j) A[proj::lp(i, j)] = fmaf(-l, A[proj::lp(j, k)], A[proj::lp(i, j)]);
+    }
+  }
+  return ok;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(PF_BLOCK, 2)
+    k_proj_pf(ProjArgs<T> P, const int* __restrict__ list, int count, int* __restrict__ pre_out,
+              int* __restrict__ pre_count) {
+  __shared__ int s_pre[PF_BLOCK + 1], s_wsum[PF_BLOCK / 32], s_base;
+  for (int chunk = blockIdx.x; chunk * PF_BLOCK < count; chunk += gridDim.x) {
+    const int t = chunk * PF_BLOCK + threadIdx.x;
+    int open = 0;
+    if (t < count) {
+      const int s = list[t];
+      const int q0 = P.moff[s], b0 = P.boff[s];
+      SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
+                     P.boff[s + 1] - b0, P.pd[P.sp_patch[s]].mubd};
+      if (certify_pd_f32<D>(tab)) P.nneg[s] = 0;
+      else open = 1;
+    }
+    block_prefix<PF_BLOCK>(open, s_pre, s_wsum);
+    if (threadIdx.x == 0) s_base = s_pre[PF_BLOCK] > 0 ? (int)atomicAdd(pre_count, s_pre[PF_BLOCK]) : 0;
+    __syncthreads();
+    if (open) pre_out[s_base + s_pre[threadIdx.x]] = t;
+    __syncthreads();
+  }
+}
+
+// Phase 0b (the PSD test, interior spans): one thread per span forms H_r and
+// runs the FP64 LDL^T test of proj::ldlt_psd, on the class positions pre[0
+// .. *pre_count) the certificate left open (every span of the class when
+// pre is null: then count spans in class order).  Spans that pass keep their
 // Hessian (nneg = 0); the class positions of the others are appended to
 // sel_out (block by block: the order of the blocks' groups varies from run
 // to run, the per-span results do not), and the later phases run on that
@@ -227,18 +386,21 @@ __global__ void __launch_bounds__(P1Block<D>::value, 1)
 // its other lanes idle.
 template <int D> struct P0Block;
 template <> struct P0Block<5> { static constexpr int value = 224; };  // 224 x 120 doubles = 210 KB
+template <> struct P0Block<8> { static constexpr int value = 64; };   // 64 x 300 doubles = 150 KB
 template <typename T, int D>
 __global__ void __launch_bounds__(P0Block<D>::value, 1)
-    k_proj_p0(ProjArgs<T> P, const int* __restrict__ list, int count, int* __restrict__ sel_out,
-              int* __restrict__ sel_count) {
+    k_proj_p0(ProjArgs<T> P, const int* __restrict__ list, int count, const int* __restrict__ pre,
+              const int* __restrict__ pre_count, int* __restrict__ sel_out, int* __restrict__ sel_count) {
   constexpr int B0 = P0Block<D>::value;
   extern __shared__ __align__(16) double smd[];
   __shared__ int s_pre[B0 + 1], s_wsum[B0 / 32], s_base;
   const proj::View A{smd + threadIdx.x, B0};
-  for (int chunk = blockIdx.x; chunk * B0 < count; chunk += gridDim.x) {
-    const int t = chunk * B0 + threadIdx.x;
-    int fail = 0;
-    if (t < count) {
+  const int m = pre ? *pre_count : count;
+  for (int chunk = blockIdx.x; chunk * B0 < m; chunk += gridDim.x) {
+    const int i = chunk * B0 + threadIdx.x;
+    int fail = 0, t = 0;
+    if (i < m) {
+      t = pre ? pre[i] : i;
       const int s = list[t];
       const int q0 = P.moff[s], b0 = P.boff[s];
       SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
@@ -447,6 +609,8 @@ constexpr size_t p2_smem() { return sizeof(double) * (size_t)(4 * 3 * D) * P2_BL
 // can be issued separately (phase < 0: both).
 template <int D>
 constexpr size_t p0_smem() { return sizeof(double) * (size_t)Smem<D>::NP * P0Block<D>::value; }
+template <int D>
+constexpr size_t pf_smem() { return 0; }
 
 // Class k of the span lists: 0 = interior spans (five derivative vectors,
 // D = 5), 1 = spans at or next to the border (D = 8).  Phase 1 and phase 2
@@ -458,16 +622,36 @@ cudaError_t run_class(bsc_ctx* c, int k, const int* list, int count, cudaStream_
   if (count <= 0) return cudaSuccess;
   cudaError_t e;
   ProjArgs<T> P = proj_args<T>(c, k);
-  const bool psd = k == 0 && c->proj_psd;
-  const int* sel = psd ? c->proj_sel : nullptr;
-  const int* cnt = c->proj_cnt + (psd ? 2 : k);
+  // the PSD test: interior class in every path; border class (FP64 test
+  // only: its 24 x 24 H_r does not fit the certificate's registers) when it
+  // runs through these phase kernels (border path 1)
+  const bool psd = c->proj_psd && (k == 0 || phase < 0);
+  const int* sel = psd ? (k == 0 ? c->proj_sel : c->proj_sel1) : nullptr;
+  const int* cnt = c->proj_cnt + (psd ? (k == 0 ? 2 : 4) : k);
   if (phase != 1) {
+    if constexpr (D == 8) {
+      if (psd) {
+        // proj_cnt[4]: border spans failing the FP64 test
+        if ((e = cudaMemsetAsync(c->proj_cnt + 4, 0, sizeof(int), st)) != cudaSuccess) return e;
+        BSC_COUNT(c, 1);
+        k_proj_p0<T, D><<<c->p0_grid1, P0Block<D>::value, p0_smem<D>(), st>>>(P, list, count, nullptr, nullptr,
+                                                                               c->proj_sel1, c->proj_cnt + 4);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
+    }
     if (psd) {
       if constexpr (D == 5) {
-        if ((e = cudaMemsetAsync(c->proj_cnt + 2, 0, sizeof(int), st)) != cudaSuccess) return e;
+        // proj_cnt[2]: spans failing the FP64 test; proj_cnt[3]: spans the FP32 certificate left open
+        if ((e = cudaMemsetAsync(c->proj_cnt + 2, 0, 2 * sizeof(int), st)) != cudaSuccess) return e;
+        const bool cert = c->proj_psd == 2;
+        if (cert) {
+          BSC_COUNT(c, 1);
+          k_proj_pf<T, D><<<c->pf_grid, PF_BLOCK, pf_smem<D>(), st>>>(P, list, count, c->proj_pre, c->proj_cnt + 3);
+          if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         BSC_COUNT(c, 1);
-        k_proj_p0<T, D><<<c->p0_grid, P0Block<D>::value, p0_smem<D>(), st>>>(P, list, count, c->proj_sel,
-                                                                            c->proj_cnt + 2);
+        k_proj_p0<T, D><<<c->p0_grid, P0Block<D>::value, p0_smem<D>(), st>>>(
+            P, list, count, cert ? c->proj_pre : nullptr, c->proj_cnt + 3, c->proj_sel, c->proj_cnt + 2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
       }
     }
@@ -563,6 +747,21 @@ cudaError_t p2_grid_of(bsc_ctx* c, int count, int* grid) {
 template <typename T, int D>
 cudaError_t setup_class(bsc_ctx* c, int k, int count) {
   cudaError_t e;
+  if constexpr (D == 8) {
+    if ((e = cudaFuncSetAttribute(k_proj_p0<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)p0_smem<D>())) != cudaSuccess)
+      return e;
+    int per0 = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per0, k_proj_p0<T, D>, P0Block<D>::value,
+                                                           p0_smem<D>())) != cudaSuccess)
+      return e;
+    per0 = per0 < 1 ? 1 : per0;
+    int g0 = per0 * c->num_sms;
+    const int need0 = (count + P0Block<D>::value - 1) / P0Block<D>::value;
+    if (g0 > need0) g0 = need0;
+    c->p0_grid1 = g0 < 1 ? 1 : g0;
+    if ((e = cudaMalloc(&c->proj_sel1, sizeof(int) * (size_t)(count > 0 ? count : 1))) != cudaSuccess) return e;
+  }
   if constexpr (D == 5) {
     if ((e = cudaFuncSetAttribute(k_proj_p0<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)p0_smem<D>())) != cudaSuccess)
@@ -577,6 +776,19 @@ cudaError_t setup_class(bsc_ctx* c, int k, int count) {
     if (g0 > need0) g0 = need0;
     c->p0_grid = g0 < 1 ? 1 : g0;
     if ((e = cudaMalloc(&c->proj_sel, sizeof(int) * (size_t)(count > 0 ? count : 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&c->proj_pre, sizeof(int) * (size_t)(count > 0 ? count : 1))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_proj_pf<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)pf_smem<D>())) != cudaSuccess)
+      return e;
+    int perf = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf, k_proj_pf<T, D>, PF_BLOCK, pf_smem<D>())) !=
+        cudaSuccess)
+      return e;
+    perf = perf < 1 ? 1 : perf;
+    int gf = perf * c->num_sms;
+    const int needf = (count + PF_BLOCK - 1) / PF_BLOCK;
+    if (gf > needf) gf = needf;
+    c->pf_grid = gf < 1 ? 1 : gf;
   }
   if ((e = cudaFuncSetAttribute(k_proj_p1<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)p1_smem<D>())) != cudaSuccess)
@@ -639,11 +851,11 @@ cudaError_t setup_projection(bsc_ctx* c) {
   {
     // the class sizes as device counts (the phase kernels read their span
     // count from the device: the PSD test's compacted count, or these)
-    const int h[4] = {n0, n1, 0, 0};
-    if ((e = cudaMalloc(&c->proj_cnt, sizeof(int) * 4)) != cudaSuccess) return e;
+    const int h[6] = {n0, n1, 0, 0, 0, 0};
+    if ((e = cudaMalloc(&c->proj_cnt, sizeof(int) * 6)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(c->proj_cnt, h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   }
-  c->proj_psd = 1;
+  c->proj_psd = 2;
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
     if ((e = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming)) != cudaSuccess) return e;

@@ -294,7 +294,7 @@ def test_autotune_choices(pair):
     split = batch.pcg_split()
     assert sum(split) == t["pcg_grid"] and min(split) >= 1
     assert t["p2_variant"] in (0, 1) and all(ms > 0 for ms in t["p2_ms"])
-    assert t["psd_test"] in (0, 1) and all(ms > 0 for ms in t["psd_ms"])
+    assert t["psd_test"] in (0, 1, 2) and all(ms > 0 for ms in t["psd_ms"])
     assert t["pcg_form"] in (0, 1, 2) and min(t["pcg_form_ms"]) == t["pcg_form_ms"][t["pcg_form"]]
     # both occupancy variants of the projection's eigenpair phase: bitwise the same
     outs = []

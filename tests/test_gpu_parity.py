@@ -147,23 +147,57 @@ def test_psd_test_changes_nothing(case, orc):
     with no eigenvalue below -1e-14 ||H_r||: projected span Hessians with and
     without it agree to 1e-13 and both match the oracle's Jacobi projection;
     the spans it lets through are those without a projected eigenvalue (up
-    to spans whose smallest eigenvalue lies within the thresholds' band)."""
+    to spans whose smallest eigenvalue lies within the thresholds' band).
+    The FP32 certificate in front of it changes nothing, bit for bit."""
     pat, prob, ctx = case
     C = ctx.to_device(pat.C)
-    ctx.set_psd_test(False)
-    E0, g0, H0 = ctx.span_terms(C, project=True)
-    nneg0, _ = ctx.projection_stats()
-    ctx.set_psd_test(True)
-    E1, g1, H1 = ctx.span_terms(C, project=True)
-    nneg1, _ = ctx.projection_stats()
+    try:
+        ctx.set_psd_test(0)
+        E0, g0, H0 = ctx.span_terms(C, project=True)
+        nneg0, _ = ctx.projection_stats()
+        ctx.set_psd_test(1)
+        E1, g1, H1 = ctx.span_terms(C, project=True)
+        nneg1, _ = ctx.projection_stats()
+        cnt1 = ctx.psd_counts()
+        ctx.set_psd_test(2)
+        E2, g2, H2 = ctx.span_terms(C, project=True)
+        nneg2, _ = ctx.projection_stats()
+        cnt2 = ctx.psd_counts()
+    finally:
+        ctx.set_psd_test(2)
     _, _, oH = prob.span_eval_projected(pat.C, True)
     H0h, H1h = H0.double().cpu().numpy(), H1.double().cpu().numpy()
     print(f"{pat.name}: {int((nneg0 > 0).sum())} of {pat.n_spans} spans projected; with / without the test "
-          f"{rel(H1h, H0h):.1e}")
+          f"{rel(H1h, H0h):.1e}; interior spans {cnt2[0]}, FP64-tested after the FP32 certificate {cnt2[1]}, "
+          f"eigendecomposed {cnt2[2]}")
     assert rel(H1h, H0h) < 1e-13 and rel(H1h, oH) < 1e-12
+    # the FP32 certificate only skips spans the FP64 test would pass: bitwise the same
+    assert torch.equal(H1, H2) and np.array_equal(nneg1, nneg2)
+    assert cnt1[0] == cnt2[0] and cnt1[1] == cnt1[0] and cnt1[2] == cnt2[2] and cnt2[2] <= cnt2[1] <= cnt2[0]
     # the two decisions use thresholds of the same size on different norms:
     # only spans whose smallest eigenvalue sits within that band may differ
     assert int(((nneg0 > 0) != (nneg1 > 0)).sum()) <= max(1, pat.n_spans // 1000)
+
+
+def test_border_psd_test_changes_nothing(case, orc):
+    """Border path 1 (the phase kernels with D = 8) with the FP64 PSD test
+    in front: the projected span Hessians agree with the path without it to
+    1e-13 and with the oracle's Jacobi projection to 1e-12."""
+    pat, prob, ctx = case
+    C = ctx.to_device(pat.C)
+    out = {}
+    try:
+        ctx.set_border_path(1)
+        for mode in (0, 1):
+            ctx.set_psd_test(mode)
+            out[mode] = ctx.span_terms(C, project=True)[2].double().cpu().numpy()
+    finally:
+        ctx.set_psd_test(2)
+        ctx.set_border_path(0)
+    _, _, oH = prob.span_eval_projected(pat.C, True)
+    print(f"{pat.name}: border path 1 with / without the test {rel(out[1], out[0]):.1e}, vs oracle "
+          f"{rel(out[1], oH):.1e}")
+    assert rel(out[1], out[0]) < 1e-13 and rel(out[1], oH) < 1e-12
 
 
 @pytest.mark.parametrize("form", [1, 2], ids=["pipelined", "two_pass"])

@@ -84,6 +84,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="bsc", choices=["bsc", "reference"])
     p.add_argument("--workload", default="wrinkle1024", choices=sorted(WORKLOADS))
+    p.add_argument("--tuning-out", default=None,
+                   help="write the autotuner's choices for the main workload to this JSON file")
+    p.add_argument("--tuning-in", default=None,
+                   help="apply these autotuner choices (from --tuning-out) instead of autotuning the main workload: "
+                        "a run under a profiler, whose timings differ, then launches the same kernels")
     p.add_argument("--k-layout", default="symmetric", choices=("symmetric", "full"),
                    help="layout of the Newton step's matrix (bsc_set_k_storage; symmetric is the library default)")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -184,7 +189,7 @@ def projection_flops(nred, nneg, nm, nb, psd=False, open_frac=1.0, border_psd=Fa
     certificate's own work is FP32 and not counted), and only the spans with
     a projected eigenvalue go on to the formation again and the
     eigendecomposition.  Border spans (n = 24) pay the FP64 test when it
-    runs on them (border_psd: border path 1 with the test on)."""
+    is on (border_psd: every border path tests first)."""
     n = nred
     D = n // 3
     form = nm * 2 * (36 * D + 9 * D * (D + 1)) + nb * (2 * D * (D + 1))  # T_k and blocks per point
@@ -247,6 +252,16 @@ def stacked(ctx, arrays, torch, np):
     for p, a in enumerate(arrays):
         out[:, ctx.cp_offset[p]:ctx.cp_offset[p + 1]] = np.asarray(a).T
     return torch.from_numpy(out)
+
+
+def apply_tuning(ctx, t):
+    """The autotuner's choices (bsc_tuning as a dict) set through the C ABI."""
+    ctx.set_tiles([max(int(v), 0) for v in t["tile_tu"]])
+    ctx.set_border_path(int(t["border_path"]))
+    ctx.set_p2_variant(int(t["p2_variant"]))
+    ctx.set_psd_test(int(t["psd_test"]))
+    ctx.set_pcg_grid(int(t["pcg_grid"]))
+    ctx.set_pcg_form(int(t["pcg_form"]))
 
 
 def time_newton(ctx, C, C0, Chat, steps, warmup, flush, stream, torch):
@@ -318,7 +333,15 @@ def run_gpu(args):
     C = C0.clone()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
-    tuning = ctx.autotune(C0, Chat)
+    if args.tuning_in:
+        with open(args.tuning_in) as fh:
+            tuning = json.load(fh)
+        apply_tuning(ctx, tuning)
+    else:
+        tuning = ctx.autotune(C0, Chat)
+    if args.tuning_out and rank == 0:
+        with open(args.tuning_out, "w") as fh:
+            json.dump(tuning, fh)
 
     barrier()
     clocks = ClockSampler(local).start()
@@ -344,7 +367,7 @@ def run_gpu(args):
     open_frac = psd_counts[1] / max(psd_counts[0], 1)
     for s_ in range(Nsp):
         flops += projection_flops(int(nred[s_]), int(nneg[s_]), int(nm[s_]), int(nb[s_]), psd, open_frac,
-                                  psd and tuning.get("border_path") == 1)
+                                  psd)
     achieved_tflops = flops / (proj_ms * 1e-3) / 1e12
 
     # e2e: the same Newton step through the C ABI from pinned host buffers
@@ -461,7 +484,8 @@ def run_gpu(args):
         roof_proj = {"kernel": "SPD projection (k_proj_pf: FP32 certificate; k_proj_p0, k_proj_p1, k_proj_p2, "
                                "k_proj_corr, k_project_ring: FP64)",
                      "psd_counts": {"interior_spans": psd_counts[0], "fp64_tested": psd_counts[1],
-                                    "eigendecomposed": psd_counts[2], "mode": tuning.get("psd_test")},
+                                    "eigendecomposed": psd_counts[2], "border_spans": psd_counts[3],
+                                    "border_eigendecomposed": psd_counts[4], "mode": tuning.get("psd_test")},
                      "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                      "traffic": projection_traffic(args.workload, prec == bsc.FP32, tuning),
@@ -721,7 +745,7 @@ def measure_drape(bsc, flush, stream, torch, np, steps, warmup):
             psd = bool(tuning.get("psd_test"))
             pc = ctx.psd_counts()
             fl = sum(projection_flops(int(nred[i]), int(nneg[i]), int(nm[i]), int(nb[i]), psd,
-                                      pc[1] / max(pc[0], 1), psd and tuning.get("border_path") == 1)
+                                      pc[1] / max(pc[0], 1), psd)
                      for i in range(pat.n_spans))
             pms = ph["project"] / k
             out[name]["projection"] = {"ms": pms, "algorithmic_flops": fl,

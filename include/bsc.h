@@ -321,10 +321,12 @@ bsc_status bsc_set_p2_variant(bsc_ctx* ctx, int variant);
  * another mode. */
 bsc_status bsc_set_psd_test(bsc_ctx* ctx, int mode);
 
-/* Span counts of the last interior projection (host array of 3 ints): the
- * interior spans, those the FP64 PSD test ran on (all of them in mode 1,
- * the certificate's open ones in mode 2, none in mode 0) and those that went
- * on to the eigendecomposition. */
+/* Span counts of the last projection (host array of 5 ints): the interior
+ * spans, those the FP64 PSD test ran on (all of them in mode 1, the
+ * certificate's open ones in mode 2, none in mode 0), those that went on to
+ * the eigendecomposition; the border spans, and those of them that went on
+ * to the eigendecomposition (all of them unless the border class runs
+ * through the phase kernels, border path 1, with the PSD test on). */
 bsc_status bsc_psd_counts(bsc_ctx* ctx, int* out);
 
 /* Form of the persistent block-Jacobi PCG (the same iterates up to rounding):

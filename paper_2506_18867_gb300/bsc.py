@@ -511,8 +511,9 @@ class Context:
         self._check(self._lib.bsc_set_psd_test(self._h, int(mode)))
 
     def psd_counts(self):
-        """(interior spans, spans the FP64 test ran on, spans eigendecomposed) of the last projection."""
-        out = (ct.c_int * 3)()
+        """(interior spans, interior spans the FP64 test ran on, interior spans eigendecomposed,
+        border spans, border spans eigendecomposed) of the last projection."""
+        out = (ct.c_int * 5)()
         self._check(self._lib.bsc_psd_counts(self._h, out))
         return tuple(out)
 

@@ -830,12 +830,15 @@ bsc_status bsc_set_psd_test(bsc_ctx* c, int mode) {
 
 bsc_status bsc_psd_counts(bsc_ctx* c, int* out) {
   if (!c || !out) return BSC_ERR_INVALID_ARG;
-  int h[4] = {0, 0, 0, 0};
+  int h[6] = {0, 0, 0, 0, 0, 0};
   CK(cudaMemcpyAsync(h, c->proj_cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "bsc_psd_counts");
   CK(cudaStreamSynchronize(c->stream), "bsc_psd_counts");
   out[0] = h[0];
   out[1] = c->proj_psd == 2 ? h[3] : (c->proj_psd == 1 ? h[0] : 0);
   out[2] = c->proj_psd ? h[2] : h[0];
+  const bool border_test = c->proj_psd != 0;  // every border path tests first
+  out[3] = h[1];
+  out[4] = border_test ? h[4] : h[1];
   return BSC_OK;
 }
 

@@ -49,6 +49,7 @@ struct RingArgs {
   int* __restrict__ status;
   const double* __restrict__ rg;  // [16][Nm] g_q,beta in the Helmert basis
   const double* __restrict__ rl;  // [8][Nb] L_q in the Helmert basis
+  int* fail_count;                // spans failing the PSD test (counted when it runs)
 };
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -285,7 +286,12 @@ struct RingP1Out {
   int* kneg;    // [count]
 };
 
-template <typename T, bool P1ONLY>
+// PSD: before the tridiagonalisation, the warp factors H_r + tau I (LDL^T in
+// FP64, tau = 1e-14 tr(H_r) / n, lane j updating column j from the pivot
+// column it receives by shuffles); a span whose pivots are all positive has
+// no eigenvalue below -tau, keeps its Hessian and leaves the warp free for
+// the next span.
+template <typename T, bool P1ONLY, bool PSD>
 __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const int* __restrict__ list, int count,
                                                          unsigned int* __restrict__ work, RingP1Out out) {
   constexpr int WARPS = RBLOCK / 32;
@@ -370,6 +376,46 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
           for (int c = 0; c < 3; ++c)
             if (c == dp) col[3 * k + c] += WB * Lt[k] * Lk;
       }
+    }
+
+    if (PSD) {
+      double dj = 0.0;
+#pragma unroll
+      for (int i = 0; i < RN; ++i)
+        if (i == lane) dj = col[i];
+      double tr = lane < RN ? dj : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      bool pass = tr > 0.0 && isfinite(tr);
+      const double tau = NEG_REL * tr * (1.0 / RN);
+      double w[RN];
+#pragma unroll
+      for (int i = 0; i < RN; ++i) w[i] = col[i] + (i == lane ? tau : 0.0);
+      for (int k = 0; k < RN && pass; ++k) {
+        double ck[RN], dk = 0.0, cj = 0.0;
+#pragma unroll
+        for (int i = 0; i < RN; ++i) {
+          ck[i] = shfl(w[i], k);  // column k = row k of the trailing matrix
+          if (i == k) dk = ck[i];
+          if (i == lane) cj = ck[i];
+        }
+        pass = dk > 0.0 && isfinite(dk);  // the same on every lane
+        if (pass && lane > k && lane < RN) {
+          const double l = cj / dk;
+#pragma unroll
+          for (int i = 0; i < RN; ++i)
+            if (i > k) w[i] = fma(-l, ck[i], w[i]);
+        }
+      }
+      if (pass) {
+        if (lane == 0) {
+          P.nneg[s] = 0;
+          if (P1ONLY) out.kneg[idx] = 0;
+        }
+        __syncwarp();
+        continue;
+      }
+      if (lane == 0) atomicAdd(P.fail_count, 1);
     }
 
     // ---- Householder tridiagonalisation, lane k owns column k
@@ -554,6 +600,18 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
 
 }  // namespace
 
+template <typename T>
+void launch_ring_t(RingArgs<T> P, const int* list, int count, unsigned int* work, RingP1Out out, int g,
+                   cudaStream_t st, bool p1only, bool psd) {
+  if (p1only) {
+    if (psd) k_project_ring<T, true, true><<<g, RBLOCK, 0, st>>>(P, list, count, work, out);
+    else k_project_ring<T, true, false><<<g, RBLOCK, 0, st>>>(P, list, count, work, out);
+  } else {
+    if (psd) k_project_ring<T, false, true><<<g, RBLOCK, 0, st>>>(P, list, count, work, out);
+    else k_project_ring<T, false, false><<<g, RBLOCK, 0, st>>>(P, list, count, work, out);
+  }
+}
+
 cudaError_t setup_projection_ring() {
   double h[8][9];
   for (int k = 1; k <= 8; ++k) {
@@ -587,6 +645,7 @@ cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* 
   if (count <= 0) return cudaSuccess;
   BSC_COUNT(c, 1);
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->proj_cnt + 4, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   const int need = (count + RBLOCK / 32 - 1) / (RBLOCK / 32);
   int g = ring_grid(c->num_sms);
@@ -596,19 +655,13 @@ cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* 
   if (c->precision == BSC_FP64) {
     RingArgs<double> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const double*)c->tab_mem,
                        (const double*)c->tab_bd, (const double*)c->A_mem, (double*)c->H_span, c->nneg, c->dstatus,
-                       c->red_g, c->red_l};
-    if (p1only)
-      k_project_ring<double, true><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work, out);
-    else
-      k_project_ring<double, false><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work, out);
+                       c->red_g, c->red_l, c->proj_cnt + 4};
+    launch_ring_t<double>(P, c->bucket_list + first, count, work, out, g, st, p1only, c->proj_psd != 0);
   } else {
     RingArgs<float> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const float*)c->tab_mem,
                       (const float*)c->tab_bd, (const float*)c->A_mem, (float*)c->H_span, c->nneg, c->dstatus,
-                      c->red_g, c->red_l};
-    if (p1only)
-      k_project_ring<float, true><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work, out);
-    else
-      k_project_ring<float, false><<<g, RBLOCK, 0, st>>>(P, c->bucket_list + first, count, work, out);
+                      c->red_g, c->red_l, c->proj_cnt + 4};
+    launch_ring_t<float>(P, c->bucket_list + first, count, work, out, g, st, p1only, c->proj_psd != 0);
   }
   return cudaGetLastError();
 }

@@ -179,15 +179,17 @@ def test_psd_test_changes_nothing(case, orc):
     assert int(((nneg0 > 0) != (nneg1 > 0)).sum()) <= max(1, pat.n_spans // 1000)
 
 
-def test_border_psd_test_changes_nothing(case, orc):
-    """Border path 1 (the phase kernels with D = 8) with the FP64 PSD test
-    in front: the projected span Hessians agree with the path without it to
-    1e-13 and with the oracle's Jacobi projection to 1e-12."""
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["warp", "thread", "warp_items"])
+def test_border_psd_test_changes_nothing(case, orc, path):
+    """Every border path with the FP64 PSD test in front (the phase kernels'
+    thread-per-span test on path 1, the warp's own LDL^T on paths 0 and 2):
+    the projected span Hessians agree with the path without it to 1e-13 and
+    with the oracle's Jacobi projection to 1e-12."""
     pat, prob, ctx = case
     C = ctx.to_device(pat.C)
     out = {}
     try:
-        ctx.set_border_path(1)
+        ctx.set_border_path(path)
         for mode in (0, 1):
             ctx.set_psd_test(mode)
             out[mode] = ctx.span_terms(C, project=True)[2].double().cpu().numpy()
@@ -195,7 +197,7 @@ def test_border_psd_test_changes_nothing(case, orc):
         ctx.set_psd_test(2)
         ctx.set_border_path(0)
     _, _, oH = prob.span_eval_projected(pat.C, True)
-    print(f"{pat.name}: border path 1 with / without the test {rel(out[1], out[0]):.1e}, vs oracle "
+    print(f"{pat.name}: border path {path} with / without the test {rel(out[1], out[0]):.1e}, vs oracle "
           f"{rel(out[1], oH):.1e}")
     assert rel(out[1], out[0]) < 1e-13 and rel(out[1], oH) < 1e-12
 

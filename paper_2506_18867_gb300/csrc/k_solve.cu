@@ -582,11 +582,12 @@ cudaError_t launch_coop_pipe(int grid, PcgArgs<T> A, PipeVecs<T> V, cudaStream_t
 
 template <typename T>
 cudaError_t pcg_t(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit, int sym,
-                  const double* gate = nullptr, const double* gate_bb = nullptr) {
+                  const double* gate = nullptr, const double* gate_bb = nullptr, int dinv_ready = 0) {
   const int N = c->N;
   cudaError_t e;
   if ((e = cudaMemsetAsync(c->sync, 0, sizeof(unsigned int) * 2 * (size_t)c->P, c->stream)) != cudaSuccess) return e;
-  k_block_jacobi<T><<<(N + 255) / 256, 256, 0, c->stream>>>(N, (const T*)K, (T*)c->Dinv, c->dstatus, sym ? 0 : 12);
+  if (!dinv_ready)
+    k_block_jacobi<T><<<(N + 255) / 256, 256, 0, c->stream>>>(N, (const T*)K, (T*)c->Dinv, c->dstatus, sym ? 0 : 12);
   PcgArgs<T> A;
   A.N = N; A.maxit = maxit; A.tol = tol;
   A.pd = c->pd; A.blocks = c->pcg_blocks; A.nu = c->nu; A.nv = c->nv;
@@ -737,10 +738,11 @@ cudaError_t launch_spmv(bsc_ctx* c, const void* K, const void* x, void* y, int s
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit, int sym) {
-  BSC_COUNT(c, 2);
-  if (c->precision == BSC_FP64) return pcg_t<double>(c, K, b, x, tol, maxit, sym);
-  return pcg_t<float>(c, K, b, x, tol, maxit, sym);
+cudaError_t launch_pcg(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit, int sym,
+                       int dinv_ready) {
+  BSC_COUNT(c, dinv_ready ? 1 : 2);
+  if (c->precision == BSC_FP64) return pcg_t<double>(c, K, b, x, tol, maxit, sym, nullptr, nullptr, dinv_ready);
+  return pcg_t<float>(c, K, b, x, tol, maxit, sym, nullptr, nullptr, dinv_ready);
 }
 
 cudaError_t launch_pcg_fallback(bsc_ctx* c, const void* K, const void* b, void* x, double tol, int maxit,

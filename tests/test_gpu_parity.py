@@ -263,6 +263,25 @@ def test_symmetric_storage_same_newton_step(case):
     assert e < 1e-14
 
 
+def test_fused_correction_same_matrix(case):
+    """The Newton step leaves the projection's corrections of the spans with
+    negative eigenvalues to the assembly's gather; its matrix (full layout)
+    equals the one bsc_assemble_hessian builds after the separate correction
+    pass, bit for bit (compared through a product with each)."""
+    pat, prob, ctx = case
+    try:
+        ctx.set_k_storage(False)
+        C = ctx.to_device(pat.C)
+        ctx.newton_step(C, ctx.to_device(pat.Chat))
+        x = ctx.to_device(np.random.default_rng(11).standard_normal((pat.n_cp, 3)))
+        y_step = ctx.spmv(x)
+        Kf = ctx.assemble_hessian(ctx.to_device(pat.C), project=True)
+        y_sep = ctx.spmv(x, K=Kf)
+    finally:
+        ctx.set_k_storage(True)
+    assert torch.equal(y_step, y_sep)
+
+
 def test_newton_step_fp64(case, orc):
     pat, prob, ctx = case
     sc = orc.Scene.from_patch(pat, project=True)

@@ -71,7 +71,7 @@ void free_ctx(bsc_ctx* c) {
                   c->Dinv, c->partials, c->sync, c->dstatus, c->dscalars, c->pd, c->cp_patch, c->sp_patch,
                   c->span_items, c->red_items, c->red_off, c->pcg_blocks, c->pcg_out, c->steps, c->patch_E,
                   c->pending, c->proj_work, c->proj_span[0], c->proj_span[1], c->proj_kneg[0], c->proj_kneg[1],
-                  c->red_g, c->red_l, c->red_q, c->fcg_rec, c->proj_cnt, c->proj_sel, c->proj_pre, c->proj_sel1, c->corr_pos};
+                  c->red_g, c->red_l, c->red_q, c->fcg_rec, c->proj_cnt, c->proj_sel, c->proj_pre, c->proj_sel1};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->vec)
@@ -173,10 +173,7 @@ cudaError_t enqueue_newton(bsc_ctx* c, void* C, const void* Chat) {
   mark(c, 0);
   if ((e = launch_span_eval(c, C, 1, hess_mode(1, c->project_default))) != cudaSuccess) return e;
   mark(c, 1);
-  // the projection's corrections of the spans with negative eigenvalues are
-  // applied by the assembly's gather (one pass over the scattered spans less)
-  const int fused = c->project_default == BSC_PROJECT_SPAN;
-  if (fused && (e = launch_project(c, 1)) != cudaSuccess) return e;
+  if (c->project_default == BSC_PROJECT_SPAN && (e = launch_project(c)) != cudaSuccess) return e;
   mark(c, 2);
   if ((e = contact_add(c, C, 1, 1, nullptr)) != cudaSuccess) return e;
   if ((e = launch_patch_energy(c, C, Chat, c->patch_E)) != cudaSuccess) return e;
@@ -185,7 +182,7 @@ cudaError_t enqueue_newton(bsc_ctx* c, void* C, const void* Chat) {
   // the learned solver's network reads the full stencil
   const int sym = newton_sym(c);
   // the block-Jacobi inverses come with the assembly when the PCG solves
-  if ((e = launch_assemble(c, c->K_int, sym, c->solver_cnn ? nullptr : c->Dinv, fused)) != cudaSuccess) return e;
+  if ((e = launch_assemble(c, c->K_int, sym, c->solver_cnn ? nullptr : c->Dinv)) != cudaSuccess) return e;
   mark(c, 3);
   if ((e = launch_axpy_trial(c, g, g, -2.0, rhs)) != cudaSuccess) return e;  // rhs = -g
   if (c->solver_cnn)

@@ -135,10 +135,6 @@ struct bsc_ctx {
                             // certificate of positive definiteness, then the FP64 test on the rest (autotuned)
   int* proj_pre;            // device [interior spans]: class positions the FP32 certificate left open
   int* proj_sel1;           // device [border spans]: class positions failing the border's FP64 test (path 1)
-  // corrections H -= sum lam w w^T left to the assembly (the Newton step):
-  // corr_pos[s] = (position << 1) | class of span s in its class scratch, or -1
-  int corr_fused;
-  int* corr_pos;            // device [Nsp]
   int p0_grid1;             // resident grid of the border's PSD test
   int p0_grid;              // resident grid of the PSD test
   int pf_grid;              // resident grid of the FP32 certificate
@@ -252,17 +248,12 @@ cudaError_t launch_span_eval(bsc_ctx* c, const void* C, int want_grad, int want_
 cudaError_t launch_span_eval_items(bsc_ctx* c, const void* C, int want_grad, int want_hess, const SpanItem* items,
                                    int n_items, int block_tu);
 cudaError_t setup_projection(bsc_ctx* c);
-// fused_corr: leave the rank-k corrections of the spans with negative
-// eigenvalues to the assembly (launch_assemble with the same flag): their
-// positions go to corr_pos instead of a read-modify-write of H
-cudaError_t launch_project(bsc_ctx* c, int fused_corr = 0);
+cudaError_t launch_project(bsc_ctx* c);
 // the border class alone by the given path, on the context's stream (autotuner)
 cudaError_t launch_project_border(bsc_ctx* c, int path);
 cudaError_t launch_project_interior(bsc_ctx* c, int phase);
-// Dinv (optional): also write the inverse diagonal blocks (block-Jacobi);
-// fused_corr: apply the projection's corrections recorded by
-// launch_project(c, 1) while gathering
-cudaError_t launch_assemble(bsc_ctx* c, void* K, int sym = 0, void* Dinv = nullptr, int fused_corr = 0);
+// Dinv (optional): also write the inverse diagonal blocks (block-Jacobi)
+cudaError_t launch_assemble(bsc_ctx* c, void* K, int sym = 0, void* Dinv = nullptr);
 cudaError_t launch_gradient(bsc_ctx* c, const void* C, const void* Chat, void* g);
 // per-patch incremental potential into dE[p] (with a gate: pending patches only)
 cudaError_t launch_patch_energy(bsc_ctx* c, const void* C, const void* Chat, double* dE,
@@ -438,39 +429,6 @@ __device__ __forceinline__ void block_jacobi_at(int N, int al, const T* __restri
   b[8] = (a[0] * a[4] - a[1] * a[3]) * id;
 #pragma unroll
   for (int k = 0; k < 9; ++k) Dinv[(size_t)k * N + al] = (T)b[k];
-}
-
-// The projection's pending corrections, read by the assembly: per class k
-// (0 interior, 1 border) the scratch of the spans with negative eigenvalues,
-// by position: kneg, lam (FP64, stride cs), w (T, [27 kneg] x cs).
-template <typename T>
-struct CorrArgs {
-  const int* __restrict__ pos;  // [Nsp]: (position << 1) | class, or -1; nullptr: no pending corrections
-  const int* __restrict__ kneg[2];
-  const double* __restrict__ lam[2];
-  const T* __restrict__ W[2];
-  int cs[2];
-};
-
-CorrArgs<float> corr_args_f(const bsc_ctx* c);
-CorrArgs<double> corr_args_d(const bsc_ctx* c);
-
-// Correction of the packed span-Hessian entry (a, c), a <= c, of the span
-// at scratch position cp: sum_r (lam_r w_r[a]) w_r[c], in the order and
-// precision of the projection's own correction kernel.
-template <typename T>
-__device__ __forceinline__ T corr_entry(const CorrArgs<T>& cr, int cp, int a, int c) {
-  const int k = cp & 1, pos = cp >> 1;
-  const int kneg = cr.kneg[k][pos];
-  const size_t cs = (size_t)cr.cs[k];
-  const double* __restrict__ lam = cr.lam[k];
-  const T* __restrict__ W = cr.W[k];
-  T acc = T(0);
-  for (int r = 0; r < kneg; ++r) {
-    const T la = (T)lam[r * cs + pos] * W[(27 * r + a) * cs + pos];
-    acc += la * W[(27 * r + c) * cs + pos];
-  }
-  return acc;
 }
 
 // Row alpha (patch-local index) of y = K x in the element type T; K and x

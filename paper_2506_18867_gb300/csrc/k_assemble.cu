@@ -29,16 +29,11 @@ namespace {
 // Dinv (optional): the thread of a diagonal block also writes its inverse,
 // the block-Jacobi preconditioner of the solve that follows (the same FP64
 // adjugate of the same entries as k_block_jacobi, so the same values).
-// cr.pos (optional): spans whose projection left the correction
-// H -= sum lam w w^T to this gather; each of their entries is corrected as
-// it is read, with the arithmetic of the projection's correction kernel, so
-// K is the same as after that kernel, without the read-modify-write of the
-// scattered spans' Hessian planes.
 template <typename T, bool SYM>
 __global__ void k_assemble(int N, int Nsp, const PatchDev* __restrict__ pd, const int* __restrict__ cp_patch,
                            const T* __restrict__ H, const double* __restrict__ mass,
                            const uint8_t* __restrict__ pinned, T* __restrict__ K, T* __restrict__ Dinv,
-                           int* __restrict__ status, const CorrArgs<T> cr) {
+                           int* __restrict__ status) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (SYM ? 13ll : 25ll) * N) return;
   const int s_out = (int)(t / N), al = (int)(t - (long long)s_out * N);
@@ -63,15 +58,12 @@ __global__ void k_assemble(int N, int Nsp, const PatchDev* __restrict__ pd, cons
         for (int a = a_lo; a <= a_hi; ++a) {
           const int s = sp0 + b * Su + a;
           const int la = (i - a) + 3 * (j - b), lb = (ib - a) + 3 * (jb - b);
-          const int cp = cr.pos ? cr.pos[s] : -1;
 #pragma unroll
           for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
               const int R = 3 * la + r, Cc = 3 * lb + c;
-              T h = H[(size_t)sym_upk(R, Cc, 27) * Nsp + s];
-              if (cp >= 0) h = h - corr_entry<T>(cr, cp, min(R, Cc), max(R, Cc));
-              blk[3 * r + c] += h;
+              blk[3 * r + c] += H[(size_t)sym_upk(R, Cc, 27) * Nsp + s];
             }
         }
       if (du == 0 && dv == 0) {
@@ -229,31 +221,28 @@ cudaError_t build_red_items(bsc_ctx* c) {
   return cudaMemcpy(c->red_off, off.data(), sizeof(int) * (c->P + 1), cudaMemcpyHostToDevice);
 }
 
-cudaError_t launch_assemble(bsc_ctx* c, void* K, int sym, void* Dinv, int fused_corr) {
+cudaError_t launch_assemble(bsc_ctx* c, void* K, int sym, void* Dinv) {
   BSC_COUNT(c, 1);
-  CorrArgs<double> crd = corr_args_d(c);
-  CorrArgs<float> crf = corr_args_f(c);
-  if (!fused_corr) crd.pos = crf.pos = nullptr;
   const int B = 256;
   const long long G = ((sym ? 13ll : 25ll) * c->N + B - 1) / B;
   if (c->precision == BSC_FP64) {
     if (sym)
       k_assemble<double, true><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch,
                                                                  (const double*)c->H_span, c->mass, c->pinned,
-                                                                 (double*)K, (double*)Dinv, c->dstatus, crd);
+                                                                 (double*)K, (double*)Dinv, c->dstatus);
     else
       k_assemble<double, false><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch,
                                                                   (const double*)c->H_span, c->mass, c->pinned,
-                                                                  (double*)K, (double*)Dinv, c->dstatus, crd);
+                                                                  (double*)K, (double*)Dinv, c->dstatus);
   } else {
     if (sym)
       k_assemble<float, true><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch,
                                                                 (const float*)c->H_span, c->mass, c->pinned,
-                                                                (float*)K, (float*)Dinv, c->dstatus, crf);
+                                                                (float*)K, (float*)Dinv, c->dstatus);
     else
       k_assemble<float, false><<<(unsigned)G, B, 0, c->stream>>>(c->N, c->Nsp, c->pd, c->cp_patch,
                                                                  (const float*)c->H_span, c->mass, c->pinned,
-                                                                 (float*)K, (float*)Dinv, c->dstatus, crf);
+                                                                 (float*)K, (float*)Dinv, c->dstatus);
   }
   return cudaGetLastError();
 }

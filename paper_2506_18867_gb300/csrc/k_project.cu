@@ -417,16 +417,6 @@ __global__ void __launch_bounds__(P0Block<D>::value, 1)
   }
 }
 
-// The corrections left to the assembly: corr_pos[s] = (position << 1) | k
-// for every span of class k with negative eigenvalues (its position in the
-// class scratch: the failing list's, or the class order without one).
-__global__ void k_corr_map(const int* __restrict__ cnt, const int* __restrict__ list, const int* __restrict__ sel,
-                           const int* __restrict__ kneg_in, int k, int* __restrict__ corr_pos) {
-  const int count = *cnt;
-  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < count; pos += gridDim.x * blockDim.x)
-    if (kneg_in[pos] > 0) corr_pos[list[sel ? sel[pos] : pos]] = (pos << 1) | k;
-}
-
 // Finds the owner of item i given an exclusive prefix over the block.
 template <int BLOCK>
 __device__ __forceinline__ int owner_of(const int* prefix, int i) {
@@ -682,12 +672,6 @@ cudaError_t run_class(bsc_ctx* c, int k, const int* list, int count, cudaStream_
           P, list, sel, cnt, count, c->proj_kneg[k], c->proj_span[k], c->proj_scratch[k], c->proj_work + k);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     BSC_COUNT(c, 1);
-    if (c->corr_fused) {
-      const int g = (count + 255) / 256;
-      k_corr_map<<<g < 32 * c->num_sms ? g : 32 * c->num_sms, 256, 0, st>>>(cnt, list, sel, c->proj_kneg[k], k,
-                                                                           c->corr_pos);
-      return cudaGetLastError();
-    }
     using SS = SpanScratch<D>;
     const double* sp = c->proj_span[k];
     const long long nthreads = 27ll * count;
@@ -864,8 +848,6 @@ cudaError_t setup_projection(bsc_ctx* c) {
   // the border spans fill the resident warps a few times over at most
   c->border_path = n1 > 8 * 8 * c->num_sms ? 1 : 0;
   if ((e = cudaMalloc(&c->proj_work, sizeof(unsigned int) * 4)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&c->corr_pos, sizeof(int) * (size_t)(c->Nsp > 0 ? c->Nsp : 1))) != cudaSuccess) return e;
-  c->corr_fused = 0;
   {
     // the class sizes as device counts (the phase kernels read their span
     // count from the device: the PSD test's compacted count, or these)
@@ -881,33 +863,9 @@ cudaError_t setup_projection(bsc_ctx* c) {
   return cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
 }
 
-template <typename T>
-CorrArgs<T> corr_args_t(const bsc_ctx* c) {
-  CorrArgs<T> a;
-  a.pos = c->corr_pos;
-  const int n0 = c->bucket_off[1] - c->bucket_off[0], n1 = c->bucket_off[3] - c->bucket_off[1];
-  a.cs[0] = n0;
-  a.cs[1] = n1;
-  a.kneg[0] = c->proj_kneg[0];
-  a.kneg[1] = c->proj_kneg[1];
-  a.lam[0] = c->proj_span[0] + (size_t)SpanScratch<5>::LAM * n0;
-  a.lam[1] = c->proj_span[1] + (size_t)SpanScratch<8>::LAM * n1;
-  a.W[0] = reinterpret_cast<const T*>(c->proj_span[0] + (size_t)SpanScratch<5>::W * n0);
-  a.W[1] = reinterpret_cast<const T*>(c->proj_span[1] + (size_t)SpanScratch<8>::W * n1);
-  return a;
-}
-
-CorrArgs<float> corr_args_f(const bsc_ctx* c) { return corr_args_t<float>(c); }
-CorrArgs<double> corr_args_d(const bsc_ctx* c) { return corr_args_t<double>(c); }
-
-cudaError_t launch_project(bsc_ctx* c, int fused_corr) {
-  cudaError_t e = cudaSuccess;
-  if (fused_corr) e = cudaMemsetAsync(c->corr_pos, 0xff, sizeof(int) * (size_t)c->Nsp, c->stream);
-  if (e != cudaSuccess) return e;
-  c->corr_fused = fused_corr ? 1 : 0;
-  e = c->precision == BSC_FP64 ? run_all<double>(c) : run_all<float>(c);
-  c->corr_fused = 0;
-  return e;
+cudaError_t launch_project(bsc_ctx* c) {
+  if (c->precision == BSC_FP64) return run_all<double>(c);
+  return run_all<float>(c);
 }
 
 // The interior class's phase 1 or phase 2 alone (phase 0 / 1), on the

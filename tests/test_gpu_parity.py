@@ -263,11 +263,10 @@ def test_symmetric_storage_same_newton_step(case):
     assert e < 1e-14
 
 
-def test_fused_correction_same_matrix(case):
-    """The Newton step leaves the projection's corrections of the spans with
-    negative eigenvalues to the assembly's gather; its matrix (full layout)
-    equals the one bsc_assemble_hessian builds after the separate correction
-    pass, bit for bit (compared through a product with each)."""
+def test_newton_step_matrix_equals_assembled(case):
+    """The Newton step's own matrix (full layout; its assembly also writes the
+    block-Jacobi inverses) equals the one bsc_assemble_hessian builds at the
+    same state, bit for bit (compared through a product with each)."""
     pat, prob, ctx = case
     try:
         ctx.set_k_storage(False)

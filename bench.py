@@ -867,17 +867,18 @@ def measure_learned(bsc, np, torch, flush, seeds=(1_000_000, 1_000_001, 1_000_00
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the projection
-# phase per Newton step, from one metrics-only ncu capture of the drape bench
-# (dram__bytes_* of every projection launch of one step), keyed by the autotuner's border path and
-# phase-2 variant and by a hash of the projection sources it was taken with.
-#   path 2, variant 0: ring<1> 3.7 + p2<8> 6.9 + corr 16.1 + p1<5> 57.5
-#                      + p2<5,2> 153.8 + corr 183.1 MB
-#   path 1, variant 0: p1<5> + p1<8> + p2<8> + corr + p2<5,2> + corr, 421.4 MB
-#   path 0, variant 0: ring<0> + p1<5> + p2<5,2> + corr, 413.1 MB
-PROJECTION_TRAFFIC_HASH = "6496be87f21c3bc4"
-PROJECTION_TRAFFIC = {("drape256", True, 2, 0): 421.2e6,
-                      ("drape256", True, 1, 0): 421.4e6,
-                      ("drape256", True, 0, 0): 413.1e6}
+# phase per Newton step, from a metrics-only ncu capture of the 512x512 wrinkle
+# field (every projection launch of four steps, tuning applied from a plain
+# run; profiles/k_proj_psd_wrinkle512_fp32.md), keyed by the autotuner's border
+# path and phase-2 variant and by a hash of the projection sources it was taken
+# with.  Border path 0, variant 0, per step: ring (with its PSD test) 12.1 +
+# FP32 certificate 101.2 + FP64 test 98.6 + p1 43.8 + p2 67.0 + corrections
+# 386.1 MB = 708.9 MB.
+PROJECTION_TRAFFIC_HASH = "320999ddda0c2a4f"
+PROJECTION_TRAFFIC = {("wrinkle512", True, 0, 0): 708.9e6,
+                      # the 512x512 capture scaled by the span count (1,044,484 / 260,100): every
+                      # projection kernel's traffic is per span (classes and failing shares alike)
+                      ("wrinkle1024", True, 0, 0): 708.9e6 * 1044484 / 260100}
 PROJECTION_SOURCES = ("k_project.cu", "proj_core.cuh", "k_project_ring.cu")
 # Executed FP64 work of the projection kernels of one drape step (border path 2,
 # phase-2 variant 0), from the same kind of capture with the metrics

@@ -492,6 +492,84 @@ __global__ void __launch_bounds__(EVAL_BLOCK, sizeof(T) == 4 ? 2 : 1)
   }
 }
 
+// Energy only (no gradient, no Hessian): one thread per span, its points in
+// the order of k_span_eval (membrane points, then bending points) with the
+// same per-point arithmetic, so E_span is the same as that kernel's; without
+// the slice structure a span costs a thread, not a warp's eight slices.
+template <typename T>
+__global__ void __launch_bounds__(128) k_span_energy(SpanArgs<T> P, const int* __restrict__ sp_patch) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P.Nsp) return;
+  const int p = sp_patch[s];
+  if (P.gate && P.gate[p].state != 1) return;
+  const PatchDev* pt = P.pd + p;
+  const int Su = __ldg(&pt->Su), nu = __ldg(&pt->nu), cp0 = __ldg(&pt->cp0), sp0 = __ldg(&pt->sp0);
+  const int l0 = s - sp0, a = l0 % Su, b = l0 / Su;
+  const T mu1 = (T)__ldg(&pt->mu1), mu2 = (T)__ldg(&pt->mu2), mush = (T)__ldg(&pt->mush),
+          mubd = (T)__ldg(&pt->mubd);
+  const T* __restrict__ Cp = P.C + cp0;
+  T Cl[9][3];
+  {
+    const int ac = (b + 1) * nu + a + 1;
+    T c0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) c0[c] = Cp[c * P.N + ac];
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+      const int al = (b + l / 3) * nu + a + l % 3;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Cl[l][c] = Cp[c * P.N + al] - c0[c];
+    }
+  }
+  const int q0 = P.moff[s], nm = P.moff[s + 1] - q0, r0 = P.boff[s], nb = P.boff[s + 1] - r0;
+  double E = 0.0;
+  for (int pi = 0; pi < nm; ++pi) {
+    const int q = q0 + pi;
+    const T W = P.tabm[q];
+    T gq[9][2];
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+      gq[l][0] = P.tabm[(1 + 2 * l) * P.Nm + q];
+      gq[l][1] = P.tabm[(2 + 2 * l) * P.Nm + q];
+    }
+    T f[2][3];
+#pragma unroll
+    for (int be = 0; be < 2; ++be)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T acc1 = T(0);
+#pragma unroll
+        for (int l = 0; l < 9; ++l) acc1 += Cl[l][c] * gq[l][be];
+        f[be][c] = acc1;
+      }
+    const T I5a = f[0][0] * f[0][0] + f[0][1] * f[0][1] + f[0][2] * f[0][2];
+    const T I5b = f[1][0] * f[1][0] + f[1][1] * f[1][1] + f[1][2] * f[1][2];
+    const T I6 = f[0][0] * f[1][0] + f[0][1] * f[1][1] + f[0][2] * f[1][2];
+    const T r1 = rsqrt_(I5a), r2 = rsqrt_(I5b);
+    const T s1 = I5a * r1, s2 = I5b * r2;
+    const T e1 = s1 - T(1), e2 = s2 - T(1);
+    // the product rounded on its own, then added (as k_span_eval's staged point energies)
+    E = __dadd_rn(E, (double)W * (double)(mu1 * e1 * e1 + mu2 * e2 * e2 + mush * I6 * I6));
+  }
+  for (int pi = 0; pi < nb; ++pi) {
+    const int q = r0 + pi;
+    const T WB = P.tabb[q] * mubd;
+    T L[9];
+#pragma unroll
+    for (int l = 0; l < 9; ++l) L[l] = P.tabb[(1 + l) * P.Nb + q];
+    T lap[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T acc1 = T(0);
+#pragma unroll
+      for (int l = 0; l < 9; ++l) acc1 += L[l] * Cl[l][c];
+      lap[c] = acc1;
+    }
+    E = __dadd_rn(E, 0.5 * (double)WB * (double)(lap[0] * lap[0] + lap[1] * lap[1] + lap[2] * lap[2]));
+  }
+  P.E[s] = E;
+}
+
 template <typename T>
 SpanArgs<T> make_args(bsc_ctx* c, const void* C, const SpanItem* items, const PatchStep* gate) {
   SpanArgs<T> P;
@@ -535,6 +613,10 @@ cudaError_t run(bsc_ctx* c, const void* C, int want_grad, int want_hess, const S
                 const PatchStep* gate) {
   if (n_items <= 0) return cudaSuccess;
   SpanArgs<T> P = make_args<T>(c, C, items, gate);
+  if (!want_grad && !want_hess && items == c->span_items) {
+    k_span_energy<T><<<(c->Nsp + 127) / 128, 128, 0, c->stream>>>(P, c->sp_patch);
+    return cudaGetLastError();
+  }
   CUtensorMap m;
   cudaError_t e = planes_map<T>(&m, C, c->N);
   if (e != cudaSuccess) return e;

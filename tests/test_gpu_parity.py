@@ -281,6 +281,23 @@ def test_newton_step_matrix_equals_assembled(case):
     assert torch.equal(y_step, y_sep)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_energy_kernel_matches_full_evaluation(case, precision):
+    """bsc_energy runs the thread-per-span energy kernel; the Newton step's E0
+    comes from the full span evaluation (gradient and Hessian) at the same
+    state through the same reductions: the two are equal bit for bit."""
+    pat, prob, ctx64 = case
+    ctx = ctx64 if precision == "fp64" else bsc.context_for_patch(pat, precision=bsc.FP32)
+    try:
+        C, Ch = ctx.to_device(pat.C), ctx.to_device(pat.Chat)
+        E = ctx.energy(C, Ch)
+        rep = ctx.newton_step(C, Ch)
+        assert E == rep.E0
+    finally:
+        if ctx is not ctx64:
+            ctx.close()
+
+
 def test_newton_step_fp64(case, orc):
     pat, prob, ctx = case
     sc = orc.Scene.from_patch(pat, project=True)

@@ -236,13 +236,16 @@ __global__ void __launch_bounds__(P1Block<D>::value, 1)
 //    Stability of Numerical Algorithms, 2nd ed., Thm. 9.3, one rounding more
 //    per multiplier), and U = D L^T entrywise up to 1 + theta, |theta| <=
 //    gamma_2; so X = L D L^T + E with |E| <= gamma_{n+4} |L| D |L^T|, and
-//    ||E||_2 <= gamma_{n+4} tr(L D L^T) <= 2 gamma_{n+4} tr(X).
-// Factoring X = Â - sigma I with sigma = 2.2 (2 gamma_{n+4} tr Â + gamma_16 S)
-// (the factor covers the rounding of the shift, of tr Â and of S): if every
-// pivot is positive, H_r = L D L^T + sigma I - E + (H_r - Â) has every
-// eigenvalue above sigma / 2 > 0.  Such a span has no negative eigenvalue, and the FP64 test,
-// whose margin is 1e-14 tr / n, would pass it as well: taking the
-// certificate instead changes no span's result.  The spans it cannot decide
+//    ||E||_2 <= gamma_{n+4} tr(L D L^T) = gamma_{n+4} tr(X + E), that is at
+//    most gamma_{n+4} tr(X) / (1 - gamma_{n+4}) (the diagonal of |L| D |L^T|
+//    is that of L D L^T when D > 0).
+// Factoring X = Â - sigma I with sigma = 1.1 (gamma_{n+4} tr Â + gamma_16 S)
+// (the tenth covers the rounding of the shift, u (S + sigma), and of tr Â and
+// S): if every pivot is positive, H_r = L D L^T + sigma I - E + (H_r - Â) has
+// every eigenvalue above a positive margin of a few 1e-8 tr(H_r).  Such a
+// span has no negative eigenvalue, and the FP64 test, whose margin is 1e-14
+// tr / n and whose own rounding is some 1e-15 tr, would pass it as well:
+// taking the certificate instead changes no span's result.  The spans it cannot decide
 // (their class positions appended to pre_out) go on to the FP64 test.
 constexpr int PF_BLOCK = 128;
 
@@ -330,7 +333,7 @@ __device__ __forceinline__ bool certify_pd_f32(const Tab& tab) {
 #pragma unroll
   for (int i = 0; i < n; ++i) tr += A[proj::lp(i, i)];
   if (!(tr > 0.0f) || !isfinite(tr) || !isfinite(S)) return false;
-  const float sigma = 2.2f * (2.0f * g_n4 * tr + g_16 * S);
+  const float sigma = 1.1f * (g_n4 * tr + g_16 * S);
 #pragma unroll
   for (int i = 0; i < n; ++i) A[proj::lp(i, i)] -= sigma;
   // right-looking LDL^T on the packed lower triangle: a(i, j) -= l_ik a(j, k),

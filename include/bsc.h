@@ -261,8 +261,9 @@ typedef struct bsc_tuning {
   int border_path;         /* SPD projection of the border spans: 0 one warp per
                               span, 1 one thread per span, 2 one warp per span
                               to the tridiagonal form, then one thread per
-                              eigenpair (chosen by time) */
-  double border_ms[3];     /* measured ms of the whole projection per border path */
+                              eigenpair, 3 one warp per span for the PSD test,
+                              then one warp per failing span (chosen by time) */
+  double border_ms[4];     /* measured ms of the whole projection per border path */
   int p2_variant;          /* phase 2 of the interior projection: 0 two, 1 three
                               resident blocks per SM (fewer registers; chosen by time) */
   double p2_ms[2];         /* measured ms of that phase per variant */
@@ -292,7 +293,7 @@ bsc_status bsc_set_pcg_grid(bsc_ctx* ctx, int grid);
 /* Set the tile widths by hand (4 entries, each 0, 8, 16 or 32). */
 bsc_status bsc_set_tiles(bsc_ctx* ctx, const int* tile_tu);
 
-/* Set the border projection path by hand (0, 1 or 2, see bsc_tuning); all
+/* Set the border projection path by hand (0, 1, 2 or 3, see bsc_tuning); all
  * compute the same projection up to rounding. */
 bsc_status bsc_set_border_path(bsc_ctx* ctx, int path);
 
@@ -325,8 +326,7 @@ bsc_status bsc_set_psd_test(bsc_ctx* ctx, int mode);
  * spans, those the FP64 PSD test ran on (all of them in mode 1, the
  * certificate's open ones in mode 2, none in mode 0), those that went on to
  * the eigendecomposition; the border spans, and those of them that went on
- * to the eigendecomposition (all of them unless the border class runs
- * through the phase kernels, border path 1, with the PSD test on). */
+ * to the eigendecomposition (all of them with the PSD test off). */
 bsc_status bsc_psd_counts(bsc_ctx* ctx, int* out);
 
 /* Form of the persistent block-Jacobi PCG (the same iterates up to rounding):

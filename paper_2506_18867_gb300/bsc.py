@@ -92,7 +92,7 @@ class NewtonReport(ct.Structure):
 
 class Tuning(ct.Structure):
     _fields_ = [("tile_tu", ct.c_int * 4), ("tile_ms", (ct.c_double * 4) * 4), ("pcg_grid", ct.c_int),
-                ("border_path", ct.c_int), ("border_ms", ct.c_double * 3), ("p2_variant", ct.c_int),
+                ("border_path", ct.c_int), ("border_ms", ct.c_double * 4), ("p2_variant", ct.c_int),
                 ("p2_ms", ct.c_double * 2), ("pcg_grid_cand", ct.c_int * 4), ("pcg_ms", ct.c_double * 4),
                 ("pcg_form", ct.c_int), ("pcg_form_ms", ct.c_double * 3), ("psd_test", ct.c_int),
                 ("psd_ms", ct.c_double * 3)]

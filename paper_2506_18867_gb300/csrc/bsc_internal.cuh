@@ -138,7 +138,8 @@ struct bsc_ctx {
   int p0_grid1;             // resident grid of the border's PSD test
   int p0_grid;              // resident grid of the PSD test
   int pf_grid;              // resident grid of the FP32 certificate
-  int border_path;          // 0: one warp per border span, 1: one thread per border span
+  int border_path;          // 0: one warp per border span, 1: one thread per border span, 2: warps to the
+                            // tridiagonal form then eigenpair items, 3: warps test first, then take the failing
   cudaStream_t side[2];     // forked stream of the border class
   cudaEvent_t fork_ev, join_ev[2];
 

@@ -34,7 +34,7 @@
 
 cudaError_t setup_projection_ring();
 cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* work, cudaStream_t st, bool p1only,
-                                double* sspan, int* kneg);
+                                double* sspan, int* kneg, bool two_pass = false);
 
 
 namespace {
@@ -699,7 +699,8 @@ template <typename T>
 cudaError_t run_border(bsc_ctx* c, int path, cudaStream_t st) {
   const int first = c->bucket_off[1], count = c->bucket_off[3] - c->bucket_off[1];
   static_assert(SpanScratch<8>::R == 300 && SpanScratch<8>::TN == 372, "ring phase-1 layout");
-  if (path == 0) return launch_project_ring(c, first, count, c->proj_work + 2, st, false, nullptr, nullptr);
+  if (path == 0 || path == 3)
+    return launch_project_ring(c, first, count, c->proj_work + 2, st, false, nullptr, nullptr, path == 3);
   if (path == 2) {
     cudaError_t e = launch_project_ring(c, first, count, c->proj_work + 2, st, true, c->proj_span[1], c->proj_kneg[1]);
     if (e != cudaSuccess) return e;
@@ -718,7 +719,7 @@ cudaError_t run_all(bsc_ctx* c) {
   cudaError_t e;
   const int* list0 = c->bucket_list + c->bucket_off[0];
   const int n0 = c->bucket_off[1] - c->bucket_off[0];
-  const bool early = c->border_path != 1;
+  const bool early = c->border_path != 1;  // the warp-per-span kernels fit beside the interior phase 1
   if (!early && (e = run_class<T, 5>(c, 0, list0, n0, c->stream, 0)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->fork_ev, c->stream)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(c->side[0], c->fork_ev, 0)) != cudaSuccess) return e;

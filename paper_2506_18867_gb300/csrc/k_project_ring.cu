@@ -50,6 +50,12 @@ struct RingArgs {
   const double* __restrict__ rg;  // [16][Nm] g_q,beta in the Helmert basis
   const double* __restrict__ rl;  // [8][Nb] L_q in the Helmert basis
   int* fail_count;                // spans failing the PSD test (counted when it runs)
+  // test only (fail_list != nullptr, PSD): the class positions of the spans
+  // failing the test are appended to fail_list and nothing else is done for them
+  int* fail_list;
+  // over a list (sel != nullptr): the class positions sel[0 .. *sel_count)
+  const int* sel;
+  const int* sel_count;
 };
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -305,11 +311,13 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
   double* const ee = s_e[wp];
   double* const ee2 = s_e2[wp];
   const int kp = lane / 3, dp = lane % 3;  // this lane's column j = 3 kp + dp
+  const int n_items = P.sel ? *P.sel_count : count;
   for (;;) {
     int idx = 0;
     if (lane == 0) idx = (int)atomicAdd(work, 1u);
     idx = __shfl_sync(0xffffffffu, idx, 0);
-    if (idx >= count) break;
+    if (idx >= n_items) break;
+    if (P.sel) idx = P.sel[idx];
     const int s = list[idx];
     const int q0 = P.moff[s], q1 = P.moff[s + 1], b0 = P.boff[s], b1 = P.boff[s + 1];
     const double mubd = P.pd[P.sp_patch[s]].mubd;
@@ -415,7 +423,14 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
         __syncwarp();
         continue;
       }
-      if (lane == 0) atomicAdd(P.fail_count, 1);
+      if (lane == 0) {
+        const int k = atomicAdd(P.fail_count, 1);
+        if (P.fail_list) P.fail_list[k] = idx;
+      }
+      if (P.fail_list) {
+        __syncwarp();
+        continue;
+      }
     }
 
     // ---- Householder tridiagonalisation, lane k owns column k
@@ -603,6 +618,8 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
 template <typename T>
 void launch_ring_t(RingArgs<T> P, const int* list, int count, unsigned int* work, RingP1Out out, int g,
                    cudaStream_t st, bool p1only, bool psd) {
+  // a pass over a list of failing spans runs without the test (they failed it)
+  if (P.sel) psd = false;
   if (p1only) {
     if (psd) k_project_ring<T, true, true><<<g, RBLOCK, 0, st>>>(P, list, count, work, out);
     else k_project_ring<T, true, false><<<g, RBLOCK, 0, st>>>(P, list, count, work, out);
@@ -640,10 +657,16 @@ int ring_grid(int num_sms) { return 3 * num_sms; }
 // Border class, one warp per span.  p1only: stop after the tridiagonal form
 // and hand each span to k_proj_p2<T, 8> through its class scratch (sspan,
 // laid out as reflectors [300], tridiagonal [72], scale [1]) and kneg.
+// two_pass (with the PSD test on): first every warp only tests its spans and
+// appends the failing ones to the border's list, then the warps take the
+// failing spans one each - the few expensive spans no longer queue behind
+// one another on the warps that happened to draw them.
 cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* work, cudaStream_t st, bool p1only,
-                                double* sspan, int* kneg) {
+                                double* sspan, int* kneg, bool two_pass) {
   if (count <= 0) return cudaSuccess;
-  BSC_COUNT(c, 1);
+  const bool psd = c->proj_psd != 0;
+  two_pass = two_pass && psd && !p1only;
+  BSC_COUNT(c, two_pass ? 2 : 1);
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->proj_cnt + 4, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
@@ -652,16 +675,25 @@ cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* 
   if (g > need) g = need;
   const size_t cnt = (size_t)count;
   RingP1Out out{sspan, sspan ? sspan + 300 * cnt : nullptr, sspan ? sspan + 372 * cnt : nullptr, kneg};
-  if (c->precision == BSC_FP64) {
-    RingArgs<double> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const double*)c->tab_mem,
-                       (const double*)c->tab_bd, (const double*)c->A_mem, (double*)c->H_span, c->nneg, c->dstatus,
-                       c->red_g, c->red_l, c->proj_cnt + 4};
-    launch_ring_t<double>(P, c->bucket_list + first, count, work, out, g, st, p1only, c->proj_psd != 0);
-  } else {
-    RingArgs<float> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const float*)c->tab_mem,
-                      (const float*)c->tab_bd, (const float*)c->A_mem, (float*)c->H_span, c->nneg, c->dstatus,
-                      c->red_g, c->red_l, c->proj_cnt + 4};
-    launch_ring_t<float>(P, c->bucket_list + first, count, work, out, g, st, p1only, c->proj_psd != 0);
+  const int* list = c->bucket_list + first;
+  for (int pass = 0; pass < (two_pass ? 2 : 1); ++pass) {
+    if (pass == 1 && (e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+    int* fail_list = two_pass && pass == 0 ? c->proj_sel1 : nullptr;
+    const int* sel = pass == 1 ? c->proj_sel1 : nullptr;
+    const int* sel_count = pass == 1 ? c->proj_cnt + 4 : nullptr;
+    if (c->precision == BSC_FP64) {
+      RingArgs<double> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off,
+                         (const double*)c->tab_mem, (const double*)c->tab_bd, (const double*)c->A_mem,
+                         (double*)c->H_span, c->nneg, c->dstatus, c->red_g, c->red_l, c->proj_cnt + 4, fail_list,
+                         sel, sel_count};
+      launch_ring_t<double>(P, list, count, work, out, g, st, p1only, psd);
+    } else {
+      RingArgs<float> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const float*)c->tab_mem,
+                        (const float*)c->tab_bd, (const float*)c->A_mem, (float*)c->H_span, c->nneg, c->dstatus,
+                        c->red_g, c->red_l, c->proj_cnt + 4, fail_list, sel, sel_count};
+      launch_ring_t<float>(P, list, count, work, out, g, st, p1only, psd);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }

@@ -86,12 +86,13 @@ def test_lumped_mass(case):
     assert rel(ctx.lumped_mass(), prob.lumped_mass()) < 1e-13
 
 
-@pytest.mark.parametrize("project,border_path", [(False, 0), (True, 0), (True, 1), (True, 2)],
-                         ids=["raw", "proj-warp", "proj-thread", "proj-warp-items"])
+@pytest.mark.parametrize("project,border_path", [(False, 0), (True, 0), (True, 1), (True, 2), (True, 3)],
+                         ids=["raw", "proj-warp", "proj-thread", "proj-warp-items", "proj-warp-two-pass"])
 def test_span_terms_fp64(case, project, border_path):
     """Span terms against the oracle; projected by every path of the border
     spans (one warp per span; one thread per span; one warp per span to the
-    tridiagonal form, then one thread per eigenpair)."""
+    tridiagonal form, then one thread per eigenpair; one warp per span for
+    the PSD test, then one warp per failing span)."""
     pat, prob, ctx = case
     C = ctx.to_device(pat.C)
     ctx.set_border_path(border_path)
@@ -179,7 +180,7 @@ def test_psd_test_changes_nothing(case, orc):
     assert int(((nneg0 > 0) != (nneg1 > 0)).sum()) <= max(1, pat.n_spans // 1000)
 
 
-@pytest.mark.parametrize("path", [0, 1, 2], ids=["warp", "thread", "warp_items"])
+@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["warp", "thread", "warp_items", "warp_two_pass"])
 def test_border_psd_test_changes_nothing(case, orc, path):
     """Every border path with the FP64 PSD test in front (the phase kernels'
     thread-per-span test on path 1, the warp's own LDL^T on paths 0 and 2):
@@ -345,7 +346,7 @@ def test_gauss_rules_projected(orc, rule):
     _, _, oHp = prob.span_eval_projected(pat.C, orc.PROJECT_POINT)
     with bsc.context_for_patch(pat, precision=bsc.FP64, quadrature=(rule, rule)) as ctx:
         C = ctx.to_device(pat.C)
-        for path in (0, 1, 2):
+        for path in (0, 1, 2, 3):
             ctx.set_border_path(path)
             _, _, H = ctx.span_terms(C, project=bsc.PROJECT_SPAN)
             assert rel(H.cpu().numpy(), oHs) < 1e-12, path

@@ -909,15 +909,19 @@ PCG_TRAFFIC_PER_CP_ITER = 4.451e9 / (32 * 262144)
 PCG_TRAFFIC_HASH = "ddd6b7a6ebab236b"
 PCG_TRAFFIC_FORM = 2
 PCG_TRAFFIC_WORKLOADS = ("wrinkle512", "wrinkle1024")
+# the solver kernels and the product rows they inline
+PCG_SOURCES = ("k_solve.cu", "bsc_internal.cuh")
 
 
 def pcg_traffic(workload, fp32, tuning, iters, k_sym=True):
     import hashlib
     if workload not in PCG_TRAFFIC_WORKLOADS or not fp32 or tuning.get("pcg_form") != PCG_TRAFFIC_FORM or not k_sym:
         return None
-    with open(os.path.join(ROOT, "paper_2506_18867_gb300", "csrc", "k_solve.cu"), "rb") as fh:
-        h = hashlib.sha256(fh.read()).hexdigest()[:16]
-    if h != PCG_TRAFFIC_HASH:
+    hs = hashlib.sha256()
+    for f in PCG_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_18867_gb300", "csrc", f), "rb") as fh:
+            hs.update(fh.read())
+    if hs.hexdigest()[:16] != PCG_TRAFFIC_HASH:
         return None
     n = {"wrinkle512": 512 * 512, "wrinkle1024": 1024 * 1024}[workload]
     return PCG_TRAFFIC_PER_CP_ITER * n * iters

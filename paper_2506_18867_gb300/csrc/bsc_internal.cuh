@@ -432,6 +432,23 @@ __device__ __forceinline__ void block_jacobi_at(int N, int al, const T* __restri
   for (int k = 0; k < 9; ++k) Dinv[(size_t)k * N + al] = (T)b[k];
 }
 
+// Streaming load of a matrix entry: K is read once per product (an entry at
+// most twice, by its row and, transposed, by its neighbour's) and is far
+// larger than L1, so its lines do not allocate there and L1 keeps the
+// gathered vector entries, each read by up to 25 rows.  A cache hint only:
+// the value is that of a plain load.  (An L2 evict-first policy on top was
+// slower, measured.)
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
 // Row alpha (patch-local index) of y = K x in the element type T; K and x
 // already point at the patch's first control point, N is the plane stride.
 // X_MODE 1: x stays unchanged for the whole kernel, so it may go through the
@@ -467,13 +484,13 @@ __device__ __forceinline__ void spmv_row(int nu, int nv, int N, int al, const T*
       }
       const T* Kb = K + (size_t)slot * 9 * N + al;
       if (FUSED) {
-        y0 = fma(Kb[(size_t)2 * N], x2, fma(Kb[(size_t)N], x1, fma(Kb[0], x0, y0)));
-        y1 = fma(Kb[(size_t)5 * N], x2, fma(Kb[(size_t)4 * N], x1, fma(Kb[(size_t)3 * N], x0, y1)));
-        y2 = fma(Kb[(size_t)8 * N], x2, fma(Kb[(size_t)7 * N], x1, fma(Kb[(size_t)6 * N], x0, y2)));
+        y0 = fma(ld_stream(Kb + (size_t)2 * N), x2, fma(ld_stream(Kb + (size_t)N), x1, fma(ld_stream(Kb), x0, y0)));
+        y1 = fma(ld_stream(Kb + (size_t)5 * N), x2, fma(ld_stream(Kb + (size_t)4 * N), x1, fma(ld_stream(Kb + (size_t)3 * N), x0, y1)));
+        y2 = fma(ld_stream(Kb + (size_t)8 * N), x2, fma(ld_stream(Kb + (size_t)7 * N), x1, fma(ld_stream(Kb + (size_t)6 * N), x0, y2)));
       } else {
-        y0 += Kb[0] * x0 + Kb[(size_t)N] * x1 + Kb[(size_t)2 * N] * x2;
-        y1 += Kb[(size_t)3 * N] * x0 + Kb[(size_t)4 * N] * x1 + Kb[(size_t)5 * N] * x2;
-        y2 += Kb[(size_t)6 * N] * x0 + Kb[(size_t)7 * N] * x1 + Kb[(size_t)8 * N] * x2;
+        y0 += ld_stream(Kb) * x0 + ld_stream(Kb + (size_t)N) * x1 + ld_stream(Kb + (size_t)2 * N) * x2;
+        y1 += ld_stream(Kb + (size_t)3 * N) * x0 + ld_stream(Kb + (size_t)4 * N) * x1 + ld_stream(Kb + (size_t)5 * N) * x2;
+        y2 += ld_stream(Kb + (size_t)6 * N) * x0 + ld_stream(Kb + (size_t)7 * N) * x1 + ld_stream(Kb + (size_t)8 * N) * x2;
       }
     }
   }
@@ -512,13 +529,13 @@ __device__ __forceinline__ void spmv_row_sym(int nu, int nv, int N, int al, cons
       if (slot >= 12) {
         const T* Kb = K + (size_t)(slot - 12) * 9 * N + al;
 #pragma unroll
-        for (int e = 0; e < 9; ++e) k[e] = Kb[(size_t)e * N];
+        for (int e = 0; e < 9; ++e) k[e] = ld_stream(Kb + (size_t)e * N);
       } else {
         const T* Kb = K + (size_t)(12 - slot) * 9 * N + be;  // the neighbour's slot 24 - slot, transposed
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) k[3 * r + c] = Kb[(size_t)(3 * c + r) * N];
+          for (int c = 0; c < 3; ++c) k[3 * r + c] = ld_stream(Kb + (size_t)(3 * c + r) * N);
       }
       y0 = fma(k[2], x2, fma(k[1], x1, fma(k[0], x0, y0)));
       y1 = fma(k[5], x2, fma(k[4], x1, fma(k[3], x0, y1)));

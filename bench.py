@@ -171,7 +171,7 @@ def ldlt_flops(n):
     return f
 
 
-def projection_flops(nred, nneg, nm, nb, psd=False, open_frac=1.0, border_psd=False):
+def projection_flops(nred, nneg, nm, nb, psd=False, open_frac=1.0, border_psd=False, border_open_frac=1.0):
     """Algorithmic FP64 flops of the SPD projection of one span per Newton
     iteration as implemented: reduced Hessian formation from the reduced
     derivative vectors (the span's orthonormal basis and the vectors in it
@@ -189,7 +189,9 @@ def projection_flops(nred, nneg, nm, nb, psd=False, open_frac=1.0, border_psd=Fa
     certificate's own work is FP32 and not counted), and only the spans with
     a projected eigenvalue go on to the formation again and the
     eigendecomposition.  Border spans (n = 24) pay the FP64 test when it
-    is on (border_psd: every border path tests first)."""
+    is on (border_psd: every border path tests first) with probability
+    border_open_frac (the share the warp paths' FP32 certificate leaves
+    open; 1 without it)."""
     n = nred
     D = n // 3
     form = nm * 2 * (36 * D + 9 * D * (D + 1)) + nb * (2 * D * (D + 1))  # T_k and blocks per point
@@ -199,7 +201,7 @@ def projection_flops(nred, nneg, nm, nb, psd=False, open_frac=1.0, border_psd=Fa
         if not nneg:
             return f
     if border_psd and n == 24:
-        f += form + ldlt_flops(n)
+        f += border_open_frac * (form + ldlt_flops(n))
         if not nneg:
             return f
     f += form
@@ -365,9 +367,10 @@ def run_gpu(args):
     psd = bool(tuning.get("psd_test"))
     psd_counts = ctx.psd_counts()   # interior spans, FP64-tested, eigendecomposed
     open_frac = psd_counts[1] / max(psd_counts[0], 1)
+    border_open_frac = psd_counts[5] / max(psd_counts[3], 1)
     for s_ in range(Nsp):
         flops += projection_flops(int(nred[s_]), int(nneg[s_]), int(nm[s_]), int(nb[s_]), psd, open_frac,
-                                  psd)
+                                  psd, border_open_frac)
     achieved_tflops = flops / (proj_ms * 1e-3) / 1e12
 
     # e2e: the same Newton step through the C ABI from pinned host buffers
@@ -485,7 +488,8 @@ def run_gpu(args):
                                "k_proj_corr, k_project_ring: FP64)",
                      "psd_counts": {"interior_spans": psd_counts[0], "fp64_tested": psd_counts[1],
                                     "eigendecomposed": psd_counts[2], "border_spans": psd_counts[3],
-                                    "border_eigendecomposed": psd_counts[4], "mode": tuning.get("psd_test")},
+                                    "border_eigendecomposed": psd_counts[4], "border_fp64_tested": psd_counts[5],
+                                    "mode": tuning.get("psd_test")},
                      "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                      "traffic": projection_traffic(args.workload, prec == bsc.FP32, tuning),
@@ -745,7 +749,7 @@ def measure_drape(bsc, flush, stream, torch, np, steps, warmup):
             psd = bool(tuning.get("psd_test"))
             pc = ctx.psd_counts()
             fl = sum(projection_flops(int(nred[i]), int(nneg[i]), int(nm[i]), int(nb[i]), psd,
-                                      pc[1] / max(pc[0], 1), psd)
+                                      pc[1] / max(pc[0], 1), psd, pc[5] / max(pc[3], 1))
                      for i in range(pat.n_spans))
             pms = ph["project"] / k
             out[name]["projection"] = {"ms": pms, "algorithmic_flops": fl,

@@ -322,11 +322,14 @@ bsc_status bsc_set_p2_variant(bsc_ctx* ctx, int variant);
  * another mode. */
 bsc_status bsc_set_psd_test(bsc_ctx* ctx, int mode);
 
-/* Span counts of the last projection (host array of 5 ints): the interior
+/* Span counts of the last projection (host array of 6 ints): the interior
  * spans, those the FP64 PSD test ran on (all of them in mode 1, the
  * certificate's open ones in mode 2, none in mode 0), those that went on to
- * the eigendecomposition; the border spans, and those of them that went on
- * to the eigendecomposition (all of them with the PSD test off). */
+ * the eigendecomposition; the border spans, those of them that went on to
+ * the eigendecomposition (all of them with the PSD test off), and those the
+ * FP64 test ran on (in mode 2 on the warp border paths 0, 2 and 3 the ones
+ * the warp's FP32 certificate left open; all of them in mode 1 or on border
+ * path 1, read under the current border path; none in mode 0). */
 bsc_status bsc_psd_counts(bsc_ctx* ctx, int* out);
 
 /* Form of the persistent block-Jacobi PCG (the same iterates up to rounding):

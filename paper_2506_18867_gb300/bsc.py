@@ -512,8 +512,9 @@ class Context:
 
     def psd_counts(self):
         """(interior spans, interior spans the FP64 test ran on, interior spans eigendecomposed,
-        border spans, border spans eigendecomposed) of the last projection."""
-        out = (ct.c_int * 5)()
+        border spans, border spans eigendecomposed, border spans the FP64 test ran on) of the last
+        projection."""
+        out = (ct.c_int * 6)()
         self._check(self._lib.bsc_psd_counts(self._h, out))
         return tuple(out)
 

@@ -878,6 +878,8 @@ bsc_status bsc_psd_counts(bsc_ctx* c, int* out) {
   const bool border_test = c->proj_psd != 0;  // every border path tests first
   out[3] = h[1];
   out[4] = border_test ? h[4] : h[1];
+  // the warp paths certify in mode 2; the phase kernels' border test has no certificate
+  out[5] = c->proj_psd == 0 ? 0 : (c->proj_psd == 2 && c->border_path != 1 ? h[5] : h[1]);
   return BSC_OK;
 }
 

@@ -56,6 +56,10 @@ struct RingArgs {
   // over a list (sel != nullptr): the class positions sel[0 .. *sel_count)
   const int* sel;
   const int* sel_count;
+  // with the PSD test: an FP32 certificate first (ring_certify_f32); the
+  // spans it leaves to the FP64 test are counted in *open_count
+  int cert;
+  int* open_count;
 };
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -292,6 +296,136 @@ struct RingP1Out {
   int* kneg;    // [count]
 };
 
+// FP32 certificate of positive definiteness of a border span's H_r, one warp,
+// lane j forming column j of H_r in FP32 exactly as the FP64 formation below
+// does in FP64, then factoring H_r - sigma I.  The argument is the interior
+// class's (k_proj_pf), with n = 24 and this formation's rounding count:
+//  - every term of an entry (a product of two reduced derivative entries and
+//    one d^2 Psi / df^2 entry, or of W_b and two bending entries) meets at
+//    most 3 roundings of its inputs to FP32 (4 for W_b, a product formed in
+//    FP64), 2 in t (membrane) or in W_b L_k (bending), and one per
+//    accumulation into the entry, 2 n_mem + n_bd in all: m = 6 + 2 n_mem +
+//    n_bd roundings bound every term, so with the same S as the interior
+//    class, ||H_r - F||_2 <= gamma_m S for the computed F;
+//  - the factorisation reads only the entries on and below the diagonal of
+//    each lane's column (the pivot column k is taken from lane k): it is the
+//    LDL^T of the symmetric matrix F_L with that lower triangle, whose entries
+//    obey the same bound, and its rounding is that of the interior
+//    certificate (multipliers by a correctly rounded reciprocal and a
+//    product), ||E||_2 <= gamma_{n+4} tr(F_L) / (1 - gamma_{n+4}).
+// With sigma = 1.1 (gamma_{n+4} tr + gamma_m S), every pivot of F_L - sigma I
+// positive means every eigenvalue of H_r above a margin of order
+// 1e-6 tr(H_r): the FP64 test below (margin 1e-14 tr / n) would pass the
+// span as well, so taking the certificate changes no span's result.
+template <typename T>
+__device__ __forceinline__ bool ring_certify_f32(const RingArgs<T>& P, int q0, int q1, int b0, int b1, double mubd,
+                                                 int lane, int kp, int dp) {
+  constexpr float u = 5.9604644775390625e-8f;  // 2^-24
+  constexpr float g_n4 = (RN + 4) * u / (1.0f - (RN + 4) * u);
+  const int m = 6 + 2 * (q1 - q0) + (b1 - b0);
+  if (m > 4096) return false;
+  const float g_m = m * u / (1.0f - m * u);
+  float col[RN];
+#pragma unroll
+  for (int i = 0; i < RN; ++i) col[i] = 0.0f;
+  float S = 0.0f;
+  for (int q = q0; q < q1; ++q) {
+    float gt[8][2], g2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        gt[k][b] = (float)P.rg[(size_t)(2 * k + b) * P.Nm + q];
+        g2 = fmaf(gt[k][b], gt[k][b], g2);
+      }
+    float A6[6][6], a2 = 0.0f;
+    {
+      int e = 0;
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c) {
+          const float v = (float)P.A[(e++) * P.Nm + q];
+          A6[r][c] = v;
+          A6[c][r] = v;
+          a2 = fmaf(r == c ? v : 2.0f * v, v, a2);
+        }
+    }
+    S = fmaf(3.0f * g2, __fsqrt_ru(a2), S);
+    if (lane < RN) {
+      float gk0 = 0.0f, gk1 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k == kp) { gk0 = gt[k][0]; gk1 = gt[k][1]; }
+      float t[2][3];
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+          for (int z = 0; z < 3; ++z)
+            if (z == dp) { a0 = A6[3 * b + c][z]; a1 = A6[3 * b + c][3 + z]; }
+          t[b][c] = fmaf(gk1, a1, gk0 * a0);
+        }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          col[3 * k + c] = fmaf(gt[k][1], t[1][c], fmaf(gt[k][0], t[0][c], col[3 * k + c]));
+    }
+  }
+  for (int q = b0; q < b1; ++q) {
+    const float WB = (float)((double)P.tabb[q] * mubd);
+    float Lt[8], l2 = 0.0f, Lk = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      Lt[k] = (float)P.rl[(size_t)k * P.Nb + q];
+      l2 = fmaf(Lt[k], Lt[k], l2);
+      if (k == kp) Lk = Lt[k];
+    }
+    S = fmaf(3.0f * fabsf(WB), l2, S);
+    if (lane < RN) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (c == dp) col[3 * k + c] = fmaf(WB * Lt[k], Lk, col[3 * k + c]);
+    }
+  }
+  float dj = 0.0f;
+#pragma unroll
+  for (int i = 0; i < RN; ++i)
+    if (i == lane) dj = col[i];
+  float tr = lane < RN ? dj : 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  if (!(tr > 0.0f) || !isfinite(tr) || !isfinite(S)) return false;
+  const float sigma = 1.1f * (g_n4 * tr + g_m * S);
+#pragma unroll
+  for (int i = 0; i < RN; ++i)
+    if (i == lane) col[i] -= sigma;
+  bool pass = true;
+#pragma unroll
+  for (int k = 0; k < RN; ++k) {
+    float ck[RN], dk = 0.0f, cj = 0.0f;
+#pragma unroll
+    for (int i = k; i < RN; ++i) {
+      ck[i] = __shfl_sync(0xffffffffu, col[i], k);  // column k of the trailing matrix, from lane k
+      if (i == lane) cj = ck[i];
+    }
+    dk = ck[k];
+    pass = pass && dk > 0.0f && isfinite(dk);  // the same on every lane
+    if (!pass) break;
+    if (lane > k && lane < RN) {
+      const float l = cj * __frcp_rn(dk);
+#pragma unroll
+      for (int i = k + 1; i < RN; ++i) col[i] = fmaf(-l, ck[i], col[i]);
+    }
+  }
+  return pass;
+}
+
 // PSD: before the tridiagonalisation, the warp factors H_r + tau I (LDL^T in
 // FP64, tau = 1e-14 tr(H_r) / n, lane j updating column j from the pivot
 // column it receives by shuffles); a span whose pivots are all positive has
@@ -321,6 +455,18 @@ __global__ void __launch_bounds__(RBLOCK) k_project_ring(RingArgs<T> P, const in
     const int s = list[idx];
     const int q0 = P.moff[s], q1 = P.moff[s + 1], b0 = P.boff[s], b1 = P.boff[s + 1];
     const double mubd = P.pd[P.sp_patch[s]].mubd;
+
+    if (PSD && P.cert) {
+      if (ring_certify_f32<T>(P, q0, q1, b0, b1, mubd, lane, kp, dp)) {
+        if (lane == 0) {
+          P.nneg[s] = 0;
+          if (P1ONLY) out.kneg[idx] = 0;
+        }
+        __syncwarp();
+        continue;
+      }
+      if (lane == 0) atomicAdd(P.open_count, 1);
+    }
 
     // ---- column lane of H_r = sum_q (G~ (x) I3) A_q (G~ (x) I3)^T + bending
     double col[RN];
@@ -668,7 +814,8 @@ cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* 
   two_pass = two_pass && psd && !p1only;
   BSC_COUNT(c, two_pass ? 2 : 1);
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned int), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->proj_cnt + 4, 0, sizeof(int), st);
+  // proj_cnt[4]: border spans failing the FP64 test; [5]: those the certificate left to it
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->proj_cnt + 4, 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   const int need = (count + RBLOCK / 32 - 1) / (RBLOCK / 32);
   int g = ring_grid(c->num_sms);
@@ -685,12 +832,13 @@ cudaError_t launch_project_ring(bsc_ctx* c, int first, int count, unsigned int* 
       RingArgs<double> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off,
                          (const double*)c->tab_mem, (const double*)c->tab_bd, (const double*)c->A_mem,
                          (double*)c->H_span, c->nneg, c->dstatus, c->red_g, c->red_l, c->proj_cnt + 4, fail_list,
-                         sel, sel_count};
+                         sel, sel_count, c->proj_psd == 2, c->proj_cnt + 5};
       launch_ring_t<double>(P, list, count, work, out, g, st, p1only, psd);
     } else {
       RingArgs<float> P{c->Nsp, c->Nmem, c->Nbd, c->pd, c->sp_patch, c->mem_off, c->bd_off, (const float*)c->tab_mem,
                         (const float*)c->tab_bd, (const float*)c->A_mem, (float*)c->H_span, c->nneg, c->dstatus,
-                        c->red_g, c->red_l, c->proj_cnt + 4, fail_list, sel, sel_count};
+                        c->red_g, c->red_l, c->proj_cnt + 4, fail_list, sel, sel_count, c->proj_psd == 2,
+                        c->proj_cnt + 5};
       launch_ring_t<float>(P, list, count, work, out, g, st, p1only, psd);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -183,24 +183,33 @@ def test_psd_test_changes_nothing(case, orc):
 @pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["warp", "thread", "warp_items", "warp_two_pass"])
 def test_border_psd_test_changes_nothing(case, orc, path):
     """Every border path with the FP64 PSD test in front (the phase kernels'
-    thread-per-span test on path 1, the warp's own LDL^T on paths 0 and 2):
-    the projected span Hessians agree with the path without it to 1e-13 and
-    with the oracle's Jacobi projection to 1e-12."""
+    thread-per-span test on path 1, the warp's own LDL^T on paths 0, 2 and
+    3): the projected span Hessians agree with the path without it to 1e-13
+    and with the oracle's Jacobi projection to 1e-12.  The warp paths' FP32
+    certificate in front of the test (mode 2) changes nothing, bit for bit,
+    and leaves at least the failing spans to the FP64 test."""
     pat, prob, ctx = case
     C = ctx.to_device(pat.C)
-    out = {}
+    out, raw, cnt = {}, {}, {}
     try:
         ctx.set_border_path(path)
-        for mode in (0, 1):
+        for mode in (0, 1, 2):
             ctx.set_psd_test(mode)
-            out[mode] = ctx.span_terms(C, project=True)[2].double().cpu().numpy()
+            raw[mode] = ctx.span_terms(C, project=True)[2]
+            out[mode] = raw[mode].double().cpu().numpy()
+            cnt[mode] = ctx.psd_counts()
     finally:
         ctx.set_psd_test(2)
         ctx.set_border_path(0)
     _, _, oH = prob.span_eval_projected(pat.C, True)
     print(f"{pat.name}: border path {path} with / without the test {rel(out[1], out[0]):.1e}, vs oracle "
-          f"{rel(out[1], oH):.1e}")
+          f"{rel(out[1], oH):.1e}; border spans {cnt[2][3]}, FP64-tested after the certificate {cnt[2][5]}, "
+          f"eigendecomposed {cnt[2][4]}")
     assert rel(out[1], out[0]) < 1e-13 and rel(out[1], oH) < 1e-12
+    assert torch.equal(raw[1], raw[2])
+    assert cnt[1][5] == cnt[1][3] and cnt[1][4] == cnt[2][4] and cnt[2][4] <= cnt[2][5] <= cnt[2][3]
+    if path == 1:
+        assert cnt[2][5] == cnt[2][3]
 
 
 @pytest.mark.parametrize("form", [1, 2], ids=["pipelined", "two_pass"])

@@ -71,7 +71,8 @@ void free_ctx(bsc_ctx* c) {
                   c->Dinv, c->partials, c->sync, c->dstatus, c->dscalars, c->pd, c->cp_patch, c->sp_patch,
                   c->span_items, c->red_items, c->red_off, c->pcg_blocks, c->pcg_out, c->steps, c->patch_E,
                   c->pending, c->proj_work, c->proj_span[0], c->proj_span[1], c->proj_kneg[0], c->proj_kneg[1],
-                  c->red_g, c->red_l, c->red_q, c->fcg_rec, c->proj_cnt, c->proj_sel, c->proj_pre, c->proj_sel1};
+                  c->red_g, c->red_l, c->red_q, c->fcg_rec, c->proj_cnt, c->proj_sel, c->proj_pre, c->proj_sel1,
+                  c->red_g2, c->red_l2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->vec)

@@ -118,6 +118,8 @@ struct bsc_ctx {
   // reduced bases of the projection (rest geometry only, computed at create)
   double* red_g;      // [16][Nmem] g_q,beta of each membrane point in its span's reduced basis
   double* red_l;      // [8][Nbd] L_q of each bending point in its span's reduced basis
+  float2* red_g2;     // FP32 contexts: red_g as double-float splits (hi, lo)
+  float2* red_l2;     // FP32 contexts: red_l as double-float splits
   double* red_q;      // [45][n interior] orthonormal basis of each interior span (class order)
   double* helmert;    // device [72]: the border spans' basis (Helmert contrasts)
   // two span classes: 0 interior (reduced size 15), 1 at or next to the border (24)

@@ -30,6 +30,8 @@
 // in the class scratch.  The border spans run concurrently on a forked
 // stream (k_project_ring, or the phase kernels with D = 8).
 #include "bsc_internal.cuh"
+#include <type_traits>
+
 #include "proj_core.cuh"
 
 cudaError_t setup_projection_ring();
@@ -56,6 +58,10 @@ struct ProjArgs {
   const double* __restrict__ rl;  // [8][Nb] bending vectors in the span's reduced basis
   const double* __restrict__ rq;  // the class's bases: [9 D][count] per span, or one 9 x 8 basis
   int rq_per_span;                // 1: rq holds a basis per span (class order)
+  // FP32 contexts: rg and rl as double-float splits (hi, lo), for the
+  // double-float formation of the PSD test
+  const float2* __restrict__ rg2;
+  const float2* __restrict__ rl2;
 };
 
 // Eigenvalues below -NEG_REL * ||T|| are projected; above that they are
@@ -82,6 +88,28 @@ struct SpanTab {
   __device__ double a6(int q, int e) const { return (double)A[e * Nm + q]; }
   __device__ double gr(int q, int k, int be) const { return rg[(size_t)(2 * k + be) * Nm + q]; }
   __device__ double lr(int q, int k) const { return rl[(size_t)k * Nb + q]; }
+};
+
+// SpanTab with the double-float inputs of span_form_df (FP32 tables).
+struct SpanTabDF {
+  const float* tabb;   // offset to the span's first bending point
+  const float* A;      // offset to the span's first membrane point
+  const float2* rg2;   // offset like A
+  const float2* rl2;   // offset like tabb
+  int Nm, Nb, nmq, nbq;
+  proj::DF mu;         // the patch's bending modulus as a double-float
+  __device__ int nm() const { return nmq; }
+  __device__ int nb() const { return nbq; }
+  __device__ float a6f(int q, int e) const { return A[e * Nm + q]; }
+  __device__ proj::DF gr2(int q, int k, int be) const {
+    const float2 v = rg2[(size_t)(2 * k + be) * Nm + q];
+    return {v.x, v.y};
+  }
+  __device__ proj::DF lr2(int q, int k) const {
+    const float2 v = rl2[(size_t)k * Nb + q];
+    return {v.x, v.y};
+  }
+  __device__ proj::DF wb2(int q) const { return proj::df_mul_f(mu, tabb[q]); }
 };
 
 // Helmert contrasts q_k = (1, ..., 1, -k, 0, ...) / sqrt(k (k + 1)) (k ones),
@@ -406,10 +434,18 @@ __global__ void __launch_bounds__(P0Block<D>::value, 1)
       t = pre ? pre[i] : i;
       const int s = list[t];
       const int q0 = P.moff[s], b0 = P.boff[s];
-      SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
-                     P.boff[s + 1] - b0, P.pd[P.sp_patch[s]].mubd};
-      proj::span_form<D>(tab, A);
-      fail = proj::ldlt_psd<D>(A, NEG_REL) ? 0 : 1;
+      if constexpr (std::is_same<T, float>::value) {
+        // FP32 tables: formation and test in double-float on the FP32 pipe
+        const SpanTabDF tab{P.tabb + b0, P.A + q0, P.rg2 + q0, P.rl2 + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
+                            P.boff[s + 1] - b0, proj::df_split(P.pd[P.sp_patch[s]].mubd)};
+        proj::span_form_df<D>(tab, A);
+        fail = proj::ldlt_psd_df<D>(A, NEG_REL) ? 0 : 1;
+      } else {
+        SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
+                       P.boff[s + 1] - b0, P.pd[P.sp_patch[s]].mubd};
+        proj::span_form<D>(tab, A);
+        fail = proj::ldlt_psd<D>(A, NEG_REL) ? 0 : 1;
+      }
       if (!fail) P.nneg[s] = 0;
     }
     block_prefix<B0>(fail, s_pre, s_wsum);
@@ -545,6 +581,7 @@ ProjArgs<T> proj_args(bsc_ctx* c, int k) {
   P.A = (const T*)c->A_mem; P.H = (T*)c->H_span;
   P.nneg = c->nneg; P.status = c->dstatus;
   P.rg = c->red_g; P.rl = c->red_l;
+  P.rg2 = c->red_g2; P.rl2 = c->red_l2;
   P.rq = k == 0 ? c->red_q : c->helmert;
   P.rq_per_span = k == 0 ? 1 : 0;
   return P;
@@ -556,7 +593,8 @@ ProjArgs<T> proj_args(bsc_ctx* c, int k) {
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_reduce_points(ProjArgs<T> P, const int* __restrict__ list, int n0, int count, double* __restrict__ rq,
-                    double* __restrict__ rg, double* __restrict__ rl) {
+                    double* __restrict__ rg, double* __restrict__ rl, float2* __restrict__ rg2,
+                    float2* __restrict__ rl2) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
     const int s = list[t];
     const int q0 = P.moff[s], b0 = P.boff[s];
@@ -581,6 +619,11 @@ __global__ void __launch_bounds__(128)
         }
         rg[(size_t)(2 * k) * P.Nm + q0 + q] = a0;
         rg[(size_t)(2 * k + 1) * P.Nm + q0 + q] = a1;
+        if (rg2) {
+          const proj::DF s0 = proj::df_split(a0), s1 = proj::df_split(a1);
+          rg2[(size_t)(2 * k) * P.Nm + q0 + q] = make_float2(s0.h, s0.l);
+          rg2[(size_t)(2 * k + 1) * P.Nm + q0 + q] = make_float2(s1.h, s1.l);
+        }
       }
     for (int q = 0; q < tab.nb(); ++q)
       for (int k = 0; k < D; ++k) {
@@ -588,6 +631,10 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int l = 0; l < 9; ++l) a += Q[9 * k + l] * tab.L(q, l);
         rl[(size_t)k * P.Nb + b0 + q] = a;
+        if (rl2) {
+          const proj::DF sa = proj::df_split(a);
+          rl2[(size_t)k * P.Nb + b0 + q] = make_float2(sa.h, sa.l);
+        }
       }
   }
 }
@@ -598,7 +645,8 @@ cudaError_t reduce_points(bsc_ctx* c) {
   if (count <= 0) return cudaSuccess;
   BSC_COUNT(c, 1);
   k_reduce_points<T><<<(count + 127) / 128, 128, 0, c->stream>>>(proj_args<T>(c, 0), c->bucket_list, n0, count,
-                                                                  c->red_q, c->red_g, c->red_l);
+                                                                  c->red_q, c->red_g, c->red_l, c->red_g2,
+                                                                  c->red_l2);
   return cudaGetLastError();
 }
 
@@ -837,6 +885,11 @@ cudaError_t setup_projection(bsc_ctx* c) {
   if ((e = cudaMalloc(&c->red_g, sizeof(double) * 16 * (size_t)(c->Nmem > 0 ? c->Nmem : 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->red_l, sizeof(double) * 8 * (size_t)(c->Nbd > 0 ? c->Nbd : 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->red_q, sizeof(double) * 45 * (size_t)(n0 > 0 ? n0 : 1))) != cudaSuccess) return e;
+  if (c->precision != BSC_FP64) {
+    if ((e = cudaMalloc(&c->red_g2, sizeof(float2) * 16 * (size_t)(c->Nmem > 0 ? c->Nmem : 1))) != cudaSuccess)
+      return e;
+    if ((e = cudaMalloc(&c->red_l2, sizeof(float2) * 8 * (size_t)(c->Nbd > 0 ? c->Nbd : 1))) != cudaSuccess) return e;
+  }
   if (c->precision == BSC_FP64) {
     if ((e = setup_class<double, 5>(c, 0, n0)) != cudaSuccess) return e;
     if ((e = setup_class<double, 8>(c, 1, n1)) != cudaSuccess) return e;

@@ -396,6 +396,172 @@ BSC_PHASE bool ldlt_psd(const View& A, double neg_rel) {
   return true;
 }
 
+#ifdef __CUDACC__
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi) / 2 once normalised), about 48 significant bits.
+// GB300 retires 64 times as many FP32 as FP64 operations per clock, so the
+// ~15 FP32 operations of a double-float multiply-add cost a quarter of the
+// FP64 instruction they replace.  The error-free transformations are Knuth's
+// two-sum, Dekker's fast two-sum (|a| >= |b|) and the FMA two-product; every
+// operation is an explicitly rounded intrinsic, so no contraction or
+// reassociation can change them.
+// ---------------------------------------------------------------------------
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// x * a with a in FP32 (exact product of the high parts plus the low part's)
+__device__ __forceinline__ DF df_mul_f(DF x, float a) {
+  const float p = __fmul_rn(x.h, a);
+  return {p, __fmaf_rn(x.l, a, __fmaf_rn(x.h, a, -p))};
+}
+// x * y (the lo * lo term, below 2^-48 of the product, is dropped)
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.h, y.h);
+  return {p, __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, __fmaf_rn(x.h, y.h, -p)))};
+}
+// x + y for unnormalised x, y, normalised result
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const DF s = df_two_sum(x.h, y.h);
+  return df_fast_two_sum(s.h, __fadd_rn(__fadd_rn(x.l, y.l), s.l));
+}
+__device__ __forceinline__ DF df_norm(DF x) { return df_fast_two_sum(x.h, x.l); }
+__device__ __forceinline__ DF df_neg(DF x) { return {-x.h, -x.l}; }
+// 1 / x by one Newton step from the FP32 reciprocal
+__device__ __forceinline__ DF df_rcp(DF x) {
+  const float r = __frcp_rn(x.h);
+  const float p = __fmul_rn(x.h, r);
+  const float e = __fmaf_rn(-x.l, r, __fsub_rn(__fsub_rn(1.0f, p), __fmaf_rn(x.h, r, -p)));  // 1 - x r
+  return df_fast_two_sum(r, __fmul_rn(r, e));
+}
+__device__ __forceinline__ DF df_split(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+// a slot of a double View holds a double-float during the double-float phases
+__device__ __forceinline__ DF& df_at(const View& A, int i) { return *reinterpret_cast<DF*>(&A[i]); }
+
+// span_form in double-float arithmetic, for tables in FP32 (a6, wb's FP32
+// factor exact) with the reduced vectors as double-float splits (gr2, lr2,
+// and the bending weight's FP64 factor as mu2): each entry's accumulation
+// carries about 2^-47 of the sum of its terms' magnitudes, some 30 times the
+// FP64 formation's rounding and far below the PSD test's threshold.  A
+// holds the double-float entries (df_at) on return.
+template <int D, class Tab>
+__device__ __noinline__ void span_form_df(const Tab& tab, const View& A) {
+  constexpr int n = 3 * D;
+  constexpr int NP = n * (n + 1) / 2;
+#pragma unroll 1
+  for (int k = 0; k < NP; ++k) df_at(A, k) = DF{0.0f, 0.0f};
+  const int nm = tab.nm(), nb = tab.nb();
+  for (int q = 0; q < nm; ++q) {
+    DF g[D][2];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      g[k][0] = tab.gr2(q, k, 0);
+      g[k][1] = tab.gr2(q, k, 1);
+    }
+    float A6[6][6];
+    {
+      int e = 0;
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c) {
+          A6[r][c] = tab.a6f(q, e++);
+          A6[c][r] = A6[r][c];
+        }
+    }
+#pragma unroll 1
+    for (int k = 0; k < D; ++k) {
+      DF gk0 = g[0][0], gk1 = g[0][1];
+#pragma unroll
+      for (int z = 1; z < D; ++z)
+        if (z == k) { gk0 = g[z][0]; gk1 = g[z][1]; }
+      DF Tk[3][6];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) Tk[c][j] = df_add(df_mul_f(gk0, A6[c][j]), df_mul_f(gk1, A6[3 + c][j]));
+#pragma unroll
+      for (int k2 = 0; k2 < D; ++k2) {
+        if (k2 > k) break;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int dd = 0; dd < 3; ++dd) {
+            if (k2 == k && dd > c) continue;
+            DF& a = df_at(A, lp(3 * k + c, 3 * k2 + dd));
+            const DF t = df_add(df_mul(Tk[c][dd], g[k2][0]), df_mul(Tk[c][3 + dd], g[k2][1]));
+            a = df_add(a, t);
+          }
+      }
+    }
+  }
+  for (int q = 0; q < nb; ++q) {
+    const DF WB = tab.wb2(q);
+    DF Lr[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) Lr[k] = tab.lr2(q, k);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const DF wl = df_norm(df_mul(WB, Lr[k]));
+#pragma unroll
+      for (int k2 = 0; k2 <= k; ++k2)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          DF& a = df_at(A, lp(3 * k + c, 3 * k2 + c));
+          a = df_add(a, df_mul(wl, Lr[k2]));
+        }
+    }
+  }
+}
+
+// ldlt_psd in double-float on the double-float H_r that span_form_df left in
+// A: the same test (H_r + tau I positive definite, tau = neg_rel tr / n), its
+// backward error about n 2^-46 tr(H_r) instead of n 2^-53 tr(H_r) - both far
+// inside the projection's accuracy.  Destroys A.
+template <int D>
+__device__ __noinline__ bool ldlt_psd_df(const View& A, double neg_rel) {
+  constexpr int n = 3 * D;
+  DF tr{0.0f, 0.0f};
+#pragma unroll
+  for (int i = 0; i < n; ++i) tr = df_add(tr, df_at(A, lp(i, i)));
+  if (!(tr.h > 0.0f) || !isfinite(tr.h)) return false;
+  const float tau = (float)(neg_rel / n) * tr.h;
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    DF& a = df_at(A, lp(i, i));
+    a = df_add(a, DF{tau, 0.0f});
+  }
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    const DF dk = df_at(A, lp(k, k));
+    if (!(dk.h > 0.0f) || !isfinite(dk.h)) return false;
+    const DF r = df_rcp(dk);
+#pragma unroll 1
+    for (int i = k + 1; i < n; ++i) {
+      const int ri = i * (i + 1) / 2;
+      const DF l = df_neg(df_norm(df_mul(df_at(A, ri + k), r)));
+#pragma unroll 1
+      for (int j = k + 1; j <= i; ++j) {
+        DF& a = df_at(A, ri + j);
+        a = df_add(a, df_mul(l, df_at(A, j * (j + 1) / 2 + k)));
+      }
+    }
+  }
+  return true;
+}
+#endif  // __CUDACC__
+
 // Phase 1 of a span: reduced Hessian (span_form), then span_tridiag.
 template <int D, class Tab>
 BSC_PHASE int span_phase1(const Tab& tab, const View& A, const View& R, double* tn_out, double neg_rel);

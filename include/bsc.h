@@ -322,6 +322,17 @@ bsc_status bsc_set_p2_variant(bsc_ctx* ctx, int variant);
  * another mode. */
 bsc_status bsc_set_psd_test(bsc_ctx* ctx, int mode);
 
+/* Arithmetic of the projection's PSD test and of its phase 1 (formation of
+ * the reduced Hessian, Householder tridiagonal form) on the thread-per-span
+ * kernels: 0 FP64; 1 double-float, pairs of FP32 numbers with about 48
+ * significant bits, which GB300's FP32 pipe runs several times faster than
+ * its FP64 pipe runs FP64 (backward errors about 2^-47 ||H_r|| instead of
+ * 2^-53, so eigenvalues are projected below -1e-12 ||T|| instead of -1e-14;
+ * the eigenpair phase stays FP64).  Default: 1 in FP32 contexts, 0 in
+ * FP64 contexts (Sec. 5.1 projection, unchanged up to rounding).  Errors:
+ * BSC_ERR_INVALID_ARG for another mode. */
+bsc_status bsc_set_proj_arith(bsc_ctx* ctx, int mode);
+
 /* Span counts of the last projection (host array of 6 ints): the interior
  * spans, those the FP64 PSD test ran on (all of them in mode 1, the
  * certificate's open ones in mode 2, none in mode 0), those that went on to

@@ -46,7 +46,7 @@ EXPORTS = ("bsc_create", "bsc_destroy", "bsc_last_error", "bsc_set_stream", "bsc
            "bsc_cnn_create", "bsc_cnn_destroy", "bsc_cnn_set_params", "bsc_cnn_get_params", "bsc_cnn_prepare",
            "bsc_cnn_apply", "bsc_cnn_loss_grad", "bsc_cnn_adam_step", "bsc_cnn_activations", "bsc_solve_fcg",
            "bsc_set_learned_solver", "bsc_cnn_set_stall_window", "bsc_set_wait_limit", "bsc_set_pcg_form",
-           "bsc_set_psd_test", "bsc_contact_attach", "bsc_contact_detach", "bsc_contact_vertices",
+           "bsc_set_psd_test", "bsc_set_proj_arith", "bsc_contact_attach", "bsc_contact_detach", "bsc_contact_vertices",
            "bsc_contact_step_bound", "bsc_contact_stats", "bsc_create_window", "bsc_window_energy_rows",
            "bsc_window_pcg_begin", "bsc_window_pcg_product", "bsc_window_pcg_update", "bsc_window_pcg_direction",
            "bsc_axpy", "bsc_set_k_storage", "bsc_psd_counts")
@@ -188,6 +188,7 @@ def load(path: str = LIB_PATH):
     lib.bsc_set_wait_limit.argtypes = [P, ct.c_longlong, I]
     lib.bsc_set_pcg_form.argtypes = [P, I]
     lib.bsc_set_psd_test.argtypes = [P, I]
+    lib.bsc_set_proj_arith.argtypes = [P, I]
     lib.bsc_contact_attach.argtypes = [P, ct.POINTER(D), I, ct.POINTER(ct.c_int32), I, I, I, D, D]
     lib.bsc_contact_detach.argtypes = [P]
     lib.bsc_contact_vertices.argtypes = [P, V, ct.POINTER(D), I, ct.POINTER(I)]
@@ -509,6 +510,11 @@ class Context:
         """PSD test before the interior spans' eigendecomposition: 0 / False
         none, 1 / True the FP64 LDL^T test, 2 the FP32 certificate first."""
         self._check(self._lib.bsc_set_psd_test(self._h, int(mode)))
+
+    def set_proj_arith(self, mode):
+        """Arithmetic of the projection's PSD test and phase 1: 0 FP64, 1 double-float
+        (pairs of FP32 numbers; the default of FP32 contexts)."""
+        self._check(self._lib.bsc_set_proj_arith(self._h, int(mode)))
 
     def psd_counts(self):
         """(interior spans, interior spans the FP64 test ran on, interior spans eigendecomposed,

@@ -868,6 +868,15 @@ bsc_status bsc_set_psd_test(bsc_ctx* c, int mode) {
   return BSC_OK;
 }
 
+bsc_status bsc_set_proj_arith(bsc_ctx* c, int mode) {
+  if (!c) return BSC_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 1) return fail(c, BSC_ERR_INVALID_ARG, "bsc_set_proj_arith: mode must be 0 or 1");
+  CK(cudaStreamSynchronize(c->gstream), "bsc_set_proj_arith");
+  c->proj_df = mode;
+  drop_graph(c);
+  return BSC_OK;
+}
+
 bsc_status bsc_psd_counts(bsc_ctx* c, int* out) {
   if (!c || !out) return BSC_ERR_INVALID_ARG;
   int h[6] = {0, 0, 0, 0, 0, 0};

@@ -133,6 +133,7 @@ struct bsc_ctx {
   int* proj_cnt;            // device [6]: class sizes (interior, border); interior spans failing the PSD
                             // test, left open by the certificate; border spans failing the test
   int* proj_sel;            // device [interior spans]: class positions of the spans failing the PSD test
+  int proj_df;              // PSD test and phase 1 in double-float (1) or FP64 (0)
   int proj_psd;             // interior class: 0 no PSD test, 1 the FP64 LDL^T test first, 2 an FP32
                             // certificate of positive definiteness, then the FP64 test on the rest (autotuned)
   int* proj_pre;            // device [interior spans]: class positions the FP32 certificate left open

@@ -62,11 +62,18 @@ struct ProjArgs {
   // double-float formation of the PSD test
   const float2* __restrict__ rg2;
   const float2* __restrict__ rl2;
+  int df;  // p0 and p1 in double-float (bsc_set_proj_arith)
 };
 
 // Eigenvalues below -NEG_REL * ||T|| are projected; above that they are
 // rounding noise of exact zeros (their contribution is below 1e-14 ||H||).
 constexpr double NEG_REL = 1e-14;
+// The same threshold after the double-float phase 1: its rounding leaves the
+// exact zero eigenvalues of a rank-deficient span (border spans in the
+// Helmert basis) at up to some 1e-13 ||T||, so eigenvalues are counted below
+// -1e-12 ||T|| there; the few between -1e-12 and -1e-14 ||T|| stay (their
+// clamping would change the span by less than 1e-12 ||H||).
+constexpr double NEG_REL_DF = 1e-12;
 // A basis candidate whose residual after orthogonalisation is below
 // RANK_REL of its norm lies in the span of the previous ones.
 constexpr double RANK_REL = 1e-13;
@@ -90,17 +97,25 @@ struct SpanTab {
   __device__ double lr(int q, int k) const { return rl[(size_t)k * Nb + q]; }
 };
 
-// SpanTab with the double-float inputs of span_form_df (FP32 tables).
+// SpanTab with the double-float inputs of span_form_df: the reduced vectors
+// as double-float splits; the tables' FP32 entries (FP32 contexts) are exact,
+// FP64 ones (FP64 contexts) are split as they are read.
+template <typename T>
 struct SpanTabDF {
-  const float* tabb;   // offset to the span's first bending point
-  const float* A;      // offset to the span's first membrane point
+  static constexpr bool kFloatA6 = std::is_same<T, float>::value;
+  const T* tabb;       // offset to the span's first bending point
+  const T* A;          // offset to the span's first membrane point
   const float2* rg2;   // offset like A
   const float2* rl2;   // offset like tabb
   int Nm, Nb, nmq, nbq;
-  proj::DF mu;         // the patch's bending modulus as a double-float
+  double mubd;         // the patch's bending modulus
+  proj::DF mu;         // and as a double-float
   __device__ int nm() const { return nmq; }
   __device__ int nb() const { return nbq; }
-  __device__ float a6f(int q, int e) const { return A[e * Nm + q]; }
+  __device__ proj::DF a6(int q, int e) const {
+    if constexpr (kFloatA6) return {(float)A[e * Nm + q], 0.0f};
+    else return proj::df_split((double)A[e * Nm + q]);
+  }
   __device__ proj::DF gr2(int q, int k, int be) const {
     const float2 v = rg2[(size_t)(2 * k + be) * Nm + q];
     return {v.x, v.y};
@@ -109,8 +124,18 @@ struct SpanTabDF {
     const float2 v = rl2[(size_t)k * Nb + q];
     return {v.x, v.y};
   }
-  __device__ proj::DF wb2(int q) const { return proj::df_mul_f(mu, tabb[q]); }
+  __device__ proj::DF wb2(int q) const {
+    if constexpr (kFloatA6) return proj::df_mul_f(mu, (float)tabb[q]);
+    else return proj::df_split((double)tabb[q] * mubd);
+  }
 };
+template <typename T>
+__device__ __forceinline__ SpanTabDF<T> span_tab_df(const ProjArgs<T>& P, int s) {
+  const int q0 = P.moff[s], b0 = P.boff[s];
+  const double mubd = P.pd[P.sp_patch[s]].mubd;
+  return SpanTabDF<T>{P.tabb + b0, P.A + q0, P.rg2 + q0, P.rl2 + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
+                      P.boff[s + 1] - b0, mubd, proj::df_split(mubd)};
+}
 
 // Helmert contrasts q_k = (1, ..., 1, -k, 0, ...) / sqrt(k (k + 1)) (k ones),
 // k = 1..8: an orthonormal basis of the vectors of R^9 that sum to zero, the
@@ -226,10 +251,16 @@ __global__ void __launch_bounds__(P1Block<D>::value, 1)
   for (int t = blockIdx.x * B1 + threadIdx.x; t < count; t += gridDim.x * B1) {
     const int s = list[sel ? sel[t] : t];
     const int q0 = P.moff[s], b0 = P.boff[s];
-    SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
-                   P.boff[s + 1] - b0, P.pd[P.sp_patch[s]].mubd};
     double tn = 0.0;
-    int kneg = proj::span_phase1<D>(tab, A, R, &tn, NEG_REL);
+    int kneg;
+    if (P.df) {
+      // formation and tridiagonal form in double-float on the FP32 pipe
+      kneg = proj::span_phase1_df<D>(span_tab_df<T>(P, s), A, R, &tn, NEG_REL_DF);
+    } else {
+      SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
+                     P.boff[s + 1] - b0, P.pd[P.sp_patch[s]].mubd};
+      kneg = proj::span_phase1<D>(tab, A, R, &tn, NEG_REL);
+    }
     if (kneg < 0) {
       atomicOr(P.status, BSC_STATUS_NUMERIC_FLAG);
       kneg = 0;
@@ -434,13 +465,12 @@ __global__ void __launch_bounds__(P0Block<D>::value, 1)
       t = pre ? pre[i] : i;
       const int s = list[t];
       const int q0 = P.moff[s], b0 = P.boff[s];
-      if constexpr (std::is_same<T, float>::value) {
-        // FP32 tables: formation and test in double-float on the FP32 pipe
-        const SpanTabDF tab{P.tabb + b0, P.A + q0, P.rg2 + q0, P.rl2 + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
-                            P.boff[s + 1] - b0, proj::df_split(P.pd[P.sp_patch[s]].mubd)};
-        proj::span_form_df<D>(tab, A);
+      if (P.df) {
+        // formation and test in double-float on the FP32 pipe
+        proj::span_form_df<D>(span_tab_df<T>(P, s), A);
         fail = proj::ldlt_psd_df<D>(A, NEG_REL) ? 0 : 1;
       } else {
+        const int q0 = P.moff[s], b0 = P.boff[s];
         SpanTab<T> tab{P.tabm + q0, P.tabb + b0, P.A + q0, P.rg + q0, P.rl + b0, P.Nm, P.Nb, P.moff[s + 1] - q0,
                        P.boff[s + 1] - b0, P.pd[P.sp_patch[s]].mubd};
         proj::span_form<D>(tab, A);
@@ -582,6 +612,7 @@ ProjArgs<T> proj_args(bsc_ctx* c, int k) {
   P.nneg = c->nneg; P.status = c->dstatus;
   P.rg = c->red_g; P.rl = c->red_l;
   P.rg2 = c->red_g2; P.rl2 = c->red_l2;
+  P.df = c->proj_df;
   P.rq = k == 0 ? c->red_q : c->helmert;
   P.rq_per_span = k == 0 ? 1 : 0;
   return P;
@@ -885,7 +916,7 @@ cudaError_t setup_projection(bsc_ctx* c) {
   if ((e = cudaMalloc(&c->red_g, sizeof(double) * 16 * (size_t)(c->Nmem > 0 ? c->Nmem : 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->red_l, sizeof(double) * 8 * (size_t)(c->Nbd > 0 ? c->Nbd : 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->red_q, sizeof(double) * 45 * (size_t)(n0 > 0 ? n0 : 1))) != cudaSuccess) return e;
-  if (c->precision != BSC_FP64) {
+  {
     if ((e = cudaMalloc(&c->red_g2, sizeof(float2) * 16 * (size_t)(c->Nmem > 0 ? c->Nmem : 1))) != cudaSuccess)
       return e;
     if ((e = cudaMalloc(&c->red_l2, sizeof(float2) * 8 * (size_t)(c->Nbd > 0 ? c->Nbd : 1))) != cudaSuccess) return e;
@@ -913,6 +944,8 @@ cudaError_t setup_projection(bsc_ctx* c) {
     if ((e = cudaMemcpy(c->proj_cnt, h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   }
   c->proj_psd = 2;
+  // FP32 contexts: the projection's FP64-level work on the FP32 pipe (double-float)
+  c->proj_df = c->precision == BSC_FP64 ? 0 : 1;
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
     if ((e = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming)) != cudaSuccess) return e;

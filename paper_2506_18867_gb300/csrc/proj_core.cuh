@@ -449,9 +449,30 @@ __device__ __forceinline__ DF df_split(double v) {
 // a slot of a double View holds a double-float during the double-float phases
 __device__ __forceinline__ DF& df_at(const View& A, int i) { return *reinterpret_cast<DF*>(&A[i]); }
 
-// span_form in double-float arithmetic, for tables in FP32 (a6, wb's FP32
-// factor exact) with the reduced vectors as double-float splits (gr2, lr2,
-// and the bending weight's FP64 factor as mu2): each entry's accumulation
+// Scales the NP double-float entries of A by the power of two that brings the
+// largest to [1, 2) (exact; FP32's exponent range is that of the scaled
+// problem, so squares and reciprocals of small entries stay normal) and
+// returns the inverse scale (1 for a zero matrix).
+template <int NP>
+__device__ __forceinline__ float df_scale_unit(const View& A) {
+  float mx = 0.0f;
+#pragma unroll 1
+  for (int e = 0; e < NP; ++e) mx = fmaxf(mx, fabsf(df_at(A, e).h));
+  if (!(mx > 0.0f) || !isfinite(mx)) return 1.0f;
+  const int ex = ilogbf(mx);
+  const float sc = ldexpf(1.0f, -ex);
+#pragma unroll 1
+  for (int e = 0; e < NP; ++e) {
+    DF& a = df_at(A, e);
+    a = DF{__fmul_rn(a.h, sc), __fmul_rn(a.l, sc)};
+  }
+  return ldexpf(1.0f, ex);
+}
+
+
+// span_form in double-float arithmetic: Tab gives the reduced vectors as
+// double-float splits (gr2, lr2), d^2 Psi / df^2 (a6, exact floats when
+// Tab::kFloatA6) and the bending weights (wb2) as double-floats; each entry's accumulation
 // carries about 2^-47 of the sum of its terms' magnitudes, some 30 times the
 // FP64 formation's rounding and far below the PSD test's threshold.  A
 // holds the double-float entries (df_at) on return.
@@ -469,14 +490,14 @@ __device__ __noinline__ void span_form_df(const Tab& tab, const View& A) {
       g[k][0] = tab.gr2(q, k, 0);
       g[k][1] = tab.gr2(q, k, 1);
     }
-    float A6[6][6];
+    DF A6[6][6];
     {
       int e = 0;
 #pragma unroll
       for (int r = 0; r < 6; ++r)
 #pragma unroll
         for (int c = r; c < 6; ++c) {
-          A6[r][c] = tab.a6f(q, e++);
+          A6[r][c] = tab.a6(q, e++);
           A6[c][r] = A6[r][c];
         }
     }
@@ -490,7 +511,12 @@ __device__ __noinline__ void span_form_df(const Tab& tab, const View& A) {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int j = 0; j < 6; ++j) Tk[c][j] = df_add(df_mul_f(gk0, A6[c][j]), df_mul_f(gk1, A6[3 + c][j]));
+        for (int j = 0; j < 6; ++j) {
+          if constexpr (Tab::kFloatA6)  // FP32 tables: the entries are exact floats
+            Tk[c][j] = df_add(df_mul_f(gk0, A6[c][j].h), df_mul_f(gk1, A6[3 + c][j].h));
+          else
+            Tk[c][j] = df_add(df_mul(gk0, A6[c][j]), df_mul(gk1, A6[3 + c][j]));
+        }
 #pragma unroll
       for (int k2 = 0; k2 < D; ++k2) {
         if (k2 > k) break;
@@ -535,6 +561,15 @@ __device__ __noinline__ bool ldlt_psd_df(const View& A, double neg_rel) {
   DF tr{0.0f, 0.0f};
 #pragma unroll
   for (int i = 0; i < n; ++i) tr = df_add(tr, df_at(A, lp(i, i)));
+  // the factorisation forms no squares: only a trace far from 1 (2^+-60) is
+  // brought to [1, 2) first, so that pivots and reciprocals stay normal (the
+  // test does not depend on the scale)
+  if (tr.h > 0.0f && isfinite(tr.h) && abs(ilogbf(tr.h)) > 60) {
+    df_scale_unit<n * (n + 1) / 2>(A);
+    tr = DF{0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < n; ++i) tr = df_add(tr, df_at(A, lp(i, i)));
+  }
   if (!(tr.h > 0.0f) || !isfinite(tr.h)) return false;
   const float tau = (float)(neg_rel / n) * tr.h;
 #pragma unroll 1
@@ -559,6 +594,144 @@ __device__ __noinline__ bool ldlt_psd_df(const View& A, double neg_rel) {
     }
   }
   return true;
+}
+__device__ __forceinline__ double df_to_double(DF x) { return (double)x.h + (double)x.l; }
+// sqrt(x), x > 0: the FP32 root corrected by its exact remainder (FMA)
+__device__ __forceinline__ DF df_sqrt(DF x) {
+  const float r = __fsqrt_rn(x.h);
+  const float rem = __fadd_rn(__fmaf_rn(-r, r, x.h), x.l);
+  return df_fast_two_sum(r, __fmul_rn(rem, __fmul_rn(0.5f, __frcp_rn(r))));
+}
+
+// Cascaded double-float sum (Ogita, Rump & Oishi, "Accurate sum and dot
+// product", Sum2 / Dot2): the high parts add with one FP32 addition per term,
+// the two-sum errors and the terms' low parts collect in a second FP32
+// accumulator; one normalisation at the end.  As accurate as a double-float
+// sum, with one dependent addition per term on the critical path.
+struct DFAcc {
+  float h = 0.0f, l = 0.0f;
+  __device__ __forceinline__ void add(DF x) {
+    const float s = __fadd_rn(h, x.h), bb = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(x.h, bb));
+    l = __fadd_rn(l, __fadd_rn(err, x.l));
+    h = s;
+  }
+  __device__ __forceinline__ DF result() const {
+    const DF r = df_two_sum(h, l);
+    return df_fast_two_sum(r.h, r.l);
+  }
+};
+
+// span_tridiag in double-float on the double-float H_r that span_form_df left
+// in A: the same Householder steps, the reflectors, tau and the tridiagonal
+// then converted to FP64 (A and R as span_tridiag leaves them), so phase 2
+// runs unchanged.  Each step is backward stable with unit roundoff about
+// 2^-47, so the tridiagonal's eigenvalues lie within about n 2^-47 ||H_r||
+// of H_r's.  The scaling and the inertia count run in FP64 as before.
+template <int D>
+__device__ __noinline__ int span_tridiag_df(const View& A, const View& R, double* tn_out, double neg_rel) {
+  constexpr int n = 3 * D;
+  constexpr int NP = n * (n + 1) / 2;
+  // largest entry in [1, 2); the reflector pairs (v, tau) do not depend on
+  // the scale, the tridiagonal is scaled back as it is stored
+  const double unscale = (double)df_scale_unit<NP>(A);
+#pragma unroll 1
+  for (int k = 0; k < n - 2; ++k) {
+    R[k] = df_to_double(df_at(A, lp(k, k))) * unscale;
+    const DF x0 = df_at(A, lp(k + 1, k));
+    DFAcc sacc;
+#pragma unroll 2
+    for (int i = k + 2; i < n; ++i) {
+      const DF a = df_at(A, lp(i, k));
+      sacc.add(df_mul(a, a));
+    }
+    const DF sigma = sacc.result();
+    // a column below the subdiagonal at 2^-50 of the largest entry or less
+    // (below the double-float rounding) is taken as zero, as the FP64
+    // version takes an exact zero: no reflection
+    if (sigma.h < 7.8886091e-31f /* 2^-100 */) {
+      R[n + k] = df_to_double(x0) * unscale;
+      df_at(A, lp(k, k)) = DF{0.0f, 0.0f};
+      continue;
+    }
+    const DF nrm = df_sqrt(df_add(df_mul(x0, x0), sigma));
+    const DF alpha = x0.h >= 0.0f ? df_neg(nrm) : nrm;
+    const DF v0 = df_add(x0, df_neg(alpha));
+    const DF r2 = df_rcp(df_add(df_mul(v0, v0), sigma));
+    const DF t{2.0f * r2.h, 2.0f * r2.l};
+    R[n + k] = df_to_double(alpha) * unscale;
+    df_at(A, lp(k, k)) = t;
+    df_at(A, lp(k + 1, k)) = v0;
+    // p_i = t sum_j A(i, j) v_j over the trailing block, into R[2n + i]
+#pragma unroll 1
+    for (int i = k + 1; i < n; ++i) {
+      DFAcc acc;
+      const int ri = i * (i + 1) / 2;
+#pragma unroll 2
+      for (int j = k + 1; j <= i; ++j) acc.add(df_mul(df_at(A, ri + j), df_at(A, j * (j + 1) / 2 + k)));
+#pragma unroll 2
+      for (int j = i + 1; j < n; ++j) acc.add(df_mul(df_at(A, j * (j + 1) / 2 + i), df_at(A, j * (j + 1) / 2 + k)));
+      df_at(R, 2 * n + i) = df_norm(df_mul(t, acc.result()));
+    }
+    DFAcc vacc;
+#pragma unroll 2
+    for (int i = k + 1; i < n; ++i) vacc.add(df_mul(df_at(A, i * (i + 1) / 2 + k), df_at(R, 2 * n + i)));
+    const DF vp = vacc.result();
+    const DF K = df_norm(df_mul(DF{0.5f * t.h, 0.5f * t.l}, vp));
+#pragma unroll 1
+    for (int i = k + 1; i < n; ++i) {  // w = p - K v
+      DF& w = df_at(R, 2 * n + i);
+      w = df_add(w, df_neg(df_mul(K, df_at(A, i * (i + 1) / 2 + k))));
+    }
+#pragma unroll 1
+    for (int i = k + 1; i < n; ++i) {  // A -= v w^T + w v^T
+      const DF vi = df_at(A, i * (i + 1) / 2 + k), wi = df_at(R, 2 * n + i);
+      const int ri = i * (i + 1) / 2;
+#pragma unroll 2
+      for (int j = k + 1; j <= i; ++j) {
+        DF& a = df_at(A, ri + j);
+        DFAcc u;
+        u.h = a.h;
+        u.l = a.l;
+        u.add(df_neg(df_mul(vi, df_at(R, 2 * n + j))));
+        u.add(df_neg(df_mul(wi, df_at(A, j * (j + 1) / 2 + k))));
+        a = u.result();
+      }
+    }
+  }
+  R[n - 2] = df_to_double(df_at(A, lp(n - 2, n - 2))) * unscale;
+  R[n + n - 2] = df_to_double(df_at(A, lp(n - 1, n - 2))) * unscale;
+  R[n - 1] = df_to_double(df_at(A, lp(n - 1, n - 1))) * unscale;
+  R[2 * n - 1] = 0.0;
+  // the reflectors and tau to FP64 in place (the other entries are not read again)
+#pragma unroll 1
+  for (int e = 0; e < NP; ++e) A[e] = df_to_double(df_at(A, e));
+
+  // scale to ||T|| <= 1; e^2 -> R[2n..3n)
+  double tn = 0.0;
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    const double r = fabs(R[i]) + fabs(R[n + i]) + (i > 0 ? fabs(R[n + i - 1]) : 0.0);
+    tn = fmax(tn, r);
+  }
+  *tn_out = tn;
+  if (!(tn > 0.0) || !isfinite(tn)) return isfinite(tn) ? 0 : -1;
+  const double itn = 1.0 / tn;
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    const double ds = R[i] * itn, es = R[n + i] * itn;
+    R[i] = ds;
+    R[n + i] = es;
+    R[2 * n + i] = es * es;
+  }
+  return sturm<n>(R, -neg_rel);
+}
+
+template <int D, class Tab>
+__device__ __noinline__ int span_phase1_df(const Tab& tab, const View& A, const View& R, double* tn_out,
+                                           double neg_rel) {
+  span_form_df<D>(tab, A);
+  return span_tridiag_df<D>(A, R, tn_out, neg_rel);
 }
 #endif  // __CUDACC__
 

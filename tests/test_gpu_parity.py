@@ -322,6 +322,71 @@ def test_newton_step_fp64(case, orc):
     assert rel(to_n3(C) - pat.C, oC - pat.C) < 1e-9
 
 
+@pytest.mark.parametrize("border_path", [0, 1], ids=["warp", "thread"])
+def test_double_float_projection_fp64(case, orc, border_path):
+    """The projection's PSD test and phase 1 in double-float arithmetic (pairs
+    of FP32 numbers, about 48 bits) in an FP64 context: with and without the
+    PSD test, the projected span Hessians match the oracle's Jacobi
+    projection to 1e-12 and the FP64 arithmetic's result to 1e-12 (border
+    path 1 runs the border class through the same thread-per-span phases
+    with D = 8), and the Newton step reaches the oracle's positions at the
+    FP64 step's bounds."""
+    pat, prob, ctx = case
+    C = ctx.to_device(pat.C)
+    out = {}
+    try:
+        ctx.set_border_path(border_path)
+        for df in (0, 1):
+            ctx.set_proj_arith(df)
+            for mode in (0, 2):
+                ctx.set_psd_test(mode)
+                out[df, mode] = ctx.span_terms(C, project=True)[2].double().cpu().numpy()
+        ctx.set_psd_test(2)
+        ctx.set_proj_arith(1)
+        sc = orc.Scene.from_patch(pat, project=True)
+        oC, orep = orc.newton_step(prob, sc, pat.C, pat.Chat, solver=0 if pat.n_cp <= 4096 else 1, pcg_tol=1e-14)
+        Cs = ctx.to_device(pat.C)
+        rep = ctx.newton_step(Cs, ctx.to_device(pat.Chat))
+    finally:
+        ctx.set_proj_arith(0)
+        ctx.set_psd_test(2)
+        ctx.set_border_path(0)
+    _, _, oH = prob.span_eval_projected(pat.C, True)
+    errs = {k: rel(v, oH) for k, v in out.items()}
+    print(f"{pat.name}: border path {border_path}, vs oracle (arith, psd mode): "
+          + ", ".join(f"{k}: {e:.1e}" for k, e in errs.items())
+          + f"; double-float vs FP64 {rel(out[1, 2], out[0, 2]):.1e}")
+    assert max(errs.values()) < 1e-12
+    assert rel(out[1, 2], out[0, 2]) < 1e-12 and rel(out[1, 0], out[0, 0]) < 1e-12
+    assert rep.status == 0 and rep.alpha == orep.alpha
+    width = np.ptp(pat.rest, axis=0).max()
+    assert np.abs(to_n3(Cs) - oC).max() <= 1e-10 * width
+
+
+def test_double_float_projection_fp32():
+    """In an FP32 context (double-float by default) the FP32 certificate in
+    front of the double-float PSD test changes nothing, bit for bit; against
+    the FP64 arithmetic the projected span Hessians differ at the FP32
+    storage's rounding only, on a state with many indefinite spans."""
+    pat = inputs.config_wrinkle(1, 64, 0.25)
+    with bsc.context_for_patch(pat, precision=bsc.FP32) as ctx:
+        C = ctx.to_device(pat.C)
+        H = {}
+        for df in (1, 0):
+            ctx.set_proj_arith(df)
+            for mode in (1, 2):
+                ctx.set_psd_test(mode)
+                H[df, mode] = ctx.span_terms(C, project=True)[2]
+                if df == 1 and mode == 2:
+                    nneg = ctx.projection_stats()[0]
+        assert torch.equal(H[1, 1], H[1, 2]) and torch.equal(H[0, 1], H[0, 2])
+        e = rel(H[1, 2].double().cpu().numpy(), H[0, 2].double().cpu().numpy())
+        print(f"wrinkle 64x64 FP32: {int((nneg > 0).sum())} of {pat.n_spans} spans projected; "
+              f"double-float vs FP64 arithmetic {e:.1e}")
+        assert int((nneg > 0).sum()) > pat.n_spans // 50
+        assert e < 1e-6
+
+
 def test_deterministic_bitwise(case):
     pat, prob, ctx = case
     C = ctx.to_device(pat.C)

@@ -480,10 +480,11 @@ def run_gpu(args):
                     "launch_ms_source": "solve phase of bsc_phase_times (rhs, block-Jacobi inverses and the PCG "
                                         "launch, CUDA events on the launching stream)",
                     "peak_source": hbm_src,
-                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one k_pcg launch (two-pass "
+                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one k_pcg launch (three-pass "
                                       "form, symmetric layout) of the 512x512 wrinkle field "
                                       "(profiles/k_pcg_wrinkle512_fp32.md), scaled by control points x iterations "
-                                      "to this launch; null for another form or layout, or once the kernel changed"}
+                                      "to this launch (a lower bound above 512x512: the vectors leave L2); null "
+                                      "for another form or layout, or once the kernel changed"}
         roof_proj = {"kernel": "SPD projection (k_proj_pf: FP32 certificate; k_proj_p0, k_proj_p1, k_proj_p2, "
                                "k_proj_corr, k_project_ring: FP64)",
                      "psd_counts": {"interior_spans": psd_counts[0], "fp64_tested": psd_counts[1],
@@ -875,14 +876,14 @@ def measure_learned(bsc, np, torch, flush, seeds=(1_000_000, 1_000_001, 1_000_00
 # field (every projection launch of four steps, tuning applied from a plain
 # run; profiles/k_proj_psd_wrinkle512_fp32.md), keyed by the autotuner's border
 # path and phase-2 variant and by a hash of the projection sources it was taken
-# with.  Border path 0, variant 0, per step: ring (with its PSD test) 12.1 +
-# FP32 certificate 101.2 + FP64 test 98.6 + p1 43.8 + p2 67.0 + corrections
-# 386.1 MB = 708.9 MB.
-PROJECTION_TRAFFIC_HASH = "320999ddda0c2a4f"
-PROJECTION_TRAFFIC = {("wrinkle512", True, 0, 0): 708.9e6,
+# with.  Border path 3, variant 0, per step: border certificate and test 7.2 +
+# failing border spans 5.8 + FP32 certificate 101.2 + double-float test 93.0 +
+# p1 43.8 + p2 66.2 + corrections 386.1 MB = 703.2 MB.
+PROJECTION_TRAFFIC_HASH = "5842105465480ff7"
+PROJECTION_TRAFFIC = {("wrinkle512", True, 3, 0): 703.2e6,
                       # the 512x512 capture scaled by the span count (1,044,484 / 260,100): every
                       # projection kernel's traffic is per span (classes and failing shares alike)
-                      ("wrinkle1024", True, 0, 0): 708.9e6 * 1044484 / 260100}
+                      ("wrinkle1024", True, 3, 0): 703.2e6 * 1044484 / 260100}
 PROJECTION_SOURCES = ("k_project.cu", "proj_core.cuh", "k_project_ring.cu")
 # Executed FP64 work of the projection kernels of one drape step (border path 2,
 # phase-2 variant 0), from the same kind of capture with the metrics
@@ -903,15 +904,16 @@ def projection_executed(workload, fp32, tuning, launch_ms, sm_mhz, num_sms):
             "fp64_pipe_busy": cycles / (num_sms * launch_ms * 1e-3 * sm_mhz * 1e6)}
 
 
-# DRAM bytes (read + write) of one k_pcg launch (two-pass form, symmetric
-# matrix layout, FP32) on the 512x512 wrinkle field, 32 iterations: 3.999 GB
-# read + 0.452 GB written (profiles/k_pcg_wrinkle512_fp32.md), i.e. 530.6 B
-# per control point and iteration; it scales with both where K (0.47 KB per
-# control point) does not fit the 129 MB L2, so from 512x512 up.  Keyed by a
-# hash of the solver source, the form and the layout.
-PCG_TRAFFIC_PER_CP_ITER = 4.451e9 / (32 * 262144)
-PCG_TRAFFIC_HASH = "ddd6b7a6ebab236b"
-PCG_TRAFFIC_FORM = 2
+# DRAM bytes (read + write) of one k_pcg launch (three-pass form, symmetric
+# matrix layout, FP32) on the 512x512 wrinkle field, 32 iterations: 3.933 GB
+# read + 0.137 GB written (metrics-only capture, profiles/k_pcg_wrinkle512_fp32.md),
+# i.e. 485.2 B per control point and iteration.  K (0.47 KB per control point)
+# is about the L2's size there and the vectors mostly stay in L2, so the figure
+# scaled by control points x iterations to 1024x1024 is a lower bound.  Keyed
+# by a hash of the solver sources, the form and the layout.
+PCG_TRAFFIC_PER_CP_ITER = 4.0705e9 / (32 * 262144)
+PCG_TRAFFIC_HASH = "8e1f937dcdb4bbe0"
+PCG_TRAFFIC_FORM = 0
 PCG_TRAFFIC_WORKLOADS = ("wrinkle512", "wrinkle1024")
 # the solver kernels and the product rows they inline
 PCG_SOURCES = ("k_solve.cu", "bsc_internal.cuh")

@@ -437,20 +437,15 @@ __device__ __forceinline__ void block_jacobi_at(int N, int al, const T* __restri
 
 // Streaming load of a matrix entry: K is read once per product (an entry at
 // most twice, by its row and, transposed, by its neighbour's) and is far
-// larger than L1, so its lines do not allocate there and L1 keeps the
-// gathered vector entries, each read by up to 25 rows.  A cache hint only:
-// the value is that of a plain load.  (An L2 evict-first policy on top was
-// slower, measured.)
-__device__ __forceinline__ float ld_stream(const float* p) {
-  float v;
-  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ double ld_stream(const double* p) {
-  double v;
-  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
-  return v;
-}
+// larger than L1, so its lines are cached in L2 only (ld.global.cg) and L1
+// keeps the gathered vector entries, each read by up to 25 rows.  A cache
+// hint only: the value is that of a plain load.  The built-in leaves the
+// compiler free to schedule these loads around the solver's stores, which
+// inline-PTX loads with the same caching did not (same-GPU A/B at 1024x1024:
+// solve 7.10 ms with the PTX form, 6.36 ms with this one; an L2 evict-first
+// policy on top was slower still).
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcg(p); }
 
 // Row alpha (patch-local index) of y = K x in the element type T; K and x
 // already point at the patch's first control point, N is the plane stride.

@@ -905,14 +905,14 @@ def projection_executed(workload, fp32, tuning, launch_ms, sm_mhz, num_sms):
 
 
 # DRAM bytes (read + write) of one k_pcg launch (three-pass form, symmetric
-# matrix layout, FP32) on the 512x512 wrinkle field, 32 iterations: 3.933 GB
-# read + 0.137 GB written (metrics-only capture, profiles/k_pcg_wrinkle512_fp32.md),
-# i.e. 485.2 B per control point and iteration.  K (0.47 KB per control point)
+# matrix layout, FP32) on the 512x512 wrinkle field, 32 iterations: 3.689 GB
+# read + 0.448 GB written (metrics-only capture, profiles/k_pcg_wrinkle512_fp32.md),
+# i.e. 493 B per control point and iteration.  K (0.47 KB per control point)
 # is about the L2's size there and the vectors mostly stay in L2, so the figure
 # scaled by control points x iterations to 1024x1024 is a lower bound.  Keyed
 # by a hash of the solver sources, the form and the layout.
-PCG_TRAFFIC_PER_CP_ITER = 4.0705e9 / (32 * 262144)
-PCG_TRAFFIC_HASH = "8e1f937dcdb4bbe0"
+PCG_TRAFFIC_PER_CP_ITER = 4.137e9 / (32 * 262144)
+PCG_TRAFFIC_HASH = "7074a97bc3177eaf"
 PCG_TRAFFIC_FORM = 0
 PCG_TRAFFIC_WORKLOADS = ("wrinkle512", "wrinkle1024")
 # the solver kernels and the product rows they inline

@@ -316,6 +316,12 @@ bsc_status bsc_set_p2_variant(bsc_ctx* ctx, int variant);
  *     eigenvalue above sigma / 2, so the span keeps its Hessian without the
  *     FP64 test, which would have passed it too.  Only the spans the
  *     certificate leaves open go through the FP64 test.
+ * The border spans (order 24) are tested too whenever the mode is not 0:
+ * the warp-per-span paths (bsc_set_border_path 0, 2, 3) form H_r with one
+ * column per lane and, in mode 2, certify in FP32 first (the same argument
+ * with n = 24), then run the FP64 test; path 1 runs the FP64 test alone.
+ * The "FP64 test" of the thread-per-span kernels runs in double-float when
+ * bsc_set_proj_arith selects it (the default of FP32 contexts).
  * The projected matrix is the same in modes 1 and 2 bit for bit, and the
  * same as in mode 0 up to eigenvalues of size tau.  bsc_autotune keeps the
  * fastest mode for the state it is given.  Errors: BSC_ERR_INVALID_ARG for

@@ -498,6 +498,10 @@ def run_gpu(args):
                      "peak_source": "GB300 FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x "
                                     "2.07 GHz = 1.26 TFLOP/s (nominal 1.25); no FP64 entry in the measured peaks",
                      "frac_of_dfma_microbenchmark": achieved_tflops / FP64_DFMA_MEASURED_TFLOPS,
+                     "arithmetic": ("PSD test and phase 1 of the thread-per-span kernels in double-float (pairs of "
+                                    "FP32) on the FP32 pipe, the eigenpair phase and the border warps' test in "
+                                    "FP64; the algorithmic FP64 flops of all of it are counted against the FP64 "
+                                    "peak") if prec == bsc.FP32 else "FP64 throughout",
                      "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of the projection launches "
                                        "of one step (ncu capture summarised in profiles/), null when no capture "
                                        "of the current kernels exists for this workload",

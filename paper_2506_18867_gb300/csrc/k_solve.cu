@@ -233,14 +233,22 @@ __global__ void __launch_bounds__(BLOCK) k_pcg(PcgArgs<T> A) {
       if (FORM == 2) {
         const T tb = (T)beta;
         for (int al = tid; al < Np; al += stride) {
+          // the row's own q and p are loaded before its stencil product, so
+          // their DRAM latency overlaps the matrix loads
+          T qo[3], po[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            qo[c] = qv[c * N + al];
+            po[c] = pv[c * N + al];
+          }
           T y[3];
           if (SYM) spmv_row_sym<T>(nu, nv, N, al, K, zv, y);
           else spmv_row<T>(nu, nv, N, al, K, zv, y);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const int k = c * N + al;
-            const T q_ = y[c] + tb * qv[k];
-            const T p_ = zv[k] + tb * pv[k];
+            const T q_ = y[c] + tb * qo[c];
+            const T p_ = zv[k] + tb * po[c];
             qv[k] = q_;
             pv[k] = p_;
             l_pq += (double)p_ * (double)q_;

@@ -452,13 +452,16 @@ __device__ __forceinline__ DF& df_at(const View& A, int i) { return *reinterpret
 // Scales the NP double-float entries of A by the power of two that brings the
 // largest to [1, 2) (exact; FP32's exponent range is that of the scaled
 // problem, so squares and reciprocals of small entries stay normal) and
-// returns the inverse scale (1 for a zero matrix).
+// returns the inverse scale (1 when it leaves A unscaled).
 template <int NP>
 __device__ __forceinline__ float df_scale_unit(const View& A) {
   float mx = 0.0f;
 #pragma unroll 1
   for (int e = 0; e < NP; ++e) mx = fmaxf(mx, fabsf(df_at(A, e).h));
-  if (!(mx > 0.0f) || !isfinite(mx)) return 1.0f;
+  // a zero, non-finite or vanishing matrix (largest entry below 2^-100,
+  // whose scale factor could overflow FP32) stays as it is: its columns fall
+  // below the no-reflection threshold, as exact zeros do in FP64
+  if (!(mx >= 7.8886091e-31f) || !isfinite(mx)) return 1.0f;
   const int ex = ilogbf(mx);
   const float sc = ldexpf(1.0f, -ex);
 #pragma unroll 1

@@ -10,7 +10,10 @@
 //      far (for re-orthogonalisation inside clusters).
 // The span Hessian in HBM is corrected in place, P = H - sum lam w w^T over
 // the negative eigenpairs.  __host__ __device__ so the same code runs on the
-// host for checks.
+// host for checks.  The PSD test and phase 1 also come in double-float
+// versions (device only: span_form_df, ldlt_psd_df, span_tridiag_df), pairs
+// of FP32 numbers on the FP32 pipe, which GB300 runs many times faster than
+// its FP64 pipe; phase 2 stays FP64.
 #pragma once
 
 #include <math.h>
